@@ -1,0 +1,194 @@
+/*
+ * nolsm.h — C ABI of the NOLSM density step on one GPU (libnolsm.so).
+ *
+ * The non-orthogonal local submatrix method (arXiv 2205.12182, Section II,
+ * "Overview of the Problem"): for every column block C_b of the sparse,
+ * non-orthogonal one-particle Hamiltonian H0 and overlap S, gather the dense
+ * submatrices T_b(H0), T_b(S) on the rows where the combined pattern of the
+ * block's columns is non-zero (step 1), evaluate
+ *     T_b(D) = 1/2 (I - sign(T_b(S)^-1 T_b(H0) - mu I)) T_b(S)^-1      (Eq. 8)
+ * with a Newton-Schulz-type sign iteration (Eq. 6) (step 2), and write the
+ * block's own columns back into a sparse D with the input's pattern (step 3).
+ * The chemical potential mu is set so that Tr(D S) equals the electron count
+ * (Section V-A), and the band energy is Tr(D H0) (Eq. 4).
+ *
+ * Conventions for every call:
+ *  - Functions return nolsm_status; no C++ exception crosses the ABI.  After an
+ *    error the context is sticky-failed (every later call returns the same code)
+ *    until nolsm_build_submatrices succeeds again; nolsm_last_error() says why.
+ *  - Work is ordered on the CUDA stream given to nolsm_create.  Calls that return
+ *    host scalars (nolsm_set_mu, nolsm_band_energy, nolsm_sign_batch statistics)
+ *    synchronise that stream; the others only enqueue.
+ *  - The caller owns every buffer it passes.  Device-resident H0/S values must
+ *    stay valid and unchanged until the next nolsm_build_submatrices or
+ *    nolsm_destroy (the context reads them again for the band energy); host-
+ *    resident inputs are copied.  The context owns its submatrix, factor,
+ *    iterate and scratch buffers and frees them in nolsm_destroy.
+ *  - Matrices are square, symmetric, and H0 and S share one CSR pattern:
+ *    int64 row pointers, int32 column indices ascending within each row,
+ *    float64 values.  The pattern must be structurally symmetric and hold the
+ *    full diagonal.
+ */
+#ifndef NOLSM_H
+#define NOLSM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NOLSM_ABI_VERSION 1
+
+typedef enum nolsm_status {
+  NOLSM_OK = 0,
+  NOLSM_EINVAL = 1,      /* bad argument, size or pattern */
+  NOLSM_ENOMEM = 2,      /* device or host allocation failed */
+  NOLSM_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+  NOLSM_ENOTPD = 4,      /* a submatrix T_b(S) is not positive definite */
+  NOLSM_ENOCONV = 5,     /* ||X^2 - I||_F above tolerance after max_iter */
+  NOLSM_EBRACKET = 6,    /* N(mu) does not bracket the electron count */
+  NOLSM_ETIMEOUT = 7,    /* a bounded device-side wait ran out */
+  NOLSM_ENOTBUILT = 8,   /* call needs nolsm_build_submatrices / nolsm_sign_batch first */
+  NOLSM_ENONFINITE = 9   /* NaN or Inf met in the inputs or an iterate */
+} nolsm_status;
+
+typedef enum nolsm_memory {
+  NOLSM_MEM_DEVICE = 0,  /* pointer is device memory of the context's GPU */
+  NOLSM_MEM_HOST = 1     /* pointer is host memory (pinned or pageable) */
+} nolsm_memory;
+
+typedef enum nolsm_precision {
+  /* Sign iteration with FP32 operands and FP32 accumulation (SIMT). */
+  NOLSM_PREC_FP32 = 1,
+  /* FP16 operands, FP32 accumulation on the tensor cores (tcgen05, TMEM);
+   * the own-column slab gets the final Newton-Schulz steps in FP32. */
+  NOLSM_PREC_MIXED_FP16 = 2,
+  /* As MIXED_FP16 with BF16 operands (an accuracy/throughput variant). */
+  NOLSM_PREC_MIXED_BF16 = 3
+} nolsm_precision;
+
+typedef enum nolsm_bounds {
+  NOLSM_BOUNDS_GERSHGORIN = 0,  /* Gershgorin discs of A0 = L^-1 T(H0) L^-T */
+  NOLSM_BOUNDS_LANCZOS = 1,     /* Lanczos extreme Ritz values widened by their residuals */
+  NOLSM_BOUNDS_LEARNED = 2      /* learned predictor (needs mlp weights), guarded by Gershgorin */
+} nolsm_bounds;
+
+typedef enum nolsm_chol_precision {
+  NOLSM_CHOL_FP64 = 0,          /* Cholesky factor and its inverse in FP64 */
+  NOLSM_CHOL_FP32 = 1           /* both in FP32 (faster on parts with a slow FP64 unit) */
+} nolsm_chol_precision;
+
+/* One CSR matrix (see the conventions above). */
+typedef struct nolsm_csr {
+  int64_t n;               /* dimension N */
+  int64_t nnz;             /* stored entries */
+  const int64_t* row_ptr;  /* n+1 entries, row_ptr[0] = 0, row_ptr[n] = nnz */
+  const int32_t* col;      /* nnz column indices, ascending within a row */
+  const double* val;       /* nnz values */
+  int32_t memory;          /* nolsm_memory of row_ptr, col and val */
+} nolsm_csr;
+
+typedef struct nolsm_options {
+  int32_t precision;       /* nolsm_precision (default MIXED_FP16) */
+  int32_t bounds;          /* nolsm_bounds (default GERSHGORIN) */
+  int32_t chol_precision;  /* nolsm_chol_precision (default FP64) */
+  int32_t scaled;          /* 1: scaled Newton-Schulz (Chen & Chow 2014), 0: Eq. 6 as written */
+  double sign_tol;         /* stop when ||X^2 - I||_F <= sign_tol; <= 0 picks the precision's default */
+  int32_t max_iter;        /* matrix iterations per sign evaluation (default 100) */
+  int32_t refine_iters;    /* FP32 Newton-Schulz steps on the own-column slab (0..3, default 1) */
+  double spin_factor;      /* electrons per orbital: N_e = spin_factor Tr(DS), E = spin_factor Tr(DH0) (default 2) */
+  double lower_bound;      /* scaled iteration: lower bound on |eig(X_0)| when bounds give none (default 1e-3) */
+  double alpha_margin;     /* relative safety margin on the spectral radius bound (default 0.02) */
+  int64_t wait_budget;     /* bound on every device-side spin wait, in polls (default 1<<22) */
+  const char* mlp_path;    /* weights of the learned bound predictor, or NULL */
+} nolsm_options;
+
+/* Statistics of the last sign evaluation. */
+typedef struct nolsm_sign_stats {
+  double mu;               /* chemical potential of the evaluation */
+  double n_electrons;      /* spin_factor * Tr(D S) over all blocks' own columns */
+  double band_energy;      /* spin_factor * Tr(D H0) from the same block traces */
+  double max_residual;     /* max over blocks of ||X^2 - I||_F at exit of the matrix iteration */
+  double iters_avg;        /* matrix iterations (each = two matrix products) per block */
+  int32_t iters_min;
+  int32_t iters_max;
+  int32_t n_blocks;
+  int32_t n_restarted;     /* blocks restarted with the Gershgorin bound after residual growth */
+  double flops_paper;      /* 2 n_b^3 per product, true n_b (the paper's count, Section V-B) */
+  double flops_executed;   /* products as executed on padded tiles */
+  double ms;               /* device time of the evaluation (CUDA events) */
+} nolsm_sign_stats;
+
+typedef struct nolsm_ctx nolsm_ctx;
+
+/* Fill *opt with the defaults listed above. */
+nolsm_status nolsm_default_options(nolsm_options* opt);
+
+/* Create a context on the current CUDA device; cuda_stream is a cudaStream_t (NULL =
+ * legacy default stream).  opt may be NULL for defaults.  *ctx is set on success. */
+nolsm_status nolsm_create(nolsm_ctx** ctx, const nolsm_options* opt, void* cuda_stream);
+
+/* Step 1 of the submatrix method and everything that does not depend on mu
+ * (Section II; Eq. 8).  For block b with own columns blk_cols[blk_ptr[b]..blk_ptr[b+1])
+ * the index set I_b is every row holding a stored entry in one of those columns,
+ * unioned with extra_idx[extra_ptr[b]..extra_ptr[b+1]) when extra_ptr is not NULL
+ * (a geometric neighbourhood).  blk_* and extra_* are host arrays.  The call
+ * gathers T_b(H0) and T_b(S), factors T_b(S) = L L^T, forms A0 = L^-1 T_b(H0) L^-T
+ * (so that sign(T_b(S)^-1 T_b(H0) - mu) = L^-T sign(A0 - mu) L^T) and its spectral
+ * bounds.  n_b = |I_b| must not exceed 4096.  Errors: EINVAL (sizes, pattern,
+ * n_b), ENOTPD, ENONFINITE, ENOMEM, ECUDA. */
+nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const nolsm_csr* S,
+                                     int32_t n_blocks, const int32_t* blk_ptr, const int32_t* blk_cols,
+                                     const int32_t* extra_ptr, const int32_t* extra_idx);
+
+/* Step 2 at one chemical potential (Eq. 8 with the iteration of Eq. 6): for every
+ * block, X -> sign(A0 - mu I), then the block traces of D S and D H0 over its own
+ * columns.  Fills *out when out is not NULL (synchronises).  Errors: ENOTBUILT,
+ * ENOCONV, ETIMEOUT, ENONFINITE, ECUDA. */
+nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out);
+
+/* Chemical potential by bisection (Section V-A: the mu that makes the system
+ * charge neutral).  Each step evaluates nolsm_sign_batch at the bracket midpoint;
+ * it stops when |N(mu) - n_electrons| <= tol_n * n_electrons, when the bracket is
+ * below 1e-10 Ha, or after max_steps.  mu_lo >= mu_hi selects the bracket
+ * [min lower bound, max upper bound] over the blocks.  Outputs may be NULL.
+ * Errors: EBRACKET (the bracket does not contain the count), plus those of
+ * nolsm_sign_batch. */
+nolsm_status nolsm_set_mu(nolsm_ctx* ctx, double n_electrons, double mu_lo, double mu_hi, double tol_n,
+                          int32_t max_steps, double* mu_out, double* n_out, int32_t* steps_out);
+
+/* Step 3 at the mu of the last sign evaluation: D_b[:, C_b] = L^-T 1/2 (I - X) L^-1[:, C_b]
+ * written into d_val (nnz values on the H0/S pattern; entries (i, c) with c an
+ * own column of exactly one block; entries of columns owned by no block are 0).
+ * memory says where d_val lives; d_val may be NULL to keep D inside the context
+ * only (nolsm_band_energy uses it).  Errors: ENOTBUILT, EINVAL, ECUDA. */
+nolsm_status nolsm_density(nolsm_ctx* ctx, double* d_val, int32_t memory);
+
+/* Band energy spin_factor * Tr(D H0) = spin_factor * sum_ij D_ij H0_ji (Eq. 4) of the D
+ * assembled by the last nolsm_density, accumulated in FP64.  Synchronises. */
+nolsm_status nolsm_band_energy(nolsm_ctx* ctx, double* e_out);
+
+/* Number of blocks, and n_b / |C_b| of block b (host query of the build). */
+nolsm_status nolsm_block_info(const nolsm_ctx* ctx, int32_t b, int32_t* n_b, int32_t* n_cols);
+
+/* Index set I_b of block b copied to idx_out (host, n_b entries). */
+nolsm_status nolsm_block_index_set(const nolsm_ctx* ctx, int32_t b, int32_t* idx_out);
+
+/* Per-block spectral bounds [lo, hi] of A0 used by the iteration (host arrays of n_blocks). */
+nolsm_status nolsm_block_bounds(const nolsm_ctx* ctx, double* lo, double* hi);
+
+/* Per-block Newton-Schulz iteration counts of the last sign evaluation (host array). */
+nolsm_status nolsm_block_iters(const nolsm_ctx* ctx, int32_t* iters);
+
+/* Message of the last error of ctx (never NULL; "" when none).  ctx may be NULL. */
+const char* nolsm_last_error(const nolsm_ctx* ctx);
+
+/* Release every resource of ctx (NULL is a no-op). */
+void nolsm_destroy(nolsm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NOLSM_H */
