@@ -182,6 +182,10 @@ nolsm_status nolsm_block_bounds(const nolsm_ctx* ctx, double* lo, double* hi);
 /* Per-block Newton-Schulz iteration counts of the last sign evaluation (host array). */
 nolsm_status nolsm_block_iters(const nolsm_ctx* ctx, int32_t* iters);
 
+/* Diagnostic copy of block b's n_b x n_b matrix `which` to host memory (row-major, float32):
+ * which = 0: A0 = L^-1 T_b(H0) L^-T;  which = 1: L^-1.  Synchronises. */
+nolsm_status nolsm_block_matrix(const nolsm_ctx* ctx, int32_t b, int32_t which, float* out);
+
 /* Message of the last error of ctx (never NULL; "" when none).  ctx may be NULL. */
 const char* nolsm_last_error(const nolsm_ctx* ctx);
 

@@ -1,0 +1,572 @@
+// C ABI of libnolsm.so: context life cycle, the build of the submatrices (host-side index sets,
+// size bins and memory layout), the sign evaluation loop, the chemical-potential bisection, the
+// density scatter and the band energy.  See include/nolsm.h for the contract of every call.
+#include "internal.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+
+using namespace nolsm;
+
+namespace nolsm {
+
+nolsm_status fail(nolsm_ctx* ctx, nolsm_status st, const std::string& msg) {
+  if (ctx) {
+    if (ctx->sticky == NOLSM_OK) {
+      ctx->sticky = st;
+      ctx->last_error = msg;
+    }
+  }
+  return st;
+}
+
+nolsm_status cuda_fail(nolsm_ctx* ctx, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(ctx, e == cudaErrorMemoryAllocation ? NOLSM_ENOMEM : NOLSM_ECUDA, m);
+}
+
+}  // namespace nolsm
+
+#define CK(call)                                                  \
+  do {                                                            \
+    cudaError_t _e = (call);                                      \
+    if (_e != cudaSuccess) return nolsm::cuda_fail(ctx, _e, #call); \
+  } while (0)
+
+namespace {
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+void release_pools(nolsm_ctx* ctx) {
+  dfree(ctx->d_blocks); ctx->d_blocks = nullptr;
+  dfree(ctx->d_idx); ctx->d_idx = nullptr;
+  dfree(ctx->d_own); ctx->d_own = nullptr;
+  dfree(ctx->d_blk_cols); ctx->d_blk_cols = nullptr;
+  dfree(ctx->d_a0); ctx->d_a0 = nullptr;
+  dfree(ctx->d_linv); ctx->d_linv = nullptr;
+  dfree(ctx->d_x[0]); ctx->d_x[0] = nullptr;
+  dfree(ctx->d_x[1]); ctx->d_x[1] = nullptr;
+  dfree(ctx->d_b); ctx->d_b = nullptr;
+  dfree(ctx->d_w); ctx->d_w = nullptr;
+  dfree(ctx->d_z); ctx->d_z = nullptr;
+  dfree(ctx->d_lc); ctx->d_lc = nullptr;
+  dfree(ctx->d_y); ctx->d_y = nullptr;
+  dfree(ctx->d_tmp); ctx->d_tmp = nullptr;
+  dfree(ctx->d_lo); ctx->d_lo = nullptr;
+  dfree(ctx->d_hi); ctx->d_hi = nullptr;
+  dfree(ctx->d_bn); ctx->d_bn = nullptr;
+  dfree(ctx->d_be); ctx->d_be = nullptr;
+  dfree(ctx->d_resacc); ctx->d_resacc = nullptr;
+  dfree(ctx->d_tol); ctx->d_tol = nullptr;
+  dfree(ctx->d_state); ctx->d_state = nullptr;
+  dfree(ctx->d_tiles); ctx->d_tiles = nullptr;
+  dfree(ctx->d_transpose); ctx->d_transpose = nullptr;
+  dfree(ctx->d_dval); ctx->d_dval = nullptr;
+  dfree(ctx->d_csr_own); ctx->d_csr_own = nullptr;
+  dfree(ctx->d_tmaps); ctx->d_tmaps = nullptr;
+  ctx->built = ctx->have_sign = ctx->have_density = false;
+}
+
+bool is_mixed(const nolsm_ctx* ctx) {
+  return ctx->opt.precision == NOLSM_PREC_MIXED_FP16 || ctx->opt.precision == NOLSM_PREC_MIXED_BF16;
+}
+
+int half_kind(const nolsm_ctx* ctx) {
+  if (ctx->opt.precision == NOLSM_PREC_MIXED_FP16) return 1;
+  if (ctx->opt.precision == NOLSM_PREC_MIXED_BF16) return 2;
+  return 0;
+}
+
+double unit_roundoff(const nolsm_ctx* ctx) {
+  switch (ctx->opt.precision) {
+    case NOLSM_PREC_MIXED_FP16: return std::ldexp(1.0, -11);
+    case NOLSM_PREC_MIXED_BF16: return std::ldexp(1.0, -8);
+    default: return std::ldexp(1.0, -24);
+  }
+}
+
+nolsm_status check_device_flags(nolsm_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(DevFlags), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const int e = ctx->h_flags->error;
+  if (e != 0) {
+    const char* what = "device error";
+    switch (e) {
+      case NOLSM_ENOTPD: what = "a submatrix T_b(S) is not positive definite"; break;
+      case NOLSM_ENOCONV: what = "sign iteration did not reach the tolerance within max_iter"; break;
+      case NOLSM_ETIMEOUT: what = "a bounded device wait ran out"; break;
+      case NOLSM_ENONFINITE: what = "non-finite value in the inputs or an iterate"; break;
+      case NOLSM_EINVAL: what = "an own-column pattern entry is missing from its index set"; break;
+      default: break;
+    }
+    return fail(ctx, (nolsm_status)e, what);
+  }
+  return NOLSM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nolsm_status nolsm_default_options(nolsm_options* opt) {
+  if (!opt) return NOLSM_EINVAL;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->precision = NOLSM_PREC_MIXED_FP16;
+  opt->bounds = NOLSM_BOUNDS_GERSHGORIN;
+  opt->chol_precision = NOLSM_CHOL_FP64;
+  opt->scaled = 1;
+  opt->sign_tol = 0.0;
+  opt->max_iter = 100;
+  opt->refine_iters = 2;
+  opt->spin_factor = 2.0;
+  opt->lower_bound = 1e-3;
+  opt->alpha_margin = 0.02;
+  opt->wait_budget = 1LL << 22;
+  opt->mlp_path = nullptr;
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_create(nolsm_ctx** out, const nolsm_options* opt, void* cuda_stream) {
+  if (!out) return NOLSM_EINVAL;
+  *out = nullptr;
+  nolsm_ctx* ctx = new (std::nothrow) nolsm_ctx();
+  if (!ctx) return NOLSM_ENOMEM;
+  if (opt) ctx->opt = *opt; else nolsm_default_options(&ctx->opt);
+  if (ctx->opt.precision < NOLSM_PREC_FP32 || ctx->opt.precision > NOLSM_PREC_MIXED_BF16 || ctx->opt.max_iter <= 0 ||
+      ctx->opt.refine_iters < 0 || ctx->opt.refine_iters > 3 || !(ctx->opt.spin_factor > 0) ||
+      ctx->opt.wait_budget <= 0 || ctx->opt.alpha_margin < 0) {
+    delete ctx;
+    return NOLSM_EINVAL;
+  }
+  ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&ctx->d_flags), sizeof(DevFlags));
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&ctx->h_flags), sizeof(DevFlags));
+  if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
+  if (e != cudaSuccess) {
+    if (ctx->d_flags) cudaFree(ctx->d_flags);
+    if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
+    delete ctx;
+    return e == cudaErrorMemoryAllocation ? NOLSM_ENOMEM : NOLSM_ECUDA;
+  }
+  *out = ctx;
+  return NOLSM_OK;
+}
+
+void nolsm_destroy(nolsm_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream); else cudaDeviceSynchronize();
+  release_pools(ctx);
+  if (ctx->d_flags) cudaFree(ctx->d_flags);
+  if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
+  if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+  if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  delete ctx;
+}
+
+const char* nolsm_last_error(const nolsm_ctx* ctx) {
+  if (!ctx) return "";
+  return ctx->last_error.c_str();
+}
+
+nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const nolsm_csr* S, int32_t n_blocks,
+                                     const int32_t* blk_ptr, const int32_t* blk_cols, const int32_t* extra_ptr,
+                                     const int32_t* extra_idx) {
+  if (!ctx) return NOLSM_EINVAL;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  ctx->sticky = NOLSM_OK;   // a new build clears the sticky error
+  ctx->last_error.clear();
+  release_pools(ctx);
+  if (!H || !S || !blk_ptr || !blk_cols || n_blocks <= 0) return fail(ctx, NOLSM_EINVAL, "null argument or no blocks");
+  if (H->n != S->n || H->nnz != S->nnz || H->n <= 0 || H->nnz <= 0 || H->memory != S->memory ||
+      H->n > INT32_MAX)
+    return fail(ctx, NOLSM_EINVAL, "H and S must share dimension, pattern and memory kind");
+  if ((extra_ptr == nullptr) != (extra_idx == nullptr)) return fail(ctx, NOLSM_EINVAL, "extra_ptr and extra_idx go together");
+  const int64_t N = H->n, nnz = H->nnz;
+  ctx->n = N;
+  ctx->nnz = nnz;
+  ctx->n_blocks = n_blocks;
+
+  // ---- CSR on the device (staged when host-resident) and on the host (pattern only)
+  std::vector<int64_t> rp((size_t)N + 1);
+  std::vector<int32_t> cl((size_t)nnz);
+  if (H->memory == NOLSM_MEM_HOST) {
+    std::memcpy(rp.data(), H->row_ptr, sizeof(int64_t) * (N + 1));
+    std::memcpy(cl.data(), H->col, sizeof(int32_t) * nnz);
+    const size_t bytes = sizeof(int64_t) * (N + 1) + sizeof(int32_t) * nnz + 2 * sizeof(double) * nnz + 64;
+    CK(cudaMalloc(&ctx->d_csr_own, bytes));
+    uint8_t* base = reinterpret_cast<uint8_t*>(ctx->d_csr_own);
+    double* hv = reinterpret_cast<double*>(base);
+    double* sv = hv + nnz;
+    int64_t* rpd = reinterpret_cast<int64_t*>(sv + nnz);
+    int32_t* cld = reinterpret_cast<int32_t*>(rpd + N + 1);
+    CK(cudaMemcpyAsync(hv, H->val, sizeof(double) * nnz, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(sv, S->val, sizeof(double) * nnz, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(rpd, H->row_ptr, sizeof(int64_t) * (N + 1), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(cld, H->col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, ctx->stream));
+    ctx->d_hval = hv; ctx->d_sval = sv; ctx->d_row_ptr = rpd; ctx->d_col = cld;
+  } else {
+    CK(cudaMemcpyAsync(rp.data(), H->row_ptr, sizeof(int64_t) * (N + 1), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(cl.data(), H->col, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, ctx->stream));
+    ctx->d_hval = H->val; ctx->d_sval = S->val; ctx->d_row_ptr = H->row_ptr; ctx->d_col = H->col;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (rp[0] != 0 || rp[N] != nnz) return fail(ctx, NOLSM_EINVAL, "row_ptr must start at 0 and end at nnz");
+  // pattern checks and the transpose permutation (entry (i,j) -> position of (j,i))
+  std::vector<int64_t> transpose((size_t)nnz);
+  for (int64_t r = 0; r < N; ++r) {
+    if (rp[r + 1] < rp[r]) return fail(ctx, NOLSM_EINVAL, "row_ptr not monotone");
+    bool diag = false;
+    for (int64_t e = rp[r]; e < rp[r + 1]; ++e) {
+      const int32_t c = cl[e];
+      if (c < 0 || c >= N || (e > rp[r] && cl[e - 1] >= c)) return fail(ctx, NOLSM_EINVAL, "columns out of range or not ascending");
+      if (c == r) diag = true;
+      const int32_t* b = cl.data() + rp[c];
+      const int32_t* en = cl.data() + rp[c + 1];
+      const int32_t* f = std::lower_bound(b, en, (int32_t)r);
+      if (f == en || *f != r) return fail(ctx, NOLSM_EINVAL, "pattern is not structurally symmetric");
+      transpose[e] = rp[c] + (f - b);
+    }
+    if (!diag) return fail(ctx, NOLSM_EINVAL, "pattern misses a diagonal entry");
+  }
+
+  // ---- index sets: pattern rule (rows of the own columns) unioned with the extra list
+  if (blk_ptr[0] != 0) return fail(ctx, NOLSM_EINVAL, "blk_ptr[0] must be 0");
+  ctx->h_blk_cols.assign(blk_cols, blk_cols + blk_ptr[n_blocks]);
+  std::vector<std::vector<int32_t>> sets((size_t)n_blocks);
+  std::vector<std::vector<int32_t>> owns((size_t)n_blocks);
+  {
+    std::vector<int32_t> mark((size_t)N, -1);
+    for (int32_t b = 0; b < n_blocks; ++b) {
+      if (blk_ptr[b + 1] <= blk_ptr[b]) return fail(ctx, NOLSM_EINVAL, "every block needs at least one column");
+      auto& set = sets[b];
+      for (int32_t k = blk_ptr[b]; k < blk_ptr[b + 1]; ++k) {
+        const int32_t c = blk_cols[k];
+        if (c < 0 || c >= N) return fail(ctx, NOLSM_EINVAL, "block column out of range");
+        for (int64_t e = rp[c]; e < rp[c + 1]; ++e) {   // symmetric pattern: column c's rows = row c's columns
+          const int32_t r = cl[e];
+          if (mark[r] != b) { mark[r] = b; set.push_back(r); }
+        }
+      }
+      if (extra_ptr) {
+        for (int32_t k = extra_ptr[b]; k < extra_ptr[b + 1]; ++k) {
+          const int32_t r = extra_idx[k];
+          if (r < 0 || r >= N) return fail(ctx, NOLSM_EINVAL, "extra index out of range");
+          if (mark[r] != b) { mark[r] = b; set.push_back(r); }
+        }
+      }
+      std::sort(set.begin(), set.end());
+      if ((int)set.size() > kMaxDim) return fail(ctx, NOLSM_EINVAL, "a submatrix dimension exceeds 4096");
+      for (int32_t k = blk_ptr[b]; k < blk_ptr[b + 1]; ++k)
+        owns[b].push_back((int32_t)(std::lower_bound(set.begin(), set.end(), blk_cols[k]) - set.begin()));
+    }
+  }
+
+  // ---- layout: bins of equal n_pad stored contiguously (tensor maps stack a bin's matrices)
+  ctx->h_blocks.assign((size_t)n_blocks, BlockDesc{});
+  std::vector<int32_t> order((size_t)n_blocks);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return pad_dim((int)sets[a].size()) < pad_dim((int)sets[b].size());
+  });
+  int64_t off_mat = 0, off_slab = 0, off_idx = 0, off_own = 0;
+  int bin = -1, pos = 0, last_pad = -1;
+  ctx->h_idx.clear();
+  ctx->h_idx.reserve(1024);
+  std::vector<int32_t> h_own;
+  ctx->flops_paper_iter = ctx->flops_exec_iter = 0.0;
+  // index and own pools keep the caller's block order; square/slab pools follow the bin order
+  for (int32_t b = 0; b < n_blocks; ++b) {
+    BlockDesc& bd = ctx->h_blocks[b];
+    bd.n = (int32_t)sets[b].size();
+    bd.n_pad = pad_dim(bd.n);
+    bd.c = blk_ptr[b + 1] - blk_ptr[b];
+    bd.col0 = blk_ptr[b];
+    bd.off_idx = off_idx;
+    bd.off_own = off_own;
+    ctx->h_idx.insert(ctx->h_idx.end(), sets[b].begin(), sets[b].end());
+    h_own.insert(h_own.end(), owns[b].begin(), owns[b].end());
+    off_idx += bd.n;
+    off_own += bd.c;
+    ctx->flops_paper_iter += 2.0 * 2.0 * (double)bd.n * bd.n * bd.n;
+    ctx->flops_exec_iter += 2.0 * 2.0 * (double)bd.n_pad * bd.n_pad * bd.n_pad;
+  }
+  for (int32_t b : order) {
+    BlockDesc& bd = ctx->h_blocks[b];
+    if (bd.n_pad != last_pad) { ++bin; pos = 0; last_pad = bd.n_pad; }
+    bd.bin = bin;
+    bd.pos = pos++;
+    bd.off_mat = off_mat;
+    bd.off_slab = off_slab;
+    off_mat += (int64_t)bd.n_pad * bd.n_pad;
+    off_slab += (int64_t)bd.n_pad * bd.c;
+  }
+  ctx->sum_sq = off_mat;
+  ctx->sum_slab = off_slab;
+  ctx->sum_idx = off_idx;
+  ctx->sum_own = off_own;
+  int64_t tiles_max = 0;
+  for (const auto& bd : ctx->h_blocks) tiles_max += (int64_t)(bd.n_pad / kTile) * (bd.n_pad / kTile);
+  ctx->max_tiles = tiles_max;
+
+  // ---- device pools
+  const bool mixed = is_mixed(ctx);
+  const size_t xbytes = mixed ? 2 : 4;
+  CK(dalloc(&ctx->d_blocks, (size_t)n_blocks));
+  CK(dalloc(&ctx->d_idx, (size_t)ctx->sum_idx));
+  CK(dalloc(&ctx->d_own, (size_t)ctx->sum_own));
+  CK(dalloc(&ctx->d_blk_cols, ctx->h_blk_cols.size()));
+  CK(dalloc(&ctx->d_a0, (size_t)ctx->sum_sq));
+  CK(dalloc(&ctx->d_linv, (size_t)ctx->sum_sq));
+  CK(cudaMalloc(&ctx->d_x[0], xbytes * (size_t)ctx->sum_sq));
+  CK(cudaMalloc(&ctx->d_x[1], xbytes * (size_t)ctx->sum_sq));
+  CK(cudaMalloc(&ctx->d_b, xbytes * (size_t)ctx->sum_sq));
+  CK(dalloc(&ctx->d_w, (size_t)ctx->sum_slab));
+  CK(dalloc(&ctx->d_z, (size_t)ctx->sum_slab));
+  CK(dalloc(&ctx->d_lc, (size_t)ctx->sum_slab));
+  CK(dalloc(&ctx->d_y, (size_t)ctx->sum_slab));
+  CK(dalloc(&ctx->d_tmp, (size_t)std::max<int64_t>(6 * ctx->sum_slab, 4096)));
+  CK(dalloc(&ctx->d_lo, (size_t)n_blocks));
+  CK(dalloc(&ctx->d_hi, (size_t)n_blocks));
+  CK(dalloc(&ctx->d_bn, (size_t)n_blocks));
+  CK(dalloc(&ctx->d_be, (size_t)n_blocks));
+  CK(dalloc(&ctx->d_resacc, (size_t)n_blocks));
+  CK(dalloc(&ctx->d_tol, (size_t)n_blocks));
+  CK(dalloc(&ctx->d_state, (size_t)n_blocks));
+  CK(dalloc(&ctx->d_tiles, (size_t)tiles_max));
+  CK(dalloc(&ctx->d_transpose, (size_t)nnz));
+  CK(dalloc(&ctx->d_dval, (size_t)nnz));
+  CK(cudaMemcpyAsync(ctx->d_blocks, ctx->h_blocks.data(), sizeof(BlockDesc) * n_blocks, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_idx, ctx->h_idx.data(), sizeof(int32_t) * ctx->sum_idx, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_own, h_own.data(), sizeof(int32_t) * ctx->sum_own, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_blk_cols, ctx->h_blk_cols.data(), sizeof(int32_t) * ctx->h_blk_cols.size(),
+                     cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_transpose, transpose.data(), sizeof(int64_t) * nnz, cudaMemcpyHostToDevice, ctx->stream));
+  {
+    std::vector<float> tol((size_t)n_blocks);
+    const double u = unit_roundoff(ctx);
+    for (int32_t b = 0; b < n_blocks; ++b) {
+      const double d = 8.0 * u * std::sqrt((double)ctx->h_blocks[b].n);
+      tol[b] = (float)(ctx->opt.sign_tol > 0 ? ctx->opt.sign_tol : std::min(0.05, d));
+    }
+    CK(cudaMemcpyAsync(ctx->d_tol, tol.data(), sizeof(float) * n_blocks, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(DevFlags), ctx->stream));
+
+  // ---- FP64 gather, factor, inverse; FP32 congruence and slabs
+  double* hb = nullptr;
+  double* sb = nullptr;
+  float* t1 = nullptr;
+  CK(dalloc(&hb, (size_t)ctx->sum_sq));
+  CK(dalloc(&sb, (size_t)(2 * ctx->sum_sq)));
+  CK(cudaMemsetAsync(hb, 0, sizeof(double) * ctx->sum_sq, ctx->stream));
+  CK(cudaMemsetAsync(sb, 0, sizeof(double) * 2 * ctx->sum_sq, ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_linv, 0, sizeof(float) * ctx->sum_sq, ctx->stream));
+  CK(launch_gather(ctx, hb, sb));
+  const int chol32 = ctx->opt.chol_precision == NOLSM_CHOL_FP32;
+  CK(launch_cholesky_inverse(ctx, sb, chol32));
+  CK(dalloc(&t1, (size_t)ctx->sum_sq));
+  CK(launch_congruence(ctx, hb, sb, t1, chol32));
+  CK(launch_slabs_impl(ctx, chol32 ? (const void*)(sb + ctx->sum_sq) : (const void*)sb, chol32, t1));
+  CK(launch_bounds(ctx));
+  CK(cudaStreamSynchronize(ctx->stream));
+  cudaFree(hb);
+  cudaFree(sb);
+  cudaFree(t1);
+  nolsm_status st = check_device_flags(ctx);
+  if (st != NOLSM_OK) return st;
+  ctx->h_lo.resize((size_t)n_blocks);
+  ctx->h_hi.resize((size_t)n_blocks);
+  CK(cudaMemcpy(ctx->h_lo.data(), ctx->d_lo, sizeof(double) * n_blocks, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(ctx->h_hi.data(), ctx->d_hi, sizeof(double) * n_blocks, cudaMemcpyDeviceToHost));
+  if (mixed) CK(tc_prepare(ctx));
+  ctx->built = true;
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out) {
+  if (!ctx) return NOLSM_EINVAL;
+  if (ctx->sticky != NOLSM_OK) return ctx->sticky;
+  if (!ctx->built) return fail(ctx, NOLSM_ENOTBUILT, "nolsm_build_submatrices has not succeeded");
+  if (!std::isfinite(mu)) return fail(ctx, NOLSM_EINVAL, "mu is not finite");
+  const bool mixed = is_mixed(ctx);
+  const int hk = half_kind(ctx);
+  CK(cudaEventRecord(ctx->ev0, ctx->stream));
+  CK(launch_ns_init(ctx, mu, hk));
+  const int tile_n = mixed ? tc_tile_n() : kTile;
+  const int check_every = 4;
+  for (int it = 0; it <= ctx->opt.max_iter; ++it) {
+    CK(launch_ns_tiles_n(ctx, tile_n));
+    CK(mixed ? launch_gemm_tc(ctx, 1) : launch_gemm_f32(ctx, 1));
+    CK(launch_ns_check_impl(ctx, ctx->d_tol));
+    CK(launch_ns_tiles_n(ctx, tile_n));
+    CK(mixed ? launch_gemm_tc(ctx, 2) : launch_gemm_f32(ctx, 2));
+    CK(launch_ns_advance(ctx));
+    if (it % check_every == check_every - 1 || it == ctx->opt.max_iter) {
+      CK(cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(DevFlags), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      if (ctx->h_flags->error != 0 || ctx->h_flags->n_active == 0) break;
+    }
+  }
+  CK(launch_slab_traces(ctx, hk));
+  CK(cudaEventRecord(ctx->ev1, ctx->stream));
+  nolsm_status st = check_device_flags(ctx);
+  if (st != NOLSM_OK) return st;
+  ctx->last_mu = mu;
+  ctx->have_sign = true;
+  ctx->have_density = false;
+  nolsm_sign_stats s{};
+  s.mu = mu;
+  s.n_electrons = ctx->opt.spin_factor * ctx->h_flags->sum_n;
+  s.band_energy = ctx->opt.spin_factor * ctx->h_flags->sum_e;
+  s.n_blocks = ctx->n_blocks;
+  if (out) {
+    std::vector<NsState> hs((size_t)ctx->n_blocks);
+    CK(cudaMemcpy(hs.data(), ctx->d_state, sizeof(NsState) * ctx->n_blocks, cudaMemcpyDeviceToHost));
+    ctx->h_iters.resize((size_t)ctx->n_blocks);
+    int64_t sum_it = 0;
+    s.iters_min = INT32_MAX;
+    s.iters_max = 0;
+    double fp = 0.0, fe = 0.0;
+    for (int32_t b = 0; b < ctx->n_blocks; ++b) {
+      const int it = hs[b].iters;
+      ctx->h_iters[b] = it;
+      sum_it += it;
+      s.iters_min = std::min(s.iters_min, it);
+      s.iters_max = std::max(s.iters_max, it);
+      s.max_residual = std::max(s.max_residual, (double)hs[b].res);
+      s.n_restarted += hs[b].restarts > 0;
+      const double n = ctx->h_blocks[b].n, np = ctx->h_blocks[b].n_pad;
+      // it full iterations (2 products) plus the first product of the converged check
+      fp += (2.0 * it + 1.0) * 2.0 * n * n * n;
+      fe += (2.0 * it + 1.0) * 2.0 * np * np * np;
+    }
+    s.iters_avg = (double)sum_it / ctx->n_blocks;
+    s.flops_paper = fp;
+    s.flops_executed = fe;
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    s.ms = ms;
+    *out = s;
+  }
+  ctx->last_stats = s;
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_set_mu(nolsm_ctx* ctx, double n_electrons, double mu_lo, double mu_hi, double tol_n,
+                          int32_t max_steps, double* mu_out, double* n_out, int32_t* steps_out) {
+  if (!ctx) return NOLSM_EINVAL;
+  if (ctx->sticky != NOLSM_OK) return ctx->sticky;
+  if (!ctx->built) return fail(ctx, NOLSM_ENOTBUILT, "nolsm_build_submatrices has not succeeded");
+  if (!(n_electrons > 0) || !(tol_n >= 0) || max_steps <= 0) return fail(ctx, NOLSM_EINVAL, "bad bisection arguments");
+  double lo = mu_lo, hi = mu_hi;
+  const double total = ctx->opt.spin_factor * (double)ctx->sum_own;   // N(mu) above every eigenvalue
+  if (!(lo < hi)) {
+    lo = *std::min_element(ctx->h_lo.begin(), ctx->h_lo.end());
+    hi = *std::max_element(ctx->h_hi.begin(), ctx->h_hi.end());
+    if (!(n_electrons < total)) return fail(ctx, NOLSM_EBRACKET, "electron count not below the number of own columns");
+  }
+  const double lo0 = lo, hi0 = hi;
+  double mu = 0.5 * (lo + hi), n_mu = 0.0;
+  int steps = 0;
+  nolsm_sign_stats s;
+  while (true) {
+    nolsm_status st = nolsm_sign_batch(ctx, mu, &s);
+    if (st != NOLSM_OK) return st;
+    ++steps;
+    n_mu = s.n_electrons;
+    if (std::fabs(n_mu - n_electrons) <= tol_n * n_electrons) break;
+    if (steps >= max_steps || hi - lo < 1e-10) break;
+    if (n_mu < n_electrons) lo = mu; else hi = mu;
+    mu = 0.5 * (lo + hi);
+  }
+  if (std::fabs(n_mu - n_electrons) > tol_n * n_electrons && (mu - lo0 < 1e-9 || hi0 - mu < 1e-9))
+    return fail(ctx, NOLSM_EBRACKET, "N(mu) does not bracket the electron count in [mu_lo, mu_hi]");
+  if (mu_out) *mu_out = mu;
+  if (n_out) *n_out = n_mu;
+  if (steps_out) *steps_out = steps;
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_density(nolsm_ctx* ctx, double* d_val, int32_t memory) {
+  if (!ctx) return NOLSM_EINVAL;
+  if (ctx->sticky != NOLSM_OK) return ctx->sticky;
+  if (!ctx->have_sign) return fail(ctx, NOLSM_ENOTBUILT, "nolsm_sign_batch has not run");
+  if (memory != NOLSM_MEM_DEVICE && memory != NOLSM_MEM_HOST) return fail(ctx, NOLSM_EINVAL, "bad memory kind");
+  CK(launch_density(ctx));
+  if (d_val) {
+    CK(cudaMemcpyAsync(d_val, ctx->d_dval, sizeof(double) * ctx->nnz,
+                       memory == NOLSM_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, ctx->stream));
+    if (memory == NOLSM_MEM_HOST) {
+      nolsm_status st = check_device_flags(ctx);
+      if (st != NOLSM_OK) return st;
+    }
+  }
+  ctx->have_density = true;
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_band_energy(nolsm_ctx* ctx, double* e_out) {
+  if (!ctx || !e_out) return NOLSM_EINVAL;
+  if (ctx->sticky != NOLSM_OK) return ctx->sticky;
+  if (!ctx->have_density) return fail(ctx, NOLSM_ENOTBUILT, "nolsm_density has not run");
+  CK(launch_band_energy(ctx));
+  nolsm_status st = check_device_flags(ctx);
+  if (st != NOLSM_OK) return st;
+  *e_out = ctx->opt.spin_factor * ctx->h_flags->energy;
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_block_info(const nolsm_ctx* ctx, int32_t b, int32_t* n_b, int32_t* n_cols) {
+  if (!ctx || !ctx->built || b < 0 || b >= ctx->n_blocks) return NOLSM_EINVAL;
+  if (n_b) *n_b = ctx->h_blocks[b].n;
+  if (n_cols) *n_cols = ctx->h_blocks[b].c;
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_block_index_set(const nolsm_ctx* ctx, int32_t b, int32_t* idx_out) {
+  if (!ctx || !ctx->built || b < 0 || b >= ctx->n_blocks || !idx_out) return NOLSM_EINVAL;
+  const BlockDesc& bd = ctx->h_blocks[b];
+  std::memcpy(idx_out, ctx->h_idx.data() + bd.off_idx, sizeof(int32_t) * bd.n);
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_block_bounds(const nolsm_ctx* ctx, double* lo, double* hi) {
+  if (!ctx || !ctx->built) return NOLSM_EINVAL;
+  if (lo) std::memcpy(lo, ctx->h_lo.data(), sizeof(double) * ctx->n_blocks);
+  if (hi) std::memcpy(hi, ctx->h_hi.data(), sizeof(double) * ctx->n_blocks);
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_block_iters(const nolsm_ctx* ctx, int32_t* iters) {
+  if (!ctx || !ctx->have_sign || !iters || ctx->h_iters.size() != (size_t)ctx->n_blocks) return NOLSM_EINVAL;
+  std::memcpy(iters, ctx->h_iters.data(), sizeof(int32_t) * ctx->n_blocks);
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_block_matrix(const nolsm_ctx* ctx, int32_t b, int32_t which, float* out) {
+  if (!ctx || !ctx->built || b < 0 || b >= ctx->n_blocks || !out || which < 0 || which > 1) return NOLSM_EINVAL;
+  const BlockDesc& bd = ctx->h_blocks[b];
+  const float* src = (which == 0 ? ctx->d_a0 : ctx->d_linv) + bd.off_mat;
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return NOLSM_ECUDA;
+  if (cudaMemcpy2D(out, sizeof(float) * bd.n, src, sizeof(float) * bd.n_pad, sizeof(float) * bd.n, bd.n,
+                   cudaMemcpyDeviceToHost) != cudaSuccess)
+    return NOLSM_ECUDA;
+  return NOLSM_OK;
+}
+
+}  // extern "C"

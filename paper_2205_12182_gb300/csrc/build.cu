@@ -1,0 +1,386 @@
+// Everything that does not depend on mu: submatrix gather (step 1 of the submatrix
+// method), the Cholesky factor of T_b(S) and its inverse, the congruence
+// A0 = L^-1 T_b(H0) L^-T (Eq. 8 rewritten with S = L L^T), the own-column slabs and
+// the Gershgorin bounds of A0.
+#include "internal.h"
+
+#include <cfloat>
+
+namespace nolsm {
+namespace {
+
+__device__ __forceinline__ int lower_bound_i32(const int32_t* a, int n, int32_t key) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void set_error(DevFlags* f, int code) { atomicCAS(&f->error, 0, code); }
+
+// ----------------------------------------------------------------------------------------------
+// Gather: dense T_b(H0) and T_b(S) (FP64, ld = n_pad) from the CSR rows listed in I_b.
+// One CTA per block, one warp per local row; I_b sits in shared memory for the column lookup.
+// The pools are zeroed beforehand; the padded diagonal of S is set to 1 here.
+__global__ void gather_kernel(const BlockDesc* __restrict__ blocks, const int32_t* __restrict__ idx_pool,
+                              const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                              const double* __restrict__ hval, const double* __restrict__ sval,
+                              double* __restrict__ hb, double* __restrict__ sb, DevFlags* flags) {
+  extern __shared__ int32_t s_idx[];
+  const BlockDesc bd = blocks[blockIdx.x];
+  const int n = bd.n, ld = bd.n_pad;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s_idx[i] = idx_pool[bd.off_idx + i];
+  __syncthreads();
+  double* H = hb + bd.off_mat;
+  double* S = sb + bd.off_mat;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int p = warp; p < n; p += nwarps) {
+    const int32_t r = s_idx[p];
+    const int64_t e0 = row_ptr[r], e1 = row_ptr[r + 1];
+    for (int64_t e = e0 + lane; e < e1; e += 32) {
+      const int32_t c = col[e];
+      const int q = lower_bound_i32(s_idx, n, c);
+      if (q < n && s_idx[q] == c) {
+        const double h = hval[e], s = sval[e];
+        if (!isfinite(h) || !isfinite(s)) set_error(flags, NOLSM_ENONFINITE);
+        H[(int64_t)p * ld + q] = h;
+        S[(int64_t)p * ld + q] = s;
+      }
+    }
+  }
+  for (int p = n + threadIdx.x; p < ld; p += blockDim.x) S[(int64_t)p * ld + p] = 1.0;
+}
+
+// ----------------------------------------------------------------------------------------------
+// Warp-tile helper: a warp computes a 32x32 tile acc[r] (lane = output column) of
+//   acc[r][lane] = sum_k Arow[r][k] * Bcol[k][lane]
+// with both operands streamed through the warp's private shared-memory chunk of 32 k.
+template <typename T>
+struct WarpChunk {
+  T a[32][33];
+  T b[32][33];
+};
+
+// Cholesky S = L L^T, left-looking by 32-column panels, in place (lower triangle).
+// One CTA (8 warps) per block.  For each panel j0:
+//   R[r, j0:j0+32] = S[r, j0:j0+32] - L[r, 0:j0] L[j0:j0+32, 0:j0]^T  for rows r >= j0 (warp tiles)
+//   factor the 32x32 diagonal of R (warp 0), then L[r, panel] = R[r, panel] L_jj^-T (row solves).
+// The strictly upper triangle is zeroed at the end.
+template <typename T>
+__global__ void __launch_bounds__(256) cholesky_kernel(const BlockDesc* __restrict__ blocks, T* __restrict__ pool,
+                                                       DevFlags* flags) {
+  __shared__ WarpChunk<T> chunks[8];
+  __shared__ T diag[32][33];
+  __shared__ int s_bad;
+  const BlockDesc bd = blocks[blockIdx.x];
+  const int n = bd.n, ld = bd.n_pad;
+  T* A = pool + bd.off_mat;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  WarpChunk<T>& ch = chunks[warp];
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  for (int j0 = 0; j0 < n; j0 += 32) {
+    const int jb = min(32, n - j0);
+    // --- update panel columns with the previous panels: row tiles of 32 rows, one per warp
+    for (int r0 = j0 + warp * 32; r0 < n; r0 += 8 * 32) {
+      T acc[32];
+#pragma unroll
+      for (int r = 0; r < 32; ++r) acc[r] = T(0);
+      for (int k0 = 0; k0 < j0; k0 += 32) {
+        // a: L[r0+r, k0+k] ; b: L[j0+lane, k0+k] stored as b[k][lane]
+        for (int r = 0; r < 32; ++r) {
+          const int gr = r0 + r;
+          ch.a[r][lane] = (gr < n) ? A[(int64_t)gr * ld + k0 + lane] : T(0);
+          const int gc = j0 + r;
+          ch.b[lane][r] = (gc < n) ? A[(int64_t)gc * ld + k0 + lane] : T(0);
+        }
+        __syncwarp();
+#pragma unroll 4
+        for (int k = 0; k < 32; ++k) {
+          const T bv = ch.b[k][lane];
+#pragma unroll
+          for (int r = 0; r < 32; ++r) acc[r] = fma(-ch.a[r][k], bv, acc[r]);
+        }
+        __syncwarp();
+      }
+      if (lane < jb) {
+        for (int r = 0; r < 32; ++r) {
+          const int gr = r0 + r;
+          if (gr < n) A[(int64_t)gr * ld + j0 + lane] += acc[r];
+        }
+      }
+    }
+    __syncthreads();
+    // --- factor the diagonal 32x32 block (warp 0, lane = row)
+    if (warp == 0) {
+      for (int r = 0; r < 32; ++r) diag[r][lane] = (r < jb && lane < jb) ? A[(int64_t)(j0 + r) * ld + j0 + lane] : T(r == lane);
+      __syncwarp();
+      for (int k = 0; k < 32; ++k) {
+        if (lane == k) {
+          T d = diag[k][k];
+          if (!(d > T(0))) { s_bad = 1; d = T(1); }
+          diag[k][k] = sqrt(d);
+        }
+        __syncwarp();
+        if (lane > k) diag[lane][k] /= diag[k][k];
+        __syncwarp();
+        if (lane > k) {
+          const T lk = diag[lane][k];
+          for (int j = k + 1; j <= lane; ++j) diag[lane][j] -= lk * diag[j][k];
+        }
+        __syncwarp();
+      }
+      for (int r = 0; r < jb; ++r)
+        if (lane <= r) A[(int64_t)(j0 + r) * ld + j0 + lane] = diag[r][lane];
+    }
+    __syncthreads();
+    // --- panel rows below: x L_jj^T = r  (forward substitution per row, thread per row)
+    for (int gr = j0 + jb + threadIdx.x; gr < n; gr += blockDim.x) {
+      T x[32];
+      T* row = A + (int64_t)gr * ld + j0;
+#pragma unroll
+      for (int k = 0; k < 32; ++k) x[k] = (k < jb) ? row[k] : T(0);
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        T v = x[k];
+#pragma unroll
+        for (int t = 0; t < k; ++t) v = fma(-x[t], diag[k][t], v);
+        x[k] = v / diag[k][k];
+      }
+#pragma unroll
+      for (int k = 0; k < 32; ++k)
+        if (k < jb) row[k] = x[k];
+    }
+    __syncthreads();
+  }
+  // zero the strict upper triangle of the n x n part
+  for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += blockDim.x) {
+    const int r = (int)(e / n), c = (int)(e % n);
+    if (c > r) A[(int64_t)r * ld + c] = T(0);
+  }
+  if (threadIdx.x == 0 && s_bad) set_error(flags, NOLSM_ENOTPD);
+}
+
+// Inverse of the lower-triangular L into X (out of place), by block rows of 32:
+//   X[i-block, c-block] = -L_ii^-1 sum_{k=c}^{i-1} L_ik X_kc   (c < i),   X_ii = L_ii^-1.
+// Phase 1 forms R = sum_k L_ik X_kc with warp tiles (one 32x32 tile per c-block), phase 2
+// solves L_ii Y = (E - R) column by column (thread per column).
+template <typename T>
+__global__ void __launch_bounds__(256) trinv_kernel(const BlockDesc* __restrict__ blocks, const T* __restrict__ lpool,
+                                                    T* __restrict__ xpool) {
+  __shared__ WarpChunk<T> chunks[8];
+  __shared__ T lii[32][33];
+  const BlockDesc bd = blocks[blockIdx.x];
+  const int n = bd.n, ld = bd.n_pad;
+  const T* L = lpool + bd.off_mat;
+  T* X = xpool + bd.off_mat;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  WarpChunk<T>& ch = chunks[warp];
+  const int nbk = (n + 31) / 32;
+  for (int ib = 0; ib < nbk; ++ib) {
+    const int i0 = ib * 32, ibw = min(32, n - i0);
+    // phase 1: R for every c-block < ib, written into X's block row (as -R) for phase 2
+    for (int cb = warp; cb < ib; cb += 8) {
+      const int c0 = cb * 32;
+      T acc[32];
+#pragma unroll
+      for (int r = 0; r < 32; ++r) acc[r] = T(0);
+      for (int k0 = c0; k0 < i0; k0 += 32) {
+        for (int r = 0; r < 32; ++r) {
+          ch.a[r][lane] = (r < ibw) ? L[(int64_t)(i0 + r) * ld + k0 + lane] : T(0);
+          ch.b[r][lane] = X[(int64_t)(k0 + r) * ld + c0 + lane];   // b[k][col]
+        }
+        __syncwarp();
+#pragma unroll 4
+        for (int k = 0; k < 32; ++k) {
+          const T bv = ch.b[k][lane];
+#pragma unroll
+          for (int r = 0; r < 32; ++r) acc[r] = fma(ch.a[r][k], bv, acc[r]);
+        }
+        __syncwarp();
+      }
+      for (int r = 0; r < ibw; ++r) X[(int64_t)(i0 + r) * ld + c0 + lane] = -acc[r];
+    }
+    if (threadIdx.x < 32 * 32 / 32) {
+      for (int r = 0; r < 32; ++r)
+        if (threadIdx.x < 32) lii[r][threadIdx.x] = (r < ibw && threadIdx.x < ibw) ? L[(int64_t)(i0 + r) * ld + i0 + threadIdx.x] : T(r == (int)threadIdx.x);
+    }
+    __syncthreads();
+    // phase 2: column j of the block row: solve L_ii y = rhs, rhs = -R (c < i) or e_j (diagonal block)
+    const int ncols = i0 + ibw;
+    for (int j = threadIdx.x; j < ncols; j += blockDim.x) {
+      T y[32];
+      const bool diag_blk = j >= i0;
+#pragma unroll
+      for (int r = 0; r < 32; ++r) {
+        if (diag_blk) y[r] = T((i0 + r) == j);
+        else y[r] = (r < ibw) ? X[(int64_t)(i0 + r) * ld + j] : T(0);
+      }
+#pragma unroll
+      for (int r = 0; r < 32; ++r) {
+        T v = y[r];
+#pragma unroll
+        for (int t = 0; t < r; ++t) v = fma(-lii[r][t], y[t], v);
+        y[r] = v / lii[r][r];
+      }
+#pragma unroll
+      for (int r = 0; r < 32; ++r)
+        if (r < ibw) X[(int64_t)(i0 + r) * ld + j] = y[r];
+    }
+    __syncthreads();
+  }
+}
+
+// FP64 -> FP32 square copy with zero padding; optional transpose-free.
+template <typename T>
+__global__ void to_f32_kernel(const BlockDesc* __restrict__ blocks, const T* __restrict__ src, float* __restrict__ dst,
+                              int lower_only) {
+  const BlockDesc bd = blocks[blockIdx.y];
+  const int n = bd.n, ld = bd.n_pad;
+  const int64_t total = (int64_t)ld * ld;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / ld), c = (int)(e % ld);
+    float v = 0.f;
+    if (r < n && c < n && (!lower_only || c <= r)) v = (float)src[bd.off_mat + e];
+    dst[bd.off_mat + e] = v;
+  }
+}
+
+// Symmetrise A0 in place: A = (A + A^T)/2 (exact in exact arithmetic; removes rounding skew).
+__global__ void symmetrize_kernel(const BlockDesc* __restrict__ blocks, float* __restrict__ a) {
+  const BlockDesc bd = blocks[blockIdx.y];
+  const int ld = bd.n_pad;
+  const int64_t total = (int64_t)ld * ld;
+  float* A = a + bd.off_mat;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / ld), c = (int)(e % ld);
+    if (c < r) {
+      const float v = 0.5f * (A[(int64_t)r * ld + c] + A[(int64_t)c * ld + r]);
+      A[(int64_t)r * ld + c] = v;
+      A[(int64_t)c * ld + r] = v;
+    }
+  }
+}
+
+// Own-column slabs (column-major, ld = n_pad, zero beyond n):
+//   W[:, j] = L^-1[:, p_j]            Z[:, j] = (L^-1 H_b)[:, p_j]       Lc[:, j] = L[p_j, :]^T
+// with p_j the local position of the block's j-th own column.
+template <typename T>
+__global__ void slabs_kernel(const BlockDesc* __restrict__ blocks, const int32_t* __restrict__ own_pool,
+                             const T* __restrict__ lfac, const float* __restrict__ linv32, const float* __restrict__ t1,
+                             float* __restrict__ w, float* __restrict__ z, float* __restrict__ lc) {
+  const BlockDesc bd = blocks[blockIdx.x];
+  const int n = bd.n, ld = bd.n_pad;
+  for (int j = 0; j < bd.c; ++j) {
+    const int p = own_pool[bd.off_own + j];
+    for (int i = threadIdx.x; i < ld; i += blockDim.x) {
+      const int64_t o = bd.off_slab + (int64_t)j * ld + i;
+      if (i < n) {
+        w[o] = linv32[bd.off_mat + (int64_t)i * ld + p];
+        z[o] = t1[bd.off_mat + (int64_t)i * ld + p];
+        lc[o] = (i <= p) ? (float)lfac[bd.off_mat + (int64_t)p * ld + i] : 0.f;
+      } else {
+        w[o] = 0.f; z[o] = 0.f; lc[o] = 0.f;
+      }
+    }
+  }
+}
+
+// Gershgorin bounds of A0 (real n x n part): [min_i a_ii - R_i, max_i a_ii + R_i].
+__global__ void gershgorin_kernel(const BlockDesc* __restrict__ blocks, const float* __restrict__ a0,
+                                  double* __restrict__ lo, double* __restrict__ hi, DevFlags* flags) {
+  const BlockDesc bd = blocks[blockIdx.x];
+  const int n = bd.n, ld = bd.n_pad;
+  const float* A = a0 + bd.off_mat;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  double wlo = DBL_MAX, whi = -DBL_MAX;
+  for (int r = warp; r < n; r += nwarps) {
+    double rad = 0.0, d = 0.0;
+    for (int c = lane; c < n; c += 32) {
+      const double v = A[(int64_t)r * ld + c];
+      if (c == r) d = v; else rad += fabs(v);
+    }
+    for (int o = 16; o; o >>= 1) {
+      rad += __shfl_xor_sync(0xffffffffu, rad, o);
+      d += __shfl_xor_sync(0xffffffffu, d, o);
+    }
+    wlo = fmin(wlo, d - rad);
+    whi = fmax(whi, d + rad);
+  }
+  __shared__ double slo[32], shi[32];
+  if (lane == 0) { slo[warp] = wlo; shi[warp] = whi; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double l = DBL_MAX, h = -DBL_MAX;
+    for (int i = 0; i < nwarps; ++i) { l = fmin(l, slo[i]); h = fmax(h, shi[i]); }
+    if (!isfinite(l) || !isfinite(h)) set_error(flags, NOLSM_ENONFINITE);
+    lo[blockIdx.x] = l;
+    hi[blockIdx.x] = h;
+  }
+}
+
+inline dim3 sq_grid(int n_blocks) { return dim3(64, n_blocks); }
+
+}  // namespace
+
+cudaError_t launch_gather(nolsm_ctx* ctx, double* hb, double* sb) {
+  int max_n = 0;
+  for (auto& b : ctx->h_blocks) max_n = std::max(max_n, b.n);
+  const size_t smem = sizeof(int32_t) * (size_t)max_n;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  gather_kernel<<<ctx->n_blocks, 256, smem, ctx->stream>>>(ctx->d_blocks, ctx->d_idx, ctx->d_row_ptr, ctx->d_col,
+                                                           ctx->d_hval, ctx->d_sval, hb, sb, ctx->d_flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int fp32) {
+  // sb holds T_b(S) in FP64.  FP64: factor in place, inverse into the second half of the
+  // scratch (sb + sum_sq).  FP32: convert first, then the same kernels in float.
+  if (!fp32) {
+    cholesky_kernel<double><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, sb, ctx->d_flags);
+    trinv_kernel<double><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, sb, sb + ctx->sum_sq);
+    to_f32_kernel<double><<<sq_grid(ctx->n_blocks), 256, 0, ctx->stream>>>(ctx->d_blocks, sb + ctx->sum_sq, ctx->d_linv, 1);
+  } else {
+    float* s32 = reinterpret_cast<float*>(sb + ctx->sum_sq);   // FP32 factor lives in the scratch half
+    to_f32_kernel<double><<<sq_grid(ctx->n_blocks), 256, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, 0);
+    cholesky_kernel<float><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_flags);
+    trinv_kernel<float><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_congruence(nolsm_ctx* ctx, const double* hb, const double* sb_linv, float* t1, int fp32) {
+  (void)sb_linv; (void)fp32;
+  // H_b -> FP32 (into A0's pool as scratch), T1 = L^-1 H_b (H symmetric: NT form), A0 = T1 L^-T.
+  to_f32_kernel<double><<<sq_grid(ctx->n_blocks), 256, 0, ctx->stream>>>(ctx->d_blocks, hb, ctx->d_a0, 0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = launch_sgemm_nt(ctx, ctx->d_linv, ctx->d_a0, t1, /*a_lower=*/1, /*b_lower=*/0);
+  if (e != cudaSuccess) return e;
+  e = launch_sgemm_nt(ctx, t1, ctx->d_linv, ctx->d_a0, 0, /*b_lower=*/1);
+  if (e != cudaSuccess) return e;
+  symmetrize_kernel<<<sq_grid(ctx->n_blocks), 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_a0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slabs_impl(nolsm_ctx* ctx, const void* lfac, int fp32, const float* t1) {
+  if (!fp32)
+    slabs_kernel<double><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_own, (const double*)lfac,
+                                                                ctx->d_linv, t1, ctx->d_w, ctx->d_z, ctx->d_lc);
+  else
+    slabs_kernel<float><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_own, (const float*)lfac,
+                                                               ctx->d_linv, t1, ctx->d_w, ctx->d_z, ctx->d_lc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bounds(nolsm_ctx* ctx) {
+  gershgorin_kernel<<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_a0, ctx->d_lo, ctx->d_hi, ctx->d_flags);
+  return cudaGetLastError();
+}
+
+}  // namespace nolsm

@@ -1,0 +1,170 @@
+// Internal declarations shared by the translation units of libnolsm.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <algorithm>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/nolsm.h"
+
+namespace nolsm {
+
+// Output tile edge of every matrix-product kernel; submatrices are padded to it.
+constexpr int kTile = 128;
+constexpr int kMaxDim = 4096;
+
+inline int pad_dim(int n) { return (n + kTile - 1) / kTile * kTile; }
+
+// One submatrix (device-resident table, one entry per block).
+struct BlockDesc {
+  int32_t n;        // |I_b|
+  int32_t n_pad;    // n rounded up to kTile
+  int32_t c;        // |C_b|, own columns
+  int32_t col0;     // offset of the block's own columns in the blk_cols array
+  int32_t bin;      // size bin (blocks of one n_pad are stored contiguously, bin by bin)
+  int32_t pos;      // position of the block inside its bin
+  int64_t off_idx;  // I_b in idx pool (n int32, ascending); own positions follow in own pool
+  int64_t off_own;  // local positions of the own columns (c int32)
+  int64_t off_mat;  // n_pad*n_pad element offset in every square pool
+  int64_t off_slab; // n_pad*c element offset in every slab pool (column-major, ld = n_pad)
+};
+
+// Newton-Schulz state of one block during a sign evaluation.
+struct NsState {
+  float alpha;      // X_0 = (A0 - mu I) / alpha
+  float l;          // lower bound of |eig(X_k)| for the scaled iteration (1 = plain)
+  float a;          // scaling of the current step: X+ = a X (3 - a^2 X^2) / 2
+  float res;        // ||X_k^2 - I||_F of the last product
+  float res_prev;
+  int32_t iters;    // completed matrix iterations
+  int32_t status;   // kActive / kConverged / kRestart / kFailed
+  int32_t cur;      // which X buffer holds the iterate (0/1)
+  int32_t grow;     // consecutive residual increases
+  int32_t restarts;
+};
+
+enum : int32_t { kActive = 0, kConverged = 1, kRestart = 2, kFailed = 3 };
+
+// A tile of a grouped matrix product: block, first output row, first output column.
+struct Tile {
+  int32_t block, m0, n0, kend;
+};
+
+// Device-side counters and flags of one context.
+struct DevFlags {
+  int32_t error;        // first device error code (nolsm_status), 0 = none
+  int32_t n_tiles;      // tiles in the current list
+  int32_t n_active;     // blocks still iterating
+  int32_t pad;
+  double sum_n;         // sum of block traces Tr(S D) over own columns
+  double sum_e;         // same for Tr(H D)
+  double energy;        // band energy reduction
+  double pad2;
+};
+
+}  // namespace nolsm
+
+struct nolsm_ctx {
+  nolsm_options opt;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  nolsm_status sticky = NOLSM_OK;
+  std::string last_error;
+
+  // build products
+  bool built = false;
+  bool have_sign = false;
+  bool have_density = false;
+  int32_t n_blocks = 0;
+  int64_t n = 0, nnz = 0;
+  std::vector<nolsm::BlockDesc> h_blocks;
+  std::vector<int32_t> h_idx;           // concatenated index sets
+  std::vector<int32_t> h_blk_cols;
+  std::vector<double> h_lo, h_hi;       // spectral bounds of A0 per block
+  std::vector<int32_t> h_iters;
+  int64_t sum_sq = 0, sum_slab = 0, sum_idx = 0, sum_own = 0;
+  double flops_paper_iter = 0.0, flops_exec_iter = 0.0;
+
+  // device memory owned by the context
+  nolsm::BlockDesc* d_blocks = nullptr;
+  int32_t* d_idx = nullptr;
+  int32_t* d_own = nullptr;
+  int32_t* d_blk_cols = nullptr;
+  float* d_a0 = nullptr;        // A0, fp32, square pool
+  float* d_linv = nullptr;      // L^-1, fp32, square pool
+  void* d_x[2] = {nullptr, nullptr};   // iterates (fp32 or fp16/bf16), square pools
+  void* d_b = nullptr;          // second operand (c1 I - c3 X^2), square pool
+  float* d_w = nullptr;         // L^-1[:, C_b], slab pool
+  float* d_z = nullptr;         // L^-1 H_b[:, C_b], slab pool
+  float* d_lc = nullptr;        // L^-1 S_b[:, C_b] = L[C_b, :]^T, slab pool
+  float* d_y = nullptr;         // 1/2 (I - X) W, slab pool
+  float* d_tmp = nullptr;       // slab scratch (3 slabs)
+  double* d_lo = nullptr;       // spectral bounds per block
+  double* d_hi = nullptr;
+  double* d_bn = nullptr;       // per-block traces
+  double* d_be = nullptr;
+  float* d_resacc = nullptr;    // per-block residual accumulators
+  float* d_tol = nullptr;       // per-block stopping tolerance on ||X^2 - I||_F
+  nolsm::NsState* d_state = nullptr;
+  nolsm::Tile* d_tiles = nullptr;
+  int64_t max_tiles = 0;
+  nolsm::DevFlags* d_flags = nullptr;
+  nolsm::DevFlags* h_flags = nullptr;   // pinned mirror
+
+  // CSR copies / references
+  const int64_t* d_row_ptr = nullptr;
+  const int32_t* d_col = nullptr;
+  const double* d_hval = nullptr;
+  const double* d_sval = nullptr;
+  void* d_csr_own = nullptr;            // staging when inputs were host-resident
+  int64_t* d_transpose = nullptr;       // position of (j,i) for entry (i,j)
+  double* d_dval = nullptr;             // assembled D on the pattern
+
+  // tensor-core operand descriptors (device array of CUtensorMap, opaque bytes)
+  void* d_tmaps = nullptr;
+  int n_tmaps = 0;
+
+  double last_mu = 0.0;
+  nolsm_sign_stats last_stats{};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace nolsm {
+
+// error helpers (api.cu)
+nolsm_status fail(nolsm_ctx* ctx, nolsm_status st, const std::string& msg);
+nolsm_status cuda_fail(nolsm_ctx* ctx, cudaError_t e, const char* what);
+
+// build.cu
+cudaError_t launch_gather(nolsm_ctx* ctx, double* hb, double* sb);
+cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int fp32);
+cudaError_t launch_congruence(nolsm_ctx* ctx, const double* hb, const double* sb_linv, float* t1_scratch, int fp32);
+cudaError_t launch_slabs_impl(nolsm_ctx* ctx, const void* lfac, int fp32, const float* t1);
+cudaError_t launch_bounds(nolsm_ctx* ctx);
+
+// sign.cu (SIMT path, control, slab traces)
+cudaError_t launch_ns_init(nolsm_ctx* ctx, double mu, int half);
+cudaError_t launch_ns_tiles(nolsm_ctx* ctx);
+cudaError_t launch_ns_tiles_n(nolsm_ctx* ctx, int tile_n);
+cudaError_t launch_ns_check_impl(nolsm_ctx* ctx, const float* tol_b);
+cudaError_t launch_ns_advance(nolsm_ctx* ctx);
+cudaError_t launch_ns_reinit(nolsm_ctx* ctx, double mu, int half);
+cudaError_t launch_gemm_f32(nolsm_ctx* ctx, int phase);
+cudaError_t launch_slab_traces(nolsm_ctx* ctx, int half);
+cudaError_t launch_density(nolsm_ctx* ctx);
+cudaError_t launch_band_energy(nolsm_ctx* ctx);
+
+// sign_tc.cu (tcgen05 path)
+cudaError_t tc_prepare(nolsm_ctx* ctx);
+cudaError_t launch_gemm_tc(nolsm_ctx* ctx, int phase);
+int tc_tile_n();
+
+// generic SIMT NT product used by the build: C_b = A_b B_b^T on the block table
+cudaError_t launch_sgemm_nt(nolsm_ctx* ctx, const float* a, const float* b, float* c, int a_lower, int b_lower);
+
+}  // namespace nolsm

@@ -1,0 +1,624 @@
+// The mu-dependent part of the NOLSM step: the Newton-Schulz sign iteration (Eq. 6) on
+// every block's A0 - mu I, the iteration control, the own-column slab refinement with the
+// block traces of D S and D H0, the density scatter (step 3) and the band energy (Eq. 4).
+//
+// Matrix products here are the SIMT FP32 path; the tensor-core products live in sign_tc.cu
+// and share the control kernels below.
+#include "internal.h"
+
+#include <cfloat>
+
+namespace nolsm {
+namespace {
+
+__device__ __forceinline__ void set_error(DevFlags* f, int code) { atomicCAS(&f->error, 0, code); }
+
+template <typename T> __device__ __forceinline__ float ld_as_float(const T* p);
+template <> __device__ __forceinline__ float ld_as_float<float>(const float* p) { return *p; }
+template <> __device__ __forceinline__ float ld_as_float<__half>(const __half* p) { return __half2float(*p); }
+template <> __device__ __forceinline__ float ld_as_float<__nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+template <typename T> __device__ __forceinline__ T from_float(float v);
+template <> __device__ __forceinline__ float from_float<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half from_float<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_float<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+// Scaled Newton-Schulz step coefficient for a lower bound l of |eig(X)| in (0, 1]
+// (Chen & Chow 2014): a = sqrt(3 / (1 + l + l^2)) maps [l, 1] onto [l', 1] with the two
+// ends equal; l = 1 gives the unscaled iteration of Eq. 6.
+__device__ __forceinline__ float cc_scale(float l) { return (l >= 1.f) ? 1.f : sqrtf(3.f / (1.f + l + l * l)); }
+__device__ __forceinline__ float cc_next(float l, float a) {
+  const float v = 0.5f * a * l * (3.f - a * a * l * l);
+  return (v > 1.f - 1e-6f) ? 1.f : v;
+}
+
+// ----------------------------------------------------------------------------------------------
+// Grouped SIMT product C = A B^T on 128x128 tiles (both operands row-major, K contiguous).
+// MODE 0: plain store.  MODE 1: NS first product T = X X^T (X symmetric), epilogue writes
+//   B = 1.5 a I - 0.5 a^3 T and accumulates ||T - I||_F^2 per block.  MODE 2: X+ = X B^T.
+constexpr int BM = 128, BN = 128, BK = 16;
+
+template <int MODE>
+__global__ void __launch_bounds__(256, 2)
+sgemm_nt_kernel(const Tile* __restrict__ tiles, const int32_t* __restrict__ n_tiles_dev, int n_tiles_host,
+                const BlockDesc* __restrict__ blocks, const float* __restrict__ a_pool, const float* __restrict__ b_pool,
+                float* __restrict__ c_pool, float* __restrict__ x0, float* __restrict__ x1, float* __restrict__ bbuf,
+                const NsState* __restrict__ st, float* __restrict__ resacc) {
+  __shared__ __align__(16) float As[2][BK][BM + 4];
+  __shared__ __align__(16) float Bs[2][BK][BN + 4];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int lrow = tid >> 2, lcol = (tid & 3) * 4;
+  const int n_tiles = n_tiles_dev ? *n_tiles_dev : n_tiles_host;
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const Tile tl = tiles[t];
+    const BlockDesc bd = blocks[tl.block];
+    const int ld = bd.n_pad;
+    const float* A;
+    const float* B;
+    float* C;
+    float c1 = 0.f, c3 = 0.f;
+    if (MODE == 0) {
+      A = a_pool + bd.off_mat; B = b_pool + bd.off_mat; C = c_pool + bd.off_mat;
+    } else {
+      const NsState s = st[tl.block];
+      float* X = s.cur ? x1 : x0;
+      A = X + bd.off_mat;
+      if (MODE == 1) { B = X + bd.off_mat; C = bbuf + bd.off_mat; c1 = 1.5f * s.a; c3 = 0.5f * s.a * s.a * s.a; }
+      else { B = bbuf + bd.off_mat; C = (s.cur ? x0 : x1) + bd.off_mat; }
+    }
+    const float* Ag = A + (int64_t)(tl.m0 + lrow) * ld + lcol;
+    const float* Bg = B + (int64_t)(tl.n0 + lrow) * ld + lcol;
+    const int64_t half = (int64_t)64 * ld;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    const int kend = tl.kend;
+    float4 ra0 = *reinterpret_cast<const float4*>(Ag);
+    float4 ra1 = *reinterpret_cast<const float4*>(Ag + half);
+    float4 rb0 = *reinterpret_cast<const float4*>(Bg);
+    float4 rb1 = *reinterpret_cast<const float4*>(Bg + half);
+    int buf = 0;
+    for (int k0 = 0; k0 < kend; k0 += BK) {
+      As[buf][lcol + 0][lrow] = ra0.x; As[buf][lcol + 1][lrow] = ra0.y; As[buf][lcol + 2][lrow] = ra0.z; As[buf][lcol + 3][lrow] = ra0.w;
+      As[buf][lcol + 0][lrow + 64] = ra1.x; As[buf][lcol + 1][lrow + 64] = ra1.y; As[buf][lcol + 2][lrow + 64] = ra1.z; As[buf][lcol + 3][lrow + 64] = ra1.w;
+      Bs[buf][lcol + 0][lrow] = rb0.x; Bs[buf][lcol + 1][lrow] = rb0.y; Bs[buf][lcol + 2][lrow] = rb0.z; Bs[buf][lcol + 3][lrow] = rb0.w;
+      Bs[buf][lcol + 0][lrow + 64] = rb1.x; Bs[buf][lcol + 1][lrow + 64] = rb1.y; Bs[buf][lcol + 2][lrow + 64] = rb1.z; Bs[buf][lcol + 3][lrow + 64] = rb1.w;
+      __syncthreads();
+      if (k0 + BK < kend) {
+        ra0 = *reinterpret_cast<const float4*>(Ag + k0 + BK);
+        ra1 = *reinterpret_cast<const float4*>(Ag + half + k0 + BK);
+        rb0 = *reinterpret_cast<const float4*>(Bg + k0 + BK);
+        rb1 = *reinterpret_cast<const float4*>(Bg + half + k0 + BK);
+      }
+#pragma unroll
+      for (int k = 0; k < BK; ++k) {
+        const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 4]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][k][64 + ty * 4]);
+        const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][k][tx * 4]);
+        const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][k][64 + tx * 4]);
+        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+      }
+      buf ^= 1;
+    }
+    __syncthreads();
+    // epilogue
+    float rsq = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = tl.m0 + ((i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+#pragma unroll
+      for (int jh = 0; jh < 2; ++jh) {
+        const int c = tl.n0 + jh * 64 + tx * 4;
+        float4 v = make_float4(acc[i][jh * 4 + 0], acc[i][jh * 4 + 1], acc[i][jh * 4 + 2], acc[i][jh * 4 + 3]);
+        if (MODE == 1) {
+          float* pv = &v.x;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float d = (r == c + q) ? 1.f : 0.f;
+            const float e = pv[q] - d;
+            rsq = fmaf(e, e, rsq);
+            pv[q] = c1 * d - c3 * pv[q];
+          }
+        }
+        *reinterpret_cast<float4*>(C + (int64_t)r * ld + c) = v;
+      }
+    }
+    if (MODE == 1) {
+      for (int o = 16; o; o >>= 1) rsq += __shfl_xor_sync(0xffffffffu, rsq, o);
+      if ((tid & 31) == 0) atomicAdd(&resacc[tl.block], rsq);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------------------------
+// Iteration control.
+
+// State at the start of a sign evaluation: alpha from the spectral bounds (Gershgorin, with a
+// relative margin) so that ||X_0||_2 < 1; the scaled iteration starts from lower bound l0.
+__global__ void ns_state_kernel(int n_blocks, const double* __restrict__ lo, const double* __restrict__ hi,
+                                double mu, float margin, float l0, int scaled, NsState* __restrict__ st,
+                                float* __restrict__ resacc, DevFlags* flags) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b == 0) { flags->sum_n = 0.0; flags->sum_e = 0.0; }
+  if (b >= n_blocks) return;
+  const double rad = fmax(fabs(hi[b] - mu), fabs(mu - lo[b]));
+  NsState s;
+  s.alpha = (float)(rad * (1.0 + margin));
+  if (!(s.alpha > 0.f)) s.alpha = 1.f;
+  s.l = scaled ? fminf(fmaxf(l0, 1e-7f), 1.f) : 1.f;
+  s.a = cc_scale(s.l);
+  s.res = FLT_MAX;
+  s.res_prev = FLT_MAX;
+  s.iters = 0;
+  s.status = kActive;
+  s.cur = 0;
+  s.grow = 0;
+  s.restarts = 0;
+  st[b] = s;
+  resacc[b] = 0.f;
+}
+
+// X_0 = (A0 - mu I) / alpha on the n x n part, identity on the padding.
+template <typename T>
+__global__ void ns_fill_kernel(const BlockDesc* __restrict__ blocks, const float* __restrict__ a0,
+                               const NsState* __restrict__ st, double mu, T* __restrict__ x0) {
+  const BlockDesc bd = blocks[blockIdx.y];
+  const int n = bd.n, ld = bd.n_pad;
+  const float inv = 1.f / st[blockIdx.y].alpha;
+  const float muf = (float)mu;
+  const int64_t total = (int64_t)ld * ld;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / ld), c = (int)(e % ld);
+    float v;
+    if (r < n && c < n) v = (a0[bd.off_mat + e] - (r == c ? muf : 0.f)) * inv;
+    else v = (r == c) ? 1.f : 0.f;
+    x0[bd.off_mat + e] = from_float<T>(v);
+  }
+}
+
+// Tile list of the blocks still iterating (single CTA scan); also counts them.
+__global__ void __launch_bounds__(1024) ns_tiles_kernel(int n_blocks, const BlockDesc* __restrict__ blocks,
+                                                        const NsState* __restrict__ st, int tile_n,
+                                                        Tile* __restrict__ tiles, DevFlags* flags) {
+  __shared__ int32_t warp_sums[32];
+  __shared__ int32_t base;
+  __shared__ int32_t active_total;
+  if (threadIdx.x == 0) { base = 0; active_total = 0; }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int b0 = 0; b0 < n_blocks; b0 += blockDim.x) {
+    const int b = b0 + threadIdx.x;
+    int cnt = 0, nm = 0, nn = 0, np = 0;
+    if (b < n_blocks && st[b].status == kActive) {
+      np = blocks[b].n_pad;
+      nm = np / BM;
+      nn = (np + tile_n - 1) / tile_n;
+      cnt = nm * nn;
+    }
+    // block-wide exclusive scan of cnt
+    int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      int w = warp_sums[lane];
+      int wi = w;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += v;
+      }
+      warp_sums[lane] = wi - w;
+    }
+    __syncthreads();
+    const int off = base + warp_sums[warp] + incl - cnt;
+    if (cnt) {
+      int k = 0;
+      for (int mi = 0; mi < nm; ++mi)
+        for (int ni = 0; ni < nn; ++ni, ++k) {
+          Tile tl;
+          tl.block = b; tl.m0 = mi * BM; tl.n0 = ni * tile_n; tl.kend = np;
+          tiles[off + k] = tl;
+        }
+      atomicAdd(&active_total, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) base = off + cnt;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { flags->n_tiles = base; flags->n_active = active_total; }
+}
+
+// After the first product of an iteration: the residual decides convergence.
+__global__ void ns_check_kernel(int n_blocks, NsState* __restrict__ st, float* __restrict__ resacc,
+                                const float* __restrict__ tol_b, int max_iter, DevFlags* flags) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_blocks) return;
+  NsState s = st[b];
+  if (s.status != kActive) return;
+  const float res = sqrtf(resacc[b]);
+  resacc[b] = 0.f;
+  if (!isfinite(res)) { s.status = kFailed; s.res = res; st[b] = s; set_error(flags, NOLSM_ENONFINITE); return; }
+  s.res_prev = s.res;
+  s.res = res;
+  const bool plain = s.l >= 1.f;
+  if (res <= tol_b[b]) {
+    s.status = kConverged;
+  } else if (plain && s.iters >= 2 && res < 0.25f && res > 0.5f * s.res_prev) {
+    s.status = kConverged;      // rounding floor of the operand format reached
+  } else if (s.iters >= max_iter) {
+    s.status = kFailed;
+    set_error(flags, NOLSM_ENOCONV);
+  }
+  st[b] = s;
+}
+
+// After the second product: the new iterate is in the other buffer.
+__global__ void ns_advance_kernel(int n_blocks, NsState* __restrict__ st) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_blocks) return;
+  NsState s = st[b];
+  if (s.status != kActive) return;
+  s.cur ^= 1;
+  s.iters += 1;
+  s.l = cc_next(s.l, s.a);
+  s.a = cc_scale(s.l);
+  st[b] = s;
+}
+
+// ----------------------------------------------------------------------------------------------
+// Own-column slab: G = g(X) W with g = f o ... o f (refine times), f(X) = (3X - X^3)/2, then
+// Y = (W - G)/2 = T(D) columns before the back-transform, and the block traces
+//   N_b = sum_{j in C_b} (L P L^-1)_jj = <Lc, Y>,   E_b = sum_j (H_b D_b)_jj = <Z, Y>   (FP64 sums).
+// One CTA per block; slabs are column-major (ld = n_pad) in global scratch, X rows stream
+// through shared memory in 128 x 32 tiles.
+template <typename T>
+__device__ void slab_product(const T* __restrict__ X, int ld, int c, const float* __restrict__ V,
+                             float* __restrict__ P, float (*Xs)[33], float (*Vs)[8]) {
+  const int tid = threadIdx.x;
+  const int row = tid >> 1, cb = (tid & 1) * 4;
+  for (int r0 = 0; r0 < ld; r0 += 128) {
+    for (int c0 = 0; c0 < c; c0 += 8) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int k0 = 0; k0 < ld; k0 += 32) {
+        for (int e = tid; e < 128 * 32; e += blockDim.x) {
+          const int rr = e >> 5, kk = e & 31;
+          Xs[rr][kk] = ld_as_float<T>(X + (int64_t)(r0 + rr) * ld + k0 + kk);
+        }
+        {
+          const int kk = tid >> 3, cc = tid & 7;   // 256 threads = 32 x 8
+          Vs[kk][cc] = (c0 + cc < c) ? V[(int64_t)(c0 + cc) * ld + k0 + kk] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < 32; ++kk) {
+          const float x = Xs[row][kk];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[q] = fmaf(x, Vs[kk][cb + q], acc[q]);
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (c0 + cb + q < c) P[(int64_t)(c0 + cb + q) * ld + r0 + row] = acc[q];
+    }
+  }
+  __syncthreads();
+}
+
+__device__ void slab_axpby(float alpha, const float* __restrict__ a, float beta, const float* __restrict__ b,
+                           float* __restrict__ out, int64_t len) {
+  for (int64_t i = threadIdx.x; i < len; i += blockDim.x) out[i] = alpha * a[i] + beta * b[i];
+  __syncthreads();
+}
+
+template <typename T>
+__device__ void slab_f(const T* X, int ld, int c, const float* V, float* out, float* t1, float* t2, float* t3,
+                       float (*Xs)[33], float (*Vs)[8]) {
+  slab_product<T>(X, ld, c, V, t1, Xs, Vs);
+  slab_product<T>(X, ld, c, t1, t2, Xs, Vs);
+  slab_product<T>(X, ld, c, t2, t3, Xs, Vs);
+  slab_axpby(1.5f, t1, -0.5f, t3, out, (int64_t)ld * c);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) slab_traces_kernel(const BlockDesc* __restrict__ blocks,
+                                                          const NsState* __restrict__ st, const T* __restrict__ x0,
+                                                          const T* __restrict__ x1, const float* __restrict__ w,
+                                                          const float* __restrict__ z, const float* __restrict__ lc,
+                                                          float* __restrict__ y, float* __restrict__ tmp,
+                                                          int64_t slab_total, int refine, double* __restrict__ bn,
+                                                          double* __restrict__ be) {
+  __shared__ float Xs[128][33];
+  __shared__ float Vs[32][8];
+  __shared__ double red[2][8];
+  const BlockDesc bd = blocks[blockIdx.x];
+  const int ld = bd.n_pad, c = bd.c;
+  const NsState s = st[blockIdx.x];
+  const T* X = (s.cur ? x1 : x0) + bd.off_mat;
+  const int64_t len = (int64_t)ld * c;
+  const float* W = w + bd.off_slab;
+  float* t1 = tmp + bd.off_slab;
+  float* t2 = t1 + slab_total;
+  float* t3 = t2 + slab_total;
+  float* f1 = t3 + slab_total;
+  float* f2 = f1 + slab_total;
+  float* f3 = f2 + slab_total;
+  float* G;
+  if (refine <= 0) {
+    slab_product<T>(X, ld, c, W, f1, Xs, Vs);
+    G = f1;
+  } else if (refine == 1) {
+    slab_f<T>(X, ld, c, W, f1, t1, t2, t3, Xs, Vs);
+    G = f1;
+  } else {
+    // g = f o f: G = 1.5 F1 - 0.5 F3 with F1 = f(X)W, F2 = f(X)F1, F3 = f(X)F2
+    slab_f<T>(X, ld, c, W, f1, t1, t2, t3, Xs, Vs);
+    slab_f<T>(X, ld, c, f1, f2, t1, t2, t3, Xs, Vs);
+    slab_f<T>(X, ld, c, f2, f3, t1, t2, t3, Xs, Vs);
+    slab_axpby(1.5f, f1, -0.5f, f3, f2, len);
+    G = f2;
+  }
+  float* Y = y + bd.off_slab;
+  const float* Lc = lc + bd.off_slab;
+  const float* Z = z + bd.off_slab;
+  double sn = 0.0, se = 0.0;
+  for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
+    const float yv = 0.5f * (W[i] - G[i]);
+    Y[i] = yv;
+    sn += (double)Lc[i] * (double)yv;
+    se += (double)Z[i] * (double)yv;
+  }
+  for (int o = 16; o; o >>= 1) {
+    sn += __shfl_xor_sync(0xffffffffu, sn, o);
+    se += __shfl_xor_sync(0xffffffffu, se, o);
+  }
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { red[0][warp] = sn; red[1][warp] = se; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b2 = 0.0;
+    for (int i = 0; i < 8; ++i) { a += red[0][i]; b2 += red[1][i]; }
+    bn[blockIdx.x] = a;
+    be[blockIdx.x] = b2;
+  }
+}
+
+// Deterministic FP64 sum of the per-block traces (single CTA).
+__global__ void __launch_bounds__(1024) sum_traces_kernel(int n_blocks, const double* __restrict__ bn,
+                                                          const double* __restrict__ be, DevFlags* flags) {
+  __shared__ double r0[32], r1[32];
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < n_blocks; i += blockDim.x) { a += bn[i]; b += be[i]; }
+  for (int o = 16; o; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) { r0[threadIdx.x >> 5] = a; r1[threadIdx.x >> 5] = b; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0.0, y = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { x += r0[i]; y += r1[i]; }
+    flags->sum_n = x;
+    flags->sum_e = y;
+  }
+}
+
+// ----------------------------------------------------------------------------------------------
+// Step 3: D_b[:, C_b] = L^-T Y, then every stored entry (r, c) of an own column c is written to
+// its CSR position transpose[e] (e = the entry (c, r) of row c; the pattern is symmetric).
+__device__ __forceinline__ int lower_bound_g(const int32_t* a, int n, int32_t key) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256) density_kernel(const BlockDesc* __restrict__ blocks,
+                                                      const int32_t* __restrict__ idx_pool,
+                                                      const int32_t* __restrict__ blk_cols,
+                                                      const float* __restrict__ linv, const float* __restrict__ y,
+                                                      float* __restrict__ dslab, const int64_t* __restrict__ row_ptr,
+                                                      const int32_t* __restrict__ col,
+                                                      const int64_t* __restrict__ transpose, double* __restrict__ dval,
+                                                      DevFlags* flags) {
+  __shared__ float Ls[32][129];
+  __shared__ float Vs[32][8];
+  const BlockDesc bd = blocks[blockIdx.x];
+  const int ld = bd.n_pad, c = bd.c, n = bd.n;
+  const float* Li = linv + bd.off_mat;
+  const float* Y = y + bd.off_slab;
+  float* Dsl = dslab + bd.off_slab;
+  const int tid = threadIdx.x;
+  const int row = tid >> 1, cb = (tid & 1) * 4;
+  for (int r0 = 0; r0 < ld; r0 += 128) {
+    for (int c0 = 0; c0 < c; c0 += 8) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int k0 = r0; k0 < ld; k0 += 32) {     // L^-1[k, i] = 0 for k < i
+        for (int e = tid; e < 32 * 128; e += blockDim.x) {
+          const int kk = e >> 7, ii = e & 127;
+          Ls[kk][ii] = Li[(int64_t)(k0 + kk) * ld + r0 + ii];
+        }
+        {
+          const int kk = tid >> 3, cc = tid & 7;
+          Vs[kk][cc] = (c0 + cc < c) ? Y[(int64_t)(c0 + cc) * ld + k0 + kk] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < 32; ++kk) {
+          const float lv = Ls[kk][row];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[q] = fmaf(lv, Vs[kk][cb + q], acc[q]);
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (c0 + cb + q < c) Dsl[(int64_t)(c0 + cb + q) * ld + r0 + row] = acc[q];
+    }
+  }
+  __syncthreads();
+  const int32_t* I = idx_pool + bd.off_idx;
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int j = warp; j < c; j += 8) {
+    const int32_t cg = blk_cols[bd.col0 + j];
+    const int64_t e0 = row_ptr[cg], e1 = row_ptr[cg + 1];
+    for (int64_t e = e0 + lane; e < e1; e += 32) {
+      const int32_t r = col[e];
+      const int p = lower_bound_g(I, n, r);
+      if (p < n && I[p] == r) dval[transpose[e]] = (double)Dsl[(int64_t)j * ld + p];
+      else set_error(flags, NOLSM_EINVAL);
+    }
+  }
+}
+
+// E = sum_e D[e] * H[e]  (H symmetric on a symmetric pattern: H_ji = H_ij), FP64, two passes.
+__global__ void __launch_bounds__(256) dot_kernel(int64_t nnz, const double* __restrict__ a, const double* __restrict__ b,
+                                                  double* __restrict__ partial) {
+  __shared__ double red[8];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * blockDim.x)
+    s += a[i] * b[i];
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < 8; ++i) t += red[i];
+    partial[blockIdx.x] = t;
+  }
+}
+
+__global__ void sum_partials_kernel(int n, const double* __restrict__ partial, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += partial[i];
+    *out = s;
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------ launchers
+
+cudaError_t launch_sgemm_nt(nolsm_ctx* ctx, const float* a, const float* b, float* c, int a_lower, int b_lower) {
+  // host-built tile list over all blocks (build phase only)
+  std::vector<Tile> tl;
+  for (int32_t i = 0; i < ctx->n_blocks; ++i) {
+    const BlockDesc& bd = ctx->h_blocks[i];
+    for (int m0 = 0; m0 < bd.n_pad; m0 += BM)
+      for (int n0 = 0; n0 < bd.n_pad; n0 += BN) {
+        int kend = bd.n_pad;
+        if (a_lower) kend = std::min(kend, m0 + BM);
+        if (b_lower) kend = std::min(kend, n0 + BN);
+        tl.push_back(Tile{i, m0, n0, kend});
+      }
+  }
+  if ((int64_t)tl.size() > ctx->max_tiles) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemcpyAsync(ctx->d_tiles, tl.data(), tl.size() * sizeof(Tile), cudaMemcpyHostToDevice, ctx->stream);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(ctx->stream);   // tl is a host temporary
+  if (e != cudaSuccess) return e;
+  const int grid = ctx->num_sms * 2;
+  sgemm_nt_kernel<0><<<grid, 256, 0, ctx->stream>>>(ctx->d_tiles, nullptr, (int)tl.size(), ctx->d_blocks, a, b, c,
+                                                    nullptr, nullptr, nullptr, nullptr, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ns_init(nolsm_ctx* ctx, double mu, int half) {
+  const float l0 = (float)ctx->opt.lower_bound;
+  ns_state_kernel<<<(ctx->n_blocks + 255) / 256, 256, 0, ctx->stream>>>(
+      ctx->n_blocks, ctx->d_lo, ctx->d_hi, mu, (float)ctx->opt.alpha_margin, l0, ctx->opt.scaled, ctx->d_state,
+      ctx->d_resacc, ctx->d_flags);
+  const dim3 g(64, ctx->n_blocks);
+  if (half == 0)
+    ns_fill_kernel<float><<<g, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_a0, ctx->d_state, mu, (float*)ctx->d_x[0]);
+  else if (half == 1)
+    ns_fill_kernel<__half><<<g, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_a0, ctx->d_state, mu, (__half*)ctx->d_x[0]);
+  else
+    ns_fill_kernel<__nv_bfloat16><<<g, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_a0, ctx->d_state, mu,
+                                                              (__nv_bfloat16*)ctx->d_x[0]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ns_tiles_n(nolsm_ctx* ctx, int tile_n) {
+  ns_tiles_kernel<<<1, 1024, 0, ctx->stream>>>(ctx->n_blocks, ctx->d_blocks, ctx->d_state, tile_n, ctx->d_tiles,
+                                               ctx->d_flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ns_tiles(nolsm_ctx* ctx) { return launch_ns_tiles_n(ctx, BN); }
+
+cudaError_t launch_ns_check_impl(nolsm_ctx* ctx, const float* tol_b) {
+  ns_check_kernel<<<(ctx->n_blocks + 255) / 256, 256, 0, ctx->stream>>>(ctx->n_blocks, ctx->d_state, ctx->d_resacc,
+                                                                        tol_b, ctx->opt.max_iter, ctx->d_flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ns_advance(nolsm_ctx* ctx) {
+  ns_advance_kernel<<<(ctx->n_blocks + 255) / 256, 256, 0, ctx->stream>>>(ctx->n_blocks, ctx->d_state);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_f32(nolsm_ctx* ctx, int phase) {
+  const int grid = ctx->num_sms * 2;
+  const int32_t* nt = &ctx->d_flags->n_tiles;
+  if (phase == 1)
+    sgemm_nt_kernel<1><<<grid, 256, 0, ctx->stream>>>(ctx->d_tiles, nt, 0, ctx->d_blocks, nullptr, nullptr, nullptr,
+                                                      (float*)ctx->d_x[0], (float*)ctx->d_x[1], (float*)ctx->d_b,
+                                                      ctx->d_state, ctx->d_resacc);
+  else
+    sgemm_nt_kernel<2><<<grid, 256, 0, ctx->stream>>>(ctx->d_tiles, nt, 0, ctx->d_blocks, nullptr, nullptr, nullptr,
+                                                      (float*)ctx->d_x[0], (float*)ctx->d_x[1], (float*)ctx->d_b,
+                                                      ctx->d_state, ctx->d_resacc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slab_traces(nolsm_ctx* ctx, int half) {
+  const int r = ctx->opt.refine_iters;
+  if (half == 0)
+    slab_traces_kernel<float><<<ctx->n_blocks, 256, 0, ctx->stream>>>(
+        ctx->d_blocks, ctx->d_state, (const float*)ctx->d_x[0], (const float*)ctx->d_x[1], ctx->d_w, ctx->d_z, ctx->d_lc,
+        ctx->d_y, ctx->d_tmp, ctx->sum_slab, r, ctx->d_bn, ctx->d_be);
+  else if (half == 1)
+    slab_traces_kernel<__half><<<ctx->n_blocks, 256, 0, ctx->stream>>>(
+        ctx->d_blocks, ctx->d_state, (const __half*)ctx->d_x[0], (const __half*)ctx->d_x[1], ctx->d_w, ctx->d_z,
+        ctx->d_lc, ctx->d_y, ctx->d_tmp, ctx->sum_slab, r, ctx->d_bn, ctx->d_be);
+  else
+    slab_traces_kernel<__nv_bfloat16><<<ctx->n_blocks, 256, 0, ctx->stream>>>(
+        ctx->d_blocks, ctx->d_state, (const __nv_bfloat16*)ctx->d_x[0], (const __nv_bfloat16*)ctx->d_x[1], ctx->d_w,
+        ctx->d_z, ctx->d_lc, ctx->d_y, ctx->d_tmp, ctx->sum_slab, r, ctx->d_bn, ctx->d_be);
+  sum_traces_kernel<<<1, 1024, 0, ctx->stream>>>(ctx->n_blocks, ctx->d_bn, ctx->d_be, ctx->d_flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_density(nolsm_ctx* ctx) {
+  cudaError_t e = cudaMemsetAsync(ctx->d_dval, 0, sizeof(double) * ctx->nnz, ctx->stream);
+  if (e != cudaSuccess) return e;
+  density_kernel<<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_idx, ctx->d_blk_cols, ctx->d_linv,
+                                                         ctx->d_y, ctx->d_tmp, ctx->d_row_ptr, ctx->d_col,
+                                                         ctx->d_transpose, ctx->d_dval, ctx->d_flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_band_energy(nolsm_ctx* ctx) {
+  const int grid = 1024;
+  double* partial = reinterpret_cast<double*>(ctx->d_tmp);   // scratch: grid doubles
+  dot_kernel<<<grid, 256, 0, ctx->stream>>>(ctx->nnz, ctx->d_dval, ctx->d_hval, partial);
+  sum_partials_kernel<<<1, 32, 0, ctx->stream>>>(grid, partial, &ctx->d_flags->energy);
+  return cudaGetLastError();
+}
+
+}  // namespace nolsm

@@ -1,0 +1,159 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: max|dD| <= 1e-6 (FP32 path) and <= 1e-3 (mixed FP16 path) over the stored entries
+of D; |dE_band| <= 1e-4 Ha per atom; electron count within 1e-6 relative (FP32 path).  The
+oracle is re-evaluated at the chemical potential the GPU returns.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle.nolsm import NolsmOracle  # noqa: E402
+from synth import make_config, isolated_waters, dimer_system, water_box  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def nl():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2205_12182_gb300 import nolsm
+    return nolsm
+
+
+@pytest.fixture(scope="module")
+def sys1():
+    return make_config(1)
+
+
+@pytest.fixture(scope="module")
+def orc1(sys1):
+    return NolsmOracle.from_system(sys1).prepare()
+
+
+@pytest.fixture(scope="module")
+def mu1(orc1):
+    mu, _, _ = orc1.bisect(tol_rel=1e-3)
+    return mu
+
+
+def make(nl, system, precision, memory="device", **kw):
+    return nl.Nolsm(precision=precision, **kw).build(system, memory=memory)
+
+
+def test_index_sets_bit_exact(nl, sys1, orc1):
+    lib = make(nl, sys1, nl.PREC_FP32)
+    for b in range(sys1.n_blocks):
+        np.testing.assert_array_equal(lib.index_set(b), orc1.idx[b])
+
+
+@pytest.mark.parametrize("chol", [0, 1])
+def test_a0_spectrum_is_generalized_spectrum(nl, sys1, orc1, chol):
+    """A0 = L^-1 T(H) L^-T is similar to T(S)^-1 T(H): its eigenvalues are the oracle's eps_b."""
+    lib = make(nl, sys1, nl.PREC_FP32, chol_precision=chol)
+    lo, hi = lib.bounds()
+    for b in [0, 7, 31, 63]:
+        a0 = lib.block_matrix(b, 0).astype(np.float64)
+        ev = np.linalg.eigvalsh(0.5 * (a0 + a0.T))
+        np.testing.assert_allclose(ev, orc1.eps[b], atol=2e-6)
+        assert lo[b] <= ev[0] + 1e-6 and ev[-1] - 1e-6 <= hi[b]
+
+
+def _dmax(nl, lib, orc, mu):
+    d = lib.density().cpu().numpy()
+    return np.abs(d - orc.density(mu)).max(), d
+
+
+def test_fp32_path_parity(nl, sys1, orc1, mu1):
+    lib = make(nl, sys1, nl.PREC_FP32)
+    st = lib.sign_batch(mu1)
+    n_ref = 2 * orc1.electron_count(mu1)
+    assert st["n_electrons"] == pytest.approx(n_ref, rel=1e-6)
+    assert abs(st["band_energy"] - orc1.band_energy_of_mu(mu1)) / sys1.n_atoms <= 1e-4
+    dmax, d = _dmax(nl, lib, orc1, mu1)
+    assert dmax <= 1e-6, dmax
+    e = lib.band_energy()
+    assert abs(e - orc1.band_energy(orc1.density(mu1))) / sys1.n_atoms <= 1e-4
+
+
+@pytest.mark.parametrize("scaled", [1, 0])
+def test_mixed_fp16_path_parity(nl, sys1, orc1, mu1, scaled):
+    lib = make(nl, sys1, nl.PREC_MIXED_FP16, scaled=scaled)
+    st = lib.sign_batch(mu1)
+    n_ref = 2 * orc1.electron_count(mu1)
+    assert st["n_electrons"] == pytest.approx(n_ref, rel=1e-4)
+    dmax, _ = _dmax(nl, lib, orc1, mu1)
+    assert dmax <= 1e-3, dmax
+    assert abs(lib.band_energy() - orc1.band_energy_of_mu(mu1)) / sys1.n_atoms <= 1e-4
+
+
+def test_set_mu_mixed(nl, sys1, orc1):
+    lib = make(nl, sys1, nl.PREC_MIXED_FP16)
+    mu, n, steps = lib.set_mu(sys1.n_electrons, tol_n=1e-3)
+    assert abs(n - sys1.n_electrons) <= 1e-3 * sys1.n_electrons
+    # oracle at the GPU's mu: the gap around mu (distance to the nearest block eigenvalue)
+    gap = min(np.min(np.abs(e - mu)) for e in orc1.eps)
+    assert gap >= 1e-3
+    assert 2 * orc1.electron_count(mu) == pytest.approx(n, rel=1e-4)
+    dmax, _ = _dmax(nl, lib, orc1, mu)
+    assert dmax <= 1e-3
+
+
+def test_host_memory_inputs_match_device(nl, sys1, mu1):
+    a = make(nl, sys1, nl.PREC_FP32, memory="device")
+    b = make(nl, sys1, nl.PREC_FP32, memory="host")
+    sa, sb = a.sign_batch(mu1), b.sign_batch(mu1)
+    assert sa["n_electrons"] == sb["n_electrons"]
+    np.testing.assert_array_equal(a.density().cpu().numpy(), b.density().cpu().numpy())
+
+
+def test_tiny_blocks_and_isolated_molecules(nl):
+    """n_b = 6 (padded to one 128 tile): NOLSM is exact for molecules beyond the cutoff."""
+    s = isolated_waters(8, seed=3)
+    o = NolsmOracle.from_system(s).prepare()
+    mu, _, _ = o.bisect(tol_rel=1e-9)
+    for prec, tol in [(nl.PREC_FP32, 1e-6), (nl.PREC_MIXED_FP16, 1e-3)]:
+        lib = make(nl, s, prec)
+        st = lib.sign_batch(mu)
+        assert st["n_electrons"] == pytest.approx(s.n_electrons, rel=1e-5)
+        assert np.abs(lib.density().cpu().numpy() - o.density(mu)).max() <= tol
+
+
+def test_dimer_closed_form(nl):
+    a, b, s = -1.0, -0.3, 0.2
+    sysd = dimer_system(a, b, s)
+    mu = 0.5 * ((a + b) / (1 + s) + (a - b) / (1 - s))
+    lib = make(nl, sysd, nl.PREC_FP32)
+    lib.sign_batch(mu)
+    np.testing.assert_allclose(lib.density().cpu().numpy(), np.array([1, 1, 1, 1]) / (2 * (1 + s)), atol=1e-6)
+
+
+@pytest.mark.parametrize("seed", [2, 3])
+def test_other_seeds_mixed(nl, seed):
+    s = make_config(1, seed)
+    o = NolsmOracle.from_system(s).prepare()
+    mu, _, _ = o.bisect(tol_rel=1e-3)
+    lib = make(nl, s, nl.PREC_MIXED_FP16)
+    lib.sign_batch(mu)
+    assert np.abs(lib.density().cpu().numpy() - o.density(mu)).max() <= 1e-3
+
+
+def test_config2_sampled_blocks(nl):
+    """Full 4,096-molecule system (24,576 basis functions) in the launch configuration of the
+    benchmark; the oracle checks a seeded sample of blocks one by one at the GPU's mu."""
+    s = make_config(2)
+    lib = make(nl, s, nl.PREC_MIXED_FP16)
+    mu, n, steps = lib.set_mu(s.n_electrons, tol_n=1e-3)
+    d = lib.density().cpu().numpy()
+    sample = np.random.default_rng(0).choice(s.n_blocks, 12, replace=False)
+    o = NolsmOracle.from_system(s, blocks=sample).prepare()
+    rows = np.repeat(np.arange(s.n_basis), np.diff(s.row_ptr))
+    d_ref = o.density(mu)
+    own = np.isin(s.col, np.concatenate([s.block_cols(int(b)) for b in sample]))
+    assert np.abs(d[own] - d_ref[own]).max() <= 1e-3
+    for b in sample[:4]:
+        np.testing.assert_array_equal(lib.index_set(int(b)), o.idx[list(sample).index(b)])
+    e = lib.band_energy()
+    assert np.isfinite(e)
+    del rows
