@@ -117,7 +117,7 @@ typedef struct nolsm_sign_stats {
   int32_t n_blocks;
   int32_t n_restarted;     /* blocks restarted with the Gershgorin bound after residual growth */
   double flops_paper;      /* 2 n_b^3 per product, true n_b (the paper's count, Section V-B) */
-  double flops_executed;   /* products as executed on padded tiles */
+  double flops_executed;   /* as executed: padded n, upper-triangular tiles (n_pad^2 (n_pad + 128) per product) */
   double ms;               /* device time of the evaluation (CUDA events) */
 } nolsm_sign_stats;
 
@@ -179,11 +179,14 @@ nolsm_status nolsm_block_index_set(const nolsm_ctx* ctx, int32_t b, int32_t* idx
 /* Per-block spectral bounds [lo, hi] of A0 used by the iteration (host arrays of n_blocks). */
 nolsm_status nolsm_block_bounds(const nolsm_ctx* ctx, double* lo, double* hi);
 
-/* Per-block Newton-Schulz iteration counts of the last sign evaluation (host array). */
-nolsm_status nolsm_block_iters(const nolsm_ctx* ctx, int32_t* iters);
+/* Per-block state of the last sign evaluation (host arrays of n_blocks; any may be NULL):
+ * completed matrix iterations, ||X^2 - I||_F of the last product, and the exit status
+ * (0 still iterating, 1 converged, 2 restarted, 3 failed).  Synchronises. */
+nolsm_status nolsm_block_state(const nolsm_ctx* ctx, int32_t* iters, double* residual, int32_t* status);
 
 /* Diagnostic copy of block b's n_b x n_b matrix `which` to host memory (row-major, float32):
- * which = 0: A0 = L^-1 T_b(H0) L^-T;  which = 1: L^-1.  Synchronises. */
+ * which = 0: A0 = L^-1 T_b(H0) L^-T;  1: L^-1;  2, 3: the two iterate buffers X;  4: the
+ * second-operand buffer of the last product.  Synchronises. */
 nolsm_status nolsm_block_matrix(const nolsm_ctx* ctx, int32_t b, int32_t which, float* out);
 
 /* Message of the last error of ctx (never NULL; "" when none).  ctx may be NULL. */

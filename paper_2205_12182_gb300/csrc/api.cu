@@ -302,7 +302,7 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
     off_idx += bd.n;
     off_own += bd.c;
     ctx->flops_paper_iter += 2.0 * 2.0 * (double)bd.n * bd.n * bd.n;
-    ctx->flops_exec_iter += 2.0 * 2.0 * (double)bd.n_pad * bd.n_pad * bd.n_pad;
+    ctx->flops_exec_iter += 2.0 * (double)bd.n_pad * bd.n_pad * (bd.n_pad + kTile);
   }
   for (int32_t b : order) {
     BlockDesc& bd = ctx->h_blocks[b];
@@ -453,7 +453,8 @@ nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out) 
       const double n = ctx->h_blocks[b].n, np = ctx->h_blocks[b].n_pad;
       // it full iterations (2 products) plus the first product of the converged check
       fp += (2.0 * it + 1.0) * 2.0 * n * n * n;
-      fe += (2.0 * it + 1.0) * 2.0 * np * np * np;
+      // executed: upper-triangular 128-row tiles only, np^2 (np + 128) per product
+      fe += (2.0 * it + 1.0) * np * np * (np + kTile);
     }
     s.iters_avg = (double)sum_it / ctx->n_blocks;
     s.flops_paper = fp;
@@ -552,20 +553,43 @@ nolsm_status nolsm_block_bounds(const nolsm_ctx* ctx, double* lo, double* hi) {
   return NOLSM_OK;
 }
 
-nolsm_status nolsm_block_iters(const nolsm_ctx* ctx, int32_t* iters) {
-  if (!ctx || !ctx->have_sign || !iters || ctx->h_iters.size() != (size_t)ctx->n_blocks) return NOLSM_EINVAL;
-  std::memcpy(iters, ctx->h_iters.data(), sizeof(int32_t) * ctx->n_blocks);
+nolsm_status nolsm_block_state(const nolsm_ctx* ctx, int32_t* iters, double* residual, int32_t* status) {
+  if (!ctx || !ctx->built) return NOLSM_EINVAL;
+  std::vector<NsState> hs((size_t)ctx->n_blocks);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return NOLSM_ECUDA;
+  if (cudaMemcpy(hs.data(), ctx->d_state, sizeof(NsState) * ctx->n_blocks, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return NOLSM_ECUDA;
+  for (int32_t b = 0; b < ctx->n_blocks; ++b) {
+    if (iters) iters[b] = hs[b].iters;
+    if (residual) residual[b] = hs[b].res;
+    if (status) status[b] = hs[b].status;
+  }
   return NOLSM_OK;
 }
 
 nolsm_status nolsm_block_matrix(const nolsm_ctx* ctx, int32_t b, int32_t which, float* out) {
-  if (!ctx || !ctx->built || b < 0 || b >= ctx->n_blocks || !out || which < 0 || which > 1) return NOLSM_EINVAL;
+  if (!ctx || !ctx->built || b < 0 || b >= ctx->n_blocks || !out || which < 0 || which > 4) return NOLSM_EINVAL;
   const BlockDesc& bd = ctx->h_blocks[b];
-  const float* src = (which == 0 ? ctx->d_a0 : ctx->d_linv) + bd.off_mat;
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return NOLSM_ECUDA;
-  if (cudaMemcpy2D(out, sizeof(float) * bd.n, src, sizeof(float) * bd.n_pad, sizeof(float) * bd.n, bd.n,
-                   cudaMemcpyDeviceToHost) != cudaSuccess)
+  if (which <= 1) {
+    const float* src = (which == 0 ? ctx->d_a0 : ctx->d_linv) + bd.off_mat;
+    if (cudaMemcpy2D(out, sizeof(float) * bd.n, src, sizeof(float) * bd.n_pad, sizeof(float) * bd.n, bd.n,
+                     cudaMemcpyDeviceToHost) != cudaSuccess)
+      return NOLSM_ECUDA;
+    return NOLSM_OK;
+  }
+  const void* pool = which == 2 ? ctx->d_x[0] : which == 3 ? ctx->d_x[1] : ctx->d_b;
+  const int hk = half_kind(ctx);
+  const size_t es = hk ? 2 : 4;
+  std::vector<uint8_t> raw((size_t)bd.n * bd.n * es);
+  if (cudaMemcpy2D(raw.data(), es * bd.n, reinterpret_cast<const uint8_t*>(pool) + es * bd.off_mat, es * bd.n_pad,
+                   es * bd.n, bd.n, cudaMemcpyDeviceToHost) != cudaSuccess)
     return NOLSM_ECUDA;
+  for (size_t i = 0; i < (size_t)bd.n * bd.n; ++i) {
+    if (hk == 0) out[i] = reinterpret_cast<const float*>(raw.data())[i];
+    else if (hk == 1) out[i] = __half2float(reinterpret_cast<const __half*>(raw.data())[i]);
+    else out[i] = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(raw.data())[i]);
+  }
   return NOLSM_OK;
 }
 

@@ -109,7 +109,9 @@ sgemm_nt_kernel(const Tile* __restrict__ tiles, const int32_t* __restrict__ n_ti
       buf ^= 1;
     }
     __syncthreads();
-    // epilogue
+    // epilogue.  MODE 0 writes the full tile.  MODE 1/2 tiles lie on or above the block diagonal:
+    // entry (r, c) with c > r is written at (r, c) and (c, r), the diagonal once, c < r skipped, so
+    // every iterate is exactly symmetric (the products read the transpose of their B operand).
     float rsq = 0.f;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -118,17 +120,25 @@ sgemm_nt_kernel(const Tile* __restrict__ tiles, const int32_t* __restrict__ n_ti
       for (int jh = 0; jh < 2; ++jh) {
         const int c = tl.n0 + jh * 64 + tx * 4;
         float4 v = make_float4(acc[i][jh * 4 + 0], acc[i][jh * 4 + 1], acc[i][jh * 4 + 2], acc[i][jh * 4 + 3]);
-        if (MODE == 1) {
-          float* pv = &v.x;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float d = (r == c + q) ? 1.f : 0.f;
-            const float e = pv[q] - d;
-            rsq = fmaf(e, e, rsq);
-            pv[q] = c1 * d - c3 * pv[q];
-          }
+        if (MODE == 0) {
+          *reinterpret_cast<float4*>(C + (int64_t)r * ld + c) = v;
+          continue;
         }
-        *reinterpret_cast<float4*>(C + (int64_t)r * ld + c) = v;
+        float* pv = &v.x;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int cq = c + q;
+          if (cq < r) continue;
+          float o = pv[q];
+          if (MODE == 1) {
+            const float d = (r == cq) ? 1.f : 0.f;
+            const float e = o - d;
+            rsq = fmaf((r == cq) ? 1.f : 2.f, e * e, rsq);
+            o = c1 * d - c3 * o;
+          }
+          C[(int64_t)r * ld + cq] = o;
+          if (cq > r) C[(int64_t)cq * ld + r] = o;
+        }
       }
     }
     if (MODE == 1) {
@@ -196,12 +206,12 @@ __global__ void __launch_bounds__(1024) ns_tiles_kernel(int n_blocks, const Bloc
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int b0 = 0; b0 < n_blocks; b0 += blockDim.x) {
     const int b = b0 + threadIdx.x;
-    int cnt = 0, nm = 0, nn = 0, np = 0;
+    int cnt = 0, nm = 0, np = 0;
     if (b < n_blocks && st[b].status == kActive) {
       np = blocks[b].n_pad;
       nm = np / BM;
-      nn = (np + tile_n - 1) / tile_n;
-      cnt = nm * nn;
+      // row tile mi covers columns [mi*BM, np): the upper triangle including the diagonal tile
+      for (int mi = 0; mi < nm; ++mi) cnt += (np - mi * BM + tile_n - 1) / tile_n;
     }
     // block-wide exclusive scan of cnt
     int incl = cnt;
@@ -225,9 +235,9 @@ __global__ void __launch_bounds__(1024) ns_tiles_kernel(int n_blocks, const Bloc
     if (cnt) {
       int k = 0;
       for (int mi = 0; mi < nm; ++mi)
-        for (int ni = 0; ni < nn; ++ni, ++k) {
+        for (int n0 = mi * BM; n0 < np; n0 += tile_n, ++k) {
           Tile tl;
-          tl.block = b; tl.m0 = mi * BM; tl.n0 = ni * tile_n; tl.kend = np;
+          tl.block = b; tl.m0 = mi * BM; tl.n0 = n0; tl.kend = np;
           tiles[off + k] = tl;
         }
       atomicAdd(&active_total, 1);

@@ -138,6 +138,7 @@ __device__ __forceinline__ uint32_t make_idesc(int fmt, int m, int n) {
 template <typename T> struct Pack;
 template <> struct Pack<__half> {
   static constexpr int fmt = 0;
+  __device__ static __half one(float a) { return __float2half_rn(a); }
   __device__ static uint32_t two(float a, float b) {
     __half2 h = __floats2half2_rn(a, b);
     return *reinterpret_cast<uint32_t*>(&h);
@@ -145,6 +146,7 @@ template <> struct Pack<__half> {
 };
 template <> struct Pack<__nv_bfloat16> {
   static constexpr int fmt = 1;
+  __device__ static __nv_bfloat16 one(float a) { return __float2bfloat16_rn(a); }
   __device__ static uint32_t two(float a, float b) {
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<uint32_t*>(&h);
@@ -302,27 +304,47 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_cons
       const int r = tl.m0 + row_in_tile;
       T* orow = out + (int64_t)r * ld + tl.n0;
       float rsq = 0.f;
+      // Tiles lie on or above the block diagonal.  Entry (r, c): c > r is stored at (r, c) and at
+      // (c, r), the diagonal once, c < r (left part of a diagonal tile) not at all, so every
+      // iterate is exactly symmetric -- the products read the transpose of their B operand, and
+      // with a non-symmetric iterate the iteration would be X (3 - X X^T) / 2, which doubles
+      // antisymmetric rounding errors each step once converged.
       for (int c0 = 0; c0 < tn; c0 += 32) {
+        const int cg0 = tl.n0 + c0;
         uint32_t v[32];
         tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * TN + c0), v);
-        uint32_t packed[16];
+        if (cg0 + 31 < r) continue;              // whole chunk left of the diagonal (warp-uniform ld done)
+        float f[32];
 #pragma unroll
-        for (int j = 0; j < 32; j += 2) {
-          float f0 = __uint_as_float(v[j]), f1 = __uint_as_float(v[j + 1]);
+        for (int j = 0; j < 32; ++j) {
+          float x = __uint_as_float(v[j]);
           if (p.phase == 1) {
-            const int cg = tl.n0 + c0 + j;
-            const float d0 = (cg == r) ? 1.f : 0.f, d1 = (cg + 1 == r) ? 1.f : 0.f;
-            const float e0 = f0 - d0, e1 = f1 - d1;
-            rsq = fmaf(e0, e0, fmaf(e1, e1, rsq));
-            f0 = c1 * d0 - c3 * f0;
-            f1 = c1 * d1 - c3 * f1;
+            const int cg = cg0 + j;
+            const float d = (cg == r) ? 1.f : 0.f;
+            const float e = x - d;
+            const float w = (cg > r) ? 2.f : ((cg == r) ? 1.f : 0.f);
+            rsq = fmaf(w, e * e, rsq);
+            x = c1 * d - c3 * x;
           }
-          packed[j >> 1] = Pack<T>::two(f0, f1);
+          f[j] = x;
         }
-        uint4* dst = reinterpret_cast<uint4*>(orow + c0);
+        if (cg0 >= r) {
+          uint32_t packed[16];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          dst[u] = make_uint4(packed[4 * u], packed[4 * u + 1], packed[4 * u + 2], packed[4 * u + 3]);
+          for (int j = 0; j < 32; j += 2) packed[j >> 1] = Pack<T>::two(f[j], f[j + 1]);
+          uint4* dst = reinterpret_cast<uint4*>(orow + c0);
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            dst[u] = make_uint4(packed[4 * u], packed[4 * u + 1], packed[4 * u + 2], packed[4 * u + 3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (cg0 + j >= r) orow[c0 + j] = Pack<T>::one(f[j]);
+        }
+        // mirror: column cg of this tile becomes row cg; lanes hold consecutive rows r
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (cg0 + j > r) out[(int64_t)(cg0 + j) * ld + r] = Pack<T>::one(f[j]);
       }
       tc_fence_before();
       mbar_arrive(&tempty_bar[acc]);

@@ -24,7 +24,7 @@ CHOL_FP64, CHOL_FP32 = 0, 1
 
 FUNCTIONS = ["nolsm_default_options", "nolsm_create", "nolsm_build_submatrices", "nolsm_sign_batch", "nolsm_set_mu",
              "nolsm_density", "nolsm_band_energy", "nolsm_block_info", "nolsm_block_index_set", "nolsm_block_bounds",
-             "nolsm_block_iters", "nolsm_block_matrix", "nolsm_last_error", "nolsm_destroy"]
+             "nolsm_block_state", "nolsm_block_matrix", "nolsm_last_error", "nolsm_destroy"]
 
 
 class NolsmCsr(C.Structure):
@@ -73,7 +73,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "nolsm_block_info": (i32, [P, i32, pi32, pi32]),
         "nolsm_block_index_set": (i32, [P, i32, P]),
         "nolsm_block_bounds": (i32, [P, P, P]),
-        "nolsm_block_iters": (i32, [P, P]),
+        "nolsm_block_state": (i32, [P, P, P, P]),
         "nolsm_block_matrix": (i32, [P, i32, i32, P]),
         "nolsm_last_error": (C.c_char_p, [P]),
         "nolsm_destroy": (None, [P]),
@@ -167,10 +167,12 @@ def nolsm_block_bounds(ctx, n_blocks):
     return lo, hi
 
 
-def nolsm_block_iters(ctx, n_blocks) -> np.ndarray:
+def nolsm_block_state(ctx, n_blocks):
     it = np.empty(n_blocks, np.int32)
-    _check(ctx, _lib.nolsm_block_iters(ctx, it.ctypes.data))
-    return it
+    res = np.empty(n_blocks)
+    st = np.empty(n_blocks, np.int32)
+    _check(ctx, _lib.nolsm_block_state(ctx, it.ctypes.data, res.ctypes.data, st.ctypes.data))
+    return it, res, st
 
 
 def nolsm_block_matrix(ctx, b, which=0) -> np.ndarray:
@@ -277,7 +279,10 @@ class Nolsm:
         return nolsm_block_bounds(self.ctx, self.n_blocks)
 
     def iters(self):
-        return nolsm_block_iters(self.ctx, self.n_blocks)
+        return nolsm_block_state(self.ctx, self.n_blocks)[0]
+
+    def block_state(self):
+        return nolsm_block_state(self.ctx, self.n_blocks)
 
     def block_matrix(self, b, which=0):
         return nolsm_block_matrix(self.ctx, b, which)
