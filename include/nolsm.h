@@ -189,6 +189,12 @@ nolsm_status nolsm_block_state(const nolsm_ctx* ctx, int32_t* iters, double* res
  * second-operand buffer of the last product.  Synchronises. */
 nolsm_status nolsm_block_matrix(const nolsm_ctx* ctx, int32_t b, int32_t which, float* out);
 
+/* Cumulative counters of ctx since nolsm_create or the last reset (reset != 0 zeroes them after
+ * reading): kernels launched by the library, and the device time (CUDA events on the context
+ * stream, ms) and executed flops of the Newton-Schulz matrix-product launches.  Synchronises. */
+nolsm_status nolsm_counters(nolsm_ctx* ctx, int64_t* launches, int64_t* gemm_launches, double* gemm_ms,
+                            double* gemm_flops, int32_t reset);
+
 /* Message of the last error of ctx (never NULL; "" when none).  ctx may be NULL. */
 const char* nolsm_last_error(const nolsm_ctx* ctx);
 

@@ -174,6 +174,7 @@ void nolsm_destroy(nolsm_ctx* ctx) {
   if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  for (auto e : ctx->gemm_ev) cudaEventDestroy(e);
   delete ctx;
 }
 
@@ -376,6 +377,7 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   CK(cudaMemsetAsync(hb, 0, sizeof(double) * ctx->sum_sq, ctx->stream));
   CK(cudaMemsetAsync(sb, 0, sizeof(double) * 2 * ctx->sum_sq, ctx->stream));
   CK(cudaMemsetAsync(ctx->d_linv, 0, sizeof(float) * ctx->sum_sq, ctx->stream));
+  ctx->n_launches += 10;   // gather, factor, inverse, conversions, two products, symmetrise, slabs, bounds
   CK(launch_gather(ctx, hb, sb));
   const int chol32 = ctx->opt.chol_precision == NOLSM_CHOL_FP32;
   CK(launch_cholesky_inverse(ctx, sb, chol32));
@@ -398,6 +400,41 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   return NOLSM_OK;
 }
 
+namespace {
+
+// Event pair around one matrix-product launch (recorded on the context stream).
+cudaError_t gemm_timed(nolsm_ctx* ctx, bool mixed, int phase) {
+  const int k = ctx->gemm_ev_used;
+  if ((int)ctx->gemm_ev.size() < 2 * (k + 1)) {
+    cudaEvent_t a, b;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&b);
+    if (e != cudaSuccess) return e;
+    ctx->gemm_ev.push_back(a);
+    ctx->gemm_ev.push_back(b);
+  }
+  cudaError_t e = cudaEventRecord(ctx->gemm_ev[2 * k], ctx->stream);
+  if (e != cudaSuccess) return e;
+  e = mixed ? launch_gemm_tc(ctx, phase) : launch_gemm_f32(ctx, phase);
+  if (e != cudaSuccess) return e;
+  ctx->gemm_ev_used = k + 1;
+  ctx->n_launches += 1;
+  ctx->n_gemm += 1;
+  return cudaEventRecord(ctx->gemm_ev[2 * k + 1], ctx->stream);
+}
+
+// Sum the recorded product durations (the stream has been synchronised).
+void harvest_gemm_events(nolsm_ctx* ctx) {
+  for (int k = 0; k < ctx->gemm_ev_used; ++k) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->gemm_ev[2 * k], ctx->gemm_ev[2 * k + 1]) == cudaSuccess) ctx->gemm_ms += ms;
+  }
+  ctx->gemm_ev_used = 0;
+}
+
+}  // namespace
+
 nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out) {
   if (!ctx) return NOLSM_EINVAL;
   if (ctx->sticky != NOLSM_OK) return ctx->sticky;
@@ -407,28 +444,45 @@ nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out) 
   const int hk = half_kind(ctx);
   CK(cudaEventRecord(ctx->ev0, ctx->stream));
   CK(launch_ns_init(ctx, mu, hk));
+  ctx->n_launches += 2;
   const int tile_n = mixed ? tc_tile_n() : kTile;
   const int check_every = 4;
+  ctx->gemm_ev_used = 0;
   for (int it = 0; it <= ctx->opt.max_iter; ++it) {
     CK(launch_ns_tiles_n(ctx, tile_n));
-    CK(mixed ? launch_gemm_tc(ctx, 1) : launch_gemm_f32(ctx, 1));
+    CK(gemm_timed(ctx, mixed, 1));
     CK(launch_ns_check_impl(ctx, ctx->d_tol));
     CK(launch_ns_tiles_n(ctx, tile_n));
-    CK(mixed ? launch_gemm_tc(ctx, 2) : launch_gemm_f32(ctx, 2));
+    CK(gemm_timed(ctx, mixed, 2));
     CK(launch_ns_advance(ctx));
+    ctx->n_launches += 4;
     if (it % check_every == check_every - 1 || it == ctx->opt.max_iter) {
       CK(cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(DevFlags), cudaMemcpyDeviceToHost, ctx->stream));
       CK(cudaStreamSynchronize(ctx->stream));
+      harvest_gemm_events(ctx);
       if (ctx->h_flags->error != 0 || ctx->h_flags->n_active == 0) break;
     }
   }
   CK(launch_slab_traces(ctx, hk));
+  ctx->n_launches += 2;
   CK(cudaEventRecord(ctx->ev1, ctx->stream));
   nolsm_status st = check_device_flags(ctx);
+  harvest_gemm_events(ctx);
   if (st != NOLSM_OK) return st;
   ctx->last_mu = mu;
   ctx->have_sign = true;
   ctx->have_density = false;
+  {
+    // executed product flops of this evaluation (counters), from the per-block iteration counts
+    std::vector<NsState> hs((size_t)ctx->n_blocks);
+    CK(cudaMemcpy(hs.data(), ctx->d_state, sizeof(NsState) * ctx->n_blocks, cudaMemcpyDeviceToHost));
+    double fe = 0.0;
+    for (int32_t b = 0; b < ctx->n_blocks; ++b) {
+      const double np = ctx->h_blocks[b].n_pad;
+      fe += (2.0 * hs[b].iters + 1.0) * np * np * (np + kTile);
+    }
+    ctx->gemm_flops += fe;
+  }
   nolsm_sign_stats s{};
   s.mu = mu;
   s.n_electrons = ctx->opt.spin_factor * ctx->h_flags->sum_n;
@@ -509,6 +563,7 @@ nolsm_status nolsm_density(nolsm_ctx* ctx, double* d_val, int32_t memory) {
   if (!ctx->have_sign) return fail(ctx, NOLSM_ENOTBUILT, "nolsm_sign_batch has not run");
   if (memory != NOLSM_MEM_DEVICE && memory != NOLSM_MEM_HOST) return fail(ctx, NOLSM_EINVAL, "bad memory kind");
   CK(launch_density(ctx));
+  ctx->n_launches += 1;
   if (d_val) {
     CK(cudaMemcpyAsync(d_val, ctx->d_dval, sizeof(double) * ctx->nnz,
                        memory == NOLSM_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, ctx->stream));
@@ -526,6 +581,7 @@ nolsm_status nolsm_band_energy(nolsm_ctx* ctx, double* e_out) {
   if (ctx->sticky != NOLSM_OK) return ctx->sticky;
   if (!ctx->have_density) return fail(ctx, NOLSM_ENOTBUILT, "nolsm_density has not run");
   CK(launch_band_energy(ctx));
+  ctx->n_launches += 2;
   nolsm_status st = check_device_flags(ctx);
   if (st != NOLSM_OK) return st;
   *e_out = ctx->opt.spin_factor * ctx->h_flags->energy;
@@ -550,6 +606,22 @@ nolsm_status nolsm_block_bounds(const nolsm_ctx* ctx, double* lo, double* hi) {
   if (!ctx || !ctx->built) return NOLSM_EINVAL;
   if (lo) std::memcpy(lo, ctx->h_lo.data(), sizeof(double) * ctx->n_blocks);
   if (hi) std::memcpy(hi, ctx->h_hi.data(), sizeof(double) * ctx->n_blocks);
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_counters(nolsm_ctx* ctx, int64_t* launches, int64_t* gemm_launches, double* gemm_ms,
+                            double* gemm_flops, int32_t reset) {
+  if (!ctx) return NOLSM_EINVAL;
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return NOLSM_ECUDA;
+  harvest_gemm_events(ctx);
+  if (launches) *launches = ctx->n_launches;
+  if (gemm_launches) *gemm_launches = ctx->n_gemm;
+  if (gemm_ms) *gemm_ms = ctx->gemm_ms;
+  if (gemm_flops) *gemm_flops = ctx->gemm_flops;
+  if (reset) {
+    ctx->n_launches = ctx->n_gemm = 0;
+    ctx->gemm_ms = ctx->gemm_flops = 0.0;
+  }
   return NOLSM_OK;
 }
 

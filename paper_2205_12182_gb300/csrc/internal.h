@@ -129,6 +129,15 @@ struct nolsm_ctx {
   void* d_tmaps = nullptr;
   int n_tmaps = 0;
 
+  // counters (nolsm_counters): every launch through a launcher, and event pairs around the
+  // matrix-product launches of the sign iteration
+  int64_t n_launches = 0;
+  int64_t n_gemm = 0;
+  double gemm_ms = 0.0;
+  double gemm_flops = 0.0;
+  std::vector<cudaEvent_t> gemm_ev;     // pairs, reused
+  int gemm_ev_used = 0;
+
   double last_mu = 0.0;
   nolsm_sign_stats last_stats{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;

@@ -24,7 +24,7 @@ CHOL_FP64, CHOL_FP32 = 0, 1
 
 FUNCTIONS = ["nolsm_default_options", "nolsm_create", "nolsm_build_submatrices", "nolsm_sign_batch", "nolsm_set_mu",
              "nolsm_density", "nolsm_band_energy", "nolsm_block_info", "nolsm_block_index_set", "nolsm_block_bounds",
-             "nolsm_block_state", "nolsm_block_matrix", "nolsm_last_error", "nolsm_destroy"]
+             "nolsm_block_state", "nolsm_block_matrix", "nolsm_counters", "nolsm_last_error", "nolsm_destroy"]
 
 
 class NolsmCsr(C.Structure):
@@ -75,6 +75,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "nolsm_block_bounds": (i32, [P, P, P]),
         "nolsm_block_state": (i32, [P, P, P, P]),
         "nolsm_block_matrix": (i32, [P, i32, i32, P]),
+        "nolsm_counters": (i32, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), pf64, pf64, i32]),
         "nolsm_last_error": (C.c_char_p, [P]),
         "nolsm_destroy": (None, [P]),
     }
@@ -182,6 +183,13 @@ def nolsm_block_matrix(ctx, b, which=0) -> np.ndarray:
     return out
 
 
+def nolsm_counters(ctx, reset=False) -> dict:
+    la, ga = C.c_int64(), C.c_int64()
+    ms, fl = C.c_double(), C.c_double()
+    _check(ctx, _lib.nolsm_counters(ctx, C.byref(la), C.byref(ga), C.byref(ms), C.byref(fl), int(bool(reset))))
+    return {"launches": la.value, "gemm_launches": ga.value, "gemm_ms": ms.value, "gemm_flops": fl.value}
+
+
 def nolsm_last_error(ctx) -> str:
     return _lib.nolsm_last_error(ctx).decode()
 
@@ -215,6 +223,7 @@ class Nolsm:
             stream = torch.cuda.current_stream().cuda_stream
         self.ctx = nolsm_create(o, stream)
         self._keep = []
+        self._cache = {}
 
     def close(self):
         if self.ctx:
@@ -227,22 +236,24 @@ class Nolsm:
         except Exception:
             pass
 
-    def build(self, system, memory="device"):
+    def stage(self, system, memory="device"):
+        """CSR arrays of `system` as torch tensors on the device or in pinned host memory (cached)."""
         import torch
+        key = (id(system), memory)
+        if key not in self._cache:
+            arrs = [np.ascontiguousarray(system.row_ptr, np.int64), np.ascontiguousarray(system.col, np.int32),
+                    np.ascontiguousarray(system.h, np.float64), np.ascontiguousarray(system.s, np.float64)]
+            if memory == "device":
+                ts = [torch.from_numpy(a).to(torch.device("cuda")) for a in arrs]
+            else:
+                ts = [torch.from_numpy(a).pin_memory() for a in arrs]
+            self._cache[key] = (system, ts)
+        return self._cache[key][1]
+
+    def build(self, system, memory="device"):
         n, nnz = system.n_basis, system.nnz
-        if memory == "device":
-            dev = torch.device("cuda")
-            rp = torch.from_numpy(np.ascontiguousarray(system.row_ptr, np.int64)).to(dev)
-            cl = torch.from_numpy(np.ascontiguousarray(system.col, np.int32)).to(dev)
-            hv = torch.from_numpy(np.ascontiguousarray(system.h, np.float64)).to(dev)
-            sv = torch.from_numpy(np.ascontiguousarray(system.s, np.float64)).to(dev)
-            kind = MEM_DEVICE
-        else:
-            rp = torch.from_numpy(np.ascontiguousarray(system.row_ptr, np.int64)).pin_memory()
-            cl = torch.from_numpy(np.ascontiguousarray(system.col, np.int32)).pin_memory()
-            hv = torch.from_numpy(np.ascontiguousarray(system.h, np.float64)).pin_memory()
-            sv = torch.from_numpy(np.ascontiguousarray(system.s, np.float64)).pin_memory()
-            kind = MEM_HOST
+        rp, cl, hv, sv = self.stage(system, memory)
+        kind = MEM_DEVICE if memory == "device" else MEM_HOST
         self._keep = [rp, cl, hv, sv]
         H = make_csr(n, nnz, rp, cl, hv, kind)
         S = make_csr(n, nnz, rp, cl, sv, kind)
@@ -283,6 +294,9 @@ class Nolsm:
 
     def block_state(self):
         return nolsm_block_state(self.ctx, self.n_blocks)
+
+    def counters(self, reset=False):
+        return nolsm_counters(self.ctx, reset)
 
     def block_matrix(self, b, which=0):
         return nolsm_block_matrix(self.ctx, b, which)
