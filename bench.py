@@ -116,7 +116,7 @@ def run_ours(args):
     import torch
     from paper_2205_12182_gb300 import nolsm
     from paper_2205_12182_gb300.distributed import set_mu_distributed
-    from synth import make_config
+    from synth import make_config, water_box
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -130,7 +130,12 @@ def run_ours(args):
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
 
-    system = make_config(2, seed=WORKLOAD["seed"] + rank)
+    if args.side != 16:
+        system = water_box(args.side, seed=WORKLOAD["seed"] + rank, neighbourhood=8.0)
+        WORKLOAD.update(workload=f"water-{args.side ** 3}", molecules=args.side ** 3, atoms=3 * args.side ** 3,
+                        basis=6 * args.side ** 3, box_A=3.1 * args.side, blocks=args.side ** 3)
+    else:
+        system = make_config(2, seed=WORKLOAD["seed"] + rank)
     n_e_global = system.n_electrons * world
 
     def mu_fn(lib, s):
@@ -338,6 +343,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
+    ap.add_argument("--side", type=int, default=16,
+                    help="molecules per box edge (16: the 4,096-molecule workload; smaller boxes for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
