@@ -346,6 +346,9 @@ def main():
     ap.add_argument("--side", type=int, default=16,
                     help="molecules per box edge (16: the 4,096-molecule workload; smaller boxes for profiling)")
     args = ap.parse_args()
+    if args.impl == "ours":
+        from paper_2205_12182_gb300.build import build
+        build()      # idempotent: compiles libnolsm.so only when it is missing or stale
     if args.impl == "reference":
         run_reference(args)
     else:
