@@ -76,8 +76,9 @@ typedef enum nolsm_bounds {
 } nolsm_bounds;
 
 typedef enum nolsm_chol_precision {
-  NOLSM_CHOL_FP64 = 0,          /* Cholesky factor and its inverse in FP64 */
-  NOLSM_CHOL_FP32 = 1           /* both in FP32 (faster on parts with a slow FP64 unit) */
+  NOLSM_CHOL_FP64 = 0,          /* Cholesky factor of T_b(S) in FP64, its triangular inverse in FP32 */
+  NOLSM_CHOL_FP32 = 1,          /* factor and inverse in FP32 */
+  NOLSM_CHOL_FP64_INV64 = 2     /* factor and inverse in FP64 */
 } nolsm_chol_precision;
 
 /* One CSR matrix (see the conventions above). */

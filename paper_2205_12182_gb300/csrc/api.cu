@@ -145,7 +145,8 @@ nolsm_status nolsm_create(nolsm_ctx** out, const nolsm_options* opt, void* cuda_
   if (opt) ctx->opt = *opt; else nolsm_default_options(&ctx->opt);
   if (ctx->opt.precision < NOLSM_PREC_FP32 || ctx->opt.precision > NOLSM_PREC_MIXED_BF16 || ctx->opt.max_iter <= 0 ||
       ctx->opt.refine_iters < 0 || ctx->opt.refine_iters > 3 || !(ctx->opt.spin_factor > 0) ||
-      ctx->opt.wait_budget <= 0 || ctx->opt.alpha_margin < 0) {
+      ctx->opt.wait_budget <= 0 || ctx->opt.alpha_margin < 0 || ctx->opt.chol_precision < 0 ||
+      ctx->opt.chol_precision > NOLSM_CHOL_FP64_INV64) {
     delete ctx;
     return NOLSM_EINVAL;
   }
@@ -322,6 +323,9 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   int64_t tiles_max = 0;
   for (const auto& bd : ctx->h_blocks) tiles_max += (int64_t)(bd.n_pad / kTile) * (bd.n_pad / kTile);
   ctx->max_tiles = tiles_max;
+  ctx->max_tiles_tc = 0;
+  for (const auto& bd : ctx->h_blocks)
+    for (int m0 = 0; m0 < bd.n_pad; m0 += kTile) ctx->max_tiles_tc += (bd.n_pad - m0 + 255) / 256;
 
   // ---- device pools
   const bool mixed = is_mixed(ctx);
@@ -379,8 +383,9 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   CK(cudaMemsetAsync(ctx->d_linv, 0, sizeof(float) * ctx->sum_sq, ctx->stream));
   ctx->n_launches += 10;   // gather, factor, inverse, conversions, two products, symmetrise, slabs, bounds
   CK(launch_gather(ctx, hb, sb));
-  const int chol32 = ctx->opt.chol_precision == NOLSM_CHOL_FP32;
-  CK(launch_cholesky_inverse(ctx, sb, chol32));
+  const int chol_mode = ctx->opt.chol_precision;
+  const int chol32 = chol_mode == NOLSM_CHOL_FP32;
+  CK(launch_cholesky_inverse(ctx, sb, chol_mode));
   CK(dalloc(&t1, (size_t)ctx->sum_sq));
   CK(launch_congruence(ctx, hb, sb, t1, chol32));
   CK(launch_slabs_impl(ctx, chol32 ? (const void*)(sb + ctx->sum_sq) : (const void*)sb, chol32, t1));

@@ -248,22 +248,6 @@ __global__ void to_f32_kernel(const BlockDesc* __restrict__ blocks, const T* __r
   }
 }
 
-// Symmetrise A0 in place: A = (A + A^T)/2 (exact in exact arithmetic; removes rounding skew).
-__global__ void symmetrize_kernel(const BlockDesc* __restrict__ blocks, float* __restrict__ a) {
-  const BlockDesc bd = blocks[blockIdx.y];
-  const int ld = bd.n_pad;
-  const int64_t total = (int64_t)ld * ld;
-  float* A = a + bd.off_mat;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(e / ld), c = (int)(e % ld);
-    if (c < r) {
-      const float v = 0.5f * (A[(int64_t)r * ld + c] + A[(int64_t)c * ld + r]);
-      A[(int64_t)r * ld + c] = v;
-      A[(int64_t)c * ld + r] = v;
-    }
-  }
-}
-
 // Own-column slabs (column-major, ld = n_pad, zero beyond n):
 //   W[:, j] = L^-1[:, p_j]            Z[:, j] = (L^-1 H_b)[:, p_j]       Lc[:, j] = L[p_j, :]^T
 // with p_j the local position of the block's j-th own column.
@@ -295,26 +279,29 @@ __global__ void gershgorin_kernel(const BlockDesc* __restrict__ blocks, const fl
   const int n = bd.n, ld = bd.n_pad;
   const float* A = a0 + bd.off_mat;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  double wlo = DBL_MAX, whi = -DBL_MAX;
+  // FP32 sums; the radius is rounded up by a relative n*2^-23 so the discs stay enclosing
+  float wlo = FLT_MAX, whi = -FLT_MAX;
+  const float up = 1.f + (float)n * 1.2e-7f;
   for (int r = warp; r < n; r += nwarps) {
-    double rad = 0.0, d = 0.0;
+    float rad = 0.f, d = 0.f;
     for (int c = lane; c < n; c += 32) {
-      const double v = A[(int64_t)r * ld + c];
-      if (c == r) d = v; else rad += fabs(v);
+      const float v = A[(int64_t)r * ld + c];
+      if (c == r) d = v; else rad += fabsf(v);
     }
     for (int o = 16; o; o >>= 1) {
       rad += __shfl_xor_sync(0xffffffffu, rad, o);
       d += __shfl_xor_sync(0xffffffffu, d, o);
     }
-    wlo = fmin(wlo, d - rad);
-    whi = fmax(whi, d + rad);
+    rad *= up;
+    wlo = fminf(wlo, d - rad);
+    whi = fmaxf(whi, d + rad);
   }
-  __shared__ double slo[32], shi[32];
+  __shared__ float slo[32], shi[32];
   if (lane == 0) { slo[warp] = wlo; shi[warp] = whi; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double l = DBL_MAX, h = -DBL_MAX;
-    for (int i = 0; i < nwarps; ++i) { l = fmin(l, slo[i]); h = fmax(h, shi[i]); }
+    float l = FLT_MAX, h = -FLT_MAX;
+    for (int i = 0; i < nwarps; ++i) { l = fminf(l, slo[i]); h = fmaxf(h, shi[i]); }
     if (!isfinite(l) || !isfinite(h)) set_error(flags, NOLSM_ENONFINITE);
     lo[blockIdx.x] = l;
     hi[blockIdx.x] = h;
@@ -338,15 +325,18 @@ cudaError_t launch_gather(nolsm_ctx* ctx, double* hb, double* sb) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int fp32) {
-  // sb holds T_b(S) in FP64.  FP64: factor in place, inverse into the second half of the
-  // scratch (sb + sum_sq).  FP32: convert first, then the same kernels in float.
-  if (!fp32) {
+cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode) {
+  // sb holds T_b(S) in FP64 (first sum_sq doubles); the second half is scratch.
+  float* s32 = reinterpret_cast<float*>(sb + ctx->sum_sq);   // FP32 factor lives in the scratch half
+  if (mode == NOLSM_CHOL_FP64_INV64) {
     cholesky_kernel<double><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, sb, ctx->d_flags);
     trinv_kernel<double><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, sb, sb + ctx->sum_sq);
     to_f32_kernel<double><<<sq_grid(ctx->n_blocks), 256, 0, ctx->stream>>>(ctx->d_blocks, sb + ctx->sum_sq, ctx->d_linv, 1);
+  } else if (mode == NOLSM_CHOL_FP64) {
+    cholesky_kernel<double><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, sb, ctx->d_flags);
+    to_f32_kernel<double><<<sq_grid(ctx->n_blocks), 256, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, 1);
+    trinv_kernel<float><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
   } else {
-    float* s32 = reinterpret_cast<float*>(sb + ctx->sum_sq);   // FP32 factor lives in the scratch half
     to_f32_kernel<double><<<sq_grid(ctx->n_blocks), 256, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, 0);
     cholesky_kernel<float><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_flags);
     trinv_kernel<float><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
@@ -360,12 +350,10 @@ cudaError_t launch_congruence(nolsm_ctx* ctx, const double* hb, const double* sb
   to_f32_kernel<double><<<sq_grid(ctx->n_blocks), 256, 0, ctx->stream>>>(ctx->d_blocks, hb, ctx->d_a0, 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = launch_sgemm_nt(ctx, ctx->d_linv, ctx->d_a0, t1, /*a_lower=*/1, /*b_lower=*/0);
+  e = launch_sgemm_nt(ctx, ctx->d_linv, ctx->d_a0, t1, /*a_lower=*/1, /*b_lower=*/0, /*sym=*/0);
   if (e != cudaSuccess) return e;
-  e = launch_sgemm_nt(ctx, t1, ctx->d_linv, ctx->d_a0, 0, /*b_lower=*/1);
-  if (e != cudaSuccess) return e;
-  symmetrize_kernel<<<sq_grid(ctx->n_blocks), 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_a0);
-  return cudaGetLastError();
+  // A0 is symmetric: upper tiles only, mirrored stores (exactly symmetric, half the work)
+  return launch_sgemm_nt(ctx, t1, ctx->d_linv, ctx->d_a0, 0, /*b_lower=*/1, /*sym=*/1);
 }
 
 cudaError_t launch_slabs_impl(nolsm_ctx* ctx, const void* lfac, int fp32, const float* t1) {

@@ -112,7 +112,8 @@ struct nolsm_ctx {
   float* d_tol = nullptr;       // per-block stopping tolerance on ||X^2 - I||_F
   nolsm::NsState* d_state = nullptr;
   nolsm::Tile* d_tiles = nullptr;
-  int64_t max_tiles = 0;
+  int64_t max_tiles = 0;        // full tile count (capacity of d_tiles)
+  int64_t max_tiles_tc = 0;     // upper-triangular tensor-core tiles of all blocks
   nolsm::DevFlags* d_flags = nullptr;
   nolsm::DevFlags* h_flags = nullptr;   // pinned mirror
 
@@ -151,7 +152,7 @@ nolsm_status cuda_fail(nolsm_ctx* ctx, cudaError_t e, const char* what);
 
 // build.cu
 cudaError_t launch_gather(nolsm_ctx* ctx, double* hb, double* sb);
-cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int fp32);
+cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode);
 cudaError_t launch_congruence(nolsm_ctx* ctx, const double* hb, const double* sb_linv, float* t1_scratch, int fp32);
 cudaError_t launch_slabs_impl(nolsm_ctx* ctx, const void* lfac, int fp32, const float* t1);
 cudaError_t launch_bounds(nolsm_ctx* ctx);
@@ -174,6 +175,7 @@ cudaError_t launch_gemm_tc(nolsm_ctx* ctx, int phase);
 int tc_tile_n();
 
 // generic SIMT NT product used by the build: C_b = A_b B_b^T on the block table
-cudaError_t launch_sgemm_nt(nolsm_ctx* ctx, const float* a, const float* b, float* c, int a_lower, int b_lower);
+cudaError_t launch_sgemm_nt(nolsm_ctx* ctx, const float* a, const float* b, float* c, int a_lower, int b_lower,
+                            int sym);
 
 }  // namespace nolsm

@@ -36,6 +36,7 @@ __device__ __forceinline__ float cc_next(float l, float a) {
 // Grouped SIMT product C = A B^T on 128x128 tiles (both operands row-major, K contiguous).
 // MODE 0: plain store.  MODE 1: NS first product T = X X^T (X symmetric), epilogue writes
 //   B = 1.5 a I - 0.5 a^3 T and accumulates ||T - I||_F^2 per block.  MODE 2: X+ = X B^T.
+// MODE 3: plain store of a product known to be symmetric (upper tiles, mirrored).
 constexpr int BM = 128, BN = 128, BK = 16;
 
 template <int MODE>
@@ -58,7 +59,7 @@ sgemm_nt_kernel(const Tile* __restrict__ tiles, const int32_t* __restrict__ n_ti
     const float* B;
     float* C;
     float c1 = 0.f, c3 = 0.f;
-    if (MODE == 0) {
+    if (MODE == 0 || MODE == 3) {
       A = a_pool + bd.off_mat; B = b_pool + bd.off_mat; C = c_pool + bd.off_mat;
     } else {
       const NsState s = st[tl.block];
@@ -523,13 +524,14 @@ __global__ void sum_partials_kernel(int n, const double* __restrict__ partial, d
 
 // ------------------------------------------------------------------------------------------------ launchers
 
-cudaError_t launch_sgemm_nt(nolsm_ctx* ctx, const float* a, const float* b, float* c, int a_lower, int b_lower) {
+cudaError_t launch_sgemm_nt(nolsm_ctx* ctx, const float* a, const float* b, float* c, int a_lower, int b_lower,
+                            int sym) {
   // host-built tile list over all blocks (build phase only)
   std::vector<Tile> tl;
   for (int32_t i = 0; i < ctx->n_blocks; ++i) {
     const BlockDesc& bd = ctx->h_blocks[i];
     for (int m0 = 0; m0 < bd.n_pad; m0 += BM)
-      for (int n0 = 0; n0 < bd.n_pad; n0 += BN) {
+      for (int n0 = sym ? m0 : 0; n0 < bd.n_pad; n0 += BN) {
         int kend = bd.n_pad;
         if (a_lower) kend = std::min(kend, m0 + BM);
         if (b_lower) kend = std::min(kend, n0 + BN);
@@ -542,8 +544,12 @@ cudaError_t launch_sgemm_nt(nolsm_ctx* ctx, const float* a, const float* b, floa
   e = cudaStreamSynchronize(ctx->stream);   // tl is a host temporary
   if (e != cudaSuccess) return e;
   const int grid = ctx->num_sms * 2;
-  sgemm_nt_kernel<0><<<grid, 256, 0, ctx->stream>>>(ctx->d_tiles, nullptr, (int)tl.size(), ctx->d_blocks, a, b, c,
-                                                    nullptr, nullptr, nullptr, nullptr, nullptr);
+  if (sym)
+    sgemm_nt_kernel<3><<<grid, 256, 0, ctx->stream>>>(ctx->d_tiles, nullptr, (int)tl.size(), ctx->d_blocks, a, b, c,
+                                                      nullptr, nullptr, nullptr, nullptr, nullptr);
+  else
+    sgemm_nt_kernel<0><<<grid, 256, 0, ctx->stream>>>(ctx->d_tiles, nullptr, (int)tl.size(), ctx->d_blocks, a, b, c,
+                                                      nullptr, nullptr, nullptr, nullptr, nullptr);
   return cudaGetLastError();
 }
 

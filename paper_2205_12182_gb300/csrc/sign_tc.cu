@@ -46,6 +46,7 @@ struct TcParams {
   DevFlags* flags;
   long long budget;             // polls per wait
   int phase;                    // 1 or 2
+  int tile_base;                // first tile of this launch in the list
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -155,6 +156,26 @@ template <> struct Pack<__nv_bfloat16> {
 
 __device__ __forceinline__ void set_error(DevFlags* f, int code) { atomicCAS(&f->error, 0, code); }
 
+// Everything a role needs about one tile, resolved once per launch into shared memory (the
+// chain tile -> block descriptor -> iteration state is three dependent global loads).
+struct TileInfo {
+  int64_t out_off;    // element offset of the output matrix in its pool
+  int32_t row_a;      // TMA row of the A box (bin-stacked coordinates)
+  int32_t row_b;      // TMA row of the first B box
+  int32_t m0, n0;     // tile origin inside the block
+  int32_t tn, kend;   // tile width (128 or 256), K extent
+  int32_t ld;         // n_pad of the block
+  int32_t map_a;      // tensor-map index of A
+  int32_t map_b;      // tensor-map index of B
+  int32_t out_sel;    // 0: x0, 1: x1, 2: bbuf
+  int32_t block;
+  float c1, c3;       // phase-1 epilogue coefficients
+  int32_t pad;
+};
+constexpr int MAX_LOCAL = 352;                // tiles per CTA per launch
+constexpr int INFO_BYTES = MAX_LOCAL * (int)sizeof(TileInfo);
+constexpr int SMEM_TOTAL = SMEM_BYTES + INFO_BYTES;
+
 template <typename T>
 __global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_constant__ TcParams p) {
   extern __shared__ uint8_t smem_raw[];
@@ -168,8 +189,35 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_cons
   uint64_t* drain_bar = bars + 2 * STAGES + 4;     // [1]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  TileInfo* info = reinterpret_cast<TileInfo*>(smem + STAGES * STAGE_BYTES + 256);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_tiles = *p.n_tiles;
+  const int first = p.tile_base + (int)blockIdx.x;
+  int n_local = (n_tiles > first) ? (n_tiles - first + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  n_local = min(n_local, MAX_LOCAL);
+  for (int i = threadIdx.x; i < n_local; i += NUM_THREADS) {
+    const Tile tl = p.tiles[first + i * (int)gridDim.x];
+    const BlockDesc bd = p.blocks[tl.block];
+    const NsState s = p.st[tl.block];
+    TileInfo f;
+    f.m0 = tl.m0;
+    f.n0 = tl.n0;
+    f.kend = tl.kend;
+    f.ld = bd.n_pad;
+    f.tn = min(TN, bd.n_pad - tl.n0);
+    f.row_a = bd.pos * bd.n_pad + tl.m0;
+    f.row_b = bd.pos * bd.n_pad + tl.n0;
+    f.map_a = bd.bin * 3 + s.cur;
+    f.map_b = (p.phase == 1) ? f.map_a : bd.bin * 3 + 2;
+    f.out_sel = (p.phase == 1) ? 2 : (s.cur ^ 1);
+    f.out_off = bd.off_mat;
+    f.block = tl.block;
+    f.c1 = 1.5f * s.a;
+    f.c3 = 0.5f * s.a * s.a * s.a;
+    f.pad = 0;
+    info[i] = f;
+  }
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
     for (int a = 0; a < 2; ++a) { mbar_init(&tfull_bar[a], 1); mbar_init(&tempty_bar[a], 128); }
@@ -187,7 +235,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_cons
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  const int n_tiles = *p.n_tiles;
   const long long budget = p.budget;
   // draining our own copies / products never depends on the caller's budget
   const long long drain_budget = budget > (1LL << 22) ? budget : (1LL << 22);
@@ -200,23 +247,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_cons
       uint32_t armed = 0;                  // bit s: stage s has been armed at least once
       uint32_t arm_parity = 0;             // bit s: phase parity of the last arm of stage s
       bool ok = true;
-      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-        const Tile tl = p.tiles[t];
-        const BlockDesc bd = p.blocks[tl.block];
-        const int cur = p.st[tl.block].cur;
-        const CUtensorMap* mx = p.tmaps + bd.bin * 3 + cur;
-        const CUtensorMap* mb = (p.phase == 1) ? mx : (p.tmaps + bd.bin * 3 + 2);
-        const int row_a = bd.pos * bd.n_pad + tl.m0;
-        const int row_b = bd.pos * bd.n_pad + tl.n0;
-        const int tn = min(TN, bd.n_pad - tl.n0);
-        const uint32_t bytes = A_BYTES + tn * TK * 2;
-        for (int k0 = 0; k0 < tl.kend; k0 += TK) {
+      for (int i = 0; i < n_local && ok; ++i) {
+        const TileInfo& f = info[i];
+        const CUtensorMap* ma = p.tmaps + f.map_a;
+        const CUtensorMap* mb = p.tmaps + f.map_b;
+        const uint32_t bytes = A_BYTES + f.tn * TK * 2;
+        for (int k0 = 0; k0 < f.kend; k0 += TK) {
           if (!mbar_wait(&empty_bar[s], ph ^ 1u, budget, abort_flag)) { ok = false; break; }
           mbar_expect_tx(&full_bar[s], bytes);
           uint8_t* a_dst = stage_base + s * STAGE_BYTES;
           uint8_t* b_dst = a_dst + A_BYTES;
-          tma_load_2d(a_dst, mx, &full_bar[s], k0, row_a);
-          for (int h = 0; h < tn; h += TM) tma_load_2d(b_dst + h * TK * 2, mb, &full_bar[s], k0, row_b + h);
+          tma_load_2d(a_dst, ma, &full_bar[s], k0, f.row_a);
+          for (int h = 0; h < f.tn; h += TM) tma_load_2d(b_dst + h * TK * 2, mb, &full_bar[s], k0, f.row_b + h);
           armed |= 1u << s;
           arm_parity = (arm_parity & ~(1u << s)) | (ph << s);
           if (++s == STAGES) { s = 0; ph ^= 1u; }
@@ -239,15 +281,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_cons
       uint32_t tph[2] = {0u, 0u};
       int acc = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-        const Tile tl = p.tiles[t];
-        const BlockDesc bd = p.blocks[tl.block];
-        const int tn = min(TN, bd.n_pad - tl.n0);
-        const uint32_t idesc = make_idesc(Pack<T>::fmt, TM, tn);
+      for (int i = 0; i < n_local && ok; ++i) {
+        const TileInfo& f = info[i];
+        const uint32_t idesc = make_idesc(Pack<T>::fmt, TM, f.tn);
         if (!mbar_wait(&tempty_bar[acc], tph[acc] ^ 1u, budget, abort_flag)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * TN);
-        for (int k0 = 0; k0 < tl.kend; k0 += TK) {
+        for (int k0 = 0; k0 < f.kend; k0 += TK) {
           if (!mbar_wait(&full_bar[s], ph, budget, abort_flag)) { ok = false; break; }
           tc_fence_after();
           const uint32_t a_addr = smem_u32(stage_base + s * STAGE_BYTES);
@@ -282,27 +322,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_cons
     const int row_in_tile = q * 32 + lane;
     uint32_t tph[2] = {0u, 0u};
     int acc = 0;
-    T* const xout0 = reinterpret_cast<T*>(p.x0);
-    T* const xout1 = reinterpret_cast<T*>(p.x1);
-    T* const bout = reinterpret_cast<T*>(p.bbuf);
-    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-      const Tile tl = p.tiles[t];
-      const BlockDesc bd = p.blocks[tl.block];
-      const NsState s = p.st[tl.block];
-      const int ld = bd.n_pad;
-      const int tn = min(TN, ld - tl.n0);
+    T* const pools[3] = {reinterpret_cast<T*>(p.x0), reinterpret_cast<T*>(p.x1), reinterpret_cast<T*>(p.bbuf)};
+    for (int i = 0; i < n_local; ++i) {
+      const TileInfo& f = info[i];
+      const int ld = f.ld;
+      const int tn = f.tn;
       if (!mbar_wait(&tfull_bar[acc], tph[acc], budget, abort_flag)) {
         set_error(p.flags, NOLSM_ETIMEOUT);
         *abort_flag = 1;
         break;
       }
       tc_fence_after();
-      T* out;
-      if (p.phase == 1) out = bout + bd.off_mat;
-      else out = (s.cur ? xout0 : xout1) + bd.off_mat;
-      const float c1 = 1.5f * s.a, c3 = 0.5f * s.a * s.a * s.a;
-      const int r = tl.m0 + row_in_tile;
-      T* orow = out + (int64_t)r * ld + tl.n0;
+      T* out = pools[f.out_sel] + f.out_off;
+      const float c1 = f.c1, c3 = f.c3;
+      const int r = f.m0 + row_in_tile;
+      T* orow = out + (int64_t)r * ld + f.n0;
       float rsq = 0.f;
       // Tiles lie on or above the block diagonal.  Entry (r, c): c > r is stored at (r, c) and at
       // (c, r), the diagonal once, c < r (left part of a diagonal tile) not at all, so every
@@ -310,11 +344,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_cons
       // with a non-symmetric iterate the iteration would be X (3 - X X^T) / 2, which doubles
       // antisymmetric rounding errors each step once converged.
       for (int c0 = 0; c0 < tn; c0 += 32) {
-        const int cg0 = tl.n0 + c0;
+        const int cg0 = f.n0 + c0;
         uint32_t v[32];
         tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * TN + c0), v);
         if (cg0 + 31 < r) continue;              // whole chunk left of the diagonal (warp-uniform ld done)
-        float f[32];
+        float fv[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           float x = __uint_as_float(v[j]);
@@ -326,12 +360,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_cons
             rsq = fmaf(w, e * e, rsq);
             x = c1 * d - c3 * x;
           }
-          f[j] = x;
+          fv[j] = x;
         }
         if (cg0 >= r) {
           uint32_t packed[16];
 #pragma unroll
-          for (int j = 0; j < 32; j += 2) packed[j >> 1] = Pack<T>::two(f[j], f[j + 1]);
+          for (int j = 0; j < 32; j += 2) packed[j >> 1] = Pack<T>::two(fv[j], fv[j + 1]);
           uint4* dst = reinterpret_cast<uint4*>(orow + c0);
 #pragma unroll
           for (int u = 0; u < 4; ++u)
@@ -339,12 +373,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_cons
         } else {
 #pragma unroll
           for (int j = 0; j < 32; ++j)
-            if (cg0 + j >= r) orow[c0 + j] = Pack<T>::one(f[j]);
+            if (cg0 + j >= r) orow[c0 + j] = Pack<T>::one(fv[j]);
         }
         // mirror: column cg of this tile becomes row cg; lanes hold consecutive rows r
 #pragma unroll
         for (int j = 0; j < 32; ++j)
-          if (cg0 + j > r) out[(int64_t)(cg0 + j) * ld + r] = Pack<T>::one(f[j]);
+          if (cg0 + j > r) out[(int64_t)(cg0 + j) * ld + r] = Pack<T>::one(fv[j]);
       }
       tc_fence_before();
       mbar_arrive(&tempty_bar[acc]);
@@ -352,7 +386,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_cons
       acc ^= 1;
       if (p.phase == 1) {
         for (int o = 16; o; o >>= 1) rsq += __shfl_xor_sync(0xffffffffu, rsq, o);
-        if (lane == 0) atomicAdd(&p.resacc[tl.block], rsq);
+        if (lane == 0) atomicAdd(&p.resacc[f.block], rsq);
       }
     }
     asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -422,9 +456,9 @@ cudaError_t tc_prepare(nolsm_ctx* ctx) {
   if (e != cudaSuccess) return e;
   static bool attr_done = false;
   if (!attr_done) {
-    e = cudaFuncSetAttribute(ns_tc_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    e = cudaFuncSetAttribute(ns_tc_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TOTAL);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(ns_tc_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    e = cudaFuncSetAttribute(ns_tc_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TOTAL);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
@@ -448,11 +482,18 @@ cudaError_t launch_gemm_tc(nolsm_ctx* ctx, int phase) {
   p.budget = ctx->opt.wait_budget;
   p.phase = phase;
   const int grid = ctx->num_sms;
-  if (ctx->opt.precision == NOLSM_PREC_MIXED_BF16)
-    ns_tc_kernel<__nv_bfloat16><<<grid, NUM_THREADS, SMEM_BYTES, ctx->stream>>>(p);
-  else
-    ns_tc_kernel<__half><<<grid, NUM_THREADS, SMEM_BYTES, ctx->stream>>>(p);
-  return cudaGetLastError();
+  // each CTA resolves at most MAX_LOCAL tiles per launch; cover the largest possible list
+  const int64_t per_launch = (int64_t)MAX_LOCAL * grid;
+  for (int64_t base = 0; base < std::max<int64_t>(ctx->max_tiles_tc, 1); base += per_launch) {
+    p.tile_base = (int)base;
+    if (ctx->opt.precision == NOLSM_PREC_MIXED_BF16)
+      ns_tc_kernel<__nv_bfloat16><<<grid, NUM_THREADS, SMEM_TOTAL, ctx->stream>>>(p);
+    else
+      ns_tc_kernel<__half><<<grid, NUM_THREADS, SMEM_TOTAL, ctx->stream>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 int tc_tile_n() { return TN; }
