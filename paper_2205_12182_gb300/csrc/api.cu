@@ -37,15 +37,31 @@ nolsm_status cuda_fail(nolsm_ctx* ctx, cudaError_t e, const char* what) {
 
 namespace {
 
-template <typename T>
-cudaError_t dalloc(T** p, size_t count) {
-  *p = nullptr;
-  if (count == 0) count = 1;
-  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
-}
-
 void dfree(void* p) {
   if (p) cudaFree(p);
+}
+
+// Make *p hold at least count elements; a pool keeps its allocation across builds and only
+// grows (rebuilding the same system allocates nothing).
+template <typename T>
+cudaError_t dalloc(nolsm_ctx* ctx, T** p, size_t count) {
+  if (count == 0) count = 1;
+  const size_t bytes = count * sizeof(T);
+  void** key = reinterpret_cast<void**>(p);
+  for (auto& kv : ctx->caps)
+    if (kv.first == key) {
+      if (kv.second >= bytes && *p) return cudaSuccess;
+      dfree(*p);
+      *p = nullptr;
+      cudaError_t e = cudaMalloc(key, bytes);
+      kv.second = (e == cudaSuccess) ? bytes : 0;
+      return e;
+    }
+  dfree(*p);
+  *p = nullptr;
+  cudaError_t e = cudaMalloc(key, bytes);
+  ctx->caps.emplace_back(key, e == cudaSuccess ? bytes : 0);
+  return e;
 }
 
 void release_pools(nolsm_ctx* ctx) {
@@ -75,6 +91,9 @@ void release_pools(nolsm_ctx* ctx) {
   dfree(ctx->d_dval); ctx->d_dval = nullptr;
   dfree(ctx->d_csr_own); ctx->d_csr_own = nullptr;
   dfree(ctx->d_tmaps); ctx->d_tmaps = nullptr;
+  dfree(ctx->d_sb); ctx->d_sb = nullptr;
+  dfree(ctx->d_t1); ctx->d_t1 = nullptr;
+  ctx->caps.clear();
   ctx->built = ctx->have_sign = ctx->have_density = false;
 }
 
@@ -191,7 +210,7 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   ctx->sticky = NOLSM_OK;   // a new build clears the sticky error
   ctx->last_error.clear();
-  release_pools(ctx);
+  ctx->built = ctx->have_sign = ctx->have_density = false;
   if (!H || !S || !blk_ptr || !blk_cols || n_blocks <= 0) return fail(ctx, NOLSM_EINVAL, "null argument or no blocks");
   if (H->n != S->n || H->nnz != S->nnz || H->n <= 0 || H->nnz <= 0 || H->memory != S->memory ||
       H->n > INT32_MAX)
@@ -209,7 +228,7 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
     std::memcpy(rp.data(), H->row_ptr, sizeof(int64_t) * (N + 1));
     std::memcpy(cl.data(), H->col, sizeof(int32_t) * nnz);
     const size_t bytes = sizeof(int64_t) * (N + 1) + sizeof(int32_t) * nnz + 2 * sizeof(double) * nnz + 64;
-    CK(cudaMalloc(&ctx->d_csr_own, bytes));
+    CK(dalloc(ctx, reinterpret_cast<uint8_t**>(&ctx->d_csr_own), bytes));
     uint8_t* base = reinterpret_cast<uint8_t*>(ctx->d_csr_own);
     double* hv = reinterpret_cast<double*>(base);
     double* sv = hv + nnz;
@@ -330,30 +349,30 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   // ---- device pools
   const bool mixed = is_mixed(ctx);
   const size_t xbytes = mixed ? 2 : 4;
-  CK(dalloc(&ctx->d_blocks, (size_t)n_blocks));
-  CK(dalloc(&ctx->d_idx, (size_t)ctx->sum_idx));
-  CK(dalloc(&ctx->d_own, (size_t)ctx->sum_own));
-  CK(dalloc(&ctx->d_blk_cols, ctx->h_blk_cols.size()));
-  CK(dalloc(&ctx->d_a0, (size_t)ctx->sum_sq));
-  CK(dalloc(&ctx->d_linv, (size_t)ctx->sum_sq));
-  CK(cudaMalloc(&ctx->d_x[0], xbytes * (size_t)ctx->sum_sq));
-  CK(cudaMalloc(&ctx->d_x[1], xbytes * (size_t)ctx->sum_sq));
-  CK(cudaMalloc(&ctx->d_b, xbytes * (size_t)ctx->sum_sq));
-  CK(dalloc(&ctx->d_w, (size_t)ctx->sum_slab));
-  CK(dalloc(&ctx->d_z, (size_t)ctx->sum_slab));
-  CK(dalloc(&ctx->d_lc, (size_t)ctx->sum_slab));
-  CK(dalloc(&ctx->d_y, (size_t)ctx->sum_slab));
-  CK(dalloc(&ctx->d_tmp, (size_t)std::max<int64_t>(6 * ctx->sum_slab, 4096)));
-  CK(dalloc(&ctx->d_lo, (size_t)n_blocks));
-  CK(dalloc(&ctx->d_hi, (size_t)n_blocks));
-  CK(dalloc(&ctx->d_bn, (size_t)n_blocks));
-  CK(dalloc(&ctx->d_be, (size_t)n_blocks));
-  CK(dalloc(&ctx->d_resacc, (size_t)n_blocks));
-  CK(dalloc(&ctx->d_tol, (size_t)n_blocks));
-  CK(dalloc(&ctx->d_state, (size_t)n_blocks));
-  CK(dalloc(&ctx->d_tiles, (size_t)tiles_max));
-  CK(dalloc(&ctx->d_transpose, (size_t)nnz));
-  CK(dalloc(&ctx->d_dval, (size_t)nnz));
+  CK(dalloc(ctx, &ctx->d_blocks, (size_t)n_blocks));
+  CK(dalloc(ctx, &ctx->d_idx, (size_t)ctx->sum_idx));
+  CK(dalloc(ctx, &ctx->d_own, (size_t)ctx->sum_own));
+  CK(dalloc(ctx, &ctx->d_blk_cols, ctx->h_blk_cols.size()));
+  CK(dalloc(ctx, &ctx->d_a0, (size_t)ctx->sum_sq));
+  CK(dalloc(ctx, &ctx->d_linv, (size_t)ctx->sum_sq));
+  CK(dalloc(ctx, reinterpret_cast<uint8_t**>(&ctx->d_x[0]), xbytes * (size_t)ctx->sum_sq));
+  CK(dalloc(ctx, reinterpret_cast<uint8_t**>(&ctx->d_x[1]), xbytes * (size_t)ctx->sum_sq));
+  CK(dalloc(ctx, reinterpret_cast<uint8_t**>(&ctx->d_b), xbytes * (size_t)ctx->sum_sq));
+  CK(dalloc(ctx, &ctx->d_w, (size_t)ctx->sum_slab));
+  CK(dalloc(ctx, &ctx->d_z, (size_t)ctx->sum_slab));
+  CK(dalloc(ctx, &ctx->d_lc, (size_t)ctx->sum_slab));
+  CK(dalloc(ctx, &ctx->d_y, (size_t)ctx->sum_slab));
+  CK(dalloc(ctx, &ctx->d_tmp, (size_t)std::max<int64_t>(6 * ctx->sum_slab, 4096)));
+  CK(dalloc(ctx, &ctx->d_lo, (size_t)n_blocks));
+  CK(dalloc(ctx, &ctx->d_hi, (size_t)n_blocks));
+  CK(dalloc(ctx, &ctx->d_bn, (size_t)n_blocks));
+  CK(dalloc(ctx, &ctx->d_be, (size_t)n_blocks));
+  CK(dalloc(ctx, &ctx->d_resacc, (size_t)n_blocks));
+  CK(dalloc(ctx, &ctx->d_tol, (size_t)n_blocks));
+  CK(dalloc(ctx, &ctx->d_state, (size_t)n_blocks));
+  CK(dalloc(ctx, &ctx->d_tiles, (size_t)tiles_max));
+  CK(dalloc(ctx, &ctx->d_transpose, (size_t)nnz));
+  CK(dalloc(ctx, &ctx->d_dval, (size_t)nnz));
   CK(cudaMemcpyAsync(ctx->d_blocks, ctx->h_blocks.data(), sizeof(BlockDesc) * n_blocks, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->d_idx, ctx->h_idx.data(), sizeof(int32_t) * ctx->sum_idx, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->d_own, h_own.data(), sizeof(int32_t) * ctx->sum_own, cudaMemcpyHostToDevice, ctx->stream));
@@ -372,28 +391,18 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   }
   CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(DevFlags), ctx->stream));
 
-  // ---- FP64 gather, factor, inverse; FP32 congruence and slabs
-  double* hb = nullptr;
-  double* sb = nullptr;
-  float* t1 = nullptr;
-  CK(dalloc(&hb, (size_t)ctx->sum_sq));
-  CK(dalloc(&sb, (size_t)(2 * ctx->sum_sq)));
-  CK(cudaMemsetAsync(hb, 0, sizeof(double) * ctx->sum_sq, ctx->stream));
-  CK(cudaMemsetAsync(sb, 0, sizeof(double) * 2 * ctx->sum_sq, ctx->stream));
-  CK(cudaMemsetAsync(ctx->d_linv, 0, sizeof(float) * ctx->sum_sq, ctx->stream));
-  ctx->n_launches += 10;   // gather, factor, inverse, conversions, two products, symmetrise, slabs, bounds
-  CK(launch_gather(ctx, hb, sb));
+  // ---- gather (H FP32 into A0's pool, S FP64), factor, inverse, congruence, slabs, bounds
+  CK(dalloc(ctx, &ctx->d_sb, (size_t)(2 * ctx->sum_sq)));
+  CK(dalloc(ctx, &ctx->d_t1, (size_t)ctx->sum_sq));
+  double* sb = ctx->d_sb;
+  ctx->n_launches += 8;   // gather, factor, inverse (+conversion), two products, slabs, bounds
+  CK(launch_gather(ctx, ctx->d_a0, sb));
   const int chol_mode = ctx->opt.chol_precision;
   const int chol32 = chol_mode == NOLSM_CHOL_FP32;
   CK(launch_cholesky_inverse(ctx, sb, chol_mode));
-  CK(dalloc(&t1, (size_t)ctx->sum_sq));
-  CK(launch_congruence(ctx, hb, sb, t1, chol32));
-  CK(launch_slabs_impl(ctx, chol32 ? (const void*)(sb + ctx->sum_sq) : (const void*)sb, chol32, t1));
+  CK(launch_congruence(ctx, ctx->d_t1));
+  CK(launch_slabs_impl(ctx, chol32 ? (const void*)(sb + ctx->sum_sq) : (const void*)sb, chol32, ctx->d_t1));
   CK(launch_bounds(ctx));
-  CK(cudaStreamSynchronize(ctx->stream));
-  cudaFree(hb);
-  cudaFree(sb);
-  cudaFree(t1);
   nolsm_status st = check_device_flags(ctx);
   if (st != NOLSM_OK) return st;
   ctx->h_lo.resize((size_t)n_blocks);

@@ -21,21 +21,27 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t* a, int n, int32_t 
 __device__ __forceinline__ void set_error(DevFlags* f, int code) { atomicCAS(&f->error, 0, code); }
 
 // ----------------------------------------------------------------------------------------------
-// Gather: dense T_b(H0) and T_b(S) (FP64, ld = n_pad) from the CSR rows listed in I_b.
-// One CTA per block, one warp per local row; I_b sits in shared memory for the column lookup.
-// The pools are zeroed beforehand; the padded diagonal of S is set to 1 here.
+// Gather: dense T_b(H0) (FP32) and T_b(S) (FP64), ld = n_pad, from the CSR rows listed in I_b.
+// One CTA per block: it first writes the block's whole padded region (zeros, and a unit
+// diagonal of S on the padding), then one warp per local row scatters the row's stored entries;
+// I_b sits in shared memory for the column lookup (binary search).
 __global__ void gather_kernel(const BlockDesc* __restrict__ blocks, const int32_t* __restrict__ idx_pool,
                               const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                               const double* __restrict__ hval, const double* __restrict__ sval,
-                              double* __restrict__ hb, double* __restrict__ sb, DevFlags* flags) {
+                              float* __restrict__ hb, double* __restrict__ sb, DevFlags* flags) {
   extern __shared__ int32_t s_idx[];
   const BlockDesc bd = blocks[blockIdx.x];
   const int n = bd.n, ld = bd.n_pad;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s_idx[i] = idx_pool[bd.off_idx + i];
-  __syncthreads();
-  double* H = hb + bd.off_mat;
+  float* H = hb + bd.off_mat;
   double* S = sb + bd.off_mat;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int r = warp; r < ld; r += nwarps)
+    for (int c = lane; c < ld; c += 32) {
+      H[(int64_t)r * ld + c] = 0.f;
+      S[(int64_t)r * ld + c] = (r == c && r >= n) ? 1.0 : 0.0;
+    }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s_idx[i] = idx_pool[bd.off_idx + i];
+  __syncthreads();
   for (int p = warp; p < n; p += nwarps) {
     const int32_t r = s_idx[p];
     const int64_t e0 = row_ptr[r], e1 = row_ptr[r + 1];
@@ -45,12 +51,11 @@ __global__ void gather_kernel(const BlockDesc* __restrict__ blocks, const int32_
       if (q < n && s_idx[q] == c) {
         const double h = hval[e], s = sval[e];
         if (!isfinite(h) || !isfinite(s)) set_error(flags, NOLSM_ENONFINITE);
-        H[(int64_t)p * ld + q] = h;
+        H[(int64_t)p * ld + q] = (float)h;
         S[(int64_t)p * ld + q] = s;
       }
     }
   }
-  for (int p = n + threadIdx.x; p < ld; p += blockDim.x) S[(int64_t)p * ld + p] = 1.0;
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -70,7 +75,7 @@ struct WarpChunk {
 // The strictly upper triangle is zeroed at the end.
 template <typename T>
 __global__ void __launch_bounds__(256) cholesky_kernel(const BlockDesc* __restrict__ blocks, T* __restrict__ pool,
-                                                       DevFlags* flags) {
+                                                       float* __restrict__ l32, DevFlags* flags) {
   __shared__ WarpChunk<T> chunks[8];
   __shared__ T diag[32][33];
   __shared__ int s_bad;
@@ -155,10 +160,14 @@ __global__ void __launch_bounds__(256) cholesky_kernel(const BlockDesc* __restri
     }
     __syncthreads();
   }
-  // zero the strict upper triangle of the n x n part
-  for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += blockDim.x) {
-    const int r = (int)(e / n), c = (int)(e % n);
-    if (c > r) A[(int64_t)r * ld + c] = T(0);
+  // Only the lower triangle of A is the factor (the strict upper part still holds S).  With
+  // l32 given, the factor is also written there in FP32, zero above the diagonal and on the
+  // padding.
+  if (l32) {
+    float* Lf = l32 + bd.off_mat;
+    for (int r = warp; r < ld; r += 8)
+      for (int c = lane; c < ld; c += 32)
+        Lf[(int64_t)r * ld + c] = (r < n && c <= r) ? (float)A[(int64_t)r * ld + c] : 0.f;
   }
   if (threadIdx.x == 0 && s_bad) set_error(flags, NOLSM_ENOTPD);
 }
@@ -178,6 +187,10 @@ __global__ void __launch_bounds__(256) trinv_kernel(const BlockDesc* __restrict_
   T* X = xpool + bd.off_mat;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   WarpChunk<T>& ch = chunks[warp];
+  // the output's upper triangle and padding stay zero
+  for (int r = warp; r < ld; r += 8)
+    for (int c = lane; c < ld; c += 32) X[(int64_t)r * ld + c] = T(0);
+  __syncthreads();
   const int nbk = (n + 31) / 32;
   for (int ib = 0; ib < nbk; ++ib) {
     const int i0 = ib * 32, ibw = min(32, n - i0);
@@ -312,7 +325,7 @@ inline dim3 sq_grid(int n_blocks) { return dim3(64, n_blocks); }
 
 }  // namespace
 
-cudaError_t launch_gather(nolsm_ctx* ctx, double* hb, double* sb) {
+cudaError_t launch_gather(nolsm_ctx* ctx, float* hb, double* sb) {
   int max_n = 0;
   for (auto& b : ctx->h_blocks) max_n = std::max(max_n, b.n);
   const size_t smem = sizeof(int32_t) * (size_t)max_n;
@@ -329,28 +342,23 @@ cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode) {
   // sb holds T_b(S) in FP64 (first sum_sq doubles); the second half is scratch.
   float* s32 = reinterpret_cast<float*>(sb + ctx->sum_sq);   // FP32 factor lives in the scratch half
   if (mode == NOLSM_CHOL_FP64_INV64) {
-    cholesky_kernel<double><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, sb, ctx->d_flags);
+    cholesky_kernel<double><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, sb, nullptr, ctx->d_flags);
     trinv_kernel<double><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, sb, sb + ctx->sum_sq);
     to_f32_kernel<double><<<sq_grid(ctx->n_blocks), 256, 0, ctx->stream>>>(ctx->d_blocks, sb + ctx->sum_sq, ctx->d_linv, 1);
   } else if (mode == NOLSM_CHOL_FP64) {
-    cholesky_kernel<double><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, sb, ctx->d_flags);
-    to_f32_kernel<double><<<sq_grid(ctx->n_blocks), 256, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, 1);
+    cholesky_kernel<double><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, ctx->d_flags);
     trinv_kernel<float><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
   } else {
     to_f32_kernel<double><<<sq_grid(ctx->n_blocks), 256, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, 0);
-    cholesky_kernel<float><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_flags);
+    cholesky_kernel<float><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, s32, nullptr, ctx->d_flags);
     trinv_kernel<float><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_congruence(nolsm_ctx* ctx, const double* hb, const double* sb_linv, float* t1, int fp32) {
-  (void)sb_linv; (void)fp32;
-  // H_b -> FP32 (into A0's pool as scratch), T1 = L^-1 H_b (H symmetric: NT form), A0 = T1 L^-T.
-  to_f32_kernel<double><<<sq_grid(ctx->n_blocks), 256, 0, ctx->stream>>>(ctx->d_blocks, hb, ctx->d_a0, 0);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  e = launch_sgemm_nt(ctx, ctx->d_linv, ctx->d_a0, t1, /*a_lower=*/1, /*b_lower=*/0, /*sym=*/0);
+cudaError_t launch_congruence(nolsm_ctx* ctx, float* t1) {
+  // T_b(H0) (FP32) sits in A0's pool.  T1 = L^-1 H_b (H symmetric: NT form), A0 = T1 L^-T.
+  cudaError_t e = launch_sgemm_nt(ctx, ctx->d_linv, ctx->d_a0, t1, /*a_lower=*/1, /*b_lower=*/0, /*sym=*/0);
   if (e != cudaSuccess) return e;
   // A0 is symmetric: upper tiles only, mirrored stores (exactly symmetric, half the work)
   return launch_sgemm_nt(ctx, t1, ctx->d_linv, ctx->d_a0, 0, /*b_lower=*/1, /*sym=*/1);

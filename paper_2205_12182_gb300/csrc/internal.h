@@ -126,6 +126,12 @@ struct nolsm_ctx {
   int64_t* d_transpose = nullptr;       // position of (j,i) for entry (i,j)
   double* d_dval = nullptr;             // assembled D on the pattern
 
+  // build scratch kept across builds: FP64 S and its factor (2 sum_sq doubles), T1 (sum_sq floats)
+  double* d_sb = nullptr;
+  float* d_t1 = nullptr;
+  // capacity in bytes of every pool the context owns (pools only grow)
+  std::vector<std::pair<void**, size_t>> caps;
+
   // tensor-core operand descriptors (device array of CUtensorMap, opaque bytes)
   void* d_tmaps = nullptr;
   int n_tmaps = 0;
@@ -151,9 +157,9 @@ nolsm_status fail(nolsm_ctx* ctx, nolsm_status st, const std::string& msg);
 nolsm_status cuda_fail(nolsm_ctx* ctx, cudaError_t e, const char* what);
 
 // build.cu
-cudaError_t launch_gather(nolsm_ctx* ctx, double* hb, double* sb);
+cudaError_t launch_gather(nolsm_ctx* ctx, float* hb, double* sb);
 cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode);
-cudaError_t launch_congruence(nolsm_ctx* ctx, const double* hb, const double* sb_linv, float* t1_scratch, int fp32);
+cudaError_t launch_congruence(nolsm_ctx* ctx, float* t1_scratch);
 cudaError_t launch_slabs_impl(nolsm_ctx* ctx, const void* lfac, int fp32, const float* t1);
 cudaError_t launch_bounds(nolsm_ctx* ctx);
 
