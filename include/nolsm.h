@@ -196,6 +196,25 @@ nolsm_status nolsm_block_matrix(const nolsm_ctx* ctx, int32_t b, int32_t which, 
 nolsm_status nolsm_counters(nolsm_ctx* ctx, int64_t* launches, int64_t* gemm_launches, double* gemm_ms,
                             double* gemm_flops, int32_t reset);
 
+/* Band energy spin_factor * sum_e d_val[e] * h_val[e] over nnz stored entries (the reduction of
+ * nolsm_band_energy), for callers that must not allocate device memory: the call needs no
+ * context, makes no cudaMalloc/cudaFree or other allocating call, and keeps its partial sums in
+ * a fixed 32 KB array in device memory that the library declares at file scope (every GPU that
+ * loads the library holds it until the process exits).  d_val and h_val are device arrays on
+ * one symmetric pattern (so H0_ji = H0_ij), e_out is one device double, all owned by the caller;
+ * work is enqueued on cuda_stream (a cudaStream_t, NULL = legacy default stream) and the call
+ * returns without synchronising.  The paper has no counterpart: this is a library convenience.
+ * Limits and behaviour:
+ *  - nnz may not exceed 268,435,456 (4,096 partial sums of 65,536 entries); larger inputs,
+ *    nnz <= 0, null pointers or spin_factor <= 0 return NOLSM_EINVAL before any launch.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *    that device current; make that first call before any stream capture.
+ *  - Every call on a device shares the array and leaves its partial sums in it; calls whose work
+ *    overlaps on the GPU (other streams, no ordering between them) race on it.
+ *  - Returns NOLSM_ECUDA when the lookup or a launch fails. */
+nolsm_status nolsm_band_energy_noalloc(int64_t nnz, const double* d_val, const double* h_val, double spin_factor,
+                                       double* e_out, void* cuda_stream);
+
 /* Message of the last error of ctx (never NULL; "" when none).  ctx may be NULL. */
 const char* nolsm_last_error(const nolsm_ctx* ctx);
 

@@ -24,7 +24,8 @@ CHOL_FP64, CHOL_FP32, CHOL_FP64_INV64 = 0, 1, 2
 
 FUNCTIONS = ["nolsm_default_options", "nolsm_create", "nolsm_build_submatrices", "nolsm_sign_batch", "nolsm_set_mu",
              "nolsm_density", "nolsm_band_energy", "nolsm_block_info", "nolsm_block_index_set", "nolsm_block_bounds",
-             "nolsm_block_state", "nolsm_block_matrix", "nolsm_counters", "nolsm_last_error", "nolsm_destroy"]
+             "nolsm_block_state", "nolsm_block_matrix", "nolsm_counters", "nolsm_band_energy_noalloc",
+             "nolsm_last_error", "nolsm_destroy"]
 
 
 class NolsmCsr(C.Structure):
@@ -76,6 +77,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "nolsm_block_state": (i32, [P, P, P, P]),
         "nolsm_block_matrix": (i32, [P, i32, i32, P]),
         "nolsm_counters": (i32, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), pf64, pf64, i32]),
+        "nolsm_band_energy_noalloc": (i32, [i64, P, P, f64, P, P]),
         "nolsm_last_error": (C.c_char_p, [P]),
         "nolsm_destroy": (None, [P]),
     }
@@ -188,6 +190,12 @@ def nolsm_counters(ctx, reset=False) -> dict:
     ms, fl = C.c_double(), C.c_double()
     _check(ctx, _lib.nolsm_counters(ctx, C.byref(la), C.byref(ga), C.byref(ms), C.byref(fl), int(bool(reset))))
     return {"launches": la.value, "gemm_launches": ga.value, "gemm_ms": ms.value, "gemm_flops": fl.value}
+
+
+def nolsm_band_energy_noalloc(nnz, d_val, h_val, spin_factor, e_out, stream=None):
+    """Band energy into the device double e_out without allocating (see include/nolsm.h)."""
+    _check(None, _lib.nolsm_band_energy_noalloc(int(nnz), _ptr(d_val), _ptr(h_val), float(spin_factor),
+                                                _ptr(e_out), stream))
 
 
 def nolsm_last_error(ctx) -> str:
