@@ -90,6 +90,9 @@ void release_pools(nolsm_ctx* ctx) {
   dfree(ctx->d_transpose); ctx->d_transpose = nullptr;
   dfree(ctx->d_dval); ctx->d_dval = nullptr;
   dfree(ctx->d_csr_own); ctx->d_csr_own = nullptr;
+  dfree(ctx->d_bptr); ctx->d_bptr = nullptr;
+  dfree(ctx->d_extra); ctx->d_extra = nullptr;
+  dfree(ctx->d_nb); ctx->d_nb = nullptr;
   dfree(ctx->d_tmaps); ctx->d_tmaps = nullptr;
   dfree(ctx->d_sb); ctx->d_sb = nullptr;
   dfree(ctx->d_t1); ctx->d_t1 = nullptr;
@@ -220,13 +223,22 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   ctx->n = N;
   ctx->nnz = nnz;
   ctx->n_blocks = n_blocks;
+  if (blk_ptr[0] != 0) return fail(ctx, NOLSM_EINVAL, "blk_ptr[0] must be 0");
+  for (int32_t b = 0; b < n_blocks; ++b) {
+    if (blk_ptr[b + 1] <= blk_ptr[b]) return fail(ctx, NOLSM_EINVAL, "every block needs at least one column");
+    if (extra_ptr && extra_ptr[b + 1] < extra_ptr[b]) return fail(ctx, NOLSM_EINVAL, "extra_ptr not monotone");
+  }
+  if (extra_ptr && extra_ptr[0] != 0) return fail(ctx, NOLSM_EINVAL, "extra_ptr[0] must be 0");
+  const int64_t n_cols = blk_ptr[n_blocks];
+  const int64_t n_extra = extra_ptr ? extra_ptr[n_blocks] : 0;
+  ctx->h_blk_cols.assign(blk_cols, blk_cols + n_cols);
+  for (int64_t k = 0; k < n_cols; ++k)
+    if (blk_cols[k] < 0 || blk_cols[k] >= N) return fail(ctx, NOLSM_EINVAL, "block column out of range");
 
-  // ---- CSR on the device (staged when host-resident) and on the host (pattern only)
+  // ---- CSR on the device (staged when host-resident); the row pointers also on the host
   std::vector<int64_t> rp((size_t)N + 1);
-  std::vector<int32_t> cl((size_t)nnz);
   if (H->memory == NOLSM_MEM_HOST) {
     std::memcpy(rp.data(), H->row_ptr, sizeof(int64_t) * (N + 1));
-    std::memcpy(cl.data(), H->col, sizeof(int32_t) * nnz);
     const size_t bytes = sizeof(int64_t) * (N + 1) + sizeof(int32_t) * nnz + 2 * sizeof(double) * nnz + 64;
     CK(dalloc(ctx, reinterpret_cast<uint8_t**>(&ctx->d_csr_own), bytes));
     uint8_t* base = reinterpret_cast<uint8_t*>(ctx->d_csr_own);
@@ -241,58 +253,49 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
     ctx->d_hval = hv; ctx->d_sval = sv; ctx->d_row_ptr = rpd; ctx->d_col = cld;
   } else {
     CK(cudaMemcpyAsync(rp.data(), H->row_ptr, sizeof(int64_t) * (N + 1), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(cl.data(), H->col, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, ctx->stream));
     ctx->d_hval = H->val; ctx->d_sval = S->val; ctx->d_row_ptr = H->row_ptr; ctx->d_col = H->col;
   }
   CK(cudaStreamSynchronize(ctx->stream));
   if (rp[0] != 0 || rp[N] != nnz) return fail(ctx, NOLSM_EINVAL, "row_ptr must start at 0 and end at nnz");
-  // pattern checks and the transpose permutation (entry (i,j) -> position of (j,i))
-  std::vector<int64_t> transpose((size_t)nnz);
-  for (int64_t r = 0; r < N; ++r) {
-    if (rp[r + 1] < rp[r]) return fail(ctx, NOLSM_EINVAL, "row_ptr not monotone");
-    bool diag = false;
-    for (int64_t e = rp[r]; e < rp[r + 1]; ++e) {
-      const int32_t c = cl[e];
-      if (c < 0 || c >= N || (e > rp[r] && cl[e - 1] >= c)) return fail(ctx, NOLSM_EINVAL, "columns out of range or not ascending");
-      if (c == r) diag = true;
-      const int32_t* b = cl.data() + rp[c];
-      const int32_t* en = cl.data() + rp[c + 1];
-      const int32_t* f = std::lower_bound(b, en, (int32_t)r);
-      if (f == en || *f != r) return fail(ctx, NOLSM_EINVAL, "pattern is not structurally symmetric");
-      transpose[e] = rp[c] + (f - b);
-    }
-    if (!diag) return fail(ctx, NOLSM_EINVAL, "pattern misses a diagonal entry");
+  // candidates of each block's index set: the own columns' row counts plus its extra list
+  int64_t max_cand = 1;
+  for (int32_t b = 0; b < n_blocks; ++b) {
+    int64_t m = extra_ptr ? (extra_ptr[b + 1] - extra_ptr[b]) : 0;
+    for (int32_t k = blk_ptr[b]; k < blk_ptr[b + 1]; ++k) m += rp[blk_cols[k] + 1] - rp[blk_cols[k]];
+    max_cand = std::max(max_cand, m);
   }
+  if (max_cand > kMaxCandidates)
+    return fail(ctx, NOLSM_EINVAL, "a block's own columns and extra list hold more than 32768 entries");
+  int cap = 256;
+  while (cap < max_cand) cap <<= 1;
 
-  // ---- index sets: pattern rule (rows of the own columns) unioned with the extra list
-  if (blk_ptr[0] != 0) return fail(ctx, NOLSM_EINVAL, "blk_ptr[0] must be 0");
-  ctx->h_blk_cols.assign(blk_cols, blk_cols + blk_ptr[n_blocks]);
-  std::vector<std::vector<int32_t>> sets((size_t)n_blocks);
-  std::vector<std::vector<int32_t>> owns((size_t)n_blocks);
+  // ---- transpose positions, pattern checks and index sets on the device
+  CK(dalloc(ctx, &ctx->d_idx, (size_t)n_blocks * kMaxDim));
+  CK(dalloc(ctx, &ctx->d_own, (size_t)n_cols));
+  CK(dalloc(ctx, &ctx->d_blk_cols, (size_t)n_cols));
+  CK(dalloc(ctx, &ctx->d_bptr, (size_t)(2 * (n_blocks + 1))));
+  CK(dalloc(ctx, &ctx->d_extra, (size_t)std::max<int64_t>(n_extra, 1)));
+  CK(dalloc(ctx, &ctx->d_nb, (size_t)n_blocks));
+  CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(DevFlags), ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_blk_cols, blk_cols, sizeof(int32_t) * n_cols, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_bptr, blk_ptr, sizeof(int32_t) * (n_blocks + 1), cudaMemcpyHostToDevice, ctx->stream));
+  if (extra_ptr) {
+    CK(cudaMemcpyAsync(ctx->d_bptr + n_blocks + 1, extra_ptr, sizeof(int32_t) * (n_blocks + 1), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_extra, extra_idx, sizeof(int32_t) * n_extra, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  CK(launch_transpose(ctx));
+  CK(launch_index_sets(ctx, ctx->d_bptr, extra_ptr ? ctx->d_bptr + n_blocks + 1 : nullptr,
+                       extra_ptr ? ctx->d_extra : nullptr, ctx->d_nb, cap));
+  ctx->n_launches += 2;
+  std::vector<int32_t> nb((size_t)n_blocks);
+  CK(cudaMemcpyAsync(nb.data(), ctx->d_nb, sizeof(int32_t) * n_blocks, cudaMemcpyDeviceToHost, ctx->stream));
   {
-    std::vector<int32_t> mark((size_t)N, -1);
-    for (int32_t b = 0; b < n_blocks; ++b) {
-      if (blk_ptr[b + 1] <= blk_ptr[b]) return fail(ctx, NOLSM_EINVAL, "every block needs at least one column");
-      auto& set = sets[b];
-      for (int32_t k = blk_ptr[b]; k < blk_ptr[b + 1]; ++k) {
-        const int32_t c = blk_cols[k];
-        if (c < 0 || c >= N) return fail(ctx, NOLSM_EINVAL, "block column out of range");
-        for (int64_t e = rp[c]; e < rp[c + 1]; ++e) {   // symmetric pattern: column c's rows = row c's columns
-          const int32_t r = cl[e];
-          if (mark[r] != b) { mark[r] = b; set.push_back(r); }
-        }
-      }
-      if (extra_ptr) {
-        for (int32_t k = extra_ptr[b]; k < extra_ptr[b + 1]; ++k) {
-          const int32_t r = extra_idx[k];
-          if (r < 0 || r >= N) return fail(ctx, NOLSM_EINVAL, "extra index out of range");
-          if (mark[r] != b) { mark[r] = b; set.push_back(r); }
-        }
-      }
-      std::sort(set.begin(), set.end());
-      if ((int)set.size() > kMaxDim) return fail(ctx, NOLSM_EINVAL, "a submatrix dimension exceeds 4096");
-      for (int32_t k = blk_ptr[b]; k < blk_ptr[b + 1]; ++k)
-        owns[b].push_back((int32_t)(std::lower_bound(set.begin(), set.end(), blk_cols[k]) - set.begin()));
+    nolsm_status st0 = check_device_flags(ctx);
+    if (st0 != NOLSM_OK) {
+      ctx->last_error = "pattern not symmetric / columns out of order or range / missing diagonal, or a "
+                        "submatrix dimension above 4096";
+      return st0;
     }
   }
 
@@ -300,28 +303,18 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   ctx->h_blocks.assign((size_t)n_blocks, BlockDesc{});
   std::vector<int32_t> order((size_t)n_blocks);
   std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-    return pad_dim((int)sets[a].size()) < pad_dim((int)sets[b].size());
-  });
-  int64_t off_mat = 0, off_slab = 0, off_idx = 0, off_own = 0;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return pad_dim(nb[a]) < pad_dim(nb[b]); });
+  int64_t off_mat = 0, off_slab = 0;
   int bin = -1, pos = 0, last_pad = -1;
-  ctx->h_idx.clear();
-  ctx->h_idx.reserve(1024);
-  std::vector<int32_t> h_own;
   ctx->flops_paper_iter = ctx->flops_exec_iter = 0.0;
-  // index and own pools keep the caller's block order; square/slab pools follow the bin order
   for (int32_t b = 0; b < n_blocks; ++b) {
     BlockDesc& bd = ctx->h_blocks[b];
-    bd.n = (int32_t)sets[b].size();
+    bd.n = nb[b];
     bd.n_pad = pad_dim(bd.n);
     bd.c = blk_ptr[b + 1] - blk_ptr[b];
     bd.col0 = blk_ptr[b];
-    bd.off_idx = off_idx;
-    bd.off_own = off_own;
-    ctx->h_idx.insert(ctx->h_idx.end(), sets[b].begin(), sets[b].end());
-    h_own.insert(h_own.end(), owns[b].begin(), owns[b].end());
-    off_idx += bd.n;
-    off_own += bd.c;
+    bd.off_idx = (int64_t)b * kMaxDim;
+    bd.off_own = blk_ptr[b];
     ctx->flops_paper_iter += 2.0 * 2.0 * (double)bd.n * bd.n * bd.n;
     ctx->flops_exec_iter += 2.0 * (double)bd.n_pad * bd.n_pad * (bd.n_pad + kTile);
   }
@@ -337,8 +330,8 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   }
   ctx->sum_sq = off_mat;
   ctx->sum_slab = off_slab;
-  ctx->sum_idx = off_idx;
-  ctx->sum_own = off_own;
+  ctx->sum_idx = (int64_t)n_blocks * kMaxDim;
+  ctx->sum_own = n_cols;
   int64_t tiles_max = 0;
   for (const auto& bd : ctx->h_blocks) tiles_max += (int64_t)(bd.n_pad / kTile) * (bd.n_pad / kTile);
   ctx->max_tiles = tiles_max;
@@ -350,9 +343,6 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   const bool mixed = is_mixed(ctx);
   const size_t xbytes = mixed ? 2 : 4;
   CK(dalloc(ctx, &ctx->d_blocks, (size_t)n_blocks));
-  CK(dalloc(ctx, &ctx->d_idx, (size_t)ctx->sum_idx));
-  CK(dalloc(ctx, &ctx->d_own, (size_t)ctx->sum_own));
-  CK(dalloc(ctx, &ctx->d_blk_cols, ctx->h_blk_cols.size()));
   CK(dalloc(ctx, &ctx->d_a0, (size_t)ctx->sum_sq));
   CK(dalloc(ctx, &ctx->d_linv, (size_t)ctx->sum_sq));
   CK(dalloc(ctx, reinterpret_cast<uint8_t**>(&ctx->d_x[0]), xbytes * (size_t)ctx->sum_sq));
@@ -371,14 +361,8 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   CK(dalloc(ctx, &ctx->d_tol, (size_t)n_blocks));
   CK(dalloc(ctx, &ctx->d_state, (size_t)n_blocks));
   CK(dalloc(ctx, &ctx->d_tiles, (size_t)tiles_max));
-  CK(dalloc(ctx, &ctx->d_transpose, (size_t)nnz));
   CK(dalloc(ctx, &ctx->d_dval, (size_t)nnz));
   CK(cudaMemcpyAsync(ctx->d_blocks, ctx->h_blocks.data(), sizeof(BlockDesc) * n_blocks, cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(ctx->d_idx, ctx->h_idx.data(), sizeof(int32_t) * ctx->sum_idx, cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(ctx->d_own, h_own.data(), sizeof(int32_t) * ctx->sum_own, cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(ctx->d_blk_cols, ctx->h_blk_cols.data(), sizeof(int32_t) * ctx->h_blk_cols.size(),
-                     cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(ctx->d_transpose, transpose.data(), sizeof(int64_t) * nnz, cudaMemcpyHostToDevice, ctx->stream));
   {
     std::vector<float> tol((size_t)n_blocks);
     const double u = unit_roundoff(ctx);
@@ -389,7 +373,6 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
     CK(cudaMemcpyAsync(ctx->d_tol, tol.data(), sizeof(float) * n_blocks, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
   }
-  CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(DevFlags), ctx->stream));
 
   // ---- gather (H FP32 into A0's pool, S FP64), factor, inverse, congruence, slabs, bounds
   CK(dalloc(ctx, &ctx->d_sb, (size_t)(2 * ctx->sum_sq)));
@@ -612,7 +595,9 @@ nolsm_status nolsm_block_info(const nolsm_ctx* ctx, int32_t b, int32_t* n_b, int
 nolsm_status nolsm_block_index_set(const nolsm_ctx* ctx, int32_t b, int32_t* idx_out) {
   if (!ctx || !ctx->built || b < 0 || b >= ctx->n_blocks || !idx_out) return NOLSM_EINVAL;
   const BlockDesc& bd = ctx->h_blocks[b];
-  std::memcpy(idx_out, ctx->h_idx.data() + bd.off_idx, sizeof(int32_t) * bd.n);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return NOLSM_ECUDA;
+  if (cudaMemcpy(idx_out, ctx->d_idx + bd.off_idx, sizeof(int32_t) * bd.n, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return NOLSM_ECUDA;
   return NOLSM_OK;
 }
 

@@ -1,0 +1,178 @@
+// Step 1 of the submatrix method on the GPU: the pattern checks, the transpose position of every
+// stored entry, and the index set I_b of every block -- the rows holding a stored entry in any of
+// the block's own columns (on the combined pattern of H0 and S), unioned with the block's extra
+// indices -- sorted ascending, with the local positions of the own columns.
+#include "internal.h"
+
+#include <climits>
+
+namespace nolsm {
+namespace {
+
+__device__ __forceinline__ void set_error(DevFlags* f, int code) { atomicCAS(&f->error, 0, code); }
+
+// One warp per row r: column range/order checks, the diagonal, and for entry (r, c) the
+// position of (c, r) in row c (binary search; a miss means the pattern is not symmetric).
+__global__ void transpose_kernel(int64_t n, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                 int64_t* __restrict__ transpose, DevFlags* flags) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
+    const int64_t e0 = row_ptr[r], e1 = row_ptr[r + 1];
+    bool diag = false;
+    if (e1 < e0) set_error(flags, NOLSM_EINVAL);
+    for (int64_t e = e0 + lane; e < e1; e += 32) {
+      const int32_t c = col[e];
+      if (c < 0 || c >= n || (e > e0 && col[e - 1] >= c)) { set_error(flags, NOLSM_EINVAL); continue; }
+      if (c == r) diag = true;
+      int64_t lo = row_ptr[c], hi = row_ptr[c + 1];
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (col[mid] < r) lo = mid + 1; else hi = mid;
+      }
+      if (lo < row_ptr[c + 1] && col[lo] == r) transpose[e] = lo;
+      else set_error(flags, NOLSM_EINVAL);
+    }
+    if (!__any_sync(0xffffffffu, diag) && lane == 0) set_error(flags, NOLSM_EINVAL);
+  }
+}
+
+// One CTA per block: gather the candidate rows into shared memory, bitonic sort, keep the first
+// of every run of equal values.  I_b goes to idx[b * kMaxDim ...], |I_b| to n_out[b], and the
+// local position of own column j to own[blk_ptr[b] + j].  More than kMaxDim distinct rows, or
+// more than cap candidates, is an EINVAL error for the block.
+__global__ void __launch_bounds__(512) index_set_kernel(int64_t n, const int64_t* __restrict__ row_ptr,
+                                                        const int32_t* __restrict__ col,
+                                                        const int32_t* __restrict__ blk_ptr,
+                                                        const int32_t* __restrict__ blk_cols,
+                                                        const int32_t* __restrict__ extra_ptr,
+                                                        const int32_t* __restrict__ extra_idx, int cap,
+                                                        int32_t* __restrict__ idx, int32_t* __restrict__ own,
+                                                        int32_t* __restrict__ n_out, DevFlags* flags) {
+  extern __shared__ int32_t cand[];          // cap entries
+  __shared__ int32_t s_count;
+  __shared__ int32_t warp_tot[16];
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_count = 0;
+  __syncthreads();
+  // candidates: the rows of every own column (row c's columns: the pattern is symmetric) + extras
+  const int32_t c0 = blk_ptr[b], c1 = blk_ptr[b + 1];
+  for (int32_t k = c0; k < c1; ++k) {
+    const int32_t c = blk_cols[k];
+    if (c < 0 || c >= n) { if (tid == 0) set_error(flags, NOLSM_EINVAL); continue; }
+    const int64_t e0 = row_ptr[c], e1 = row_ptr[c + 1];
+    const int deg = (int)(e1 - e0);
+    const int base = s_count;
+    __syncthreads();
+    for (int i = tid; i < deg; i += blockDim.x)
+      if (base + i < cap) cand[base + i] = col[e0 + i];
+    __syncthreads();
+    if (tid == 0) s_count = base + deg;
+    __syncthreads();
+  }
+  if (extra_ptr) {
+    const int32_t x0 = extra_ptr[b], x1 = extra_ptr[b + 1];
+    const int base = s_count;
+    for (int i = tid; i < x1 - x0; i += blockDim.x) {
+      const int32_t v = extra_idx[x0 + i];
+      if (v < 0 || v >= n) set_error(flags, NOLSM_EINVAL);
+      if (base + i < cap) cand[base + i] = min(max(v, 0), (int32_t)n - 1);
+    }
+    __syncthreads();
+    if (tid == 0) s_count = base + (x1 - x0);
+    __syncthreads();
+  }
+  const int m = s_count;
+  if (m > cap) {
+    if (tid == 0) { set_error(flags, NOLSM_EINVAL); n_out[b] = 0; }
+    return;
+  }
+  int p2 = 1;
+  while (p2 < m) p2 <<= 1;
+  for (int i = m + tid; i < p2; i += blockDim.x) cand[i] = INT_MAX;
+  __syncthreads();
+  // bitonic sort, ascending
+  for (int k = 2; k <= p2; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < p2; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const int32_t a = cand[i], c = cand[l];
+          const bool up = (i & k) == 0;
+          if ((a > c) == up) { cand[i] = c; cand[l] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  // unique: positions by a block-wide scan over chunks of blockDim
+  __shared__ int32_t s_base;
+  if (tid == 0) s_base = 0;
+  __syncthreads();
+  const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int i0 = 0; i0 < m; i0 += blockDim.x) {
+    const int i = i0 + tid;
+    const int keep = (i < m) && (i == 0 || cand[i] != cand[i - 1]);
+    const unsigned ballot = __ballot_sync(0xffffffffu, keep);
+    const int before = __popc(ballot & ((1u << lane) - 1u));
+    if (lane == 0) warp_tot[warp] = __popc(ballot);
+    __syncthreads();
+    int off = s_base;
+    for (int w = 0; w < warp; ++w) off += warp_tot[w];
+    const int32_t v = (i < m) ? cand[i] : 0;
+    __syncthreads();
+    if (keep && off + before < kMaxDim) idx[(int64_t)b * kMaxDim + off + before] = v;
+    if (tid == 0) {
+      int t = 0;
+      for (int w = 0; w < nw; ++w) t += warp_tot[w];
+      s_base += t;
+    }
+    __syncthreads();
+  }
+  const int nb = s_base;
+  if (tid == 0) n_out[b] = nb;
+  if (nb > kMaxDim) {
+    if (tid == 0) set_error(flags, NOLSM_EINVAL);
+    return;
+  }
+  __syncthreads();
+  // own-column positions (every own column is its own row's diagonal, so it is in I_b)
+  const int32_t* I = idx + (int64_t)b * kMaxDim;
+  for (int32_t k = c0 + tid; k < c1; k += blockDim.x) {
+    const int32_t c = blk_cols[k];
+    int lo = 0, hi = nb;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (I[mid] < c) lo = mid + 1; else hi = mid;
+    }
+    own[k] = lo;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_transpose(nolsm_ctx* ctx) {
+  const int threads = 256;
+  const int64_t warps_needed = ctx->n;
+  const int grid = (int)std::min<int64_t>((warps_needed * 32 + threads - 1) / threads, (int64_t)ctx->num_sms * 16);
+  transpose_kernel<<<grid, threads, 0, ctx->stream>>>(ctx->n, ctx->d_row_ptr, ctx->d_col, ctx->d_transpose,
+                                                      ctx->d_flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_index_sets(nolsm_ctx* ctx, const int32_t* d_blk_ptr, const int32_t* d_extra_ptr,
+                              const int32_t* d_extra_idx, int32_t* d_nb, int cap) {
+  const size_t smem = sizeof(int32_t) * (size_t)cap;
+  static size_t attr = 0;
+  if (smem > 48 * 1024 && smem > attr) {
+    cudaError_t e = cudaFuncSetAttribute(index_set_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = smem;
+  }
+  index_set_kernel<<<ctx->n_blocks, 512, smem, ctx->stream>>>(ctx->n, ctx->d_row_ptr, ctx->d_col, d_blk_ptr,
+                                                              ctx->d_blk_cols, d_extra_ptr, d_extra_idx, cap,
+                                                              ctx->d_idx, ctx->d_own, d_nb, ctx->d_flags);
+  return cudaGetLastError();
+}
+
+}  // namespace nolsm

@@ -16,6 +16,7 @@ namespace nolsm {
 // Output tile edge of every matrix-product kernel; submatrices are padded to it.
 constexpr int kTile = 128;
 constexpr int kMaxDim = 4096;
+constexpr int kMaxCandidates = 32768;   // own-column rows + extra indices of one block
 
 inline int pad_dim(int n) { return (n + kTile - 1) / kTile * kTile; }
 
@@ -83,7 +84,6 @@ struct nolsm_ctx {
   int32_t n_blocks = 0;
   int64_t n = 0, nnz = 0;
   std::vector<nolsm::BlockDesc> h_blocks;
-  std::vector<int32_t> h_idx;           // concatenated index sets
   std::vector<int32_t> h_blk_cols;
   std::vector<double> h_lo, h_hi;       // spectral bounds of A0 per block
   std::vector<int32_t> h_iters;
@@ -95,6 +95,9 @@ struct nolsm_ctx {
   int32_t* d_idx = nullptr;
   int32_t* d_own = nullptr;
   int32_t* d_blk_cols = nullptr;
+  int32_t* d_bptr = nullptr;    // blk_ptr then extra_ptr (device copies)
+  int32_t* d_extra = nullptr;   // extra indices (device copy)
+  int32_t* d_nb = nullptr;      // |I_b| per block
   float* d_a0 = nullptr;        // A0, fp32, square pool
   float* d_linv = nullptr;      // L^-1, fp32, square pool
   void* d_x[2] = {nullptr, nullptr};   // iterates (fp32 or fp16/bf16), square pools
@@ -179,6 +182,11 @@ cudaError_t launch_band_energy(nolsm_ctx* ctx);
 cudaError_t tc_prepare(nolsm_ctx* ctx);
 cudaError_t launch_gemm_tc(nolsm_ctx* ctx, int phase);
 int tc_tile_n();
+
+// index.cu
+cudaError_t launch_transpose(nolsm_ctx* ctx);
+cudaError_t launch_index_sets(nolsm_ctx* ctx, const int32_t* d_blk_ptr, const int32_t* d_extra_ptr,
+                              const int32_t* d_extra_idx, int32_t* d_nb, int cap);
 
 // generic SIMT NT product used by the build: C_b = A_b B_b^T on the block table
 cudaError_t launch_sgemm_nt(nolsm_ctx* ctx, const float* a, const float* b, float* c, int a_lower, int b_lower,
