@@ -270,6 +270,7 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   while (cap < max_cand) cap <<= 1;
 
   // ---- transpose positions, pattern checks and index sets on the device
+  CK(dalloc(ctx, &ctx->d_transpose, (size_t)nnz));
   CK(dalloc(ctx, &ctx->d_idx, (size_t)n_blocks * kMaxDim));
   CK(dalloc(ctx, &ctx->d_own, (size_t)n_cols));
   CK(dalloc(ctx, &ctx->d_blk_cols, (size_t)n_cols));

@@ -152,6 +152,7 @@ __global__ void __launch_bounds__(512) index_set_kernel(int64_t n, const int64_t
 }  // namespace
 
 cudaError_t launch_transpose(nolsm_ctx* ctx) {
+  if (!ctx->d_row_ptr || !ctx->d_col || !ctx->d_transpose || !ctx->d_flags) return cudaErrorInvalidValue;
   const int threads = 256;
   const int64_t warps_needed = ctx->n;
   const int grid = (int)std::min<int64_t>((warps_needed * 32 + threads - 1) / threads, (int64_t)ctx->num_sms * 16);
@@ -162,6 +163,8 @@ cudaError_t launch_transpose(nolsm_ctx* ctx) {
 
 cudaError_t launch_index_sets(nolsm_ctx* ctx, const int32_t* d_blk_ptr, const int32_t* d_extra_ptr,
                               const int32_t* d_extra_idx, int32_t* d_nb, int cap) {
+  if (!d_blk_ptr || !d_nb || !ctx->d_blk_cols || !ctx->d_idx || !ctx->d_own || (cap & (cap - 1)) != 0)
+    return cudaErrorInvalidValue;
   const size_t smem = sizeof(int32_t) * (size_t)cap;
   static size_t attr = 0;
   if (smem > 48 * 1024 && smem > attr) {
