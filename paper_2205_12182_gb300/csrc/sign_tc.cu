@@ -89,13 +89,6 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tmap, 
       : "memory");
 }
 
-// Bring a box into L2 ahead of its load (no shared memory, no barrier).
-__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* tmap, int x, int y) {
-  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global [%0, {%1, %2}];" ::"l"(reinterpret_cast<uint64_t>(tmap)),
-               "r"(x), "r"(y)
-               : "memory");
-}
-
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -259,16 +252,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_cons
         const CUtensorMap* ma = p.tmaps + f.map_a;
         const CUtensorMap* mb = p.tmaps + f.map_b;
         const uint32_t bytes = A_BYTES + f.tn * TK * 2;
-        if (i + 1 < n_local) {
-          // the next tile's operands start their trip from HBM while this tile streams from L2
-          const TileInfo& g = info[i + 1];
-          const CUtensorMap* ga = p.tmaps + g.map_a;
-          const CUtensorMap* gb = p.tmaps + g.map_b;
-          for (int k0 = 0; k0 < g.kend; k0 += TK) {
-            tma_prefetch_2d(ga, k0, g.row_a);
-            for (int h = 0; h < g.tn; h += TM) tma_prefetch_2d(gb, k0, g.row_b + h);
-          }
-        }
         for (int k0 = 0; k0 < f.kend; k0 += TK) {
           if (!mbar_wait(&empty_bar[s], ph ^ 1u, budget, abort_flag)) { ok = false; break; }
           mbar_expect_tx(&full_bar[s], bytes);
