@@ -71,8 +71,11 @@ typedef enum nolsm_precision {
 
 typedef enum nolsm_bounds {
   NOLSM_BOUNDS_GERSHGORIN = 0,  /* Gershgorin discs of A0 = L^-1 T(H0) L^-T */
-  NOLSM_BOUNDS_LANCZOS = 1,     /* Lanczos extreme Ritz values widened by their residuals */
-  NOLSM_BOUNDS_LEARNED = 2      /* learned predictor (needs mlp weights), guarded by Gershgorin */
+  NOLSM_BOUNDS_LANCZOS = 1,     /* Lanczos extreme Ritz values of A0 widened by the last Lanczos
+                                   coefficient; the first iteration is unscaled (see nolsm_sign_batch) */
+  NOLSM_BOUNDS_LEARNED = 2      /* network predictions (nolsm_set_predictor) for the scale and the lower
+                                   bound; capped by Gershgorin, first iteration unscaled, a block whose
+                                   residual blows up restarts from the Gershgorin scale */
 } nolsm_bounds;
 
 typedef enum nolsm_chol_precision {
@@ -103,7 +106,7 @@ typedef struct nolsm_options {
   double lower_bound;      /* scaled iteration: lower bound on |eig(X_0)| when bounds give none (default 1e-3) */
   double alpha_margin;     /* relative safety margin on the spectral radius bound (default 0.02) */
   int64_t wait_budget;     /* bound on every device-side spin wait, in polls (default 1<<22) */
-  const char* mlp_path;    /* weights of the learned bound predictor, or NULL */
+  int32_t lanczos_steps;   /* Lanczos steps per block for NOLSM_BOUNDS_LANCZOS (default 24, at most 64) */
 } nolsm_options;
 
 /* Statistics of the last sign evaluation. */
@@ -214,6 +217,51 @@ nolsm_status nolsm_counters(nolsm_ctx* ctx, int64_t* launches, int64_t* gemm_lau
  *  - Returns NOLSM_ECUDA when the lookup or a launch fails. */
 nolsm_status nolsm_band_energy_noalloc(int64_t nnz, const double* d_val, const double* h_val, double spin_factor,
                                        double* e_out, void* cuda_stream);
+
+/* ---- learned spectral bounds -------------------------------------------------------------
+ * A network 32 -> 128 -> 128 -> 3 (GELU) predicts per block, from 32 features of A0 at a given mu,
+ * lambda_min(A0), lambda_max(A0) and log10 of the distance from mu to the nearest eigenvalue of
+ * A0.  The paper leaves the scaling of the sign iteration open (Section II, Eq. 6); these
+ * predictions set the scale and the lower bound of the scaled iteration.  Parameters are one
+ * float32 vector of 21,123 entries in the order W1 (128x32, row-major), b1, W2 (128x128), b2,
+ * W3 (3x128), b3; `norm` is 70 floats: feature means (32), feature scales (32), target means (3),
+ * target scales (3); inputs and targets are standardised with them inside the kernels. */
+
+/* Features of every block at mu into feat (device, n_blocks x 32 float32, row per block):
+ * n/512, |C_b|/n, mu, Gershgorin lo and hi, mean/std/min/max of diag(A0), ||offdiag||_F/sqrt(n),
+ * mean/max/std of the Gershgorin radii, Tr(A0^2)/n, Tr(A0)/n, sqrt(Tr(A0^2)/n - (Tr A0/n)^2),
+ * mean(diag) - mu, min|diag - mu|, fractions of diag below mu / within 0.05 / within 0.1 Ha of mu,
+ * mean and max |offdiag|, skewness and kurtosis of diag, fraction of discs containing mu, min and
+ * mean (|a_ii - mu| - R_i), relative position of mu in the Gershgorin interval, log10 of the
+ * Gershgorin scale, |C_b|/100, 1.  Enqueued only. */
+nolsm_status nolsm_block_features(nolsm_ctx* ctx, double mu, float* feat);
+
+/* Lanczos on every block (steps <= 64, full reorthogonalisation): op 0 on A0, op 1 on
+ * |A0 - mu| = X (A0 - mu) with X the iterate of the last nolsm_sign_batch (its mu).  out (device,
+ * n_blocks x 4 float32): smallest and largest Ritz value, last Lanczos coefficient, steps taken.
+ * Synchronises. */
+nolsm_status nolsm_block_lanczos(nolsm_ctx* ctx, int32_t steps, int32_t op, float* out);
+
+typedef struct nolsm_mlp nolsm_mlp;
+
+/* Create a network on the current device (params: host, or NULL for zeros; norm: host, 70). */
+nolsm_status nolsm_mlp_create(nolsm_mlp** mlp, const float* params, const float* norm, void* cuda_stream);
+/* Copy the FP32 parameters to host memory (21,123 floats).  Synchronises. */
+nolsm_status nolsm_mlp_get_params(const nolsm_mlp* mlp, float* params);
+/* Gradient of (1/n) sum_s 1/2 sum_k w_k (y_k - t_k)^2 over n samples (x: device n x 32, t: device
+ * n x 3, both raw; w: host 3 weights) with the FP32 parameters; kept for nolsm_mlp_adam and
+ * copied to grad (device, 21,123) when not NULL; loss to *loss (host) when not NULL (synchronises). */
+nolsm_status nolsm_mlp_gradient(nolsm_mlp* mlp, const float* x, const float* t, int32_t n, const float* w,
+                                float* grad, double* loss);
+/* One Adam step (bias-corrected moments) with the last gradient; refreshes the BF16 copy. */
+nolsm_status nolsm_mlp_adam(nolsm_mlp* mlp, float lr, float beta1, float beta2, float eps);
+/* Predictions for n samples (x: device n x 32 raw features; y: device n x 3) with BF16 weights and
+ * FP32 accumulation. */
+nolsm_status nolsm_mlp_predict(const nolsm_mlp* mlp, const float* x, int32_t n, float* y);
+void nolsm_mlp_destroy(nolsm_mlp* mlp);
+
+/* Use mlp (kept by the caller, alive while ctx uses it) for NOLSM_BOUNDS_LEARNED; NULL detaches. */
+nolsm_status nolsm_set_predictor(nolsm_ctx* ctx, const nolsm_mlp* mlp);
 
 /* Message of the last error of ctx (never NULL; "" when none).  ctx may be NULL. */
 const char* nolsm_last_error(const nolsm_ctx* ctx);

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnolsm.so")
-SOURCES = ["api.cu", "index.cu", "build.cu", "sign.cu", "sign_tc.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "index.cu", "build.cu", "sign.cu", "sign_tc.cu", "learn.cu", "noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "internal.h"), os.path.join(ROOT, "include", "nolsm.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -95,6 +95,10 @@ void release_pools(nolsm_ctx* ctx) {
   dfree(ctx->d_nb); ctx->d_nb = nullptr;
   dfree(ctx->d_tmaps); ctx->d_tmaps = nullptr;
   dfree(ctx->d_sb); ctx->d_sb = nullptr;
+  dfree(ctx->d_feat); ctx->d_feat = nullptr;
+  dfree(ctx->d_pred); ctx->d_pred = nullptr;
+  dfree(ctx->d_lz); ctx->d_lz = nullptr;
+  dfree(ctx->d_lz_basis); ctx->d_lz_basis = nullptr;
   dfree(ctx->d_t1); ctx->d_t1 = nullptr;
   ctx->caps.clear();
   ctx->built = ctx->have_sign = ctx->have_density = false;
@@ -137,6 +141,22 @@ nolsm_status check_device_flags(nolsm_ctx* ctx) {
   return NOLSM_OK;
 }
 
+// Lanczos on every block into out (device n_blocks x 4), or into the context's d_lz when out is NULL.
+nolsm_status run_lanczos(nolsm_ctx* ctx, double mu, int op, int steps, float* out) {
+  int max_pad = kTile;
+  for (const auto& b : ctx->h_blocks) max_pad = std::max(max_pad, b.n_pad);
+  const int64_t stride = (int64_t)(steps + 1) * max_pad;
+  CK(dalloc(ctx, &ctx->d_lz_basis, (size_t)stride * ctx->n_blocks));
+  if (!out) {
+    CK(dalloc(ctx, &ctx->d_lz, (size_t)4 * ctx->n_blocks));
+    out = ctx->d_lz;
+  }
+  CK(launch_lanczos(ctx, mu, op, steps, ctx->d_lz_basis, stride, out));
+  ctx->n_launches += 1;
+  CK(cudaStreamSynchronize(ctx->stream));
+  return NOLSM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -155,7 +175,7 @@ nolsm_status nolsm_default_options(nolsm_options* opt) {
   opt->lower_bound = 1e-3;
   opt->alpha_margin = 0.02;
   opt->wait_budget = 1LL << 22;
-  opt->mlp_path = nullptr;
+  opt->lanczos_steps = 24;
   return NOLSM_OK;
 }
 
@@ -168,7 +188,8 @@ nolsm_status nolsm_create(nolsm_ctx** out, const nolsm_options* opt, void* cuda_
   if (ctx->opt.precision < NOLSM_PREC_FP32 || ctx->opt.precision > NOLSM_PREC_MIXED_BF16 || ctx->opt.max_iter <= 0 ||
       ctx->opt.refine_iters < 0 || ctx->opt.refine_iters > 3 || !(ctx->opt.spin_factor > 0) ||
       ctx->opt.wait_budget <= 0 || ctx->opt.alpha_margin < 0 || ctx->opt.chol_precision < 0 ||
-      ctx->opt.chol_precision > NOLSM_CHOL_FP64_INV64) {
+      ctx->opt.chol_precision > NOLSM_CHOL_FP64_INV64 || ctx->opt.bounds < NOLSM_BOUNDS_GERSHGORIN ||
+      ctx->opt.bounds > NOLSM_BOUNDS_LEARNED || ctx->opt.lanczos_steps < 1 || ctx->opt.lanczos_steps > 64) {
     delete ctx;
     return NOLSM_EINVAL;
   }
@@ -387,6 +408,10 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   CK(launch_congruence(ctx, ctx->d_t1));
   CK(launch_slabs_impl(ctx, chol32 ? (const void*)(sb + ctx->sum_sq) : (const void*)sb, chol32, ctx->d_t1));
   CK(launch_bounds(ctx));
+  if (ctx->opt.bounds == NOLSM_BOUNDS_LANCZOS) {
+    nolsm_status st_l = run_lanczos(ctx, 0.0, 0, ctx->opt.lanczos_steps, nullptr);
+    if (st_l != NOLSM_OK) return st_l;
+  }
   nolsm_status st = check_device_flags(ctx);
   if (st != NOLSM_OK) return st;
   ctx->h_lo.resize((size_t)n_blocks);
@@ -441,7 +466,18 @@ nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out) 
   const bool mixed = is_mixed(ctx);
   const int hk = half_kind(ctx);
   CK(cudaEventRecord(ctx->ev0, ctx->stream));
-  CK(launch_ns_init(ctx, mu, hk));
+  const int mode = ctx->opt.bounds;
+  const float* pred = nullptr;
+  if (mode == NOLSM_BOUNDS_LEARNED) {
+    if (!ctx->predictor) return fail(ctx, NOLSM_EINVAL, "learned bounds need nolsm_set_predictor");
+    CK(dalloc(ctx, &ctx->d_feat, (size_t)32 * ctx->n_blocks));
+    CK(dalloc(ctx, &ctx->d_pred, (size_t)3 * ctx->n_blocks));
+    CK(launch_features(ctx, mu, ctx->d_feat));
+    CK(mlp_predict_on(ctx->predictor, ctx->stream, ctx->d_feat, ctx->n_blocks, ctx->d_pred));
+    ctx->n_launches += 2;
+    pred = ctx->d_pred;
+  }
+  CK(launch_ns_init(ctx, mu, hk, mode, mode == NOLSM_BOUNDS_LANCZOS ? ctx->d_lz : nullptr, pred));
   ctx->n_launches += 2;
   const int tile_n = mixed ? tc_tile_n() : kTile;
   const int check_every = 4;
@@ -449,11 +485,15 @@ nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out) 
   for (int it = 0; it <= ctx->opt.max_iter; ++it) {
     CK(launch_ns_tiles_n(ctx, tile_n));
     CK(gemm_timed(ctx, mixed, 1));
-    CK(launch_ns_check_impl(ctx, ctx->d_tol));
+    CK(launch_ns_check_impl(ctx, ctx->d_tol, mode != NOLSM_BOUNDS_GERSHGORIN));
     CK(launch_ns_tiles_n(ctx, tile_n));
     CK(gemm_timed(ctx, mixed, 2));
     CK(launch_ns_advance(ctx));
     ctx->n_launches += 4;
+    if (mode != NOLSM_BOUNDS_GERSHGORIN) {
+      CK(launch_ns_restart(ctx, mu, hk));
+      ctx->n_launches += 2;
+    }
     if (it % check_every == check_every - 1 || it == ctx->opt.max_iter) {
       CK(cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(DevFlags), cudaMemcpyDeviceToHost, ctx->stream));
       CK(cudaStreamSynchronize(ctx->stream));
@@ -606,6 +646,26 @@ nolsm_status nolsm_block_bounds(const nolsm_ctx* ctx, double* lo, double* hi) {
   if (!ctx || !ctx->built) return NOLSM_EINVAL;
   if (lo) std::memcpy(lo, ctx->h_lo.data(), sizeof(double) * ctx->n_blocks);
   if (hi) std::memcpy(hi, ctx->h_hi.data(), sizeof(double) * ctx->n_blocks);
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_block_features(nolsm_ctx* ctx, double mu, float* feat) {
+  if (!ctx || !ctx->built || !feat || !std::isfinite(mu)) return NOLSM_EINVAL;
+  if (launch_features(ctx, mu, feat) != cudaSuccess) return NOLSM_ECUDA;
+  ctx->n_launches += 1;
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_block_lanczos(nolsm_ctx* ctx, int32_t steps, int32_t op, float* out) {
+  if (!ctx || !ctx->built || !out || steps < 1 || steps > 64 || op < 0 || op > 1) return NOLSM_EINVAL;
+  if (op == 1 && !ctx->have_sign) return NOLSM_ENOTBUILT;
+  if (ctx->sticky != NOLSM_OK) return ctx->sticky;
+  return run_lanczos(ctx, ctx->last_mu, op, steps, out);
+}
+
+nolsm_status nolsm_set_predictor(nolsm_ctx* ctx, const nolsm_mlp* mlp) {
+  if (!ctx) return NOLSM_EINVAL;
+  ctx->predictor = mlp;
   return NOLSM_OK;
 }
 

@@ -148,6 +148,13 @@ struct nolsm_ctx {
   std::vector<cudaEvent_t> gemm_ev;     // pairs, reused
   int gemm_ev_used = 0;
 
+  // spectral bounds beyond Gershgorin
+  const struct nolsm_mlp* predictor = nullptr;
+  float* d_feat = nullptr;      // n_blocks x 32 features
+  float* d_pred = nullptr;      // n_blocks x 3 predictions
+  float* d_lz = nullptr;        // n_blocks x 4 Lanczos results on A0
+  float* d_lz_basis = nullptr;  // Lanczos basis scratch
+
   double last_mu = 0.0;
   nolsm_sign_stats last_stats{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -167,10 +174,12 @@ cudaError_t launch_slabs_impl(nolsm_ctx* ctx, const void* lfac, int fp32, const 
 cudaError_t launch_bounds(nolsm_ctx* ctx);
 
 // sign.cu (SIMT path, control, slab traces)
-cudaError_t launch_ns_init(nolsm_ctx* ctx, double mu, int half);
+cudaError_t launch_ns_init(nolsm_ctx* ctx, double mu, int half, int mode, const float* lz, const float* pred);
+cudaError_t launch_ns_restart(nolsm_ctx* ctx, double mu, int half);
 cudaError_t launch_ns_tiles(nolsm_ctx* ctx);
 cudaError_t launch_ns_tiles_n(nolsm_ctx* ctx, int tile_n);
 cudaError_t launch_ns_check_impl(nolsm_ctx* ctx, const float* tol_b);
+cudaError_t launch_ns_check_impl(nolsm_ctx* ctx, const float* tol_b, int detect_divergence);
 cudaError_t launch_ns_advance(nolsm_ctx* ctx);
 cudaError_t launch_ns_reinit(nolsm_ctx* ctx, double mu, int half);
 cudaError_t launch_gemm_f32(nolsm_ctx* ctx, int phase);
@@ -182,6 +191,11 @@ cudaError_t launch_band_energy(nolsm_ctx* ctx);
 cudaError_t tc_prepare(nolsm_ctx* ctx);
 cudaError_t launch_gemm_tc(nolsm_ctx* ctx, int phase);
 int tc_tile_n();
+
+// learn.cu
+cudaError_t launch_features(nolsm_ctx* ctx, double mu, float* feat);
+cudaError_t launch_lanczos(nolsm_ctx* ctx, double mu, int op, int k, float* basis, int64_t stride, float* out);
+cudaError_t mlp_predict_on(const struct nolsm_mlp* m, cudaStream_t s, const float* x, int n, float* y);
 
 // index.cu
 cudaError_t launch_transpose(nolsm_ctx* ctx);

@@ -154,18 +154,37 @@ sgemm_nt_kernel(const Tile* __restrict__ tiles, const int32_t* __restrict__ n_ti
 
 // State at the start of a sign evaluation: alpha from the spectral bounds (Gershgorin, with a
 // relative margin) so that ||X_0||_2 < 1; the scaled iteration starts from lower bound l0.
+// mode 0: Gershgorin scale, lower bound l0.  mode 1: Lanczos Ritz values widened by the last
+// Lanczos coefficient.  mode 2: network predictions (lambda_min, lambda_max, log10 distance of mu to
+// the nearest eigenvalue): scale 1.25 x the predicted radius, lower bound half the predicted
+// distance.  A scale below the rigorous Gershgorin one starts with one unscaled step, which maps
+// any eigenvalue in (0, sqrt 3) into (0, 1]; the Gershgorin scale stays the cap.
 __global__ void ns_state_kernel(int n_blocks, const double* __restrict__ lo, const double* __restrict__ hi,
-                                double mu, float margin, float l0, int scaled, NsState* __restrict__ st,
-                                float* __restrict__ resacc, DevFlags* flags) {
+                                double mu, float margin, float l0, int scaled, int mode,
+                                const float* __restrict__ lz, const float* __restrict__ pred,
+                                NsState* __restrict__ st, float* __restrict__ resacc, DevFlags* flags) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b == 0) { flags->sum_n = 0.0; flags->sum_e = 0.0; }
   if (b >= n_blocks) return;
   const double rad = fmax(fabs(hi[b] - mu), fabs(mu - lo[b]));
+  float alpha = (float)(rad * (1.0 + margin));
+  if (!(alpha > 0.f)) alpha = 1.f;
+  float l = l0;
+  bool plain_first = false;
+  if (mode == 1 && lz) {
+    const float w = fabsf(lz[4 * b + 2]);
+    const float r = fmaxf(lz[4 * b + 1] + w - (float)mu, (float)mu - lz[4 * b + 0] + w) * (1.f + margin);
+    if (r > 0.f && r < alpha) { alpha = r; plain_first = true; }
+  } else if (mode == 2 && pred) {
+    const float r = 1.25f * fmaxf(pred[3 * b + 1] - (float)mu, (float)mu - pred[3 * b + 0]);
+    if (r > 0.f && r < alpha) { alpha = r; plain_first = true; }
+    const float dist = exp10f(fminf(fmaxf(pred[3 * b + 2], -8.f), 1.f));
+    l = 0.5f * dist / alpha;
+  }
   NsState s;
-  s.alpha = (float)(rad * (1.0 + margin));
-  if (!(s.alpha > 0.f)) s.alpha = 1.f;
-  s.l = scaled ? fminf(fmaxf(l0, 1e-7f), 1.f) : 1.f;
-  s.a = cc_scale(s.l);
+  s.alpha = alpha;
+  s.l = scaled ? fminf(fmaxf(l, 1e-7f), 0.9f) : 1.f;
+  s.a = plain_first ? 1.f : cc_scale(s.l);
   s.res = FLT_MAX;
   s.res_prev = FLT_MAX;
   s.iters = 0;
@@ -173,6 +192,46 @@ __global__ void ns_state_kernel(int n_blocks, const double* __restrict__ lo, con
   s.cur = 0;
   s.grow = 0;
   s.restarts = 0;
+  st[b] = s;
+  resacc[b] = 0.f;
+}
+
+// Restart of diverged blocks: X_0 again, with the Gershgorin scale and lower bound l0.
+template <typename T>
+__global__ void ns_restart_fill_kernel(const BlockDesc* __restrict__ blocks, const float* __restrict__ a0,
+                                       const NsState* __restrict__ st, const double* __restrict__ lo,
+                                       const double* __restrict__ hi, double mu, float margin, T* __restrict__ x0) {
+  const int b = blockIdx.y;
+  if (st[b].status != kRestart) return;
+  const BlockDesc bd = blocks[b];
+  const int n = bd.n, ld = bd.n_pad;
+  const float alpha = (float)(fmax(fabs(hi[b] - mu), fabs(mu - lo[b])) * (1.0 + margin));
+  const float inv = 1.f / alpha, muf = (float)mu;
+  const int64_t total = (int64_t)ld * ld;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / ld), c = (int)(e % ld);
+    float v;
+    if (r < n && c < n) v = (a0[bd.off_mat + e] - (r == c ? muf : 0.f)) * inv;
+    else v = (r == c) ? 1.f : 0.f;
+    x0[bd.off_mat + e] = from_float<T>(v);
+  }
+}
+
+__global__ void ns_restart_state_kernel(int n_blocks, const double* __restrict__ lo, const double* __restrict__ hi,
+                                        double mu, float margin, float l0, int scaled, NsState* __restrict__ st,
+                                        float* __restrict__ resacc) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_blocks) return;
+  NsState s = st[b];
+  if (s.status != kRestart) return;
+  s.alpha = (float)(fmax(fabs(hi[b] - mu), fabs(mu - lo[b])) * (1.0 + margin));
+  s.l = scaled ? fminf(fmaxf(l0, 1e-7f), 1.f) : 1.f;
+  s.a = cc_scale(s.l);
+  s.res = FLT_MAX;
+  s.res_prev = FLT_MAX;
+  s.cur = 0;
+  s.grow = 0;
+  s.status = kActive;
   st[b] = s;
   resacc[b] = 0.f;
 }
@@ -251,14 +310,24 @@ __global__ void __launch_bounds__(1024) ns_tiles_kernel(int n_blocks, const Bloc
 }
 
 // After the first product of an iteration: the residual decides convergence.
-__global__ void ns_check_kernel(int n_blocks, NsState* __restrict__ st, float* __restrict__ resacc,
-                                const float* __restrict__ tol_b, int max_iter, DevFlags* flags) {
+__global__ void ns_check_kernel(int n_blocks, const BlockDesc* __restrict__ blocks, NsState* __restrict__ st,
+                                float* __restrict__ resacc, const float* __restrict__ tol_b, int max_iter,
+                                int detect_divergence, DevFlags* flags) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= n_blocks) return;
   NsState s = st[b];
   if (s.status != kActive) return;
   const float res = sqrtf(resacc[b]);
   resacc[b] = 0.f;
+  // after the first step every eigenvalue of a well-scaled iterate lies in [-1, 1], so
+  // ||X^2 - I||_F <= sqrt(n_pad); beyond that the scale was too small: restart (once per block)
+  if (detect_divergence && s.iters >= 1 && s.restarts == 0 &&
+      (!isfinite(res) || res > 1.5f * sqrtf((float)blocks[b].n_pad))) {
+    s.status = kRestart;
+    s.restarts += 1;
+    st[b] = s;
+    return;
+  }
   if (!isfinite(res)) { s.status = kFailed; s.res = res; st[b] = s; set_error(flags, NOLSM_ENONFINITE); return; }
   s.res_prev = s.res;
   s.res = res;
@@ -553,11 +622,11 @@ cudaError_t launch_sgemm_nt(nolsm_ctx* ctx, const float* a, const float* b, floa
   return cudaGetLastError();
 }
 
-cudaError_t launch_ns_init(nolsm_ctx* ctx, double mu, int half) {
+cudaError_t launch_ns_init(nolsm_ctx* ctx, double mu, int half, int mode, const float* lz, const float* pred) {
   const float l0 = (float)ctx->opt.lower_bound;
   ns_state_kernel<<<(ctx->n_blocks + 255) / 256, 256, 0, ctx->stream>>>(
-      ctx->n_blocks, ctx->d_lo, ctx->d_hi, mu, (float)ctx->opt.alpha_margin, l0, ctx->opt.scaled, ctx->d_state,
-      ctx->d_resacc, ctx->d_flags);
+      ctx->n_blocks, ctx->d_lo, ctx->d_hi, mu, (float)ctx->opt.alpha_margin, l0, ctx->opt.scaled, mode, lz, pred,
+      ctx->d_state, ctx->d_resacc, ctx->d_flags);
   const dim3 g(64, ctx->n_blocks);
   if (half == 0)
     ns_fill_kernel<float><<<g, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_a0, ctx->d_state, mu, (float*)ctx->d_x[0]);
@@ -577,9 +646,31 @@ cudaError_t launch_ns_tiles_n(nolsm_ctx* ctx, int tile_n) {
 
 cudaError_t launch_ns_tiles(nolsm_ctx* ctx) { return launch_ns_tiles_n(ctx, BN); }
 
-cudaError_t launch_ns_check_impl(nolsm_ctx* ctx, const float* tol_b) {
-  ns_check_kernel<<<(ctx->n_blocks + 255) / 256, 256, 0, ctx->stream>>>(ctx->n_blocks, ctx->d_state, ctx->d_resacc,
-                                                                        tol_b, ctx->opt.max_iter, ctx->d_flags);
+cudaError_t launch_ns_check_impl(nolsm_ctx* ctx, const float* tol_b, int detect_divergence) {
+  ns_check_kernel<<<(ctx->n_blocks + 255) / 256, 256, 0, ctx->stream>>>(ctx->n_blocks, ctx->d_blocks, ctx->d_state,
+                                                                        ctx->d_resacc, tol_b, ctx->opt.max_iter,
+                                                                        detect_divergence, ctx->d_flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ns_check_impl(nolsm_ctx* ctx, const float* tol_b) { return launch_ns_check_impl(ctx, tol_b, 0); }
+
+cudaError_t launch_ns_restart(nolsm_ctx* ctx, double mu, int half) {
+  const dim3 g(64, ctx->n_blocks);
+  const float margin = (float)ctx->opt.alpha_margin;
+  if (half == 0)
+    ns_restart_fill_kernel<float><<<g, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_a0, ctx->d_state, ctx->d_lo,
+                                                              ctx->d_hi, mu, margin, (float*)ctx->d_x[0]);
+  else if (half == 1)
+    ns_restart_fill_kernel<__half><<<g, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_a0, ctx->d_state, ctx->d_lo,
+                                                               ctx->d_hi, mu, margin, (__half*)ctx->d_x[0]);
+  else
+    ns_restart_fill_kernel<__nv_bfloat16><<<g, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_a0, ctx->d_state,
+                                                                      ctx->d_lo, ctx->d_hi, mu, margin,
+                                                                      (__nv_bfloat16*)ctx->d_x[0]);
+  ns_restart_state_kernel<<<(ctx->n_blocks + 255) / 256, 256, 0, ctx->stream>>>(
+      ctx->n_blocks, ctx->d_lo, ctx->d_hi, mu, margin, (float)ctx->opt.lower_bound, ctx->opt.scaled, ctx->d_state,
+      ctx->d_resacc);
   return cudaGetLastError();
 }
 

@@ -25,7 +25,12 @@ CHOL_FP64, CHOL_FP32, CHOL_FP64_INV64 = 0, 1, 2
 FUNCTIONS = ["nolsm_default_options", "nolsm_create", "nolsm_build_submatrices", "nolsm_sign_batch", "nolsm_set_mu",
              "nolsm_density", "nolsm_band_energy", "nolsm_block_info", "nolsm_block_index_set", "nolsm_block_bounds",
              "nolsm_block_state", "nolsm_block_matrix", "nolsm_counters", "nolsm_band_energy_noalloc",
+             "nolsm_block_features", "nolsm_block_lanczos", "nolsm_mlp_create", "nolsm_mlp_get_params",
+             "nolsm_mlp_gradient", "nolsm_mlp_adam", "nolsm_mlp_predict", "nolsm_mlp_destroy", "nolsm_set_predictor",
              "nolsm_last_error", "nolsm_destroy"]
+
+N_PARAMS = 32 * 128 + 128 + 128 * 128 + 128 + 128 * 3 + 3
+N_FEATURES, N_OUTPUTS = 32, 3
 
 
 class NolsmCsr(C.Structure):
@@ -37,7 +42,7 @@ class NolsmOptions(C.Structure):
     _fields_ = [("precision", C.c_int32), ("bounds", C.c_int32), ("chol_precision", C.c_int32),
                 ("scaled", C.c_int32), ("sign_tol", C.c_double), ("max_iter", C.c_int32),
                 ("refine_iters", C.c_int32), ("spin_factor", C.c_double), ("lower_bound", C.c_double),
-                ("alpha_margin", C.c_double), ("wait_budget", C.c_int64), ("mlp_path", C.c_char_p)]
+                ("alpha_margin", C.c_double), ("wait_budget", C.c_int64), ("lanczos_steps", C.c_int32)]
 
 
 class NolsmSignStats(C.Structure):
@@ -78,6 +83,15 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "nolsm_block_matrix": (i32, [P, i32, i32, P]),
         "nolsm_counters": (i32, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), pf64, pf64, i32]),
         "nolsm_band_energy_noalloc": (i32, [i64, P, P, f64, P, P]),
+        "nolsm_block_features": (i32, [P, f64, P]),
+        "nolsm_block_lanczos": (i32, [P, i32, i32, P]),
+        "nolsm_mlp_create": (i32, [C.POINTER(P), P, P, P]),
+        "nolsm_mlp_get_params": (i32, [P, P]),
+        "nolsm_mlp_gradient": (i32, [P, P, P, i32, P, P, pf64]),
+        "nolsm_mlp_adam": (i32, [P, C.c_float, C.c_float, C.c_float, C.c_float]),
+        "nolsm_mlp_predict": (i32, [P, P, i32, P]),
+        "nolsm_mlp_destroy": (None, [P]),
+        "nolsm_set_predictor": (i32, [P, P]),
         "nolsm_last_error": (C.c_char_p, [P]),
         "nolsm_destroy": (None, [P]),
     }
@@ -198,6 +212,51 @@ def nolsm_band_energy_noalloc(nnz, d_val, h_val, spin_factor, e_out, stream=None
                                                 _ptr(e_out), stream))
 
 
+def nolsm_block_features(ctx, mu, feat):
+    _check(ctx, _lib.nolsm_block_features(ctx, float(mu), _ptr(feat)))
+
+
+def nolsm_block_lanczos(ctx, steps, op, out):
+    _check(ctx, _lib.nolsm_block_lanczos(ctx, int(steps), int(op), _ptr(out)))
+
+
+def nolsm_mlp_create(params, norm, stream=None):
+    m = C.c_void_p()
+    p = None if params is None else np.ascontiguousarray(params, np.float32)
+    nrm = np.ascontiguousarray(norm, np.float32)
+    _check(None, _lib.nolsm_mlp_create(C.byref(m), None if p is None else p.ctypes.data, nrm.ctypes.data, stream))
+    return m
+
+
+def nolsm_mlp_get_params(mlp) -> np.ndarray:
+    out = np.empty(N_PARAMS, np.float32)
+    _check(None, _lib.nolsm_mlp_get_params(mlp, out.ctypes.data))
+    return out
+
+
+def nolsm_mlp_gradient(mlp, x, t, n, w, grad=None):
+    ww = np.ascontiguousarray(w, np.float32)
+    loss = C.c_double()
+    _check(None, _lib.nolsm_mlp_gradient(mlp, _ptr(x), _ptr(t), int(n), ww.ctypes.data, _ptr(grad), C.byref(loss)))
+    return loss.value
+
+
+def nolsm_mlp_adam(mlp, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    _check(None, _lib.nolsm_mlp_adam(mlp, lr, beta1, beta2, eps))
+
+
+def nolsm_mlp_predict(mlp, x, n, y):
+    _check(None, _lib.nolsm_mlp_predict(mlp, _ptr(x), int(n), _ptr(y)))
+
+
+def nolsm_mlp_destroy(mlp):
+    _lib.nolsm_mlp_destroy(mlp)
+
+
+def nolsm_set_predictor(ctx, mlp):
+    _check(ctx, _lib.nolsm_set_predictor(ctx, mlp))
+
+
 def nolsm_last_error(ctx) -> str:
     return _lib.nolsm_last_error(ctx).decode()
 
@@ -303,8 +362,80 @@ class Nolsm:
     def block_state(self):
         return nolsm_block_state(self.ctx, self.n_blocks)
 
+    def features(self, mu):
+        import torch
+        f = torch.empty((self.n_blocks, N_FEATURES), dtype=torch.float32, device="cuda")
+        nolsm_block_features(self.ctx, mu, f)
+        return f
+
+    def lanczos(self, steps, op=0):
+        import torch
+        out = torch.empty((self.n_blocks, 4), dtype=torch.float32, device="cuda")
+        nolsm_block_lanczos(self.ctx, steps, op, out)
+        return out
+
+    def set_predictor(self, predictor):
+        self._predictor = predictor
+        nolsm_set_predictor(self.ctx, predictor.mlp if predictor is not None else None)
+
     def counters(self, reset=False):
         return nolsm_counters(self.ctx, reset)
 
     def block_matrix(self, b, which=0):
         return nolsm_block_matrix(self.ctx, b, which)
+
+
+class BoundPredictor:
+    """The spectral-bound network on the GPU; weights live in a raw float32 file plus JSON metadata."""
+
+    def __init__(self, params=None, norm=None, stream=None):
+        if norm is None:
+            norm = np.concatenate([np.zeros(N_FEATURES), np.ones(N_FEATURES), np.zeros(N_OUTPUTS), np.ones(N_OUTPUTS)])
+        self.norm = np.asarray(norm, np.float32)
+        self.mlp = nolsm_mlp_create(params, self.norm, stream)
+
+    def close(self):
+        if self.mlp:
+            nolsm_mlp_destroy(self.mlp)
+            self.mlp = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        return nolsm_mlp_get_params(self.mlp)
+
+    def gradient(self, x, t, w=(1.0, 1.0, 1.0), grad=None):
+        return nolsm_mlp_gradient(self.mlp, x, t, x.shape[0], w, grad)
+
+    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        nolsm_mlp_adam(self.mlp, lr, beta1, beta2, eps)
+
+    def predict(self, x):
+        import torch
+        y = torch.empty((x.shape[0], N_OUTPUTS), dtype=torch.float32, device=x.device)
+        nolsm_mlp_predict(self.mlp, x, x.shape[0], y)
+        return y
+
+    def save(self, path, meta=None):
+        import json
+        base = path[:-5] if path.endswith(".json") else path
+        self.params().astype("<f4").tofile(base + ".bin")
+        info = {"layers": [32, 128, 128, 3], "activation": "gelu", "n_params": N_PARAMS,
+                "params_file": os.path.basename(base + ".bin"), "dtype": "float32 little-endian",
+                "norm": [float(v) for v in self.norm], "outputs": ["lambda_min", "lambda_max", "log10_dist_mu"]}
+        if meta:
+            info.update(meta)
+        with open(base + ".json", "w") as f:
+            json.dump(info, f, indent=1)
+
+    @classmethod
+    def load(cls, path, stream=None):
+        import json
+        base = path[:-5] if path.endswith(".json") else path
+        info = json.load(open(base + ".json"))
+        params = np.fromfile(os.path.join(os.path.dirname(base + ".json"), info["params_file"]), dtype="<f4")
+        return cls(params, np.asarray(info["norm"], np.float32), stream)

@@ -1,0 +1,145 @@
+"""Spectral bounds beyond Gershgorin and the bound-predictor network, against the FP64 references.
+
+* the network's gradient, Adam step and BF16 inference against oracle/mlp.py;
+* Lanczos extreme Ritz values of A0 against the oracle's generalized eigenvalues, and the distance
+  from mu to the spectrum (Lanczos on |A0 - mu|) against the same eigenvalues;
+* features against their definitions on the A0 the library returns;
+* the sign with Lanczos or predicted bounds keeps the accuracy, and a bad prediction costs
+  iterations (or a restart) but not accuracy.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import mlp as om  # noqa: E402
+from oracle.nolsm import NolsmOracle  # noqa: E402
+from synth import make_config  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def nl():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2205_12182_gb300 import nolsm
+    return nolsm
+
+
+@pytest.fixture(scope="module")
+def sys1():
+    return make_config(1)
+
+
+@pytest.fixture(scope="module")
+def orc1(sys1):
+    return NolsmOracle.from_system(sys1).prepare()
+
+
+@pytest.fixture(scope="module")
+def mu1(orc1):
+    return orc1.bisect(tol_rel=1e-3)[0]
+
+
+def bf16_round(a):
+    return torch.from_numpy(np.asarray(a, np.float32)).bfloat16().float().numpy().astype(np.float64)
+
+
+def test_gradient_matches_reference(nl):
+    rng = np.random.default_rng(0)
+    params = om.flatten(om.init_params(3)).astype(np.float32)
+    x = rng.normal(size=(67, 32)).astype(np.float32)       # ragged: not a multiple of the CTA chunk
+    t = rng.normal(size=(67, 3)).astype(np.float32)
+    w = np.array([1.0, 0.5, 2.0])
+    bp = nl.BoundPredictor(params)
+    g = torch.zeros(nl.N_PARAMS, device="cuda")
+    loss = bp.gradient(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda(), w, g)
+    p64 = om.unflatten(params.astype(np.float64))
+    ref = om.flatten(om.backward(p64, x.astype(np.float64), t.astype(np.float64), w))
+    np.testing.assert_allclose(g.cpu().numpy(), ref, rtol=1e-4, atol=2e-6)
+    assert loss == pytest.approx(om.loss(p64, x.astype(np.float64), t.astype(np.float64), w), rel=1e-5)
+    # one Adam step from the same gradient: the reference's update rule
+    bp.adam(lr=1e-2)
+    p_ref = om.unflatten(params.astype(np.float64))
+    om.adam_step(p_ref, om.unflatten(g.cpu().numpy().astype(np.float64)), {}, lr=1e-2)
+    np.testing.assert_allclose(bp.params(), om.flatten(p_ref), rtol=0, atol=1e-6)
+
+
+def test_inference_matches_reference_with_bf16_weights(nl):
+    rng = np.random.default_rng(1)
+    params = om.flatten(om.init_params(4)).astype(np.float32)
+    norm = np.concatenate([rng.normal(size=32), rng.uniform(0.5, 2, 32), rng.normal(size=3),
+                           rng.uniform(0.5, 2, 3)]).astype(np.float32)
+    x = rng.normal(size=(100, 32)).astype(np.float32)
+    bp = nl.BoundPredictor(params, norm)
+    y = bp.predict(torch.from_numpy(x).cuda()).cpu().numpy()
+    p = om.unflatten(bf16_round(params))
+    xn = (x.astype(np.float64) - norm[:32]) / norm[32:64]
+    yref, _ = om.forward(p, xn)
+    yref = yref * norm[67:70] + norm[64:67]
+    np.testing.assert_allclose(y, yref, rtol=1e-4, atol=1e-4)
+
+
+def test_lanczos_extremes_and_distance(nl, sys1, orc1, mu1):
+    lib = nl.Nolsm(precision=nl.PREC_FP32).build(sys1)
+    lz = lib.lanczos(64, op=0).cpu().numpy()
+    for b in range(sys1.n_blocks):
+        assert lz[b, 0] == pytest.approx(orc1.eps[b][0], abs=1e-5)
+        assert lz[b, 1] == pytest.approx(orc1.eps[b][-1], abs=1e-5)
+    lib.sign_batch(mu1)
+    ld = lib.lanczos(64, op=1).cpu().numpy()
+    dist = np.array([np.min(np.abs(e - mu1)) for e in orc1.eps])
+    # a Ritz value never lies below the smallest eigenvalue of the positive matrix |A0 - mu|
+    assert np.all(ld[:, 0] >= dist * (1 - 1e-4) - 1e-6)
+    rel = np.abs(ld[:, 0] - dist) / dist
+    assert np.median(rel) < 1e-2 and np.quantile(rel, 0.9) < 0.1
+
+
+def test_features_follow_their_definitions(nl, sys1):
+    lib = nl.Nolsm(precision=nl.PREC_FP32).build(sys1)
+    mu = -0.45
+    f = lib.features(mu).cpu().numpy()
+    lo, hi = lib.bounds()
+    for b in [0, 13, 63]:
+        a = lib.block_matrix(b, 0).astype(np.float64)
+        n = a.shape[0]
+        d = np.diag(a)
+        off = a - np.diag(d)
+        assert f[b, 0] == pytest.approx(n / 512)
+        assert f[b, 2] == pytest.approx(mu)
+        assert f[b, 3] == pytest.approx(lo[b], abs=1e-5) and f[b, 4] == pytest.approx(hi[b], abs=1e-5)
+        assert f[b, 5] == pytest.approx(d.mean(), abs=1e-5)
+        assert f[b, 9] == pytest.approx(np.sqrt((off ** 2).sum() / n), rel=1e-4)
+        assert f[b, 13] == pytest.approx((a * a).sum() / n, rel=1e-4)
+        assert f[b, 18] == pytest.approx(np.mean(d < mu), abs=1e-6)
+        assert f[b, 31] == 1.0
+
+
+def test_lanczos_bounds_keep_accuracy_and_save_iterations(nl, sys1, orc1, mu1):
+    ref = orc1.density(mu1)
+    g = nl.Nolsm(precision=nl.PREC_MIXED_FP16).build(sys1)
+    sg = g.sign_batch(mu1)
+    lz = nl.Nolsm(precision=nl.PREC_MIXED_FP16, bounds=nl.BOUNDS_LANCZOS).build(sys1)
+    sl = lz.sign_batch(mu1)
+    assert np.abs(lz.density().cpu().numpy() - ref).max() <= 1e-3
+    assert sl["iters_avg"] <= sg["iters_avg"]
+
+
+def constant_predictor(nl, lam_min, lam_max, log_dist):
+    norm = np.concatenate([np.zeros(32), np.ones(32), [lam_min, lam_max, log_dist], np.ones(3)]).astype(np.float32)
+    return nl.BoundPredictor(np.zeros(nl.N_PARAMS, np.float32), norm)
+
+
+@pytest.mark.parametrize("case", ["radius_far_too_small", "lower_bound_far_too_large"])
+def test_bad_predictions_cost_iterations_not_accuracy(nl, sys1, orc1, mu1, case):
+    if case == "radius_far_too_small":
+        pred = constant_predictor(nl, mu1 - 0.05, mu1 + 0.05, -2.0)   # true radius ~0.6
+    else:
+        pred = constant_predictor(nl, -1.2, -0.3, 0.5)                  # distance 3 Ha: l = 0.9 cap
+    lib = nl.Nolsm(precision=nl.PREC_MIXED_FP16, bounds=nl.BOUNDS_LEARNED).build(sys1)
+    lib.set_predictor(pred)
+    st = lib.sign_batch(mu1)
+    assert np.abs(lib.density().cpu().numpy() - orc1.density(mu1)).max() <= 1e-3
+    assert st["n_electrons"] == pytest.approx(2 * orc1.electron_count(mu1), rel=1e-4)
+    if case == "radius_far_too_small":
+        assert st["n_restarted"] > 0
