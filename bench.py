@@ -33,6 +33,7 @@ WORKLOAD = {"workload": "water-4096", "molecules": 4096, "atoms": 12288, "basis"
             "blocks": 4096, "index_rule": "pattern + 8 A neighbourhood", "seed": 11}
 METRIC = "atoms/s & sign-GEMM TFLOP/s (% FP16 peak) at max|dD|<=1e-3 vs FP32 plain"
 TOL_N = 1e-3
+WEIGHTS = os.path.join(ROOT, "paper_2205_12182_gb300", "weights", "bounds_mlp.json")
 
 
 def peaks():
@@ -143,7 +144,9 @@ def run_ours(args):
             return lib.set_mu(s.n_electrons, tol_n=TOL_N)
         return set_mu_distributed(lib, n_e_global, tol_n=TOL_N, group=None)
 
-    lib = nolsm.Nolsm(precision=nolsm.PREC_MIXED_FP16)
+    predictor = nolsm.BoundPredictor.load(WEIGHTS)
+    lib = nolsm.Nolsm(precision=nolsm.PREC_MIXED_FP16, bounds=nolsm.BOUNDS_LEARNED)
+    lib.set_predictor(predictor)
     d_dev = torch.empty(system.nnz, dtype=torch.float64, device=dev)
 
     def barrier():
@@ -216,7 +219,8 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f16",
         "data": "synthetic (seeded water boxes; no dataset)",
-        "config": dict(WORKLOAD, mu_tol_rel=TOL_N, precision="FP16 operands / FP32 accumulate, FP64 Cholesky",
+        "config": dict(WORKLOAD, mu_tol_rel=TOL_N, bounds="learned (predictor weights committed, trained on other seeds)",
+                       precision="FP16 operands / FP32 accumulate, FP64 Cholesky factor",
                        l2="working set > 10 GB >> 129 MB L2 (no flush needed)",
                        parallelism=f"dp{world} (one box per rank, shared mu)"),
         "sign_gemm": {
@@ -245,6 +249,8 @@ def run_ours(args):
         "parity": parity,
         "result": {"mu": mu, "n_electrons": n, "band_energy": e},
     }
+    if not args.no_variants:
+        line["variants"] = variants(nolsm, system, mu_fn, d_dev, predictor, barrier, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(system, seconds=args.cpu_seconds)
     lib.close()
@@ -252,6 +258,33 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def variants(nolsm, system, mu_fn, d_dev, predictor, barrier, world, steps=2):
+    """atoms/s of the same full step with other precision / bound choices (1 warm-up, `steps` timed)."""
+    out = {}
+    cases = {
+        "fp32_plain": dict(precision=nolsm.PREC_FP32, scaled=0),
+        "mixed_fp16_gershgorin": dict(precision=nolsm.PREC_MIXED_FP16),
+        "mixed_fp16_learned_fp32_cholesky": dict(precision=nolsm.PREC_MIXED_FP16, bounds=nolsm.BOUNDS_LEARNED,
+                                                 chol_precision=nolsm.CHOL_FP32),
+    }
+    for name, kw in cases.items():
+        lib = nolsm.Nolsm(**kw)
+        if kw.get("bounds") == nolsm.BOUNDS_LEARNED:
+            lib.set_predictor(predictor)
+        solve(lib, system, mu_fn, d_dev, "device")
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            mu, n, st, e = solve(lib, system, mu_fn, d_dev, "device")
+        barrier()
+        dt = (time.perf_counter() - t0) / steps
+        s = lib.sign_batch(mu)
+        out[name] = {"value": WORKLOAD["atoms"] * world / dt, "unit": "atoms/s", "ms_per_step": dt * 1e3,
+                     "mu_steps": st, "ns_iters_avg": s["iters_avg"]}
+        lib.close()
+    return out
 
 
 def load_traffic():
@@ -343,6 +376,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--side", type=int, default=16,
                     help="molecules per box edge (16: the 4,096-molecule workload; smaller boxes for profiling)")
     args = ap.parse_args()

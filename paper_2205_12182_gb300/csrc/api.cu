@@ -407,7 +407,13 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   CK(launch_cholesky_inverse(ctx, sb, chol_mode));
   CK(launch_congruence(ctx, ctx->d_t1));
   CK(launch_slabs_impl(ctx, chol32 ? (const void*)(sb + ctx->sum_sq) : (const void*)sb, chol32, ctx->d_t1));
+  CK(dalloc(ctx, &ctx->d_rowd, (size_t)ctx->n_blocks * kMaxDim));
+  CK(dalloc(ctx, &ctx->d_rowr, (size_t)ctx->n_blocks * kMaxDim));
   CK(launch_bounds(ctx));
+  // mu-independent features once per build (the mu-dependent ones are refreshed in O(n))
+  CK(dalloc(ctx, &ctx->d_feat_static, (size_t)32 * ctx->n_blocks));
+  CK(launch_features(ctx, 0.0, ctx->d_feat_static));
+  ctx->n_launches += 1;
   if (ctx->opt.bounds == NOLSM_BOUNDS_LANCZOS) {
     nolsm_status st_l = run_lanczos(ctx, 0.0, 0, ctx->opt.lanczos_steps, nullptr);
     if (st_l != NOLSM_OK) return st_l;
@@ -472,7 +478,7 @@ nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out) 
     if (!ctx->predictor) return fail(ctx, NOLSM_EINVAL, "learned bounds need nolsm_set_predictor");
     CK(dalloc(ctx, &ctx->d_feat, (size_t)32 * ctx->n_blocks));
     CK(dalloc(ctx, &ctx->d_pred, (size_t)3 * ctx->n_blocks));
-    CK(launch_features(ctx, mu, ctx->d_feat));
+    CK(launch_features_mu(ctx, mu, ctx->d_feat));
     CK(mlp_predict_on(ctx->predictor, ctx->stream, ctx->d_feat, ctx->n_blocks, ctx->d_pred));
     ctx->n_launches += 2;
     pred = ctx->d_pred;
@@ -560,8 +566,46 @@ nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out) 
   return NOLSM_OK;
 }
 
-nolsm_status nolsm_set_mu(nolsm_ctx* ctx, double n_electrons, double mu_lo, double mu_hi, double tol_n,
-                          int32_t max_steps, double* mu_out, double* n_out, int32_t* steps_out) {
+namespace {
+
+// First point of the bisection from the predictor: over a grid of mu (coarse, then fine around the
+// best coarse point) the mean predicted log10 distance from mu to the blocks' spectra peaks in
+// the gap, where the electron count settles.  Returns NaN when unavailable.
+double predicted_gap_mu(nolsm_ctx* ctx, double lo, double hi) {
+  if (!ctx->predictor) return NAN;
+  const int G = 40;
+  if (dalloc(ctx, &ctx->d_feat, (size_t)32 * ctx->n_blocks) != cudaSuccess ||
+      dalloc(ctx, &ctx->d_pred, (size_t)3 * ctx->n_blocks) != cudaSuccess ||
+      dalloc(ctx, &ctx->d_scores, (size_t)2 * G) != cudaSuccess)
+    return NAN;
+  double a = lo, b = hi, best = NAN;
+  for (int level = 0; level < 2; ++level) {
+    const double h = (b - a) / (G + 1);
+    for (int g = 0; g < G; ++g) {
+      const double mu = a + (g + 1) * h;
+      if (launch_features_mu(ctx, mu, ctx->d_feat) != cudaSuccess ||
+          mlp_predict_on(ctx->predictor, ctx->stream, ctx->d_feat, ctx->n_blocks, ctx->d_pred) != cudaSuccess ||
+          launch_score(ctx, ctx->d_pred, ctx->d_scores + g) != cudaSuccess)
+        return NAN;
+    }
+    ctx->n_launches += 3 * G;
+    std::vector<float> sc(G);
+    if (cudaMemcpyAsync(sc.data(), ctx->d_scores, sizeof(float) * G, cudaMemcpyDeviceToHost, ctx->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+      return NAN;
+    int gb = (int)(std::max_element(sc.begin(), sc.end()) - sc.begin());
+    best = a + (gb + 1) * h;
+    a = best - h;
+    b = best + h;
+  }
+  return best;
+}
+
+}  // namespace
+
+extern "C" nolsm_status nolsm_set_mu(nolsm_ctx* ctx, double n_electrons, double mu_lo, double mu_hi, double tol_n,
+                                     int32_t max_steps, double* mu_out, double* n_out, int32_t* steps_out) {
   if (!ctx) return NOLSM_EINVAL;
   if (ctx->sticky != NOLSM_OK) return ctx->sticky;
   if (!ctx->built) return fail(ctx, NOLSM_ENOTBUILT, "nolsm_build_submatrices has not succeeded");
@@ -575,6 +619,10 @@ nolsm_status nolsm_set_mu(nolsm_ctx* ctx, double n_electrons, double mu_lo, doub
   }
   const double lo0 = lo, hi0 = hi;
   double mu = 0.5 * (lo + hi), n_mu = 0.0;
+  if (ctx->opt.bounds == NOLSM_BOUNDS_LEARNED) {
+    const double guess = predicted_gap_mu(ctx, lo, hi);
+    if (std::isfinite(guess) && guess > lo && guess < hi) mu = guess;
+  }
   int steps = 0;
   nolsm_sign_stats s;
   while (true) {
@@ -651,7 +699,7 @@ nolsm_status nolsm_block_bounds(const nolsm_ctx* ctx, double* lo, double* hi) {
 
 nolsm_status nolsm_block_features(nolsm_ctx* ctx, double mu, float* feat) {
   if (!ctx || !ctx->built || !feat || !std::isfinite(mu)) return NOLSM_EINVAL;
-  if (launch_features(ctx, mu, feat) != cudaSuccess) return NOLSM_ECUDA;
+  if (launch_features_mu(ctx, mu, feat) != cudaSuccess) return NOLSM_ECUDA;
   ctx->n_launches += 1;
   return NOLSM_OK;
 }

@@ -287,7 +287,8 @@ __global__ void slabs_kernel(const BlockDesc* __restrict__ blocks, const int32_t
 
 // Gershgorin bounds of A0 (real n x n part): [min_i a_ii - R_i, max_i a_ii + R_i].
 __global__ void gershgorin_kernel(const BlockDesc* __restrict__ blocks, const float* __restrict__ a0,
-                                  double* __restrict__ lo, double* __restrict__ hi, DevFlags* flags) {
+                                  double* __restrict__ lo, double* __restrict__ hi, float* __restrict__ row_diag,
+                                  float* __restrict__ row_rad, DevFlags* flags) {
   const BlockDesc bd = blocks[blockIdx.x];
   const int n = bd.n, ld = bd.n_pad;
   const float* A = a0 + bd.off_mat;
@@ -304,6 +305,10 @@ __global__ void gershgorin_kernel(const BlockDesc* __restrict__ blocks, const fl
     for (int o = 16; o; o >>= 1) {
       rad += __shfl_xor_sync(0xffffffffu, rad, o);
       d += __shfl_xor_sync(0xffffffffu, d, o);
+    }
+    if (lane == 0 && row_diag) {
+      row_diag[bd.off_idx + r] = d;      // per-row data for features at any mu (stride kMaxDim)
+      row_rad[bd.off_idx + r] = rad;
     }
     rad *= up;
     wlo = fminf(wlo, d - rad);
@@ -375,7 +380,8 @@ cudaError_t launch_slabs_impl(nolsm_ctx* ctx, const void* lfac, int fp32, const 
 }
 
 cudaError_t launch_bounds(nolsm_ctx* ctx) {
-  gershgorin_kernel<<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_a0, ctx->d_lo, ctx->d_hi, ctx->d_flags);
+  gershgorin_kernel<<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_a0, ctx->d_lo, ctx->d_hi,
+                                                             ctx->d_rowd, ctx->d_rowr, ctx->d_flags);
   return cudaGetLastError();
 }
 

@@ -137,6 +137,75 @@ __global__ void __launch_bounds__(256) features_kernel(const BlockDesc* __restri
   }
 }
 
+// Features at a new mu from the mu-independent ones (computed once per build) and the per-row
+// diagonal and Gershgorin radius: O(n) per block instead of O(n^2).
+__global__ void __launch_bounds__(128) features_mu_kernel(const BlockDesc* __restrict__ blocks,
+                                                          const float* __restrict__ fstatic,
+                                                          const float* __restrict__ row_diag,
+                                                          const float* __restrict__ row_rad, double mu, float margin,
+                                                          float* __restrict__ feat) {
+  __shared__ float red[4];
+  const BlockDesc bd = blocks[blockIdx.x];
+  const int n = bd.n;
+  const float m = (float)mu;
+  const float* D = row_diag + bd.off_idx;
+  const float* R = row_rad + bd.off_idx;
+  float mn = FLT_MAX, below = 0, n05 = 0, n1 = 0, disc = 0, medge = FLT_MAX, sedge = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float dm = D[i] - m, ad = fabsf(dm), e = ad - R[i];
+    mn = fminf(mn, ad);
+    below += (dm < 0.f);
+    n05 += (ad < 0.05f);
+    n1 += (ad < 0.1f);
+    disc += (ad <= R[i]);
+    medge = fminf(medge, e);
+    sedge += e;
+  }
+  for (int o = 16; o; o >>= 1) {
+    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    medge = fminf(medge, __shfl_xor_sync(0xffffffffu, medge, o));
+  }
+  below = block_sum(below, red);
+  n05 = block_sum(n05, red);
+  n1 = block_sum(n1, red);
+  disc = block_sum(disc, red);
+  sedge = block_sum(sedge, red);
+  __shared__ float smn[4], sme[4];
+  if ((threadIdx.x & 31) == 0) { smn[threadIdx.x >> 5] = mn; sme[threadIdx.x >> 5] = medge; }
+  __syncthreads();
+  const float* fs = fstatic + (int64_t)blockIdx.x * NI;
+  float* f = feat + (int64_t)blockIdx.x * NI;
+  if (threadIdx.x < NI) f[threadIdx.x] = fs[threadIdx.x];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const float nf = (float)n;
+    float mn_all = FLT_MAX, me_all = FLT_MAX;
+    for (int w = 0; w < 4; ++w) { mn_all = fminf(mn_all, smn[w]); me_all = fminf(me_all, sme[w]); }
+    const float lo = fs[3], hi = fs[4];
+    f[2] = m;
+    f[16] = fs[5] - m;
+    f[17] = mn_all;
+    f[18] = below / nf;
+    f[19] = n05 / nf;
+    f[20] = n1 / nf;
+    f[25] = disc / nf;
+    f[26] = me_all;
+    f[27] = sedge / nf;
+    f[28] = (hi > lo) ? (m - lo) / (hi - lo) : 0.5f;
+    f[29] = log10f(fmaxf(fmaxf(fabsf(hi - m), fabsf(m - lo)) * (1.f + margin), 1e-6f));
+  }
+}
+
+// score = mean over blocks of the predicted log10 distance from mu to the nearest eigenvalue
+__global__ void __launch_bounds__(256) score_kernel(int n_blocks, const float* __restrict__ pred,
+                                                    float* __restrict__ score) {
+  __shared__ float red[8];
+  float s = 0.f;
+  for (int b = threadIdx.x; b < n_blocks; b += blockDim.x) s += pred[3 * b + 2];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) *score = s / (float)n_blocks;
+}
+
 // ------------------------------------------------------------------------------------------ Lanczos
 // One CTA per block; k steps with full (twice-repeated classical Gram-Schmidt) reorthogonalisation
 // against the stored basis.  op 0: v -> A0 v.  op 1: v -> X (A0 - mu) v with X the converged sign
@@ -422,6 +491,17 @@ constexpr size_t PRED_SMEM = sizeof(float) * (NH * 33 + NH * 129 + NO * NH + NI 
 cudaError_t launch_features(nolsm_ctx* ctx, double mu, float* feat) {
   features_kernel<<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_a0, ctx->d_lo, ctx->d_hi, mu,
                                                           (float)ctx->opt.alpha_margin, feat);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_features_mu(nolsm_ctx* ctx, double mu, float* feat) {
+  features_mu_kernel<<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_feat_static, ctx->d_rowd,
+                                                             ctx->d_rowr, mu, (float)ctx->opt.alpha_margin, feat);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_score(nolsm_ctx* ctx, const float* pred, float* score) {
+  score_kernel<<<1, 256, 0, ctx->stream>>>(ctx->n_blocks, pred, score);
   return cudaGetLastError();
 }
 

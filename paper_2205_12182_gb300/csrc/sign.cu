@@ -201,14 +201,14 @@ template <typename T>
 __global__ void ns_restart_fill_kernel(const BlockDesc* __restrict__ blocks, const float* __restrict__ a0,
                                        const NsState* __restrict__ st, const double* __restrict__ lo,
                                        const double* __restrict__ hi, double mu, float margin, T* __restrict__ x0) {
-  const int b = blockIdx.y;
+  const int b = blockIdx.x;
   if (st[b].status != kRestart) return;
   const BlockDesc bd = blocks[b];
   const int n = bd.n, ld = bd.n_pad;
   const float alpha = (float)(fmax(fabs(hi[b] - mu), fabs(mu - lo[b])) * (1.0 + margin));
   const float inv = 1.f / alpha, muf = (float)mu;
   const int64_t total = (int64_t)ld * ld;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
     const int r = (int)(e / ld), c = (int)(e % ld);
     float v;
     if (r < n && c < n) v = (a0[bd.off_mat + e] - (r == c ? muf : 0.f)) * inv;
@@ -656,7 +656,7 @@ cudaError_t launch_ns_check_impl(nolsm_ctx* ctx, const float* tol_b, int detect_
 cudaError_t launch_ns_check_impl(nolsm_ctx* ctx, const float* tol_b) { return launch_ns_check_impl(ctx, tol_b, 0); }
 
 cudaError_t launch_ns_restart(nolsm_ctx* ctx, double mu, int half) {
-  const dim3 g(64, ctx->n_blocks);
+  const dim3 g(ctx->n_blocks);
   const float margin = (float)ctx->opt.alpha_margin;
   if (half == 0)
     ns_restart_fill_kernel<float><<<g, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_a0, ctx->d_state, ctx->d_lo,

@@ -143,3 +143,29 @@ def test_bad_predictions_cost_iterations_not_accuracy(nl, sys1, orc1, mu1, case)
     assert st["n_electrons"] == pytest.approx(2 * orc1.electron_count(mu1), rel=1e-4)
     if case == "radius_far_too_small":
         assert st["n_restarted"] > 0
+
+
+def test_trained_predictor_saves_iterations_on_held_out_box(nl):
+    """The committed predictor (trained on other seeds) against Gershgorin bounds on a held-out
+    1,728-molecule box: fewer iterations and bisection steps, same accuracy on sampled blocks."""
+    import os
+    from synth import water_box
+    s = water_box(12, seed=201, neighbourhood=8.0)
+    weights = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                           "paper_2205_12182_gb300", "weights", "bounds_mlp.json")
+    pred = nl.BoundPredictor.load(weights)
+    g = nl.Nolsm(precision=nl.PREC_MIXED_FP16).build(s)
+    mu_g, n_g, steps_g = g.set_mu(s.n_electrons, tol_n=1e-3)
+    it_g = g.sign_batch(mu_g)["iters_avg"]
+    lr = nl.Nolsm(precision=nl.PREC_MIXED_FP16, bounds=nl.BOUNDS_LEARNED).build(s)
+    lr.set_predictor(pred)
+    mu_l, n_l, steps_l = lr.set_mu(s.n_electrons, tol_n=1e-3)
+    it_l = lr.sign_batch(mu_l)["iters_avg"]
+    assert steps_l <= steps_g
+    assert lr.sign_batch(mu_g)["iters_avg"] < it_g
+    d = lr.density().cpu().numpy()
+    sample = np.random.default_rng(2).choice(s.n_blocks, 6, replace=False)
+    o = NolsmOracle.from_system(s, blocks=sample).prepare()
+    ref = o.density(mu_g)
+    own = np.isin(s.col, np.concatenate([s.block_cols(int(b)) for b in sample]))
+    assert np.abs(d[own] - ref[own]).max() <= 1e-3
