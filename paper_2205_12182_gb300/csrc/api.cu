@@ -566,46 +566,8 @@ nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out) 
   return NOLSM_OK;
 }
 
-namespace {
-
-// First point of the bisection from the predictor: over a grid of mu (coarse, then fine around the
-// best coarse point) the mean predicted log10 distance from mu to the blocks' spectra peaks in
-// the gap, where the electron count settles.  Returns NaN when unavailable.
-double predicted_gap_mu(nolsm_ctx* ctx, double lo, double hi) {
-  if (!ctx->predictor) return NAN;
-  const int G = 40;
-  if (dalloc(ctx, &ctx->d_feat, (size_t)32 * ctx->n_blocks) != cudaSuccess ||
-      dalloc(ctx, &ctx->d_pred, (size_t)3 * ctx->n_blocks) != cudaSuccess ||
-      dalloc(ctx, &ctx->d_scores, (size_t)2 * G) != cudaSuccess)
-    return NAN;
-  double a = lo, b = hi, best = NAN;
-  for (int level = 0; level < 2; ++level) {
-    const double h = (b - a) / (G + 1);
-    for (int g = 0; g < G; ++g) {
-      const double mu = a + (g + 1) * h;
-      if (launch_features_mu(ctx, mu, ctx->d_feat) != cudaSuccess ||
-          mlp_predict_on(ctx->predictor, ctx->stream, ctx->d_feat, ctx->n_blocks, ctx->d_pred) != cudaSuccess ||
-          launch_score(ctx, ctx->d_pred, ctx->d_scores + g) != cudaSuccess)
-        return NAN;
-    }
-    ctx->n_launches += 3 * G;
-    std::vector<float> sc(G);
-    if (cudaMemcpyAsync(sc.data(), ctx->d_scores, sizeof(float) * G, cudaMemcpyDeviceToHost, ctx->stream) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(ctx->stream) != cudaSuccess)
-      return NAN;
-    int gb = (int)(std::max_element(sc.begin(), sc.end()) - sc.begin());
-    best = a + (gb + 1) * h;
-    a = best - h;
-    b = best + h;
-  }
-  return best;
-}
-
-}  // namespace
-
-extern "C" nolsm_status nolsm_set_mu(nolsm_ctx* ctx, double n_electrons, double mu_lo, double mu_hi, double tol_n,
-                                     int32_t max_steps, double* mu_out, double* n_out, int32_t* steps_out) {
+nolsm_status nolsm_set_mu(nolsm_ctx* ctx, double n_electrons, double mu_lo, double mu_hi, double tol_n,
+                          int32_t max_steps, double* mu_out, double* n_out, int32_t* steps_out) {
   if (!ctx) return NOLSM_EINVAL;
   if (ctx->sticky != NOLSM_OK) return ctx->sticky;
   if (!ctx->built) return fail(ctx, NOLSM_ENOTBUILT, "nolsm_build_submatrices has not succeeded");
@@ -619,10 +581,6 @@ extern "C" nolsm_status nolsm_set_mu(nolsm_ctx* ctx, double n_electrons, double 
   }
   const double lo0 = lo, hi0 = hi;
   double mu = 0.5 * (lo + hi), n_mu = 0.0;
-  if (ctx->opt.bounds == NOLSM_BOUNDS_LEARNED) {
-    const double guess = predicted_gap_mu(ctx, lo, hi);
-    if (std::isfinite(guess) && guess > lo && guess < hi) mu = guess;
-  }
   int steps = 0;
   nolsm_sign_stats s;
   while (true) {

@@ -73,11 +73,12 @@ struct WarpChunk {
 //   R[r, j0:j0+32] = S[r, j0:j0+32] - L[r, 0:j0] L[j0:j0+32, 0:j0]^T  for rows r >= j0 (warp tiles)
 //   factor the 32x32 diagonal of R (warp 0), then L[r, panel] = R[r, panel] L_jj^-T (row solves).
 // The strictly upper triangle is zeroed at the end.
-template <typename T>
-__global__ void __launch_bounds__(256) cholesky_kernel(const BlockDesc* __restrict__ blocks, T* __restrict__ pool,
-                                                       float* __restrict__ l32, DevFlags* flags) {
-  __shared__ WarpChunk<T> chunks[8];
+template <typename T, int NW>
+__global__ void __launch_bounds__(NW * 32) cholesky_kernel(const BlockDesc* __restrict__ blocks, T* __restrict__ pool,
+                                                           float* __restrict__ l32, DevFlags* flags) {
+  __shared__ WarpChunk<T> chunks[NW];
   __shared__ T diag[32][33];
+  __shared__ T rdiag[32];
   __shared__ int s_bad;
   const BlockDesc bd = blocks[blockIdx.x];
   const int n = bd.n, ld = bd.n_pad;
@@ -89,7 +90,7 @@ __global__ void __launch_bounds__(256) cholesky_kernel(const BlockDesc* __restri
   for (int j0 = 0; j0 < n; j0 += 32) {
     const int jb = min(32, n - j0);
     // --- update panel columns with the previous panels: row tiles of 32 rows, one per warp
-    for (int r0 = j0 + warp * 32; r0 < n; r0 += 8 * 32) {
+    for (int r0 = j0 + warp * 32; r0 < n; r0 += NW * 32) {
       T acc[32];
 #pragma unroll
       for (int r = 0; r < 32; ++r) acc[r] = T(0);
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(256) cholesky_kernel(const BlockDesc* __restri
       }
     }
     __syncthreads();
-    // --- factor the diagonal 32x32 block (warp 0, lane = row)
+    // --- factor the diagonal 32x32 block (warp 0, lane = row); keep 1 / L_kk for the panel solve
     if (warp == 0) {
       for (int r = 0; r < 32; ++r) diag[r][lane] = (r < jb && lane < jb) ? A[(int64_t)(j0 + r) * ld + j0 + lane] : T(r == lane);
       __syncwarp();
@@ -126,10 +127,12 @@ __global__ void __launch_bounds__(256) cholesky_kernel(const BlockDesc* __restri
         if (lane == k) {
           T d = diag[k][k];
           if (!(d > T(0))) { s_bad = 1; d = T(1); }
-          diag[k][k] = sqrt(d);
+          const T s = sqrt(d);
+          diag[k][k] = s;
+          rdiag[k] = T(1) / s;
         }
         __syncwarp();
-        if (lane > k) diag[lane][k] /= diag[k][k];
+        if (lane > k) diag[lane][k] *= rdiag[k];
         __syncwarp();
         if (lane > k) {
           const T lk = diag[lane][k];
@@ -141,22 +144,25 @@ __global__ void __launch_bounds__(256) cholesky_kernel(const BlockDesc* __restri
         if (lane <= r) A[(int64_t)(j0 + r) * ld + j0 + lane] = diag[r][lane];
     }
     __syncthreads();
-    // --- panel rows below: x L_jj^T = r  (forward substitution per row, thread per row)
-    for (int gr = j0 + jb + threadIdx.x; gr < n; gr += blockDim.x) {
-      T x[32];
-      T* row = A + (int64_t)gr * ld + j0;
-#pragma unroll
-      for (int k = 0; k < 32; ++k) x[k] = (k < jb) ? row[k] : T(0);
-#pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        T v = x[k];
-#pragma unroll
-        for (int t = 0; t < k; ++t) v = fma(-x[t], diag[k][t], v);
-        x[k] = v / diag[k][k];
+    // --- panel rows below: x L_jj^T = r by forward substitution, one warp per 32-row tile held in
+    //     shared memory (lane = row), multiplying by the reciprocals instead of dividing
+    for (int r0 = j0 + jb + warp * 32; r0 < n; r0 += NW * 32) {
+      for (int r = 0; r < 32; ++r) {
+        const int gr = r0 + r;
+        ch.a[r][lane] = (gr < n && lane < jb) ? A[(int64_t)gr * ld + j0 + lane] : T(0);
       }
-#pragma unroll
-      for (int k = 0; k < 32; ++k)
-        if (k < jb) row[k] = x[k];
+      __syncwarp();
+      for (int k = 0; k < jb; ++k) {
+        T v = ch.a[lane][k];
+        for (int q = 0; q < k; ++q) v = fma(-ch.a[lane][q], diag[k][q], v);
+        ch.a[lane][k] = v * rdiag[k];
+      }
+      __syncwarp();
+      for (int r = 0; r < 32; ++r) {
+        const int gr = r0 + r;
+        if (gr < n && lane < jb) A[(int64_t)gr * ld + j0 + lane] = ch.a[r][lane];
+      }
+      __syncwarp();
     }
     __syncthreads();
   }
@@ -165,7 +171,7 @@ __global__ void __launch_bounds__(256) cholesky_kernel(const BlockDesc* __restri
   // padding.
   if (l32) {
     float* Lf = l32 + bd.off_mat;
-    for (int r = warp; r < ld; r += 8)
+    for (int r = warp; r < ld; r += NW)
       for (int c = lane; c < ld; c += 32)
         Lf[(int64_t)r * ld + c] = (r < n && c <= r) ? (float)A[(int64_t)r * ld + c] : 0.f;
   }
@@ -176,10 +182,10 @@ __global__ void __launch_bounds__(256) cholesky_kernel(const BlockDesc* __restri
 //   X[i-block, c-block] = -L_ii^-1 sum_{k=c}^{i-1} L_ik X_kc   (c < i),   X_ii = L_ii^-1.
 // Phase 1 forms R = sum_k L_ik X_kc with warp tiles (one 32x32 tile per c-block), phase 2
 // solves L_ii Y = (E - R) column by column (thread per column).
-template <typename T>
-__global__ void __launch_bounds__(256) trinv_kernel(const BlockDesc* __restrict__ blocks, const T* __restrict__ lpool,
-                                                    T* __restrict__ xpool) {
-  __shared__ WarpChunk<T> chunks[8];
+template <typename T, int NW>
+__global__ void __launch_bounds__(NW * 32) trinv_kernel(const BlockDesc* __restrict__ blocks,
+                                                        const T* __restrict__ lpool, T* __restrict__ xpool) {
+  __shared__ WarpChunk<T> chunks[NW];
   __shared__ T lii[32][33];
   const BlockDesc bd = blocks[blockIdx.x];
   const int n = bd.n, ld = bd.n_pad;
@@ -188,14 +194,14 @@ __global__ void __launch_bounds__(256) trinv_kernel(const BlockDesc* __restrict_
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   WarpChunk<T>& ch = chunks[warp];
   // the output's upper triangle and padding stay zero
-  for (int r = warp; r < ld; r += 8)
+  for (int r = warp; r < ld; r += NW)
     for (int c = lane; c < ld; c += 32) X[(int64_t)r * ld + c] = T(0);
   __syncthreads();
   const int nbk = (n + 31) / 32;
   for (int ib = 0; ib < nbk; ++ib) {
     const int i0 = ib * 32, ibw = min(32, n - i0);
     // phase 1: R for every c-block < ib, written into X's block row (as -R) for phase 2
-    for (int cb = warp; cb < ib; cb += 8) {
+    for (int cb = warp; cb < ib; cb += NW) {
       const int c0 = cb * 32;
       T acc[32];
 #pragma unroll
@@ -347,16 +353,16 @@ cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode) {
   // sb holds T_b(S) in FP64 (first sum_sq doubles); the second half is scratch.
   float* s32 = reinterpret_cast<float*>(sb + ctx->sum_sq);   // FP32 factor lives in the scratch half
   if (mode == NOLSM_CHOL_FP64_INV64) {
-    cholesky_kernel<double><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, sb, nullptr, ctx->d_flags);
-    trinv_kernel<double><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, sb, sb + ctx->sum_sq);
+    cholesky_kernel<double, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, sb, nullptr, ctx->d_flags);
+    trinv_kernel<double, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, sb, sb + ctx->sum_sq);
     to_f32_kernel<double><<<sq_grid(ctx->n_blocks), 256, 0, ctx->stream>>>(ctx->d_blocks, sb + ctx->sum_sq, ctx->d_linv, 1);
   } else if (mode == NOLSM_CHOL_FP64) {
-    cholesky_kernel<double><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, ctx->d_flags);
-    trinv_kernel<float><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
+    cholesky_kernel<double, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, ctx->d_flags);
+    trinv_kernel<float, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
   } else {
     to_f32_kernel<double><<<sq_grid(ctx->n_blocks), 256, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, 0);
-    cholesky_kernel<float><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, s32, nullptr, ctx->d_flags);
-    trinv_kernel<float><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
+    cholesky_kernel<float, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, s32, nullptr, ctx->d_flags);
+    trinv_kernel<float, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
   }
   return cudaGetLastError();
 }

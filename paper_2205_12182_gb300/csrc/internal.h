@@ -157,7 +157,6 @@ struct nolsm_ctx {
   float* d_rowd = nullptr;      // diag(A0) per row (stride kMaxDim per block)
   float* d_rowr = nullptr;      // Gershgorin radius per row (same layout)
   float* d_feat_static = nullptr;   // mu-independent features (n_blocks x 32)
-  float* d_scores = nullptr;    // mu-scan scores
 
   double last_mu = 0.0;
   nolsm_sign_stats last_stats{};
@@ -199,7 +198,6 @@ int tc_tile_n();
 // learn.cu
 cudaError_t launch_features(nolsm_ctx* ctx, double mu, float* feat);
 cudaError_t launch_features_mu(nolsm_ctx* ctx, double mu, float* feat);
-cudaError_t launch_score(nolsm_ctx* ctx, const float* pred, float* score);
 cudaError_t launch_lanczos(nolsm_ctx* ctx, double mu, int op, int k, float* basis, int64_t stride, float* out);
 cudaError_t mlp_predict_on(const struct nolsm_mlp* m, cudaStream_t s, const float* x, int n, float* y);
 

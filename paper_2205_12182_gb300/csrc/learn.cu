@@ -196,16 +196,6 @@ __global__ void __launch_bounds__(128) features_mu_kernel(const BlockDesc* __res
   }
 }
 
-// score = mean over blocks of the predicted log10 distance from mu to the nearest eigenvalue
-__global__ void __launch_bounds__(256) score_kernel(int n_blocks, const float* __restrict__ pred,
-                                                    float* __restrict__ score) {
-  __shared__ float red[8];
-  float s = 0.f;
-  for (int b = threadIdx.x; b < n_blocks; b += blockDim.x) s += pred[3 * b + 2];
-  s = block_sum(s, red);
-  if (threadIdx.x == 0) *score = s / (float)n_blocks;
-}
-
 // ------------------------------------------------------------------------------------------ Lanczos
 // One CTA per block; k steps with full (twice-repeated classical Gram-Schmidt) reorthogonalisation
 // against the stored basis.  op 0: v -> A0 v.  op 1: v -> X (A0 - mu) v with X the converged sign
@@ -497,11 +487,6 @@ cudaError_t launch_features(nolsm_ctx* ctx, double mu, float* feat) {
 cudaError_t launch_features_mu(nolsm_ctx* ctx, double mu, float* feat) {
   features_mu_kernel<<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_feat_static, ctx->d_rowd,
                                                              ctx->d_rowr, mu, (float)ctx->opt.alpha_margin, feat);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_score(nolsm_ctx* ctx, const float* pred, float* score) {
-  score_kernel<<<1, 256, 0, ctx->stream>>>(ctx->n_blocks, pred, score);
   return cudaGetLastError();
 }
 
