@@ -187,6 +187,7 @@ __global__ void __launch_bounds__(NW * 32) trinv_kernel(const BlockDesc* __restr
                                                         const T* __restrict__ lpool, T* __restrict__ xpool) {
   __shared__ WarpChunk<T> chunks[NW];
   __shared__ T lii[32][33];
+  __shared__ T rli[32];
   const BlockDesc bd = blocks[blockIdx.x];
   const int n = bd.n, ld = bd.n_pad;
   const T* L = lpool + bd.off_mat;
@@ -222,31 +223,34 @@ __global__ void __launch_bounds__(NW * 32) trinv_kernel(const BlockDesc* __restr
       }
       for (int r = 0; r < ibw; ++r) X[(int64_t)(i0 + r) * ld + c0 + lane] = -acc[r];
     }
-    if (threadIdx.x < 32 * 32 / 32) {
+    if (threadIdx.x < 32) {
       for (int r = 0; r < 32; ++r)
-        if (threadIdx.x < 32) lii[r][threadIdx.x] = (r < ibw && threadIdx.x < ibw) ? L[(int64_t)(i0 + r) * ld + i0 + threadIdx.x] : T(r == (int)threadIdx.x);
+        lii[r][threadIdx.x] = (r < ibw && (int)threadIdx.x < ibw) ? L[(int64_t)(i0 + r) * ld + i0 + threadIdx.x]
+                                                                  : T(r == (int)threadIdx.x);
+      rli[threadIdx.x] = T(1) / ((threadIdx.x < (unsigned)ibw) ? L[(int64_t)(i0 + threadIdx.x) * ld + i0 + threadIdx.x]
+                                                                : T(1));
     }
     __syncthreads();
-    // phase 2: column j of the block row: solve L_ii y = rhs, rhs = -R (c < i) or e_j (diagonal block)
+    // phase 2: for every column j of the block row, L_ii y = rhs with rhs = -R (c < i) or e_j
+    // (diagonal block); one warp per 32 columns held in shared memory (lane = column)
     const int ncols = i0 + ibw;
-    for (int j = threadIdx.x; j < ncols; j += blockDim.x) {
-      T y[32];
-      const bool diag_blk = j >= i0;
-#pragma unroll
+    for (int jc = warp * 32; jc < ncols; jc += NW * 32) {
+      const int j = jc + lane;
       for (int r = 0; r < 32; ++r) {
-        if (diag_blk) y[r] = T((i0 + r) == j);
-        else y[r] = (r < ibw) ? X[(int64_t)(i0 + r) * ld + j] : T(0);
+        T v = T(0);
+        if (j < ncols && r < ibw) v = (j >= i0) ? T((i0 + r) == j) : X[(int64_t)(i0 + r) * ld + j];
+        ch.a[r][lane] = v;
       }
-#pragma unroll
-      for (int r = 0; r < 32; ++r) {
-        T v = y[r];
-#pragma unroll
-        for (int t = 0; t < r; ++t) v = fma(-lii[r][t], y[t], v);
-        y[r] = v / lii[r][r];
+      __syncwarp();
+      for (int r = 0; r < ibw; ++r) {
+        T v = ch.a[r][lane];
+        for (int q = 0; q < r; ++q) v = fma(-lii[r][q], ch.a[q][lane], v);
+        ch.a[r][lane] = v * rli[r];
       }
-#pragma unroll
-      for (int r = 0; r < 32; ++r)
-        if (r < ibw) X[(int64_t)(i0 + r) * ld + j] = y[r];
+      __syncwarp();
+      if (j < ncols)
+        for (int r = 0; r < ibw; ++r) X[(int64_t)(i0 + r) * ld + j] = ch.a[r][lane];
+      __syncwarp();
     }
     __syncthreads();
   }
