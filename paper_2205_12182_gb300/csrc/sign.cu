@@ -7,6 +7,7 @@
 #include "internal.h"
 
 #include <cfloat>
+#include <type_traits>
 
 namespace nolsm {
 namespace {
@@ -362,14 +363,40 @@ __global__ void ns_advance_kernel(int n_blocks, NsState* __restrict__ st) {
 //   N_b = sum_{j in C_b} (L P L^-1)_jj = <Lc, Y>,   E_b = sum_j (H_b D_b)_jj = <Z, Y>   (FP64 sums).
 // One CTA per block; slabs are column-major (ld = n_pad) in global scratch, X rows stream
 // through shared memory in 128 x 32 tiles.
+// Compensated accumulation (Dot2 of Ogita, Rump & Oishi 2005): the rounding error of each
+// product (by FMA) and of each addition (TwoSum) is summed on the side; the FP32 path uses it for
+// the slab products and the back-transform, where the error budget is tightest.
+struct Acc2 {
+  float s = 0.f, e = 0.f;
+  __device__ __forceinline__ void add_prod(float x, float y) {
+    const float p = x * y;
+    const float pe = fmaf(x, y, -p);
+    const float t = s + p;
+    const float z = t - s;
+    e += ((s - (t - z)) + (p - z)) + pe;
+    s = t;
+  }
+  __device__ __forceinline__ float value() const { return s + e; }
+};
+
+template <bool COMP>
+struct AccSel;
+template <> struct AccSel<false> {
+  float s = 0.f;
+  __device__ __forceinline__ void add_prod(float x, float y) { s = fmaf(x, y, s); }
+  __device__ __forceinline__ float value() const { return s; }
+};
+template <> struct AccSel<true> : Acc2 {};
+
 template <typename T>
 __device__ void slab_product(const T* __restrict__ X, int ld, int c, const float* __restrict__ V,
                              float* __restrict__ P, float (*Xs)[33], float (*Vs)[8]) {
+  constexpr bool COMP = std::is_same<T, float>::value;
   const int tid = threadIdx.x;
   const int row = tid >> 1, cb = (tid & 1) * 4;
   for (int r0 = 0; r0 < ld; r0 += 128) {
     for (int c0 = 0; c0 < c; c0 += 8) {
-      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      AccSel<COMP> acc[4];
       for (int k0 = 0; k0 < ld; k0 += 32) {
         for (int e = tid; e < 128 * 32; e += blockDim.x) {
           const int rr = e >> 5, kk = e & 31;
@@ -384,13 +411,13 @@ __device__ void slab_product(const T* __restrict__ X, int ld, int c, const float
         for (int kk = 0; kk < 32; ++kk) {
           const float x = Xs[row][kk];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) acc[q] = fmaf(x, Vs[kk][cb + q], acc[q]);
+          for (int q = 0; q < 4; ++q) acc[q].add_prod(x, Vs[kk][cb + q]);
         }
         __syncthreads();
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        if (c0 + cb + q < c) P[(int64_t)(c0 + cb + q) * ld + r0 + row] = acc[q];
+        if (c0 + cb + q < c) P[(int64_t)(c0 + cb + q) * ld + r0 + row] = acc[q].value();
     }
   }
   __syncthreads();
@@ -506,6 +533,7 @@ __device__ __forceinline__ int lower_bound_g(const int32_t* a, int n, int32_t ke
   return lo;
 }
 
+template <bool COMP>
 __global__ void __launch_bounds__(256) density_kernel(const BlockDesc* __restrict__ blocks,
                                                       const int32_t* __restrict__ idx_pool,
                                                       const int32_t* __restrict__ blk_cols,
@@ -525,7 +553,7 @@ __global__ void __launch_bounds__(256) density_kernel(const BlockDesc* __restric
   const int row = tid >> 1, cb = (tid & 1) * 4;
   for (int r0 = 0; r0 < ld; r0 += 128) {
     for (int c0 = 0; c0 < c; c0 += 8) {
-      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      AccSel<COMP> acc[4];
       for (int k0 = r0; k0 < ld; k0 += 32) {     // L^-1[k, i] = 0 for k < i
         for (int e = tid; e < 32 * 128; e += blockDim.x) {
           const int kk = e >> 7, ii = e & 127;
@@ -540,13 +568,13 @@ __global__ void __launch_bounds__(256) density_kernel(const BlockDesc* __restric
         for (int kk = 0; kk < 32; ++kk) {
           const float lv = Ls[kk][row];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) acc[q] = fmaf(lv, Vs[kk][cb + q], acc[q]);
+          for (int q = 0; q < 4; ++q) acc[q].add_prod(lv, Vs[kk][cb + q]);
         }
         __syncthreads();
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        if (c0 + cb + q < c) Dsl[(int64_t)(c0 + cb + q) * ld + r0 + row] = acc[q];
+        if (c0 + cb + q < c) Dsl[(int64_t)(c0 + cb + q) * ld + r0 + row] = acc[q].value();
     }
   }
   __syncthreads();
@@ -714,9 +742,14 @@ cudaError_t launch_slab_traces(nolsm_ctx* ctx, int half) {
 cudaError_t launch_density(nolsm_ctx* ctx) {
   cudaError_t e = cudaMemsetAsync(ctx->d_dval, 0, sizeof(double) * ctx->nnz, ctx->stream);
   if (e != cudaSuccess) return e;
-  density_kernel<<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_idx, ctx->d_blk_cols, ctx->d_linv,
-                                                         ctx->d_y, ctx->d_tmp, ctx->d_row_ptr, ctx->d_col,
-                                                         ctx->d_transpose, ctx->d_dval, ctx->d_flags);
+  if (ctx->opt.precision == NOLSM_PREC_FP32)
+    density_kernel<true><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_idx, ctx->d_blk_cols,
+                                                                 ctx->d_linv, ctx->d_y, ctx->d_tmp, ctx->d_row_ptr,
+                                                                 ctx->d_col, ctx->d_transpose, ctx->d_dval, ctx->d_flags);
+  else
+    density_kernel<false><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_idx, ctx->d_blk_cols,
+                                                                  ctx->d_linv, ctx->d_y, ctx->d_tmp, ctx->d_row_ptr,
+                                                                  ctx->d_col, ctx->d_transpose, ctx->d_dval, ctx->d_flags);
   return cudaGetLastError();
 }
 
