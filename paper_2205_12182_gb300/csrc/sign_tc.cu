@@ -192,12 +192,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_cons
   TileInfo* info = reinterpret_cast<TileInfo*>(smem + STAGES * STAGE_BYTES + 256);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // Each CTA takes a contiguous run of the tile list: the list holds a block's tiles together, so
+  // one SM walks through whole blocks and re-reads each iterate from L2 rather than HBM.
   const int n_tiles = *p.n_tiles;
-  const int first = p.tile_base + (int)blockIdx.x;
-  int n_local = (n_tiles > first) ? (n_tiles - first + (int)gridDim.x - 1) / (int)gridDim.x : 0;
-  n_local = min(n_local, MAX_LOCAL);
+  const int span = min(max(n_tiles - p.tile_base, 0), MAX_LOCAL * (int)gridDim.x);
+  const int first = p.tile_base + (int)(((int64_t)span * blockIdx.x) / gridDim.x);
+  const int n_local = p.tile_base + (int)(((int64_t)span * (blockIdx.x + 1)) / gridDim.x) - first;
   for (int i = threadIdx.x; i < n_local; i += NUM_THREADS) {
-    const Tile tl = p.tiles[first + i * (int)gridDim.x];
+    const Tile tl = p.tiles[first + i];
     const BlockDesc bd = p.blocks[tl.block];
     const NsState s = p.st[tl.block];
     TileInfo f;
