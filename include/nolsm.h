@@ -81,7 +81,11 @@ typedef enum nolsm_bounds {
 typedef enum nolsm_chol_precision {
   NOLSM_CHOL_FP64 = 0,          /* Cholesky factor of T_b(S) in FP64, its triangular inverse in FP32 */
   NOLSM_CHOL_FP32 = 1,          /* factor and inverse in FP32 */
-  NOLSM_CHOL_FP64_INV64 = 2     /* factor and inverse in FP64 */
+  NOLSM_CHOL_FP64_INV64 = 2,    /* factor and inverse in FP64 */
+  NOLSM_CHOL_DF64 = 3           /* factor in double-float pairs (Dekker; 48-bit significand) on the FP32
+                                   pipe with FP64 32x32 diagonal blocks, stored as FP64; inverse in FP32.
+                                   The factor feeds the rest of the path through its FP32 rounding (and
+                                   the trace slab), where it agrees with the FP64 factor */
 } nolsm_chol_precision;
 
 /* One CSR matrix (see the conventions above). */
@@ -97,9 +101,12 @@ typedef struct nolsm_csr {
 typedef struct nolsm_options {
   int32_t precision;       /* nolsm_precision (default MIXED_FP16) */
   int32_t bounds;          /* nolsm_bounds (default GERSHGORIN) */
-  int32_t chol_precision;  /* nolsm_chol_precision (default FP64) */
+  int32_t chol_precision;  /* nolsm_chol_precision (default DF64) */
   int32_t scaled;          /* 1: scaled Newton-Schulz (Chen & Chow 2014), 0: Eq. 6 as written */
-  double sign_tol;         /* stop when ||X^2 - I||_F <= sign_tol; <= 0 picks the precision's default */
+  double sign_tol;         /* stop the full-matrix iteration when ||X^2 - I||_F <= sign_tol; <= 0 picks
+                              min(0.05, max(8 u sqrt(n_b), t)) with u the operand format's unit roundoff
+                              and t = 0.02, 4e-4, 0 for refine_iters >= 2, 1, 0 (the refinement steps
+                              on the own columns finish the convergence) */
   int32_t max_iter;        /* matrix iterations per sign evaluation (default 100) */
   int32_t refine_iters;    /* FP32 Newton-Schulz steps on the own-column slab (0..3, default 1) */
   double spin_factor;      /* electrons per orbital: N_e = spin_factor Tr(DS), E = spin_factor Tr(DH0) (default 2) */
@@ -190,7 +197,8 @@ nolsm_status nolsm_block_state(const nolsm_ctx* ctx, int32_t* iters, double* res
 
 /* Diagnostic copy of block b's n_b x n_b matrix `which` to host memory (row-major, float32):
  * which = 0: A0 = L^-1 T_b(H0) L^-T;  1: L^-1;  2, 3: the two iterate buffers X;  4: the
- * second-operand buffer of the last product.  Synchronises. */
+ * second-operand buffer of the last product;  5: the Cholesky factor L of T_b(S) (FP32 rounding
+ * of the factor as computed, zero above the diagonal).  Synchronises. */
 nolsm_status nolsm_block_matrix(const nolsm_ctx* ctx, int32_t b, int32_t which, float* out);
 
 /* Cumulative counters of ctx since nolsm_create or the last reset (reset != 0 zeroes them after

@@ -166,7 +166,7 @@ nolsm_status nolsm_default_options(nolsm_options* opt) {
   std::memset(opt, 0, sizeof(*opt));
   opt->precision = NOLSM_PREC_MIXED_FP16;
   opt->bounds = NOLSM_BOUNDS_GERSHGORIN;
-  opt->chol_precision = NOLSM_CHOL_FP64;
+  opt->chol_precision = NOLSM_CHOL_DF64;
   opt->scaled = 1;
   opt->sign_tol = 0.0;
   opt->max_iter = 100;
@@ -188,7 +188,7 @@ nolsm_status nolsm_create(nolsm_ctx** out, const nolsm_options* opt, void* cuda_
   if (ctx->opt.precision < NOLSM_PREC_FP32 || ctx->opt.precision > NOLSM_PREC_MIXED_BF16 || ctx->opt.max_iter <= 0 ||
       ctx->opt.refine_iters < 0 || ctx->opt.refine_iters > 3 || !(ctx->opt.spin_factor > 0) ||
       ctx->opt.wait_budget <= 0 || ctx->opt.alpha_margin < 0 || ctx->opt.chol_precision < 0 ||
-      ctx->opt.chol_precision > NOLSM_CHOL_FP64_INV64 || ctx->opt.bounds < NOLSM_BOUNDS_GERSHGORIN ||
+      ctx->opt.chol_precision > NOLSM_CHOL_DF64 || ctx->opt.bounds < NOLSM_BOUNDS_GERSHGORIN ||
       ctx->opt.bounds > NOLSM_BOUNDS_LEARNED || ctx->opt.lanczos_steps < 1 || ctx->opt.lanczos_steps > 64) {
     delete ctx;
     return NOLSM_EINVAL;
@@ -386,11 +386,18 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   CK(dalloc(ctx, &ctx->d_dval, (size_t)nnz));
   CK(cudaMemcpyAsync(ctx->d_blocks, ctx->h_blocks.data(), sizeof(BlockDesc) * n_blocks, cudaMemcpyHostToDevice, ctx->stream));
   {
+    // Full-matrix iterations stop once the own-column refinement can finish the job: an
+    // eigenvalue 1 - delta of X goes to about 1 - 1.5 delta^2 under one step of Eq. 6, so r
+    // refinement steps need ||X^2 - I||_F ~ 2 delta no smaller than 0.02 (r >= 2: 3.4 delta^4 is
+    // FP32 rounding for delta = 0.01) or 4e-4 (r = 1); never below the operand format's floor
+    // 8 u sqrt(n) and never above 0.05.  Each further full iteration only adds rounding.
     std::vector<float> tol((size_t)n_blocks);
     const double u = unit_roundoff(ctx);
+    const int r = ctx->opt.refine_iters;
+    const double t_refine = r >= 2 ? 0.02 : r == 1 ? 4e-4 : 0.0;
     for (int32_t b = 0; b < n_blocks; ++b) {
       const double d = 8.0 * u * std::sqrt((double)ctx->h_blocks[b].n);
-      tol[b] = (float)(ctx->opt.sign_tol > 0 ? ctx->opt.sign_tol : std::min(0.05, d));
+      tol[b] = (float)(ctx->opt.sign_tol > 0 ? ctx->opt.sign_tol : std::min(0.05, std::max(d, t_refine)));
     }
     CK(cudaMemcpyAsync(ctx->d_tol, tol.data(), sizeof(float) * n_blocks, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -508,7 +515,7 @@ nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out) 
     }
   }
   CK(launch_slab_traces(ctx, hk));
-  ctx->n_launches += 2;
+  ctx->n_launches += 1;   // sum_traces (the slab launches count themselves)
   CK(cudaEventRecord(ctx->ev1, ctx->stream));
   nolsm_status st = check_device_flags(ctx);
   harvest_gemm_events(ctx);
@@ -706,9 +713,28 @@ nolsm_status nolsm_block_state(const nolsm_ctx* ctx, int32_t* iters, double* res
 }
 
 nolsm_status nolsm_block_matrix(const nolsm_ctx* ctx, int32_t b, int32_t which, float* out) {
-  if (!ctx || !ctx->built || b < 0 || b >= ctx->n_blocks || !out || which < 0 || which > 4) return NOLSM_EINVAL;
+  if (!ctx || !ctx->built || b < 0 || b >= ctx->n_blocks || !out || which < 0 || which > 5) return NOLSM_EINVAL;
   const BlockDesc& bd = ctx->h_blocks[b];
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return NOLSM_ECUDA;
+  if (which == 5) {
+    // the factor: FP32 copy in the scratch half of the S pool for CHOL_FP32, else the FP64 lower triangle
+    const size_t nn = (size_t)bd.n * bd.n;
+    if (ctx->opt.chol_precision == NOLSM_CHOL_FP32) {
+      const float* src = reinterpret_cast<const float*>(ctx->d_sb + ctx->sum_sq) + bd.off_mat;
+      if (cudaMemcpy2D(out, sizeof(float) * bd.n, src, sizeof(float) * bd.n_pad, sizeof(float) * bd.n, bd.n,
+                       cudaMemcpyDeviceToHost) != cudaSuccess)
+        return NOLSM_ECUDA;
+    } else {
+      std::vector<double> l(nn);
+      if (cudaMemcpy2D(l.data(), sizeof(double) * bd.n, ctx->d_sb + bd.off_mat, sizeof(double) * bd.n_pad,
+                       sizeof(double) * bd.n, bd.n, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return NOLSM_ECUDA;
+      for (size_t i = 0; i < nn; ++i) out[i] = (float)l[i];
+    }
+    for (int r = 0; r < bd.n; ++r)
+      for (int c = r + 1; c < bd.n; ++c) out[(size_t)r * bd.n + c] = 0.f;
+    return NOLSM_OK;
+  }
   if (which <= 1) {
     const float* src = (which == 0 ? ctx->d_a0 : ctx->d_linv) + bd.off_mat;
     if (cudaMemcpy2D(out, sizeof(float) * bd.n, src, sizeof(float) * bd.n_pad, sizeof(float) * bd.n, bd.n,

@@ -178,6 +178,250 @@ __global__ void __launch_bounds__(NW * 32) cholesky_kernel(const BlockDesc* __re
   if (threadIdx.x == 0 && s_bad) set_error(flags, NOLSM_ENOTPD);
 }
 
+// ----------------------------------------------------------------------------------------------
+// Double-float arithmetic (Dekker 1971, "A floating-point technique for extending the available
+// precision"): a value is the unevaluated sum h + l of two FP32 numbers with |l| <= ulp(h)/2, a
+// 48-bit significand.  Products use the exact FMA split p + e = a*b (TwoProd); sums use Knuth's
+// branch-free TwoSum.  The multiply-accumulate below drops a.l*b.l and the rounding of the low
+// word, so k terms carry an error of order k * 2^-48 times the sum of |terms| -- the FP64
+// bound with 2^-48 in place of 2^-53.  On this GPU the FP32 pipe issues ~58 times the FP64 pipe's
+// multiply-adds, so one pair update (12 FP32 instructions) is ~5 times cheaper than one DFMA.
+struct __align__(8) df32 {
+  float h, l;
+};
+
+__device__ __forceinline__ df32 df_from_bits(float2 raw) {   // FP64 bit pattern stored as float2
+  const double x = __hiloint2double(__float_as_int(raw.y), __float_as_int(raw.x));
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ float2 df_to_bits(df32 a) {
+  const double x = (double)a.h + (double)a.l;
+  return make_float2(__int_as_float(__double2loint(x)), __int_as_float(__double2hiint(x)));
+}
+__device__ __forceinline__ double df_to_double(df32 a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ df32 df_from_double(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+// TwoSum renormalisation: h = fl(h + l), l = the exact remainder.
+__device__ __forceinline__ df32 df_norm(df32 a) {
+  const float s = a.h + a.l;
+  const float bb = s - a.h;
+  return {s, (a.h - (s - bb)) + (a.l - bb)};
+}
+// acc += a * b
+__device__ __forceinline__ void df_fma(df32& acc, df32 a, df32 b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  const float s = acc.h + p;
+  const float bb = s - acc.h;
+  const float err = (acc.h - (s - bb)) + (p - bb);
+  acc.h = s;
+  acc.l += err + e;
+}
+__device__ __forceinline__ df32 df_add(df32 a, df32 b) {
+  const float s = a.h + b.h;
+  const float bb = s - a.h;
+  const float err = (a.h - (s - bb)) + (b.h - bb);
+  return df_norm({s, err + a.l + b.l});
+}
+__device__ __forceinline__ df32 df_neg(df32 a) { return {-a.h, -a.l}; }
+
+// acc -= a * b
+__device__ __forceinline__ void df_fms(df32& acc, df32 a, df32 b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  const float s = acc.h - p;
+  const float bb = s - acc.h;
+  const float err = (acc.h - (s - bb)) - (p + bb);
+  acc.h = s;
+  acc.l += err - e;
+}
+
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+struct WarpChunkDF {
+  df32 a[32][33];
+  df32 b[32][33];
+};
+
+// Cholesky S = L L^T in double-float, left-looking by 32-column panels, in place over the FP64
+// pool (a pair occupies the 8 bytes of the double it replaces).  One CTA of NW warps per block.
+//   0. the lower triangle of S is converted from FP64 to pairs;
+//   for each panel j0:
+//   1. R[r, panel] = S[r, panel] - L[r, 0:j0] L[panel, 0:j0]^T for rows r >= j0 (warp tiles, pairs;
+//      both operands copied to the warp's shared chunk with cp.async, row-major);
+//   2. warp 0 factors the 32x32 diagonal block of R in FP64 and inverts it (FP64), keeping
+//      L_jj^-T as pairs; its scratch is warp 0's own chunk (idle in this phase);
+//   3. L[r, panel] = R[r, panel] L_jj^-T for the rows below, as another warp-tile product.
+//   4. finally the lower triangle is converted back to FP64; with l32 given, its FP32 rounding
+//      is also written there (zero above the diagonal and on the padding).
+// The diagonal blocks are O(n 32^2) of the O(n^3/6) work, so FP64 there costs little.
+template <int NW>
+__global__ void __launch_bounds__(NW * 32, 3) cholesky_df_kernel(const BlockDesc* __restrict__ blocks,
+                                                                 double* __restrict__ pool, float* __restrict__ l32,
+                                                                 DevFlags* flags) {
+  __shared__ WarpChunkDF chunks[NW];
+  __shared__ double rdiag[32];
+  __shared__ int s_bad;
+  const BlockDesc bd = blocks[blockIdx.x];
+  const int n = bd.n, ld = bd.n_pad;
+  float2* A = reinterpret_cast<float2*>(pool + bd.off_mat);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  WarpChunkDF& ch = chunks[warp];
+  // phase-2 scratch in warp 0's chunk: diag (FP64) over b, its inverse (FP64) over a, then
+  // binv[k][c] = (L_jj^-T)[k][c] as pairs over b (read by every warp in phase 3)
+  double(*diag)[33] = reinterpret_cast<double(*)[33]>(&chunks[0].b[0][0]);
+  double(*dinv)[33] = reinterpret_cast<double(*)[33]>(&chunks[0].a[0][0]);
+  df32(*binv)[33] = chunks[0].b;
+  if (threadIdx.x == 0) s_bad = 0;
+  for (int r = warp; r < n; r += NW)
+    for (int c = lane; c <= r; c += 32) {
+      const df32 v = df_from_bits(A[(int64_t)r * ld + c]);
+      A[(int64_t)r * ld + c] = make_float2(v.h, v.l);
+    }
+  __syncthreads();
+  for (int j0 = 0; j0 < n; j0 += 32) {
+    const int jb = min(32, n - j0);
+    // 1. panel update, one 32-row tile per warp at a time
+    for (int r0 = j0 + warp * 32; r0 < n; r0 += NW * 32) {
+      df32 acc[32];
+#pragma unroll
+      for (int r = 0; r < 32; ++r) acc[r] = {0.f, 0.f};
+      for (int k0 = 0; k0 < j0; k0 += 32) {
+        // a[r][k] = L[r0 + r, k0 + k],  b[c][k] = L[j0 + c, k0 + k]  (columns k0 + k < j0 <= rows)
+        for (int r = 0; r < 32; ++r) {
+          if (r0 + r < n) cp_async8(&ch.a[r][lane], A + (int64_t)(r0 + r) * ld + k0 + lane);
+          else ch.a[r][lane] = {0.f, 0.f};
+          if (j0 + r < n) cp_async8(&ch.b[r][lane], A + (int64_t)(j0 + r) * ld + k0 + lane);
+          else ch.b[r][lane] = {0.f, 0.f};
+        }
+        cp_async_wait_all();
+        __syncwarp();
+#pragma unroll 2
+        for (int k = 0; k < 32; ++k) {
+          const df32 bv = ch.b[lane][k];
+#pragma unroll
+          for (int r = 0; r < 32; ++r) df_fms(acc[r], ch.a[r][k], bv);
+        }
+        __syncwarp();
+      }
+      if (lane < jb) {
+        for (int r = 0; r < 32; ++r) {
+          const int gr = r0 + r;
+          if (gr < n && j0 + lane <= gr) {
+            const float2 s = A[(int64_t)gr * ld + j0 + lane];
+            const df32 v = df_add({s.x, s.y}, acc[r]);
+            A[(int64_t)gr * ld + j0 + lane] = make_float2(v.h, v.l);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // 2. diagonal block in FP64 (warp 0, lane = row), then its inverse (lane = column)
+    if (warp == 0) {
+      for (int r = 0; r < 32; ++r) {
+        double v = (r == lane) ? 1.0 : 0.0;
+        if (r < jb && lane < jb && lane <= r) {
+          const float2 s = A[(int64_t)(j0 + r) * ld + j0 + lane];
+          v = df_to_double({s.x, s.y});
+        }
+        diag[r][lane] = v;
+      }
+      __syncwarp();
+      for (int k = 0; k < 32; ++k) {
+        if (lane == k) {
+          double d = diag[k][k];
+          if (!(d > 0.0)) { s_bad = 1; d = 1.0; }
+          const double s = sqrt(d);
+          diag[k][k] = s;
+          rdiag[k] = 1.0 / s;
+        }
+        __syncwarp();
+        if (lane > k) diag[lane][k] *= rdiag[k];
+        __syncwarp();
+        if (lane > k) {
+          const double lk = diag[lane][k];
+          for (int j = k + 1; j <= lane; ++j) diag[lane][j] -= lk * diag[j][k];
+        }
+        __syncwarp();
+      }
+      // column `lane` of L_jj^-1 by forward substitution (zero above the diagonal)
+      for (int r = 0; r < 32; ++r) {
+        double v = (r == lane) ? 1.0 : 0.0;
+        if (r > lane)
+          for (int q = lane; q < r; ++q) v = fma(-diag[r][q], dinv[q][lane], v);
+        dinv[r][lane] = (r >= lane) ? v * rdiag[r] : 0.0;
+      }
+      for (int r = 0; r < jb; ++r)
+        if (lane <= r) {
+          const df32 v = df_from_double(diag[r][lane]);
+          A[(int64_t)(j0 + r) * ld + j0 + lane] = make_float2(v.h, v.l);
+        }
+      __syncwarp();
+      for (int k = 0; k < 32; ++k) binv[k][lane] = df_from_double(dinv[lane][k]);
+    }
+    __syncthreads();
+    // 3. rows below the diagonal block: L[r, panel] = R[r, panel] L_jj^-T
+    for (int r0 = j0 + jb + warp * 32; r0 < n; r0 += NW * 32) {
+      df32 acc[32];
+#pragma unroll
+      for (int r = 0; r < 32; ++r) acc[r] = {0.f, 0.f};
+      for (int r = 0; r < 32; ++r) {
+        const int gr = r0 + r;
+        if (gr < n && lane < jb) cp_async8(&ch.a[r][lane], A + (int64_t)gr * ld + j0 + lane);
+        else ch.a[r][lane] = {0.f, 0.f};
+      }
+      cp_async_wait_all();
+      __syncwarp();
+#pragma unroll 2
+      for (int k = 0; k < 32; ++k) {
+        const df32 bv = binv[k][lane];
+#pragma unroll
+        for (int r = 0; r < 32; ++r) df_fma(acc[r], ch.a[r][k], bv);
+      }
+      if (lane < jb)
+        for (int r = 0; r < 32; ++r) {
+          const int gr = r0 + r;
+          if (gr < n) {
+            const df32 v = df_norm(acc[r]);
+            A[(int64_t)gr * ld + j0 + lane] = make_float2(v.h, v.l);
+          }
+        }
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+  // 4. back to FP64 (lower triangle), and the FP32 copy of the factor
+  for (int r = warp; r < n; r += NW)
+    for (int c = lane; c <= r; c += 32) {
+      const float2 s = A[(int64_t)r * ld + c];
+      A[(int64_t)r * ld + c] = df_to_bits({s.x, s.y});
+    }
+  if (l32) {
+    float* Lf = l32 + bd.off_mat;
+    for (int r = warp; r < ld; r += NW)
+      for (int c = lane; c < ld; c += 32) {
+        float v = 0.f;
+        if (r < n && c <= r) {
+          const float2 s = A[(int64_t)r * ld + c];
+          v = (float)__hiloint2double(__float_as_int(s.y), __float_as_int(s.x));
+        }
+        Lf[(int64_t)r * ld + c] = v;
+      }
+  }
+  if (threadIdx.x == 0 && s_bad) set_error(flags, NOLSM_ENOTPD);
+}
+
 // Inverse of the lower-triangular L into X (out of place), by block rows of 32:
 //   X[i-block, c-block] = -L_ii^-1 sum_{k=c}^{i-1} L_ik X_kc   (c < i),   X_ii = L_ii^-1.
 // Phase 1 forms R = sum_k L_ik X_kc with warp tiles (one 32x32 tile per c-block), phase 2
@@ -356,7 +600,10 @@ cudaError_t launch_gather(nolsm_ctx* ctx, float* hb, double* sb) {
 cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode) {
   // sb holds T_b(S) in FP64 (first sum_sq doubles); the second half is scratch.
   float* s32 = reinterpret_cast<float*>(sb + ctx->sum_sq);   // FP32 factor lives in the scratch half
-  if (mode == NOLSM_CHOL_FP64_INV64) {
+  if (mode == NOLSM_CHOL_DF64) {
+    cholesky_df_kernel<4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, ctx->d_flags);
+    trinv_kernel<float, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
+  } else if (mode == NOLSM_CHOL_FP64_INV64) {
     cholesky_kernel<double, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, sb, nullptr, ctx->d_flags);
     trinv_kernel<double, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, sb, sb + ctx->sum_sq);
     to_f32_kernel<double><<<sq_grid(ctx->n_blocks), 256, 0, ctx->stream>>>(ctx->d_blocks, sb + ctx->sum_sq, ctx->d_linv, 1);

@@ -6,6 +6,8 @@
 // and share the control kernels below.
 #include "internal.h"
 
+#include <cooperative_groups.h>
+
 #include <cfloat>
 #include <type_traits>
 
@@ -38,10 +40,14 @@ __device__ __forceinline__ float cc_next(float l, float a) {
 // MODE 0: plain store.  MODE 1: NS first product T = X X^T (X symmetric), epilogue writes
 //   B = 1.5 a I - 0.5 a^3 T and accumulates ||T - I||_F^2 per block.  MODE 2: X+ = X B^T.
 // MODE 3: plain store of a product known to be symmetric (upper tiles, mirrored).
+// TWO: two-level summation for the FP32 path -- each BK-wide slice of k is summed into fresh
+// registers and then added to the running sum, so a length-n dot product carries about
+// (BK + n / BK) roundings instead of n (one extra add per slice; twice the accumulator registers,
+// one CTA per SM).
 constexpr int BM = 128, BN = 128, BK = 16;
 
-template <int MODE>
-__global__ void __launch_bounds__(256, 2)
+template <int MODE, bool TWO>
+__global__ void __launch_bounds__(256, TWO ? 1 : 2)
 sgemm_nt_kernel(const Tile* __restrict__ tiles, const int32_t* __restrict__ n_tiles_dev, int n_tiles_host,
                 const BlockDesc* __restrict__ blocks, const float* __restrict__ a_pool, const float* __restrict__ b_pool,
                 float* __restrict__ c_pool, float* __restrict__ x0, float* __restrict__ x1, float* __restrict__ bbuf,
@@ -96,6 +102,14 @@ sgemm_nt_kernel(const Tile* __restrict__ tiles, const int32_t* __restrict__ n_ti
         rb1 = *reinterpret_cast<const float4*>(Bg + half + k0 + BK);
       }
 #pragma unroll
+      float part[TWO ? 8 : 1][TWO ? 8 : 1];
+      if constexpr (TWO) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) part[i][j] = 0.f;
+      }
+#pragma unroll
       for (int k = 0; k < BK; ++k) {
         const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 4]);
         const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][k][64 + ty * 4]);
@@ -106,7 +120,16 @@ sgemm_nt_kernel(const Tile* __restrict__ tiles, const int32_t* __restrict__ n_ti
 #pragma unroll
         for (int i = 0; i < 8; ++i)
 #pragma unroll
-          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+          for (int j = 0; j < 8; ++j) {
+            if constexpr (TWO) part[i][j] = fmaf(av[i], bv[j], part[i][j]);
+            else acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+          }
+      }
+      if constexpr (TWO) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] += part[i][j];
       }
       buf ^= 1;
     }
@@ -398,9 +421,18 @@ __device__ void slab_product(const T* __restrict__ X, int ld, int c, const float
     for (int c0 = 0; c0 < c; c0 += 8) {
       AccSel<COMP> acc[4];
       for (int k0 = 0; k0 < ld; k0 += 32) {
-        for (int e = tid; e < 128 * 32; e += blockDim.x) {
-          const int rr = e >> 5, kk = e & 31;
-          Xs[rr][kk] = ld_as_float<T>(X + (int64_t)(r0 + rr) * ld + k0 + kk);
+        {   // 16 independent loads per thread in flight (blockDim.x == 256)
+          float xv[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int e = tid + j * 256;
+            xv[j] = ld_as_float<T>(X + (int64_t)(r0 + (e >> 5)) * ld + k0 + (e & 31));
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int e = tid + j * 256;
+            Xs[e >> 5][e & 31] = xv[j];
+          }
         }
         {
           const int kk = tid >> 3, cc = tid & 7;   // 256 threads = 32 x 8
@@ -438,19 +470,275 @@ __device__ void slab_f(const T* X, int ld, int c, const float* V, float* out, fl
   slab_axpby(1.5f, t1, -0.5f, t3, out, (int64_t)ld * c);
 }
 
+// ---- Own-column slab with X resident in shared memory: one cluster of kSlabCluster CTAs per
+// block.  CTA q holds rows [qR, qR + R) of X (R = n_pad / kSlabCluster, a contiguous range of the
+// row-major block, copied once with cp.async).  Every product X V (V: n_pad x 8, all columns of a
+// group of up to 8 own columns) is computed slice by slice; each CTA writes its rows of the result
+// into every CTA's copy of the next V through distributed shared memory, and a cluster barrier
+// separates the products.  X is read from HBM once per evaluation instead of once per product.
+// Within a CTA, thread (rp, ks) = (tid / 8, tid % 8) forms the row pair 2rp, 2rp + 1 over the
+// 16-byte k-chunks ks, ks + 8, ...; a butterfly over the 8 lanes of a group leaves the sums in all
+// of them, and lane ks then writes the rows to cluster rank ks.
+constexpr int kSlabCluster = 8;
+constexpr size_t kSmemOptin = 227 * 1024;
+
+template <typename T>
+__host__ __device__ inline size_t slab_cluster_smem(int n_pad) {
+  const size_t R = (size_t)n_pad / kSlabCluster, ck = 16 / sizeof(T);
+  return R * n_pad * sizeof(T)                          // this CTA's rows of X
+         + 2 * ((size_t)n_pad / ck) * (ck * 8 + 4) * 4  // two full slabs of 8 columns (padded chunks)
+         + 4 * R * 8 * 4;                               // local rows: W, t1, t3 / F, F1
+}
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <typename T> __device__ __forceinline__ void ld_chunk(const T* p, float* out);
+template <> __device__ __forceinline__ void ld_chunk<float>(const float* p, float* out) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+}
+template <> __device__ __forceinline__ void ld_chunk<__half>(const __half* p, float* out) {
+  const uint4 v = *reinterpret_cast<const uint4*>(p);
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[i]));
+    out[2 * i] = f.x; out[2 * i + 1] = f.y;
+  }
+}
+template <> __device__ __forceinline__ void ld_chunk<__nv_bfloat16>(const __nv_bfloat16* p, float* out) {
+  const uint4 v = *reinterpret_cast<const uint4*>(p);
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[i]));
+    out[2 * i] = f.x; out[2 * i + 1] = f.y;
+  }
+}
+
+// Rows 2 rpi, 2 rpi + 1 of Xs V (8 columns), reduced over the 8 k-slices of the lane group.
+template <typename T>
+__device__ __forceinline__ void slab_rowpair(const T* __restrict__ Xs, int ld, const float* __restrict__ V, int rpi,
+                                             int ks, float (&out)[2][8]) {
+  constexpr bool COMP = std::is_same<T, float>::value;
+  constexpr int CK = 16 / (int)sizeof(T);
+  constexpr int VS = CK * 8 + 4;
+  AccSel<COMP> acc[2][8];
+  const T* x0 = Xs + (size_t)(2 * rpi) * ld;
+  const T* x1 = x0 + ld;
+  const int nch = ld / CK;
+  for (int g = ks; g < nch; g += 8) {
+    float a0[CK], a1[CK];
+    ld_chunk<T>(x0 + g * CK, a0);
+    ld_chunk<T>(x1 + g * CK, a1);
+    const float* v = V + g * VS;
+#pragma unroll
+    for (int kk = 0; kk < CK; ++kk) {
+      const float4 va = *reinterpret_cast<const float4*>(v + kk * 8);
+      const float4 vb = *reinterpret_cast<const float4*>(v + kk * 8 + 4);
+      const float vv[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
+#pragma unroll
+      for (int cc = 0; cc < 8; ++cc) {
+        acc[0][cc].add_prod(a0[kk], vv[cc]);
+        acc[1][cc].add_prod(a1[kk], vv[cc]);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) {
+      if constexpr (COMP) {
+        // compensated butterfly: TwoSum of the leading parts, the errors summed on the side
+        float s = acc[i][cc].s, e = acc[i][cc].e;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+          const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+          const float e2 = __shfl_xor_sync(0xffffffffu, e, o);
+          const float t = s + s2;
+          const float z = t - s;
+          const float err = (s - (t - z)) + (s2 - z);
+          s = t;
+          e = (e + e2) + err;
+        }
+        out[i][cc] = s + e;
+      } else {
+        float s = acc[i][cc].s;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        out[i][cc] = s;
+      }
+    }
+}
+
+template <typename T>
+__global__ void __cluster_dims__(kSlabCluster, 1, 1) __launch_bounds__(256)
+    slab_cluster_kernel(const BlockDesc* __restrict__ blocks, const NsState* __restrict__ st, const T* __restrict__ x0,
+                        const T* __restrict__ x1, const float* __restrict__ w, const float* __restrict__ z,
+                        const float* __restrict__ lc, float* __restrict__ y, int refine, size_t cluster_cap,
+                        double* __restrict__ bn, double* __restrict__ be) {
+  namespace cg = cooperative_groups;
+  constexpr int CK = 16 / (int)sizeof(T);
+  constexpr int VS = CK * 8 + 4;
+  extern __shared__ __align__(16) uint8_t slab_smem[];
+  __shared__ double wred[8][2];
+  __shared__ double cred[kSlabCluster][2];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int b = blockIdx.x / kSlabCluster;
+  const int q = (int)cluster.block_rank();
+  const BlockDesc bd = blocks[b];
+  const int ld = bd.n_pad;
+  if (slab_cluster_smem<T>(ld) > cluster_cap) return;   // the whole cluster: handled by slab_traces_kernel
+  const int R = ld / kSlabCluster;
+  const int tid = threadIdx.x, ks = tid & 7, rp = tid >> 3;
+  T* Xs = reinterpret_cast<T*>(slab_smem);
+  const int vlen = (ld / CK) * VS;
+  float* const Vb0 = reinterpret_cast<float*>(slab_smem + (size_t)R * ld * sizeof(T));
+  auto vb = [&](int i) { return Vb0 + i * vlen; };
+  float* Wl = Vb0 + 2 * vlen;
+  float* T1 = Wl + R * 8;
+  float* T3 = T1 + R * 8;
+  float* F1 = T3 + R * 8;
+
+  const NsState s = st[b];
+  {
+    const T* X = (s.cur ? x1 : x0) + bd.off_mat + (int64_t)q * R * ld;
+    const int nvec = (int)((size_t)R * ld * sizeof(T) / 16);
+    for (int i = tid; i < nvec; i += blockDim.x)
+      cp_async16(reinterpret_cast<uint8_t*>(Xs) + (size_t)i * 16, reinterpret_cast<const uint8_t*>(X) + (size_t)i * 16);
+  }
+  auto vpos = [&](int k) { return (k / CK) * VS + (k % CK) * 8; };
+  // rows of X_q Vin -> local rows (Lout) and/or every rank's copy of Vout
+  auto product = [&](const float* Vin, float* Lout, float* Vout) {
+    for (int rpi = rp; rpi < R / 2; rpi += 32) {
+      float o[2][8];
+      slab_rowpair<T>(Xs, ld, Vin, rpi, ks, o);
+      if (Lout && ks == 0) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          float4* d = reinterpret_cast<float4*>(Lout + (2 * rpi + i) * 8);
+          d[0] = make_float4(o[i][0], o[i][1], o[i][2], o[i][3]);
+          d[1] = make_float4(o[i][4], o[i][5], o[i][6], o[i][7]);
+        }
+      }
+      if (Vout) {
+        float* dst = cluster.map_shared_rank(Vout, (unsigned)ks);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          float4* d = reinterpret_cast<float4*>(dst + vpos(q * R + 2 * rpi + i));
+          d[0] = make_float4(o[i][0], o[i][1], o[i][2], o[i][3]);
+          d[1] = make_float4(o[i][4], o[i][5], o[i][6], o[i][7]);
+        }
+      }
+    }
+  };
+  // local rows (R x 8) -> every rank's copy of Vout
+  auto broadcast_rows = [&](const float* Lsrc, float* Vout) {
+    for (int e = tid; e < R * 8 * kSlabCluster; e += blockDim.x) {
+      const int rank = e / (R * 8), le = e % (R * 8);
+      float* dst = cluster.map_shared_rank(Vout, (unsigned)rank);
+      dst[vpos(q * R + (le >> 3)) + (le & 7)] = Lsrc[le];
+    }
+  };
+  cp_async_wait_all();
+  __syncthreads();
+
+  double sn = 0.0, se = 0.0;
+  for (int c0 = 0; c0 < bd.c; c0 += 8) {
+    const int cw = min(8, bd.c - c0);
+    for (int e = tid; e < R * 8; e += blockDim.x) {
+      const int cc = e & 7;
+      Wl[e] = (cc < cw) ? w[bd.off_slab + (int64_t)(c0 + cc) * ld + q * R + (e >> 3)] : 0.f;
+    }
+    __syncthreads();
+    broadcast_rows(Wl, vb(0));
+    cluster.sync();
+    const float* G;
+    if (refine <= 0) {
+      product(vb(0), T1, nullptr);
+      __syncthreads();
+      G = T1;
+    } else {
+      // f(X) V = 1.5 X V - 0.5 X (X (X V)); refine >= 2 evaluates g = f o f as 1.5 F1 - 0.5 F3
+      // with F1 = f(X) W, F2 = f(X) F1, F3 = f(X) F2
+      const int nf = refine >= 2 ? 3 : 1;
+      int cur = 0;
+      for (int f = 0; f < nf; ++f) {
+        product(vb(cur), T1, vb(cur ^ 1));
+        cluster.sync();
+        product(vb(cur ^ 1), nullptr, vb(cur));
+        cluster.sync();
+        product(vb(cur), T3, nullptr);
+        __syncthreads();
+        for (int e = tid; e < R * 8; e += blockDim.x) {
+          const float v = 1.5f * T1[e] + -0.5f * T3[e];
+          T3[e] = v;
+          if (f == 0) F1[e] = v;
+        }
+        __syncthreads();
+        if (f + 1 < nf) {
+          broadcast_rows(T3, vb(cur ^ 1));
+          cluster.sync();
+          cur ^= 1;
+        }
+      }
+      if (nf > 1) {
+        for (int e = tid; e < R * 8; e += blockDim.x) T3[e] = 1.5f * F1[e] + -0.5f * T3[e];
+        __syncthreads();
+      }
+      G = T3;
+    }
+    for (int e = tid; e < R * 8; e += blockDim.x) {
+      const int cc = e & 7;
+      if (cc >= cw) continue;
+      const int64_t o = bd.off_slab + (int64_t)(c0 + cc) * ld + q * R + (e >> 3);
+      const float yv = 0.5f * (Wl[e] - G[e]);
+      y[o] = yv;
+      sn += (double)lc[o] * (double)yv;
+      se += (double)z[o] * (double)yv;
+    }
+    cluster.sync();   // every rank is done with both slab copies before the next group overwrites them
+  }
+  for (int o = 16; o; o >>= 1) {
+    sn += __shfl_xor_sync(0xffffffffu, sn, o);
+    se += __shfl_xor_sync(0xffffffffu, se, o);
+  }
+  if ((tid & 31) == 0) { wred[tid >> 5][0] = sn; wred[tid >> 5][1] = se; }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, c2 = 0.0;
+    for (int i = 0; i < 8; ++i) { a += wred[i][0]; c2 += wred[i][1]; }
+    double* dst = cluster.map_shared_rank(&cred[0][0], 0u);
+    dst[2 * q] = a;
+    dst[2 * q + 1] = c2;
+  }
+  cluster.sync();
+  if (q == 0 && tid == 0) {
+    double a = 0.0, c2 = 0.0;
+    for (int i = 0; i < kSlabCluster; ++i) { a += cred[i][0]; c2 += cred[i][1]; }
+    bn[b] = a;
+    be[b] = c2;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) slab_traces_kernel(const BlockDesc* __restrict__ blocks,
                                                           const NsState* __restrict__ st, const T* __restrict__ x0,
                                                           const T* __restrict__ x1, const float* __restrict__ w,
                                                           const float* __restrict__ z, const float* __restrict__ lc,
                                                           float* __restrict__ y, float* __restrict__ tmp,
-                                                          int64_t slab_total, int refine, double* __restrict__ bn,
-                                                          double* __restrict__ be) {
+                                                          int64_t slab_total, int refine, size_t cluster_cap,
+                                                          double* __restrict__ bn, double* __restrict__ be) {
   __shared__ float Xs[128][33];
   __shared__ float Vs[32][8];
   __shared__ double red[2][8];
   const BlockDesc bd = blocks[blockIdx.x];
   const int ld = bd.n_pad, c = bd.c;
+  if (slab_cluster_smem<T>(ld) <= cluster_cap) return;   // resident in a cluster (slab_cluster_kernel)
   const NsState s = st[blockIdx.x];
   const T* X = (s.cur ? x1 : x0) + bd.off_mat;
   const int64_t len = (int64_t)ld * c;
@@ -640,13 +928,20 @@ cudaError_t launch_sgemm_nt(nolsm_ctx* ctx, const float* a, const float* b, floa
   if (e != cudaSuccess) return e;
   e = cudaStreamSynchronize(ctx->stream);   // tl is a host temporary
   if (e != cudaSuccess) return e;
-  const int grid = ctx->num_sms * 2;
-  if (sym)
-    sgemm_nt_kernel<3><<<grid, 256, 0, ctx->stream>>>(ctx->d_tiles, nullptr, (int)tl.size(), ctx->d_blocks, a, b, c,
-                                                      nullptr, nullptr, nullptr, nullptr, nullptr);
+  const bool two = ctx->opt.precision == NOLSM_PREC_FP32;
+  const int grid = ctx->num_sms * (two ? 1 : 2);   // persistent: one wave of resident CTAs
+  if (sym && two)
+    sgemm_nt_kernel<3, true><<<grid, 256, 0, ctx->stream>>>(ctx->d_tiles, nullptr, (int)tl.size(), ctx->d_blocks, a,
+                                                            b, c, nullptr, nullptr, nullptr, nullptr, nullptr);
+  else if (sym)
+    sgemm_nt_kernel<3, false><<<grid, 256, 0, ctx->stream>>>(ctx->d_tiles, nullptr, (int)tl.size(), ctx->d_blocks, a,
+                                                             b, c, nullptr, nullptr, nullptr, nullptr, nullptr);
+  else if (two)
+    sgemm_nt_kernel<0, true><<<grid, 256, 0, ctx->stream>>>(ctx->d_tiles, nullptr, (int)tl.size(), ctx->d_blocks, a,
+                                                            b, c, nullptr, nullptr, nullptr, nullptr, nullptr);
   else
-    sgemm_nt_kernel<0><<<grid, 256, 0, ctx->stream>>>(ctx->d_tiles, nullptr, (int)tl.size(), ctx->d_blocks, a, b, c,
-                                                      nullptr, nullptr, nullptr, nullptr, nullptr);
+    sgemm_nt_kernel<0, false><<<grid, 256, 0, ctx->stream>>>(ctx->d_tiles, nullptr, (int)tl.size(), ctx->d_blocks, a,
+                                                             b, c, nullptr, nullptr, nullptr, nullptr, nullptr);
   return cudaGetLastError();
 }
 
@@ -708,33 +1003,54 @@ cudaError_t launch_ns_advance(nolsm_ctx* ctx) {
 }
 
 cudaError_t launch_gemm_f32(nolsm_ctx* ctx, int phase) {
-  const int grid = ctx->num_sms * 2;
+  const int grid = ctx->num_sms;   // one resident CTA per SM (two-level summation)
   const int32_t* nt = &ctx->d_flags->n_tiles;
   if (phase == 1)
-    sgemm_nt_kernel<1><<<grid, 256, 0, ctx->stream>>>(ctx->d_tiles, nt, 0, ctx->d_blocks, nullptr, nullptr, nullptr,
+    sgemm_nt_kernel<1, true><<<grid, 256, 0, ctx->stream>>>(ctx->d_tiles, nt, 0, ctx->d_blocks, nullptr, nullptr, nullptr,
                                                       (float*)ctx->d_x[0], (float*)ctx->d_x[1], (float*)ctx->d_b,
                                                       ctx->d_state, ctx->d_resacc);
   else
-    sgemm_nt_kernel<2><<<grid, 256, 0, ctx->stream>>>(ctx->d_tiles, nt, 0, ctx->d_blocks, nullptr, nullptr, nullptr,
+    sgemm_nt_kernel<2, true><<<grid, 256, 0, ctx->stream>>>(ctx->d_tiles, nt, 0, ctx->d_blocks, nullptr, nullptr, nullptr,
                                                       (float*)ctx->d_x[0], (float*)ctx->d_x[1], (float*)ctx->d_b,
                                                       ctx->d_state, ctx->d_resacc);
   return cudaGetLastError();
 }
 
-cudaError_t launch_slab_traces(nolsm_ctx* ctx, int half) {
+namespace {
+template <typename T>
+cudaError_t slab_launch(nolsm_ctx* ctx) {
   const int r = ctx->opt.refine_iters;
-  if (half == 0)
-    slab_traces_kernel<float><<<ctx->n_blocks, 256, 0, ctx->stream>>>(
-        ctx->d_blocks, ctx->d_state, (const float*)ctx->d_x[0], (const float*)ctx->d_x[1], ctx->d_w, ctx->d_z, ctx->d_lc,
-        ctx->d_y, ctx->d_tmp, ctx->sum_slab, r, ctx->d_bn, ctx->d_be);
-  else if (half == 1)
-    slab_traces_kernel<__half><<<ctx->n_blocks, 256, 0, ctx->stream>>>(
-        ctx->d_blocks, ctx->d_state, (const __half*)ctx->d_x[0], (const __half*)ctx->d_x[1], ctx->d_w, ctx->d_z,
-        ctx->d_lc, ctx->d_y, ctx->d_tmp, ctx->sum_slab, r, ctx->d_bn, ctx->d_be);
-  else
-    slab_traces_kernel<__nv_bfloat16><<<ctx->n_blocks, 256, 0, ctx->stream>>>(
-        ctx->d_blocks, ctx->d_state, (const __nv_bfloat16*)ctx->d_x[0], (const __nv_bfloat16*)ctx->d_x[1], ctx->d_w,
-        ctx->d_z, ctx->d_lc, ctx->d_y, ctx->d_tmp, ctx->sum_slab, r, ctx->d_bn, ctx->d_be);
+  // dynamic shared memory of the cluster kernel: the largest resident block that fits
+  size_t cap = 0;
+  bool any_big = false;
+  for (const BlockDesc& bd : ctx->h_blocks) {
+    const size_t need = slab_cluster_smem<T>(bd.n_pad);
+    if (need <= kSmemOptin) cap = std::max(cap, need);
+    else any_big = true;
+  }
+  const T* x0 = (const T*)ctx->d_x[0];
+  const T* x1 = (const T*)ctx->d_x[1];
+  if (cap > 0) {
+    cudaError_t e = cudaFuncSetAttribute(slab_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+    if (e != cudaSuccess) return e;
+    slab_cluster_kernel<T><<<ctx->n_blocks * kSlabCluster, 256, cap, ctx->stream>>>(
+        ctx->d_blocks, ctx->d_state, x0, x1, ctx->d_w, ctx->d_z, ctx->d_lc, ctx->d_y, r, cap, ctx->d_bn, ctx->d_be);
+    ctx->n_launches += 1;
+  }
+  if (any_big) {
+    slab_traces_kernel<T><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_state, x0, x1, ctx->d_w,
+                                                                 ctx->d_z, ctx->d_lc, ctx->d_y, ctx->d_tmp,
+                                                                 ctx->sum_slab, r, cap, ctx->d_bn, ctx->d_be);
+    ctx->n_launches += 1;
+  }
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_slab_traces(nolsm_ctx* ctx, int half) {
+  cudaError_t e = half == 0 ? slab_launch<float>(ctx) : half == 1 ? slab_launch<__half>(ctx)
+                                                                  : slab_launch<__nv_bfloat16>(ctx);
+  if (e != cudaSuccess) return e;
   sum_traces_kernel<<<1, 1024, 0, ctx->stream>>>(ctx->n_blocks, ctx->d_bn, ctx->d_be, ctx->d_flags);
   return cudaGetLastError();
 }

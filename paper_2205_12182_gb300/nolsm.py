@@ -20,7 +20,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOTPD", "ENOCONV", "EBRACKE
 MEM_DEVICE, MEM_HOST = 0, 1
 PREC_FP32, PREC_MIXED_FP16, PREC_MIXED_BF16 = 1, 2, 3
 BOUNDS_GERSHGORIN, BOUNDS_LANCZOS, BOUNDS_LEARNED = 0, 1, 2
-CHOL_FP64, CHOL_FP32, CHOL_FP64_INV64 = 0, 1, 2
+CHOL_FP64, CHOL_FP32, CHOL_FP64_INV64, CHOL_DF64 = 0, 1, 2, 3
 
 FUNCTIONS = ["nolsm_default_options", "nolsm_create", "nolsm_build_submatrices", "nolsm_sign_batch", "nolsm_set_mu",
              "nolsm_density", "nolsm_band_energy", "nolsm_block_info", "nolsm_block_index_set", "nolsm_block_bounds",

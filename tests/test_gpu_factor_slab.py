@@ -1,0 +1,92 @@
+"""The S factorisation modes and both own-column slab kernels against independent references.
+
+* the Cholesky factor of T_b(S) in every mode against LAPACK's FP64 factor (numpy.linalg.cholesky);
+* the double-float factor and the FP64 one give the same FP32 factor, L^-1 and A0;
+* blocks too large for the shared-memory-resident slab kernel (n_pad 640 in the FP32 path, 896 in
+  the mixed path) run through the one-CTA slab kernel and keep the parity bar; blocks of n_pad 512
+  in the FP32 path run through the resident kernel with compensated sums.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle.nolsm import NolsmOracle  # noqa: E402
+from synth import make_config, water_box  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def nl():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2205_12182_gb300 import nolsm
+    return nolsm
+
+
+@pytest.fixture(scope="module")
+def sys1():
+    return make_config(1)
+
+
+@pytest.fixture(scope="module")
+def orc1(sys1):
+    return NolsmOracle.from_system(sys1)
+
+
+@pytest.mark.parametrize("chol", [0, 1, 2, 3])
+def test_factor_matches_lapack(nl, sys1, orc1, chol):
+    lib = nl.Nolsm(precision=nl.PREC_FP32, chol_precision=chol).build(sys1)
+    for b in [0, 5, 31, 63]:
+        _, _, sb = orc1.submatrices(b)
+        ref = np.linalg.cholesky(sb)
+        got = lib.block_matrix(b, 5).astype(np.float64)
+        assert got.shape == ref.shape
+        if chol == nl.CHOL_FP32:
+            np.testing.assert_allclose(got, ref, rtol=0, atol=2e-5)
+            continue
+        # an FP64-accurate factor rounds to LAPACK's FP32 rounding, up to rounding-boundary cases
+        ref32 = ref.astype(np.float32)
+        diff = np.abs(got - ref32.astype(np.float64))
+        ulp = np.spacing(np.abs(ref32)).astype(np.float64)
+        assert np.all(diff <= ulp), (b, float((diff / np.maximum(ulp, 1e-45)).max()))
+        assert np.count_nonzero(diff) <= 1e-3 * diff.size
+
+
+def test_double_float_and_fp64_factor_agree_downstream(nl, sys1):
+    a = nl.Nolsm(precision=nl.PREC_FP32, chol_precision=nl.CHOL_FP64).build(sys1)
+    d = nl.Nolsm(precision=nl.PREC_FP32, chol_precision=nl.CHOL_DF64).build(sys1)
+    for b in [0, 17, 63]:
+        la, ld = a.block_matrix(b, 5), d.block_matrix(b, 5)
+        assert np.mean(la == ld) >= 0.999
+        np.testing.assert_allclose(ld, la, rtol=0, atol=np.spacing(np.float32(4.0)))
+        for which in (1, 0):
+            x, y = a.block_matrix(b, which), d.block_matrix(b, which)
+            np.testing.assert_allclose(y, x, rtol=0, atol=1e-5 * max(1.0, float(np.abs(x).max())))
+
+
+def _sampled_parity(nl, s, precision, n_sample, seed=0):
+    lib = nl.Nolsm(precision=precision).build(s)
+    mu, n, _ = lib.set_mu(s.n_electrons, tol_n=1e-3)
+    d = lib.density().cpu().numpy()
+    sample = np.random.default_rng(seed).choice(s.n_blocks, n_sample, replace=False)
+    o = NolsmOracle.from_system(s, blocks=sample).prepare()
+    assert min(np.min(np.abs(e - mu)) for e in o.eps) >= 1e-3
+    own = np.isin(s.col, np.concatenate([s.block_cols(int(b)) for b in sample]))
+    ref = o.density(mu)
+    return np.abs(d[own] - ref[own]).max()
+
+
+def test_fp32_path_resident_slab_n512(nl):
+    s = water_box(10, seed=7, neighbourhood=8.0)        # n_b ~470, n_pad 512
+    assert _sampled_parity(nl, s, nl.PREC_FP32, 6) <= 1e-6
+
+
+def test_fp32_path_blocks_beyond_resident_slab(nl):
+    s = water_box(6, seed=5, neighbourhood=9.0)         # n_b ~560, n_pad 640
+    assert _sampled_parity(nl, s, nl.PREC_FP32, 6) <= 1e-6
+
+
+def test_mixed_path_blocks_beyond_resident_slab(nl):
+    s = water_box(8, seed=5, neighbourhood=10.0)        # n_b ~850, n_pad 896
+    assert _sampled_parity(nl, s, nl.PREC_MIXED_FP16, 6) <= 1e-3

@@ -48,7 +48,7 @@ def test_index_sets_bit_exact(nl, sys1, orc1):
         np.testing.assert_array_equal(lib.index_set(b), orc1.idx[b])
 
 
-@pytest.mark.parametrize("chol", [0, 1, 2])
+@pytest.mark.parametrize("chol", [0, 1, 2, 3])
 def test_a0_spectrum_is_generalized_spectrum(nl, sys1, orc1, chol):
     """A0 = L^-1 T(H) L^-T is similar to T(S)^-1 T(H): its eigenvalues are the oracle's eps_b."""
     lib = make(nl, sys1, nl.PREC_FP32, chol_precision=chol)
@@ -65,7 +65,7 @@ def _dmax(nl, lib, orc, mu):
     return np.abs(d - orc.density(mu)).max(), d
 
 
-@pytest.mark.parametrize("chol", [0, 2])
+@pytest.mark.parametrize("chol", [0, 2, 3])
 def test_fp32_path_parity(nl, sys1, orc1, mu1, chol):
     lib = make(nl, sys1, nl.PREC_FP32, chol_precision=chol)
     st = lib.sign_batch(mu1)
