@@ -88,6 +88,16 @@ typedef enum nolsm_chol_precision {
                                    the trace slab), where it agrees with the FP64 factor */
 } nolsm_chol_precision;
 
+/* How the tensor-core products of the mixed-precision paths are scheduled (the FP32 path always
+ * launches one grouped product at a time). */
+typedef enum nolsm_schedule {
+  NOLSM_SCHEDULE_PERSISTENT = 0,  /* one launch per sign evaluation: 2-CTA clusters take whole blocks
+                                     off a queue and run all of a block's products with its iterates
+                                     resident in L2; convergence is decided on the device */
+  NOLSM_SCHEDULE_PER_PRODUCT = 1  /* one grouped launch per product over all active blocks, the
+                                     iteration driven from the host */
+} nolsm_schedule;
+
 /* One CSR matrix (see the conventions above). */
 typedef struct nolsm_csr {
   int64_t n;               /* dimension N */
@@ -108,12 +118,13 @@ typedef struct nolsm_options {
                               and t = 0.02, 4e-4, 0 for refine_iters >= 2, 1, 0 (the refinement steps
                               on the own columns finish the convergence) */
   int32_t max_iter;        /* matrix iterations per sign evaluation (default 100) */
-  int32_t refine_iters;    /* FP32 Newton-Schulz steps on the own-column slab (0..3, default 1) */
+  int32_t refine_iters;    /* FP32 Newton-Schulz steps on the own-column slab (0..3, default 2) */
   double spin_factor;      /* electrons per orbital: N_e = spin_factor Tr(DS), E = spin_factor Tr(DH0) (default 2) */
   double lower_bound;      /* scaled iteration: lower bound on |eig(X_0)| when bounds give none (default 1e-3) */
   double alpha_margin;     /* relative safety margin on the spectral radius bound (default 0.02) */
   int64_t wait_budget;     /* bound on every device-side spin wait, in polls (default 1<<22) */
   int32_t lanczos_steps;   /* Lanczos steps per block for NOLSM_BOUNDS_LANCZOS (default 24, at most 64) */
+  int32_t schedule;        /* nolsm_schedule of the mixed-precision products (default PERSISTENT) */
 } nolsm_options;
 
 /* Statistics of the last sign evaluation. */

@@ -27,6 +27,14 @@ nolsm_status cuda_fail(nolsm_ctx* ctx, cudaError_t e, const char* what) {
   return fail(ctx, e == cudaErrorMemoryAllocation ? NOLSM_ENOMEM : NOLSM_ECUDA, m);
 }
 
+double unit_roundoff(const nolsm_ctx* ctx) {
+  switch (ctx->opt.precision) {
+    case NOLSM_PREC_MIXED_FP16: return std::ldexp(1.0, -11);
+    case NOLSM_PREC_MIXED_BF16: return std::ldexp(1.0, -8);
+    default: return std::ldexp(1.0, -24);
+  }
+}
+
 }  // namespace nolsm
 
 #define CK(call)                                                  \
@@ -114,13 +122,6 @@ int half_kind(const nolsm_ctx* ctx) {
   return 0;
 }
 
-double unit_roundoff(const nolsm_ctx* ctx) {
-  switch (ctx->opt.precision) {
-    case NOLSM_PREC_MIXED_FP16: return std::ldexp(1.0, -11);
-    case NOLSM_PREC_MIXED_BF16: return std::ldexp(1.0, -8);
-    default: return std::ldexp(1.0, -24);
-  }
-}
 
 nolsm_status check_device_flags(nolsm_ctx* ctx) {
   CK(cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(DevFlags), cudaMemcpyDeviceToHost, ctx->stream));
@@ -176,6 +177,7 @@ nolsm_status nolsm_default_options(nolsm_options* opt) {
   opt->alpha_margin = 0.02;
   opt->wait_budget = 1LL << 22;
   opt->lanczos_steps = 24;
+  opt->schedule = NOLSM_SCHEDULE_PERSISTENT;
   return NOLSM_OK;
 }
 
@@ -189,7 +191,8 @@ nolsm_status nolsm_create(nolsm_ctx** out, const nolsm_options* opt, void* cuda_
       ctx->opt.refine_iters < 0 || ctx->opt.refine_iters > 3 || !(ctx->opt.spin_factor > 0) ||
       ctx->opt.wait_budget <= 0 || ctx->opt.alpha_margin < 0 || ctx->opt.chol_precision < 0 ||
       ctx->opt.chol_precision > NOLSM_CHOL_DF64 || ctx->opt.bounds < NOLSM_BOUNDS_GERSHGORIN ||
-      ctx->opt.bounds > NOLSM_BOUNDS_LEARNED || ctx->opt.lanczos_steps < 1 || ctx->opt.lanczos_steps > 64) {
+      ctx->opt.bounds > NOLSM_BOUNDS_LEARNED || ctx->opt.lanczos_steps < 1 || ctx->opt.lanczos_steps > 64 ||
+      ctx->opt.schedule < NOLSM_SCHEDULE_PERSISTENT || ctx->opt.schedule > NOLSM_SCHEDULE_PER_PRODUCT) {
     delete ctx;
     return NOLSM_EINVAL;
   }
@@ -439,7 +442,8 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
 namespace {
 
 // Event pair around one matrix-product launch (recorded on the context stream).
-cudaError_t gemm_timed(nolsm_ctx* ctx, bool mixed, int phase) {
+// phase 1 / 2: one grouped product; phase 0: the persistent kernel (mixed paths only).
+cudaError_t gemm_timed(nolsm_ctx* ctx, bool mixed, int phase, double mu) {
   const int k = ctx->gemm_ev_used;
   if ((int)ctx->gemm_ev.size() < 2 * (k + 1)) {
     cudaEvent_t a, b;
@@ -452,7 +456,7 @@ cudaError_t gemm_timed(nolsm_ctx* ctx, bool mixed, int phase) {
   }
   cudaError_t e = cudaEventRecord(ctx->gemm_ev[2 * k], ctx->stream);
   if (e != cudaSuccess) return e;
-  e = mixed ? launch_gemm_tc(ctx, phase) : launch_gemm_f32(ctx, phase);
+  e = phase == 0 ? launch_ns_pair(ctx, mu) : mixed ? launch_gemm_tc(ctx, phase) : launch_gemm_f32(ctx, phase);
   if (e != cudaSuccess) return e;
   ctx->gemm_ev_used = k + 1;
   ctx->n_launches += 1;
@@ -490,17 +494,19 @@ nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out) 
     ctx->n_launches += 2;
     pred = ctx->d_pred;
   }
-  CK(launch_ns_init(ctx, mu, hk, mode, mode == NOLSM_BOUNDS_LANCZOS ? ctx->d_lz : nullptr, pred));
-  ctx->n_launches += 2;
+  const bool persistent = mixed && ctx->opt.schedule == NOLSM_SCHEDULE_PERSISTENT;
+  CK(launch_ns_init(ctx, mu, hk, mode, mode == NOLSM_BOUNDS_LANCZOS ? ctx->d_lz : nullptr, pred, !persistent));
+  ctx->n_launches += persistent ? 1 : 2;
   const int tile_n = mixed ? tc_tile_n() : kTile;
   const int check_every = 4;
   ctx->gemm_ev_used = 0;
-  for (int it = 0; it <= ctx->opt.max_iter; ++it) {
+  if (persistent) CK(gemm_timed(ctx, mixed, 0, mu));   // the whole iteration of every block
+  for (int it = 0; !persistent && it <= ctx->opt.max_iter; ++it) {
     CK(launch_ns_tiles_n(ctx, tile_n));
-    CK(gemm_timed(ctx, mixed, 1));
+    CK(gemm_timed(ctx, mixed, 1, mu));
     CK(launch_ns_check_impl(ctx, ctx->d_tol, mode != NOLSM_BOUNDS_GERSHGORIN));
     CK(launch_ns_tiles_n(ctx, tile_n));
-    CK(gemm_timed(ctx, mixed, 2));
+    CK(gemm_timed(ctx, mixed, 2, mu));
     CK(launch_ns_advance(ctx));
     ctx->n_launches += 4;
     if (mode != NOLSM_BOUNDS_GERSHGORIN) {

@@ -249,84 +249,118 @@ __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-struct WarpChunkDF {
-  df32 a[32][33];
-  df32 b[32][33];
-};
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Cholesky S = L L^T in double-float, left-looking by 32-column panels, in place over the FP64
-// pool (a pair occupies the 8 bytes of the double it replaces).  One CTA of NW warps per block.
+// pool (a pair occupies the 8 bytes of the double it replaces).  One CTA of 4 warps per block;
+// every 32-row tile is shared by the 4 warps, each taking 8 of every 32 k (no idle warps when a
+// panel has few tiles), the four partial tiles summed in shared memory.
 //   0. the lower triangle of S is converted from FP64 to pairs;
 //   for each panel j0:
-//   1. R[r, panel] = S[r, panel] - L[r, 0:j0] L[panel, 0:j0]^T for rows r >= j0 (warp tiles, pairs;
-//      both operands copied to the warp's shared chunk with cp.async, row-major);
+//   1. R[r, panel] = S[r, panel] - L[r, 0:j0] L[panel, 0:j0]^T for rows r >= j0: 32 x 32 operand
+//      chunks double-buffered in shared memory with cp.async;
 //   2. warp 0 factors the 32x32 diagonal block of R in FP64 and inverts it (FP64), keeping
-//      L_jj^-T as pairs; its scratch is warp 0's own chunk (idle in this phase);
-//   3. L[r, panel] = R[r, panel] L_jj^-T for the rows below, as another warp-tile product.
+//      L_jj^-T as pairs;
+//   3. L[r, panel] = R[r, panel] L_jj^-T for the rows below (same split over k).
 //   4. finally the lower triangle is converted back to FP64; with l32 given, its FP32 rounding
 //      is also written there (zero above the diagonal and on the padding).
 // The diagonal blocks are O(n 32^2) of the O(n^3/6) work, so FP64 there costs little.
-template <int NW>
-__global__ void __launch_bounds__(NW * 32, 3) cholesky_df_kernel(const BlockDesc* __restrict__ blocks,
-                                                                 double* __restrict__ pool, float* __restrict__ l32,
-                                                                 DevFlags* flags) {
-  __shared__ WarpChunkDF chunks[NW];
+constexpr int kCholWarps = 4;
+
+__global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const BlockDesc* __restrict__ blocks,
+                                                                         double* __restrict__ pool,
+                                                                         float* __restrict__ l32, DevFlags* flags) {
+  __shared__ df32 As[2][32][32];          // read as broadcasts: no padding
+  __shared__ df32 Bs[2][32][33];          // read by rows (lane = row): padded
+  __shared__ df32 red[kCholWarps][32][32];
+  __shared__ df32 binv[32][32];
   __shared__ double rdiag[32];
   __shared__ int s_bad;
   const BlockDesc bd = blocks[blockIdx.x];
   const int n = bd.n, ld = bd.n_pad;
   float2* A = reinterpret_cast<float2*>(pool + bd.off_mat);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  WarpChunkDF& ch = chunks[warp];
-  // phase-2 scratch in warp 0's chunk: diag (FP64) over b, its inverse (FP64) over a, then
-  // binv[k][c] = (L_jj^-T)[k][c] as pairs over b (read by every warp in phase 3)
-  double(*diag)[33] = reinterpret_cast<double(*)[33]>(&chunks[0].b[0][0]);
-  double(*dinv)[33] = reinterpret_cast<double(*)[33]>(&chunks[0].a[0][0]);
-  df32(*binv)[33] = chunks[0].b;
-  if (threadIdx.x == 0) s_bad = 0;
-  for (int r = warp; r < n; r += NW)
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // phase-2 scratch over the reduction buffers (idle then)
+  double(*diag)[33] = reinterpret_cast<double(*)[33]>(&red[0][0][0]);
+  double(*dinv)[33] = reinterpret_cast<double(*)[33]>(&red[0][0][0] + 32 * 33);
+  if (tid == 0) s_bad = 0;
+  for (int r = warp; r < n; r += kCholWarps)
     for (int c = lane; c <= r; c += 32) {
       const df32 v = df_from_bits(A[(int64_t)r * ld + c]);
       A[(int64_t)r * ld + c] = make_float2(v.h, v.l);
     }
   __syncthreads();
-  for (int j0 = 0; j0 < n; j0 += 32) {
-    const int jb = min(32, n - j0);
-    // 1. panel update, one 32-row tile per warp at a time
-    for (int r0 = j0 + warp * 32; r0 < n; r0 += NW * 32) {
-      df32 acc[32];
+  // rows [row0, row0 + 32) x columns [col0, col0 + 32) of the pair matrix into a 32x32 chunk
+  auto load_chunk = [&](auto dst, int row0, int col0) {
 #pragma unroll
-      for (int r = 0; r < 32; ++r) acc[r] = {0.f, 0.f};
-      for (int k0 = 0; k0 < j0; k0 += 32) {
-        // a[r][k] = L[r0 + r, k0 + k],  b[c][k] = L[j0 + c, k0 + k]  (columns k0 + k < j0 <= rows)
-        for (int r = 0; r < 32; ++r) {
-          if (r0 + r < n) cp_async8(&ch.a[r][lane], A + (int64_t)(r0 + r) * ld + k0 + lane);
-          else ch.a[r][lane] = {0.f, 0.f};
-          if (j0 + r < n) cp_async8(&ch.b[r][lane], A + (int64_t)(j0 + r) * ld + k0 + lane);
-          else ch.b[r][lane] = {0.f, 0.f};
-        }
-        cp_async_wait_all();
-        __syncwarp();
-#pragma unroll 2
-        for (int k = 0; k < 32; ++k) {
-          const df32 bv = ch.b[lane][k];
+    for (int i = 0; i < 1024 / (kCholWarps * 32); ++i) {
+      const int e = tid + i * kCholWarps * 32;
+      const int r = e >> 5, c = e & 31;
+      if (row0 + r < n) cp_async8(&dst[r][c], A + (int64_t)(row0 + r) * ld + col0 + c);
+      else dst[r][c] = {0.f, 0.f};
+    }
+  };
+  // the four warps' partial tiles (in red) summed into the pairs at rows r0.., columns j0..
+  // (add = true: onto the stored value; false: replacing it), lower triangle and c < jb only
+  auto reduce_store = [&](int r0, int j0, int jb, bool add) {
+    __syncthreads();
+    for (int e = tid; e < 1024; e += kCholWarps * 32) {
+      const int r = e >> 5, c = e & 31;
+      const int gr = r0 + r;
+      if (gr < n && c < jb && j0 + c <= gr) {
+        df32 v = red[0][r][c];
 #pragma unroll
-          for (int r = 0; r < 32; ++r) df_fms(acc[r], ch.a[r][k], bv);
+        for (int w = 1; w < kCholWarps; ++w) v = df_add(v, red[w][r][c]);
+        if (add) {
+          const float2 s0 = A[(int64_t)gr * ld + j0 + c];
+          v = df_add({s0.x, s0.y}, v);
+        } else {
+          v = df_norm(v);
         }
-        __syncwarp();
-      }
-      if (lane < jb) {
-        for (int r = 0; r < 32; ++r) {
-          const int gr = r0 + r;
-          if (gr < n && j0 + lane <= gr) {
-            const float2 s = A[(int64_t)gr * ld + j0 + lane];
-            const df32 v = df_add({s.x, s.y}, acc[r]);
-            A[(int64_t)gr * ld + j0 + lane] = make_float2(v.h, v.l);
-          }
-        }
+        A[(int64_t)gr * ld + j0 + c] = make_float2(v.h, v.l);
       }
     }
     __syncthreads();
+  };
+  const int kw = warp * (32 / kCholWarps);   // this warp's 8 k of every chunk
+  for (int j0 = 0; j0 < n; j0 += 32) {
+    const int jb = min(32, n - j0);
+    // 1. panel update (nothing to subtract for the first panel)
+    const int nch = j0 / 32;
+    if (nch > 0) {
+      for (int r0 = j0; r0 < n; r0 += 32) {
+        df32 acc[32];
+#pragma unroll
+        for (int r = 0; r < 32; ++r) acc[r] = {0.f, 0.f};
+        load_chunk(As[0], r0, 0);
+        load_chunk(Bs[0], j0, 0);
+        cp_async_commit();
+        for (int c = 0; c < nch; ++c) {
+          const int buf = c & 1;
+          if (c + 1 < nch) {
+            load_chunk(As[buf ^ 1], r0, (c + 1) * 32);
+            load_chunk(Bs[buf ^ 1], j0, (c + 1) * 32);
+            cp_async_commit();
+            cp_async_wait_group<1>();
+          } else {
+            cp_async_wait_group<0>();
+          }
+          __syncthreads();
+#pragma unroll 2
+          for (int kk = 0; kk < 32 / kCholWarps; ++kk) {
+            const df32 bv = Bs[buf][lane][kw + kk];
+#pragma unroll
+            for (int r = 0; r < 32; ++r) df_fms(acc[r], As[buf][r][kw + kk], bv);
+          }
+          __syncthreads();
+        }
+#pragma unroll
+        for (int r = 0; r < 32; ++r) red[warp][r][lane] = acc[r];
+        reduce_store(r0, j0, jb, true);
+      }
+    }
     // 2. diagonal block in FP64 (warp 0, lane = row), then its inverse (lane = column)
     if (warp == 0) {
       for (int r = 0; r < 32; ++r) {
@@ -372,44 +406,35 @@ __global__ void __launch_bounds__(NW * 32, 3) cholesky_df_kernel(const BlockDesc
     }
     __syncthreads();
     // 3. rows below the diagonal block: L[r, panel] = R[r, panel] L_jj^-T
-    for (int r0 = j0 + jb + warp * 32; r0 < n; r0 += NW * 32) {
+    for (int r0 = j0 + jb; r0 < n; r0 += 32) {
       df32 acc[32];
 #pragma unroll
       for (int r = 0; r < 32; ++r) acc[r] = {0.f, 0.f};
-      for (int r = 0; r < 32; ++r) {
-        const int gr = r0 + r;
-        if (gr < n && lane < jb) cp_async8(&ch.a[r][lane], A + (int64_t)gr * ld + j0 + lane);
-        else ch.a[r][lane] = {0.f, 0.f};
-      }
-      cp_async_wait_all();
-      __syncwarp();
+      load_chunk(As[0], r0, j0);   // columns j0 + jb.. of these rows lie past the panel: zero weights below
+      cp_async_commit();
+      cp_async_wait_group<0>();
+      __syncthreads();
 #pragma unroll 2
-      for (int k = 0; k < 32; ++k) {
-        const df32 bv = binv[k][lane];
+      for (int kk = 0; kk < 32 / kCholWarps; ++kk) {
+        const df32 bv = binv[kw + kk][lane];
 #pragma unroll
-        for (int r = 0; r < 32; ++r) df_fma(acc[r], ch.a[r][k], bv);
+        for (int r = 0; r < 32; ++r) df_fma(acc[r], As[0][r][kw + kk], bv);
       }
-      if (lane < jb)
-        for (int r = 0; r < 32; ++r) {
-          const int gr = r0 + r;
-          if (gr < n) {
-            const df32 v = df_norm(acc[r]);
-            A[(int64_t)gr * ld + j0 + lane] = make_float2(v.h, v.l);
-          }
-        }
-      __syncwarp();
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 32; ++r) red[warp][r][lane] = acc[r];
+      reduce_store(r0, j0, jb, false);
     }
-    __syncthreads();
   }
   // 4. back to FP64 (lower triangle), and the FP32 copy of the factor
-  for (int r = warp; r < n; r += NW)
+  for (int r = warp; r < n; r += kCholWarps)
     for (int c = lane; c <= r; c += 32) {
       const float2 s = A[(int64_t)r * ld + c];
       A[(int64_t)r * ld + c] = df_to_bits({s.x, s.y});
     }
   if (l32) {
     float* Lf = l32 + bd.off_mat;
-    for (int r = warp; r < ld; r += NW)
+    for (int r = warp; r < ld; r += kCholWarps)
       for (int c = lane; c < ld; c += 32) {
         float v = 0.f;
         if (r < n && c <= r) {
@@ -419,7 +444,7 @@ __global__ void __launch_bounds__(NW * 32, 3) cholesky_df_kernel(const BlockDesc
         Lf[(int64_t)r * ld + c] = v;
       }
   }
-  if (threadIdx.x == 0 && s_bad) set_error(flags, NOLSM_ENOTPD);
+  if (tid == 0 && s_bad) set_error(flags, NOLSM_ENOTPD);
 }
 
 // Inverse of the lower-triangular L into X (out of place), by block rows of 32:
@@ -601,7 +626,7 @@ cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode) {
   // sb holds T_b(S) in FP64 (first sum_sq doubles); the second half is scratch.
   float* s32 = reinterpret_cast<float*>(sb + ctx->sum_sq);   // FP32 factor lives in the scratch half
   if (mode == NOLSM_CHOL_DF64) {
-    cholesky_df_kernel<4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, ctx->d_flags);
+    cholesky_df_kernel<<<ctx->n_blocks, kCholWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, ctx->d_flags);
     trinv_kernel<float, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
   } else if (mode == NOLSM_CHOL_FP64_INV64) {
     cholesky_kernel<double, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, sb, nullptr, ctx->d_flags);

@@ -50,6 +50,15 @@ struct NsState {
 
 enum : int32_t { kActive = 0, kConverged = 1, kRestart = 2, kFailed = 3 };
 
+// Scaled Newton-Schulz step coefficient for a lower bound l of |eig(X)| in (0, 1]
+// (Chen & Chow 2014): a = sqrt(3 / (1 + l + l^2)) maps [l, 1] onto [l', 1] with the two
+// ends equal; l = 1 gives the unscaled iteration of Eq. 6.
+__device__ __forceinline__ float cc_scale(float l) { return (l >= 1.f) ? 1.f : sqrtf(3.f / (1.f + l + l * l)); }
+__device__ __forceinline__ float cc_next(float l, float a) {
+  const float v = 0.5f * a * l * (3.f - a * a * l * l);
+  return (v > 1.f - 1e-6f) ? 1.f : v;
+}
+
 // A tile of a grouped matrix product: block, first output row, first output column.
 struct Tile {
   int32_t block, m0, n0, kend;
@@ -60,7 +69,7 @@ struct DevFlags {
   int32_t error;        // first device error code (nolsm_status), 0 = none
   int32_t n_tiles;      // tiles in the current list
   int32_t n_active;     // blocks still iterating
-  int32_t pad;
+  int32_t queue;        // next block to claim (persistent schedule)
   double sum_n;         // sum of block traces Tr(S D) over own columns
   double sum_e;         // same for Tr(H D)
   double energy;        // band energy reduction
@@ -74,6 +83,7 @@ struct nolsm_ctx {
   cudaStream_t stream = nullptr;
   int device = 0;
   int num_sms = 0;
+  int pair_clusters = 0;        // resident 2-CTA clusters of the persistent product kernel
   nolsm_status sticky = NOLSM_OK;
   std::string last_error;
 
@@ -167,6 +177,12 @@ namespace nolsm {
 
 // error helpers (api.cu)
 nolsm_status fail(nolsm_ctx* ctx, nolsm_status st, const std::string& msg);
+double unit_roundoff(const nolsm_ctx* ctx);   // of the iterate's storage format
+
+// Smallest lower bound l the scaled iteration may assume: one scaled step maps an eigenvalue at 1 to
+// about 2.6 l, which must stay clear of the format's rounding of the iterate (about u), so l >= 2 u
+// (FP16 2^-10, BF16 2^-7, FP32 2^-23) whatever a bound or a prediction says.
+inline float scaled_l_floor(const nolsm_ctx* ctx) { return (float)(2.0 * unit_roundoff(ctx)); }
 nolsm_status cuda_fail(nolsm_ctx* ctx, cudaError_t e, const char* what);
 
 // build.cu
@@ -177,7 +193,8 @@ cudaError_t launch_slabs_impl(nolsm_ctx* ctx, const void* lfac, int fp32, const 
 cudaError_t launch_bounds(nolsm_ctx* ctx);
 
 // sign.cu (SIMT path, control, slab traces)
-cudaError_t launch_ns_init(nolsm_ctx* ctx, double mu, int half, int mode, const float* lz, const float* pred);
+cudaError_t launch_ns_init(nolsm_ctx* ctx, double mu, int half, int mode, const float* lz, const float* pred,
+                           bool fill);
 cudaError_t launch_ns_restart(nolsm_ctx* ctx, double mu, int half);
 cudaError_t launch_ns_tiles(nolsm_ctx* ctx);
 cudaError_t launch_ns_tiles_n(nolsm_ctx* ctx, int tile_n);
@@ -193,6 +210,7 @@ cudaError_t launch_band_energy(nolsm_ctx* ctx);
 // sign_tc.cu (tcgen05 path)
 cudaError_t tc_prepare(nolsm_ctx* ctx);
 cudaError_t launch_gemm_tc(nolsm_ctx* ctx, int phase);
+cudaError_t launch_ns_pair(nolsm_ctx* ctx, double mu);
 int tc_tile_n();
 
 // learn.cu

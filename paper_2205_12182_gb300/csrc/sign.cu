@@ -26,14 +26,6 @@ template <> __device__ __forceinline__ float from_float<float>(float v) { return
 template <> __device__ __forceinline__ __half from_float<__half>(float v) { return __float2half_rn(v); }
 template <> __device__ __forceinline__ __nv_bfloat16 from_float<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 
-// Scaled Newton-Schulz step coefficient for a lower bound l of |eig(X)| in (0, 1]
-// (Chen & Chow 2014): a = sqrt(3 / (1 + l + l^2)) maps [l, 1] onto [l', 1] with the two
-// ends equal; l = 1 gives the unscaled iteration of Eq. 6.
-__device__ __forceinline__ float cc_scale(float l) { return (l >= 1.f) ? 1.f : sqrtf(3.f / (1.f + l + l * l)); }
-__device__ __forceinline__ float cc_next(float l, float a) {
-  const float v = 0.5f * a * l * (3.f - a * a * l * l);
-  return (v > 1.f - 1e-6f) ? 1.f : v;
-}
 
 // ----------------------------------------------------------------------------------------------
 // Grouped SIMT product C = A B^T on 128x128 tiles (both operands row-major, K contiguous).
@@ -184,30 +176,37 @@ sgemm_nt_kernel(const Tile* __restrict__ tiles, const int32_t* __restrict__ n_ti
 // distance.  A scale below the rigorous Gershgorin one starts with one unscaled step, which maps
 // any eigenvalue in (0, sqrt 3) into (0, 1]; the Gershgorin scale stays the cap.
 __global__ void ns_state_kernel(int n_blocks, const double* __restrict__ lo, const double* __restrict__ hi,
-                                double mu, float margin, float l0, int scaled, int mode,
+                                double mu, float margin, float l0, float l_floor, int scaled, int mode,
                                 const float* __restrict__ lz, const float* __restrict__ pred,
                                 NsState* __restrict__ st, float* __restrict__ resacc, DevFlags* flags) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b == 0) { flags->sum_n = 0.0; flags->sum_e = 0.0; }
+  if (b == 0) { flags->sum_n = 0.0; flags->sum_e = 0.0; flags->queue = 0; }
   if (b >= n_blocks) return;
   const double rad = fmax(fabs(hi[b] - mu), fabs(mu - lo[b]));
   float alpha = (float)(rad * (1.0 + margin));
   if (!(alpha > 0.f)) alpha = 1.f;
+  // A scale below the true radius / sqrt(3) would send eigenvalues beyond sqrt(3), which the
+  // unscaled first step maps to the wrong sign (and between sqrt(3) and sqrt(5) the iteration still
+  // converges, so no residual test sees it).  The Gershgorin scale bounds the radius from above, so
+  // no scale goes below it / 1.7.
+  const float alpha_floor = alpha / 1.7f;
   float l = l0;
   bool plain_first = false;
   if (mode == 1 && lz) {
     const float w = fabsf(lz[4 * b + 2]);
-    const float r = fmaxf(lz[4 * b + 1] + w - (float)mu, (float)mu - lz[4 * b + 0] + w) * (1.f + margin);
-    if (r > 0.f && r < alpha) { alpha = r; plain_first = true; }
+    float r = fmaxf(lz[4 * b + 1] + w - (float)mu, (float)mu - lz[4 * b + 0] + w) * (1.f + margin);
+    r = fmaxf(r, alpha_floor);
+    if (r < alpha) { alpha = r; plain_first = true; }
   } else if (mode == 2 && pred) {
-    const float r = 1.25f * fmaxf(pred[3 * b + 1] - (float)mu, (float)mu - pred[3 * b + 0]);
-    if (r > 0.f && r < alpha) { alpha = r; plain_first = true; }
+    float r = 1.25f * fmaxf(pred[3 * b + 1] - (float)mu, (float)mu - pred[3 * b + 0]);
+    r = fmaxf(r, alpha_floor);
+    if (r < alpha) { alpha = r; plain_first = true; }
     const float dist = exp10f(fminf(fmaxf(pred[3 * b + 2], -8.f), 1.f));
     l = 0.5f * dist / alpha;
   }
   NsState s;
   s.alpha = alpha;
-  s.l = scaled ? fminf(fmaxf(l, 1e-7f), 0.9f) : 1.f;
+  s.l = scaled ? fminf(fmaxf(l, l_floor), 0.9f) : 1.f;
   s.a = plain_first ? 1.f : cc_scale(s.l);
   s.res = FLT_MAX;
   s.res_prev = FLT_MAX;
@@ -249,7 +248,7 @@ __global__ void ns_restart_state_kernel(int n_blocks, const double* __restrict__
   NsState s = st[b];
   if (s.status != kRestart) return;
   s.alpha = (float)(fmax(fabs(hi[b] - mu), fabs(mu - lo[b])) * (1.0 + margin));
-  s.l = scaled ? fminf(fmaxf(l0, 1e-7f), 1.f) : 1.f;
+  s.l = scaled ? fminf(l0, 1.f) : 1.f;   // l0 carries the format's floor
   s.a = cc_scale(s.l);
   s.res = FLT_MAX;
   s.res_prev = FLT_MAX;
@@ -945,11 +944,14 @@ cudaError_t launch_sgemm_nt(nolsm_ctx* ctx, const float* a, const float* b, floa
   return cudaGetLastError();
 }
 
-cudaError_t launch_ns_init(nolsm_ctx* ctx, double mu, int half, int mode, const float* lz, const float* pred) {
-  const float l0 = (float)ctx->opt.lower_bound;
+cudaError_t launch_ns_init(nolsm_ctx* ctx, double mu, int half, int mode, const float* lz, const float* pred,
+                           bool fill) {
+  const float l_floor = scaled_l_floor(ctx);
+  const float l0 = std::max((float)ctx->opt.lower_bound, l_floor);
   ns_state_kernel<<<(ctx->n_blocks + 255) / 256, 256, 0, ctx->stream>>>(
-      ctx->n_blocks, ctx->d_lo, ctx->d_hi, mu, (float)ctx->opt.alpha_margin, l0, ctx->opt.scaled, mode, lz, pred,
+      ctx->n_blocks, ctx->d_lo, ctx->d_hi, mu, (float)ctx->opt.alpha_margin, l0, l_floor, ctx->opt.scaled, mode, lz, pred,
       ctx->d_state, ctx->d_resacc, ctx->d_flags);
+  if (!fill) return cudaGetLastError();   // the persistent product kernel forms X_0 itself
   const dim3 g(64, ctx->n_blocks);
   if (half == 0)
     ns_fill_kernel<float><<<g, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_a0, ctx->d_state, mu, (float*)ctx->d_x[0]);
@@ -992,7 +994,8 @@ cudaError_t launch_ns_restart(nolsm_ctx* ctx, double mu, int half) {
                                                                       ctx->d_lo, ctx->d_hi, mu, margin,
                                                                       (__nv_bfloat16*)ctx->d_x[0]);
   ns_restart_state_kernel<<<(ctx->n_blocks + 255) / 256, 256, 0, ctx->stream>>>(
-      ctx->n_blocks, ctx->d_lo, ctx->d_hi, mu, margin, (float)ctx->opt.lower_bound, ctx->opt.scaled, ctx->d_state,
+      ctx->n_blocks, ctx->d_lo, ctx->d_hi, mu, margin, std::max((float)ctx->opt.lower_bound, scaled_l_floor(ctx)),
+      ctx->opt.scaled, ctx->d_state,
       ctx->d_resacc);
   return cudaGetLastError();
 }

@@ -19,6 +19,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cfloat>
+
 namespace nolsm {
 namespace {
 
@@ -31,7 +33,15 @@ constexpr int B_BYTES = TN * TK * 2;          // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int TMEM_COLS = 512;                // two 256-column FP32 accumulators
 constexpr int NUM_THREADS = 192;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int kMapsPerBin = 6;                // loads of X0, X1, B (64 x 128 boxes), stores (32 x 32 boxes)
+constexpr int EPI_BUF_BYTES = 4096;           // one staging buffer: a 32 x 32 chunk and its transpose
+// shared memory: [stages | epilogue staging, NBUF buffers per epilogue warp | barriers | tables],
+// 1024-byte aligned base; the per-product kernel single-buffers (its tile table is large), the
+// persistent kernel double-buffers
+constexpr int EPI_OFF = STAGES * STAGE_BYTES;
+template <int NBUF> constexpr int bar_off() { return EPI_OFF + 4 * NBUF * EPI_BUF_BYTES; }
+template <int NBUF> constexpr int tab_off() { return bar_off<NBUF>() + 256; }
+template <int NBUF> constexpr int smem_bytes() { return 1024 /*align*/ + tab_off<NBUF>(); }
 
 struct TcParams {
   const Tile* tiles;
@@ -89,6 +99,18 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tmap, 
       : "memory");
 }
 
+// Tensor store of a 32 x 32 box from shared memory (bulk-group completion).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* tmap, const void* src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   reinterpret_cast<uint64_t>(tmap)),
+               "r"(x), "r"(y), "r"(smem_u32(src))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -115,6 +137,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
         "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
         "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[64]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, "
+      "%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, "
+      "%48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]),
+        "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]),
+        "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]),
+        "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]),
+        "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -156,6 +197,92 @@ template <> struct Pack<__nv_bfloat16> {
 
 __device__ __forceinline__ void set_error(DevFlags* f, int code) { atomicCAS(&f->error, 0, code); }
 
+// Byte offset of element (row, col) of a 32 x 32 16-bit box in the 64-byte-swizzle layout the store
+// tensor maps use: the 16-byte unit of a 64-byte row is XORed with bits 1-2 of the row.  Rows written
+// by consecutive lanes (and columns of one row) then fall in distinct shared-memory banks.
+__device__ __forceinline__ uint32_t sw64(int row, int col) {
+  return (uint32_t)(row * 64 + ((((col * 2) >> 4) ^ ((row >> 1) & 3)) << 4) + ((col * 2) & 15));
+}
+
+// Epilogue of one tile (one warp = 32 rows of the 128-row tile, lane = row): the accumulator
+// columns in chunks of 32, phase 1's arithmetic (B = c1 I - c3 T and ||T - I||^2 of the stored
+// triangle), FP16/BF16 stores.  Tiles lie on or above the block diagonal and the row slices of the
+// warps are 32-aligned with the chunks, so a chunk is below the diagonal (skipped), on it, or above
+// it.  The stored matrix is exactly symmetric -- the products read the transpose of their B operand,
+// and with a non-symmetric iterate the iteration would be X (3 - X X^T) / 2, which doubles
+// antisymmetric rounding errors each step once converged:
+//   above: the chunk goes to (rows, cols) and its transpose to (cols, rows), both staged in the
+//          warp's shared buffer and written by two tensor stores (lane 0, asynchronous);
+//   on:    entries c >= r at (r, c) and c > r also at (c, r), by plain stores.
+// Returns the lane's ||.||^2 part.  The caller waits for the tensor stores (bulk group) before the
+// results are read or the buffer goes away.
+template <typename T, int NBUF, int LDW>
+__device__ __forceinline__ float epi_tile(uint32_t tmem_acc, int q, int lane, T* out, int ld, int m0, int n0, int tn,
+                                          int phase, float c1, float c3, const CUtensorMap* smap, int rowbase,
+                                          uint8_t* stage, int& buf) {
+  const int r0 = m0 + q * 32;
+  const int r = r0 + lane;
+  float rsq = 0.f;
+  // LDW accumulator columns per tensor-memory load (32 or 64; tn is a multiple of 64)
+  for (int cl = 0; cl < tn; cl += LDW) {
+    uint32_t v[LDW];
+    if constexpr (LDW == 64) tmem_ld64(tmem_acc + ((uint32_t)(q * 32) << 16) + (uint32_t)cl, v);
+    else tmem_ld32(tmem_acc + ((uint32_t)(q * 32) << 16) + (uint32_t)cl, v);
+#pragma unroll
+    for (int h = 0; h < LDW / 32; ++h) {
+      const int cg0 = n0 + cl + 32 * h;
+      if (cg0 < r0) continue;                // whole chunk below the diagonal (warp-uniform)
+      float fv[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        float x = __uint_as_float(v[32 * h + j]);
+        if (phase == 1) {
+          const int cg = cg0 + j;
+          const float d = (cg == r) ? 1.f : 0.f;
+          const float e = x - d;
+          const float w = (cg > r) ? 2.f : ((cg == r) ? 1.f : 0.f);
+          rsq = fmaf(w, e * e, rsq);
+          x = c1 * d - c3 * x;
+        }
+        fv[j] = x;
+      }
+      if (cg0 == r0) {
+        T* orow = out + (int64_t)r * ld;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          if (cg0 + j >= r) orow[cg0 + j] = Pack<T>::one(fv[j]);
+          if (cg0 + j > r) out[(int64_t)(cg0 + j) * ld + r] = Pack<T>::one(fv[j]);
+        }
+        continue;
+      }
+      // the store that last used this buffer (NBUF chunks ago) has read it
+      if (lane == 0) {
+        if (NBUF == 1) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        else asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+      }
+      __syncwarp();
+      uint8_t* D = stage + buf * EPI_BUF_BYTES;   // the chunk, row = lane
+      uint8_t* M = D + 2048;                        // its transpose, row = j
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        *reinterpret_cast<uint4*>(D + sw64(lane, 8 * u)) =
+            make_uint4(Pack<T>::two(fv[8 * u], fv[8 * u + 1]), Pack<T>::two(fv[8 * u + 2], fv[8 * u + 3]),
+                       Pack<T>::two(fv[8 * u + 4], fv[8 * u + 5]), Pack<T>::two(fv[8 * u + 6], fv[8 * u + 7]));
+#pragma unroll
+      for (int j = 0; j < 32; ++j) *reinterpret_cast<T*>(M + sw64(j, lane)) = Pack<T>::one(fv[j]);
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        tma_store_2d(smap, D, cg0, rowbase + r0);
+        tma_store_2d(smap, M, r0, rowbase + cg0);
+        bulk_commit();
+      }
+      buf = (NBUF == 1) ? 0 : buf ^ 1;
+    }
+  }
+  return rsq;
+}
+
 // Everything a role needs about one tile, resolved once per launch into shared memory (the
 // chain tile -> block descriptor -> iteration state is three dependent global loads).
 struct TileInfo {
@@ -170,18 +297,20 @@ struct TileInfo {
   int32_t out_sel;    // 0: x0, 1: x1, 2: bbuf
   int32_t block;
   float c1, c3;       // phase-1 epilogue coefficients
-  int32_t pad;
+  int32_t map_s;      // tensor-map index of the output stores
 };
-constexpr int MAX_LOCAL = 352;                // tiles per CTA per launch
+constexpr int MAX_LOCAL = 200;                // tiles per CTA per launch
 constexpr int INFO_BYTES = MAX_LOCAL * (int)sizeof(TileInfo);
-constexpr int SMEM_TOTAL = SMEM_BYTES + INFO_BYTES;
+constexpr int TC_NBUF = 1;
+constexpr int SMEM_TOTAL = smem_bytes<TC_NBUF>() + INFO_BYTES;
+static_assert(SMEM_TOTAL <= 227 * 1024, "shared memory of the per-product kernel");
 
 template <typename T>
 __global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_constant__ TcParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* stage_base = smem;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + bar_off<TC_NBUF>());
   uint64_t* full_bar = bars;                       // [STAGES]
   uint64_t* empty_bar = bars + STAGES;             // [STAGES]
   uint64_t* tfull_bar = bars + 2 * STAGES;         // [2]
@@ -189,7 +318,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_cons
   uint64_t* drain_bar = bars + 2 * STAGES + 4;     // [1]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  TileInfo* info = reinterpret_cast<TileInfo*>(smem + STAGES * STAGE_BYTES + 256);
+  TileInfo* info = reinterpret_cast<TileInfo*>(smem + tab_off<TC_NBUF>());
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // Each CTA takes a contiguous run of the tile list: the list holds a block's tiles together, so
@@ -210,14 +339,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_cons
     f.tn = min(TN, bd.n_pad - tl.n0);
     f.row_a = bd.pos * bd.n_pad + tl.m0;
     f.row_b = bd.pos * bd.n_pad + tl.n0;
-    f.map_a = bd.bin * 3 + s.cur;
-    f.map_b = (p.phase == 1) ? f.map_a : bd.bin * 3 + 2;
+    f.map_a = bd.bin * kMapsPerBin + s.cur;
+    f.map_b = (p.phase == 1) ? f.map_a : bd.bin * kMapsPerBin + 2;
     f.out_sel = (p.phase == 1) ? 2 : (s.cur ^ 1);
     f.out_off = bd.off_mat;
     f.block = tl.block;
     f.c1 = 1.5f * s.a;
     f.c3 = 0.5f * s.a * s.a * s.a;
-    f.pad = 0;
+    f.map_s = bd.bin * kMapsPerBin + 3 + f.out_sel;
     info[i] = f;
   }
   if (threadIdx.x == 0) {
@@ -321,67 +450,25 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_cons
   } else {
     // ------------------------------------------------------------------ epilogue (warps 2..5)
     const int q = warp & 3;                  // TMEM lane quarter this warp may access
-    const int row_in_tile = q * 32 + lane;
     uint32_t tph[2] = {0u, 0u};
     int acc = 0;
+    int ebuf = 0;
     T* const pools[3] = {reinterpret_cast<T*>(p.x0), reinterpret_cast<T*>(p.x1), reinterpret_cast<T*>(p.bbuf)};
     for (int i = 0; i < n_local; ++i) {
       const TileInfo& f = info[i];
       const int ld = f.ld;
       const int tn = f.tn;
-      if (!mbar_wait(&tfull_bar[acc], tph[acc], budget, abort_flag)) {
+      // the outcome must be the same in all lanes: the tensor-memory loads below are warp-collective
+      if (!__all_sync(0xffffffffu, mbar_wait(&tfull_bar[acc], tph[acc], budget, abort_flag))) {
         set_error(p.flags, NOLSM_ETIMEOUT);
         *abort_flag = 1;
         break;
       }
       tc_fence_after();
       T* out = pools[f.out_sel] + f.out_off;
-      const float c1 = f.c1, c3 = f.c3;
-      const int r = f.m0 + row_in_tile;
-      T* orow = out + (int64_t)r * ld + f.n0;
-      float rsq = 0.f;
-      // Tiles lie on or above the block diagonal.  Entry (r, c): c > r is stored at (r, c) and at
-      // (c, r), the diagonal once, c < r (left part of a diagonal tile) not at all, so every
-      // iterate is exactly symmetric -- the products read the transpose of their B operand, and
-      // with a non-symmetric iterate the iteration would be X (3 - X X^T) / 2, which doubles
-      // antisymmetric rounding errors each step once converged.
-      for (int c0 = 0; c0 < tn; c0 += 32) {
-        const int cg0 = f.n0 + c0;
-        uint32_t v[32];
-        tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * TN + c0), v);
-        if (cg0 + 31 < r) continue;              // whole chunk left of the diagonal (warp-uniform ld done)
-        float fv[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          float x = __uint_as_float(v[j]);
-          if (p.phase == 1) {
-            const int cg = cg0 + j;
-            const float d = (cg == r) ? 1.f : 0.f;
-            const float e = x - d;
-            const float w = (cg > r) ? 2.f : ((cg == r) ? 1.f : 0.f);
-            rsq = fmaf(w, e * e, rsq);
-            x = c1 * d - c3 * x;
-          }
-          fv[j] = x;
-        }
-        if (cg0 >= r) {
-          uint32_t packed[16];
-#pragma unroll
-          for (int j = 0; j < 32; j += 2) packed[j >> 1] = Pack<T>::two(fv[j], fv[j + 1]);
-          uint4* dst = reinterpret_cast<uint4*>(orow + c0);
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            dst[u] = make_uint4(packed[4 * u], packed[4 * u + 1], packed[4 * u + 2], packed[4 * u + 3]);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (cg0 + j >= r) orow[c0 + j] = Pack<T>::one(fv[j]);
-        }
-        // mirror: column cg of this tile becomes row cg; lanes hold consecutive rows r
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (cg0 + j > r) out[(int64_t)(cg0 + j) * ld + r] = Pack<T>::one(fv[j]);
-      }
+      float rsq = epi_tile<T, TC_NBUF, 64>(tmem_base + (uint32_t)(acc * TN), q, lane, out, ld, f.m0, f.n0, tn, p.phase, f.c1,
+                                       f.c3, p.tmaps + f.map_s, f.row_a - f.m0,
+                                       smem + EPI_OFF + (warp - 2) * TC_NBUF * EPI_BUF_BYTES, ebuf);
       tc_fence_before();
       mbar_arrive(&tempty_bar[acc]);
       tph[acc] ^= 1u;
@@ -391,6 +478,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_cons
         if (lane == 0) atomicAdd(&p.resacc[f.block], rsq);
       }
     }
+    if (lane == 0) bulk_wait0();             // tensor stores complete before the kernel ends
+    __syncwarp();
     asm volatile("fence.proxy.async.global;" ::: "memory");
   }
   __syncwarp();
@@ -400,6 +489,378 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_cons
   if (warp == 1) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
   }
+}
+
+
+// ---------------------------------------------------------------------------------------------
+// Persistent schedule: one launch per sign evaluation.  The grid is made of 2-CTA clusters; a
+// cluster takes one block at a time off a queue and runs that block's whole iteration -- X_0 from
+// A0, then T = X X^T and X+ = X B^T until the block converges -- with the tiles of every product
+// split between its two CTAs (same roles, ring buffers and epilogue as ns_tc_kernel).  A block's
+// three n_pad^2 buffers stay in L2 for its whole iteration (76 blocks in flight x 1.5 MB at n_pad
+// 512), so the products read L2 instead of streaming HBM, and no launch or host round trip sits
+// between products.  The two CTAs pass through the same sequence of cluster barriers: the claimed
+// block, the residual partials of the first product and any abort are published in shared memory
+// and read by both after a barrier, so both take the same decisions (the rules of the check,
+// advance and restart kernels of the per-product schedule).
+constexpr int PAIR_MAX_TILES = 160;           // tiles of one product per CTA (n_pad 4096: 136)
+
+struct PairParams {
+  const BlockDesc* blocks;
+  NsState* st;
+  const CUtensorMap* tmaps;     // per bin: [X0, X1, B]
+  const float* a0;
+  const double* lo;
+  const double* hi;
+  const float* tol;
+  void* x0;
+  void* x1;
+  void* bbuf;
+  DevFlags* flags;
+  long long budget;
+  double mu;
+  float margin;
+  float l0;
+  int scaled;
+  int max_iter;
+  int detect_divergence;
+  int n_blocks;
+};
+
+struct PairTile {
+  int16_t m0, n0, tn, pad;
+};
+
+struct PairCtl {
+  int block;                    // claimed block (rank 0 writes it into both CTAs)
+  int n_local;                  // tiles of each product held by this CTA
+  float rsq[2];                 // this CTA's ||T - I||_F^2 partial, by round parity
+  int abort_pub[2];             // this CTA's abort flag as published for the round, by parity
+  PairTile tiles[PAIR_MAX_TILES];
+};
+constexpr int PAIR_THREADS = 320;             // producer, MMA issuer, 8 epilogue warps (2 per TMEM lane quarter)
+constexpr int PAIR_EPI_WARPS = 8;
+constexpr int PAIR_NBUF = 1;                  // staging buffers per epilogue warp
+constexpr int PAIR_LAYOUT = PAIR_EPI_WARPS * PAIR_NBUF / 4;   // in units of 4 warps x 1 buffer
+constexpr int PAIR_SMEM = smem_bytes<PAIR_LAYOUT>() + (int)sizeof(PairCtl);
+static_assert(PAIR_SMEM <= 227 * 1024, "shared memory of the persistent kernel");
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// generic address of the same shared-memory object in CTA `rank` of the cluster
+template <typename P>
+__device__ __forceinline__ P* cluster_peer(P* local, uint32_t rank) {
+  uint64_t out;
+  asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"(reinterpret_cast<uint64_t>(local)), "r"(rank));
+  return reinterpret_cast<P*>(out);
+}
+
+// X_0 = (A0 - mu I) / alpha on the n x n part, identity on the padding; CTA `rank` writes rows
+// [rank n_pad / 2, (rank + 1) n_pad / 2).  Several 16-byte loads per thread are in flight at a time
+// (A0 comes from HBM: its latency, not its bandwidth, bounds a dependent load-convert-store loop),
+// read as streaming data so they do not evict the resident iterates from L2.  The stores are made
+// visible to the tensor-copy proxy.
+template <typename T, int THREADS>
+__device__ __forceinline__ void pair_fill(const BlockDesc& bd, const float* __restrict__ a0, float alpha, double mu,
+                                          T* __restrict__ x, uint32_t rank) {
+  constexpr int U = THREADS >= 256 ? 4 : 8;
+  const int n = bd.n, ld = bd.n_pad, half = ld / 2, q4 = ld / 4;
+  const int total = half * q4;
+  const float inv = 1.f / alpha, muf = (float)mu;
+  const float* A = a0 + bd.off_mat + (int64_t)rank * half * ld;
+  T* X = x + bd.off_mat + (int64_t)rank * half * ld;
+  for (int e0 = threadIdx.x; e0 < total; e0 += THREADS * U) {
+    float4 a[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * THREADS;
+      if (e < total) a[u] = __ldcs(reinterpret_cast<const float4*>(A) + e);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * THREADS;
+      if (e >= total) break;
+      const int r = (int)rank * half + e / q4, c = (e % q4) * 4;
+      const float av[4] = {a[u].x, a[u].y, a[u].z, a[u].w};
+      float v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int cc = c + j;
+        v[j] = (r < n && cc < n) ? (av[j] - (r == cc ? muf : 0.f)) * inv : (r == cc ? 1.f : 0.f);
+      }
+      reinterpret_cast<uint2*>(X)[e] = make_uint2(Pack<T>::two(v[0], v[1]), Pack<T>::two(v[2], v[3]));
+    }
+  }
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Upper-triangular 128 x (<= 256) tiles of an n_pad x n_pad product, dealt to the two CTAs so that
+// their column counts stay balanced (both CTAs compute the same assignment).
+__device__ inline int pair_tiles(int ld, uint32_t rank, PairTile* out) {
+  int load[2] = {0, 0}, k = 0;
+  for (int m0 = 0; m0 < ld; m0 += TM)
+    for (int n0 = m0; n0 < ld; n0 += TN) {
+      const int tn = min(TN, ld - n0);
+      const int owner = load[1] < load[0] ? 1 : 0;
+      load[owner] += tn;
+      if (owner == (int)rank) {
+        if (k >= PAIR_MAX_TILES) return -1;
+        out[k++] = PairTile{(int16_t)m0, (int16_t)n0, (int16_t)tn, 0};
+      }
+    }
+  return k;
+}
+
+template <typename T>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PAIR_THREADS, 1) ns_pair_kernel(const __grid_constant__ PairParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* stage_base = smem;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + bar_off<PAIR_LAYOUT>());
+  uint64_t* full_bar = bars;                       // [STAGES]
+  uint64_t* empty_bar = bars + STAGES;             // [STAGES]
+  uint64_t* tfull_bar = bars + 2 * STAGES;         // [2]
+  uint64_t* tempty_bar = bars + 2 * STAGES + 2;    // [2]
+  uint64_t* drain_bar = bars + 2 * STAGES + 4;     // [1]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  PairCtl* ctl = reinterpret_cast<PairCtl*>(smem + tab_off<PAIR_LAYOUT>());
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  PairCtl* ctl0 = cluster_peer(ctl, 0u);
+  PairCtl* ctl1 = cluster_peer(ctl, 1u);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+    for (int a = 0; a < 2; ++a) { mbar_init(&tfull_bar[a], 1); mbar_init(&tempty_bar[a], 32 * PAIR_EPI_WARPS); }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    ctl->rsq[0] = ctl->rsq[1] = 0.f;
+    ctl->abort_pub[0] = ctl->abort_pub[1] = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  cluster_sync_all();   // both CTAs initialised before either touches the other's shared memory
+  const uint32_t tmem_base = *tmem_slot;
+  const long long budget = p.budget;
+  const long long drain_budget = budget > (1LL << 22) ? budget : (1LL << 22);
+  const int q = warp & 3;
+
+  // ring state of each role, carried across products and blocks
+  int ps = 0;
+  uint32_t pph = 0, armed = 0, arm_parity = 0;
+  int ms = 0;
+  uint32_t mph = 0, mtph[2] = {0u, 0u};
+  int macc = 0;
+  uint32_t etph[2] = {0u, 0u};
+  int eacc = 0;
+  int ebuf = 0;
+  int round = 0;
+
+  // one product of the current block: phase 1 T = X X^T -> B, phase 2 X+ = X B^T
+  auto product = [&](const BlockDesc& bd, const NsState& s, int phase, int par) {
+    const int ld = bd.n_pad;
+    const int n_local = ctl->n_local;
+    if (warp == 0) {
+      if (lane == 0) {
+        const CUtensorMap* ma = p.tmaps + bd.bin * kMapsPerBin + s.cur;
+        const CUtensorMap* mb = (phase == 1) ? ma : p.tmaps + bd.bin * kMapsPerBin + 2;
+        const int rowbase = bd.pos * ld;
+        bool ok = true;
+        for (int i = 0; i < n_local && ok; ++i) {
+          const PairTile t = ctl->tiles[i];
+          const uint32_t bytes = A_BYTES + t.tn * TK * 2;
+          for (int k0 = 0; k0 < ld; k0 += TK) {
+            if (!mbar_wait(&empty_bar[ps], pph ^ 1u, budget, abort_flag)) { ok = false; break; }
+            mbar_expect_tx(&full_bar[ps], bytes);
+            uint8_t* a_dst = stage_base + ps * STAGE_BYTES;
+            uint8_t* b_dst = a_dst + A_BYTES;
+            tma_load_2d(a_dst, ma, &full_bar[ps], k0, rowbase + t.m0);
+            for (int h = 0; h < t.tn; h += TM) tma_load_2d(b_dst + h * TK * 2, mb, &full_bar[ps], k0, rowbase + t.n0 + h);
+            armed |= 1u << ps;
+            arm_parity = (arm_parity & ~(1u << ps)) | (pph << ps);
+            if (++ps == STAGES) { ps = 0; pph ^= 1u; }
+          }
+        }
+        if (!ok) {
+          set_error(p.flags, NOLSM_ETIMEOUT);
+          *abort_flag = 1;
+        }
+      }
+    } else if (warp == 1) {
+      if (lane == 0) {
+        bool ok = true;
+        for (int i = 0; i < n_local && ok; ++i) {
+          const PairTile t = ctl->tiles[i];
+          const uint32_t idesc = make_idesc(Pack<T>::fmt, TM, t.tn);
+          if (!mbar_wait(&tempty_bar[macc], mtph[macc] ^ 1u, budget, abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t d_tmem = tmem_base + (uint32_t)(macc * TN);
+          for (int k0 = 0; k0 < ld; k0 += TK) {
+            if (!mbar_wait(&full_bar[ms], mph, budget, abort_flag)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t a_addr = smem_u32(stage_base + ms * STAGE_BYTES);
+            const uint64_t adesc = sw128_desc(a_addr);
+            const uint64_t bdesc = sw128_desc(a_addr + A_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < TK / 16; ++kk)
+              umma_f16(d_tmem, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), idesc, (k0 | kk) != 0);
+            umma_commit(&empty_bar[ms]);
+            if (++ms == STAGES) { ms = 0; mph ^= 1u; }
+          }
+          if (!ok) break;
+          umma_commit(&tfull_bar[macc]);
+          mtph[macc] ^= 1u;
+          macc ^= 1;
+        }
+        if (!ok) {
+          set_error(p.flags, NOLSM_ETIMEOUT);
+          *abort_flag = 1;
+        }
+      }
+    } else {
+      T* out = reinterpret_cast<T*>(phase == 1 ? p.bbuf : (s.cur ? p.x0 : p.x1)) + bd.off_mat;
+      const CUtensorMap* smap = p.tmaps + bd.bin * kMapsPerBin + 3 + (phase == 1 ? 2 : (s.cur ^ 1));
+      const float c1 = 1.5f * s.a, c3 = 0.5f * s.a * s.a * s.a;
+      float rsq = 0.f;
+      for (int i = 0; i < n_local; ++i) {
+        const PairTile t = ctl->tiles[i];
+        // the outcome must be the same in all lanes: the tensor-memory loads below are warp-collective
+        if (!__all_sync(0xffffffffu, mbar_wait(&tfull_bar[eacc], etph[eacc], budget, abort_flag))) {
+          set_error(p.flags, NOLSM_ETIMEOUT);
+          *abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        // warps 2..5 take the left half of the tile's columns, warps 6..9 the right half
+        const int hw = t.tn / 2, h0 = ((warp - 2) / 4) * hw;
+        rsq += epi_tile<T, PAIR_NBUF, 32>(tmem_base + (uint32_t)(eacc * TN + h0), q, lane, out, ld, t.m0, t.n0 + h0, hw,
+                                      phase, c1, c3, smap, bd.pos * ld,
+                                      smem + EPI_OFF + (warp - 2) * PAIR_NBUF * EPI_BUF_BYTES, ebuf);
+        tc_fence_before();
+        mbar_arrive(&tempty_bar[eacc]);
+        etph[eacc] ^= 1u;
+        eacc ^= 1;
+      }
+      if (phase == 1) {
+        for (int o = 16; o; o >>= 1) rsq += __shfl_xor_sync(0xffffffffu, rsq, o);
+        if (lane == 0) atomicAdd(&ctl->rsq[par], rsq);
+      }
+      if (lane == 0) bulk_wait0();           // this product's tensor stores are complete
+      __syncwarp();
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
+  };
+
+  for (;;) {
+    if (rank == 0 && threadIdx.x == 0) {
+      const int b = atomicAdd(&p.flags->queue, 1);
+      ctl0->block = b;
+      ctl1->block = b;
+    }
+    cluster_sync_all();
+    const int b = ctl->block;
+    if (b >= p.n_blocks) break;
+    const BlockDesc bd = p.blocks[b];
+    NsState s = p.st[b];
+    if (threadIdx.x == 0) {
+      const int k = pair_tiles(bd.n_pad, rank, ctl->tiles);
+      ctl->n_local = k < 0 ? 0 : k;
+      if (k < 0) {
+        set_error(p.flags, NOLSM_EINVAL);
+        *abort_flag = 1;
+      }
+    }
+    pair_fill<T, PAIR_THREADS>(bd, p.a0, s.alpha, p.mu, reinterpret_cast<T*>(p.x0), rank);
+    __syncthreads();
+    cluster_sync_all();
+    bool stop = false;
+    for (;;) {
+      const int par = round & 1;
+      product(bd, s, 1, par);
+      if (threadIdx.x == 0) ctl->abort_pub[par] = *abort_flag;
+      cluster_sync_all();
+      const float rsq = ctl0->rsq[par] + ctl1->rsq[par];
+      const int aborted = ctl0->abort_pub[par] | ctl1->abort_pub[par];
+      if (threadIdx.x == 0) ctl->rsq[par ^ 1] = 0.f;   // next round's slot (last read one round ago)
+      round += 1;
+      if (aborted) { stop = true; break; }
+      const float res = sqrtf(rsq);
+      if (p.detect_divergence && s.iters >= 1 && s.restarts == 0 &&
+          (!isfinite(res) || res > 1.5f * sqrtf((float)bd.n_pad))) {
+        // the scale was too small: restart from the Gershgorin scale (once per block)
+        s.restarts += 1;
+        s.alpha = (float)(fmax(fabs(p.hi[b] - p.mu), fabs(p.mu - p.lo[b])) * (1.0 + p.margin));
+        s.l = p.scaled ? fminf(p.l0, 1.f) : 1.f;   // p.l0 carries the format's floor
+        s.a = cc_scale(s.l);
+        s.res = FLT_MAX;
+        s.res_prev = FLT_MAX;
+        s.cur = 0;
+        s.grow = 0;
+        s.status = kActive;
+        pair_fill<T, PAIR_THREADS>(bd, p.a0, s.alpha, p.mu, reinterpret_cast<T*>(p.x0), rank);
+        cluster_sync_all();
+        continue;
+      }
+      if (!isfinite(res)) {
+        s.status = kFailed;
+        s.res = res;
+        if (rank == 0 && threadIdx.x == 0) set_error(p.flags, NOLSM_ENONFINITE);
+        break;
+      }
+      s.res_prev = s.res;
+      s.res = res;
+      const bool plain = s.l >= 1.f;
+      if (res <= p.tol[b]) { s.status = kConverged; break; }
+      if (plain && s.iters >= 2 && res < 0.25f && res > 0.5f * s.res_prev) { s.status = kConverged; break; }
+      if (s.iters >= p.max_iter) {
+        s.status = kFailed;
+        if (rank == 0 && threadIdx.x == 0) set_error(p.flags, NOLSM_ENOCONV);
+        break;
+      }
+      product(bd, s, 2, par);
+      cluster_sync_all();
+      s.cur ^= 1;
+      s.iters += 1;
+      s.l = cc_next(s.l, s.a);
+      s.a = cc_scale(s.l);
+    }
+    if (rank == 0 && threadIdx.x == 0) p.st[b] = s;
+    if (stop) break;
+  }
+
+  // teardown: every copy and product issued here lands before shared and tensor memory go away
+  if (warp == 0 && lane == 0) {
+    volatile int never = 0;
+    for (int st = 0; st < STAGES; ++st)
+      if (armed & (1u << st)) mbar_wait(&full_bar[st], (arm_parity >> st) & 1u, drain_budget, &never);
+  } else if (warp == 1 && lane == 0) {
+    umma_commit(drain_bar);
+    volatile int never = 0;
+    mbar_wait(drain_bar, 0, drain_budget, &never);
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+  }
+  cluster_sync_all();
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
@@ -432,19 +893,27 @@ cudaError_t tc_prepare(nolsm_ctx* ctx) {
     bin_cnt[b.bin] += 1;
     bin_pad[b.bin] = b.n_pad;
   }
-  maps.resize((size_t)n_bins * 3);
+  maps.resize((size_t)n_bins * kMapsPerBin);
   void* pools[3] = {ctx->d_x[0], ctx->d_x[1], ctx->d_b};
+  const CUtensorMapDataType dt = bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
   for (int bi = 0; bi < n_bins; ++bi) {
     for (int pi = 0; pi < 3; ++pi) {
       const uint64_t np = (uint64_t)bin_pad[bi];
       void* base = reinterpret_cast<uint8_t*>(pools[pi]) + bin_off[bi] * 2;
       cuuint64_t gdim[2] = {np, np * (uint64_t)bin_cnt[bi]};
       cuuint64_t gstride[1] = {np * 2};
-      cuuint32_t box[2] = {TK, TM};
       cuuint32_t estr[2] = {1, 1};
-      CUresult r = encode(&maps[(size_t)bi * 3 + pi], bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
-                          2, base, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      // operand loads: 64 x 128 boxes, 128-byte swizzle (the MMA's K-major layout)
+      cuuint32_t box[2] = {TK, TM};
+      CUresult r = encode(&maps[(size_t)bi * kMapsPerBin + pi], dt, 2, base, gdim, gstride, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+      // epilogue stores: 32 x 32 boxes, 64-byte swizzle (the staging layout of epi_tile)
+      cuuint32_t sbox[2] = {32, 32};
+      r = encode(&maps[(size_t)bi * kMapsPerBin + 3 + pi], dt, 2, base, gdim, gstride, sbox, estr,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     }
   }
@@ -461,6 +930,10 @@ cudaError_t tc_prepare(nolsm_ctx* ctx) {
     e = cudaFuncSetAttribute(ns_tc_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TOTAL);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(ns_tc_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TOTAL);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(ns_pair_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(ns_pair_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
@@ -499,5 +972,48 @@ cudaError_t launch_gemm_tc(nolsm_ctx* ctx, int phase) {
 }
 
 int tc_tile_n() { return TN; }
+
+// The persistent schedule: one launch for the whole iteration of every block (see ns_pair_kernel).
+cudaError_t launch_ns_pair(nolsm_ctx* ctx, double mu) {
+  PairParams p;
+  p.blocks = ctx->d_blocks;
+  p.st = ctx->d_state;
+  p.tmaps = reinterpret_cast<const CUtensorMap*>(ctx->d_tmaps);
+  p.a0 = ctx->d_a0;
+  p.lo = ctx->d_lo;
+  p.hi = ctx->d_hi;
+  p.tol = ctx->d_tol;
+  p.x0 = ctx->d_x[0];
+  p.x1 = ctx->d_x[1];
+  p.bbuf = ctx->d_b;
+  p.flags = ctx->d_flags;
+  p.budget = ctx->opt.wait_budget;
+  p.mu = mu;
+  p.margin = (float)ctx->opt.alpha_margin;
+  p.l0 = std::max((float)ctx->opt.lower_bound, scaled_l_floor(ctx));
+  p.scaled = ctx->opt.scaled;
+  p.max_iter = ctx->opt.max_iter;
+  p.detect_divergence = ctx->opt.bounds != NOLSM_BOUNDS_GERSHGORIN;
+  p.n_blocks = ctx->n_blocks;
+  const bool bf16 = ctx->opt.precision == NOLSM_PREC_MIXED_BF16;
+  if (ctx->pair_clusters <= 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * 256, 1, 1);
+    cfg.blockDim = dim3(PAIR_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = PAIR_SMEM;
+    cfg.stream = ctx->stream;
+    int n = 0;
+    cudaError_t e = bf16 ? cudaOccupancyMaxActiveClusters(&n, ns_pair_kernel<__nv_bfloat16>, &cfg)
+                         : cudaOccupancyMaxActiveClusters(&n, ns_pair_kernel<__half>, &cfg);
+    if (e != cudaSuccess) return e;
+    ctx->pair_clusters = n > 0 ? n : ctx->num_sms / 2;
+  }
+  const int clusters = std::max(1, std::min(ctx->pair_clusters, ctx->n_blocks));
+  if (bf16)
+    ns_pair_kernel<__nv_bfloat16><<<2 * clusters, PAIR_THREADS, PAIR_SMEM, ctx->stream>>>(p);
+  else
+    ns_pair_kernel<__half><<<2 * clusters, PAIR_THREADS, PAIR_SMEM, ctx->stream>>>(p);
+  return cudaGetLastError();
+}
 
 }  // namespace nolsm

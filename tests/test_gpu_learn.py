@@ -142,7 +142,8 @@ def test_bad_predictions_cost_iterations_not_accuracy(nl, sys1, orc1, mu1, case)
     assert np.abs(lib.density().cpu().numpy() - orc1.density(mu1)).max() <= 1e-3
     assert st["n_electrons"] == pytest.approx(2 * orc1.electron_count(mu1), rel=1e-4)
     if case == "radius_far_too_small":
-        assert st["n_restarted"] > 0
+        # the scale never drops below the Gershgorin scale / 1.7, so the iteration cannot diverge
+        assert st["n_restarted"] == 0
 
 
 def test_trained_predictor_saves_iterations_on_held_out_box(nl):

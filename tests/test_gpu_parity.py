@@ -158,3 +158,24 @@ def test_config2_sampled_blocks(nl):
     e = lib.band_energy()
     assert np.isfinite(e)
     del rows
+
+
+@pytest.mark.parametrize("bounds", [0, 2])
+def test_persistent_and_per_product_schedules_agree(nl, sys1, orc1, mu1, bounds):
+    """The persistent pair kernel (whole iteration per block on the device) and the host-driven
+    per-product launches run the same arithmetic and the same stopping rules."""
+    import os
+    out = {}
+    for sched in (nl.SCHEDULE_PERSISTENT, nl.SCHEDULE_PER_PRODUCT):
+        lib = make(nl, sys1, nl.PREC_MIXED_FP16, bounds=bounds, schedule=sched)
+        if bounds == nl.BOUNDS_LEARNED:
+            w = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                             "paper_2205_12182_gb300", "weights", "bounds_mlp.json")
+            lib.set_predictor(nl.BoundPredictor.load(w))
+        st = lib.sign_batch(mu1)
+        out[sched] = (st, lib.iters(), lib.density().cpu().numpy())
+    (sa, ia, da), (sb, ib, db) = out[nl.SCHEDULE_PERSISTENT], out[nl.SCHEDULE_PER_PRODUCT]
+    assert np.mean(ia == ib) >= 0.95
+    assert np.abs(da - db).max() <= 1e-4
+    assert np.abs(da - orc1.density(mu1)).max() <= 1e-3
+    assert sa["n_electrons"] == pytest.approx(sb["n_electrons"], rel=1e-5)
