@@ -158,6 +158,7 @@ def run_ours(args):
         solve(lib, system, mu_fn, d_dev, "device")
     barrier()
     lib.counters(reset=True)
+    lib.phase_times(reset=True)
     phase = {"steps": []}
     with ClockSampler(local) as clk:
         barrier()
@@ -172,7 +173,9 @@ def run_ours(args):
         barrier()
         wall = time.perf_counter() - t0
     dev_ms = ev0.elapsed_time(ev1)
+    _CLOCK_MAX["mhz"] = clk.summary().get("sm_max_mhz")
     cnt = lib.counters(reset=True)
+    stage_ms = {k: v / args.steps for k, v in lib.phase_times(reset=True).items()}
     t_step = max(wall, dev_ms / 1000.0) / args.steps
     if dist is not None:
         tt = torch.tensor([t_step], dtype=torch.float64, device=dev)
@@ -205,7 +208,9 @@ def run_ours(args):
     gemm_tflops = cnt["gemm_flops"] / (cnt["gemm_ms"] * 1e-3) / 1e12 if cnt["gemm_ms"] > 0 else None
     frac = gemm_tflops / pk["bf16_tflops_sustained"] if gemm_tflops else None
     st = lib.sign_batch(mu)   # statistics of one evaluation at the converged mu (not timed)
-    traffic = load_traffic()
+    n_b = np.array([nolsm.nolsm_block_info(lib.ctx, b)[0] for b in range(system.n_blocks)], np.float64)
+    roofs = rooflines(stage_ms, cnt, args.steps, n_b, pk, clk_max_mhz(), torch.cuda.get_device_properties(dev))
+    dominant = max(roofs, key=lambda r: r["ms_per_step"])
     line = {
         "metric": METRIC,
         "value": atoms / t_step,
@@ -220,7 +225,7 @@ def run_ours(args):
         "dtype": "f16",
         "data": "synthetic (seeded water boxes; no dataset)",
         "config": dict(WORKLOAD, mu_tol_rel=TOL_N, bounds="learned (predictor weights committed, trained on other seeds)",
-                       precision="FP16 operands / FP32 accumulate, FP64 Cholesky factor",
+                       precision="FP16 operands / FP32 accumulate; S factor in double-float (48-bit)",
                        l2="working set > 10 GB >> 129 MB L2 (no flush needed)",
                        parallelism=f"dp{world} (one box per rank, shared mu)"),
         "sign_gemm": {
@@ -232,16 +237,9 @@ def run_ours(args):
             "ns_iters_avg": st["iters_avg"],
             "mu_steps": phase["steps"][-1],
         },
-        "roofline": {
-            "kernel": "ns_tc_kernel (tcgen05 FP16 Newton-Schulz product)",
-            "bound": "tensor",
-            "achieved": gemm_tflops,
-            "peak": pk["bf16_tflops_sustained"],
-            "unit": "TFLOP/s",
-            "frac": frac,
-            "peak_source": pk["source"] + " bf16 sustained (FP16 dense rate = BF16 dense rate)",
-            "traffic": traffic,
-        },
+        "roofline": dominant,
+        "rooflines": roofs,
+        "stage_ms_per_step": stage_ms,
         "e2e": {"value": atoms / t_e2e, "unit": "atoms/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(cnt["launches"]),
@@ -268,6 +266,10 @@ def variants(nolsm, system, mu_fn, d_dev, predictor, barrier, world, steps=2):
         "mixed_fp16_gershgorin": dict(precision=nolsm.PREC_MIXED_FP16),
         "mixed_fp16_learned_fp32_cholesky": dict(precision=nolsm.PREC_MIXED_FP16, bounds=nolsm.BOUNDS_LEARNED,
                                                  chol_precision=nolsm.CHOL_FP32),
+        "mixed_fp16_learned_fp64_cholesky": dict(precision=nolsm.PREC_MIXED_FP16, bounds=nolsm.BOUNDS_LEARNED,
+                                                 chol_precision=nolsm.CHOL_FP64),
+        "mixed_fp16_learned_per_product_launches": dict(precision=nolsm.PREC_MIXED_FP16, bounds=nolsm.BOUNDS_LEARNED,
+                                                        schedule=nolsm.SCHEDULE_PER_PRODUCT),
     }
     for name, kw in cases.items():
         lib = nolsm.Nolsm(**kw)
@@ -287,15 +289,71 @@ def variants(nolsm, system, mu_fn, d_dev, predictor, barrier, world, steps=2):
     return out
 
 
-def load_traffic():
-    """DRAM bytes per launch of the product kernel from the committed ncu summary, if current."""
-    p = os.path.join(ROOT, "profiles", "ns_tc_kernel_traffic.json")
-    if os.path.exists(p):
-        try:
-            return json.load(open(p)).get("bytes_per_launch")
-        except (ValueError, OSError):
+_CLOCK_MAX = {"mhz": None}
+
+
+def clk_max_mhz():
+    return _CLOCK_MAX["mhz"]
+
+
+def source_hash(relpath, begin, function):
+    """sha256 (16 hex digits) of a source region: from the first line containing `begin` to the closing
+    brace (a lone '}' line) of the __global__ function `function`."""
+    import hashlib
+    lines = open(os.path.join(ROOT, relpath)).read().split("\n")
+    i0 = next(i for i, ln in enumerate(lines) if begin in ln)
+    i1 = next(i for i, ln in enumerate(lines) if "__global__" in ln and function + "(" in ln)
+    i2 = next(i for i in range(i1, len(lines)) if lines[i] == "}")
+    return hashlib.sha256("\n".join(lines[i0:i2 + 1]).encode()).hexdigest()[:16]
+
+
+def traffic_per_launch(kernel, units):
+    """DRAM bytes of one launch from the committed ncu summary profiles/<kernel>_traffic.json
+    (bytes per unit x units of this launch), or None when the kernel's source changed since."""
+    p = os.path.join(ROOT, "profiles", kernel + "_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        src = d["source"]
+        if source_hash(src["file"], src["begin"], src["function"]) != d["source_sha256_16"]:
             return None
-    return None
+        return d["dram_bytes_per_unit"] * units
+    except (ValueError, OSError, KeyError, StopIteration):
+        return None
+
+
+def rooflines(stage_ms, cnt, steps, n_b, pk, sm_max_mhz, props):
+    """The two kernels that dominate a step, each against its own bound, from the stage times measured
+    in the timed region (CUDA events on the library's stream; one launch of each per stage).
+    * the double-float Cholesky (stage 'factor'): plain FP32-pipe arithmetic; algorithmic work
+      sum_b n_b^3 / 6 multiply-adds (n_b^3 / 3 flops, FP64-equivalent); peak: every SM issues 128
+      FP32 operations per clock and a double-float multiply-add costs 12 of them;
+    * the Newton-Schulz products (stage 'products'): tensor cores, executed FLOP over their time."""
+    mhz = sm_max_mhz or 2070.0
+    out = []
+    chol_ms = stage_ms.get("factor", 0.0)
+    if chol_ms > 0:
+        flop = float(np.sum(n_b ** 3) / 3.0)
+        peak = props.multi_processor_count * 128 * mhz * 1e6 / 12.0 * 2.0 / 1e12
+        ach = flop / (chol_ms * 1e-3) / 1e12
+        out.append({"kernel": "cholesky_df_kernel (double-float S = L L^T, 4096 blocks per launch)", "bound": "alu",
+                    "achieved": ach, "peak": peak, "unit": "TFLOP/s (FP64-equivalent)", "frac": ach / peak,
+                    "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 ops/clk x {mhz:.0f} MHz"
+                                   " / 12 ops per double-float multiply-add",
+                    "ms_per_step": chol_ms,
+                    "traffic": traffic_per_launch("cholesky_df_kernel", len(n_b))})
+    prod_ms = stage_ms.get("products", 0.0)
+    if prod_ms > 0 and cnt["gemm_flops"] > 0:
+        ach = cnt["gemm_flops"] / steps / (prod_ms * 1e-3) / 1e12
+        launches = max(cnt["gemm_launches"], 1)
+        out.append({"kernel": "ns_pair_kernel (tcgen05 FP16 Newton-Schulz products, whole iteration per launch)",
+                    "bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                    "frac": ach / pk["bf16_tflops_sustained"],
+                    "peak_source": pk["source"] + " bf16 sustained (FP16 dense rate = BF16 dense rate)",
+                    "ms_per_step": prod_ms,
+                    "traffic": traffic_per_launch("ns_pair_kernel", cnt["gemm_flops"] / launches)})
+    return out
 
 
 def parity_sample(system, d, mu, n_blocks=8):

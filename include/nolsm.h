@@ -218,6 +218,26 @@ nolsm_status nolsm_block_matrix(const nolsm_ctx* ctx, int32_t b, int32_t which, 
 nolsm_status nolsm_counters(nolsm_ctx* ctx, int64_t* launches, int64_t* gemm_launches, double* gemm_ms,
                             double* gemm_flops, int32_t reset);
 
+/* Stages of the path timed by nolsm_phase_times. */
+typedef enum nolsm_phase {
+  NOLSM_PHASE_GATHER = 0,      /* index sets done: dense T_b(H0), T_b(S) from the CSR rows (step 1) */
+  NOLSM_PHASE_FACTOR = 1,      /* Cholesky factor of every T_b(S) */
+  NOLSM_PHASE_INVERSE = 2,     /* triangular inverses L^-1 */
+  NOLSM_PHASE_CONGRUENCE = 3,  /* A0 = L^-1 T_b(H0) L^-T */
+  NOLSM_PHASE_BUILD_REST = 4,  /* own-column slabs, bounds, block features, tensor maps */
+  NOLSM_PHASE_SIGN_SETUP = 5,  /* per evaluation: features at mu, predictions, initial scales */
+  NOLSM_PHASE_PRODUCTS = 6,    /* the Newton-Schulz matrix products and their iteration control */
+  NOLSM_PHASE_SLAB = 7,        /* own-column refinement and the block traces */
+  NOLSM_PHASE_DENSITY = 8,     /* back-transform and scatter of D (step 3) */
+  NOLSM_PHASE_ENERGY = 9,      /* Tr(D H0) */
+  NOLSM_NUM_PHASES = 10
+} nolsm_phase;
+
+/* Cumulative device time of each nolsm_phase (ms, CUDA event pairs recorded on the context stream
+ * around the stage's launches) since nolsm_create or the last reset: ms[p] for p < n (n at most
+ * NOLSM_NUM_PHASES).  reset != 0 zeroes them after reading.  Synchronises. */
+nolsm_status nolsm_phase_times(nolsm_ctx* ctx, double* ms, int32_t n, int32_t reset);
+
 /* Band energy spin_factor * sum_e d_val[e] * h_val[e] over nnz stored entries (the reduction of
  * nolsm_band_energy), for callers that must not allocate device memory: the call needs no
  * context, makes no cudaMalloc/cudaFree or other allocating call, and keeps its partial sums in

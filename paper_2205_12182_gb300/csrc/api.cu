@@ -35,6 +35,46 @@ double unit_roundoff(const nolsm_ctx* ctx) {
   }
 }
 
+cudaError_t phase_mark(nolsm_ctx* ctx, int phase) {
+  cudaEvent_t ev;
+  if (!ctx->ev_free.empty()) {
+    ev = ctx->ev_free.back();
+    ctx->ev_free.pop_back();
+  } else {
+    cudaError_t e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = cudaEventRecord(ev, ctx->stream);
+  if (e != cudaSuccess) return e;
+  if (ctx->ph_open >= 0) ctx->ph_pending.push_back({ctx->ph_open, ctx->ph_open_ev, ev});
+  if (phase >= 0) {
+    ctx->ph_open = phase;
+    ctx->ph_open_ev = ev;
+  } else {
+    ctx->ph_open = -1;
+    ctx->ph_open_ev = nullptr;
+    if (ctx->ph_pending.empty()) ctx->ev_free.push_back(ev);
+  }
+  return cudaSuccess;
+}
+
+// The stream has drained: accumulate every closed interval and recycle its events (an event that
+// closes one interval and opens the next is recycled once).
+void harvest_phases(nolsm_ctx* ctx) {
+  std::vector<cudaEvent_t> done;
+  for (const auto& r : ctx->ph_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) ctx->phase_ms[r.phase] += ms;
+    done.push_back(r.a);
+    done.push_back(r.b);
+  }
+  ctx->ph_pending.clear();
+  std::sort(done.begin(), done.end());
+  done.erase(std::unique(done.begin(), done.end()), done.end());
+  for (cudaEvent_t ev : done)
+    if (ev != ctx->ph_open_ev) ctx->ev_free.push_back(ev);
+}
+
 }  // namespace nolsm
 
 #define CK(call)                                                  \
@@ -411,11 +451,15 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   CK(dalloc(ctx, &ctx->d_t1, (size_t)ctx->sum_sq));
   double* sb = ctx->d_sb;
   ctx->n_launches += 8;   // gather, factor, inverse (+conversion), two products, slabs, bounds
+  CK(phase_mark(ctx, NOLSM_PHASE_GATHER));
   CK(launch_gather(ctx, ctx->d_a0, sb));
   const int chol_mode = ctx->opt.chol_precision;
   const int chol32 = chol_mode == NOLSM_CHOL_FP32;
-  CK(launch_cholesky_inverse(ctx, sb, chol_mode));
+  CK(phase_mark(ctx, NOLSM_PHASE_FACTOR));
+  CK(launch_cholesky_inverse(ctx, sb, chol_mode));   // marks the inverse stage between its launches
+  CK(phase_mark(ctx, NOLSM_PHASE_CONGRUENCE));
   CK(launch_congruence(ctx, ctx->d_t1));
+  CK(phase_mark(ctx, NOLSM_PHASE_BUILD_REST));
   CK(launch_slabs_impl(ctx, chol32 ? (const void*)(sb + ctx->sum_sq) : (const void*)sb, chol32, ctx->d_t1));
   CK(dalloc(ctx, &ctx->d_rowd, (size_t)ctx->n_blocks * kMaxDim));
   CK(dalloc(ctx, &ctx->d_rowr, (size_t)ctx->n_blocks * kMaxDim));
@@ -428,7 +472,9 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
     nolsm_status st_l = run_lanczos(ctx, 0.0, 0, ctx->opt.lanczos_steps, nullptr);
     if (st_l != NOLSM_OK) return st_l;
   }
+  CK(phase_mark(ctx, -1));
   nolsm_status st = check_device_flags(ctx);
+  harvest_phases(ctx);
   if (st != NOLSM_OK) return st;
   ctx->h_lo.resize((size_t)n_blocks);
   ctx->h_hi.resize((size_t)n_blocks);
@@ -483,6 +529,7 @@ nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out) 
   const bool mixed = is_mixed(ctx);
   const int hk = half_kind(ctx);
   CK(cudaEventRecord(ctx->ev0, ctx->stream));
+  CK(phase_mark(ctx, NOLSM_PHASE_SIGN_SETUP));
   const int mode = ctx->opt.bounds;
   const float* pred = nullptr;
   if (mode == NOLSM_BOUNDS_LEARNED) {
@@ -500,6 +547,7 @@ nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out) 
   const int tile_n = mixed ? tc_tile_n() : kTile;
   const int check_every = 4;
   ctx->gemm_ev_used = 0;
+  CK(phase_mark(ctx, NOLSM_PHASE_PRODUCTS));
   if (persistent) CK(gemm_timed(ctx, mixed, 0, mu));   // the whole iteration of every block
   for (int it = 0; !persistent && it <= ctx->opt.max_iter; ++it) {
     CK(launch_ns_tiles_n(ctx, tile_n));
@@ -520,11 +568,14 @@ nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out) 
       if (ctx->h_flags->error != 0 || ctx->h_flags->n_active == 0) break;
     }
   }
+  CK(phase_mark(ctx, NOLSM_PHASE_SLAB));
   CK(launch_slab_traces(ctx, hk));
   ctx->n_launches += 1;   // sum_traces (the slab launches count themselves)
+  CK(phase_mark(ctx, -1));
   CK(cudaEventRecord(ctx->ev1, ctx->stream));
   nolsm_status st = check_device_flags(ctx);
   harvest_gemm_events(ctx);
+  harvest_phases(ctx);
   if (st != NOLSM_OK) return st;
   ctx->last_mu = mu;
   ctx->have_sign = true;
@@ -619,7 +670,9 @@ nolsm_status nolsm_density(nolsm_ctx* ctx, double* d_val, int32_t memory) {
   if (ctx->sticky != NOLSM_OK) return ctx->sticky;
   if (!ctx->have_sign) return fail(ctx, NOLSM_ENOTBUILT, "nolsm_sign_batch has not run");
   if (memory != NOLSM_MEM_DEVICE && memory != NOLSM_MEM_HOST) return fail(ctx, NOLSM_EINVAL, "bad memory kind");
+  CK(phase_mark(ctx, NOLSM_PHASE_DENSITY));
   CK(launch_density(ctx));
+  CK(phase_mark(ctx, -1));
   ctx->n_launches += 1;
   if (d_val) {
     CK(cudaMemcpyAsync(d_val, ctx->d_dval, sizeof(double) * ctx->nnz,
@@ -637,9 +690,12 @@ nolsm_status nolsm_band_energy(nolsm_ctx* ctx, double* e_out) {
   if (!ctx || !e_out) return NOLSM_EINVAL;
   if (ctx->sticky != NOLSM_OK) return ctx->sticky;
   if (!ctx->have_density) return fail(ctx, NOLSM_ENOTBUILT, "nolsm_density has not run");
+  CK(phase_mark(ctx, NOLSM_PHASE_ENERGY));
   CK(launch_band_energy(ctx));
+  CK(phase_mark(ctx, -1));
   ctx->n_launches += 2;
   nolsm_status st = check_device_flags(ctx);
+  harvest_phases(ctx);
   if (st != NOLSM_OK) return st;
   *e_out = ctx->opt.spin_factor * ctx->h_flags->energy;
   return NOLSM_OK;
@@ -701,6 +757,16 @@ nolsm_status nolsm_counters(nolsm_ctx* ctx, int64_t* launches, int64_t* gemm_lau
     ctx->n_launches = ctx->n_gemm = 0;
     ctx->gemm_ms = ctx->gemm_flops = 0.0;
   }
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_phase_times(nolsm_ctx* ctx, double* ms, int32_t n, int32_t reset) {
+  if (!ctx || n < 0 || n > NOLSM_NUM_PHASES || (n > 0 && !ms)) return NOLSM_EINVAL;
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return NOLSM_ECUDA;
+  harvest_phases(ctx);
+  for (int32_t p = 0; p < n; ++p) ms[p] = ctx->phase_ms[p];
+  if (reset)
+    for (double& v : ctx->phase_ms) v = 0.0;
   return NOLSM_OK;
 }
 

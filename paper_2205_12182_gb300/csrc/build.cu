@@ -625,19 +625,24 @@ cudaError_t launch_gather(nolsm_ctx* ctx, float* hb, double* sb) {
 cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode) {
   // sb holds T_b(S) in FP64 (first sum_sq doubles); the second half is scratch.
   float* s32 = reinterpret_cast<float*>(sb + ctx->sum_sq);   // FP32 factor lives in the scratch half
+  cudaError_t e = cudaSuccess;
   if (mode == NOLSM_CHOL_DF64) {
     cholesky_df_kernel<<<ctx->n_blocks, kCholWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, ctx->d_flags);
+    if ((e = phase_mark(ctx, NOLSM_PHASE_INVERSE)) != cudaSuccess) return e;
     trinv_kernel<float, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
   } else if (mode == NOLSM_CHOL_FP64_INV64) {
     cholesky_kernel<double, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, sb, nullptr, ctx->d_flags);
+    if ((e = phase_mark(ctx, NOLSM_PHASE_INVERSE)) != cudaSuccess) return e;
     trinv_kernel<double, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, sb, sb + ctx->sum_sq);
     to_f32_kernel<double><<<sq_grid(ctx->n_blocks), 256, 0, ctx->stream>>>(ctx->d_blocks, sb + ctx->sum_sq, ctx->d_linv, 1);
   } else if (mode == NOLSM_CHOL_FP64) {
     cholesky_kernel<double, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, ctx->d_flags);
+    if ((e = phase_mark(ctx, NOLSM_PHASE_INVERSE)) != cudaSuccess) return e;
     trinv_kernel<float, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
   } else {
     to_f32_kernel<double><<<sq_grid(ctx->n_blocks), 256, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, 0);
     cholesky_kernel<float, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, s32, nullptr, ctx->d_flags);
+    if ((e = phase_mark(ctx, NOLSM_PHASE_INVERSE)) != cudaSuccess) return e;
     trinv_kernel<float, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
   }
   return cudaGetLastError();

@@ -156,6 +156,15 @@ struct nolsm_ctx {
   double gemm_ms = 0.0;
   double gemm_flops = 0.0;
   std::vector<cudaEvent_t> gemm_ev;     // pairs, reused
+  struct PhaseRec {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  std::vector<PhaseRec> ph_pending;     // recorded stage intervals not yet read back
+  std::vector<cudaEvent_t> ev_free;     // idle events for the stage timers
+  int ph_open = -1;
+  cudaEvent_t ph_open_ev = nullptr;
+  double phase_ms[NOLSM_NUM_PHASES] = {};
   int gemm_ev_used = 0;
 
   // spectral bounds beyond Gershgorin
@@ -178,6 +187,10 @@ namespace nolsm {
 // error helpers (api.cu)
 nolsm_status fail(nolsm_ctx* ctx, nolsm_status st, const std::string& msg);
 double unit_roundoff(const nolsm_ctx* ctx);   // of the iterate's storage format
+// Stage timers (nolsm_phase_times): phase_mark(ctx, p) closes the open stage, if any, and opens p
+// (p < 0: close only); events are read back by harvest_phases once the stream has drained.
+cudaError_t phase_mark(nolsm_ctx* ctx, int phase);
+void harvest_phases(nolsm_ctx* ctx);
 
 // Smallest lower bound l the scaled iteration may assume: one scaled step maps an eigenvalue at 1 to
 // about 2.6 l, which must stay clear of the format's rounding of the iterate (about u), so l >= 2 u
