@@ -286,10 +286,23 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
   double(*diag)[33] = reinterpret_cast<double(*)[33]>(&red[0][0][0]);
   double(*dinv)[33] = reinterpret_cast<double(*)[33]>(&red[0][0][0] + 32 * 33);
   if (tid == 0) s_bad = 0;
+  // in-place conversions of the lower triangle, four independent loads in flight per thread
   for (int r = warp; r < n; r += kCholWarps)
-    for (int c = lane; c <= r; c += 32) {
-      const df32 v = df_from_bits(A[(int64_t)r * ld + c]);
-      A[(int64_t)r * ld + c] = make_float2(v.h, v.l);
+    for (int c0 = 0; c0 <= r; c0 += 128) {
+      float2 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + 32 * u + lane;
+        if (c <= r) v[u] = A[(int64_t)r * ld + c];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + 32 * u + lane;
+        if (c <= r) {
+          const df32 d = df_from_bits(v[u]);
+          A[(int64_t)r * ld + c] = make_float2(d.h, d.l);
+        }
+      }
     }
   __syncthreads();
   // rows [row0, row0 + 32) x columns [col0, col0 + 32) of the pair matrix into a 32x32 chunk
@@ -302,9 +315,9 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
       else dst[r][c] = {0.f, 0.f};
     }
   };
-  // the four warps' partial tiles (in red) summed into the pairs at rows r0.., columns j0..
-  // (add = true: onto the stored value; false: replacing it), lower triangle and c < jb only
-  auto reduce_store = [&](int r0, int j0, int jb, bool add) {
+  // the four warps' partial tiles (in red) summed and stored as pairs at rows r0.., columns j0..
+  // (lower triangle and c < jb only)
+  auto reduce_store = [&](int r0, int j0, int jb) {
     __syncthreads();
     for (int e = tid; e < 1024; e += kCholWarps * 32) {
       const int r = e >> 5, c = e & 31;
@@ -313,12 +326,7 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
         df32 v = red[0][r][c];
 #pragma unroll
         for (int w = 1; w < kCholWarps; ++w) v = df_add(v, red[w][r][c]);
-        if (add) {
-          const float2 s0 = A[(int64_t)gr * ld + j0 + c];
-          v = df_add({s0.x, s0.y}, v);
-        } else {
-          v = df_norm(v);
-        }
+        v = df_norm(v);
         A[(int64_t)gr * ld + j0 + c] = make_float2(v.h, v.l);
       }
     }
@@ -331,9 +339,16 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
     const int nch = j0 / 32;
     if (nch > 0) {
       for (int r0 = j0; r0 < n; r0 += 32) {
+        // warp 0 starts from S itself (its loads overlap the first chunk's copies), the others from 0
         df32 acc[32];
 #pragma unroll
-        for (int r = 0; r < 32; ++r) acc[r] = {0.f, 0.f};
+        for (int r = 0; r < 32; ++r) {
+          acc[r] = {0.f, 0.f};
+          if (warp == 0 && r0 + r < n && lane < jb && j0 + lane <= r0 + r) {
+            const float2 s0 = A[(int64_t)(r0 + r) * ld + j0 + lane];
+            acc[r] = {s0.x, s0.y};
+          }
+        }
         load_chunk(As[0], r0, 0);
         load_chunk(Bs[0], j0, 0);
         cp_async_commit();
@@ -358,7 +373,7 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
         }
 #pragma unroll
         for (int r = 0; r < 32; ++r) red[warp][r][lane] = acc[r];
-        reduce_store(r0, j0, jb, true);
+        reduce_store(r0, j0, jb);
       }
     }
     // 2. diagonal block in FP64 (warp 0, lane = row), then its inverse (lane = column)
@@ -423,25 +438,38 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
       __syncthreads();
 #pragma unroll
       for (int r = 0; r < 32; ++r) red[warp][r][lane] = acc[r];
-      reduce_store(r0, j0, jb, false);
+      reduce_store(r0, j0, jb);
     }
   }
-  // 4. back to FP64 (lower triangle), and the FP32 copy of the factor
+  // 4. back to FP64 (lower triangle) and the FP32 copy of the factor (zero above the diagonal and on
+  //    the padding); the conversion issues four independent loads at a time
   for (int r = warp; r < n; r += kCholWarps)
-    for (int c = lane; c <= r; c += 32) {
-      const float2 s = A[(int64_t)r * ld + c];
-      A[(int64_t)r * ld + c] = df_to_bits({s.x, s.y});
+    for (int c0 = 0; c0 <= r; c0 += 128) {
+      float2 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + 32 * u + lane;
+        if (c <= r) v[u] = A[(int64_t)r * ld + c];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + 32 * u + lane;
+        if (c <= r) A[(int64_t)r * ld + c] = df_to_bits({v[u].x, v[u].y});
+      }
     }
   if (l32) {
     float* Lf = l32 + bd.off_mat;
     for (int r = warp; r < ld; r += kCholWarps)
-      for (int c = lane; c < ld; c += 32) {
-        float v = 0.f;
-        if (r < n && c <= r) {
-          const float2 s = A[(int64_t)r * ld + c];
-          v = (float)__hiloint2double(__float_as_int(s.y), __float_as_int(s.x));
+      for (int c0 = 0; c0 < ld; c0 += 128) {
+        float2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c = c0 + 32 * u + lane;
+          v[u] = (r < n && c <= r) ? A[(int64_t)r * ld + c] : make_float2(0.f, 0.f);
         }
-        Lf[(int64_t)r * ld + c] = v;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          Lf[(int64_t)r * ld + c0 + 32 * u + lane] = (float)__hiloint2double(__float_as_int(v[u].y), __float_as_int(v[u].x));
       }
   }
   if (tid == 0 && s_bad) set_error(flags, NOLSM_ENOTPD);
@@ -520,6 +548,121 @@ __global__ void __launch_bounds__(NW * 32) trinv_kernel(const BlockDesc* __restr
       if (j < ncols)
         for (int r = 0; r < ibw; ++r) X[(int64_t)(i0 + r) * ld + j] = ch.a[r][lane];
       __syncwarp();
+    }
+    __syncthreads();
+  }
+}
+
+// L^-1 in FP32 by block rows of 32, one CTA of four warps per block:
+//   X_ii = L_ii^-1 (32 x 32, one warp, column-parallel forward substitution with reciprocals),
+//   X_ic = -X_ii R_ic,  R_ic = sum_{k=c}^{i-1} L_ik X_kc  for every column block c < i.
+// Each 32 x 32 product R_ic is shared by the four warps over k (8 of every 32; no warp idles when
+// a block row has few column blocks), operand chunks double-buffered in shared memory with cp.async,
+// the four partial tiles summed in shared memory (which also makes the k-sum two-level).
+constexpr int kInvWarps = 4;
+
+__device__ __forceinline__ void cp_async16_b(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+}
+
+__global__ void __launch_bounds__(kInvWarps * 32, 4) trinv_tile_kernel(const BlockDesc* __restrict__ blocks,
+                                                                       const float* __restrict__ lpool,
+                                                                       float* __restrict__ xpool) {
+  __shared__ __align__(16) float As[2][32][32];   // L_ik chunk, read as broadcasts
+  __shared__ __align__(16) float Bs[2][32][32];   // X_kc chunk, row k contiguous
+  __shared__ float red[kInvWarps][32][32];
+  __shared__ float Xi[32][33];
+  __shared__ float Li[32][33];
+  __shared__ float rli[32];
+  const BlockDesc bd = blocks[blockIdx.x];
+  const int n = bd.n, ld = bd.n_pad;
+  const float* L = lpool + bd.off_mat;
+  float* X = xpool + bd.off_mat;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // entries never written below: the strict upper triangle and the padding stay zero
+  for (int r = warp; r < ld; r += kInvWarps)
+    for (int c = lane; c < ld; c += 32)
+      if (c > r || r >= n) X[(int64_t)r * ld + c] = 0.f;
+  // rows [row0, row0 + 32) x columns [col0, col0 + 32) of a matrix into a chunk (zero rows >= rows)
+  auto load_chunk = [&](float(*dst)[32], const float* src, int row0, int col0, int rows) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int e = tid + i * kInvWarps * 32;   // 256 16-byte pieces
+      const int r = e >> 3, c4 = (e & 7) * 4;
+      if (row0 + r < rows) cp_async16_b(&dst[r][c4], src + (int64_t)(row0 + r) * ld + col0 + c4);
+      else *reinterpret_cast<float4*>(&dst[r][c4]) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  const int kw = warp * (32 / kInvWarps);
+  const int nbk = (n + 31) / 32;
+  __syncthreads();
+  for (int ib = 0; ib < nbk; ++ib) {
+    const int i0 = ib * 32, ibw = min(32, n - i0);
+    // X_ii = L_ii^-1: lane = column, forward substitution (identity on the padding)
+    if (warp == 0) {
+      for (int r = 0; r < 32; ++r)
+        Li[r][lane] = (r < ibw && lane < ibw && lane <= r) ? L[(int64_t)(i0 + r) * ld + i0 + lane] : (r == lane ? 1.f : 0.f);
+      __syncwarp();
+      rli[lane] = 1.f / Li[lane][lane];
+      __syncwarp();
+      for (int r = 0; r < 32; ++r) {
+        float v = (r == lane) ? 1.f : 0.f;
+        if (r > lane)
+          for (int q = lane; q < r; ++q) v = fmaf(-Li[r][q], Xi[q][lane], v);
+        Xi[r][lane] = (r >= lane) ? v * rli[r] : 0.f;
+      }
+    }
+    __syncthreads();
+    for (int cb = 0; cb < ib; ++cb) {
+      const int c0 = cb * 32;
+      float acc[32];
+#pragma unroll
+      for (int r = 0; r < 32; ++r) acc[r] = 0.f;
+      const int nch = ib - cb;               // chunks k0 = c0, ..., i0 - 32 (X_kc = 0 for k < c)
+      load_chunk(As[0], L, i0, c0, n);
+      load_chunk(Bs[0], X, c0, c0, n);
+      cp_async_commit();
+      for (int ch = 0; ch < nch; ++ch) {
+        const int buf = ch & 1;
+        if (ch + 1 < nch) {
+          const int k1 = c0 + (ch + 1) * 32;
+          load_chunk(As[buf ^ 1], L, i0, k1, n);
+          load_chunk(Bs[buf ^ 1], X, k1, c0, n);
+          cp_async_commit();
+          cp_async_wait_group<1>();
+        } else {
+          cp_async_wait_group<0>();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 32 / kInvWarps; ++kk) {
+          const float bv = Bs[buf][kw + kk][lane];
+#pragma unroll
+          for (int r = 0; r < 32; ++r) acc[r] = fmaf(As[buf][r][kw + kk], bv, acc[r]);
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int r = 0; r < 32; ++r) red[warp][r][lane] = acc[r];
+      __syncthreads();
+      // R = sum of the four partials (into red[0]), then X_ic = -X_ii R
+      for (int e = tid; e < 1024; e += kInvWarps * 32) {
+        const int r = e >> 5, c = e & 31;
+        red[0][r][c] = (red[0][r][c] + red[1][r][c]) + (red[2][r][c] + red[3][r][c]);
+      }
+      __syncthreads();
+      for (int j = 0; j < 8; ++j) {
+        const int r = warp + kInvWarps * j;
+        float v = 0.f;
+        for (int k = 0; k <= r; ++k) v = fmaf(Xi[r][k], red[0][k][lane], v);
+        if (r < ibw) X[(int64_t)(i0 + r) * ld + c0 + lane] = -v;
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < 1024; e += kInvWarps * 32) {
+      const int r = e >> 5, c = e & 31;
+      if (r < ibw && c <= r) X[(int64_t)(i0 + r) * ld + i0 + c] = Xi[r][c];
     }
     __syncthreads();
   }
@@ -629,7 +772,7 @@ cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode) {
   if (mode == NOLSM_CHOL_DF64) {
     cholesky_df_kernel<<<ctx->n_blocks, kCholWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, ctx->d_flags);
     if ((e = phase_mark(ctx, NOLSM_PHASE_INVERSE)) != cudaSuccess) return e;
-    trinv_kernel<float, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
+    trinv_tile_kernel<<<ctx->n_blocks, kInvWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
   } else if (mode == NOLSM_CHOL_FP64_INV64) {
     cholesky_kernel<double, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, sb, nullptr, ctx->d_flags);
     if ((e = phase_mark(ctx, NOLSM_PHASE_INVERSE)) != cudaSuccess) return e;
@@ -638,12 +781,12 @@ cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode) {
   } else if (mode == NOLSM_CHOL_FP64) {
     cholesky_kernel<double, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, ctx->d_flags);
     if ((e = phase_mark(ctx, NOLSM_PHASE_INVERSE)) != cudaSuccess) return e;
-    trinv_kernel<float, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
+    trinv_tile_kernel<<<ctx->n_blocks, kInvWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
   } else {
     to_f32_kernel<double><<<sq_grid(ctx->n_blocks), 256, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, 0);
     cholesky_kernel<float, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, s32, nullptr, ctx->d_flags);
     if ((e = phase_mark(ctx, NOLSM_PHASE_INVERSE)) != cudaSuccess) return e;
-    trinv_kernel<float, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
+    trinv_tile_kernel<<<ctx->n_blocks, kInvWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
   }
   return cudaGetLastError();
 }
