@@ -218,6 +218,10 @@ nolsm_status nolsm_block_matrix(const nolsm_ctx* ctx, int32_t b, int32_t which, 
 nolsm_status nolsm_counters(nolsm_ctx* ctx, int64_t* launches, int64_t* gemm_launches, double* gemm_ms,
                             double* gemm_flops, int32_t reset);
 
+/* Replace the poll budget of every device-side wait (nolsm_options.wait_budget) for the calls that
+ * follow; budget >= 1.  A wait that runs out records NOLSM_ETIMEOUT (see nolsm_sign_batch). */
+nolsm_status nolsm_set_wait_budget(nolsm_ctx* ctx, int64_t budget);
+
 /* Stages of the path timed by nolsm_phase_times. */
 typedef enum nolsm_phase {
   NOLSM_PHASE_GATHER = 0,      /* index sets done: dense T_b(H0), T_b(S) from the CSR rows (step 1) */

@@ -142,6 +142,8 @@ void release_pools(nolsm_ctx* ctx) {
   dfree(ctx->d_extra); ctx->d_extra = nullptr;
   dfree(ctx->d_nb); ctx->d_nb = nullptr;
   dfree(ctx->d_tmaps); ctx->d_tmaps = nullptr;
+  dfree(ctx->d_cg_tmaps); ctx->d_cg_tmaps = nullptr;
+  ctx->cg_tmap_cap = 0;
   dfree(ctx->d_sb); ctx->d_sb = nullptr;
   dfree(ctx->d_feat); ctx->d_feat = nullptr;
   dfree(ctx->d_pred); ctx->d_pred = nullptr;
@@ -458,6 +460,7 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   CK(phase_mark(ctx, NOLSM_PHASE_FACTOR));
   CK(launch_cholesky_inverse(ctx, sb, chol_mode));   // marks the inverse stage between its launches
   CK(phase_mark(ctx, NOLSM_PHASE_CONGRUENCE));
+  ctx->cong_simt = !mixed;   // FP32 path: SIMT products with two-level sums; mixed: tensor cores (3 x TF32)
   CK(launch_congruence(ctx, ctx->d_t1));
   CK(phase_mark(ctx, NOLSM_PHASE_BUILD_REST));
   CK(launch_slabs_impl(ctx, chol32 ? (const void*)(sb + ctx->sum_sq) : (const void*)sb, chol32, ctx->d_t1));
@@ -757,6 +760,12 @@ nolsm_status nolsm_counters(nolsm_ctx* ctx, int64_t* launches, int64_t* gemm_lau
     ctx->n_launches = ctx->n_gemm = 0;
     ctx->gemm_ms = ctx->gemm_flops = 0.0;
   }
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_set_wait_budget(nolsm_ctx* ctx, int64_t budget) {
+  if (!ctx || budget < 1) return NOLSM_EINVAL;
+  ctx->opt.wait_budget = budget;
   return NOLSM_OK;
 }
 

@@ -792,7 +792,9 @@ cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode) {
 }
 
 cudaError_t launch_congruence(nolsm_ctx* ctx, float* t1) {
-  // T_b(H0) (FP32) sits in A0's pool.  T1 = L^-1 H_b (H symmetric: NT form), A0 = T1 L^-T.
+  // T_b(H0) (FP32) sits in A0's pool.  T1 = L^-1 H_b (H symmetric: NT form), A0 = T1 L^-T: on the
+  // tensor cores (three TF32 passes) unless the SIMT products are asked for.
+  if (!ctx->cong_simt) return launch_congruence_tc(ctx, t1);
   cudaError_t e = launch_sgemm_nt(ctx, ctx->d_linv, ctx->d_a0, t1, /*a_lower=*/1, /*b_lower=*/0, /*sym=*/0);
   if (e != cudaSuccess) return e;
   // A0 is symmetric: upper tiles only, mirrored stores (exactly symmetric, half the work)

@@ -84,6 +84,9 @@ struct nolsm_ctx {
   int device = 0;
   int num_sms = 0;
   int pair_clusters = 0;        // resident 2-CTA clusters of the persistent product kernel
+  void* d_cg_tmaps = nullptr;   // tensor maps of the congruence kernel (FP32 pools, per bin)
+  size_t cg_tmap_cap = 0;
+  bool cong_simt = false;       // congruence on the SIMT FP32 products (tests compare both)
   nolsm_status sticky = NOLSM_OK;
   std::string last_error;
 
@@ -224,6 +227,7 @@ cudaError_t launch_band_energy(nolsm_ctx* ctx);
 cudaError_t tc_prepare(nolsm_ctx* ctx);
 cudaError_t launch_gemm_tc(nolsm_ctx* ctx, int phase);
 cudaError_t launch_ns_pair(nolsm_ctx* ctx, double mu);
+cudaError_t launch_congruence_tc(nolsm_ctx* ctx, float* t1);
 int tc_tile_n();
 
 // learn.cu

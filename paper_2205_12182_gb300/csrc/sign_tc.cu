@@ -863,6 +863,280 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PAIR_THREADS, 1) ns_
   cluster_sync_all();
 }
 
+// ---------------------------------------------------------------------------------------------
+// The congruence A0 = L^-1 T_b(H0) L^-T on the tensor cores, FP32-accurate by three TF32 passes.
+// A product C = A B^T (both operands row-major, K contiguous) over a tile list of 128 x 128 tiles.
+// Each FP32 operand x is split in shared memory into hi = x rounded to TF32 (exact in TF32) and
+// lo = x - hi (exact in FP32, read as TF32), and every k-step accumulates lo_A hi_B + hi_A lo_B +
+// hi_A hi_B in FP32 tensor memory.  lo keeps 11 bits and lo_A lo_B is dropped, so a product term
+// carries about 2^-21 relative error, ten times FP32's: A0 lands within ~3e-6 of the FP32 result,
+// far below the FP16 rounding of X_0 that the mixed paths apply next (the FP32 path keeps the SIMT
+// products).
+// Roles (320 threads): warp 0 TMA producer (raw 128 x 32 FP32 boxes, 128-byte swizzle), warp 1 MMA
+// issuer (kind::tf32, M = N = 128, K = 8), warps 2..5 split each stage in place (hi over the raw box,
+// lo beside it), warps 6..9 epilogue (TMEM -> registers -> staged 32 x 32 FP32 chunks -> tensor
+// stores; with sym, tiles on or above the diagonal only, each chunk stored twice so that the output
+// is exactly symmetric).  Waits are bounded as in ns_tc_kernel.
+constexpr int CG_TN = 128;
+constexpr int CG_TK = 32;                                   // FP32 elements per 128-byte row
+constexpr int CG_STAGES = 3;
+constexpr int CG_BOX_BYTES = 128 * CG_TK * 4;               // 16 KB
+constexpr int CG_STAGE_BYTES = 4 * CG_BOX_BYTES;            // A hi, B hi, A lo, B lo
+constexpr int CG_EPI_OFF = CG_STAGES * CG_STAGE_BYTES;
+constexpr int CG_EPI_WARP_BYTES = 8192;                     // a 32 x 32 FP32 chunk and its transpose
+constexpr int CG_BAR_OFF = CG_EPI_OFF + 4 * CG_EPI_WARP_BYTES;
+constexpr int CG_SMEM = 1024 + CG_BAR_OFF + 256;
+constexpr int CG_THREADS = 320;
+constexpr int CG_TMEM_COLS = 256;                           // two 128-column accumulators
+static_assert(CG_SMEM <= 227 * 1024, "shared memory of the congruence kernel");
+
+struct CgParams {
+  const Tile* tiles;
+  int n_tiles;
+  const BlockDesc* blocks;
+  const CUtensorMap* tmaps;   // per bin: loads of [L^-1, A0 pool, T1], stores into [L^-1, A0 pool, T1]
+  int map_a, map_b, map_c;    // pools of A, B and the output (0 L^-1, 1 A0 pool, 2 T1)
+  int sym;
+  float* out_pool;
+  DevFlags* flags;
+  long long budget;
+};
+
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// byte offset of (row, byte column) in a 128-byte-row box with the 128-byte swizzle (16-byte unit XOR row % 8)
+__device__ __forceinline__ uint32_t sw128(int row, int colbytes) {
+  return (uint32_t)(row * 128 + ((((colbytes >> 4) ^ (row & 7))) << 4) + (colbytes & 15));
+}
+
+__global__ void __launch_bounds__(CG_THREADS, 1) cong_tc_kernel(const __grid_constant__ CgParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + CG_BAR_OFF);
+  uint64_t* full_bar = bars;                       // [STAGES] TMA landed
+  uint64_t* conv_bar = bars + CG_STAGES;           // [STAGES] split done
+  uint64_t* empty_bar = bars + 2 * CG_STAGES;      // [STAGES] MMA done with the stage
+  uint64_t* tfull_bar = bars + 3 * CG_STAGES;      // [2]
+  uint64_t* tempty_bar = bars + 3 * CG_STAGES + 2; // [2]
+  uint64_t* drain_bar = bars + 3 * CG_STAGES + 4;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * CG_STAGES + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int span = p.n_tiles;
+  const int first = (int)(((int64_t)span * blockIdx.x) / gridDim.x);
+  const int n_local = (int)(((int64_t)span * (blockIdx.x + 1)) / gridDim.x) - first;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < CG_STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&conv_bar[s], 128);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) { mbar_init(&tfull_bar[a], 1); mbar_init(&tempty_bar[a], 128); }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(CG_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const long long budget = p.budget;
+  const long long drain_budget = budget > (1LL << 22) ? budget : (1LL << 22);
+  uint32_t armed = 0, arm_parity = 0;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      bool ok = true;
+      for (int i = 0; i < n_local && ok; ++i) {
+        const Tile tl = p.tiles[first + i];
+        const BlockDesc bd = p.blocks[tl.block];
+        const CUtensorMap* ma = p.tmaps + bd.bin * 6 + p.map_a;
+        const CUtensorMap* mb = p.tmaps + bd.bin * 6 + p.map_b;
+        const int rowbase = bd.pos * bd.n_pad;
+        for (int k0 = 0; k0 < tl.kend; k0 += CG_TK) {
+          if (!mbar_wait(&empty_bar[s], ph ^ 1u, budget, abort_flag)) { ok = false; break; }
+          mbar_expect_tx(&full_bar[s], 2 * CG_BOX_BYTES);
+          uint8_t* st = smem + s * CG_STAGE_BYTES;
+          tma_load_2d(st, ma, &full_bar[s], k0, rowbase + tl.m0);
+          tma_load_2d(st + CG_BOX_BYTES, mb, &full_bar[s], k0, rowbase + tl.n0);
+          armed |= 1u << s;
+          arm_parity = (arm_parity & ~(1u << s)) | (ph << s);
+          if (++s == CG_STAGES) { s = 0; ph ^= 1u; }
+        }
+      }
+      if (!ok) {
+        set_error(p.flags, NOLSM_ETIMEOUT);
+        *abort_flag = 1;
+      }
+      volatile int never = 0;
+      for (int st = 0; st < CG_STAGES; ++st)
+        if (armed & (1u << st)) mbar_wait(&full_bar[st], (arm_parity >> st) & 1u, drain_budget, &never);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0, tph[2] = {0u, 0u};
+      int acc = 0;
+      bool ok = true;
+      // kind::tf32: FP32 accumulator (bit 4), A and B TF32 (format 2), both K-major, N >> 3, M >> 4
+      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(CG_TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+      for (int i = 0; i < n_local && ok; ++i) {
+        const Tile tl = p.tiles[first + i];
+        if (!mbar_wait(&tempty_bar[acc], tph[acc] ^ 1u, budget, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * CG_TN);
+        for (int k0 = 0; k0 < tl.kend; k0 += CG_TK) {
+          if (!mbar_wait(&conv_bar[s], ph, budget, abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t base = smem_u32(smem + s * CG_STAGE_BYTES);
+          const uint64_t ah = sw128_desc(base), bh = sw128_desc(base + CG_BOX_BYTES);
+          const uint64_t al = sw128_desc(base + 2 * CG_BOX_BYTES), bl = sw128_desc(base + 3 * CG_BOX_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < CG_TK / 8; ++kk) {
+            const uint64_t o = (uint64_t)(kk * 2);   // 8 FP32 = 32 bytes along K inside the swizzle atom
+            umma_tf32(d_tmem, al + o, bh + o, idesc, (k0 | kk) != 0);
+            umma_tf32(d_tmem, ah + o, bl + o, idesc, 1u);
+            umma_tf32(d_tmem, ah + o, bh + o, idesc, 1u);
+          }
+          umma_commit(&empty_bar[s]);
+          if (++s == CG_STAGES) { s = 0; ph ^= 1u; }
+        }
+        if (!ok) break;
+        umma_commit(&tfull_bar[acc]);
+        tph[acc] ^= 1u;
+        acc ^= 1;
+      }
+      if (!ok) {
+        set_error(p.flags, NOLSM_ETIMEOUT);
+        *abort_flag = 1;
+      }
+      umma_commit(drain_bar);
+      volatile int never = 0;
+      mbar_wait(drain_bar, 0, drain_budget, &never);
+    }
+  } else if (warp < 6) {
+    // ------------------------------------------------------------------ split: hi in place, lo beside it
+    const int ct = threadIdx.x - 64;            // 0..127
+    int s = 0;
+    uint32_t ph = 0;
+    for (int i = 0; i < n_local; ++i) {
+      const Tile tl = p.tiles[first + i];
+      bool ok = true;
+      for (int k0 = 0; k0 < tl.kend; k0 += CG_TK) {
+        if (!mbar_wait(&full_bar[s], ph, budget, abort_flag)) { ok = false; break; }
+        uint8_t* st = smem + s * CG_STAGE_BYTES;
+        // 2 boxes x 16 KB = 2048 float4; 16 per thread (position-wise, so the swizzle is irrelevant)
+#pragma unroll 4
+        for (int j = 0; j < 16; ++j) {
+          const int e = ct + 128 * j;           // float4 index over A hi (0..1023) then B hi (1024..2047)
+          float4* hp = reinterpret_cast<float4*>(st) + e;
+          float4* lp = reinterpret_cast<float4*>(st + 2 * CG_BOX_BYTES) + e;
+          const float4 x = *hp;
+          // hi: x rounded to the nearest TF32 (add half of the dropped range, clear it), exact in TF32
+          float4 h, l;
+          h.x = __uint_as_float((__float_as_uint(x.x) + 0x1000u) & 0xFFFFE000u); l.x = x.x - h.x;
+          h.y = __uint_as_float((__float_as_uint(x.y) + 0x1000u) & 0xFFFFE000u); l.y = x.y - h.y;
+          h.z = __uint_as_float((__float_as_uint(x.z) + 0x1000u) & 0xFFFFE000u); l.z = x.z - h.z;
+          h.w = __uint_as_float((__float_as_uint(x.w) + 0x1000u) & 0xFFFFE000u); l.w = x.w - h.w;
+          *hp = h;
+          *lp = l;
+        }
+        fence_async_smem();
+        mbar_arrive(&conv_bar[s]);
+        if (++s == CG_STAGES) { s = 0; ph ^= 1u; }
+      }
+      if (!ok) {
+        set_error(p.flags, NOLSM_ETIMEOUT);
+        *abort_flag = 1;
+        break;
+      }
+    }
+  } else {
+    // ------------------------------------------------------------------ epilogue (warps 6..9)
+    const int q = warp & 3;
+    uint8_t* stage = smem + CG_EPI_OFF + (warp - 6) * CG_EPI_WARP_BYTES;
+    uint32_t tph[2] = {0u, 0u};
+    int acc = 0;
+    for (int i = 0; i < n_local; ++i) {
+      const Tile tl = p.tiles[first + i];
+      const BlockDesc bd = p.blocks[tl.block];
+      if (!__all_sync(0xffffffffu, mbar_wait(&tfull_bar[acc], tph[acc], budget, abort_flag))) {
+        set_error(p.flags, NOLSM_ETIMEOUT);
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const int ld = bd.n_pad, rowbase = bd.pos * ld;
+      const CUtensorMap* smap = p.tmaps + bd.bin * 6 + 3 + p.map_c;
+      float* out = p.out_pool + bd.off_mat;
+      const int r0 = tl.m0 + q * 32, r = r0 + lane;
+      for (int c0 = 0; c0 < CG_TN; c0 += 32) {
+        const int cg0 = tl.n0 + c0;
+        uint32_t v[32];
+        tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * CG_TN + c0), v);
+        if (p.sym && cg0 < r0) continue;        // below the diagonal: the mirror of another chunk
+        if (p.sym && cg0 == r0) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const float x = __uint_as_float(v[j]);
+            if (cg0 + j >= r) out[(int64_t)r * ld + cg0 + j] = x;
+            if (cg0 + j > r) out[(int64_t)(cg0 + j) * ld + r] = x;
+          }
+          continue;
+        }
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        __syncwarp();
+        uint8_t* D = stage;
+        uint8_t* M = stage + 4096;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          *reinterpret_cast<uint4*>(D + sw128(lane, 16 * u)) = make_uint4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+        if (p.sym) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) *reinterpret_cast<uint32_t*>(M + sw128(j, 4 * lane)) = v[j];
+        }
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          tma_store_2d(smap, D, cg0, rowbase + r0);
+          if (p.sym) tma_store_2d(smap, M, r0, rowbase + cg0);
+          bulk_commit();
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&tempty_bar[acc]);
+      tph[acc] ^= 1u;
+      acc ^= 1;
+    }
+    if (lane == 0) bulk_wait0();
+    __syncwarp();
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(CG_TMEM_COLS) : "memory");
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -966,6 +1240,89 @@ cudaError_t launch_gemm_tc(nolsm_ctx* ctx, int phase) {
     else
       ns_tc_kernel<__half><<<grid, NUM_THREADS, SMEM_TOTAL, ctx->stream>>>(p);
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// The congruence on the tensor cores: T1 = L^-1 T_b(H0) (all tiles; L^-1 is lower triangular, so a
+// tile's K stops at m0 + 128), then A0 = T1 L^-T (tiles on or above the diagonal, K stops at
+// n0 + 128, output mirrored).  Tensor maps over the FP32 pools are encoded here, per bin.
+cudaError_t launch_congruence_tc(nolsm_ctx* ctx, float* t1) {
+  auto encode = get_encode();
+  if (!encode) return cudaErrorNotSupported;
+  int n_bins = 0;
+  for (const auto& b : ctx->h_blocks) n_bins = std::max(n_bins, b.bin + 1);
+  std::vector<int64_t> bin_off(n_bins, -1), bin_cnt(n_bins, 0);
+  std::vector<int> bin_pad(n_bins, 0);
+  for (const auto& b : ctx->h_blocks) {
+    if (b.pos == 0) bin_off[b.bin] = b.off_mat;
+    bin_cnt[b.bin] += 1;
+    bin_pad[b.bin] = b.n_pad;
+  }
+  std::vector<CUtensorMap> maps((size_t)n_bins * 6);
+  float* pools[3] = {ctx->d_linv, ctx->d_a0, t1};
+  for (int bi = 0; bi < n_bins; ++bi)
+    for (int pi = 0; pi < 3; ++pi) {
+      const uint64_t np = (uint64_t)bin_pad[bi];
+      void* base = pools[pi] + bin_off[bi];
+      cuuint64_t gdim[2] = {np, np * (uint64_t)bin_cnt[bi]};
+      cuuint64_t gstride[1] = {np * 4};
+      cuuint32_t estr[2] = {1, 1};
+      cuuint32_t box[2] = {CG_TK, TM};
+      CUresult r = encode(&maps[(size_t)bi * 6 + pi], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, gdim, gstride, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+      cuuint32_t sbox[2] = {32, 32};
+      r = encode(&maps[(size_t)bi * 6 + 3 + pi], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, gdim, gstride, sbox, estr,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+  if (ctx->cg_tmap_cap < maps.size()) {
+    if (ctx->d_cg_tmaps) cudaFree(ctx->d_cg_tmaps);
+    ctx->d_cg_tmaps = nullptr;
+    cudaError_t e = cudaMalloc(&ctx->d_cg_tmaps, maps.size() * sizeof(CUtensorMap));
+    if (e != cudaSuccess) return e;
+    ctx->cg_tmap_cap = maps.size();
+  }
+  cudaError_t e = cudaMemcpyAsync(ctx->d_cg_tmaps, maps.data(), maps.size() * sizeof(CUtensorMap),
+                                  cudaMemcpyHostToDevice, ctx->stream);
+  if (e != cudaSuccess) return e;
+  static bool attr_done = false;
+  if (!attr_done) {
+    e = cudaFuncSetAttribute(cong_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CG_SMEM);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  for (int pass = 0; pass < 2; ++pass) {
+    std::vector<Tile> tl;
+    for (int32_t i = 0; i < ctx->n_blocks; ++i) {
+      const BlockDesc& bd = ctx->h_blocks[i];
+      for (int m0 = 0; m0 < bd.n_pad; m0 += TM)
+        for (int n0 = pass ? m0 : 0; n0 < bd.n_pad; n0 += CG_TN)
+          tl.push_back(Tile{i, m0, n0, std::min(bd.n_pad, (pass ? n0 : m0) + TM)});
+    }
+    if ((int64_t)tl.size() > ctx->max_tiles) return cudaErrorInvalidValue;
+    e = cudaMemcpyAsync(ctx->d_tiles, tl.data(), tl.size() * sizeof(Tile), cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(ctx->stream);   // tl is a host temporary
+    if (e != cudaSuccess) return e;
+    CgParams p;
+    p.tiles = ctx->d_tiles;
+    p.n_tiles = (int)tl.size();
+    p.blocks = ctx->d_blocks;
+    p.tmaps = reinterpret_cast<const CUtensorMap*>(ctx->d_cg_tmaps);
+    p.map_a = pass ? 2 : 0;                   // T1 : L^-1
+    p.map_b = pass ? 0 : 1;                   // L^-1 : T_b(H0) in the A0 pool
+    p.map_c = pass ? 1 : 2;                   // A0 pool : T1
+    p.sym = pass;
+    p.out_pool = pass ? ctx->d_a0 : t1;
+    p.flags = ctx->d_flags;
+    p.budget = ctx->opt.wait_budget;
+    cong_tc_kernel<<<ctx->num_sms, CG_THREADS, CG_SMEM, ctx->stream>>>(p);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

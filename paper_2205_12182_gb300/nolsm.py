@@ -25,7 +25,8 @@ SCHEDULE_PERSISTENT, SCHEDULE_PER_PRODUCT = 0, 1
 
 FUNCTIONS = ["nolsm_default_options", "nolsm_create", "nolsm_build_submatrices", "nolsm_sign_batch", "nolsm_set_mu",
              "nolsm_density", "nolsm_band_energy", "nolsm_block_info", "nolsm_block_index_set", "nolsm_block_bounds",
-             "nolsm_block_state", "nolsm_block_matrix", "nolsm_counters", "nolsm_phase_times", "nolsm_band_energy_noalloc",
+             "nolsm_block_state", "nolsm_block_matrix", "nolsm_counters", "nolsm_phase_times", "nolsm_set_wait_budget",
+             "nolsm_band_energy_noalloc",
              "nolsm_block_features", "nolsm_block_lanczos", "nolsm_mlp_create", "nolsm_mlp_get_params",
              "nolsm_mlp_gradient", "nolsm_mlp_adam", "nolsm_mlp_predict", "nolsm_mlp_destroy", "nolsm_set_predictor",
              "nolsm_last_error", "nolsm_destroy"]
@@ -89,6 +90,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "nolsm_counters": (i32, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), pf64, pf64, i32]),
         "nolsm_band_energy_noalloc": (i32, [i64, P, P, f64, P, P]),
         "nolsm_phase_times": (i32, [P, pf64, i32, i32]),
+        "nolsm_set_wait_budget": (i32, [P, i64]),
         "nolsm_block_features": (i32, [P, f64, P]),
         "nolsm_block_lanczos": (i32, [P, i32, i32, P]),
         "nolsm_mlp_create": (i32, [C.POINTER(P), P, P, P]),
@@ -203,6 +205,11 @@ def nolsm_block_matrix(ctx, b, which=0) -> np.ndarray:
     out = np.empty((n, n), np.float32)
     _check(ctx, _lib.nolsm_block_matrix(ctx, int(b), int(which), out.ctypes.data))
     return out
+
+
+def nolsm_set_wait_budget(ctx, budget):
+    """Poll budget of every device-side wait for the calls that follow."""
+    _check(ctx, _lib.nolsm_set_wait_budget(ctx, int(budget)))
 
 
 def nolsm_phase_times(ctx, reset=False) -> dict:
@@ -396,6 +403,9 @@ class Nolsm:
 
     def phase_times(self, reset=False):
         return nolsm_phase_times(self.ctx, reset)
+
+    def set_wait_budget(self, budget):
+        nolsm_set_wait_budget(self.ctx, budget)
 
     def block_matrix(self, b, which=0):
         return nolsm_block_matrix(self.ctx, b, which)

@@ -82,11 +82,15 @@ def test_bad_pattern_rejected(nl, sys1):
     assert e.value.status == nl.EINVAL
 
 
-def test_device_wait_budget_runs_out(nl, sys1):
-    """A one-poll budget on the tensor-core kernel's mbarrier waits: the kernel records ETIMEOUT,
-    drains its own copies and products, frees tensor memory and returns; the context recovers."""
-    lib = nl.Nolsm(precision=nl.PREC_MIXED_FP16, wait_budget=1).build(sys1)
+@pytest.mark.parametrize("stage", ["build", "sign"])
+def test_device_wait_budget_runs_out(nl, sys1, stage):
+    """A one-poll budget on the tensor-core kernels' mbarrier waits (the congruence in the build, the
+    Newton-Schulz products in the sign evaluation): the kernel records ETIMEOUT, drains its own copies
+    and products, frees tensor memory and returns; the context recovers."""
+    lib = nl.Nolsm(precision=nl.PREC_MIXED_FP16, wait_budget=1 if stage == "build" else 1 << 22)
     with pytest.raises(nl.NolsmError) as e:
+        lib.build(sys1)
+        lib.set_wait_budget(1)
         lib.sign_batch(-0.45)
     assert e.value.status == nl.ETIMEOUT
     torch.cuda.synchronize()

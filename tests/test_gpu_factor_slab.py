@@ -2,6 +2,8 @@
 
 * the Cholesky factor of T_b(S) in every mode against LAPACK's FP64 factor (numpy.linalg.cholesky);
 * the double-float factor and the FP64 one give the same FP32 factor, L^-1 and A0;
+* A0 (tensor-core congruence with three TF32 passes on the mixed path, SIMT FP32 on the FP32 path)
+  against L^-1 T_b(H0) L^-T in FP64 from the library's own L^-1 and the block's H;
 * blocks too large for the shared-memory-resident slab kernel (n_pad 640 in the FP32 path, 896 in
   the mixed path) run through the one-CTA slab kernel and keep the parity bar; blocks of n_pad 512
   in the FP32 path run through the resident kernel with compensated sums.
@@ -90,3 +92,19 @@ def test_fp32_path_blocks_beyond_resident_slab(nl):
 def test_mixed_path_blocks_beyond_resident_slab(nl):
     s = water_box(8, seed=5, neighbourhood=10.0)        # n_b ~850, n_pad 896
     assert _sampled_parity(nl, s, nl.PREC_MIXED_FP16, 6) <= 1e-3
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_congruence_matches_fp64_product(nl, sys1, orc1, precision):
+    prec = nl.PREC_FP32 if precision == "fp32" else nl.PREC_MIXED_FP16
+    lib = nl.Nolsm(precision=prec).build(sys1)
+    for b in [0, 9, 40, 63]:
+        _, hb, _ = orc1.submatrices(b)
+        li = lib.block_matrix(b, 1).astype(np.float64)
+        ref = li @ hb.astype(np.float32).astype(np.float64) @ li.T
+        a0 = lib.block_matrix(b, 0).astype(np.float64)
+        np.testing.assert_array_equal(a0, a0.T)              # exactly symmetric
+        # FP32 path: SIMT FP32 products; mixed path: three TF32 passes (~2^-21 per product term,
+        # two products, ~200-term sums)
+        tol = 1e-6 if precision == "fp32" else 1e-5
+        assert np.abs(a0 - ref).max() <= tol * np.abs(ref).max()
