@@ -98,6 +98,16 @@ typedef enum nolsm_schedule {
                                      iteration driven from the host */
 } nolsm_schedule;
 
+/* Where the refinement steps on the own-column slab run on the mixed-precision paths (the FP32 path
+ * always uses the SIMT kernels). */
+typedef enum nolsm_refine_path {
+  NOLSM_REFINE_TENSOR = 0,  /* tensor cores: X in its FP16/BF16 storage times the FP32 slab split into
+                               two FP16/BF16 terms (hi + lo), FP32 accumulation; one persistent CTA per
+                               block (and 192-column piece of its own columns) runs the whole chain */
+  NOLSM_REFINE_SIMT = 1     /* FP32 SIMT products (blocks resident in an 8-CTA cluster's shared
+                               memory, one CTA per block beyond that) */
+} nolsm_refine_path;
+
 /* One CSR matrix (see the conventions above). */
 typedef struct nolsm_csr {
   int64_t n;               /* dimension N */
@@ -125,6 +135,7 @@ typedef struct nolsm_options {
   int64_t wait_budget;     /* bound on every device-side spin wait, in polls (default 1<<22) */
   int32_t lanczos_steps;   /* Lanczos steps per block for NOLSM_BOUNDS_LANCZOS (default 24, at most 64) */
   int32_t schedule;        /* nolsm_schedule of the mixed-precision products (default PERSISTENT) */
+  int32_t refine_path;     /* nolsm_refine_path of the mixed-precision paths (default TENSOR) */
 } nolsm_options;
 
 /* Statistics of the last sign evaluation. */

@@ -131,6 +131,7 @@ void release_pools(nolsm_ctx* ctx) {
   dfree(ctx->d_hi); ctx->d_hi = nullptr;
   dfree(ctx->d_bn); ctx->d_bn = nullptr;
   dfree(ctx->d_be); ctx->d_be = nullptr;
+  dfree(ctx->d_slab_units); ctx->d_slab_units = nullptr;
   dfree(ctx->d_resacc); ctx->d_resacc = nullptr;
   dfree(ctx->d_tol); ctx->d_tol = nullptr;
   dfree(ctx->d_state); ctx->d_state = nullptr;
@@ -220,6 +221,7 @@ nolsm_status nolsm_default_options(nolsm_options* opt) {
   opt->wait_budget = 1LL << 22;
   opt->lanczos_steps = 24;
   opt->schedule = NOLSM_SCHEDULE_PERSISTENT;
+  opt->refine_path = NOLSM_REFINE_TENSOR;
   return NOLSM_OK;
 }
 
@@ -234,7 +236,8 @@ nolsm_status nolsm_create(nolsm_ctx** out, const nolsm_options* opt, void* cuda_
       ctx->opt.wait_budget <= 0 || ctx->opt.alpha_margin < 0 || ctx->opt.chol_precision < 0 ||
       ctx->opt.chol_precision > NOLSM_CHOL_DF64 || ctx->opt.bounds < NOLSM_BOUNDS_GERSHGORIN ||
       ctx->opt.bounds > NOLSM_BOUNDS_LEARNED || ctx->opt.lanczos_steps < 1 || ctx->opt.lanczos_steps > 64 ||
-      ctx->opt.schedule < NOLSM_SCHEDULE_PERSISTENT || ctx->opt.schedule > NOLSM_SCHEDULE_PER_PRODUCT) {
+      ctx->opt.schedule < NOLSM_SCHEDULE_PERSISTENT || ctx->opt.schedule > NOLSM_SCHEDULE_PER_PRODUCT ||
+      ctx->opt.refine_path < NOLSM_REFINE_TENSOR || ctx->opt.refine_path > NOLSM_REFINE_SIMT) {
     delete ctx;
     return NOLSM_EINVAL;
   }
@@ -330,10 +333,15 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
     for (int32_t k = blk_ptr[b]; k < blk_ptr[b + 1]; ++k) m += rp[blk_cols[k] + 1] - rp[blk_cols[k]];
     max_cand = std::max(max_cand, m);
   }
-  if (max_cand > kMaxCandidates)
-    return fail(ctx, NOLSM_EINVAL, "a block's own columns and extra list hold more than 32768 entries");
+  // the index-set kernel sorts in shared memory: up to kMaxCandidates entries, compacted to the
+  // distinct rows whenever the next column would overflow (so one column may hold up to
+  // kMaxCandidates - kMaxDim rows)
   int cap = 256;
-  while (cap < max_cand) cap <<= 1;
+  while (cap < max_cand && cap < kMaxCandidates) cap <<= 1;
+  int64_t max_deg = 0;
+  for (int64_t r = 0; r < N; ++r) max_deg = std::max<int64_t>(max_deg, rp[r + 1] - rp[r]);
+  if (max_cand > cap && max_deg > cap - kMaxDim)
+    return fail(ctx, NOLSM_EINVAL, "a row of the pattern holds more than 28672 entries");
 
   // ---- transpose positions, pattern checks and index sets on the device
   CK(dalloc(ctx, &ctx->d_transpose, (size_t)nnz));
@@ -372,7 +380,7 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return pad_dim(nb[a]) < pad_dim(nb[b]); });
   int64_t off_mat = 0, off_slab = 0;
-  int bin = -1, pos = 0, last_pad = -1;
+  int bin = -1, pos = 0, last_pad = -1, slab_row = 0;
   ctx->flops_paper_iter = ctx->flops_exec_iter = 0.0;
   for (int32_t b = 0; b < n_blocks; ++b) {
     BlockDesc& bd = ctx->h_blocks[b];
@@ -387,9 +395,11 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   }
   for (int32_t b : order) {
     BlockDesc& bd = ctx->h_blocks[b];
-    if (bd.n_pad != last_pad) { ++bin; pos = 0; last_pad = bd.n_pad; }
+    if (bd.n_pad != last_pad) { ++bin; pos = 0; slab_row = 0; last_pad = bd.n_pad; }
     bd.bin = bin;
     bd.pos = pos++;
+    bd.slab_row = slab_row;
+    slab_row += bd.c;
     bd.off_mat = off_mat;
     bd.off_slab = off_slab;
     off_mat += (int64_t)bd.n_pad * bd.n_pad;
@@ -405,6 +415,24 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   ctx->max_tiles_tc = 0;
   for (const auto& bd : ctx->h_blocks)
     for (int m0 = 0; m0 < bd.n_pad; m0 += kTile) ctx->max_tiles_tc += (bd.n_pad - m0 + 255) / 256;
+  // pieces of the own columns for the tensor-core refinement (block, first column, width)
+  std::vector<int32_t> units_n, units_w;
+  {
+    std::vector<int32_t> by_size(order.rbegin(), order.rend());   // largest n_pad first
+    for (int32_t b : by_size) {
+      const BlockDesc& bd = ctx->h_blocks[b];
+      for (int c0 = 0; c0 < bd.c; c0 += kSlabWide) {
+        const int cw = std::min(kSlabWide, bd.c - c0);
+        std::vector<int32_t>& dst = cw <= kSlabNarrow ? units_n : units_w;
+        dst.insert(dst.end(), {b, c0, cw, 0});
+      }
+    }
+  }
+  ctx->n_units_narrow = (int32_t)(units_n.size() / 4);
+  ctx->n_units_wide = (int32_t)(units_w.size() / 4);
+  units_n.insert(units_n.end(), units_w.begin(), units_w.end());
+  ctx->h_slab_units.swap(units_n);
+  const int64_t n_units = std::max<int64_t>((int64_t)ctx->h_slab_units.size() / 4, 1);
 
   // ---- device pools
   const bool mixed = is_mixed(ctx);
@@ -422,14 +450,18 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   CK(dalloc(ctx, &ctx->d_tmp, (size_t)std::max<int64_t>(6 * ctx->sum_slab, 4096)));
   CK(dalloc(ctx, &ctx->d_lo, (size_t)n_blocks));
   CK(dalloc(ctx, &ctx->d_hi, (size_t)n_blocks));
-  CK(dalloc(ctx, &ctx->d_bn, (size_t)n_blocks));
-  CK(dalloc(ctx, &ctx->d_be, (size_t)n_blocks));
+  CK(dalloc(ctx, &ctx->d_bn, (size_t)std::max<int64_t>(n_blocks, n_units)));
+  CK(dalloc(ctx, &ctx->d_be, (size_t)std::max<int64_t>(n_blocks, n_units)));
+  CK(dalloc(ctx, &ctx->d_slab_units, (size_t)(4 * n_units)));
   CK(dalloc(ctx, &ctx->d_resacc, (size_t)n_blocks));
   CK(dalloc(ctx, &ctx->d_tol, (size_t)n_blocks));
   CK(dalloc(ctx, &ctx->d_state, (size_t)n_blocks));
   CK(dalloc(ctx, &ctx->d_tiles, (size_t)tiles_max));
   CK(dalloc(ctx, &ctx->d_dval, (size_t)nnz));
   CK(cudaMemcpyAsync(ctx->d_blocks, ctx->h_blocks.data(), sizeof(BlockDesc) * n_blocks, cudaMemcpyHostToDevice, ctx->stream));
+  if (!ctx->h_slab_units.empty())
+    CK(cudaMemcpyAsync(ctx->d_slab_units, ctx->h_slab_units.data(), sizeof(int32_t) * ctx->h_slab_units.size(),
+                       cudaMemcpyHostToDevice, ctx->stream));
   {
     // Full-matrix iterations stop once the own-column refinement can finish the job: an
     // eigenvalue 1 - delta of X goes to about 1 - 1.5 delta^2 under one step of Eq. 6, so r

@@ -37,62 +37,15 @@ __global__ void transpose_kernel(int64_t n, const int64_t* __restrict__ row_ptr,
   }
 }
 
-// One CTA per block: gather the candidate rows into shared memory, bitonic sort, keep the first
-// of every run of equal values.  I_b goes to idx[b * kMaxDim ...], |I_b| to n_out[b], and the
-// local position of own column j to own[blk_ptr[b] + j].  More than kMaxDim distinct rows, or
-// more than cap candidates, is an EINVAL error for the block.
-__global__ void __launch_bounds__(512) index_set_kernel(int64_t n, const int64_t* __restrict__ row_ptr,
-                                                        const int32_t* __restrict__ col,
-                                                        const int32_t* __restrict__ blk_ptr,
-                                                        const int32_t* __restrict__ blk_cols,
-                                                        const int32_t* __restrict__ extra_ptr,
-                                                        const int32_t* __restrict__ extra_idx, int cap,
-                                                        int32_t* __restrict__ idx, int32_t* __restrict__ own,
-                                                        int32_t* __restrict__ n_out, DevFlags* flags) {
-  extern __shared__ int32_t cand[];          // cap entries
-  __shared__ int32_t s_count;
-  __shared__ int32_t warp_tot[16];
-  const int b = blockIdx.x;
+// Sort cand[0, m) ascending (bitonic, padded to a power of two with INT_MAX) and write its distinct
+// values to I (at most kMaxDim of them; the count is returned in full).  The distinct values are then
+// copied back to cand[0, count) so that further candidates can be appended.
+__device__ int sort_unique(int32_t* cand, int m, int32_t* __restrict__ I, int32_t* warp_tot, int32_t* s_base) {
   const int tid = threadIdx.x;
-  if (tid == 0) s_count = 0;
-  __syncthreads();
-  // candidates: the rows of every own column (row c's columns: the pattern is symmetric) + extras
-  const int32_t c0 = blk_ptr[b], c1 = blk_ptr[b + 1];
-  for (int32_t k = c0; k < c1; ++k) {
-    const int32_t c = blk_cols[k];
-    if (c < 0 || c >= n) { if (tid == 0) set_error(flags, NOLSM_EINVAL); continue; }
-    const int64_t e0 = row_ptr[c], e1 = row_ptr[c + 1];
-    const int deg = (int)(e1 - e0);
-    const int base = s_count;
-    __syncthreads();
-    for (int i = tid; i < deg; i += blockDim.x)
-      if (base + i < cap) cand[base + i] = col[e0 + i];
-    __syncthreads();
-    if (tid == 0) s_count = base + deg;
-    __syncthreads();
-  }
-  if (extra_ptr) {
-    const int32_t x0 = extra_ptr[b], x1 = extra_ptr[b + 1];
-    const int base = s_count;
-    for (int i = tid; i < x1 - x0; i += blockDim.x) {
-      const int32_t v = extra_idx[x0 + i];
-      if (v < 0 || v >= n) set_error(flags, NOLSM_EINVAL);
-      if (base + i < cap) cand[base + i] = min(max(v, 0), (int32_t)n - 1);
-    }
-    __syncthreads();
-    if (tid == 0) s_count = base + (x1 - x0);
-    __syncthreads();
-  }
-  const int m = s_count;
-  if (m > cap) {
-    if (tid == 0) { set_error(flags, NOLSM_EINVAL); n_out[b] = 0; }
-    return;
-  }
   int p2 = 1;
   while (p2 < m) p2 <<= 1;
   for (int i = m + tid; i < p2; i += blockDim.x) cand[i] = INT_MAX;
   __syncthreads();
-  // bitonic sort, ascending
   for (int k = 2; k <= p2; k <<= 1)
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int i = tid; i < p2; i += blockDim.x) {
@@ -106,8 +59,7 @@ __global__ void __launch_bounds__(512) index_set_kernel(int64_t n, const int64_t
       __syncthreads();
     }
   // unique: positions by a block-wide scan over chunks of blockDim
-  __shared__ int32_t s_base;
-  if (tid == 0) s_base = 0;
+  if (tid == 0) *s_base = 0;
   __syncthreads();
   const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (int i0 = 0; i0 < m; i0 += blockDim.x) {
@@ -117,27 +69,86 @@ __global__ void __launch_bounds__(512) index_set_kernel(int64_t n, const int64_t
     const int before = __popc(ballot & ((1u << lane) - 1u));
     if (lane == 0) warp_tot[warp] = __popc(ballot);
     __syncthreads();
-    int off = s_base;
+    int off = *s_base;
     for (int w = 0; w < warp; ++w) off += warp_tot[w];
     const int32_t v = (i < m) ? cand[i] : 0;
     __syncthreads();
-    if (keep && off + before < kMaxDim) idx[(int64_t)b * kMaxDim + off + before] = v;
+    if (keep && off + before < kMaxDim) I[off + before] = v;
     if (tid == 0) {
       int t = 0;
       for (int w = 0; w < nw; ++w) t += warp_tot[w];
-      s_base += t;
+      *s_base += t;
     }
     __syncthreads();
   }
-  const int nb = s_base;
-  if (tid == 0) n_out[b] = nb;
+  const int nb = *s_base;
+  for (int i = tid; i < min(nb, kMaxDim); i += blockDim.x) cand[i] = I[i];
+  __syncthreads();
+  return nb;
+}
+
+// One CTA per block: gather the candidate rows into shared memory, bitonic sort, keep the first
+// of every run of equal values.  I_b goes to idx[b * kMaxDim ...], |I_b| to n_out[b], and the
+// local position of own column j to own[blk_ptr[b] + j].  When the next column's rows (or the next
+// piece of the extra list) would overflow the cap entries, the candidates so far are sorted and made
+// distinct first (at most kMaxDim remain).  More than kMaxDim distinct rows, or one column with more
+// than cap - kMaxDim rows, is an EINVAL error for the block.
+__global__ void __launch_bounds__(512) index_set_kernel(int64_t n, const int64_t* __restrict__ row_ptr,
+                                                        const int32_t* __restrict__ col,
+                                                        const int32_t* __restrict__ blk_ptr,
+                                                        const int32_t* __restrict__ blk_cols,
+                                                        const int32_t* __restrict__ extra_ptr,
+                                                        const int32_t* __restrict__ extra_idx, int cap,
+                                                        int32_t* __restrict__ idx, int32_t* __restrict__ own,
+                                                        int32_t* __restrict__ n_out, DevFlags* flags) {
+  extern __shared__ int32_t cand[];          // cap entries
+  __shared__ int32_t warp_tot[16];
+  __shared__ int32_t s_base;
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x;
+  int32_t* I = idx + (int64_t)b * kMaxDim;
+  int m = 0;                                 // block-uniform candidate count
+  bool bad = false;
+  // candidates: the rows of every own column (row c's columns: the pattern is symmetric) + extras
+  const int32_t c0 = blk_ptr[b], c1 = blk_ptr[b + 1];
+  for (int32_t k = c0; k < c1 && !bad; ++k) {
+    const int32_t c = blk_cols[k];
+    if (c < 0 || c >= n) { if (tid == 0) set_error(flags, NOLSM_EINVAL); continue; }
+    const int64_t e0 = row_ptr[c], e1 = row_ptr[c + 1];
+    const int deg = (int)(e1 - e0);
+    if (m + deg > cap) {
+      m = sort_unique(cand, m, I, warp_tot, &s_base);
+      if (m > kMaxDim || m + deg > cap) { bad = true; break; }
+    }
+    for (int i = tid; i < deg; i += blockDim.x) cand[m + i] = col[e0 + i];
+    m += deg;
+    __syncthreads();
+  }
+  if (extra_ptr && !bad) {
+    const int32_t x0 = extra_ptr[b], x1 = extra_ptr[b + 1];
+    for (int32_t s = x0; s < x1 && !bad;) {
+      if (m == cap) {
+        m = sort_unique(cand, m, I, warp_tot, &s_base);
+        if (m >= cap || m > kMaxDim) { bad = true; break; }
+      }
+      const int take = min(x1 - s, cap - m);
+      for (int i = tid; i < take; i += blockDim.x) {
+        const int32_t v = extra_idx[s + i];
+        if (v < 0 || v >= n) set_error(flags, NOLSM_EINVAL);
+        cand[m + i] = min(max(v, 0), (int32_t)n - 1);
+      }
+      m += take;
+      s += take;
+      __syncthreads();
+    }
+  }
+  const int nb = bad ? kMaxDim + 1 : sort_unique(cand, m, I, warp_tot, &s_base);
+  if (tid == 0) n_out[b] = bad ? 0 : nb;
   if (nb > kMaxDim) {
     if (tid == 0) set_error(flags, NOLSM_EINVAL);
     return;
   }
-  __syncthreads();
   // own-column positions (every own column is its own row's diagonal, so it is in I_b)
-  const int32_t* I = idx + (int64_t)b * kMaxDim;
   for (int32_t k = c0 + tid; k < c1; k += blockDim.x) {
     const int32_t c = blk_cols[k];
     int lo = 0, hi = nb;

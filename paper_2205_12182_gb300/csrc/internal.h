@@ -28,6 +28,7 @@ struct BlockDesc {
   int32_t col0;     // offset of the block's own columns in the blk_cols array
   int32_t bin;      // size bin (blocks of one n_pad are stored contiguously, bin by bin)
   int32_t pos;      // position of the block inside its bin
+  int32_t slab_row; // row of the block's first own column in its bin's stack of slabs (c rows of n_pad)
   int64_t off_idx;  // I_b in idx pool (n int32, ascending); own positions follow in own pool
   int64_t off_own;  // local positions of the own columns (c int32)
   int64_t off_mat;  // n_pad*n_pad element offset in every square pool
@@ -70,6 +71,8 @@ struct DevFlags {
   int32_t n_tiles;      // tiles in the current list
   int32_t n_active;     // blocks still iterating
   int32_t queue;        // next block to claim (persistent schedule)
+  int32_t slab_queue[2];  // next unit to claim by the tensor-core slab kernels (narrow, wide)
+  int32_t pad1;
   double sum_n;         // sum of block traces Tr(S D) over own columns
   double sum_e;         // same for Tr(H D)
   double energy;        // band energy reduction
@@ -122,8 +125,13 @@ struct nolsm_ctx {
   float* d_tmp = nullptr;       // slab scratch (3 slabs)
   double* d_lo = nullptr;       // spectral bounds per block
   double* d_hi = nullptr;
-  double* d_bn = nullptr;       // per-block traces
+  double* d_bn = nullptr;       // per-block traces (per slab unit on the tensor-core refinement)
   double* d_be = nullptr;
+  // own-column pieces of the tensor-core refinement: (block, first column, columns), narrow pieces
+  // (<= 32 columns) first, then wide ones (<= 192), each group largest block first
+  int32_t* d_slab_units = nullptr;
+  std::vector<int32_t> h_slab_units;
+  int32_t n_units_narrow = 0, n_units_wide = 0;
   float* d_resacc = nullptr;    // per-block residual accumulators
   float* d_tol = nullptr;       // per-block stopping tolerance on ||X^2 - I||_F
   nolsm::NsState* d_state = nullptr;
@@ -228,7 +236,10 @@ cudaError_t tc_prepare(nolsm_ctx* ctx);
 cudaError_t launch_gemm_tc(nolsm_ctx* ctx, int phase);
 cudaError_t launch_ns_pair(nolsm_ctx* ctx, double mu);
 cudaError_t launch_congruence_tc(nolsm_ctx* ctx, float* t1);
+cudaError_t launch_slab_tc(nolsm_ctx* ctx);
 int tc_tile_n();
+constexpr int kSlabNarrow = 32;   // columns of a narrow refinement piece
+constexpr int kSlabWide = 192;    // columns of a wide refinement piece
 
 // learn.cu
 cudaError_t launch_features(nolsm_ctx* ctx, double mu, float* feat);

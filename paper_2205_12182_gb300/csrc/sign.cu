@@ -1051,10 +1051,14 @@ cudaError_t slab_launch(nolsm_ctx* ctx) {
 }  // namespace
 
 cudaError_t launch_slab_traces(nolsm_ctx* ctx, int half) {
-  cudaError_t e = half == 0 ? slab_launch<float>(ctx) : half == 1 ? slab_launch<__half>(ctx)
-                                                                  : slab_launch<__nv_bfloat16>(ctx);
+  const bool tc = half != 0 && ctx->opt.refine_path == NOLSM_REFINE_TENSOR;
+  cudaError_t e = tc ? launch_slab_tc(ctx)
+                     : half == 0 ? slab_launch<float>(ctx)
+                                 : half == 1 ? slab_launch<__half>(ctx) : slab_launch<__nv_bfloat16>(ctx);
   if (e != cudaSuccess) return e;
-  sum_traces_kernel<<<1, 1024, 0, ctx->stream>>>(ctx->n_blocks, ctx->d_bn, ctx->d_be, ctx->d_flags);
+  // per-block traces, or per own-column piece on the tensor-core path
+  const int n = tc ? ctx->n_units_narrow + ctx->n_units_wide : ctx->n_blocks;
+  sum_traces_kernel<<<1, 1024, 0, ctx->stream>>>(n, ctx->d_bn, ctx->d_be, ctx->d_flags);
   return cudaGetLastError();
 }
 

@@ -33,7 +33,9 @@ constexpr int B_BYTES = TN * TK * 2;          // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int TMEM_COLS = 512;                // two 256-column FP32 accumulators
 constexpr int NUM_THREADS = 192;
-constexpr int kMapsPerBin = 6;                // loads of X0, X1, B (64 x 128 boxes), stores (32 x 32 boxes)
+// per bin: loads of X0, X1, B (64 x 128 boxes), stores into them (32 x 32 boxes), and loads of the
+// refinement's four split slab pools hi0, lo0, hi1, lo1 (64 x 16 boxes)
+constexpr int kMapsPerBin = 10;
 constexpr int EPI_BUF_BYTES = 4096;           // one staging buffer: a 32 x 32 chunk and its transpose
 // shared memory: [stages | epilogue staging, NBUF buffers per epilogue warp | barriers | tables],
 // 1024-byte aligned base; the per-product kernel single-buffers (its tile table is large), the
@@ -141,6 +143,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[64]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
@@ -181,6 +193,7 @@ template <typename T> struct Pack;
 template <> struct Pack<__half> {
   static constexpr int fmt = 0;
   __device__ static __half one(float a) { return __float2half_rn(a); }
+  __device__ static float f(__half a) { return __half2float(a); }
   __device__ static uint32_t two(float a, float b) {
     __half2 h = __floats2half2_rn(a, b);
     return *reinterpret_cast<uint32_t*>(&h);
@@ -189,6 +202,7 @@ template <> struct Pack<__half> {
 template <> struct Pack<__nv_bfloat16> {
   static constexpr int fmt = 1;
   __device__ static __nv_bfloat16 one(float a) { return __float2bfloat16_rn(a); }
+  __device__ static float f(__nv_bfloat16 a) { return __bfloat162float(a); }
   __device__ static uint32_t two(float a, float b) {
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<uint32_t*>(&h);
@@ -864,6 +878,300 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PAIR_THREADS, 1) ns_
 }
 
 // ---------------------------------------------------------------------------------------------
+// The refinement steps on the own-column slab and the block traces (Eq. 4, Eq. 8) on the tensor
+// cores.  With V_0 = W = L^-1[:, C_b] and X the final iterate in its FP16/BF16 storage, one step of
+// Eq. 6 applied to the slab is f(X) V = 1.5 X V - 0.5 X (X (X V)); refine_iters >= 2 evaluates the
+// two-step map as G = 1.5 F1 - 0.5 F3 with F1 = f(X) W, F2 = f(X) F1, F3 = f(X) F2 (nine products),
+// refine_iters = 1 takes G = f(X) W (three), 0 takes G = X W (one).  Then Y = (W - G) / 2 and the
+// block's traces N_b = <L[C_b, :]^T, Y>, E_b = <L^-1 T_b(H0)[:, C_b], Y> in FP64.
+// A product P = X V runs as 128-row tiles of M = 128, N = the piece's column count rounded up to 16,
+// K = 16 MMAs: X is the A operand exactly as stored, the FP32 slab V is the B operand split into
+// hi = V rounded to the iterate's format and lo = (V - hi) rounded again, and every k-step
+// accumulates X hi + X lo in FP32 tensor memory.  In FP16 the pair resolves V to 2^-22 of its size or
+// 2^-24 absolute (the subnormal spacing), below FP32 rounding for the O(1) entries of these slabs;
+// in BF16 to 2^-16 of its size.  Columns of a B box past the piece (the next piece's rows, or zero
+// fill past the pool) only reach accumulator columns that are never read.
+// One persistent CTA per SM takes pieces (block, up to NMAX own columns) off a queue and runs the
+// whole chain of its piece; the products are sequential (each needs every row of the previous one)
+// and separated by a CTA barrier after the epilogue's stores.  Roles (192 threads): warp 0 TMA
+// producer (a 128 x 64 box of X and N/16 16 x 64 boxes each of hi and lo per stage), warp 1 MMA
+// issuer, warps 2..5 epilogue (lane = row: TMEM -> registers, the step's arithmetic, coalesced
+// column stores of the FP32 values and of the split of the next operand; the split pools alternate
+// between two pairs).  Waits are bounded as in ns_tc_kernel.
+struct SlabParams {
+  const int32_t* units;         // (block, first own column, columns, 0) per piece
+  int n_units;
+  int32_t* queue;
+  const BlockDesc* blocks;
+  const NsState* st;
+  const CUtensorMap* tmaps;
+  const float* w;
+  const float* z;
+  const float* lc;
+  float* y;
+  float* s1;                    // P1 = X V of the current step (FP32 slab pool)
+  float* f1;                    // F1 = f(X) W (FP32 slab pool)
+  void* hl[4];                  // split pools hi0, lo0, hi1, lo1 (the iterate's format)
+  double* bn;                   // traces per piece
+  double* be;
+  DevFlags* flags;
+  long long budget;
+  int refine;
+};
+
+template <int NMAX, int NST>
+struct SlabLayout {
+  static constexpr int B_BYTES = NMAX * TK * 2;          // one of hi / lo
+  static constexpr int STAGE = A_BYTES + 2 * B_BYTES;
+  static constexpr int BAR_OFF = NST * STAGE;
+  static constexpr int SMEM = 1024 + BAR_OFF + 512;
+  static_assert(NMAX % 16 == 0 && NMAX <= 256, "MMA N");
+  static_assert(B_BYTES % 1024 == 0, "swizzle atoms of the B boxes");
+  static_assert((2 * NST + 15) * 8 <= 512, "barrier area");
+  static_assert(SMEM <= 227 * 1024, "shared memory of the slab kernel");
+};
+
+template <typename T, int NMAX, int NST>
+__global__ void __launch_bounds__(NUM_THREADS, 1) slab_tc_kernel(const __grid_constant__ SlabParams p) {
+  using L = SlabLayout<NMAX, NST>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* stage_base = smem;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
+  uint64_t* full_bar = bars;                       // [NST]
+  uint64_t* empty_bar = bars + NST;                // [NST]
+  uint64_t* tfull_bar = bars + 2 * NST;            // [2]
+  uint64_t* tempty_bar = bars + 2 * NST + 2;       // [2]
+  uint64_t* drain_bar = bars + 2 * NST + 4;        // [1]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NST + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  int* s_unit = reinterpret_cast<int*>(bars + 2 * NST + 6);
+  double* red = reinterpret_cast<double*>(bars + 2 * NST + 7);   // [4 warps][2]
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NST; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+    for (int a = 0; a < 2; ++a) { mbar_init(&tfull_bar[a], 1); mbar_init(&tempty_bar[a], 128); }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const long long budget = p.budget;
+  const long long drain_budget = budget > (1LL << 22) ? budget : (1LL << 22);
+  const int q = warp & 3;
+
+  int ps = 0;
+  uint32_t pph = 0, armed = 0, arm_parity = 0;
+  int ms = 0;
+  uint32_t mph = 0, mtph[2] = {0u, 0u};
+  int macc = 0;
+  uint32_t etph[2] = {0u, 0u};
+  int eacc = 0;
+
+  for (;;) {
+    if (threadIdx.x == 0) *s_unit = atomicAdd(p.queue, 1);
+    __syncthreads();
+    const int u = *s_unit;
+    if (u >= p.n_units || *abort_flag) break;
+    const int b = p.units[4 * u], c0 = p.units[4 * u + 1], cw = p.units[4 * u + 2];
+    const BlockDesc bd = p.blocks[b];
+    const int cur = p.st[b].cur;
+    const int ld = bd.n_pad, N = (cw + 15) & ~15;
+    const int64_t so = bd.off_slab + (int64_t)c0 * ld;   // the piece's first column in the slab pools
+    const int nf = p.refine >= 2 ? 3 : p.refine;         // steps of Eq. 6 (0: the single product G = X W)
+    const int nprod = nf == 0 ? 1 : 3 * nf;
+    {
+      // V_0 = W, split into the first pool pair
+      const int64_t len = (int64_t)cw * ld;
+      for (int64_t e = threadIdx.x; e < len; e += NUM_THREADS) {
+        const float v = p.w[so + e];
+        const T hi = Pack<T>::one(v);
+        reinterpret_cast<T*>(p.hl[0])[so + e] = hi;
+        reinterpret_cast<T*>(p.hl[1])[so + e] = Pack<T>::one(v - Pack<T>::f(hi));
+      }
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
+    __syncthreads();
+    double sn = 0.0, se = 0.0;
+    for (int pi = 0; pi < nprod && !*abort_flag; ++pi) {
+      const int src = pi & 1;                              // pool pair read by this product
+      if (warp == 0) {
+        if (lane == 0) {
+          const CUtensorMap* ma = p.tmaps + bd.bin * kMapsPerBin + cur;
+          const CUtensorMap* mh = p.tmaps + bd.bin * kMapsPerBin + 6 + 2 * src;
+          const CUtensorMap* ml = mh + 1;
+          const uint32_t bytes = (uint32_t)A_BYTES + 4u * (uint32_t)N * TK;
+          const int ra = bd.pos * ld, rb = bd.slab_row + c0;
+          bool ok = true;
+          for (int m0 = 0; m0 < ld && ok; m0 += TM)
+            for (int k0 = 0; k0 < ld; k0 += TK) {
+              if (!mbar_wait(&empty_bar[ps], pph ^ 1u, budget, abort_flag)) { ok = false; break; }
+              mbar_expect_tx(&full_bar[ps], bytes);
+              uint8_t* a_dst = stage_base + ps * L::STAGE;
+              uint8_t* h_dst = a_dst + A_BYTES;
+              uint8_t* l_dst = h_dst + L::B_BYTES;
+              tma_load_2d(a_dst, ma, &full_bar[ps], k0, ra + m0);
+              for (int h = 0; h < N; h += 16) {
+                tma_load_2d(h_dst + h * TK * 2, mh, &full_bar[ps], k0, rb + h);
+                tma_load_2d(l_dst + h * TK * 2, ml, &full_bar[ps], k0, rb + h);
+              }
+              armed |= 1u << ps;
+              arm_parity = (arm_parity & ~(1u << ps)) | (pph << ps);
+              if (++ps == NST) { ps = 0; pph ^= 1u; }
+            }
+          if (!ok) {
+            set_error(p.flags, NOLSM_ETIMEOUT);
+            *abort_flag = 1;
+          }
+        }
+      } else if (warp == 1) {
+        if (lane == 0) {
+          const uint32_t idesc = make_idesc(Pack<T>::fmt, TM, N);
+          bool ok = true;
+          for (int m0 = 0; m0 < ld && ok; m0 += TM) {
+            if (!mbar_wait(&tempty_bar[macc], mtph[macc] ^ 1u, budget, abort_flag)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t d_tmem = tmem_base + (uint32_t)(macc * TN);
+            for (int k0 = 0; k0 < ld; k0 += TK) {
+              if (!mbar_wait(&full_bar[ms], mph, budget, abort_flag)) { ok = false; break; }
+              tc_fence_after();
+              const uint32_t a_addr = smem_u32(stage_base + ms * L::STAGE);
+              const uint64_t adesc = sw128_desc(a_addr);
+              const uint64_t hdesc = sw128_desc(a_addr + A_BYTES);
+              const uint64_t ldesc = sw128_desc(a_addr + A_BYTES + L::B_BYTES);
+#pragma unroll
+              for (int kk = 0; kk < TK / 16; ++kk) {
+                umma_f16(d_tmem, adesc + (uint64_t)(kk * 2), hdesc + (uint64_t)(kk * 2), idesc, (k0 | kk) != 0);
+                umma_f16(d_tmem, adesc + (uint64_t)(kk * 2), ldesc + (uint64_t)(kk * 2), idesc, 1);
+              }
+              umma_commit(&empty_bar[ms]);
+              if (++ms == NST) { ms = 0; mph ^= 1u; }
+            }
+            if (!ok) break;
+            umma_commit(&tfull_bar[macc]);
+            mtph[macc] ^= 1u;
+            macc ^= 1;
+          }
+          if (!ok) {
+            set_error(p.flags, NOLSM_ETIMEOUT);
+            *abort_flag = 1;
+          }
+        }
+      } else {
+        const int t = pi % 3, f = pi / 3;
+        T* dh = reinterpret_cast<T*>(src ? p.hl[0] : p.hl[2]);   // the pool pair the next product reads
+        T* dl = reinterpret_cast<T*>(src ? p.hl[1] : p.hl[3]);
+        for (int m0 = 0; m0 < ld; m0 += TM) {
+          // the outcome must be the same in all lanes: the tensor-memory loads below are warp-collective
+          if (!__all_sync(0xffffffffu, mbar_wait(&tfull_bar[eacc], etph[eacc], budget, abort_flag))) {
+            set_error(p.flags, NOLSM_ETIMEOUT);
+            *abort_flag = 1;
+            break;
+          }
+          tc_fence_after();
+          const int m = m0 + q * 32 + lane;
+          const uint32_t tb = tmem_base + (uint32_t)(eacc * TN) + ((uint32_t)(q * 32) << 16);
+          for (int j0 = 0; j0 < N; j0 += 16) {
+            uint32_t v[16];
+            tmem_ld16(tb + (uint32_t)j0, v);
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+              const int j = j0 + jj;
+              if (j >= cw) break;
+              const int64_t o = so + (int64_t)j * ld + m;
+              const float x = __uint_as_float(v[jj]);
+              float nv = 0.f, g = 0.f;
+              bool split = false, last = false;
+              if (nf == 0) {
+                g = x;
+                last = true;
+              } else if (t == 0) {
+                p.s1[o] = x;
+                nv = x;
+                split = true;
+              } else if (t == 1) {
+                nv = x;
+                split = true;
+              } else {
+                const float fv = 1.5f * p.s1[o] - 0.5f * x;
+                if (f == 0 && nf > 1) p.f1[o] = fv;
+                if (f < nf - 1) {
+                  nv = fv;
+                  split = true;
+                } else {
+                  g = nf > 1 ? 1.5f * p.f1[o] - 0.5f * fv : fv;
+                  last = true;
+                }
+              }
+              if (split) {
+                const T hi = Pack<T>::one(nv);
+                dh[o] = hi;
+                dl[o] = Pack<T>::one(nv - Pack<T>::f(hi));
+              }
+              if (last) {
+                const float yv = 0.5f * (p.w[o] - g);
+                p.y[o] = yv;
+                sn += (double)p.lc[o] * (double)yv;
+                se += (double)p.z[o] * (double)yv;
+              }
+            }
+          }
+          tc_fence_before();
+          mbar_arrive(&tempty_bar[eacc]);
+          etph[eacc] ^= 1u;
+          eacc ^= 1;
+        }
+        asm volatile("fence.proxy.async.global;" ::: "memory");   // the next product's operand loads
+      }
+      __syncthreads();
+    }
+    if (warp >= 2) {
+      for (int o = 16; o; o >>= 1) {
+        sn += __shfl_xor_sync(0xffffffffu, sn, o);
+        se += __shfl_xor_sync(0xffffffffu, se, o);
+      }
+      if (lane == 0) {
+        red[2 * (warp - 2)] = sn;
+        red[2 * (warp - 2) + 1] = se;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      p.bn[u] = (red[0] + red[2]) + (red[4] + red[6]);
+      p.be[u] = (red[1] + red[3]) + (red[5] + red[7]);
+    }
+  }
+
+  // teardown: every copy and product issued here lands before shared and tensor memory go away
+  if (warp == 0 && lane == 0) {
+    volatile int never = 0;
+    for (int s = 0; s < NST; ++s)
+      if (armed & (1u << s)) mbar_wait(&full_bar[s], (arm_parity >> s) & 1u, drain_budget, &never);
+  } else if (warp == 1 && lane == 0) {
+    umma_commit(drain_bar);
+    volatile int never = 0;
+    mbar_wait(drain_bar, 0, drain_budget, &never);
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // The congruence A0 = L^-1 T_b(H0) L^-T on the tensor cores, FP32-accurate by three TF32 passes.
 // A product C = A B^T (both operands row-major, K contiguous) over a tile list of 128 x 128 tiles.
 // Each FP32 operand x is split in shared memory into hi = x rounded to TF32 (exact in TF32) and
@@ -1160,11 +1468,15 @@ cudaError_t tc_prepare(nolsm_ctx* ctx) {
   std::vector<CUtensorMap> maps;
   int n_bins = 0;
   for (const auto& b : ctx->h_blocks) n_bins = std::max(n_bins, b.bin + 1);
-  std::vector<int64_t> bin_off(n_bins, -1), bin_cnt(n_bins, 0);
+  std::vector<int64_t> bin_off(n_bins, -1), bin_cnt(n_bins, 0), bin_slab(n_bins, 0), bin_rows(n_bins, 0);
   std::vector<int> bin_pad(n_bins, 0);
   for (const auto& b : ctx->h_blocks) {
-    if (b.pos == 0) bin_off[b.bin] = b.off_mat;
+    if (b.pos == 0) {
+      bin_off[b.bin] = b.off_mat;
+      bin_slab[b.bin] = b.off_slab;
+    }
     bin_cnt[b.bin] += 1;
+    bin_rows[b.bin] += b.c;
     bin_pad[b.bin] = b.n_pad;
   }
   maps.resize((size_t)n_bins * kMapsPerBin);
@@ -1188,6 +1500,20 @@ cudaError_t tc_prepare(nolsm_ctx* ctx) {
       r = encode(&maps[(size_t)bi * kMapsPerBin + 3 + pi], dt, 2, base, gdim, gstride, sbox, estr,
                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    // the refinement's split slab pools (in the slab scratch after two FP32 slabs): each bin's slabs
+    // are a stack of c-row, n_pad-column matrices; 64 x 16 boxes, 128-byte swizzle
+    for (int pi = 0; pi < 4; ++pi) {
+      const uint64_t np = (uint64_t)bin_pad[bi];
+      void* base = reinterpret_cast<uint8_t*>(ctx->d_tmp + 2 * ctx->sum_slab) + 2 * (pi * ctx->sum_slab + bin_slab[bi]);
+      cuuint64_t gdim[2] = {np, (uint64_t)std::max<int64_t>(bin_rows[bi], 1)};
+      cuuint64_t gstride[1] = {np * 2};
+      cuuint32_t estr[2] = {1, 1};
+      cuuint32_t box[2] = {TK, 16};
+      CUresult r = encode(&maps[(size_t)bi * kMapsPerBin + 6 + pi], dt, 2, base, gdim, gstride, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     }
   }
@@ -1329,6 +1655,76 @@ cudaError_t launch_congruence_tc(nolsm_ctx* ctx, float* t1) {
 }
 
 int tc_tile_n() { return TN; }
+
+// The refinement on the tensor cores: narrow pieces (<= 32 columns, eight 24 KB stages), then wide
+// ones (<= 192 columns, three 64 KB stages), one persistent CTA per SM each.  Slab scratch: P1 and
+// F1 (FP32), then the four split pools hi0, lo0, hi1, lo1 in the iterate's format.
+cudaError_t launch_slab_tc(nolsm_ctx* ctx) {
+  const bool bf16 = ctx->opt.precision == NOLSM_PREC_MIXED_BF16;
+  using LN = SlabLayout<kSlabNarrow, 8>;
+  using LW = SlabLayout<kSlabWide, 3>;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(slab_tc_kernel<__half, kSlabNarrow, 8>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, LN::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(slab_tc_kernel<__nv_bfloat16, kSlabNarrow, 8>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, LN::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(slab_tc_kernel<__half, kSlabWide, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               LW::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(slab_tc_kernel<__nv_bfloat16, kSlabWide, 3>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, LW::SMEM);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  if (!ctx->d_tmaps || !ctx->d_tmp || !ctx->d_slab_units) return cudaErrorInvalidValue;
+  SlabParams p;
+  p.blocks = ctx->d_blocks;
+  p.st = ctx->d_state;
+  p.tmaps = reinterpret_cast<const CUtensorMap*>(ctx->d_tmaps);
+  p.w = ctx->d_w;
+  p.z = ctx->d_z;
+  p.lc = ctx->d_lc;
+  p.y = ctx->d_y;
+  p.s1 = ctx->d_tmp;
+  p.f1 = ctx->d_tmp + ctx->sum_slab;
+  uint16_t* pools = reinterpret_cast<uint16_t*>(ctx->d_tmp + 2 * ctx->sum_slab);
+  for (int i = 0; i < 4; ++i) p.hl[i] = pools + (int64_t)i * ctx->sum_slab;
+  p.flags = ctx->d_flags;
+  p.budget = ctx->opt.wait_budget;
+  p.refine = ctx->opt.refine_iters;
+  cudaError_t e = cudaMemsetAsync(&ctx->d_flags->slab_queue[0], 0, 2 * sizeof(int32_t), ctx->stream);
+  if (e != cudaSuccess) return e;
+  if (ctx->n_units_narrow > 0) {
+    p.units = ctx->d_slab_units;
+    p.n_units = ctx->n_units_narrow;
+    p.queue = &ctx->d_flags->slab_queue[0];
+    p.bn = ctx->d_bn;
+    p.be = ctx->d_be;
+    const int grid = std::min(ctx->num_sms, ctx->n_units_narrow);
+    if (bf16) slab_tc_kernel<__nv_bfloat16, kSlabNarrow, 8><<<grid, NUM_THREADS, LN::SMEM, ctx->stream>>>(p);
+    else slab_tc_kernel<__half, kSlabNarrow, 8><<<grid, NUM_THREADS, LN::SMEM, ctx->stream>>>(p);
+    ctx->n_launches += 1;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (ctx->n_units_wide > 0) {
+    p.units = ctx->d_slab_units + 4 * ctx->n_units_narrow;
+    p.n_units = ctx->n_units_wide;
+    p.queue = &ctx->d_flags->slab_queue[1];
+    p.bn = ctx->d_bn + ctx->n_units_narrow;
+    p.be = ctx->d_be + ctx->n_units_narrow;
+    const int grid = std::min(ctx->num_sms, ctx->n_units_wide);
+    if (bf16) slab_tc_kernel<__nv_bfloat16, kSlabWide, 3><<<grid, NUM_THREADS, LW::SMEM, ctx->stream>>>(p);
+    else slab_tc_kernel<__half, kSlabWide, 3><<<grid, NUM_THREADS, LW::SMEM, ctx->stream>>>(p);
+    ctx->n_launches += 1;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 // The persistent schedule: one launch for the whole iteration of every block (see ns_pair_kernel).
 cudaError_t launch_ns_pair(nolsm_ctx* ctx, double mu) {

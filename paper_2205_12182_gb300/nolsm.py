@@ -22,6 +22,7 @@ PREC_FP32, PREC_MIXED_FP16, PREC_MIXED_BF16 = 1, 2, 3
 BOUNDS_GERSHGORIN, BOUNDS_LANCZOS, BOUNDS_LEARNED = 0, 1, 2
 CHOL_FP64, CHOL_FP32, CHOL_FP64_INV64, CHOL_DF64 = 0, 1, 2, 3
 SCHEDULE_PERSISTENT, SCHEDULE_PER_PRODUCT = 0, 1
+REFINE_TENSOR, REFINE_SIMT = 0, 1
 
 FUNCTIONS = ["nolsm_default_options", "nolsm_create", "nolsm_build_submatrices", "nolsm_sign_batch", "nolsm_set_mu",
              "nolsm_density", "nolsm_band_energy", "nolsm_block_info", "nolsm_block_index_set", "nolsm_block_bounds",
@@ -48,7 +49,7 @@ class NolsmOptions(C.Structure):
                 ("scaled", C.c_int32), ("sign_tol", C.c_double), ("max_iter", C.c_int32),
                 ("refine_iters", C.c_int32), ("spin_factor", C.c_double), ("lower_bound", C.c_double),
                 ("alpha_margin", C.c_double), ("wait_budget", C.c_int64), ("lanczos_steps", C.c_int32),
-                ("schedule", C.c_int32)]
+                ("schedule", C.c_int32), ("refine_path", C.c_int32)]
 
 
 class NolsmSignStats(C.Structure):

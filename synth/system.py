@@ -310,6 +310,41 @@ def water_box(n_side: int, seed: int, spacing: float = LATTICE_SPACING,
                   8.0 * n_mol, blk_ptr, blk_cols, ep, ei)
 
 
+def water_clusters(n_side: int, seed: int, cluster=(2, 4, 4), halo: float = 8.0,
+                   spacing: float = LATTICE_SPACING, name: str | None = None) -> System:
+    """The water box of `water_box` (same seed, same molecules) cut into column blocks of
+    cluster[0] x cluster[1] x cluster[2] neighbouring lattice sites (32 molecules by default).
+
+    A block's own columns are the basis functions of its molecules; its geometric list holds every
+    molecule whose O lies within `halo` (minimum image) of any own O.  n_side must be a multiple of
+    every cluster edge.
+    """
+    cx, cy, cz = cluster
+    if n_side % cx or n_side % cy or n_side % cz:
+        raise ValueError("n_side must be a multiple of every cluster edge")
+    base = water_box(n_side, seed, spacing=spacing)
+    o_pos = base.coords[0::3]
+    box = base.box
+    i, j, k = np.meshgrid(np.arange(n_side), np.arange(n_side), np.arange(n_side), indexing="ij")
+    cid = ((i // cx) * (n_side // cy) + j // cy) * (n_side // cz) + k // cz
+    members = np.argsort(cid.ravel(), kind="stable").reshape(-1, cx * cy * cz)
+    n_blk = members.shape[0]
+    blk_ptr = (np.arange(n_blk + 1) * 6 * cx * cy * cz).astype(np.int32)
+    blk_cols = (6 * members[:, :, None] + np.arange(6)[None, None, :]).reshape(-1).astype(np.int32)
+    tree = cKDTree(np.mod(o_pos, box), boxsize=box)
+    ep = np.zeros(n_blk + 1, dtype=np.int32)
+    lists = []
+    for b in range(n_blk):
+        near = tree.query_ball_point(np.mod(o_pos[members[b]], box), r=halo)
+        mol = np.unique(np.concatenate([np.asarray(v, dtype=np.int64) for v in near]))
+        idx = (6 * mol[:, None] + np.arange(6)[None, :]).reshape(-1)
+        lists.append(idx)
+        ep[b + 1] = ep[b] + idx.size
+    return System(name or f"waterclusters{n_side ** 3}", box, base.coords, base.element, base.atom_bf_ptr,
+                  base.row_ptr, base.col, base.h, base.s, base.n_electrons, blk_ptr, blk_cols, ep,
+                  np.concatenate(lists).astype(np.int32))
+
+
 def isolated_waters(n_mol: int, seed: int, spacing: float = 10.0) -> System:
     """Waters farther apart than the cutoff: H0 and S are block diagonal."""
     m = int(round(n_mol ** (1 / 3)))
@@ -333,6 +368,8 @@ def dimer_system(a: float, b: float, s: float) -> System:
 CONFIGS = {
     1: dict(desc="64 waters, 12.4 A box, pattern rule, 1 block/molecule", seeds=(1, 2, 3, 4, 5)),
     2: dict(desc="4,096 waters, 49.6 A box, 8 A neighbourhood, 1 block/molecule", seeds=(11, 12, 13)),
+    5: dict(desc="water, 32-molecule clusters with an 8 A halo (the 1,000,000-molecule system's block "
+                 "shape), 13,824 molecules", seeds=(31,)),
 }
 
 
@@ -344,4 +381,6 @@ def make_config(config: int, seed: int | None = None) -> System:
         return water_box(4, seed, name=f"water64-s{seed}")
     if config == 2:
         return water_box(16, seed, neighbourhood=8.0, name=f"water4096-s{seed}")
+    if config == 5:
+        return water_clusters(24, seed, name=f"waterclusters13824-s{seed}")
     raise ValueError(f"unknown config {config}")
