@@ -249,6 +249,8 @@ def run_ours(args):
     }
     if not args.no_variants:
         line["variants"] = variants(nolsm, system, mu_fn, d_dev, predictor, barrier, world)
+    if not args.no_large and world == 1:
+        line["largest_blocks"] = large_blocks(nolsm, predictor, pk, parity=rank == 0 and not args.no_parity)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(system, seconds=args.cpu_seconds)
     lib.close()
@@ -286,6 +288,46 @@ def variants(nolsm, system, mu_fn, d_dev, predictor, barrier, world, steps=2):
         out[name] = {"value": WORKLOAD["atoms"] * world / dt, "unit": "atoms/s", "ms_per_step": dt * 1e3,
                      "mu_steps": st, "ns_iters_avg": s["iters_avg"]}
         lib.close()
+    return out
+
+
+def large_blocks(nolsm, predictor, pk, parity=True, steps=2, evals=3):
+    """The block shape of the 1,000,000-molecule configuration -- 32-molecule clusters with an 8 A
+    halo, n_b ~ 1,870 (n_pad 1,920) -- on a 13,824-molecule box (432 blocks): atoms/s of the full
+    step (1 warm-up, `steps` timed) and the sign products' TFLOP/s over `evals` sign evaluations at
+    the converged mu (device events around every product launch)."""
+    import torch
+    from synth import make_config
+    s = make_config(5)
+    lib = nolsm.Nolsm(precision=nolsm.PREC_MIXED_FP16, bounds=nolsm.BOUNDS_LEARNED)
+    lib.set_predictor(predictor)
+    d_dev = torch.empty(s.nnz, dtype=torch.float64, device="cuda")
+    mu_fn = lambda lib_, s_: lib_.set_mu(s_.n_electrons, tol_n=TOL_N)   # noqa: E731
+    solve(lib, s, mu_fn, d_dev, "device")
+    torch.cuda.synchronize()
+    lib.phase_times(reset=True)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        mu, n, mu_steps, e = solve(lib, s, mu_fn, d_dev, "device")
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    stage_ms = {k: v / steps for k, v in lib.phase_times(reset=True).items()}
+    lib.counters(reset=True)
+    for _ in range(evals):
+        st = lib.sign_batch(mu)
+    cnt = lib.counters(reset=True)
+    tf = cnt["gemm_flops"] / (cnt["gemm_ms"] * 1e-3) / 1e12
+    out = {"workload": "water-13824, 32-molecule clusters + 8 A halo", "blocks": s.n_blocks, "atoms": s.n_atoms,
+           "n_b": "1,860-1,872 (n_pad 1,920)", "value": s.n_atoms / dt, "unit": "atoms/s", "ms_per_step": dt * 1e3,
+           "mu_steps": mu_steps, "stage_ms_per_step": stage_ms,
+           "sign_gemm": {"tflops_executed": tf,
+                         "tflops_paper_convention": tf * st["flops_paper"] / st["flops_executed"],
+                         "pct_fp16_peak_measured": 100 * tf / pk["bf16_tflops_sustained"],
+                         "ms_per_sign_evaluation": cnt["gemm_ms"] / evals, "ns_iters_avg": st["iters_avg"],
+                         "schedule": "per-product launches, tiles dealt round-robin"}}
+    if parity:
+        out["parity"] = parity_sample(s, lib.density().cpu().numpy(), mu, n_blocks=2)
+    lib.close()
     return out
 
 
@@ -435,6 +477,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the large-block (32-molecule cluster) section")
     ap.add_argument("--side", type=int, default=16,
                     help="molecules per box edge (16: the 4,096-molecule workload; smaller boxes for profiling)")
     args = ap.parse_args()

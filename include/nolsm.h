@@ -82,10 +82,14 @@ typedef enum nolsm_chol_precision {
   NOLSM_CHOL_FP64 = 0,          /* Cholesky factor of T_b(S) in FP64, its triangular inverse in FP32 */
   NOLSM_CHOL_FP32 = 1,          /* factor and inverse in FP32 */
   NOLSM_CHOL_FP64_INV64 = 2,    /* factor and inverse in FP64 */
-  NOLSM_CHOL_DF64 = 3           /* factor in double-float pairs (Dekker; 48-bit significand) on the FP32
-                                   pipe with FP64 32x32 diagonal blocks, stored as FP64; inverse in FP32.
-                                   The factor feeds the rest of the path through its FP32 rounding (and
-                                   the trace slab), where it agrees with the FP64 factor */
+  NOLSM_CHOL_DF64 = 3,          /* factor in double-float pairs (Dekker; 48-bit significand), stored as
+                                   FP64; inverse in FP32.  Blocked by 64-column panels: each panel on
+                                   the FP32 pipe (FP64 32x32 diagonal blocks), the trailing updates on the
+                                   tensor cores from exact 7-bit slices of the factor (Ozaki scheme, 49
+                                   bits).  The factor feeds the rest of the path through its FP32
+                                   rounding (and the trace slab), where it agrees with the FP64 factor */
+  NOLSM_CHOL_DF64_SIMT = 4      /* the same double-float factor with every update on the FP32 pipe
+                                   (one left-looking launch) */
 } nolsm_chol_precision;
 
 /* How the tensor-core products of the mixed-precision paths are scheduled (the FP32 path always
@@ -94,8 +98,12 @@ typedef enum nolsm_schedule {
   NOLSM_SCHEDULE_PERSISTENT = 0,  /* one launch per sign evaluation: 2-CTA clusters take whole blocks
                                      off a queue and run all of a block's products with its iterates
                                      resident in L2; convergence is decided on the device */
-  NOLSM_SCHEDULE_PER_PRODUCT = 1  /* one grouped launch per product over all active blocks, the
-                                     iteration driven from the host */
+  NOLSM_SCHEDULE_PER_PRODUCT = 1, /* one grouped launch per product over all active blocks, the
+                                     iteration driven from the host; from n_pad 1024 on, the tiles
+                                     are dealt round-robin so that all SMs share a few blocks'
+                                     operands in L2 */
+  NOLSM_SCHEDULE_AUTO = 2         /* PERSISTENT while every block has n_pad < 1024 (the iterates of
+                                     the blocks in flight stay in L2), PER_PRODUCT otherwise */
 } nolsm_schedule;
 
 /* Where the refinement steps on the own-column slab run on the mixed-precision paths (the FP32 path
@@ -134,7 +142,7 @@ typedef struct nolsm_options {
   double alpha_margin;     /* relative safety margin on the spectral radius bound (default 0.02) */
   int64_t wait_budget;     /* bound on every device-side spin wait, in polls (default 1<<22) */
   int32_t lanczos_steps;   /* Lanczos steps per block for NOLSM_BOUNDS_LANCZOS (default 24, at most 64) */
-  int32_t schedule;        /* nolsm_schedule of the mixed-precision products (default PERSISTENT) */
+  int32_t schedule;        /* nolsm_schedule of the mixed-precision products (default AUTO) */
   int32_t refine_path;     /* nolsm_refine_path of the mixed-precision paths (default TENSOR) */
 } nolsm_options;
 
@@ -222,6 +230,11 @@ nolsm_status nolsm_block_state(const nolsm_ctx* ctx, int32_t* iters, double* res
  * second-operand buffer of the last product;  5: the Cholesky factor L of T_b(S) (FP32 rounding
  * of the factor as computed, zero above the diagonal).  Synchronises. */
 nolsm_status nolsm_block_matrix(const nolsm_ctx* ctx, int32_t b, int32_t which, float* out);
+
+/* Diagnostic copy of block b's Cholesky factor L of T_b(S) at the precision it was computed in
+ * (FP64 modes and both double-float modes: the FP64 lower triangle; CHOL_FP32: the FP32 factor
+ * widened), n_b x n_b row-major in host memory, zero above the diagonal.  Synchronises. */
+nolsm_status nolsm_block_factor(const nolsm_ctx* ctx, int32_t b, double* out);
 
 /* Cumulative counters of ctx since nolsm_create or the last reset (reset != 0 zeroes them after
  * reading): kernels launched by the library, and the device time (CUDA events on the context

@@ -132,6 +132,10 @@ void release_pools(nolsm_ctx* ctx) {
   dfree(ctx->d_bn); ctx->d_bn = nullptr;
   dfree(ctx->d_be); ctx->d_be = nullptr;
   dfree(ctx->d_slab_units); ctx->d_slab_units = nullptr;
+  dfree(ctx->d_oz_exp); ctx->d_oz_exp = nullptr;
+  dfree(ctx->d_oz_planes); ctx->d_oz_planes = nullptr;
+  dfree(ctx->d_oz_items); ctx->d_oz_items = nullptr;
+  dfree(ctx->d_oz_tmaps); ctx->d_oz_tmaps = nullptr;
   dfree(ctx->d_resacc); ctx->d_resacc = nullptr;
   dfree(ctx->d_tol); ctx->d_tol = nullptr;
   dfree(ctx->d_state); ctx->d_state = nullptr;
@@ -220,7 +224,7 @@ nolsm_status nolsm_default_options(nolsm_options* opt) {
   opt->alpha_margin = 0.02;
   opt->wait_budget = 1LL << 22;
   opt->lanczos_steps = 24;
-  opt->schedule = NOLSM_SCHEDULE_PERSISTENT;
+  opt->schedule = NOLSM_SCHEDULE_AUTO;
   opt->refine_path = NOLSM_REFINE_TENSOR;
   return NOLSM_OK;
 }
@@ -234,9 +238,9 @@ nolsm_status nolsm_create(nolsm_ctx** out, const nolsm_options* opt, void* cuda_
   if (ctx->opt.precision < NOLSM_PREC_FP32 || ctx->opt.precision > NOLSM_PREC_MIXED_BF16 || ctx->opt.max_iter <= 0 ||
       ctx->opt.refine_iters < 0 || ctx->opt.refine_iters > 3 || !(ctx->opt.spin_factor > 0) ||
       ctx->opt.wait_budget <= 0 || ctx->opt.alpha_margin < 0 || ctx->opt.chol_precision < 0 ||
-      ctx->opt.chol_precision > NOLSM_CHOL_DF64 || ctx->opt.bounds < NOLSM_BOUNDS_GERSHGORIN ||
+      ctx->opt.chol_precision > NOLSM_CHOL_DF64_SIMT || ctx->opt.bounds < NOLSM_BOUNDS_GERSHGORIN ||
       ctx->opt.bounds > NOLSM_BOUNDS_LEARNED || ctx->opt.lanczos_steps < 1 || ctx->opt.lanczos_steps > 64 ||
-      ctx->opt.schedule < NOLSM_SCHEDULE_PERSISTENT || ctx->opt.schedule > NOLSM_SCHEDULE_PER_PRODUCT ||
+      ctx->opt.schedule < NOLSM_SCHEDULE_PERSISTENT || ctx->opt.schedule > NOLSM_SCHEDULE_AUTO ||
       ctx->opt.refine_path < NOLSM_REFINE_TENSOR || ctx->opt.refine_path > NOLSM_REFINE_SIMT) {
     delete ctx;
     return NOLSM_EINVAL;
@@ -381,6 +385,7 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return pad_dim(nb[a]) < pad_dim(nb[b]); });
   int64_t off_mat = 0, off_slab = 0;
   int bin = -1, pos = 0, last_pad = -1, slab_row = 0;
+  ctx->sum_pad = 0;
   ctx->flops_paper_iter = ctx->flops_exec_iter = 0.0;
   for (int32_t b = 0; b < n_blocks; ++b) {
     BlockDesc& bd = ctx->h_blocks[b];
@@ -400,6 +405,8 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
     bd.pos = pos++;
     bd.slab_row = slab_row;
     slab_row += bd.c;
+    bd.row_off = (int32_t)ctx->sum_pad;
+    ctx->sum_pad += bd.n_pad;
     bd.off_mat = off_mat;
     bd.off_slab = off_slab;
     off_mat += (int64_t)bd.n_pad * bd.n_pad;
@@ -489,6 +496,16 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   CK(launch_gather(ctx, ctx->d_a0, sb));
   const int chol_mode = ctx->opt.chol_precision;
   const int chol32 = chol_mode == NOLSM_CHOL_FP32;
+  if (chol_mode == NOLSM_CHOL_DF64) {
+    // slicing exponents, slice planes of one panel, work items of every panel's trailing update
+    int64_t items = 0;
+    for (const auto& bd : ctx->h_blocks) items += (int64_t)(bd.n_pad / kOzPanel + 1) * (bd.n_pad / 32 + 1);
+    CK(dalloc(ctx, &ctx->d_oz_exp, (size_t)ctx->sum_pad));
+    CK(dalloc(ctx, &ctx->d_oz_planes, (size_t)(7 * kOzPanel) * (size_t)ctx->sum_pad));
+    CK(dalloc(ctx, &ctx->d_oz_items, (size_t)(2 * items)));
+    CK(dalloc(ctx, &ctx->d_oz_tmaps, (size_t)256));
+    CK(oz_prepare(ctx));
+  }
   CK(phase_mark(ctx, NOLSM_PHASE_FACTOR));
   CK(launch_cholesky_inverse(ctx, sb, chol_mode));   // marks the inverse stage between its launches
   CK(phase_mark(ctx, NOLSM_PHASE_CONGRUENCE));
@@ -576,7 +593,10 @@ nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out) 
     ctx->n_launches += 2;
     pred = ctx->d_pred;
   }
-  const bool persistent = mixed && ctx->opt.schedule == NOLSM_SCHEDULE_PERSISTENT;
+  int max_pad = 0;
+  for (const auto& bd : ctx->h_blocks) max_pad = std::max(max_pad, bd.n_pad);
+  const bool persistent = mixed && (ctx->opt.schedule == NOLSM_SCHEDULE_PERSISTENT ||
+                                    (ctx->opt.schedule == NOLSM_SCHEDULE_AUTO && max_pad < 1024));
   CK(launch_ns_init(ctx, mu, hk, mode, mode == NOLSM_BOUNDS_LANCZOS ? ctx->d_lz : nullptr, pred, !persistent));
   ctx->n_launches += persistent ? 1 : 2;
   const int tile_n = mixed ? tc_tile_n() : kTile;
@@ -822,6 +842,26 @@ nolsm_status nolsm_block_state(const nolsm_ctx* ctx, int32_t* iters, double* res
     if (residual) residual[b] = hs[b].res;
     if (status) status[b] = hs[b].status;
   }
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_block_factor(const nolsm_ctx* ctx, int32_t b, double* out) {
+  if (!ctx || !ctx->built || b < 0 || b >= ctx->n_blocks || !out) return NOLSM_EINVAL;
+  const BlockDesc& bd = ctx->h_blocks[b];
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return NOLSM_ECUDA;
+  if (ctx->opt.chol_precision == NOLSM_CHOL_FP32) {
+    std::vector<float> l((size_t)bd.n * bd.n);
+    const float* src = reinterpret_cast<const float*>(ctx->d_sb + ctx->sum_sq) + bd.off_mat;
+    if (cudaMemcpy2D(l.data(), sizeof(float) * bd.n, src, sizeof(float) * bd.n_pad, sizeof(float) * bd.n, bd.n,
+                     cudaMemcpyDeviceToHost) != cudaSuccess)
+      return NOLSM_ECUDA;
+    for (size_t i = 0; i < l.size(); ++i) out[i] = l[i];
+  } else if (cudaMemcpy2D(out, sizeof(double) * bd.n, ctx->d_sb + bd.off_mat, sizeof(double) * bd.n_pad,
+                          sizeof(double) * bd.n, bd.n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    return NOLSM_ECUDA;
+  }
+  for (int r = 0; r < bd.n; ++r)
+    for (int c = r + 1; c < bd.n; ++c) out[(size_t)r * bd.n + c] = 0.0;
   return NOLSM_OK;
 }
 

@@ -256,22 +256,28 @@ __device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.w
 // Cholesky S = L L^T in double-float, left-looking by 32-column panels, in place over the FP64
 // pool (a pair occupies the 8 bytes of the double it replaces).  One CTA of 4 warps per block;
 // every 32-row tile is shared by the 4 warps, each taking 8 of every 32 k (no idle warps when a
-// panel has few tiles), the four partial tiles summed in shared memory.
-//   0. the lower triangle of S is converted from FP64 to pairs;
-//   for each panel j0:
+// panel has few tiles), the four partial tiles summed in shared memory.  One launch covers the
+// columns [c_beg, c_end): the whole factor (0, n), or one panel of the blocked factorization whose
+// trailing updates run on the tensor cores (the columns before c_beg are then already subtracted
+// from the panel, so the left-looking sums start at c_beg).
+//   0. (c_beg = 0) the lower triangle of S is converted from FP64 to pairs; with scale_exp given,
+//      each row's slicing exponent e_r (2^e_r >= sqrt(S_rr) >= |L_rk|) is written first;
+//   for each 32-column panel j0 in [c_beg, c_end):
 //   1. R[r, panel] = S[r, panel] - L[r, 0:j0] L[panel, 0:j0]^T for rows r >= j0: 32 x 32 operand
 //      chunks double-buffered in shared memory with cp.async;
 //   2. warp 0 factors the 32x32 diagonal block of R in FP64 and inverts it (FP64), keeping
 //      L_jj^-T as pairs;
 //   3. L[r, panel] = R[r, panel] L_jj^-T for the rows below (same split over k).
-//   4. finally the lower triangle is converted back to FP64; with l32 given, its FP32 rounding
-//      is also written there (zero above the diagonal and on the padding).
+//   4. (c_end >= n) finally the lower triangle is converted back to FP64; with l32 given, its FP32
+//      rounding is also written there (zero above the diagonal and on the padding).
 // The diagonal blocks are O(n 32^2) of the O(n^3/6) work, so FP64 there costs little.
 constexpr int kCholWarps = 4;
 
 __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const BlockDesc* __restrict__ blocks,
                                                                          double* __restrict__ pool,
-                                                                         float* __restrict__ l32, DevFlags* flags) {
+                                                                         float* __restrict__ l32, DevFlags* flags,
+                                                                         int c_beg, int c_end,
+                                                                         int32_t* __restrict__ scale_exp) {
   __shared__ df32 As[2][32][32];          // read as broadcasts: no padding
   __shared__ df32 Bs[2][32][33];          // read by rows (lane = row): padded
   __shared__ df32 red[kCholWarps][32][32];
@@ -280,14 +286,27 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
   __shared__ int s_bad;
   const BlockDesc bd = blocks[blockIdx.x];
   const int n = bd.n, ld = bd.n_pad;
+  if (c_beg >= n) return;
   float2* A = reinterpret_cast<float2*>(pool + bd.off_mat);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // phase-2 scratch over the reduction buffers (idle then)
   double(*diag)[33] = reinterpret_cast<double(*)[33]>(&red[0][0][0]);
   double(*dinv)[33] = reinterpret_cast<double(*)[33]>(&red[0][0][0] + 32 * 33);
   if (tid == 0) s_bad = 0;
+  if (c_beg == 0 && scale_exp) {
+    // 2^e_r >= sqrt(S_rr), which bounds every |L_rk| (sum_k L_rk^2 = S_rr); padding rows get 0
+    for (int r = tid; r < ld; r += kCholWarps * 32) {
+      int e = 0;
+      if (r < n) {
+        const double d = reinterpret_cast<const double*>(A)[(int64_t)r * ld + r];
+        frexp(sqrt(fmax(d, 1e-300)), &e);
+      }
+      scale_exp[bd.row_off + r] = e;
+    }
+    __syncthreads();   // the diagonal is read as FP64 before the conversion below rewrites it
+  }
   // in-place conversions of the lower triangle, four independent loads in flight per thread
-  for (int r = warp; r < n; r += kCholWarps)
+  for (int r = warp; r < n && c_beg == 0; r += kCholWarps)
     for (int c0 = 0; c0 <= r; c0 += 128) {
       float2 v[4];
 #pragma unroll
@@ -333,10 +352,10 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
     __syncthreads();
   };
   const int kw = warp * (32 / kCholWarps);   // this warp's 8 k of every chunk
-  for (int j0 = 0; j0 < n; j0 += 32) {
+  for (int j0 = c_beg; j0 < min(n, c_end); j0 += 32) {
     const int jb = min(32, n - j0);
-    // 1. panel update (nothing to subtract for the first panel)
-    const int nch = j0 / 32;
+    // 1. panel update over the columns [c_beg, j0) (nothing to subtract for the first panel)
+    const int nch = (j0 - c_beg) / 32;
     if (nch > 0) {
       for (int r0 = j0; r0 < n; r0 += 32) {
         // warp 0 starts from S itself (its loads overlap the first chunk's copies), the others from 0
@@ -349,14 +368,14 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
             acc[r] = {s0.x, s0.y};
           }
         }
-        load_chunk(As[0], r0, 0);
-        load_chunk(Bs[0], j0, 0);
+        load_chunk(As[0], r0, c_beg);
+        load_chunk(Bs[0], j0, c_beg);
         cp_async_commit();
         for (int c = 0; c < nch; ++c) {
           const int buf = c & 1;
           if (c + 1 < nch) {
-            load_chunk(As[buf ^ 1], r0, (c + 1) * 32);
-            load_chunk(Bs[buf ^ 1], j0, (c + 1) * 32);
+            load_chunk(As[buf ^ 1], r0, c_beg + (c + 1) * 32);
+            load_chunk(Bs[buf ^ 1], j0, c_beg + (c + 1) * 32);
             cp_async_commit();
             cp_async_wait_group<1>();
           } else {
@@ -441,8 +460,13 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
       reduce_store(r0, j0, jb);
     }
   }
+  if (c_end < n) {
+    if (threadIdx.x == 0 && s_bad) set_error(flags, NOLSM_ENOTPD);
+    return;
+  }
   // 4. back to FP64 (lower triangle) and the FP32 copy of the factor (zero above the diagonal and on
   //    the padding); the conversion issues four independent loads at a time
+  __syncthreads();
   for (int r = warp; r < n; r += kCholWarps)
     for (int c0 = 0; c0 <= r; c0 += 128) {
       float2 v[4];
@@ -473,6 +497,45 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
       }
   }
   if (tid == 0 && s_bad) set_error(flags, NOLSM_ENOTPD);
+}
+
+// Slices of a finished 64-column panel for the tensor-core trailing update (Ozaki, Ogita, Oishi &
+// Rump 2012: error-free splitting into short pieces whose products and sums are exact).  Row r's
+// entries x = L[r, c0 + j] (a pair with |x| <= 2^e_r) are written as seven integers q_0..q_6 with
+// x = 2^(e_r - 7) sum_s q_s 2^(-7 s) + (|rest| <= 2^(e_r - 50)): |q_0| <= 128, |q_s| <= 64 after,
+// each exact in BF16.  Plane s of the block is an n_pad x 64 BF16 matrix at row 7 row_off + s n_pad
+// of the slice pool.  Only the trailing rows r >= c0 + 64 are written (rows >= n as zeros).
+__global__ void __launch_bounds__(256) chol_slice_kernel(const BlockDesc* __restrict__ blocks,
+                                                         const double* __restrict__ pool,
+                                                         const int32_t* __restrict__ scale_exp,
+                                                         __nv_bfloat16* __restrict__ planes, int c0) {
+  const BlockDesc bd = blocks[blockIdx.x];
+  const int n = bd.n, ld = bd.n_pad, t0 = c0 + 64;
+  if (t0 >= n) return;
+  const float2* A = reinterpret_cast<const float2*>(pool + bd.off_mat);
+  __nv_bfloat16* P = planes + (int64_t)7 * bd.row_off * 64;
+  const int total = (ld - t0) * 64;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int r = t0 + (e >> 6), j = e & 63;
+    float q[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (r < n) {
+      const float2 x = A[(int64_t)r * ld + c0 + j];
+      const float sc = ldexpf(1.f, 7 - scale_exp[bd.row_off + r]);
+      float h = x.x * sc, l = x.y * sc;           // |h + l| <= 128, exact scaling
+#pragma unroll
+      for (int s = 0; s < 7; ++s) {
+        q[s] = rintf(h);
+        const float d = h - q[s];                   // exact: the fraction of h
+        const float sum = d + l;                    // TwoSum(d, l), exact renormalisation
+        const float bb = sum - d;
+        const float err = (d - (sum - bb)) + (l - bb);
+        h = sum * 128.f;
+        l = err * 128.f;
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < 7; ++s) P[((int64_t)s * ld + r) * 64 + j] = __float2bfloat16_rn(q[s]);
+  }
 }
 
 // Inverse of the lower-triangular L into X (out of place), by block rows of 32:
@@ -770,7 +833,26 @@ cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode) {
   float* s32 = reinterpret_cast<float*>(sb + ctx->sum_sq);   // FP32 factor lives in the scratch half
   cudaError_t e = cudaSuccess;
   if (mode == NOLSM_CHOL_DF64) {
-    cholesky_df_kernel<<<ctx->n_blocks, kCholWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, ctx->d_flags);
+    // blocked by 64-column panels: panel on the FP32 pipe, slices, trailing update on the tensor cores
+    int max_n = 0;
+    for (const auto& bd : ctx->h_blocks) max_n = std::max(max_n, bd.n);
+    for (int pnl = 0; pnl * kOzPanel < max_n; ++pnl) {
+      const int c0 = pnl * kOzPanel;
+      cholesky_df_kernel<<<ctx->n_blocks, kCholWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, ctx->d_flags, c0,
+                                                                            c0 + kOzPanel, ctx->d_oz_exp);
+      ctx->n_launches += 1;
+      if (c0 + kOzPanel >= max_n) break;
+      chol_slice_kernel<<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, sb, ctx->d_oz_exp,
+                                                                reinterpret_cast<__nv_bfloat16*>(ctx->d_oz_planes), c0);
+      ctx->n_launches += 1;
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if ((e = launch_chol_update_tc(ctx, pnl, sb)) != cudaSuccess) return e;
+    }
+    if ((e = phase_mark(ctx, NOLSM_PHASE_INVERSE)) != cudaSuccess) return e;
+    trinv_tile_kernel<<<ctx->n_blocks, kInvWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
+  } else if (mode == NOLSM_CHOL_DF64_SIMT) {
+    cholesky_df_kernel<<<ctx->n_blocks, kCholWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, ctx->d_flags, 0,
+                                                                          1 << 30, nullptr);
     if ((e = phase_mark(ctx, NOLSM_PHASE_INVERSE)) != cudaSuccess) return e;
     trinv_tile_kernel<<<ctx->n_blocks, kInvWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
   } else if (mode == NOLSM_CHOL_FP64_INV64) {

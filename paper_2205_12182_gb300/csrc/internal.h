@@ -29,6 +29,7 @@ struct BlockDesc {
   int32_t bin;      // size bin (blocks of one n_pad are stored contiguously, bin by bin)
   int32_t pos;      // position of the block inside its bin
   int32_t slab_row; // row of the block's first own column in its bin's stack of slabs (c rows of n_pad)
+  int32_t row_off;  // sum of n_pad over the blocks laid out before this one (per-row scratch pools)
   int64_t off_idx;  // I_b in idx pool (n int32, ascending); own positions follow in own pool
   int64_t off_own;  // local positions of the own columns (c int32)
   int64_t off_mat;  // n_pad*n_pad element offset in every square pool
@@ -130,6 +131,16 @@ struct nolsm_ctx {
   // own-column pieces of the tensor-core refinement: (block, first column, columns), narrow pieces
   // (<= 32 columns) first, then wide ones (<= 192), each group largest block first
   int32_t* d_slab_units = nullptr;
+  // blocked double-float Cholesky with tensor-core trailing updates: slicing exponent per row,
+  // seven BF16 slice planes per row of the current panel, work items (block, first column) of
+  // every panel's update and where each panel's items start
+  int32_t* d_oz_exp = nullptr;
+  uint16_t* d_oz_planes = nullptr;
+  int32_t* d_oz_items = nullptr;
+  uint8_t* d_oz_tmaps = nullptr;
+  std::vector<int32_t> h_oz_items;
+  std::vector<int64_t> h_oz_panel;   // item offset of panel p (size panels + 1)
+  int64_t sum_pad = 0;
   std::vector<int32_t> h_slab_units;
   int32_t n_units_narrow = 0, n_units_wide = 0;
   float* d_resacc = nullptr;    // per-block residual accumulators
@@ -237,6 +248,9 @@ cudaError_t launch_gemm_tc(nolsm_ctx* ctx, int phase);
 cudaError_t launch_ns_pair(nolsm_ctx* ctx, double mu);
 cudaError_t launch_congruence_tc(nolsm_ctx* ctx, float* t1);
 cudaError_t launch_slab_tc(nolsm_ctx* ctx);
+cudaError_t oz_prepare(nolsm_ctx* ctx);                        // items and tensor maps of the updates
+cudaError_t launch_chol_update_tc(nolsm_ctx* ctx, int panel, double* pool);
+constexpr int kOzPanel = 64;      // panel width of the blocked double-float Cholesky
 int tc_tile_n();
 constexpr int kSlabNarrow = 32;   // columns of a narrow refinement piece
 constexpr int kSlabWide = 192;    // columns of a wide refinement piece

@@ -59,6 +59,7 @@ struct TcParams {
   long long budget;             // polls per wait
   int phase;                    // 1 or 2
   int tile_base;                // first tile of this launch in the list
+  int interleave;               // 1: tile i of the launch goes to CTA i mod grid; 0: contiguous runs
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -335,14 +336,20 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_cons
   TileInfo* info = reinterpret_cast<TileInfo*>(smem + tab_off<TC_NBUF>());
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // Each CTA takes a contiguous run of the tile list: the list holds a block's tiles together, so
-  // one SM walks through whole blocks and re-reads each iterate from L2 rather than HBM.
+  // The list holds a block's tiles together.  Small blocks: each CTA takes a contiguous run, so one
+  // SM walks through whole blocks and re-reads each iterate from L2 (152 blocks of a few MB in
+  // flight).  Large blocks (tens of MB per block): tile i goes to CTA i mod grid, so all SMs work on
+  // the same few blocks at a time and share their operand panels in L2.
   const int n_tiles = *p.n_tiles;
   const int span = min(max(n_tiles - p.tile_base, 0), MAX_LOCAL * (int)gridDim.x);
-  const int first = p.tile_base + (int)(((int64_t)span * blockIdx.x) / gridDim.x);
-  const int n_local = p.tile_base + (int)(((int64_t)span * (blockIdx.x + 1)) / gridDim.x) - first;
+  const int first = p.interleave ? p.tile_base + (int)blockIdx.x
+                                 : p.tile_base + (int)(((int64_t)span * blockIdx.x) / gridDim.x);
+  const int step = p.interleave ? (int)gridDim.x : 1;
+  const int n_local = p.interleave
+                          ? (span > (int)blockIdx.x ? (span - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0)
+                          : p.tile_base + (int)(((int64_t)span * (blockIdx.x + 1)) / gridDim.x) - first;
   for (int i = threadIdx.x; i < n_local; i += NUM_THREADS) {
-    const Tile tl = p.tiles[first + i];
+    const Tile tl = p.tiles[first + i * step];
     const BlockDesc bd = p.blocks[tl.block];
     const NsState s = p.st[tl.block];
     TileInfo f;
@@ -1172,6 +1179,275 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) slab_tc_kernel(const __grid_co
 }
 
 // ---------------------------------------------------------------------------------------------
+// Trailing update of the blocked double-float Cholesky on the tensor cores.  After panel p (columns
+// [c0, c0 + 64)) is factored, every trailing entry C[r, c] (c0 + 64 <= c <= r) loses
+// sum_{k in panel} L[r, k] L[c, k].  Each L entry is split into seven 7-bit integers on its row's
+// scale (chol_slice_kernel; Ozaki, Ogita, Oishi & Rump 2012), so
+//   L[r, k] L[c, k] = 2^(e_r + e_c - 14) sum_{s, t} q_s(r, k) q_t(c, k) 2^(-7 (s + t))
+// and the pairs with s + t = l <= 6 are summed over k by BF16 MMAs into the FP32 tensor-memory
+// accumulator of level l: every product is an integer of at most 2^14 and a level sums at most
+// 7 x 64 of them (< 2^23), so the accumulators are exact.  Pairs with s + t > 6 lie below 2^-49 of
+// the scale and are dropped (the double-float arithmetic keeps 2^-48).  The epilogue adds the levels
+// in double-float from the smallest up, scales by the power of two and subtracts from C (pairs in
+// place).
+// Work item = (block, 32 columns n0): the seven 32 x 64 B planes of rows n0.. stay in shared memory
+// (double-buffered across items) while the 128-row A tiles of rows >= n0 - 127 stream through an
+// eight-stage ring, one plane per stage; 28 pairs x 4 K-steps = 112 MMAs (M = 128, N = 32, K = 16)
+// per tile into 7 x 32 accumulator columns, two accumulator sets.  Items go round-robin to the CTAs
+// (neighbouring columns of one block run side by side and share its A planes in L2).  Roles (320
+// threads): warp 0 TMA producer, warp 1 MMA issuer, warps 2..9 epilogue (two per TMEM lane quarter,
+// 16 columns each).  Waits are bounded as in ns_tc_kernel.
+constexpr int OZ_NSL = 7;
+constexpr int OZ_TN = 32;
+constexpr int OZ_NST = 8;
+constexpr int OZ_A_BYTES = TM * kOzPanel * 2;                  // one plane of a 128-row tile
+constexpr int OZ_PLANE_B = OZ_TN * kOzPanel * 2;               // one plane of 32 rows
+constexpr int OZ_B_BYTES = OZ_NSL * OZ_PLANE_B;                // 28 KB
+constexpr int OZ_B_OFF = OZ_NST * OZ_A_BYTES;
+constexpr int OZ_BAR_OFF = OZ_B_OFF + 2 * OZ_B_BYTES;
+constexpr int OZ_SMEM = 1024 + OZ_BAR_OFF + 256;
+constexpr int OZ_THREADS = 320;
+constexpr int OZ_ACC = 256;                                     // column offset of the second set
+static_assert(OZ_NSL * OZ_TN <= OZ_ACC, "accumulator set");
+static_assert(OZ_SMEM <= 227 * 1024, "shared memory of the update kernel");
+static_assert(kOzPanel == TK, "one 128-byte swizzle row per plane row");
+
+struct OzParams {
+  const int32_t* items;         // (block, n0) pairs of this panel
+  int n_items;
+  const BlockDesc* blocks;
+  const CUtensorMap* maps;      // [0]: 64 x 128 boxes, [1]: 64 x 32 boxes over the slice planes
+  double* pool;
+  const int32_t* scale_exp;
+  int t0;                       // first trailing row / column
+  DevFlags* flags;
+  long long budget;
+};
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// first 128-row tile of column chunk n0 that reaches the diagonal
+__device__ __forceinline__ int oz_first_m(int t0, int n0) {
+  const int d = n0 - t0 - (TM - 1);
+  return t0 + (d > 0 ? (d + TM - 1) / TM : 0) * TM;
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1) chol_update_kernel(const __grid_constant__ OzParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OZ_BAR_OFF);
+  uint64_t* full_bar = bars;                        // [OZ_NST]
+  uint64_t* empty_bar = bars + OZ_NST;              // [OZ_NST]
+  uint64_t* bfull_bar = bars + 2 * OZ_NST;          // [2]
+  uint64_t* bempty_bar = bars + 2 * OZ_NST + 2;     // [2]
+  uint64_t* tfull_bar = bars + 2 * OZ_NST + 4;      // [2]
+  uint64_t* tempty_bar = bars + 2 * OZ_NST + 6;     // [2]
+  uint64_t* drain_bar = bars + 2 * OZ_NST + 8;      // [1]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * OZ_NST + 9);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < OZ_NST; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&bfull_bar[a], 1);
+      mbar_init(&bempty_bar[a], 1);
+      mbar_init(&tfull_bar[a], 1);
+      mbar_init(&tempty_bar[a], 256);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const long long budget = p.budget;
+  const long long drain_budget = budget > (1LL << 22) ? budget : (1LL << 22);
+  const int t0 = p.t0;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int ps = 0, bb = 0;
+      uint32_t pph = 0, bph[2] = {0u, 0u};
+      uint32_t armed = 0, arm_parity = 0, barmed = 0, barm_parity = 0;
+      bool ok = true;
+      for (int it = blockIdx.x; it < p.n_items && ok; it += gridDim.x) {
+        const int b = p.items[2 * it], n0 = p.items[2 * it + 1];
+        const BlockDesc bd = p.blocks[b];
+        const int np = bd.n_pad, rbase = 7 * bd.row_off;
+        if (!mbar_wait(&bempty_bar[bb], bph[bb] ^ 1u, budget, abort_flag)) { ok = false; break; }
+        mbar_expect_tx(&bfull_bar[bb], OZ_B_BYTES);
+        uint8_t* bdst = smem + OZ_B_OFF + bb * OZ_B_BYTES;
+        for (int t = 0; t < OZ_NSL; ++t) tma_load_2d(bdst + t * OZ_PLANE_B, p.maps + 1, &bfull_bar[bb], 0, rbase + t * np + n0);
+        barmed |= 1u << bb;
+        barm_parity = (barm_parity & ~(1u << bb)) | (bph[bb] << bb);
+        bph[bb] ^= 1u;
+        bb ^= 1;
+        for (int m0 = oz_first_m(t0, n0); m0 < bd.n && ok; m0 += TM)
+          for (int s = 0; s < OZ_NSL; ++s) {
+            if (!mbar_wait(&empty_bar[ps], pph ^ 1u, budget, abort_flag)) { ok = false; break; }
+            mbar_expect_tx(&full_bar[ps], OZ_A_BYTES);
+            tma_load_2d(smem + ps * OZ_A_BYTES, p.maps, &full_bar[ps], 0, rbase + s * np + m0);
+            armed |= 1u << ps;
+            arm_parity = (arm_parity & ~(1u << ps)) | (pph << ps);
+            if (++ps == OZ_NST) { ps = 0; pph ^= 1u; }
+          }
+      }
+      if (!ok) {
+        set_error(p.flags, NOLSM_ETIMEOUT);
+        *abort_flag = 1;
+      }
+      // every copy issued here lands before the CTA's shared memory goes away
+      volatile int never = 0;
+      for (int s = 0; s < OZ_NST; ++s)
+        if (armed & (1u << s)) mbar_wait(&full_bar[s], (arm_parity >> s) & 1u, drain_budget, &never);
+      for (int a = 0; a < 2; ++a)
+        if (barmed & (1u << a)) mbar_wait(&bfull_bar[a], (barm_parity >> a) & 1u, drain_budget, &never);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc(1, TM, OZ_TN);   // BF16 operands
+      int ms = 0, bb = 0, acc = 0;
+      uint32_t mph = 0, bph[2] = {0u, 0u}, tph[2] = {0u, 0u};
+      bool ok = true;
+      for (int it = blockIdx.x; it < p.n_items && ok; it += gridDim.x) {
+        const int b = p.items[2 * it], n0 = p.items[2 * it + 1];
+        const int nb = p.blocks[b].n;
+        if (!mbar_wait(&bfull_bar[bb], bph[bb], budget, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t b_addr = smem_u32(smem + OZ_B_OFF + bb * OZ_B_BYTES);
+        for (int m0 = oz_first_m(t0, n0); m0 < nb && ok; m0 += TM) {
+          if (!mbar_wait(&tempty_bar[acc], tph[acc] ^ 1u, budget, abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t d0 = tmem_base + (uint32_t)(acc * OZ_ACC);
+          for (int s = 0; s < OZ_NSL; ++s) {
+            if (!mbar_wait(&full_bar[ms], mph, budget, abort_flag)) { ok = false; break; }
+            tc_fence_after();
+            const uint64_t adesc = sw128_desc(smem_u32(smem + ms * OZ_A_BYTES));
+            for (int t = 0; t + s < OZ_NSL; ++t) {
+              const uint64_t bdesc = sw128_desc(b_addr + (uint32_t)(t * OZ_PLANE_B));
+              const uint32_t d = d0 + (uint32_t)((s + t) * OZ_TN);
+#pragma unroll
+              for (int kk = 0; kk < kOzPanel / 16; ++kk)
+                umma_f16(d, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), idesc, (s | kk) != 0);
+            }
+            umma_commit(&empty_bar[ms]);
+            if (++ms == OZ_NST) { ms = 0; mph ^= 1u; }
+          }
+          if (!ok) break;
+          umma_commit(&tfull_bar[acc]);
+          tph[acc] ^= 1u;
+          acc ^= 1;
+        }
+        if (!ok) break;
+        umma_commit(&bempty_bar[bb]);   // the item's planes are free once its products are done
+        bph[bb] ^= 1u;
+        bb ^= 1;
+      }
+      if (!ok) {
+        set_error(p.flags, NOLSM_ETIMEOUT);
+        *abort_flag = 1;
+      }
+      umma_commit(drain_bar);
+      volatile int never = 0;
+      mbar_wait(drain_bar, 0, drain_budget, &never);
+    }
+  } else {
+    const int q = warp & 3, half = (warp - 2) >> 2;
+    int acc = 0;
+    uint32_t tph[2] = {0u, 0u};
+    for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
+      const int b = p.items[2 * it], n0 = p.items[2 * it + 1];
+      const BlockDesc bd = p.blocks[b];
+      const int np = bd.n_pad, n = bd.n;
+      float2* C = reinterpret_cast<float2*>(p.pool + bd.off_mat);
+      const int32_t* ex = p.scale_exp + bd.row_off;
+      bool stop = false;
+      for (int m0 = oz_first_m(t0, n0); m0 < n; m0 += TM) {
+        if (!__all_sync(0xffffffffu, mbar_wait(&tfull_bar[acc], tph[acc], budget, abort_flag))) {
+          set_error(p.flags, NOLSM_ETIMEOUT);
+          *abort_flag = 1;
+          stop = true;
+          break;
+        }
+        tc_fence_after();
+        const int r = m0 + q * 32 + lane;
+        const int er = r < n ? ex[r] : 0;
+        for (int ch = 0; ch < 2; ++ch) {
+          const int c0 = n0 + half * 16 + ch * 8;
+          if (c0 > m0 + q * 32 + 31) continue;       // chunk above every row of this warp (uniform)
+          uint32_t v[OZ_NSL][8];
+          const uint32_t tb = tmem_base + (uint32_t)(acc * OZ_ACC + half * 16 + ch * 8) + ((uint32_t)(q * 32) << 16);
+#pragma unroll
+          for (int l = 0; l < OZ_NSL; ++l) tmem_ld8(tb + (uint32_t)(l * OZ_TN), v[l]);
+          tmem_wait_ld();
+          if (r >= n || c0 > r) continue;
+          float4* crow = reinterpret_cast<float4*>(C + (int64_t)r * np + c0);
+          float4 cv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) cv[u] = crow[u];
+          float* cf = reinterpret_cast<float*>(cv);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int c = c0 + j;
+            if (c > r) break;
+            // sum_l v_l 2^(-7 l) in double-float, smallest level first (every term is exact)
+            float h = __uint_as_float(v[OZ_NSL - 1][j]) * 0x1p-42f, lo = 0.f;
+#pragma unroll
+            for (int l = OZ_NSL - 2; l >= 0; --l) {
+              const float x = __uint_as_float(v[l][j]) * __int_as_float((127 - 7 * l) << 23);
+              const float s = h + x;
+              const float bb2 = s - h;
+              lo += (h - (s - bb2)) + (x - bb2);
+              h = s;
+            }
+            const float sc = __int_as_float((127 + er + ex[c] - 14) << 23);
+            h *= sc;
+            lo *= sc;
+            // C - (h + lo), renormalised
+            const float ch0 = cf[2 * j], cl0 = cf[2 * j + 1];
+            const float s = ch0 - h;
+            const float bb2 = s - ch0;
+            const float err = (ch0 - (s - bb2)) - (h + bb2);
+            const float t = err + cl0 - lo;
+            const float sh = s + t;                  // TwoSum(s, t)
+            const float bb3 = sh - s;
+            cf[2 * j] = sh;
+            cf[2 * j + 1] = (s - (sh - bb3)) + (t - bb3);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) crow[u] = cv[u];
+        }
+        tc_fence_before();
+        mbar_arrive(&tempty_bar[acc]);
+        tph[acc] ^= 1u;
+        acc ^= 1;
+      }
+      if (stop) break;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // The congruence A0 = L^-1 T_b(H0) L^-T on the tensor cores, FP32-accurate by three TF32 passes.
 // A product C = A B^T (both operands row-major, K contiguous) over a tile list of 128 x 128 tiles.
 // Each FP32 operand x is split in shared memory into hi = x rounded to TF32 (exact in TF32) and
@@ -1556,6 +1832,9 @@ cudaError_t launch_gemm_tc(nolsm_ctx* ctx, int phase) {
   p.flags = ctx->d_flags;
   p.budget = ctx->opt.wait_budget;
   p.phase = phase;
+  int max_pad = 0;
+  for (const auto& bd : ctx->h_blocks) max_pad = std::max(max_pad, bd.n_pad);
+  p.interleave = max_pad >= 1024;
   const int grid = ctx->num_sms;
   // each CTA resolves at most MAX_LOCAL tiles per launch; cover the largest possible list
   const int64_t per_launch = (int64_t)MAX_LOCAL * grid;
@@ -1655,6 +1934,79 @@ cudaError_t launch_congruence_tc(nolsm_ctx* ctx, float* t1) {
 }
 
 int tc_tile_n() { return TN; }
+
+// Work items (block, 32-column chunk) of every panel's trailing update, and two tensor maps over the
+// slice planes (7 n_pad rows of 64 BF16 per block, blocks in layout order).
+cudaError_t oz_prepare(nolsm_ctx* ctx) {
+  auto encode = get_encode();
+  if (!encode || !ctx->d_oz_planes) return cudaErrorNotSupported;
+  int max_pad = 0;
+  for (const auto& bd : ctx->h_blocks) max_pad = std::max(max_pad, bd.n_pad);
+  const int panels = (max_pad + kOzPanel - 1) / kOzPanel;
+  ctx->h_oz_items.clear();
+  ctx->h_oz_panel.assign((size_t)panels + 1, 0);
+  for (int pnl = 0; pnl < panels; ++pnl) {
+    ctx->h_oz_panel[pnl] = (int64_t)ctx->h_oz_items.size() / 2;
+    const int t0 = (pnl + 1) * kOzPanel;
+    for (int32_t b = 0; b < ctx->n_blocks; ++b) {
+      const BlockDesc& bd = ctx->h_blocks[b];
+      if (t0 >= bd.n) continue;
+      for (int n0 = t0; n0 < bd.n; n0 += OZ_TN) ctx->h_oz_items.insert(ctx->h_oz_items.end(), {b, n0});
+    }
+  }
+  ctx->h_oz_panel[panels] = (int64_t)ctx->h_oz_items.size() / 2;
+  if (!ctx->h_oz_items.empty()) {
+    cudaError_t e = cudaMemcpyAsync(ctx->d_oz_items, ctx->h_oz_items.data(), sizeof(int32_t) * ctx->h_oz_items.size(),
+                                    cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return e;
+  }
+  CUtensorMap maps[2];
+  const uint64_t rows = (uint64_t)7 * (uint64_t)std::max<int64_t>(ctx->sum_pad, 1);
+  cuuint64_t gdim[2] = {(cuuint64_t)kOzPanel, rows};
+  cuuint64_t gstride[1] = {(cuuint64_t)kOzPanel * 2};
+  cuuint32_t estr[2] = {1, 1};
+  cuuint32_t box_a[2] = {(cuuint32_t)kOzPanel, (cuuint32_t)TM};
+  cuuint32_t box_b[2] = {(cuuint32_t)kOzPanel, (cuuint32_t)OZ_TN};
+  CUresult r = encode(&maps[0], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ctx->d_oz_planes, gdim, gstride, box_a, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r == CUDA_SUCCESS)
+    r = encode(&maps[1], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ctx->d_oz_planes, gdim, gstride, box_b, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemcpyAsync(ctx->d_oz_tmaps, maps, sizeof(maps), cudaMemcpyHostToDevice, ctx->stream);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(ctx->stream);   // maps is a host temporary
+  if (e != cudaSuccess) return e;
+  static bool attr_done = false;
+  if (!attr_done) {
+    e = cudaFuncSetAttribute(chol_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_chol_update_tc(nolsm_ctx* ctx, int panel, double* pool) {
+  if (panel + 1 >= (int)ctx->h_oz_panel.size()) return cudaSuccess;
+  const int64_t first = ctx->h_oz_panel[panel], count = ctx->h_oz_panel[panel + 1] - first;
+  if (count <= 0) return cudaSuccess;
+  OzParams p;
+  p.items = ctx->d_oz_items + 2 * first;
+  p.n_items = (int)count;
+  p.blocks = ctx->d_blocks;
+  p.maps = reinterpret_cast<const CUtensorMap*>(ctx->d_oz_tmaps);
+  p.pool = pool;
+  p.scale_exp = ctx->d_oz_exp;
+  p.t0 = (panel + 1) * kOzPanel;
+  p.flags = ctx->d_flags;
+  p.budget = ctx->opt.wait_budget;
+  const int grid = (int)std::min<int64_t>(ctx->num_sms, count);
+  chol_update_kernel<<<grid, OZ_THREADS, OZ_SMEM, ctx->stream>>>(p);
+  ctx->n_launches += 1;
+  return cudaGetLastError();
+}
 
 // The refinement on the tensor cores: narrow pieces (<= 32 columns, eight 24 KB stages), then wide
 // ones (<= 192 columns, three 64 KB stages), one persistent CTA per SM each.  Slab scratch: P1 and

@@ -20,13 +20,13 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOTPD", "ENOCONV", "EBRACKE
 MEM_DEVICE, MEM_HOST = 0, 1
 PREC_FP32, PREC_MIXED_FP16, PREC_MIXED_BF16 = 1, 2, 3
 BOUNDS_GERSHGORIN, BOUNDS_LANCZOS, BOUNDS_LEARNED = 0, 1, 2
-CHOL_FP64, CHOL_FP32, CHOL_FP64_INV64, CHOL_DF64 = 0, 1, 2, 3
-SCHEDULE_PERSISTENT, SCHEDULE_PER_PRODUCT = 0, 1
+CHOL_FP64, CHOL_FP32, CHOL_FP64_INV64, CHOL_DF64, CHOL_DF64_SIMT = 0, 1, 2, 3, 4
+SCHEDULE_PERSISTENT, SCHEDULE_PER_PRODUCT, SCHEDULE_AUTO = 0, 1, 2
 REFINE_TENSOR, REFINE_SIMT = 0, 1
 
 FUNCTIONS = ["nolsm_default_options", "nolsm_create", "nolsm_build_submatrices", "nolsm_sign_batch", "nolsm_set_mu",
              "nolsm_density", "nolsm_band_energy", "nolsm_block_info", "nolsm_block_index_set", "nolsm_block_bounds",
-             "nolsm_block_state", "nolsm_block_matrix", "nolsm_counters", "nolsm_phase_times", "nolsm_set_wait_budget",
+             "nolsm_block_state", "nolsm_block_matrix", "nolsm_block_factor", "nolsm_counters", "nolsm_phase_times", "nolsm_set_wait_budget",
              "nolsm_band_energy_noalloc",
              "nolsm_block_features", "nolsm_block_lanczos", "nolsm_mlp_create", "nolsm_mlp_get_params",
              "nolsm_mlp_gradient", "nolsm_mlp_adam", "nolsm_mlp_predict", "nolsm_mlp_destroy", "nolsm_set_predictor",
@@ -88,6 +88,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "nolsm_block_bounds": (i32, [P, P, P]),
         "nolsm_block_state": (i32, [P, P, P, P]),
         "nolsm_block_matrix": (i32, [P, i32, i32, P]),
+        "nolsm_block_factor": (i32, [P, i32, P]),
         "nolsm_counters": (i32, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), pf64, pf64, i32]),
         "nolsm_band_energy_noalloc": (i32, [i64, P, P, f64, P, P]),
         "nolsm_phase_times": (i32, [P, pf64, i32, i32]),
@@ -205,6 +206,13 @@ def nolsm_block_matrix(ctx, b, which=0) -> np.ndarray:
     n, _ = nolsm_block_info(ctx, b)
     out = np.empty((n, n), np.float32)
     _check(ctx, _lib.nolsm_block_matrix(ctx, int(b), int(which), out.ctypes.data))
+    return out
+
+
+def nolsm_block_factor(ctx, b) -> np.ndarray:
+    n, _ = nolsm_block_info(ctx, b)
+    out = np.empty((n, n), np.float64)
+    _check(ctx, _lib.nolsm_block_factor(ctx, int(b), out.ctypes.data))
     return out
 
 
@@ -410,6 +418,9 @@ class Nolsm:
 
     def block_matrix(self, b, which=0):
         return nolsm_block_matrix(self.ctx, b, which)
+
+    def block_factor(self, b):
+        return nolsm_block_factor(self.ctx, b)
 
 
 class BoundPredictor:

@@ -36,7 +36,7 @@ def orc1(sys1):
     return NolsmOracle.from_system(sys1)
 
 
-@pytest.mark.parametrize("chol", [0, 1, 2, 3])
+@pytest.mark.parametrize("chol", [0, 1, 2, 3, 4])
 def test_factor_matches_lapack(nl, sys1, orc1, chol):
     lib = nl.Nolsm(precision=nl.PREC_FP32, chol_precision=chol).build(sys1)
     for b in [0, 5, 31, 63]:
@@ -47,12 +47,50 @@ def test_factor_matches_lapack(nl, sys1, orc1, chol):
         if chol == nl.CHOL_FP32:
             np.testing.assert_allclose(got, ref, rtol=0, atol=2e-5)
             continue
-        # an FP64-accurate factor rounds to LAPACK's FP32 rounding, up to rounding-boundary cases
+        # an FP64-accurate factor rounds to LAPACK's FP32 rounding, up to rounding-boundary cases.
+        # The tensor-core updates slice every entry on its row's scale sqrt(S_rr), so their error
+        # (~1e-13) is normwise: entries far below the scale (the decaying tail of L, down to 1e-20)
+        # carry it as many of their own ulps, and the entrywise check covers |L| >= 1e-4 there.
         ref32 = ref.astype(np.float32)
         diff = np.abs(got - ref32.astype(np.float64))
         ulp = np.spacing(np.abs(ref32)).astype(np.float64)
-        assert np.all(diff <= ulp), (b, float((diff / np.maximum(ulp, 1e-45)).max()))
-        assert np.count_nonzero(diff) <= 1e-3 * diff.size
+        sel = np.abs(ref) >= 1e-4 if chol == nl.CHOL_DF64 else np.ones(ref.shape, bool)
+        assert np.all(diff[sel] <= ulp[sel]), (b, float((diff[sel] / np.maximum(ulp[sel], 1e-45)).max()))
+        assert np.count_nonzero(diff[sel]) <= 1e-3 * diff.size
+
+
+@pytest.mark.parametrize("chol", ["df64_tensor", "df64_simt", "fp64"])
+def test_factor_fp64_accuracy(nl, sys1, orc1, chol):
+    """The factor as computed (before any FP32 rounding) against LAPACK's FP64 factor, relative to
+    the row scales sqrt(S_rr S_cc) (O(1) here): the double-float modes carry a 48-bit significand
+    (n_b ~ 200 terms: a few 1e-14), the tensor-core updates 49 bits of every slice product."""
+    mode = {"df64_tensor": nl.CHOL_DF64, "df64_simt": nl.CHOL_DF64_SIMT, "fp64": nl.CHOL_FP64}[chol]
+    bound = 1e-15 if chol == "fp64" else 1.5e-13
+    lib = nl.Nolsm(precision=nl.PREC_FP32, chol_precision=mode).build(sys1)
+    for b in [0, 5, 31, 63]:
+        _, _, sb = orc1.submatrices(b)
+        ref = np.linalg.cholesky(sb)
+        scale = np.sqrt(np.outer(np.diag(sb), np.diag(sb)))
+        err = np.abs(lib.block_factor(b) - ref) / scale
+        assert err.max() <= bound, (b, float(err.max()))
+
+
+def test_blocked_factor_on_large_blocks(nl):
+    """n_b ~ 1,900 (30 panels of the blocked factorisation, 29 tensor-core trailing updates):
+    the tensor-core factor against LAPACK and against the all-SIMT double-float factor."""
+    from synth import water_clusters
+    s = water_clusters(12, seed=41, cluster=(3, 3, 4))
+    o = NolsmOracle.from_system(s, blocks=np.array([0, 29]))
+    t = nl.Nolsm(precision=nl.PREC_MIXED_FP16, chol_precision=nl.CHOL_DF64).build(s)
+    u = nl.Nolsm(precision=nl.PREC_MIXED_FP16, chol_precision=nl.CHOL_DF64_SIMT).build(s)
+    for b in [0, 29]:
+        _, _, sb = o.submatrices(b)
+        ref = np.linalg.cholesky(sb)
+        lt, lu = t.block_factor(b), u.block_factor(b)
+        # ~n_b x 2^-48 (double-float sums over 1,900 terms) on O(1) row scales
+        assert np.abs(lt - ref).max() <= 6e-13
+        assert np.abs(lu - ref).max() <= 6e-13
+        assert np.abs(lt - lu).max() <= 6e-13
 
 
 def test_double_float_and_fp64_factor_agree_downstream(nl, sys1):
@@ -60,7 +98,8 @@ def test_double_float_and_fp64_factor_agree_downstream(nl, sys1):
     d = nl.Nolsm(precision=nl.PREC_FP32, chol_precision=nl.CHOL_DF64).build(sys1)
     for b in [0, 17, 63]:
         la, ld = a.block_matrix(b, 5), d.block_matrix(b, 5)
-        assert np.mean(la == ld) >= 0.999
+        big = np.abs(la) >= 1e-4           # below, the normwise ~1e-13 of the sliced updates shows
+        assert np.mean(la[big] == ld[big]) >= 0.999
         np.testing.assert_allclose(ld, la, rtol=0, atol=np.spacing(np.float32(4.0)))
         for which in (1, 0):
             x, y = a.block_matrix(b, which), d.block_matrix(b, which)

@@ -100,3 +100,20 @@ def test_cluster_blocks_sampled_parity(nl):
     own = np.isin(s.col, np.concatenate([s.block_cols(int(b)) for b in sample]))
     assert np.abs(d[own] - o.density(mu)[own]).max() <= 1e-3
     assert np.isfinite(e)
+
+
+def test_schedules_agree_on_large_blocks(nl):
+    """n_pad 2,048: the per-product launches deal tiles round-robin over the SMs; the persistent
+    pair kernel takes whole blocks.  Same arithmetic and stopping rules, so the same iterations."""
+    s = water_clusters(12, seed=41, cluster=(3, 3, 4))
+    out = {}
+    for sched in (nl.SCHEDULE_PERSISTENT, nl.SCHEDULE_PER_PRODUCT, nl.SCHEDULE_AUTO):
+        lib = nl.Nolsm(precision=nl.PREC_MIXED_FP16, schedule=sched).build(s)
+        st = lib.sign_batch(-0.45)
+        out[sched] = (lib.iters(), lib.density().cpu().numpy(), st["n_electrons"])
+        lib.close()
+    (ia, da, na), (ib, db, nb) = out[nl.SCHEDULE_PERSISTENT], out[nl.SCHEDULE_PER_PRODUCT]
+    assert np.mean(ia == ib) >= 0.95
+    assert np.abs(da - db).max() <= 1e-4
+    assert na == pytest.approx(nb, rel=1e-5)
+    np.testing.assert_array_equal(out[nl.SCHEDULE_AUTO][1], db)   # AUTO picks per-product here
