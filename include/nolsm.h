@@ -232,8 +232,8 @@ nolsm_status nolsm_block_state(const nolsm_ctx* ctx, int32_t* iters, double* res
 nolsm_status nolsm_block_matrix(const nolsm_ctx* ctx, int32_t b, int32_t which, float* out);
 
 /* Diagnostic copy of block b's Cholesky factor L of T_b(S) at the precision it was computed in
- * (FP64 modes and both double-float modes: the FP64 lower triangle; CHOL_FP32: the FP32 factor
- * widened), n_b x n_b row-major in host memory, zero above the diagonal.  Synchronises. */
+ * (FP64 modes: the FP64 lower triangle; double-float modes: each pair's value h + l; CHOL_FP32: the
+ * FP32 factor widened), n_b x n_b row-major in host memory, zero above the diagonal.  Synchronises. */
 nolsm_status nolsm_block_factor(const nolsm_ctx* ctx, int32_t b, double* out);
 
 /* Cumulative counters of ctx since nolsm_create or the last reset (reset != 0 zeroes them after

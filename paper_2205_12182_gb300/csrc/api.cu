@@ -512,7 +512,9 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   ctx->cong_simt = !mixed;   // FP32 path: SIMT products with two-level sums; mixed: tensor cores (3 x TF32)
   CK(launch_congruence(ctx, ctx->d_t1));
   CK(phase_mark(ctx, NOLSM_PHASE_BUILD_REST));
-  CK(launch_slabs_impl(ctx, chol32 ? (const void*)(sb + ctx->sum_sq) : (const void*)sb, chol32, ctx->d_t1));
+  // the trace slab takes the factor's FP32 rounding (FP32 and double-float modes) or the FP64 factor
+  const int l32 = chol32 || chol_mode == NOLSM_CHOL_DF64 || chol_mode == NOLSM_CHOL_DF64_SIMT;
+  CK(launch_slabs_impl(ctx, l32 ? (const void*)(sb + ctx->sum_sq) : (const void*)sb, l32, ctx->d_t1));
   CK(dalloc(ctx, &ctx->d_rowd, (size_t)ctx->n_blocks * kMaxDim));
   CK(dalloc(ctx, &ctx->d_rowr, (size_t)ctx->n_blocks * kMaxDim));
   CK(launch_bounds(ctx));
@@ -845,6 +847,16 @@ nolsm_status nolsm_block_state(const nolsm_ctx* ctx, int32_t* iters, double* res
   return NOLSM_OK;
 }
 
+// The double-float modes leave the factor as pairs (h, l) of floats in the 8 bytes of each double.
+static bool factor_in_pairs(const nolsm_ctx* ctx) {
+  return ctx->opt.chol_precision == NOLSM_CHOL_DF64 || ctx->opt.chol_precision == NOLSM_CHOL_DF64_SIMT;
+}
+static double pair_value(double raw) {
+  float hl[2];
+  std::memcpy(hl, &raw, sizeof(hl));
+  return (double)hl[0] + (double)hl[1];
+}
+
 nolsm_status nolsm_block_factor(const nolsm_ctx* ctx, int32_t b, double* out) {
   if (!ctx || !ctx->built || b < 0 || b >= ctx->n_blocks || !out) return NOLSM_EINVAL;
   const BlockDesc& bd = ctx->h_blocks[b];
@@ -856,9 +868,12 @@ nolsm_status nolsm_block_factor(const nolsm_ctx* ctx, int32_t b, double* out) {
                      cudaMemcpyDeviceToHost) != cudaSuccess)
       return NOLSM_ECUDA;
     for (size_t i = 0; i < l.size(); ++i) out[i] = l[i];
-  } else if (cudaMemcpy2D(out, sizeof(double) * bd.n, ctx->d_sb + bd.off_mat, sizeof(double) * bd.n_pad,
-                          sizeof(double) * bd.n, bd.n, cudaMemcpyDeviceToHost) != cudaSuccess) {
-    return NOLSM_ECUDA;
+  } else {
+    if (cudaMemcpy2D(out, sizeof(double) * bd.n, ctx->d_sb + bd.off_mat, sizeof(double) * bd.n_pad,
+                     sizeof(double) * bd.n, bd.n, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return NOLSM_ECUDA;
+    if (factor_in_pairs(ctx))
+      for (size_t i = 0; i < (size_t)bd.n * bd.n; ++i) out[i] = pair_value(out[i]);
   }
   for (int r = 0; r < bd.n; ++r)
     for (int c = r + 1; c < bd.n; ++c) out[(size_t)r * bd.n + c] = 0.0;
@@ -882,7 +897,7 @@ nolsm_status nolsm_block_matrix(const nolsm_ctx* ctx, int32_t b, int32_t which, 
       if (cudaMemcpy2D(l.data(), sizeof(double) * bd.n, ctx->d_sb + bd.off_mat, sizeof(double) * bd.n_pad,
                        sizeof(double) * bd.n, bd.n, cudaMemcpyDeviceToHost) != cudaSuccess)
         return NOLSM_ECUDA;
-      for (size_t i = 0; i < nn; ++i) out[i] = (float)l[i];
+      for (size_t i = 0; i < nn; ++i) out[i] = (float)(factor_in_pairs(ctx) ? pair_value(l[i]) : l[i]);
     }
     for (int r = 0; r < bd.n; ++r)
       for (int c = r + 1; c < bd.n; ++c) out[(size_t)r * bd.n + c] = 0.f;

@@ -21,24 +21,51 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t* a, int n, int32_t 
 __device__ __forceinline__ void set_error(DevFlags* f, int code) { atomicCAS(&f->error, 0, code); }
 
 // ----------------------------------------------------------------------------------------------
-// Gather: dense T_b(H0) (FP32) and T_b(S) (FP64), ld = n_pad, from the CSR rows listed in I_b.
-// One CTA per block: it first writes the block's whole padded region (zeros, and a unit
-// diagonal of S on the padding), then one warp per local row scatters the row's stored entries;
-// I_b sits in shared memory for the column lookup (binary search).
+// FP64 -> double-float pair with integer operations (the FP64 pipe of this GPU issues at 1/64 of
+// the FP32 rate): h = x rounded to nearest-even FP32, l = x - h rounded to FP32 -- the same pair as
+// (float)x and (float)(x - (double)(float)x).  Zero and |x| outside [2^-60, 2^101) take the FP64
+// route.
+__device__ __forceinline__ float2 df_pair_from_f64(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int be = (int)((b >> 52) & 0x7FFu) - 1023;
+  if (be < -60 || be > 100) {
+    const float h = (float)x;
+    return make_float2(h, (float)(x - (double)h));
+  }
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);   // 53-bit significand
+  unsigned int top = (unsigned int)(m >> 29);                             // its leading 24 bits
+  const unsigned int rest = (unsigned int)(m & 0x1FFFFFFFull);            // the other 29
+  const bool up = rest > 0x10000000u || (rest == 0x10000000u && (top & 1u));
+  top += up ? 1u : 0u;
+  const int lm = (int)rest - (up ? 0x20000000 : 0);                       // x - h in units of 2^(be-52)
+  float h = (float)top * __int_as_float((be - 23 + 127) << 23);           // exact
+  float l = (float)lm * __int_as_float((be - 52 + 127) << 23);            // rounded to 24 bits, then exact
+  if (b >> 63) { h = -h; l = -l; }
+  return make_float2(h, l);
+}
+
+// ----------------------------------------------------------------------------------------------
+// Gather: dense T_b(H0) (FP32) and T_b(S) (FP64, or double-float pairs in the same 8 bytes when
+// `pairs`), ld = n_pad, from the CSR rows listed in I_b.  One CTA per block: it first writes the
+// block's whole padded region (zeros, and a unit diagonal of S on the padding), then one warp per
+// local row scatters the row's stored entries; I_b sits in shared memory for the column lookup
+// (binary search).
 __global__ void gather_kernel(const BlockDesc* __restrict__ blocks, const int32_t* __restrict__ idx_pool,
                               const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                               const double* __restrict__ hval, const double* __restrict__ sval,
-                              float* __restrict__ hb, double* __restrict__ sb, DevFlags* flags) {
+                              float* __restrict__ hb, double* __restrict__ sb, DevFlags* flags, int pairs) {
   extern __shared__ int32_t s_idx[];
   const BlockDesc bd = blocks[blockIdx.x];
   const int n = bd.n, ld = bd.n_pad;
   float* H = hb + bd.off_mat;
   double* S = sb + bd.off_mat;
+  float2* S2 = reinterpret_cast<float2*>(S);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   for (int r = warp; r < ld; r += nwarps)
     for (int c = lane; c < ld; c += 32) {
       H[(int64_t)r * ld + c] = 0.f;
-      S[(int64_t)r * ld + c] = (r == c && r >= n) ? 1.0 : 0.0;
+      if (pairs) S2[(int64_t)r * ld + c] = make_float2((r == c && r >= n) ? 1.f : 0.f, 0.f);
+      else S[(int64_t)r * ld + c] = (r == c && r >= n) ? 1.0 : 0.0;
     }
   for (int i = threadIdx.x; i < n; i += blockDim.x) s_idx[i] = idx_pool[bd.off_idx + i];
   __syncthreads();
@@ -52,7 +79,8 @@ __global__ void gather_kernel(const BlockDesc* __restrict__ blocks, const int32_
         const double h = hval[e], s = sval[e];
         if (!isfinite(h) || !isfinite(s)) set_error(flags, NOLSM_ENONFINITE);
         H[(int64_t)p * ld + q] = (float)h;
-        S[(int64_t)p * ld + q] = s;
+        if (pairs) S2[(int64_t)p * ld + q] = df_pair_from_f64(s);
+        else S[(int64_t)p * ld + q] = s;
       }
     }
   }
@@ -190,15 +218,6 @@ struct __align__(8) df32 {
   float h, l;
 };
 
-__device__ __forceinline__ df32 df_from_bits(float2 raw) {   // FP64 bit pattern stored as float2
-  const double x = __hiloint2double(__float_as_int(raw.y), __float_as_int(raw.x));
-  const float h = (float)x;
-  return {h, (float)(x - (double)h)};
-}
-__device__ __forceinline__ float2 df_to_bits(df32 a) {
-  const double x = (double)a.h + (double)a.l;
-  return make_float2(__int_as_float(__double2loint(x)), __int_as_float(__double2hiint(x)));
-}
 __device__ __forceinline__ double df_to_double(df32 a) { return (double)a.h + (double)a.l; }
 __device__ __forceinline__ df32 df_from_double(double x) {
   const float h = (float)x;
@@ -253,23 +272,22 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Cholesky S = L L^T in double-float, left-looking by 32-column panels, in place over the FP64
-// pool (a pair occupies the 8 bytes of the double it replaces).  One CTA of 4 warps per block;
+// Cholesky S = L L^T in double-float, left-looking by 32-column panels, in place over the pool of
+// pairs the gather wrote (a pair occupies the 8 bytes of a double).  One CTA of 4 warps per block;
 // every 32-row tile is shared by the 4 warps, each taking 8 of every 32 k (no idle warps when a
 // panel has few tiles), the four partial tiles summed in shared memory.  One launch covers the
 // columns [c_beg, c_end): the whole factor (0, n), or one panel of the blocked factorization whose
 // trailing updates run on the tensor cores (the columns before c_beg are then already subtracted
 // from the panel, so the left-looking sums start at c_beg).
-//   0. (c_beg = 0) the lower triangle of S is converted from FP64 to pairs; with scale_exp given,
-//      each row's slicing exponent e_r (2^e_r >= sqrt(S_rr) >= |L_rk|) is written first;
+//   0. (c_beg = 0, scale_exp given) each row's slicing exponent e_r (2^e_r >= sqrt(S_rr) >= |L_rk|);
 //   for each 32-column panel j0 in [c_beg, c_end):
 //   1. R[r, panel] = S[r, panel] - L[r, 0:j0] L[panel, 0:j0]^T for rows r >= j0: 32 x 32 operand
 //      chunks double-buffered in shared memory with cp.async;
 //   2. warp 0 factors the 32x32 diagonal block of R in FP64 and inverts it (FP64), keeping
 //      L_jj^-T as pairs;
 //   3. L[r, panel] = R[r, panel] L_jj^-T for the rows below (same split over k).
-//   4. (c_end >= n) finally the lower triangle is converted back to FP64; with l32 given, its FP32
-//      rounding is also written there (zero above the diagonal and on the padding).
+//   4. (c_end >= n) with l32 given, the factor's FP32 rounding is written there (zero above the
+//      diagonal and on the padding); the pool keeps the pairs.
 // The diagonal blocks are O(n 32^2) of the O(n^3/6) work, so FP64 there costs little.
 constexpr int kCholWarps = 4;
 
@@ -298,31 +316,12 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
     for (int r = tid; r < ld; r += kCholWarps * 32) {
       int e = 0;
       if (r < n) {
-        const double d = reinterpret_cast<const double*>(A)[(int64_t)r * ld + r];
-        frexp(sqrt(fmax(d, 1e-300)), &e);
+        const float2 d = A[(int64_t)r * ld + r];
+        frexp(sqrt(fmax((double)d.x + (double)d.y, 1e-300)), &e);
       }
       scale_exp[bd.row_off + r] = e;
     }
-    __syncthreads();   // the diagonal is read as FP64 before the conversion below rewrites it
   }
-  // in-place conversions of the lower triangle, four independent loads in flight per thread
-  for (int r = warp; r < n && c_beg == 0; r += kCholWarps)
-    for (int c0 = 0; c0 <= r; c0 += 128) {
-      float2 v[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int c = c0 + 32 * u + lane;
-        if (c <= r) v[u] = A[(int64_t)r * ld + c];
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int c = c0 + 32 * u + lane;
-        if (c <= r) {
-          const df32 d = df_from_bits(v[u]);
-          A[(int64_t)r * ld + c] = make_float2(d.h, d.l);
-        }
-      }
-    }
   __syncthreads();
   // rows [row0, row0 + 32) x columns [col0, col0 + 32) of the pair matrix into a 32x32 chunk
   auto load_chunk = [&](auto dst, int row0, int col0) {
@@ -464,23 +463,9 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
     if (threadIdx.x == 0 && s_bad) set_error(flags, NOLSM_ENOTPD);
     return;
   }
-  // 4. back to FP64 (lower triangle) and the FP32 copy of the factor (zero above the diagonal and on
-  //    the padding); the conversion issues four independent loads at a time
+  // 4. the FP32 copy of the factor: fl(h + l) is the pair's value rounded to nearest (zero above
+  //    the diagonal and on the padding); four independent loads at a time
   __syncthreads();
-  for (int r = warp; r < n; r += kCholWarps)
-    for (int c0 = 0; c0 <= r; c0 += 128) {
-      float2 v[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int c = c0 + 32 * u + lane;
-        if (c <= r) v[u] = A[(int64_t)r * ld + c];
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int c = c0 + 32 * u + lane;
-        if (c <= r) A[(int64_t)r * ld + c] = df_to_bits({v[u].x, v[u].y});
-      }
-    }
   if (l32) {
     float* Lf = l32 + bd.off_mat;
     for (int r = warp; r < ld; r += kCholWarps)
@@ -492,8 +477,7 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
           v[u] = (r < n && c <= r) ? A[(int64_t)r * ld + c] : make_float2(0.f, 0.f);
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          Lf[(int64_t)r * ld + c0 + 32 * u + lane] = (float)__hiloint2double(__float_as_int(v[u].y), __float_as_int(v[u].x));
+        for (int u = 0; u < 4; ++u) Lf[(int64_t)r * ld + c0 + 32 * u + lane] = v[u].x + v[u].y;
       }
   }
   if (tid == 0 && s_bad) set_error(flags, NOLSM_ENOTPD);
@@ -823,8 +807,9 @@ cudaError_t launch_gather(nolsm_ctx* ctx, float* hb, double* sb) {
     cudaError_t e = cudaFuncSetAttribute(gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
+  const int pairs = ctx->opt.chol_precision == NOLSM_CHOL_DF64 || ctx->opt.chol_precision == NOLSM_CHOL_DF64_SIMT;
   gather_kernel<<<ctx->n_blocks, 256, smem, ctx->stream>>>(ctx->d_blocks, ctx->d_idx, ctx->d_row_ptr, ctx->d_col,
-                                                           ctx->d_hval, ctx->d_sval, hb, sb, ctx->d_flags);
+                                                           ctx->d_hval, ctx->d_sval, hb, sb, ctx->d_flags, pairs);
   return cudaGetLastError();
 }
 
