@@ -355,7 +355,45 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
     const int jb = min(32, n - j0);
     // 1. panel update over the columns [c_beg, j0) (nothing to subtract for the first panel)
     const int nch = (j0 - c_beg) / 32;
-    if (nch > 0) {
+    if (nch == 1) {
+      // one 32-wide chunk (the second half of a 64-column panel): whole tiles per warp, no split
+      // over k.  B = L[panel rows, c_beg..] is shared (Bs[0], lane = row); each warp stages its A
+      // rows in its own quarter of `red`.
+      for (int e = tid; e < 1024; e += kCholWarps * 32) {
+        const int r = e >> 5, c = e & 31;
+        const float2 v = (j0 + r < n) ? A[(int64_t)(j0 + r) * ld + c_beg + c] : make_float2(0.f, 0.f);
+        Bs[0][r][c] = {v.x, v.y};
+      }
+      __syncthreads();
+      df32(*Aw)[32] = red[warp];
+      for (int r0 = j0 + 32 * warp; r0 < n; r0 += 32 * kCholWarps) {
+        df32 acc[32];
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+          const bool in = r0 + r < n;
+          const float2 a = in ? A[(int64_t)(r0 + r) * ld + c_beg + lane] : make_float2(0.f, 0.f);
+          const float2 s0 = (in && lane < jb && j0 + lane <= r0 + r) ? A[(int64_t)(r0 + r) * ld + j0 + lane]
+                                                                     : make_float2(0.f, 0.f);
+          Aw[r][lane] = {a.x, a.y};
+          acc[r] = {s0.x, s0.y};
+        }
+        __syncwarp();
+#pragma unroll 2
+        for (int k = 0; k < 32; ++k) {
+          const df32 bv = Bs[0][lane][k];
+#pragma unroll
+          for (int r = 0; r < 32; ++r) df_fms(acc[r], Aw[r][k], bv);
+        }
+#pragma unroll
+        for (int r = 0; r < 32; ++r)
+          if (r0 + r < n && lane < jb && j0 + lane <= r0 + r) {
+            const df32 v = df_norm(acc[r]);
+            A[(int64_t)(r0 + r) * ld + j0 + lane] = make_float2(v.h, v.l);
+          }
+        __syncwarp();
+      }
+      __syncthreads();
+    } else if (nch > 1) {
       for (int r0 = j0; r0 < n; r0 += 32) {
         // warp 0 starts from S itself (its loads overlap the first chunk's copies), the others from 0
         df32 acc[32];
@@ -438,25 +476,35 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
       for (int k = 0; k < 32; ++k) binv[k][lane] = df_from_double(dinv[lane][k]);
     }
     __syncthreads();
-    // 3. rows below the diagonal block: L[r, panel] = R[r, panel] L_jj^-T
-    for (int r0 = j0 + jb; r0 < n; r0 += 32) {
-      df32 acc[32];
+    // 3. rows below the diagonal block: L[r, panel] = R[r, panel] L_jj^-T, whole 32-row tiles per
+    //    warp (A rows staged in the warp's quarter of `red`; binv shared)
+    {
+      df32(*Aw)[32] = red[warp];
+      for (int r0 = j0 + jb + 32 * warp; r0 < n; r0 += 32 * kCholWarps) {
+        df32 acc[32];
 #pragma unroll
-      for (int r = 0; r < 32; ++r) acc[r] = {0.f, 0.f};
-      load_chunk(As[0], r0, j0);   // columns j0 + jb.. of these rows lie past the panel: zero weights below
-      cp_async_commit();
-      cp_async_wait_group<0>();
-      __syncthreads();
+        for (int r = 0; r < 32; ++r) {
+          // columns j0 + jb.. of these rows lie past the panel: zero weights below
+          const float2 a = (r0 + r < n) ? A[(int64_t)(r0 + r) * ld + j0 + lane] : make_float2(0.f, 0.f);
+          Aw[r][lane] = {a.x, a.y};
+          acc[r] = {0.f, 0.f};
+        }
+        __syncwarp();
 #pragma unroll 2
-      for (int kk = 0; kk < 32 / kCholWarps; ++kk) {
-        const df32 bv = binv[kw + kk][lane];
+        for (int k = 0; k < 32; ++k) {
+          const df32 bv = binv[k][lane];
 #pragma unroll
-        for (int r = 0; r < 32; ++r) df_fma(acc[r], As[0][r][kw + kk], bv);
+          for (int r = 0; r < 32; ++r) df_fma(acc[r], Aw[r][k], bv);
+        }
+#pragma unroll
+        for (int r = 0; r < 32; ++r)
+          if (r0 + r < n && lane < jb) {
+            const df32 v = df_norm(acc[r]);
+            A[(int64_t)(r0 + r) * ld + j0 + lane] = make_float2(v.h, v.l);
+          }
+        __syncwarp();
       }
       __syncthreads();
-#pragma unroll
-      for (int r = 0; r < 32; ++r) red[warp][r][lane] = acc[r];
-      reduce_store(r0, j0, jb);
     }
   }
   if (c_end < n) {
