@@ -136,6 +136,7 @@ void release_pools(nolsm_ctx* ctx) {
   dfree(ctx->d_oz_planes); ctx->d_oz_planes = nullptr;
   dfree(ctx->d_oz_items); ctx->d_oz_items = nullptr;
   dfree(ctx->d_oz_tmaps); ctx->d_oz_tmaps = nullptr;
+  dfree(ctx->d_oz_w); ctx->d_oz_w = nullptr;
   dfree(ctx->d_resacc); ctx->d_resacc = nullptr;
   dfree(ctx->d_tol); ctx->d_tol = nullptr;
   dfree(ctx->d_state); ctx->d_state = nullptr;
@@ -504,6 +505,7 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
     CK(dalloc(ctx, &ctx->d_oz_planes, (size_t)(7 * kOzPanel) * (size_t)ctx->sum_pad));
     CK(dalloc(ctx, &ctx->d_oz_items, (size_t)(2 * items)));
     CK(dalloc(ctx, &ctx->d_oz_tmaps, (size_t)256));
+    CK(dalloc(ctx, &ctx->d_oz_w, (size_t)4096 * (size_t)n_blocks));
     CK(oz_prepare(ctx));
   }
   CK(phase_mark(ctx, NOLSM_PHASE_FACTOR));

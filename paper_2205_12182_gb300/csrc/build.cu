@@ -262,6 +262,27 @@ __device__ __forceinline__ void df_fms(df32& acc, df32 a, df32 b) {
   acc.l += err - e;
 }
 
+// a * b, renormalised (the low-by-low product is below the pair's precision)
+__device__ __forceinline__ df32 df_mul(df32 a, df32 b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return df_norm({p, e});
+}
+// sqrt(a) for a > 0: the FP32 root s plus one Newton correction (a - s^2) / (2 s), s^2 exact by FMA
+__device__ __forceinline__ df32 df_sqrt(df32 a) {
+  const float s = sqrtf(a.h);
+  const float r = fmaf(-s, s, a.h) + a.l;
+  return df_norm({s, r / (2.f * s)});
+}
+// 1 / a: the FP32 reciprocal r plus one Newton correction r (1 - a r), the residual in pairs
+__device__ __forceinline__ df32 df_recip(df32 a) {
+  const float r = 1.f / a.h;
+  const float e = fmaf(-a.h, r, 1.f) - a.l * r;
+  return df_norm({r, r * e});
+}
+
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gsrc) : "memory");
@@ -295,21 +316,23 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
                                                                          double* __restrict__ pool,
                                                                          float* __restrict__ l32, DevFlags* flags,
                                                                          int c_beg, int c_end,
-                                                                         int32_t* __restrict__ scale_exp) {
+                                                                         int32_t* __restrict__ scale_exp, int r_end,
+                                                                         float2* __restrict__ wout) {
   __shared__ df32 As[2][32][32];          // read as broadcasts: no padding
   __shared__ df32 Bs[2][32][33];          // read by rows (lane = row): padded
   __shared__ df32 red[kCholWarps][32][32];
   __shared__ df32 binv[32][32];
-  __shared__ double rdiag[32];
+  __shared__ df32 rd[32];
   __shared__ int s_bad;
   const BlockDesc bd = blocks[blockIdx.x];
   const int n = bd.n, ld = bd.n_pad;
   if (c_beg >= n) return;
+  const int rmax = min(n, r_end);   // rows this launch factors (the panel's diagonal block in the blocked mode)
   float2* A = reinterpret_cast<float2*>(pool + bd.off_mat);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // phase-2 scratch over the reduction buffers (idle then)
-  double(*diag)[33] = reinterpret_cast<double(*)[33]>(&red[0][0][0]);
-  double(*dinv)[33] = reinterpret_cast<double(*)[33]>(&red[0][0][0] + 32 * 33);
+  df32(*dg)[33] = reinterpret_cast<df32(*)[33]>(&red[0][0][0]);
+  df32(*dinv)[33] = reinterpret_cast<df32(*)[33]>(&red[0][0][0] + 32 * 33);
   if (tid == 0) s_bad = 0;
   if (c_beg == 0 && scale_exp) {
     // 2^e_r >= sqrt(S_rr), which bounds every |L_rk| (sum_k L_rk^2 = S_rr); padding rows get 0
@@ -366,7 +389,7 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
       }
       __syncthreads();
       df32(*Aw)[32] = red[warp];
-      for (int r0 = j0 + 32 * warp; r0 < n; r0 += 32 * kCholWarps) {
+      for (int r0 = j0 + 32 * warp; r0 < rmax; r0 += 32 * kCholWarps) {
         df32 acc[32];
 #pragma unroll
         for (int r = 0; r < 32; ++r) {
@@ -394,7 +417,7 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
       }
       __syncthreads();
     } else if (nch > 1) {
-      for (int r0 = j0; r0 < n; r0 += 32) {
+      for (int r0 = j0; r0 < rmax; r0 += 32) {
         // warp 0 starts from S itself (its loads overlap the first chunk's copies), the others from 0
         df32 acc[32];
 #pragma unroll
@@ -432,55 +455,67 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
         reduce_store(r0, j0, jb);
       }
     }
-    // 2. diagonal block in FP64 (warp 0, lane = row), then its inverse (lane = column)
+    // 2. diagonal block (warp 0, lane = row) in pairs, then its inverse (lane = column): the FP64 pipe
+    //    of this GPU issues at 1/64 of the FP32 rate, so the pivots run in double-float too
     if (warp == 0) {
       for (int r = 0; r < 32; ++r) {
-        double v = (r == lane) ? 1.0 : 0.0;
+        df32 v = {(r == lane) ? 1.f : 0.f, 0.f};
         if (r < jb && lane < jb && lane <= r) {
           const float2 s = A[(int64_t)(j0 + r) * ld + j0 + lane];
-          v = df_to_double({s.x, s.y});
+          v = {s.x, s.y};
         }
-        diag[r][lane] = v;
+        dg[r][lane] = v;
       }
       __syncwarp();
       for (int k = 0; k < 32; ++k) {
         if (lane == k) {
-          double d = diag[k][k];
-          if (!(d > 0.0)) { s_bad = 1; d = 1.0; }
-          const double s = sqrt(d);
-          diag[k][k] = s;
-          rdiag[k] = 1.0 / s;
+          df32 d = dg[k][k];
+          if (!(d.h > 0.f)) { s_bad = 1; d = {1.f, 0.f}; }
+          const df32 s = df_sqrt(d);
+          dg[k][k] = s;
+          rd[k] = df_recip(s);
         }
         __syncwarp();
-        if (lane > k) diag[lane][k] *= rdiag[k];
+        if (lane > k) dg[lane][k] = df_mul(dg[lane][k], rd[k]);
         __syncwarp();
         if (lane > k) {
-          const double lk = diag[lane][k];
-          for (int j = k + 1; j <= lane; ++j) diag[lane][j] -= lk * diag[j][k];
+          const df32 lk = dg[lane][k];
+          for (int j = k + 1; j <= lane; ++j) df_fms(dg[lane][j], lk, dg[j][k]);
         }
         __syncwarp();
       }
-      // column `lane` of L_jj^-1 by forward substitution (zero above the diagonal)
+      // column `lane` of L_jj^-1 by forward substitution (zero above the diagonal); the sum over q
+      // runs as four independent chains
       for (int r = 0; r < 32; ++r) {
-        double v = (r == lane) ? 1.0 : 0.0;
-        if (r > lane)
-          for (int q = lane; q < r; ++q) v = fma(-diag[r][q], dinv[q][lane], v);
-        dinv[r][lane] = (r >= lane) ? v * rdiag[r] : 0.0;
+        df32 v = {(r == lane) ? 1.f : 0.f, 0.f};
+        if (r > lane) {
+          df32 part[4] = {v, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+          int q = lane;
+          for (; q + 3 < r; q += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) df_fms(part[u], dg[r][q + u], dinv[q + u][lane]);
+          }
+          for (; q < r; ++q) df_fms(part[0], dg[r][q], dinv[q][lane]);
+          v = df_add(df_add(part[0], part[1]), df_add(part[2], part[3]));
+        }
+        dinv[r][lane] = (r >= lane) ? df_mul(v, rd[r]) : df32{0.f, 0.f};
       }
       for (int r = 0; r < jb; ++r)
         if (lane <= r) {
-          const df32 v = df_from_double(diag[r][lane]);
+          const df32 v = df_norm(dg[r][lane]);
           A[(int64_t)(j0 + r) * ld + j0 + lane] = make_float2(v.h, v.l);
         }
       __syncwarp();
-      for (int k = 0; k < 32; ++k) binv[k][lane] = df_from_double(dinv[lane][k]);
+      for (int k = 0; k < 32; ++k) binv[k][lane] = dinv[lane][k];
+      if (wout && j0 == c_beg)   // L_aa^-T of the panel's first half, kept for W
+        for (int k = 0; k < 32; ++k) As[0][k][lane] = binv[k][lane];
     }
     __syncthreads();
     // 3. rows below the diagonal block: L[r, panel] = R[r, panel] L_jj^-T, whole 32-row tiles per
     //    warp (A rows staged in the warp's quarter of `red`; binv shared)
     {
       df32(*Aw)[32] = red[warp];
-      for (int r0 = j0 + jb + 32 * warp; r0 < n; r0 += 32 * kCholWarps) {
+      for (int r0 = j0 + jb + 32 * warp; r0 < rmax; r0 += 32 * kCholWarps) {
         df32 acc[32];
 #pragma unroll
         for (int r = 0; r < 32; ++r) {
@@ -507,6 +542,41 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
       __syncthreads();
     }
   }
+  if (wout && c_end - c_beg == 64 && n > c_beg + 64) {
+    // W = L11^-T of the 64 x 64 diagonal block [[L_aa, 0], [L_ba, L_cc]] for the rows below:
+    // L11^-1 = [[L_aa^-1, 0], [X, L_cc^-1]] with X = -L_cc^-1 L_ba L_aa^-1.  As[0] holds L_aa^-T,
+    // binv L_cc^-T (both as pairs); T = L_ba L_aa^-1 goes to red[1], X to red[2].
+    df32(*Lba)[32] = red[0];
+    df32(*T)[32] = red[1];
+    df32(*X)[32] = red[2];
+    for (int e = tid; e < 1024; e += kCholWarps * 32) {
+      const int r = e >> 5, c = e & 31;
+      const float2 v = A[(int64_t)(c_beg + 32 + r) * ld + c_beg + c];
+      Lba[r][c] = {v.x, v.y};
+    }
+    __syncthreads();
+    for (int i = warp * 8; i < warp * 8 + 8; ++i) {     // T[i][lane] = sum_k L_ba[i][k] (L_aa^-1)[k][lane]
+      df32 acc = {0.f, 0.f};
+      for (int k = 0; k < 32; ++k) df_fma(acc, Lba[i][k], As[0][lane][k]);
+      T[i][lane] = df_norm(acc);
+    }
+    __syncthreads();
+    for (int i = warp * 8; i < warp * 8 + 8; ++i) {     // X[i][lane] = -sum_k (L_cc^-1)[i][k] T[k][lane]
+      df32 acc = {0.f, 0.f};
+      for (int k = 0; k < 32; ++k) df_fms(acc, binv[k][i], T[k][lane]);
+      X[i][lane] = df_norm(acc);
+    }
+    __syncthreads();
+    float2* W = wout + (int64_t)blockIdx.x * 4096;      // W[k][c], k, c < 64
+    for (int e = tid; e < 4096; e += kCholWarps * 32) {
+      const int k = e >> 6, c = e & 63;
+      df32 v = {0.f, 0.f};
+      if (k < 32 && c < 32) v = As[0][k][c];
+      else if (k >= 32 && c >= 32) v = binv[k - 32][c - 32];
+      else if (k < 32) v = X[c - 32][k];
+      W[e] = make_float2(v.h, v.l);
+    }
+  }
   if (c_end < n) {
     if (threadIdx.x == 0 && s_bad) set_error(flags, NOLSM_ENOTPD);
     return;
@@ -531,42 +601,71 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
   if (tid == 0 && s_bad) set_error(flags, NOLSM_ENOTPD);
 }
 
-// Slices of a finished 64-column panel for the tensor-core trailing update (Ozaki, Ogita, Oishi &
-// Rump 2012: error-free splitting into short pieces whose products and sums are exact).  Row r's
-// entries x = L[r, c0 + j] (a pair with |x| <= 2^e_r) are written as seven integers q_0..q_6 with
-// x = 2^(e_r - 7) sum_s q_s 2^(-7 s) + (|rest| <= 2^(e_r - 50)): |q_0| <= 128, |q_s| <= 64 after,
-// each exact in BF16.  Plane s of the block is an n_pad x 64 BF16 matrix at row 7 row_off + s n_pad
-// of the slice pool.  Only the trailing rows r >= c0 + 64 are written (rows >= n as zeros).
-__global__ void __launch_bounds__(256) chol_slice_kernel(const BlockDesc* __restrict__ blocks,
-                                                         const double* __restrict__ pool,
-                                                         const int32_t* __restrict__ scale_exp,
-                                                         __nv_bfloat16* __restrict__ planes, int c0) {
-  const BlockDesc bd = blocks[blockIdx.x];
+// Rows below a 64-column panel's diagonal block, L21 = A21 W with W = L11^-T from the diagonal
+// launch, in double-float; the result replaces A21 in place, and its slices go to the planes of the
+// trailing update (Ozaki, Ogita, Oishi & Rump 2012: error-free splitting into short pieces whose
+// products and sums are exact).  Row r's entries x (a pair with |x| <= 2^e_r, e_r from the diagonal
+// launch) are written as seven integers q_0..q_6 with x = 2^(e_r - 7) sum_s q_s 2^(-7 s) + rest,
+// |rest| <= 2^(e_r - 50): |q_0| <= 128 and |q_s| <= 64 after, each exact in BF16.  Plane s of the
+// block is an n_pad x 64 BF16 matrix at row 7 row_off + s n_pad of the slice pool; rows below n are
+// never read.  Grid: (64-row chunk, block); four
+// warps per CTA = two 32-row tiles x two column halves (lane = column; W is upper triangular, so
+// the first half sums over k < 32 only).  Dynamic shared memory: W (32 KB) and the A rows (32 KB).
+constexpr int kTrsmSmem = 2 * 64 * 64 * (int)sizeof(df32);
+__global__ void __launch_bounds__(128) chol_trsm_kernel(const BlockDesc* __restrict__ blocks, double* __restrict__ pool,
+                                                        const float2* __restrict__ wmat,
+                                                        const int32_t* __restrict__ scale_exp,
+                                                        __nv_bfloat16* __restrict__ planes, int c0) {
+  extern __shared__ df32 trsm_smem[];
+  df32(*Ws)[64] = reinterpret_cast<df32(*)[64]>(trsm_smem);
+  df32(*As)[64] = reinterpret_cast<df32(*)[64]>(trsm_smem + 64 * 64);   // 64 rows
+  const int b = blockIdx.y;
+  const BlockDesc bd = blocks[b];
   const int n = bd.n, ld = bd.n_pad, t0 = c0 + 64;
-  if (t0 >= n) return;
-  const float2* A = reinterpret_cast<const float2*>(pool + bd.off_mat);
+  const int rbase = t0 + blockIdx.x * 64;
+  if (rbase >= n) return;
+  float2* A = reinterpret_cast<float2*>(pool + bd.off_mat);
+  const float2* W = wmat + (int64_t)b * 4096;
+  for (int e = threadIdx.x; e < 4096; e += 128) {
+    const float2 w = W[e];
+    Ws[e >> 6][e & 63] = {w.x, w.y};
+    const int r = rbase + (e >> 6);
+    const float2 a = r < n ? A[(int64_t)r * ld + c0 + (e & 63)] : make_float2(0.f, 0.f);
+    As[e >> 6][e & 63] = {a.x, a.y};
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tile = warp >> 1, h = warp & 1, c = 32 * h + lane;
+  df32 acc[32];
+#pragma unroll
+  for (int r = 0; r < 32; ++r) acc[r] = {0.f, 0.f};
+  const int kmax = 32 * (h + 1);
+#pragma unroll 2
+  for (int k = 0; k < kmax; ++k) {
+    const df32 wv = Ws[k][c];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) df_fma(acc[r], As[32 * tile + r][k], wv);
+  }
   __nv_bfloat16* P = planes + (int64_t)7 * bd.row_off * 64;
-  const int total = (ld - t0) * 64;
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    const int r = t0 + (e >> 6), j = e & 63;
-    float q[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (r < n) {
-      const float2 x = A[(int64_t)r * ld + c0 + j];
-      const float sc = ldexpf(1.f, 7 - scale_exp[bd.row_off + r]);
-      float h = x.x * sc, l = x.y * sc;           // |h + l| <= 128, exact scaling
+#pragma unroll 4
+  for (int r = 0; r < 32; ++r) {
+    const int row = rbase + 32 * tile + r;
+    if (row >= n) break;
+    const df32 v = df_norm(acc[r]);
+    A[(int64_t)row * ld + c0 + c] = make_float2(v.h, v.l);
+    const float sc = ldexpf(1.f, 7 - scale_exp[bd.row_off + row]);
+    float hh = v.h * sc, ll = v.l * sc;
 #pragma unroll
-      for (int s = 0; s < 7; ++s) {
-        q[s] = rintf(h);
-        const float d = h - q[s];                   // exact: the fraction of h
-        const float sum = d + l;                    // TwoSum(d, l), exact renormalisation
-        const float bb = sum - d;
-        const float err = (d - (sum - bb)) + (l - bb);
-        h = sum * 128.f;
-        l = err * 128.f;
-      }
+    for (int s = 0; s < 7; ++s) {
+      const float q = rintf(hh);
+      P[((int64_t)s * ld + row) * 64 + c] = __float2bfloat16_rn(q);
+      const float d = hh - q;
+      const float sum = d + ll;
+      const float bb = sum - d;
+      const float err = (d - (sum - bb)) + (ll - bb);
+      hh = sum * 128.f;
+      ll = err * 128.f;
     }
-#pragma unroll
-    for (int s = 0; s < 7; ++s) P[((int64_t)s * ld + r) * 64 + j] = __float2bfloat16_rn(q[s]);
   }
 }
 
@@ -866,17 +965,26 @@ cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode) {
   float* s32 = reinterpret_cast<float*>(sb + ctx->sum_sq);   // FP32 factor lives in the scratch half
   cudaError_t e = cudaSuccess;
   if (mode == NOLSM_CHOL_DF64) {
-    // blocked by 64-column panels: panel on the FP32 pipe, slices, trailing update on the tensor cores
+    // blocked by 64-column panels: the 64 x 64 diagonal block and W = L11^-T (FP32 pipe, FP64
+    // 32 x 32 pivots), the rows below L21 = A21 W with their slices (FP32 pipe), and the trailing
+    // update from the slices on the tensor cores
+    static bool trsm_attr = false;
+    if (!trsm_attr) {
+      e = cudaFuncSetAttribute(chol_trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmSmem);
+      if (e != cudaSuccess) return e;
+      trsm_attr = true;
+    }
     int max_n = 0;
     for (const auto& bd : ctx->h_blocks) max_n = std::max(max_n, bd.n);
     for (int pnl = 0; pnl * kOzPanel < max_n; ++pnl) {
       const int c0 = pnl * kOzPanel;
-      cholesky_df_kernel<<<ctx->n_blocks, kCholWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, ctx->d_flags, c0,
-                                                                            c0 + kOzPanel, ctx->d_oz_exp);
+      cholesky_df_kernel<<<ctx->n_blocks, kCholWarps * 32, 0, ctx->stream>>>(
+          ctx->d_blocks, sb, s32, ctx->d_flags, c0, c0 + kOzPanel, ctx->d_oz_exp, c0 + kOzPanel, ctx->d_oz_w);
       ctx->n_launches += 1;
       if (c0 + kOzPanel >= max_n) break;
-      chol_slice_kernel<<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, sb, ctx->d_oz_exp,
-                                                                reinterpret_cast<__nv_bfloat16*>(ctx->d_oz_planes), c0);
+      const dim3 tg((max_n - c0 - kOzPanel + 63) / 64, ctx->n_blocks);
+      chol_trsm_kernel<<<tg, 128, kTrsmSmem, ctx->stream>>>(ctx->d_blocks, sb, ctx->d_oz_w, ctx->d_oz_exp,
+                                                            reinterpret_cast<__nv_bfloat16*>(ctx->d_oz_planes), c0);
       ctx->n_launches += 1;
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       if ((e = launch_chol_update_tc(ctx, pnl, sb)) != cudaSuccess) return e;
@@ -885,7 +993,7 @@ cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode) {
     trinv_tile_kernel<<<ctx->n_blocks, kInvWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
   } else if (mode == NOLSM_CHOL_DF64_SIMT) {
     cholesky_df_kernel<<<ctx->n_blocks, kCholWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, ctx->d_flags, 0,
-                                                                          1 << 30, nullptr);
+                                                                          1 << 30, nullptr, 1 << 30, nullptr);
     if ((e = phase_mark(ctx, NOLSM_PHASE_INVERSE)) != cudaSuccess) return e;
     trinv_tile_kernel<<<ctx->n_blocks, kInvWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
   } else if (mode == NOLSM_CHOL_FP64_INV64) {

@@ -138,6 +138,7 @@ struct nolsm_ctx {
   uint16_t* d_oz_planes = nullptr;
   int32_t* d_oz_items = nullptr;
   uint8_t* d_oz_tmaps = nullptr;
+  float2* d_oz_w = nullptr;          // W = L11^-T of the current panel, 64 x 64 pairs per block
   std::vector<int32_t> h_oz_items;
   std::vector<int64_t> h_oz_panel;   // item offset of panel p (size panels + 1)
   int64_t sum_pad = 0;

@@ -1182,7 +1182,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) slab_tc_kernel(const __grid_co
 // Trailing update of the blocked double-float Cholesky on the tensor cores.  After panel p (columns
 // [c0, c0 + 64)) is factored, every trailing entry C[r, c] (c0 + 64 <= c <= r) loses
 // sum_{k in panel} L[r, k] L[c, k].  Each L entry is split into seven 7-bit integers on its row's
-// scale (chol_slice_kernel; Ozaki, Ogita, Oishi & Rump 2012), so
+// scale (chol_trsm_kernel; Ozaki, Ogita, Oishi & Rump 2012), so
 //   L[r, k] L[c, k] = 2^(e_r + e_c - 14) sum_{s, t} q_s(r, k) q_t(c, k) 2^(-7 (s + t))
 // and the pairs with s + t = l <= 6 are summed over k by BF16 MMAs into the FP32 tensor-memory
 // accumulator of level l: every product is an integer of at most 2^14 and a level sums at most
