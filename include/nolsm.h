@@ -191,8 +191,11 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
 nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out);
 
 /* Chemical potential by bisection (Section V-A: the mu that makes the system
- * charge neutral).  Each step evaluates nolsm_sign_batch at the bracket midpoint;
- * it stops when |N(mu) - n_electrons| <= tol_n * n_electrons, when the bracket is
+ * charge neutral).  The first point is an Aufbau estimate when it lies inside the
+ * bracket: with k = floor(n_electrons / spin_factor) occupied orbitals, the midpoint
+ * of the k-th and (k+1)-th smallest diagonal entries of A0 over the blocks' own
+ * columns; every later step evaluates nolsm_sign_batch at the bracket midpoint.
+ * It stops when |N(mu) - n_electrons| <= tol_n * n_electrons, when the bracket is
  * below 1e-10 Ha, or after max_steps.  mu_lo >= mu_hi selects the bracket
  * [min lower bound, max upper bound] over the blocks.  Outputs may be NULL.
  * Errors: EBRACKET (the bracket does not contain the count), plus those of

@@ -137,6 +137,7 @@ void release_pools(nolsm_ctx* ctx) {
   dfree(ctx->d_oz_items); ctx->d_oz_items = nullptr;
   dfree(ctx->d_oz_tmaps); ctx->d_oz_tmaps = nullptr;
   dfree(ctx->d_oz_w); ctx->d_oz_w = nullptr;
+  dfree(ctx->d_own_diag); ctx->d_own_diag = nullptr;
   dfree(ctx->d_resacc); ctx->d_resacc = nullptr;
   dfree(ctx->d_tol); ctx->d_tol = nullptr;
   dfree(ctx->d_state); ctx->d_state = nullptr;
@@ -520,6 +521,9 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   CK(dalloc(ctx, &ctx->d_rowd, (size_t)ctx->n_blocks * kMaxDim));
   CK(dalloc(ctx, &ctx->d_rowr, (size_t)ctx->n_blocks * kMaxDim));
   CK(launch_bounds(ctx));
+  CK(dalloc(ctx, &ctx->d_own_diag, (size_t)std::max<int64_t>(ctx->sum_own, 1)));
+  CK(launch_own_diag(ctx));
+  ctx->n_launches += 1;
   // mu-independent features once per build (the mu-dependent ones are refreshed in O(n))
   CK(dalloc(ctx, &ctx->d_feat_static, (size_t)32 * ctx->n_blocks));
   CK(launch_features(ctx, 0.0, ctx->d_feat_static));
@@ -536,6 +540,8 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   ctx->h_hi.resize((size_t)n_blocks);
   CK(cudaMemcpy(ctx->h_lo.data(), ctx->d_lo, sizeof(double) * n_blocks, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(ctx->h_hi.data(), ctx->d_hi, sizeof(double) * n_blocks, cudaMemcpyDeviceToHost));
+  ctx->h_own_diag.resize((size_t)ctx->sum_own);
+  CK(cudaMemcpy(ctx->h_own_diag.data(), ctx->d_own_diag, sizeof(float) * ctx->sum_own, cudaMemcpyDeviceToHost));
   if (mixed) CK(tc_prepare(ctx));
   ctx->built = true;
   return NOLSM_OK;
@@ -704,6 +710,18 @@ nolsm_status nolsm_set_mu(nolsm_ctx* ctx, double n_electrons, double mu_lo, doub
   }
   const double lo0 = lo, hi0 = hi;
   double mu = 0.5 * (lo + hi), n_mu = 0.0;
+  {
+    // Aufbau first point: between the k-th and (k+1)-th smallest own-column diagonal entries of A0
+    const int64_t k = (int64_t)std::floor(n_electrons / ctx->opt.spin_factor);
+    std::vector<float> d = ctx->h_own_diag;
+    if (k >= 1 && k < (int64_t)d.size()) {
+      std::nth_element(d.begin(), d.begin() + k, d.end());
+      const float above = d[(size_t)k];
+      const float below = *std::max_element(d.begin(), d.begin() + k);
+      const double guess = 0.5 * ((double)below + (double)above);
+      if (guess > lo && guess < hi) mu = guess;
+    }
+  }
   int steps = 0;
   nolsm_sign_stats s;
   while (true) {

@@ -901,6 +901,14 @@ __global__ void slabs_kernel(const BlockDesc* __restrict__ blocks, const int32_t
   }
 }
 
+// Diagonal of A0 at each own column, in blk_cols order (the Aufbau first point of the mu search).
+__global__ void own_diag_kernel(const BlockDesc* __restrict__ blocks, const int32_t* __restrict__ own_pool,
+                                const float* __restrict__ row_diag, float* __restrict__ out) {
+  const BlockDesc bd = blocks[blockIdx.x];
+  for (int j = threadIdx.x; j < bd.c; j += blockDim.x)
+    out[bd.off_own + j] = row_diag[bd.off_idx + own_pool[bd.off_own + j]];
+}
+
 // Gershgorin bounds of A0 (real n x n part): [min_i a_ii - R_i, max_i a_ii + R_i].
 __global__ void gershgorin_kernel(const BlockDesc* __restrict__ blocks, const float* __restrict__ a0,
                                   double* __restrict__ lo, double* __restrict__ hi, float* __restrict__ row_diag,
@@ -1031,6 +1039,11 @@ cudaError_t launch_slabs_impl(nolsm_ctx* ctx, const void* lfac, int fp32, const 
   else
     slabs_kernel<float><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_own, (const float*)lfac,
                                                                ctx->d_linv, t1, ctx->d_w, ctx->d_z, ctx->d_lc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_own_diag(nolsm_ctx* ctx) {
+  own_diag_kernel<<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_own, ctx->d_rowd, ctx->d_own_diag);
   return cudaGetLastError();
 }
 

@@ -103,6 +103,8 @@ struct nolsm_ctx {
   std::vector<nolsm::BlockDesc> h_blocks;
   std::vector<int32_t> h_blk_cols;
   std::vector<double> h_lo, h_hi;       // spectral bounds of A0 per block
+  std::vector<float> h_own_diag;        // diagonal of A0 at every own column (first point of set_mu)
+  float* d_own_diag = nullptr;
   std::vector<int32_t> h_iters;
   int64_t sum_sq = 0, sum_slab = 0, sum_idx = 0, sum_own = 0;
   double flops_paper_iter = 0.0, flops_exec_iter = 0.0;
@@ -227,6 +229,7 @@ cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode);
 cudaError_t launch_congruence(nolsm_ctx* ctx, float* t1_scratch);
 cudaError_t launch_slabs_impl(nolsm_ctx* ctx, const void* lfac, int fp32, const float* t1);
 cudaError_t launch_bounds(nolsm_ctx* ctx);
+cudaError_t launch_own_diag(nolsm_ctx* ctx);   // d_own_diag from the per-row diagonal of A0
 
 // sign.cu (SIMT path, control, slab traces)
 cudaError_t launch_ns_init(nolsm_ctx* ctx, double mu, int half, int mode, const float* lz, const float* pred,

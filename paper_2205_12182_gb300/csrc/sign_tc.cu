@@ -622,19 +622,23 @@ __device__ __forceinline__ void pair_fill(const BlockDesc& bd, const float* __re
 }
 
 // Upper-triangular 128 x (<= 256) tiles of an n_pad x n_pad product, dealt to the two CTAs so that
-// their column counts stay balanced (both CTAs compute the same assignment).
+// their column counts stay balanced (both CTAs compute the same assignment).  Each CTA runs its
+// narrow (128-column) tiles last: the epilogue of the last tile is the tail of the product.
 __device__ inline int pair_tiles(int ld, uint32_t rank, PairTile* out) {
   int load[2] = {0, 0}, k = 0;
-  for (int m0 = 0; m0 < ld; m0 += TM)
-    for (int n0 = m0; n0 < ld; n0 += TN) {
-      const int tn = min(TN, ld - n0);
-      const int owner = load[1] < load[0] ? 1 : 0;
-      load[owner] += tn;
-      if (owner == (int)rank) {
-        if (k >= PAIR_MAX_TILES) return -1;
-        out[k++] = PairTile{(int16_t)m0, (int16_t)n0, (int16_t)tn, 0};
+  for (int pass = 0; pass < 2; ++pass) {
+    load[0] = load[1] = 0;
+    for (int m0 = 0; m0 < ld; m0 += TM)
+      for (int n0 = m0; n0 < ld; n0 += TN) {
+        const int tn = min(TN, ld - n0);
+        const int owner = load[1] < load[0] ? 1 : 0;
+        load[owner] += tn;
+        if (owner == (int)rank && (tn == TN) == (pass == 0)) {
+          if (k >= PAIR_MAX_TILES) return -1;
+          out[k++] = PairTile{(int16_t)m0, (int16_t)n0, (int16_t)tn, 0};
+        }
       }
-    }
+  }
   return k;
 }
 
