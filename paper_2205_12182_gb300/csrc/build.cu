@@ -601,6 +601,180 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
   if (tid == 0 && s_bad) set_error(flags, NOLSM_ENOTPD);
 }
 
+// ---- the 64 x 64 diagonal block of the blocked double-float Cholesky ----------------------------
+__device__ __forceinline__ df32 shfl_df(df32 v, int src) {
+  return {__shfl_sync(0xffffffffu, v.h, src), __shfl_sync(0xffffffffu, v.l, src)};
+}
+
+// One warp factors a 32 x 32 SPD block P = L L^T held in registers (lane i: row i, a[j] = P[i][j]
+// for j <= i) and inverts L (lane c: x[r] = (L^-1)[r][c]).  Column values move between lanes by
+// shuffles, so the loops are straight-line code on registers.  Returns false (in every lane) when a
+// pivot is not positive (it is then taken as 1).
+__device__ __forceinline__ bool pivot32(df32 (&a)[32], df32 (&x)[32], int lane) {
+  bool ok = true;
+  df32 rk_own = {0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    df32 d = shfl_df(a[k], k);
+    if (!(d.h > 0.f)) { ok = false; d = {1.f, 0.f}; }
+    const df32 s = df_sqrt(d);
+    const df32 rk = df_recip(s);
+    if (lane == k) { a[k] = s; rk_own = rk; }
+    if (lane > k) a[k] = df_mul(a[k], rk);
+#pragma unroll
+    for (int j = k + 1; j < 32; ++j) {
+      const df32 ljk = shfl_df(a[k], j);
+      if (lane >= j) df_fms(a[j], a[k], ljk);
+    }
+  }
+  // column `lane` of L^-1 by forward substitution: x[r] = (delta_rc - sum_{q<r} L[r][q] x[q]) / L[r][r]
+#pragma unroll
+  for (int r = 0; r < 32; ++r) {
+    df32 p0 = {(r == lane) ? 1.f : 0.f, 0.f}, p1 = {0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < r; ++q) {
+      const df32 lrq = shfl_df(a[q], r);
+      if (q & 1) df_fms(p1, lrq, x[q]);
+      else df_fms(p0, lrq, x[q]);
+    }
+    x[r] = df_mul(df_add(p0, p1), shfl_df(rk_own, r));
+  }
+  return ok;
+}
+
+// The 64 x 64 diagonal block [c0, c0 + 64) of a panel, whose earlier panels' contributions are
+// already subtracted: L11 in place (pairs) and, when rows follow below, W = L11^-T (64 x 64 pairs)
+// for chol_trsm_kernel.  Warp 0 runs the two 32 x 32 pivots in registers (pivot32); the four warps
+// share the 32 x 32 x 32 products between them:
+//   L_ba = A_ba L_aa^-T,  A_cc -= L_ba L_ba^T,  T = L_ba L_aa^-1,  X = -L_cc^-1 T,
+// so that L11^-1 = [[L_aa^-1, 0], [X, L_cc^-1]].  Entries past n are taken as the identity.  In the
+// first panel each row's slicing exponent e_r (2^e_r >= sqrt(S_rr)) is written first.
+__global__ void __launch_bounds__(128, 3) chol_diag64_kernel(const BlockDesc* __restrict__ blocks,
+                                                             double* __restrict__ pool, DevFlags* flags, int c0,
+                                                             int32_t* __restrict__ scale_exp,
+                                                             float2* __restrict__ wout) {
+  __shared__ df32 M[64][65];         // the block (lower triangle used)
+  __shared__ df32 Xa[32][33], Xc[32][33], T[32][33], X[32][33];
+  __shared__ int s_bad;
+  const BlockDesc bd = blocks[blockIdx.x];
+  const int n = bd.n, ld = bd.n_pad;
+  if (c0 >= n) return;
+  float2* A = reinterpret_cast<float2*>(pool + bd.off_mat);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nb = min(64, n - c0);
+  if (tid == 0) s_bad = 0;
+  if (c0 == 0 && scale_exp)
+    for (int r = tid; r < ld; r += 128) {
+      int e = 0;
+      if (r < n) {
+        const float2 d = A[(int64_t)r * ld + r];
+        frexp(sqrt(fmax((double)d.x + (double)d.y, 1e-300)), &e);
+      }
+      scale_exp[bd.row_off + r] = e;
+    }
+  for (int e = tid; e < 64 * 64; e += 128) {
+    const int r = e >> 6, c = e & 63;
+    df32 v = {(r == c) ? 1.f : 0.f, 0.f};
+    if (r < nb && c <= r) {
+      const float2 s = A[(int64_t)(c0 + r) * ld + c0 + c];
+      v = {s.x, s.y};
+    }
+    M[r][c] = v;
+  }
+  __syncthreads();
+  df32 a[32], x[32];
+  if (warp == 0) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) a[j] = (j <= lane) ? M[lane][j] : df32{0.f, 0.f};
+    if (!pivot32(a, x, lane) && lane == 0) s_bad = 1;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (j <= lane) M[lane][j] = df_norm(a[j]);
+      Xa[j][lane] = x[j];
+    }
+  }
+  __syncthreads();
+  // L_ba[i][j] = sum_{k <= j} A_ba[i][k] (L_aa^-1)[j][k]
+  for (int i = warp * 8; i < warp * 8 + 8; ++i) {
+    df32 acc = {0.f, 0.f};
+    for (int k = 0; k <= lane; ++k) df_fma(acc, M[32 + i][k], Xa[lane][k]);
+    T[i][lane] = df_norm(acc);
+  }
+  __syncthreads();
+  for (int i = warp * 8; i < warp * 8 + 8; ++i) M[32 + i][lane] = T[i][lane];
+  __syncthreads();
+  // A_cc[i][j] -= sum_k L_ba[i][k] L_ba[j][k]   (j <= i)
+  for (int i = warp * 8; i < warp * 8 + 8; ++i) {
+    if (lane > i) continue;
+    df32 acc = M[32 + i][32 + lane];
+    for (int k = 0; k < 32; ++k) df_fms(acc, M[32 + i][k], M[32 + lane][k]);
+    M[32 + i][32 + lane] = df_norm(acc);
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) a[j] = (j <= lane) ? M[32 + lane][32 + j] : df32{0.f, 0.f};
+    if (!pivot32(a, x, lane) && lane == 0) s_bad = 1;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (j <= lane) M[32 + lane][32 + j] = df_norm(a[j]);
+      Xc[j][lane] = x[j];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < 64 * 64; e += 128) {
+    const int r = e >> 6, c = e & 63;
+    if (r < nb && c <= r) A[(int64_t)(c0 + r) * ld + c0 + c] = make_float2(M[r][c].h, M[r][c].l);
+  }
+  if (wout && n > c0 + 64) {
+    // T = L_ba L_aa^-1, X = -L_cc^-1 T
+    for (int i = warp * 8; i < warp * 8 + 8; ++i) {
+      df32 acc = {0.f, 0.f};
+      for (int k = lane; k < 32; ++k) df_fma(acc, M[32 + i][k], Xa[k][lane]);
+      T[i][lane] = df_norm(acc);
+    }
+    __syncthreads();
+    for (int i = warp * 8; i < warp * 8 + 8; ++i) {
+      df32 acc = {0.f, 0.f};
+      for (int k = 0; k <= i; ++k) df_fms(acc, Xc[i][k], T[k][lane]);
+      X[i][lane] = df_norm(acc);
+    }
+    __syncthreads();
+    float2* W = wout + (int64_t)blockIdx.x * 4096;   // W[k][c] = (L11^-1)[c][k]
+    for (int e = tid; e < 4096; e += 128) {
+      const int k = e >> 6, c = e & 63;
+      df32 v = {0.f, 0.f};
+      if (k < 32 && c < 32) v = Xa[c][k];
+      else if (k >= 32 && c >= 32) v = Xc[c - 32][k - 32];
+      else if (k < 32) v = X[c - 32][k];
+      W[e] = make_float2(v.h, v.l);
+    }
+  }
+  if (tid == 0 && s_bad) set_error(flags, NOLSM_ENOTPD);
+}
+
+// The factor's FP32 rounding fl(h + l) from the pairs (lower triangle; zero above the diagonal and
+// on the padding), every block at once.
+__global__ void factor_f32_kernel(const BlockDesc* __restrict__ blocks, int n_blocks, const double* __restrict__ pool,
+                                  float* __restrict__ l32) {
+  for (int b = blockIdx.y; b < n_blocks; b += gridDim.y) {
+    const BlockDesc bd = blocks[b];
+    const int n = bd.n, ld = bd.n_pad;
+    const float2* A = reinterpret_cast<const float2*>(pool + bd.off_mat);
+    float* L = l32 + bd.off_mat;
+    const int64_t total = (int64_t)ld * ld;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+      const int r = (int)(e / ld), c = (int)(e % ld);
+      float v = 0.f;
+      if (r < n && c <= r) {
+        const float2 p = A[e];
+        v = p.x + p.y;
+      }
+      L[e] = v;
+    }
+  }
+}
+
 // Rows below a 64-column panel's diagonal block, L21 = A21 W with W = L11^-T from the diagonal
 // launch, in double-float; the result replaces A21 in place, and its slices go to the planes of the
 // trailing update (Ozaki, Ogita, Oishi & Rump 2012: error-free splitting into short pieces whose
@@ -986,8 +1160,8 @@ cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode) {
     for (const auto& bd : ctx->h_blocks) max_n = std::max(max_n, bd.n);
     for (int pnl = 0; pnl * kOzPanel < max_n; ++pnl) {
       const int c0 = pnl * kOzPanel;
-      cholesky_df_kernel<<<ctx->n_blocks, kCholWarps * 32, 0, ctx->stream>>>(
-          ctx->d_blocks, sb, s32, ctx->d_flags, c0, c0 + kOzPanel, ctx->d_oz_exp, c0 + kOzPanel, ctx->d_oz_w);
+      chol_diag64_kernel<<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, sb, ctx->d_flags, c0, ctx->d_oz_exp,
+                                                                 ctx->d_oz_w);
       ctx->n_launches += 1;
       if (c0 + kOzPanel >= max_n) break;
       const dim3 tg((max_n - c0 - kOzPanel + 63) / 64, ctx->n_blocks);
@@ -997,6 +1171,9 @@ cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode) {
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       if ((e = launch_chol_update_tc(ctx, pnl, sb)) != cudaSuccess) return e;
     }
+    factor_f32_kernel<<<dim3(8, std::min(ctx->n_blocks, 8192)), 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->n_blocks, sb,
+                                                                                       s32);
+    ctx->n_launches += 1;
     if ((e = phase_mark(ctx, NOLSM_PHASE_INVERSE)) != cudaSuccess) return e;
     trinv_tile_kernel<<<ctx->n_blocks, kInvWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
   } else if (mode == NOLSM_CHOL_DF64_SIMT) {
