@@ -602,50 +602,50 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
 }
 
 // ---- the 64 x 64 diagonal block of the blocked double-float Cholesky ----------------------------
-__device__ __forceinline__ df32 shfl_df(df32 v, int src) {
-  return {__shfl_sync(0xffffffffu, v.h, src), __shfl_sync(0xffffffffu, v.l, src)};
-}
-
-// One warp factors a 32 x 32 SPD block P = L L^T held in registers (lane i: row i, a[j] = P[i][j]
-// for j <= i) and inverts L (lane c: x[r] = (L^-1)[r][c]).  Column values move between lanes by
-// shuffles, so the loops are straight-line code on registers.  Returns false (in every lane) when a
-// pivot is not positive (it is then taken as 1).
-__device__ __forceinline__ bool pivot32(df32 (&a)[32], df32 (&x)[32], int lane) {
-  bool ok = true;
-  df32 rk_own = {0.f, 0.f};
-#pragma unroll
+// The CTA (128 threads) factors a 32 x 32 SPD block in shared memory, P = L L^T in place (lower
+// triangle), and writes X = L^-1 (lower triangle, zero above).  Right-looking in both: per column,
+// one thread takes the pivot, the column is scaled, and the trailing update is shared by all
+// threads.  rk receives the reciprocal pivots.  Sets *bad when a pivot is not positive (it is then
+// taken as 1).
+__device__ __forceinline__ void pivot32(df32 (*P)[65], df32 (*X)[33], df32* rk, int* bad) {
+  const int tid = threadIdx.x;
   for (int k = 0; k < 32; ++k) {
-    df32 d = shfl_df(a[k], k);
-    if (!(d.h > 0.f)) { ok = false; d = {1.f, 0.f}; }
-    const df32 s = df_sqrt(d);
-    const df32 rk = df_recip(s);
-    if (lane == k) { a[k] = s; rk_own = rk; }
-    if (lane > k) a[k] = df_mul(a[k], rk);
-#pragma unroll
-    for (int j = k + 1; j < 32; ++j) {
-      const df32 ljk = shfl_df(a[k], j);
-      if (lane >= j) df_fms(a[j], a[k], ljk);
+    if (tid == 0) {
+      df32 d = P[k][k];
+      if (!(d.h > 0.f)) { *bad = 1; d = {1.f, 0.f}; }
+      const df32 s = df_sqrt(d);
+      P[k][k] = s;
+      rk[k] = df_recip(s);
     }
-  }
-  // column `lane` of L^-1 by forward substitution: x[r] = (delta_rc - sum_{q<r} L[r][q] x[q]) / L[r][r]
-#pragma unroll
-  for (int r = 0; r < 32; ++r) {
-    df32 p0 = {(r == lane) ? 1.f : 0.f, 0.f}, p1 = {0.f, 0.f};
-#pragma unroll
-    for (int q = 0; q < r; ++q) {
-      const df32 lrq = shfl_df(a[q], r);
-      if (q & 1) df_fms(p1, lrq, x[q]);
-      else df_fms(p0, lrq, x[q]);
+    __syncthreads();
+    if (tid > k && tid < 32) P[tid][k] = df_mul(P[tid][k], rk[k]);
+    __syncthreads();
+    const int m = 31 - k;                       // trailing rows / columns
+    for (int e = tid; e < m * m; e += 128) {
+      const int i = k + 1 + e / m, j = k + 1 + e % m;
+      if (j <= i) df_fms(P[i][j], P[i][k], P[j][k]);
     }
-    x[r] = df_mul(df_add(p0, p1), shfl_df(rk_own, r));
+    __syncthreads();
   }
-  return ok;
+  for (int e = tid; e < 1024; e += 128) X[e >> 5][e & 31] = {((e >> 5) == (e & 31)) ? 1.f : 0.f, 0.f};
+  __syncthreads();
+  for (int q = 0; q < 32; ++q) {
+    // row q of X is final once scaled: X[q][c] = (delta_qc - sum_{p<q} L[q][p] X[p][c]) / L[q][q]
+    if (tid <= q) X[q][tid] = df_mul(X[q][tid], rk[q]);
+    __syncthreads();
+    const int rows = 31 - q, cols = q + 1;      // X[r][c] -= L[r][q] X[q][c] for r > q, c <= q
+    for (int e = tid; e < rows * cols; e += 128) {
+      const int r = q + 1 + e / cols, c = e % cols;
+      df_fms(X[r][c], P[r][q], X[q][c]);
+    }
+    __syncthreads();
+  }
 }
 
 // The 64 x 64 diagonal block [c0, c0 + 64) of a panel, whose earlier panels' contributions are
 // already subtracted: L11 in place (pairs) and, when rows follow below, W = L11^-T (64 x 64 pairs)
-// for chol_trsm_kernel.  Warp 0 runs the two 32 x 32 pivots in registers (pivot32); the four warps
-// share the 32 x 32 x 32 products between them:
+// for chol_trsm_kernel.  The CTA runs the two 32 x 32 pivots (pivot32) and shares the
+// 32 x 32 x 32 products between its four warps:
 //   L_ba = A_ba L_aa^-T,  A_cc -= L_ba L_ba^T,  T = L_ba L_aa^-1,  X = -L_cc^-1 T,
 // so that L11^-1 = [[L_aa^-1, 0], [X, L_cc^-1]].  Entries past n are taken as the identity.  In the
 // first panel each row's slicing exponent e_r (2^e_r >= sqrt(S_rr)) is written first.
@@ -655,6 +655,7 @@ __global__ void __launch_bounds__(128, 3) chol_diag64_kernel(const BlockDesc* __
                                                              float2* __restrict__ wout) {
   __shared__ df32 M[64][65];         // the block (lower triangle used)
   __shared__ df32 Xa[32][33], Xc[32][33], T[32][33], X[32][33];
+  __shared__ df32 rk[32];
   __shared__ int s_bad;
   const BlockDesc bd = blocks[blockIdx.x];
   const int n = bd.n, ld = bd.n_pad;
@@ -682,18 +683,7 @@ __global__ void __launch_bounds__(128, 3) chol_diag64_kernel(const BlockDesc* __
     M[r][c] = v;
   }
   __syncthreads();
-  df32 a[32], x[32];
-  if (warp == 0) {
-#pragma unroll
-    for (int j = 0; j < 32; ++j) a[j] = (j <= lane) ? M[lane][j] : df32{0.f, 0.f};
-    if (!pivot32(a, x, lane) && lane == 0) s_bad = 1;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if (j <= lane) M[lane][j] = df_norm(a[j]);
-      Xa[j][lane] = x[j];
-    }
-  }
-  __syncthreads();
+  pivot32(M, Xa, rk, &s_bad);
   // L_ba[i][j] = sum_{k <= j} A_ba[i][k] (L_aa^-1)[j][k]
   for (int i = warp * 8; i < warp * 8 + 8; ++i) {
     df32 acc = {0.f, 0.f};
@@ -711,17 +701,7 @@ __global__ void __launch_bounds__(128, 3) chol_diag64_kernel(const BlockDesc* __
     M[32 + i][32 + lane] = df_norm(acc);
   }
   __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int j = 0; j < 32; ++j) a[j] = (j <= lane) ? M[32 + lane][32 + j] : df32{0.f, 0.f};
-    if (!pivot32(a, x, lane) && lane == 0) s_bad = 1;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if (j <= lane) M[32 + lane][32 + j] = df_norm(a[j]);
-      Xc[j][lane] = x[j];
-    }
-  }
-  __syncthreads();
+  pivot32(reinterpret_cast<df32(*)[65]>(&M[32][32]), Xc, rk, &s_bad);
   for (int e = tid; e < 64 * 64; e += 128) {
     const int r = e >> 6, c = e & 63;
     if (r < nb && c <= r) A[(int64_t)(c0 + r) * ld + c0 + c] = make_float2(M[r][c].h, M[r][c].l);
