@@ -209,7 +209,8 @@ def run_ours(args):
     frac = gemm_tflops / pk["bf16_tflops_sustained"] if gemm_tflops else None
     st = lib.sign_batch(mu)   # statistics of one evaluation at the converged mu (not timed)
     n_b = np.array([nolsm.nolsm_block_info(lib.ctx, b)[0] for b in range(system.n_blocks)], np.float64)
-    roofs = rooflines(stage_ms, cnt, args.steps, n_b, pk, clk_max_mhz(), torch.cuda.get_device_properties(dev))
+    roofs = rooflines(stage_ms, cnt, args.steps, n_b, pk, clk_max_mhz(), torch.cuda.get_device_properties(dev),
+                      products_per_launch=system.n_blocks * (2 * st["iters_avg"] + 1))
     dominant = max(roofs, key=lambda r: r["ms_per_step"])
     line = {
         "metric": METRIC,
@@ -365,36 +366,70 @@ def traffic_per_launch(kernel, units):
         return None
 
 
-def rooflines(stage_ms, cnt, steps, n_b, pk, sm_max_mhz, props):
-    """The two kernels that dominate a step, each against its own bound, from the stage times measured
-    in the timed region (CUDA events on the library's stream; one launch of each per stage).
-    * the double-float Cholesky (stage 'factor'): plain FP32-pipe arithmetic; algorithmic work
-      sum_b n_b^3 / 6 multiply-adds (n_b^3 / 3 flops, FP64-equivalent); peak: every SM issues 128
-      FP32 operations per clock and a double-float multiply-add costs 12 of them;
-    * the Newton-Schulz products (stage 'products'): tensor cores, executed FLOP over their time."""
+def oz_update_tiles(n_b, panel=64, tm=128, tn=32):
+    """128 x 32 tiles of the tensor-core trailing updates of the blocked double-float Cholesky (the
+    library's work items: per panel, 32-column chunks of the trailing columns, and their 128-row
+    tiles that reach the diagonal)."""
+    tiles = 0
+    for n in n_b.astype(int):
+        for t0 in range(panel, n, panel):
+            for n0 in range(t0, n, tn):
+                d = n0 - t0 - (tm - 1)
+                m_first = t0 + (max(d, 0) + tm - 1) // tm * tm
+                tiles += len(range(m_first, n, tm))
+    return tiles
+
+
+def rooflines(stage_ms, cnt, steps, n_b, pk, sm_max_mhz, props, products_per_launch):
+    """The kernels that dominate a step, each against its own bound, from the stage times measured in
+    the timed region (CUDA events on the library's stream around each stage's launches).
+    * ns_pair_kernel (stage 'products'): tensor cores, executed FP16 FLOP over its time;
+    * chol_update_kernel ('factor_update'): tensor cores, the executed BF16 FLOP of the slice-pair
+      products (28 pairs x 2 x 128 x 32 x 64 per tile);
+    * chol_trsm_kernel ('factor_trsm'): double-float multiply-adds on the FP32 pipe, 3,072 per trailing
+      row per panel (32 columns x 32 k + 32 columns x 64 k), 2 FP64-equivalent flops each; peak: every
+      SM issues 128 FP32 operations per clock and a double-float multiply-add costs 12 of them;
+    * trinv_tile_kernel ('inverse'): FP32 pipe, n_b^3 / 6 multiply-adds per block."""
     mhz = sm_max_mhz or 2070.0
+    sms = props.multi_processor_count
+    df_peak = sms * 128 * mhz * 1e6 / 12.0 * 2.0 / 1e12
+    f32_peak = sms * 128 * mhz * 1e6 * 2.0 / 1e12
     out = []
-    chol_ms = stage_ms.get("factor", 0.0)
-    if chol_ms > 0:
-        flop = float(np.sum(n_b ** 3) / 3.0)
-        peak = props.multi_processor_count * 128 * mhz * 1e6 / 12.0 * 2.0 / 1e12
-        ach = flop / (chol_ms * 1e-3) / 1e12
-        out.append({"kernel": "cholesky_df_kernel (double-float S = L L^T, 4096 blocks per launch)", "bound": "alu",
-                    "achieved": ach, "peak": peak, "unit": "TFLOP/s (FP64-equivalent)", "frac": ach / peak,
-                    "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 ops/clk x {mhz:.0f} MHz"
-                                   " / 12 ops per double-float multiply-add",
-                    "ms_per_step": chol_ms,
-                    "traffic": traffic_per_launch("cholesky_df_kernel", len(n_b))})
     prod_ms = stage_ms.get("products", 0.0)
     if prod_ms > 0 and cnt["gemm_flops"] > 0:
         ach = cnt["gemm_flops"] / steps / (prod_ms * 1e-3) / 1e12
-        launches = max(cnt["gemm_launches"], 1)
         out.append({"kernel": "ns_pair_kernel (tcgen05 FP16 Newton-Schulz products, whole iteration per launch)",
                     "bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
                     "frac": ach / pk["bf16_tflops_sustained"],
                     "peak_source": pk["source"] + " bf16 sustained (FP16 dense rate = BF16 dense rate)",
                     "ms_per_step": prod_ms,
-                    "traffic": traffic_per_launch("ns_pair_kernel", cnt["gemm_flops"] / launches)})
+                    "traffic": traffic_per_launch("ns_pair_kernel", products_per_launch)})
+    upd_ms = stage_ms.get("factor_update", 0.0)
+    if upd_ms > 0:
+        flop = oz_update_tiles(n_b) * 28 * 2.0 * 128 * 32 * 64
+        ach = flop / (upd_ms * 1e-3) / 1e12
+        out.append({"kernel": "chol_update_kernel (Cholesky trailing updates from exact BF16 slices, tcgen05)",
+                    "bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                    "frac": ach / pk["bf16_tflops_sustained"],
+                    "peak_source": pk["source"] + " bf16 sustained", "ms_per_step": upd_ms, "traffic": None})
+    trsm_ms = stage_ms.get("factor_trsm", 0.0)
+    if trsm_ms > 0:
+        rows = sum(max(int(n) - t0, 0) for n in n_b for t0 in range(64, int(n), 64))
+        flop = rows * 3072 * 2.0
+        ach = flop / (trsm_ms * 1e-3) / 1e12
+        out.append({"kernel": "chol_trsm_kernel (rows below each 64 x 64 diagonal block, double-float)",
+                    "bound": "alu", "achieved": ach, "peak": df_peak, "unit": "TFLOP/s (FP64-equivalent)",
+                    "frac": ach / df_peak,
+                    "peak_source": f"derived: {sms} SMs x 128 FP32 ops/clk x {mhz:.0f} MHz / 12 ops per double-float "
+                                   "multiply-add", "ms_per_step": trsm_ms, "traffic": None})
+    inv_ms = stage_ms.get("inverse", 0.0)
+    if inv_ms > 0:
+        flop = float(np.sum(n_b ** 3) / 3.0)
+        ach = flop / (inv_ms * 1e-3) / 1e12
+        out.append({"kernel": "trinv_tile_kernel (L^-1 in FP32)", "bound": "alu", "achieved": ach, "peak": f32_peak,
+                    "unit": "TFLOP/s", "frac": ach / f32_peak,
+                    "peak_source": f"derived: {sms} SMs x 128 FP32 FMA/clk x 2 x {mhz:.0f} MHz",
+                    "ms_per_step": inv_ms, "traffic": None})
     return out
 
 

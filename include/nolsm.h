@@ -252,7 +252,8 @@ nolsm_status nolsm_set_wait_budget(nolsm_ctx* ctx, int64_t budget);
 /* Stages of the path timed by nolsm_phase_times. */
 typedef enum nolsm_phase {
   NOLSM_PHASE_GATHER = 0,      /* index sets done: dense T_b(H0), T_b(S) from the CSR rows (step 1) */
-  NOLSM_PHASE_FACTOR = 1,      /* Cholesky factor of every T_b(S) */
+  NOLSM_PHASE_FACTOR = 1,      /* Cholesky factor of every T_b(S) (double-float blocked mode: the 64 x 64
+                                  diagonal blocks and the FP32 copy; its other two parts below) */
   NOLSM_PHASE_INVERSE = 2,     /* triangular inverses L^-1 */
   NOLSM_PHASE_CONGRUENCE = 3,  /* A0 = L^-1 T_b(H0) L^-T */
   NOLSM_PHASE_BUILD_REST = 4,  /* own-column slabs, bounds, block features, tensor maps */
@@ -261,7 +262,9 @@ typedef enum nolsm_phase {
   NOLSM_PHASE_SLAB = 7,        /* own-column refinement and the block traces */
   NOLSM_PHASE_DENSITY = 8,     /* back-transform and scatter of D (step 3) */
   NOLSM_PHASE_ENERGY = 9,      /* Tr(D H0) */
-  NOLSM_NUM_PHASES = 10
+  NOLSM_PHASE_FACTOR_TRSM = 10,    /* blocked double-float factor: rows below each diagonal block */
+  NOLSM_PHASE_FACTOR_UPDATE = 11,  /* blocked double-float factor: tensor-core trailing updates */
+  NOLSM_NUM_PHASES = 12
 } nolsm_phase;
 
 /* Cumulative device time of each nolsm_phase (ms, CUDA event pairs recorded on the context stream

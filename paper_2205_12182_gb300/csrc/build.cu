@@ -1140,17 +1140,21 @@ cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode) {
     for (const auto& bd : ctx->h_blocks) max_n = std::max(max_n, bd.n);
     for (int pnl = 0; pnl * kOzPanel < max_n; ++pnl) {
       const int c0 = pnl * kOzPanel;
+      if (pnl > 0 && (e = phase_mark(ctx, NOLSM_PHASE_FACTOR)) != cudaSuccess) return e;
       chol_diag64_kernel<<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, sb, ctx->d_flags, c0, ctx->d_oz_exp,
                                                                  ctx->d_oz_w);
       ctx->n_launches += 1;
       if (c0 + kOzPanel >= max_n) break;
       const dim3 tg((max_n - c0 - kOzPanel + 63) / 64, ctx->n_blocks);
+      if ((e = phase_mark(ctx, NOLSM_PHASE_FACTOR_TRSM)) != cudaSuccess) return e;
       chol_trsm_kernel<<<tg, 128, kTrsmSmem, ctx->stream>>>(ctx->d_blocks, sb, ctx->d_oz_w, ctx->d_oz_exp,
                                                             reinterpret_cast<__nv_bfloat16*>(ctx->d_oz_planes), c0);
       ctx->n_launches += 1;
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if ((e = phase_mark(ctx, NOLSM_PHASE_FACTOR_UPDATE)) != cudaSuccess) return e;
       if ((e = launch_chol_update_tc(ctx, pnl, sb)) != cudaSuccess) return e;
     }
+    if ((e = phase_mark(ctx, NOLSM_PHASE_FACTOR)) != cudaSuccess) return e;
     factor_f32_kernel<<<dim3(8, std::min(ctx->n_blocks, 8192)), 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->n_blocks, sb,
                                                                                        s32);
     ctx->n_launches += 1;

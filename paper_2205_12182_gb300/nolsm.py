@@ -33,7 +33,7 @@ FUNCTIONS = ["nolsm_default_options", "nolsm_create", "nolsm_build_submatrices",
              "nolsm_last_error", "nolsm_destroy"]
 
 PHASES = ("gather", "factor", "inverse", "congruence", "build_rest", "sign_setup", "products", "slab", "density",
-          "energy")
+          "energy", "factor_trsm", "factor_update")
 
 N_PARAMS = 32 * 128 + 128 + 128 * 128 + 128 + 128 * 3 + 3
 N_FEATURES, N_OUTPUTS = 32, 3
