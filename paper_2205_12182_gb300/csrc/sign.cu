@@ -820,53 +820,64 @@ __device__ __forceinline__ int lower_bound_g(const int32_t* a, int n, int32_t ke
   return lo;
 }
 
+// D_b[:, C_b] = L^-T Y into the slab scratch: grid (128-row tile, block), each CTA one row tile for
+// every own column (L^-1[k, i] = 0 for k < i, so the sum over k starts at the tile).
 template <bool COMP>
-__global__ void __launch_bounds__(256) density_kernel(const BlockDesc* __restrict__ blocks,
-                                                      const int32_t* __restrict__ idx_pool,
-                                                      const int32_t* __restrict__ blk_cols,
-                                                      const float* __restrict__ linv, const float* __restrict__ y,
-                                                      float* __restrict__ dslab, const int64_t* __restrict__ row_ptr,
-                                                      const int32_t* __restrict__ col,
-                                                      const int64_t* __restrict__ transpose, double* __restrict__ dval,
-                                                      DevFlags* flags) {
+__global__ void __launch_bounds__(256) density_slab_kernel(const BlockDesc* __restrict__ blocks,
+                                                           const float* __restrict__ linv, const float* __restrict__ y,
+                                                           float* __restrict__ dslab) {
   __shared__ float Ls[32][129];
   __shared__ float Vs[32][8];
-  const BlockDesc bd = blocks[blockIdx.x];
-  const int ld = bd.n_pad, c = bd.c, n = bd.n;
+  const BlockDesc bd = blocks[blockIdx.y];
+  const int ld = bd.n_pad, c = bd.c;
+  const int r0 = blockIdx.x * 128;
+  if (r0 >= ld) return;
   const float* Li = linv + bd.off_mat;
   const float* Y = y + bd.off_slab;
   float* Dsl = dslab + bd.off_slab;
   const int tid = threadIdx.x;
   const int row = tid >> 1, cb = (tid & 1) * 4;
-  for (int r0 = 0; r0 < ld; r0 += 128) {
-    for (int c0 = 0; c0 < c; c0 += 8) {
-      AccSel<COMP> acc[4];
-      for (int k0 = r0; k0 < ld; k0 += 32) {     // L^-1[k, i] = 0 for k < i
-        for (int e = tid; e < 32 * 128; e += blockDim.x) {
-          const int kk = e >> 7, ii = e & 127;
-          Ls[kk][ii] = Li[(int64_t)(k0 + kk) * ld + r0 + ii];
-        }
-        {
-          const int kk = tid >> 3, cc = tid & 7;
-          Vs[kk][cc] = (c0 + cc < c) ? Y[(int64_t)(c0 + cc) * ld + k0 + kk] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int kk = 0; kk < 32; ++kk) {
-          const float lv = Ls[kk][row];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) acc[q].add_prod(lv, Vs[kk][cb + q]);
-        }
-        __syncthreads();
+  for (int c0 = 0; c0 < c; c0 += 8) {
+    AccSel<COMP> acc[4];
+    for (int k0 = r0; k0 < ld; k0 += 32) {
+      for (int e = tid; e < 32 * 128; e += blockDim.x) {
+        const int kk = e >> 7, ii = e & 127;
+        Ls[kk][ii] = Li[(int64_t)(k0 + kk) * ld + r0 + ii];
       }
+      {
+        const int kk = tid >> 3, cc = tid & 7;
+        Vs[kk][cc] = (c0 + cc < c) ? Y[(int64_t)(c0 + cc) * ld + k0 + kk] : 0.f;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int kk = 0; kk < 32; ++kk) {
+        const float lv = Ls[kk][row];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (c0 + cb + q < c) Dsl[(int64_t)(c0 + cb + q) * ld + r0 + row] = acc[q].value();
+        for (int q = 0; q < 4; ++q) acc[q].add_prod(lv, Vs[kk][cb + q]);
+      }
+      __syncthreads();
     }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (c0 + cb + q < c) Dsl[(int64_t)(c0 + cb + q) * ld + r0 + row] = acc[q].value();
   }
-  __syncthreads();
+}
+
+// Step 3: every stored entry (r, c) of an own column c is written to its CSR position transpose[e]
+// (e = the entry (c, r) of row c; the pattern is symmetric) from the block's D slab.
+__global__ void __launch_bounds__(256) density_scatter_kernel(const BlockDesc* __restrict__ blocks,
+                                                              const int32_t* __restrict__ idx_pool,
+                                                              const int32_t* __restrict__ blk_cols,
+                                                              const float* __restrict__ dslab,
+                                                              const int64_t* __restrict__ row_ptr,
+                                                              const int32_t* __restrict__ col,
+                                                              const int64_t* __restrict__ transpose,
+                                                              double* __restrict__ dval, DevFlags* flags) {
+  const BlockDesc bd = blocks[blockIdx.x];
+  const int ld = bd.n_pad, c = bd.c, n = bd.n;
+  const float* Dsl = dslab + bd.off_slab;
   const int32_t* I = idx_pool + bd.off_idx;
-  const int warp = tid >> 5, lane = tid & 31;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int j = warp; j < c; j += 8) {
     const int32_t cg = blk_cols[bd.col0 + j];
     const int64_t e0 = row_ptr[cg], e1 = row_ptr[cg + 1];
@@ -1065,14 +1076,17 @@ cudaError_t launch_slab_traces(nolsm_ctx* ctx, int half) {
 cudaError_t launch_density(nolsm_ctx* ctx) {
   cudaError_t e = cudaMemsetAsync(ctx->d_dval, 0, sizeof(double) * ctx->nnz, ctx->stream);
   if (e != cudaSuccess) return e;
+  int max_pad = 0;
+  for (const auto& bd : ctx->h_blocks) max_pad = std::max(max_pad, bd.n_pad);
+  const dim3 g(max_pad / 128, ctx->n_blocks);
   if (ctx->opt.precision == NOLSM_PREC_FP32)
-    density_kernel<true><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_idx, ctx->d_blk_cols,
-                                                                 ctx->d_linv, ctx->d_y, ctx->d_tmp, ctx->d_row_ptr,
-                                                                 ctx->d_col, ctx->d_transpose, ctx->d_dval, ctx->d_flags);
+    density_slab_kernel<true><<<g, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_linv, ctx->d_y, ctx->d_tmp);
   else
-    density_kernel<false><<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_idx, ctx->d_blk_cols,
-                                                                  ctx->d_linv, ctx->d_y, ctx->d_tmp, ctx->d_row_ptr,
-                                                                  ctx->d_col, ctx->d_transpose, ctx->d_dval, ctx->d_flags);
+    density_slab_kernel<false><<<g, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_linv, ctx->d_y, ctx->d_tmp);
+  density_scatter_kernel<<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_idx, ctx->d_blk_cols, ctx->d_tmp,
+                                                                 ctx->d_row_ptr, ctx->d_col, ctx->d_transpose,
+                                                                 ctx->d_dval, ctx->d_flags);
+  ctx->n_launches += 1;   // the second of the two (the caller counts one)
   return cudaGetLastError();
 }
 
