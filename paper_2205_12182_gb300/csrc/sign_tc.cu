@@ -1485,6 +1485,7 @@ struct CgParams {
   const CUtensorMap* tmaps;   // per bin: loads of [L^-1, A0 pool, T1], stores into [L^-1, A0 pool, T1]
   int map_a, map_b, map_c;    // pools of A, B and the output (0 L^-1, 1 A0 pool, 2 T1)
   int sym;
+  int interleave;             // 1: tile i to CTA i mod grid (large blocks); 0: contiguous runs
   float* out_pool;
   DevFlags* flags;
   long long budget;
@@ -1517,9 +1518,13 @@ __global__ void __launch_bounds__(CG_THREADS, 1) cong_tc_kernel(const __grid_con
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * CG_STAGES + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // contiguous runs of the tile list per CTA for small blocks (each SM walks whole blocks); tiles
+  // dealt round-robin for large ones, so that all SMs share a few blocks' operands in L2
   const int span = p.n_tiles;
-  const int first = (int)(((int64_t)span * blockIdx.x) / gridDim.x);
-  const int n_local = (int)(((int64_t)span * (blockIdx.x + 1)) / gridDim.x) - first;
+  const int first = p.interleave ? (int)blockIdx.x : (int)(((int64_t)span * blockIdx.x) / gridDim.x);
+  const int step = p.interleave ? (int)gridDim.x : 1;
+  const int n_local = p.interleave ? (span > (int)blockIdx.x ? (span - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0)
+                                   : (int)(((int64_t)span * (blockIdx.x + 1)) / gridDim.x) - first;
   if (threadIdx.x == 0) {
     for (int s = 0; s < CG_STAGES; ++s) {
       mbar_init(&full_bar[s], 1);
@@ -1552,7 +1557,7 @@ __global__ void __launch_bounds__(CG_THREADS, 1) cong_tc_kernel(const __grid_con
       uint32_t ph = 0;
       bool ok = true;
       for (int i = 0; i < n_local && ok; ++i) {
-        const Tile tl = p.tiles[first + i];
+        const Tile tl = p.tiles[first + i * step];
         const BlockDesc bd = p.blocks[tl.block];
         const CUtensorMap* ma = p.tmaps + bd.bin * 6 + p.map_a;
         const CUtensorMap* mb = p.tmaps + bd.bin * 6 + p.map_b;
@@ -1586,7 +1591,7 @@ __global__ void __launch_bounds__(CG_THREADS, 1) cong_tc_kernel(const __grid_con
       // kind::tf32: FP32 accumulator (bit 4), A and B TF32 (format 2), both K-major, N >> 3, M >> 4
       const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(CG_TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
       for (int i = 0; i < n_local && ok; ++i) {
-        const Tile tl = p.tiles[first + i];
+        const Tile tl = p.tiles[first + i * step];
         if (!mbar_wait(&tempty_bar[acc], tph[acc] ^ 1u, budget, abort_flag)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * CG_TN);
@@ -1625,7 +1630,7 @@ __global__ void __launch_bounds__(CG_THREADS, 1) cong_tc_kernel(const __grid_con
     int s = 0;
     uint32_t ph = 0;
     for (int i = 0; i < n_local; ++i) {
-      const Tile tl = p.tiles[first + i];
+      const Tile tl = p.tiles[first + i * step];
       bool ok = true;
       for (int k0 = 0; k0 < tl.kend; k0 += CG_TK) {
         if (!mbar_wait(&full_bar[s], ph, budget, abort_flag)) { ok = false; break; }
@@ -1663,7 +1668,7 @@ __global__ void __launch_bounds__(CG_THREADS, 1) cong_tc_kernel(const __grid_con
     uint32_t tph[2] = {0u, 0u};
     int acc = 0;
     for (int i = 0; i < n_local; ++i) {
-      const Tile tl = p.tiles[first + i];
+      const Tile tl = p.tiles[first + i * step];
       const BlockDesc bd = p.blocks[tl.block];
       if (!__all_sync(0xffffffffu, mbar_wait(&tfull_bar[acc], tph[acc], budget, abort_flag))) {
         set_error(p.flags, NOLSM_ETIMEOUT);
@@ -1870,6 +1875,8 @@ cudaError_t launch_congruence_tc(nolsm_ctx* ctx, float* t1) {
     bin_pad[b.bin] = b.n_pad;
   }
   std::vector<CUtensorMap> maps((size_t)n_bins * 6);
+  int max_pad = 0;
+  for (const auto& b : ctx->h_blocks) max_pad = std::max(max_pad, b.n_pad);
   float* pools[3] = {ctx->d_linv, ctx->d_a0, t1};
   for (int bi = 0; bi < n_bins; ++bi)
     for (int pi = 0; pi < 3; ++pi) {
@@ -1927,6 +1934,7 @@ cudaError_t launch_congruence_tc(nolsm_ctx* ctx, float* t1) {
     p.map_b = pass ? 0 : 1;                   // L^-1 : T_b(H0) in the A0 pool
     p.map_c = pass ? 1 : 2;                   // A0 pool : T1
     p.sym = pass;
+    p.interleave = max_pad >= 1024;
     p.out_pool = pass ? ctx->d_a0 : t1;
     p.flags = ctx->d_flags;
     p.budget = ctx->opt.wait_budget;
