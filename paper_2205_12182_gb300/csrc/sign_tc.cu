@@ -561,10 +561,14 @@ struct PairCtl {
 };
 constexpr int PAIR_THREADS = 320;             // producer, MMA issuer, 8 epilogue warps (2 per TMEM lane quarter)
 constexpr int PAIR_EPI_WARPS = 8;
-constexpr int PAIR_NBUF = 1;                  // staging buffers per epilogue warp
-constexpr int PAIR_LAYOUT = PAIR_EPI_WARPS * PAIR_NBUF / 4;   // in units of 4 warps x 1 buffer
-constexpr int PAIR_SMEM = smem_bytes<PAIR_LAYOUT>() + (int)sizeof(PairCtl);
+constexpr int PAIR_NBUF = 2;                  // staging buffers per epilogue warp (a chunk's store overlaps the next)
+constexpr int PAIR_STAGES = 3;                // operand stages (48 KB each)
+constexpr int PAIR_EPI_OFF = PAIR_STAGES * STAGE_BYTES;
+constexpr int PAIR_BAR_OFF = PAIR_EPI_OFF + PAIR_EPI_WARPS * PAIR_NBUF * EPI_BUF_BYTES;
+constexpr int PAIR_TAB_OFF = PAIR_BAR_OFF + 256;
+constexpr int PAIR_SMEM = 1024 + PAIR_TAB_OFF + (int)sizeof(PairCtl);
 static_assert(PAIR_SMEM <= 227 * 1024, "shared memory of the persistent kernel");
+static_assert(2 * PAIR_STAGES + 7 <= 32, "barrier area of the persistent kernel");
 
 __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
@@ -647,22 +651,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PAIR_THREADS, 1) ns_
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* stage_base = smem;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + bar_off<PAIR_LAYOUT>());
-  uint64_t* full_bar = bars;                       // [STAGES]
-  uint64_t* empty_bar = bars + STAGES;             // [STAGES]
-  uint64_t* tfull_bar = bars + 2 * STAGES;         // [2]
-  uint64_t* tempty_bar = bars + 2 * STAGES + 2;    // [2]
-  uint64_t* drain_bar = bars + 2 * STAGES + 4;     // [1]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + PAIR_BAR_OFF);
+  uint64_t* full_bar = bars;                       // [PAIR_STAGES]
+  uint64_t* empty_bar = bars + PAIR_STAGES;             // [PAIR_STAGES]
+  uint64_t* tfull_bar = bars + 2 * PAIR_STAGES;         // [2]
+  uint64_t* tempty_bar = bars + 2 * PAIR_STAGES + 2;    // [2]
+  uint64_t* drain_bar = bars + 2 * PAIR_STAGES + 4;     // [1]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * PAIR_STAGES + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  PairCtl* ctl = reinterpret_cast<PairCtl*>(smem + tab_off<PAIR_LAYOUT>());
+  PairCtl* ctl = reinterpret_cast<PairCtl*>(smem + PAIR_TAB_OFF);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = cluster_rank();
   PairCtl* ctl0 = cluster_peer(ctl, 0u);
   PairCtl* ctl1 = cluster_peer(ctl, 1u);
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+    for (int s = 0; s < PAIR_STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
     for (int a = 0; a < 2; ++a) { mbar_init(&tfull_bar[a], 1); mbar_init(&tempty_bar[a], 32 * PAIR_EPI_WARPS); }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -718,7 +722,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PAIR_THREADS, 1) ns_
             for (int h = 0; h < t.tn; h += TM) tma_load_2d(b_dst + h * TK * 2, mb, &full_bar[ps], k0, rowbase + t.n0 + h);
             armed |= 1u << ps;
             arm_parity = (arm_parity & ~(1u << ps)) | (pph << ps);
-            if (++ps == STAGES) { ps = 0; pph ^= 1u; }
+            if (++ps == PAIR_STAGES) { ps = 0; pph ^= 1u; }
           }
         }
         if (!ok) {
@@ -745,7 +749,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PAIR_THREADS, 1) ns_
             for (int kk = 0; kk < TK / 16; ++kk)
               umma_f16(d_tmem, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), idesc, (k0 | kk) != 0);
             umma_commit(&empty_bar[ms]);
-            if (++ms == STAGES) { ms = 0; mph ^= 1u; }
+            if (++ms == PAIR_STAGES) { ms = 0; mph ^= 1u; }
           }
           if (!ok) break;
           umma_commit(&tfull_bar[macc]);
@@ -775,7 +779,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PAIR_THREADS, 1) ns_
         const int hw = t.tn / 2, h0 = ((warp - 2) / 4) * hw;
         rsq += epi_tile<T, PAIR_NBUF, 32>(tmem_base + (uint32_t)(eacc * TN + h0), q, lane, out, ld, t.m0, t.n0 + h0, hw,
                                       phase, c1, c3, smap, bd.pos * ld,
-                                      smem + EPI_OFF + (warp - 2) * PAIR_NBUF * EPI_BUF_BYTES, ebuf);
+                                      smem + PAIR_EPI_OFF + (warp - 2) * PAIR_NBUF * EPI_BUF_BYTES, ebuf);
         tc_fence_before();
         mbar_arrive(&tempty_bar[eacc]);
         etph[eacc] ^= 1u;
@@ -871,7 +875,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PAIR_THREADS, 1) ns_
   // teardown: every copy and product issued here lands before shared and tensor memory go away
   if (warp == 0 && lane == 0) {
     volatile int never = 0;
-    for (int st = 0; st < STAGES; ++st)
+    for (int st = 0; st < PAIR_STAGES; ++st)
       if (armed & (1u << st)) mbar_wait(&full_bar[st], (arm_parity >> st) & 1u, drain_budget, &never);
   } else if (warp == 1 && lane == 0) {
     umma_commit(drain_bar);
