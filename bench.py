@@ -406,12 +406,15 @@ def rooflines(stage_ms, cnt, steps, n_b, pk, sm_max_mhz, props, products_per_lau
                     "traffic": traffic_per_launch("ns_pair_kernel", products_per_launch)})
     upd_ms = stage_ms.get("factor_update", 0.0)
     if upd_ms > 0:
-        flop = oz_update_tiles(n_b) * 28 * 2.0 * 128 * 32 * 64
+        tiles = oz_update_tiles(n_b)
+        flop = tiles * 28 * 2.0 * 128 * 32 * 64
         ach = flop / (upd_ms * 1e-3) / 1e12
-        out.append({"kernel": "chol_update_kernel (Cholesky trailing updates from exact BF16 slices, tcgen05)",
+        out.append({"kernel": "chol_update_kernel (Cholesky trailing updates from exact BF16 slices, tcgen05; "
+                              "7 launches per step, traffic summed)",
                     "bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
                     "frac": ach / pk["bf16_tflops_sustained"],
-                    "peak_source": pk["source"] + " bf16 sustained", "ms_per_step": upd_ms, "traffic": None})
+                    "peak_source": pk["source"] + " bf16 sustained", "ms_per_step": upd_ms,
+                    "traffic": traffic_per_launch("chol_update_kernel", tiles)})
     trsm_ms = stage_ms.get("factor_trsm", 0.0)
     if trsm_ms > 0:
         rows = sum(max(int(n) - t0, 0) for n in n_b for t0 in range(64, int(n), 64))
