@@ -250,6 +250,8 @@ def run_ours(args):
     }
     if not args.no_variants:
         line["variants"] = variants(nolsm, system, mu_fn, d_dev, predictor, barrier, world)
+    if not args.no_combination and world == 1:
+        line["combination"] = combination(nolsm, predictor, system, parity=rank == 0 and not args.no_parity)
     if not args.no_large and world == 1:
         line["largest_blocks"] = large_blocks(nolsm, predictor, pk, parity=rank == 0 and not args.no_parity)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -329,6 +331,80 @@ def large_blocks(nolsm, predictor, pk, parity=True, steps=2, evals=3):
     if parity:
         out["parity"] = parity_sample(s, lib.density().cpu().numpy(), mu, n_blocks=2)
     lib.close()
+    return out
+
+
+def combination(nolsm, predictor, system, parity=True, steps=2, evals=3):
+    """Submatrix combination (Section III-B-1, Table II) on the benchmark system: no combination,
+    Eq. 9 and Eq. 10 with the committed p(n) table.  Per criterion: the planning time on the host,
+    the submatrix statistics of Table II (count, smallest, largest, average dimension, flops of one
+    product of every submatrix, estimated TFLOP/s and speedup from p(n)), and the same full step
+    measured on the GPU with the combined blocks (1 warm-up, `steps` timed) with the products'
+    device time over `evals` sign evaluations at the converged mu."""
+    import torch
+    try:
+        pn = nolsm.load_pn_table()
+    except OSError:
+        pn = None
+    crits = [("none", None), ("eq9_cubic", nolsm.COMBINE_CUBIC)]
+    if pn is not None:
+        crits.append(("eq10_performance", nolsm.COMBINE_PERFORMANCE))
+    d_dev = torch.empty(system.nnz, dtype=torch.float64, device="cuda")
+    mu_fn = lambda lib_, s_: lib_.set_mu(s_.n_electrons, tol_n=TOL_N)   # noqa: E731
+
+    def t_est(dims):
+        """Predicted products time of one multiplication of every submatrix: sum 2 n^3 p(n) (s)."""
+        d = dims.astype(np.float64)
+        return float((2 * d ** 3 * np.interp(d, pn[0], pn[1])).sum()) if pn is not None else None
+
+    out = {"p_table": None if pn is None else {"n": [int(pn[0][0]), int(pn[0][-1])], "points": len(pn[0]),
+                                               "source": "paper_2205_12182_gb300/weights/pn_gb300.json"}}
+    base_est = None
+    for name, crit in crits:
+        t0 = time.perf_counter()
+        s, r = (system, None) if crit is None else \
+            nolsm.combine_blocks(system, crit, pn if crit == nolsm.COMBINE_PERFORMANCE else None)
+        plan_s = time.perf_counter() - t0
+        lib = nolsm.Nolsm(precision=nolsm.PREC_MIXED_FP16, bounds=nolsm.BOUNDS_LEARNED)
+        lib.set_predictor(predictor)
+        solve(lib, s, mu_fn, d_dev, "device")
+        torch.cuda.synchronize()
+        dims = np.array([nolsm.nolsm_block_info(lib.ctx, b)[0] for b in range(s.n_blocks)], np.int64)
+        if r is not None:
+            assert np.array_equal(dims, r["dim"]), "combined dimensions disagree with the built index sets"
+        flops = float((2 * dims.astype(np.float64) ** 3).sum())
+        est = t_est(dims)
+        if base_est is None:
+            base_est = est
+        t1 = time.perf_counter()
+        for _ in range(steps):
+            mu, n, mu_steps, e = solve(lib, s, mu_fn, d_dev, "device")
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t1) / steps
+        lib.phase_times(reset=True)
+        fp = 0.0
+        for _ in range(evals):
+            st = lib.sign_batch(mu)
+            fp += st["flops_paper"]
+        prod_ms = lib.phase_times(reset=True)["products"] / evals
+        row = {"submatrices": int(len(dims)), "smallest": int(dims.min()), "largest": int(dims.max()),
+               "average_dim": float(dims.mean()), "gflop_per_multiplication": flops / 1e9,
+               "estimated_tflops": flops / est / 1e12 if est else None,
+               "estimated_speedup": base_est / est if est else None,
+               "plan_seconds": plan_s,
+               "measured": {"value": WORKLOAD["atoms"] / dt, "unit": "atoms/s", "ms_per_step": dt * 1e3,
+                            "mu_steps": mu_steps, "ns_iters_avg": st["iters_avg"],
+                            "products_ms_per_sign_evaluation": prod_ms,
+                            "products_tflops_paper_convention": fp / evals / (prod_ms * 1e-3) / 1e12}}
+        if parity and crit is not None:
+            row["parity"] = parity_sample(s, lib.density().cpu().numpy(), mu, n_blocks=2)
+        out[name] = row
+        lib.close()
+    base = out["none"]["measured"]
+    for name, _ in crits[1:]:
+        m = out[name]["measured"]
+        m["speedup_full_step"] = base["ms_per_step"] / m["ms_per_step"]
+        m["speedup_products"] = base["products_ms_per_sign_evaluation"] / m["products_ms_per_sign_evaluation"]
     return out
 
 
@@ -516,6 +592,7 @@ def main():
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the large-block (32-molecule cluster) section")
+    ap.add_argument("--no-combination", action="store_true", help="skip the submatrix-combination section")
     ap.add_argument("--side", type=int, default=16,
                     help="molecules per box edge (16: the 4,096-molecule workload; smaller boxes for profiling)")
     args = ap.parse_args()

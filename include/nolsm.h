@@ -336,6 +336,52 @@ void nolsm_mlp_destroy(nolsm_mlp* mlp);
 /* Use mlp (kept by the caller, alive while ctx uses it) for NOLSM_BOUNDS_LEARNED; NULL detaches. */
 nolsm_status nolsm_set_predictor(nolsm_ctx* ctx, const nolsm_mlp* mlp);
 
+/* ---- submatrix combination ---------------------------------------------------------------
+ * Section III-B-1: column blocks whose submatrices overlap strongly are cheaper solved as one.
+ * Combining blocks a and b gives one block with own columns C_a u C_b and index set I_a u I_b, of
+ * dimension n_a + n_b - n_ab (n_ab = |I_a n I_b|).  It pays iff t(n_a + n_b - n_ab) < t(n_a) + t(n_b)
+ * with t(n) = n^3 (Eq. 9) or t(n) = p(n) n^3 (Eq. 10), p(n) the measured time per flop of the
+ * matrix products at dimension n. */
+typedef enum nolsm_combine_criterion {
+  NOLSM_COMBINE_CUBIC = 0,        /* Eq. 9: flops of the dense products */
+  NOLSM_COMBINE_PERFORMANCE = 1   /* Eq. 10: predicted run time p(n) n^3 */
+} nolsm_combine_criterion;
+
+/* Combine the column blocks of nolsm_build_submatrices' arguments (host work only: no context, no
+ * GPU, thread safe).  Index sets follow nolsm_build_submatrices (the own columns' rows in the
+ * pattern, the own columns, the extra list).  Order (the paper leaves it to earlier work): blocks
+ * are candidates when the index set of one holds an own column of the other; each step combines the
+ * candidate pair with the largest saving t(n_a) + t(n_b) - t(n_merged) > 0 whose merged dimension is
+ * at most max_dim (ties: smallest pair of ids), the combined block keeps the smaller id, and the
+ * loop stops when no candidate pays.
+ *   pattern        host CSR (row_ptr, col; val unused) of H0 and S, structurally symmetric.
+ *   blk_*, extra_* as for nolsm_build_submatrices; every column is owned by at most one block.
+ *   criterion      nolsm_combine_criterion.
+ *   pn_dim, pn_time (NOLSM_COMBINE_PERFORMANCE only; n_points >= 1 entries): sizes, strictly
+ *                  ascending and >= 1, and the measured time per flop at each (positive, finite);
+ *                  p(n) is linear in n between neighbouring sizes and constant beyond the ends.
+ *   max_dim        largest dimension a combination may produce (input blocks above it stay alone).
+ * Outputs (caller-owned host arrays; all but n_out and group may be NULL):
+ *   *n_out         number of combined blocks m, numbered in ascending order of their smallest
+ *                  input block;
+ *   group          n_blocks entries: the combined block of each input block;
+ *   out_blk_ptr    m + 1 entries (room for n_blocks + 1) and out_blk_cols (room for
+ *                  blk_ptr[n_blocks]): each combined block's own columns, its input blocks' columns
+ *                  in ascending block order;
+ *   out_extra_ptr  m + 1 entries (room for n_blocks + 1) and out_extra_idx (room for
+ *                  extra_ptr[n_blocks]): the sorted distinct union of the members' extra lists
+ *                  (only with extra input);
+ *   out_dim        m entries (room for n_blocks): n of each combined block;
+ *   cost           2 doubles: the sum of t(n) over the input blocks and over the combined blocks.
+ * Errors: EINVAL (null or inconsistent arguments, device memory, an index out of range, a column
+ * owned twice, a bad p table, max_dim < 1), ENOMEM.  Nothing is written on error. */
+nolsm_status nolsm_combine_blocks(const nolsm_csr* pattern, int32_t n_blocks, const int32_t* blk_ptr,
+                                  const int32_t* blk_cols, const int32_t* extra_ptr, const int32_t* extra_idx,
+                                  int32_t criterion, int32_t n_points, const int32_t* pn_dim, const double* pn_time,
+                                  int32_t max_dim, int32_t* n_out, int32_t* group, int32_t* out_blk_ptr,
+                                  int32_t* out_blk_cols, int32_t* out_extra_ptr, int32_t* out_extra_idx,
+                                  int32_t* out_dim, double* cost);
+
 /* Message of the last error of ctx (never NULL; "" when none).  ctx may be NULL. */
 const char* nolsm_last_error(const nolsm_ctx* ctx);
 

@@ -16,7 +16,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnolsm.so")
-SOURCES = ["api.cu", "index.cu", "build.cu", "sign.cu", "sign_tc.cu", "learn.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "index.cu", "build.cu", "sign.cu", "sign_tc.cu", "learn.cu", "noalloc.cu", "combine.cu"]
+# host-only planning code whose floating-point decisions must not depend on the host: no fused multiply-add
+PER_SOURCE = {"combine.cu": ["-Xcompiler", "-ffp-contract=off"]}
 HEADERS = [os.path.join(CSRC, "internal.h"), os.path.join(ROOT, "include", "nolsm.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -41,7 +43,7 @@ def _compile(src: str, force: bool, verbose: bool, extra) -> str:
     path = os.path.join(CSRC, src)
     obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
     if force or _stale(obj, [path] + HEADERS):
-        cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", path, "-o", obj]
+        cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *PER_SOURCE.get(src, []), *extra, "-c", path, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -23,6 +23,7 @@ BOUNDS_GERSHGORIN, BOUNDS_LANCZOS, BOUNDS_LEARNED = 0, 1, 2
 CHOL_FP64, CHOL_FP32, CHOL_FP64_INV64, CHOL_DF64, CHOL_DF64_SIMT = 0, 1, 2, 3, 4
 SCHEDULE_PERSISTENT, SCHEDULE_PER_PRODUCT, SCHEDULE_AUTO = 0, 1, 2
 REFINE_TENSOR, REFINE_SIMT = 0, 1
+COMBINE_CUBIC, COMBINE_PERFORMANCE = 0, 1
 
 FUNCTIONS = ["nolsm_default_options", "nolsm_create", "nolsm_build_submatrices", "nolsm_sign_batch", "nolsm_set_mu",
              "nolsm_density", "nolsm_band_energy", "nolsm_block_info", "nolsm_block_index_set", "nolsm_block_bounds",
@@ -30,7 +31,7 @@ FUNCTIONS = ["nolsm_default_options", "nolsm_create", "nolsm_build_submatrices",
              "nolsm_band_energy_noalloc",
              "nolsm_block_features", "nolsm_block_lanczos", "nolsm_mlp_create", "nolsm_mlp_get_params",
              "nolsm_mlp_gradient", "nolsm_mlp_adam", "nolsm_mlp_predict", "nolsm_mlp_destroy", "nolsm_set_predictor",
-             "nolsm_last_error", "nolsm_destroy"]
+             "nolsm_combine_blocks", "nolsm_last_error", "nolsm_destroy"]
 
 PHASES = ("gather", "factor", "inverse", "congruence", "build_rest", "sign_setup", "products", "slab", "density",
           "energy", "factor_trsm", "factor_update")
@@ -102,6 +103,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "nolsm_mlp_predict": (i32, [P, P, i32, P]),
         "nolsm_mlp_destroy": (None, [P]),
         "nolsm_set_predictor": (i32, [P, P]),
+        "nolsm_combine_blocks": (i32, [C.POINTER(NolsmCsr), i32, P, P, P, P, i32, i32, P, P, i32, pi32, P, P, P, P, P,
+                                       P, P]),
         "nolsm_last_error": (C.c_char_p, [P]),
         "nolsm_destroy": (None, [P]),
     }
@@ -284,6 +287,67 @@ def nolsm_mlp_destroy(mlp):
 
 def nolsm_set_predictor(ctx, mlp):
     _check(ctx, _lib.nolsm_set_predictor(ctx, mlp))
+
+
+def nolsm_combine_blocks(n, row_ptr, col, blk_ptr, blk_cols, extra_ptr=None, extra_idx=None,
+                         criterion=COMBINE_CUBIC, pn_dim=None, pn_time=None, max_dim=4096) -> dict:
+    """Host arrays in, host arrays out: the combined blocks (Eq. 9 / Eq. 10) and their dimensions."""
+    row_ptr = np.ascontiguousarray(row_ptr, np.int64)
+    col = np.ascontiguousarray(col, np.int32)
+    blk_ptr = np.ascontiguousarray(blk_ptr, np.int32)
+    blk_cols = np.ascontiguousarray(blk_cols, np.int32)
+    nb = blk_ptr.shape[0] - 1
+    has_extra = extra_ptr is not None
+    if has_extra:
+        extra_ptr = np.ascontiguousarray(extra_ptr, np.int32)
+        extra_idx = np.ascontiguousarray(extra_idx, np.int32)
+    npts = 0
+    if pn_dim is not None:
+        pn_dim = np.ascontiguousarray(pn_dim, np.int32)
+        pn_time = np.ascontiguousarray(pn_time, np.float64)
+        npts = pn_dim.shape[0]
+    pattern = make_csr(n, col.shape[0], row_ptr, col, None, MEM_HOST)
+    n_out = C.c_int32(0)
+    group = np.empty(nb, np.int32)
+    o_ptr = np.empty(nb + 1, np.int32)
+    o_cols = np.empty(max(blk_cols.shape[0], 1), np.int32)
+    o_eptr = np.empty(nb + 1, np.int32) if has_extra else None
+    o_eidx = np.empty(max(int(extra_ptr[-1]), 1), np.int32) if has_extra else None
+    o_dim = np.empty(nb, np.int32)
+    cost = np.zeros(2, np.float64)
+    _check(None, _lib.nolsm_combine_blocks(C.byref(pattern), nb, _ptr(blk_ptr), _ptr(blk_cols), _ptr(extra_ptr),
+                                           _ptr(extra_idx), int(criterion), npts, _ptr(pn_dim), _ptr(pn_time),
+                                           int(max_dim), C.byref(n_out), _ptr(group), _ptr(o_ptr), _ptr(o_cols),
+                                           _ptr(o_eptr), _ptr(o_eidx), _ptr(o_dim), _ptr(cost)))
+    m = n_out.value
+    out = {"n_blocks": m, "group": group, "blk_ptr": o_ptr[:m + 1].copy(), "blk_cols": o_cols[:o_ptr[m]].copy(),
+           "dim": o_dim[:m].copy(), "cost_in": float(cost[0]), "cost_out": float(cost[1]),
+           "extra_ptr": None, "extra_idx": None}
+    if has_extra:
+        out["extra_ptr"] = o_eptr[:m + 1].copy()
+        out["extra_idx"] = o_eidx[:o_eptr[m]].copy()
+    return out
+
+
+PN_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "pn_gb300.json")
+
+
+def load_pn_table(path: str = PN_TABLE):
+    """(sizes, time per flop) of the measured product throughput, for COMBINE_PERFORMANCE."""
+    import json
+    with open(path) as f:
+        d = json.load(f)
+    return np.asarray(d["n"], np.int32), np.asarray(d["time_per_flop"], np.float64)
+
+
+def combine_blocks(system, criterion=COMBINE_CUBIC, pn=None, max_dim=4096):
+    """(copy of a dataclass system with the combined blocks, result of nolsm_combine_blocks)."""
+    import dataclasses
+    dims, times = pn if pn is not None else (None, None)
+    r = nolsm_combine_blocks(len(system.row_ptr) - 1, system.row_ptr, system.col, system.blk_ptr, system.blk_cols,
+                             system.extra_ptr, system.extra_idx, criterion, dims, times, max_dim)
+    return dataclasses.replace(system, blk_ptr=r["blk_ptr"], blk_cols=r["blk_cols"], extra_ptr=r["extra_ptr"],
+                               extra_idx=r["extra_idx"]), r
 
 
 def nolsm_last_error(ctx) -> str:

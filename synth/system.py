@@ -363,6 +363,43 @@ def dimer_system(a: float, b: float, s: float) -> System:
                   2.0, np.array([0, 1, 2], np.int32), np.array([0, 1], np.int32))
 
 
+def dense_blocks(n: int, n_blocks: int, seed: int, noise: float = 0.1, n_unique: int | None = None) -> System:
+    """n_blocks uncoupled dense blocks of dimension n (block-diagonal H0 and S, one column block
+    per dense block, so every index set has exactly n entries): for timing the matrix products at
+    a chosen n.
+
+    S_k = I + E_k and H0_k = diag(d_k) + F_k, with E_k and F_k symmetric, entries N(0, (noise /
+    sqrt(n))^2) (spectral norm about 2 * noise), and d_k = -1 or +0.5 Ha with equal probability, so
+    the generalized spectrum lies in two clusters around -1 and +0.5 with a gap around -0.25 Ha.
+    N_e counts the states below the gap twice.  With n_unique set, only that many blocks are
+    drawn and block k repeats block k % n_unique (cheap large batches for timing).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sd = noise / np.sqrt(n)
+    hv = np.empty((n_blocks, n, n))
+    sv = np.empty((n_blocks, n, n))
+    occ = 0
+    n_unique = n_blocks if n_unique is None else max(1, min(n_unique, n_blocks))
+    for k in range(n_blocks):
+        if k >= n_unique:
+            hv[k], sv[k] = hv[k % n_unique], sv[k % n_unique]
+            occ += int((np.diag(hv[k]) < -0.25).sum())
+            continue
+        e = rng.normal(0.0, sd, size=(n, n))
+        f = rng.normal(0.0, sd, size=(n, n))
+        d = np.where(rng.random(n) < 0.5, -1.0, 0.5)
+        occ += int((d < 0).sum())
+        sv[k] = np.triu(e, 1) + np.triu(e, 1).T + np.eye(n)
+        hv[k] = np.triu(f) + np.triu(f, 1).T + np.diag(d)
+    nb = n * n_blocks
+    row_ptr = (np.arange(nb + 1, dtype=np.int64) * n)
+    col = ((np.arange(nb)[:, None] // n) * n + np.arange(n)[None, :]).reshape(-1).astype(np.int32)
+    blk_ptr = (np.arange(n_blocks + 1) * n).astype(np.int32)
+    coords = np.zeros((nb, 3))
+    return System(f"dense{n}x{n_blocks}", 0.0, coords, np.full(nb, H), np.arange(nb + 1), row_ptr, col,
+                  hv.reshape(-1), sv.reshape(-1), 2.0 * occ, blk_ptr, np.arange(nb, dtype=np.int32))
+
+
 # --------------------------------------------------------------------------- named configs
 
 CONFIGS = {
