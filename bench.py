@@ -198,10 +198,10 @@ def run_ours(args):
     h2d = system.row_ptr.astype(np.int64).nbytes + system.col.astype(np.int32).nbytes + 2 * system.nnz * 8
     d2h = system.nnz * 8 + 8 * 3
 
-    # parity spot check of this run's D against the oracle on sampled blocks (not timed)
-    parity = None
+    # D of this run on sampled blocks, compared with the oracle in the cpu_baseline leg (not timed)
+    checks = {}
     if rank == 0 and not args.no_parity:
-        parity = parity_sample(system, d_host.numpy(), mu)
+        checks["headline"] = (system, d_host.numpy().copy(), mu, 8)
 
     atoms = WORKLOAD["atoms"] * world
     pk = peaks()
@@ -245,17 +245,26 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(cnt["launches"]),
         "clocks": clk.summary(),
-        "parity": parity,
+        "parity": None,
         "result": {"mu": mu, "n_electrons": n, "band_energy": e},
     }
     if not args.no_variants:
         line["variants"] = variants(nolsm, system, mu_fn, d_dev, predictor, barrier, world)
+    want = rank == 0 and not args.no_parity
     if not args.no_combination and world == 1:
-        line["combination"] = combination(nolsm, predictor, system, parity=rank == 0 and not args.no_parity)
+        line["combination"] = combination(nolsm, predictor, system, checks if want else None)
     if not args.no_large and world == 1:
-        line["largest_blocks"] = large_blocks(nolsm, predictor, pk, parity=rank == 0 and not args.no_parity)
+        line["largest_blocks"] = large_blocks(nolsm, predictor, pk, checks if want else None)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the cpu_baseline leg: the oracle timed on the host cores, then the parity spot checks
         line["cpu_baseline"] = cpu_baseline(system, seconds=args.cpu_seconds)
+        for key, res in parity_checks(checks).items():
+            if key == "headline":
+                line["parity"] = res
+            elif key == "largest_blocks":
+                line["largest_blocks"]["parity"] = res
+            else:
+                line["combination"][key.split(".", 1)[1]]["parity"] = res
     lib.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -294,7 +303,7 @@ def variants(nolsm, system, mu_fn, d_dev, predictor, barrier, world, steps=2):
     return out
 
 
-def large_blocks(nolsm, predictor, pk, parity=True, steps=2, evals=3):
+def large_blocks(nolsm, predictor, pk, checks=None, steps=2, evals=3):
     """The block shape of the 1,000,000-molecule configuration -- 32-molecule clusters with an 8 A
     halo, n_b ~ 1,870 (n_pad 1,920) -- on a 13,824-molecule box (432 blocks): atoms/s of the full
     step (1 warm-up, `steps` timed) and the sign products' TFLOP/s over `evals` sign evaluations at
@@ -328,13 +337,13 @@ def large_blocks(nolsm, predictor, pk, parity=True, steps=2, evals=3):
                          "pct_fp16_peak_measured": 100 * tf / pk["bf16_tflops_sustained"],
                          "ms_per_sign_evaluation": cnt["gemm_ms"] / evals, "ns_iters_avg": st["iters_avg"],
                          "schedule": "per-product launches, tiles dealt round-robin"}}
-    if parity:
-        out["parity"] = parity_sample(s, lib.density().cpu().numpy(), mu, n_blocks=2)
+    if checks is not None:
+        checks["largest_blocks"] = (s, lib.density().cpu().numpy(), mu, 2)
     lib.close()
     return out
 
 
-def combination(nolsm, predictor, system, parity=True, steps=2, evals=3):
+def combination(nolsm, predictor, system, checks=None, steps=2, evals=3):
     """Submatrix combination (Section III-B-1, Table II) on the benchmark system: no combination,
     Eq. 9 and Eq. 10 with the committed p(n) table.  Per criterion: the planning time on the host,
     the submatrix statistics of Table II (count, smallest, largest, average dimension, flops of one
@@ -342,13 +351,17 @@ def combination(nolsm, predictor, system, parity=True, steps=2, evals=3):
     measured on the GPU with the combined blocks (1 warm-up, `steps` timed) with the products'
     device time over `evals` sign evaluations at the converged mu."""
     import torch
-    try:
-        pn = nolsm.load_pn_table()
-    except OSError:
-        pn = None
-    crits = [("none", None), ("eq9_cubic", nolsm.COMBINE_CUBIC)]
+    def table(path):
+        try:
+            return nolsm.load_pn_table(path)
+        except OSError:
+            return None
+    pn, pn_step = table(nolsm.PN_TABLE), table(nolsm.PN_STEP_TABLE)
+    crits = [("none", None, None), ("eq9_cubic", nolsm.COMBINE_CUBIC, None)]
     if pn is not None:
-        crits.append(("eq10_performance", nolsm.COMBINE_PERFORMANCE))
+        crits.append(("eq10_performance", nolsm.COMBINE_PERFORMANCE, pn))
+    if pn_step is not None:       # Eq. 10's rule with the whole step's measured time per flop
+        crits.append(("eq10_full_step_time", nolsm.COMBINE_PERFORMANCE, pn_step))
     d_dev = torch.empty(system.nnz, dtype=torch.float64, device="cuda")
     mu_fn = lambda lib_, s_: lib_.set_mu(s_.n_electrons, tol_n=TOL_N)   # noqa: E731
 
@@ -358,17 +371,18 @@ def combination(nolsm, predictor, system, parity=True, steps=2, evals=3):
         return float((2 * d ** 3 * np.interp(d, pn[0], pn[1])).sum()) if pn is not None else None
 
     out = {"p_table": None if pn is None else {"n": [int(pn[0][0]), int(pn[0][-1])], "points": len(pn[0]),
-                                               "source": "paper_2205_12182_gb300/weights/pn_gb300.json"}}
+                                               "source": "paper_2205_12182_gb300/weights/pn_gb300.json",
+                                               "estimates": "Table II columns use this table for every row"}}
     base_est = None
-    for name, crit in crits:
+    for name, crit, tab in crits:
         t0 = time.perf_counter()
-        s, r = (system, None) if crit is None else \
-            nolsm.combine_blocks(system, crit, pn if crit == nolsm.COMBINE_PERFORMANCE else None)
+        s, r = (system, None) if crit is None else nolsm.combine_blocks(system, crit, tab)
         plan_s = time.perf_counter() - t0
         lib = nolsm.Nolsm(precision=nolsm.PREC_MIXED_FP16, bounds=nolsm.BOUNDS_LEARNED)
         lib.set_predictor(predictor)
         solve(lib, s, mu_fn, d_dev, "device")
         torch.cuda.synchronize()
+        lib.phase_times(reset=True)
         dims = np.array([nolsm.nolsm_block_info(lib.ctx, b)[0] for b in range(s.n_blocks)], np.int64)
         if r is not None:
             assert np.array_equal(dims, r["dim"]), "combined dimensions disagree with the built index sets"
@@ -381,7 +395,7 @@ def combination(nolsm, predictor, system, parity=True, steps=2, evals=3):
             mu, n, mu_steps, e = solve(lib, s, mu_fn, d_dev, "device")
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t1) / steps
-        lib.phase_times(reset=True)
+        stage = {k: round(v / steps, 3) for k, v in lib.phase_times(reset=True).items()}
         fp = 0.0
         for _ in range(evals):
             st = lib.sign_batch(mu)
@@ -389,19 +403,22 @@ def combination(nolsm, predictor, system, parity=True, steps=2, evals=3):
         prod_ms = lib.phase_times(reset=True)["products"] / evals
         row = {"submatrices": int(len(dims)), "smallest": int(dims.min()), "largest": int(dims.max()),
                "average_dim": float(dims.mean()), "gflop_per_multiplication": flops / 1e9,
+               "histogram_128": {int(k * 128): int(c) for k, c in enumerate(np.bincount(dims // 128)) if c},
                "estimated_tflops": flops / est / 1e12 if est else None,
                "estimated_speedup": base_est / est if est else None,
                "plan_seconds": plan_s,
                "measured": {"value": WORKLOAD["atoms"] / dt, "unit": "atoms/s", "ms_per_step": dt * 1e3,
                             "mu_steps": mu_steps, "ns_iters_avg": st["iters_avg"],
                             "products_ms_per_sign_evaluation": prod_ms,
+                            "products_ms_per_average_iteration": prod_ms / st["iters_avg"],
+                            "stage_ms_per_step": stage,
                             "products_tflops_paper_convention": fp / evals / (prod_ms * 1e-3) / 1e12}}
-        if parity and crit is not None:
-            row["parity"] = parity_sample(s, lib.density().cpu().numpy(), mu, n_blocks=2)
+        if checks is not None and crit is not None:
+            checks["combination." + name] = (s, lib.density().cpu().numpy(), mu, 2)
         out[name] = row
         lib.close()
     base = out["none"]["measured"]
-    for name, _ in crits[1:]:
+    for name, _, _ in crits[1:]:
         m = out[name]["measured"]
         m["speedup_full_step"] = base["ms_per_step"] / m["ms_per_step"]
         m["speedup_products"] = base["products_ms_per_sign_evaluation"] / m["products_ms_per_sign_evaluation"]
@@ -520,6 +537,11 @@ def parity_sample(system, d, mu, n_blocks=8):
     ref = o.density(mu)
     own = np.isin(system.col, np.concatenate([system.block_cols(int(b)) for b in sample]))
     return {"blocks": int(n_blocks), "max_abs_dD": float(np.abs(d[own] - ref[own]).max())}
+
+
+def parity_checks(checks):
+    """The oracle on sampled blocks of every recorded run (system, D, mu, blocks), at the run's mu."""
+    return {key: parity_sample(*args) for key, args in checks.items()}
 
 
 # ------------------------------------------------------------------------------------ oracle

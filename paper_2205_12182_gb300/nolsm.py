@@ -330,6 +330,8 @@ def nolsm_combine_blocks(n, row_ptr, col, blk_ptr, blk_cols, extra_ptr=None, ext
 
 
 PN_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "pn_gb300.json")
+# the same measurement with the whole step's device time in the numerator (measure_pn --what step)
+PN_STEP_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "pn_step_gb300.json")
 
 
 def load_pn_table(path: str = PN_TABLE):
