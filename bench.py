@@ -255,6 +255,17 @@ def run_ours(args):
         line["combination"] = combination(nolsm, predictor, system, checks if want else None)
     if not args.no_large and world == 1:
         line["largest_blocks"] = large_blocks(nolsm, predictor, pk, checks if want else None)
+    if not args.no_globule and world == 1:
+        from synth import atom_blocks, make_config
+        g = make_config(3)
+        line["globule"] = combination(nolsm, predictor, g, checks if want else None, tag="globule", combine=False)
+        line["globule"]["workload"] = (f"protein-like globule, {g.n_atoms} atoms ({g.n_basis} basis functions), "
+                                       f"{g.n_blocks} blocks of 10-200 atoms, 8 A neighbourhood")
+        ga = atom_blocks(g)
+        line["combination_globule"] = combination(nolsm, predictor, ga, checks if want else None,
+                                                  tag="combination_globule")
+        line["combination_globule"]["workload"] = (f"the same globule, one block per atom ({ga.n_blocks} blocks) "
+                                                   "before combination, 8 A neighbourhood")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the cpu_baseline leg: the oracle timed on the host cores, then the parity spot checks
         line["cpu_baseline"] = cpu_baseline(system, seconds=args.cpu_seconds)
@@ -264,7 +275,8 @@ def run_ours(args):
             elif key == "largest_blocks":
                 line["largest_blocks"]["parity"] = res
             else:
-                line["combination"][key.split(".", 1)[1]]["parity"] = res
+                section, name = key.split(".", 1)
+                line[section][name]["parity"] = res
     lib.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -343,7 +355,7 @@ def large_blocks(nolsm, predictor, pk, checks=None, steps=2, evals=3):
     return out
 
 
-def combination(nolsm, predictor, system, checks=None, steps=2, evals=3):
+def combination(nolsm, predictor, system, checks=None, steps=2, evals=3, tag="combination", combine=True):
     """Submatrix combination (Section III-B-1, Table II) on the benchmark system: no combination,
     Eq. 9 and Eq. 10 with the committed p(n) table.  Per criterion: the planning time on the host,
     the submatrix statistics of Table II (count, smallest, largest, average dimension, flops of one
@@ -357,11 +369,13 @@ def combination(nolsm, predictor, system, checks=None, steps=2, evals=3):
         except OSError:
             return None
     pn, pn_step = table(nolsm.PN_TABLE), table(nolsm.PN_STEP_TABLE)
-    crits = [("none", None, None), ("eq9_cubic", nolsm.COMBINE_CUBIC, None)]
-    if pn is not None:
-        crits.append(("eq10_performance", nolsm.COMBINE_PERFORMANCE, pn))
-    if pn_step is not None:       # Eq. 10's rule with the whole step's measured time per flop
-        crits.append(("eq10_full_step_time", nolsm.COMBINE_PERFORMANCE, pn_step))
+    crits = [("none", None, None)]
+    if combine:
+        crits.append(("eq9_cubic", nolsm.COMBINE_CUBIC, None))
+        if pn is not None:
+            crits.append(("eq10_performance", nolsm.COMBINE_PERFORMANCE, pn))
+        if pn_step is not None:       # Eq. 10's rule with the whole step's measured time per flop
+            crits.append(("eq10_full_step_time", nolsm.COMBINE_PERFORMANCE, pn_step))
     d_dev = torch.empty(system.nnz, dtype=torch.float64, device="cuda")
     mu_fn = lambda lib_, s_: lib_.set_mu(s_.n_electrons, tol_n=TOL_N)   # noqa: E731
 
@@ -407,14 +421,14 @@ def combination(nolsm, predictor, system, checks=None, steps=2, evals=3):
                "estimated_tflops": flops / est / 1e12 if est else None,
                "estimated_speedup": base_est / est if est else None,
                "plan_seconds": plan_s,
-               "measured": {"value": WORKLOAD["atoms"] / dt, "unit": "atoms/s", "ms_per_step": dt * 1e3,
+               "measured": {"value": system.n_atoms / dt, "unit": "atoms/s", "ms_per_step": dt * 1e3,
                             "mu_steps": mu_steps, "ns_iters_avg": st["iters_avg"],
                             "products_ms_per_sign_evaluation": prod_ms,
                             "products_ms_per_average_iteration": prod_ms / st["iters_avg"],
                             "stage_ms_per_step": stage,
                             "products_tflops_paper_convention": fp / evals / (prod_ms * 1e-3) / 1e12}}
-        if checks is not None and crit is not None:
-            checks["combination." + name] = (s, lib.density().cpu().numpy(), mu, 2)
+        if checks is not None:
+            checks[tag + "." + name] = (s, lib.density().cpu().numpy(), mu, 2)
         out[name] = row
         lib.close()
     base = out["none"]["measured"]
@@ -615,6 +629,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the large-block (32-molecule cluster) section")
     ap.add_argument("--no-combination", action="store_true", help="skip the submatrix-combination section")
+    ap.add_argument("--no-globule", action="store_true", help="skip the protein-like globule section")
     ap.add_argument("--side", type=int, default=16,
                     help="molecules per box edge (16: the 4,096-molecule workload; smaller boxes for profiling)")
     args = ap.parse_args()

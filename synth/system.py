@@ -363,6 +363,173 @@ def dimer_system(a: float, b: float, s: float) -> System:
                   2.0, np.array([0, 1, 2], np.int32), np.array([0, 1], np.int32))
 
 
+def _chain_walk(rng: np.random.Generator, n: int, centre: np.ndarray, radius: float, bond: float = 1.5,
+                min_dist: float = 1.2, tries: int = 50) -> np.ndarray:
+    """Self-avoiding random walk of n atoms, steps of `bond` A in uniform directions, kept inside a
+    sphere and at least `min_dist` from every atom but its predecessor.  A step that fails `tries`
+    times ends the chain and a new one starts at a free random point of the sphere."""
+    pos = np.zeros((n, 3))
+    cells: dict = {}
+
+    def key(p):
+        return tuple(np.floor(p / min_dist).astype(np.int64))
+
+    def free(p, pred):
+        if np.linalg.norm(p - centre) > radius:
+            return False
+        k = key(p)
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dz in (-1, 0, 1):
+                    for j in cells.get((k[0] + dx, k[1] + dy, k[2] + dz), ()):
+                        if j != pred and np.sum((pos[j] - p) ** 2) < min_dist * min_dist:
+                            return False
+        return True
+
+    def restart():
+        for _ in range(100000):
+            v = rng.normal(size=3)
+            p = centre + v / np.linalg.norm(v) * radius * rng.random() ** (1.0 / 3.0)
+            if free(p, -1):
+                return p
+        raise RuntimeError("globule is full")
+
+    pos[0] = centre
+    cells.setdefault(key(pos[0]), []).append(0)
+    for i in range(1, n):
+        for _ in range(tries):
+            v = rng.normal(size=3)
+            p = pos[i - 1] + bond * v / np.linalg.norm(v)
+            if free(p, i - 1):
+                break
+        else:
+            p = restart()
+        pos[i] = p
+        cells.setdefault(key(p), []).append(i)
+    return pos
+
+
+def _kmeans_groups(rng: np.random.Generator, points: np.ndarray, k: int, weight: int, cap: int) -> list:
+    """Groups of point indices: k-means (k-means++ seeding, seeded), then every group whose
+    weight * size exceeds `cap` split in two along its longest extent until none does."""
+    from scipy.cluster.vq import kmeans2
+    _, label = kmeans2(points, k, minit="++", seed=rng, iter=20)
+    out, todo = [], [np.flatnonzero(label == g) for g in range(k)]
+    while todo:
+        g = todo.pop()
+        if g.size == 0:
+            continue
+        if g.size * weight <= cap:
+            out.append(g)
+            continue
+        ext = points[g].max(0) - points[g].min(0)
+        ax = int(np.argmax(ext))
+        order = g[np.argsort(points[g, ax], kind="stable")]
+        todo += [order[: g.size // 2], order[g.size // 2:]]
+    return sorted(out, key=lambda g: int(g.min()))
+
+
+def protein_globule(seed: int, n_protein: int = 12000, n_water: int = 6000, box: float = 100.0,
+                    radius: float = 40.0, neighbourhood: float | None = 8.0, blocks: str = "clusters",
+                    name: str | None = None) -> System:
+    """A protein-like globule in water: a self-avoiding random-walk chain of n_protein C/N/O/H/S atoms
+    (bond 1.5 A, non-bonded atoms >= 1.2 A apart, inside a sphere of `radius` at the box centre;
+    element fractions H .49, C .31, N .09, O .10, S .01) and n_water waters outside it (O at least
+    2.8 A from every other O -- at 2.5 A some molecules find no orientation free of clashes -- and
+    2.5 A from every chain atom, random orientation) in a periodic box.
+
+    Blocks (blocks="clusters"): the chain atoms k-means-clustered into groups of about 120 atoms,
+    the waters (whole molecules) into groups of about 10, groups above 200 atoms split;
+    blocks="atoms": one block per atom (the starting point of a submatrix combination).  Own
+    columns are the blocks' basis functions; the index set of a block adds, to the pattern rule,
+    every atom within `neighbourhood` of one of its atoms (minimum image).
+
+    Electron count: the invented minimal-basis model has no gap at the valence count (the p and H
+    levels form one band around -0.45 Ha), so N_e = 2 per heavy atom fills the band of heavy-atom s
+    levels below the largest gap near it (about 0.1 Ha, near -0.6 Ha).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    centre = np.full(3, box / 2)
+    chain = _chain_walk(rng, n_protein, centre, radius)
+    chain_el = rng.choice(np.array([H, C, N, O, S]), size=n_protein, p=[0.49, 0.31, 0.09, 0.10, 0.01])
+    # waters by random sequential addition outside the globule
+    near_chain = cKDTree(chain)
+    o_pos = np.zeros((n_water, 3))
+    cells: dict = {}
+    n_cell = int(box // 2.8)                 # periodic cell grid, cells at least 2.8 A wide
+    got = 0
+    while got < n_water:
+        cand = rng.random((4096, 3)) * box
+        ok = (np.linalg.norm(cand - centre, axis=1) > radius) & (near_chain.query(cand)[0] >= 2.5)
+        for p in cand[ok]:
+            k = tuple(np.floor(p / box * n_cell).astype(np.int64) % n_cell)
+            clash = False
+            for dx in (-1, 0, 1):
+                for dy in (-1, 0, 1):
+                    for dz in (-1, 0, 1):
+                        nk = ((k[0] + dx) % n_cell, (k[1] + dy) % n_cell, (k[2] + dz) % n_cell)
+                        for j in cells.get(nk, ()):
+                            d = o_pos[j] - p
+                            d -= box * np.round(d / box)
+                            if d @ d < 2.8 * 2.8:
+                                clash = True
+            if clash:
+                continue
+            o_pos[got] = p
+            cells.setdefault(k, []).append(got)
+            got += 1
+            if got == n_water:
+                break
+    waters = _place_waters(rng, o_pos, box)
+    coords = np.concatenate([chain, waters])
+    element = np.concatenate([chain_el, np.tile(np.array([O, H, H]), n_water)])
+    bf_ptr, row_ptr, col, h, s = build_matrices(coords, element, box, rng)
+    groups = _kmeans_groups(rng, chain, max(1, round(n_protein / 120)), 1, 200)
+    groups += [n_protein + 3 * g[:, None] + np.arange(3)[None, :]
+               for g in _kmeans_groups(rng, o_pos, max(1, round(n_water / 10)), 3, 200)]
+    if blocks == "atoms":
+        groups = [np.array([a]) for a in range(coords.shape[0])]
+    elif blocks != "clusters":
+        raise ValueError(blocks)
+    blk_ptr, blk_cols, ep, ei = _atom_group_blocks(coords, box, bf_ptr, groups, neighbourhood)
+    n_e = 2.0 * float((element != H).sum())
+    return System(name or f"globule{coords.shape[0]}", box, coords, element, bf_ptr, row_ptr, col, h, s, n_e,
+                  blk_ptr, blk_cols, ep, ei)
+
+
+def _atom_group_blocks(coords, box, bf_ptr, groups, neighbourhood):
+    """Column blocks of atom groups: own columns = the group's basis functions; with a
+    neighbourhood, the extra list = the basis functions of every atom within it of a group atom."""
+    tree = cKDTree(np.mod(coords, box), boxsize=box)
+    cols, ptr, extra, eptr = [], [0], [], [0]
+    for g in groups:
+        atoms = np.sort(np.asarray(g).reshape(-1))
+        c = np.concatenate([np.arange(bf_ptr[a], bf_ptr[a + 1]) for a in atoms])
+        cols.append(c)
+        ptr.append(ptr[-1] + c.size)
+        if neighbourhood is not None:
+            near = tree.query_ball_point(np.mod(coords[atoms], box), r=neighbourhood)
+            at = np.unique(np.concatenate([np.asarray(v, dtype=np.int64) for v in near]))
+            e = np.concatenate([np.arange(bf_ptr[a], bf_ptr[a + 1]) for a in at])
+            extra.append(e)
+            eptr.append(eptr[-1] + e.size)
+    ep = ei = None
+    if neighbourhood is not None:
+        ep, ei = np.array(eptr, np.int32), np.concatenate(extra).astype(np.int32)
+    return np.array(ptr, np.int32), np.concatenate(cols).astype(np.int32), ep, ei
+
+
+def atom_blocks(system: System, neighbourhood: float | None = 8.0) -> System:
+    """The same matrices with one column block per atom (and its neighbourhood list): the starting
+    point of a submatrix combination."""
+    import dataclasses
+    groups = [np.array([a]) for a in range(system.n_atoms)]
+    blk_ptr, blk_cols, ep, ei = _atom_group_blocks(system.coords, system.box, system.atom_bf_ptr, groups,
+                                                   neighbourhood)
+    return dataclasses.replace(system, name=system.name + "-atoms", blk_ptr=blk_ptr, blk_cols=blk_cols,
+                               extra_ptr=ep, extra_idx=ei)
+
+
 def dense_blocks(n: int, n_blocks: int, seed: int, noise: float = 0.1, n_unique: int | None = None) -> System:
     """n_blocks uncoupled dense blocks of dimension n (block-diagonal H0 and S, one column block
     per dense block, so every index set has exactly n entries): for timing the matrix products at
@@ -405,6 +572,8 @@ def dense_blocks(n: int, n_blocks: int, seed: int, noise: float = 0.1, n_unique:
 CONFIGS = {
     1: dict(desc="64 waters, 12.4 A box, pattern rule, 1 block/molecule", seeds=(1, 2, 3, 4, 5)),
     2: dict(desc="4,096 waters, 49.6 A box, 8 A neighbourhood, 1 block/molecule", seeds=(11, 12, 13)),
+    3: dict(desc="protein-like globule, 12,000 chain atoms in 6,000 waters (30,000 atoms), 100 A box, "
+                 "10-200-atom blocks, pattern rule", seeds=(21, 22, 23)),
     5: dict(desc="water, 32-molecule clusters with an 8 A halo (the 1,000,000-molecule system's block "
                  "shape), 13,824 molecules", seeds=(31,)),
 }
@@ -418,6 +587,8 @@ def make_config(config: int, seed: int | None = None) -> System:
         return water_box(4, seed, name=f"water64-s{seed}")
     if config == 2:
         return water_box(16, seed, neighbourhood=8.0, name=f"water4096-s{seed}")
+    if config == 3:
+        return protein_globule(seed, name=f"globule30000-s{seed}")
     if config == 5:
         return water_clusters(24, seed, name=f"waterclusters13824-s{seed}")
     raise ValueError(f"unknown config {config}")

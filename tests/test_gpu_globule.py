@@ -1,0 +1,84 @@
+"""The protein-like globule (30,000 atoms, 701 blocks of 12-485 own columns, ragged n_b ~160-2,700
+with the 8 A neighbourhood) through the GPU path, against the oracle on sampled blocks.
+
+Ragged sizes put blocks of every bin into one batch; the largest pads to n_pad >= 1,024, so the
+default schedule runs per-product launches with tiles dealt round-robin.  The bound predictor was
+trained on water boxes only: on the globule it is out of distribution, which may cost iterations
+or a restart but not accuracy.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle.nolsm import NolsmOracle  # noqa: E402
+from synth import make_config  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def nl():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2205_12182_gb300 import nolsm
+    return nolsm
+
+
+@pytest.fixture(scope="module")
+def globule():
+    return make_config(3)
+
+
+@pytest.fixture(scope="module")
+def mixed(nl, globule):
+    lib = nl.Nolsm(precision=nl.PREC_MIXED_FP16).build(globule)
+    mu, n, steps = lib.set_mu(globule.n_electrons, tol_n=1e-3)
+    dims = np.array([nl.nolsm_block_info(lib.ctx, b)[0] for b in range(globule.n_blocks)])
+    out = dict(mu=mu, n=n, d=lib.density().cpu().numpy(), e=lib.band_energy(), dims=dims)
+    lib.close()
+    return out
+
+
+@pytest.fixture(scope="module")
+def sample_oracle(globule, mixed):
+    order = np.argsort(mixed["dims"])
+    sample = np.unique([order[0], order[len(order) // 2], order[-1]])
+    o = NolsmOracle.from_system(globule, blocks=sample).prepare()
+    own = np.isin(globule.col, np.concatenate([globule.block_cols(int(b)) for b in sample]))
+    return o, own
+
+
+def test_ragged_sizes(globule, mixed):
+    d = mixed["dims"]
+    assert d.min() < 256 and d.max() > 2048 and globule.n_blocks == 701
+
+
+def test_mixed_path_parity(globule, mixed, sample_oracle):
+    o, own = sample_oracle
+    assert abs(mixed["n"] - globule.n_electrons) <= 1e-3 * globule.n_electrons
+    assert np.abs(mixed["d"][own] - o.density(mixed["mu"])[own]).max() <= 1e-3
+    assert np.isfinite(mixed["e"])
+
+
+def test_fp32_path_parity(nl, globule, mixed, sample_oracle):
+    o, own = sample_oracle
+    lib = nl.Nolsm(precision=nl.PREC_FP32).build(globule)
+    lib.sign_batch(mixed["mu"])
+    d = lib.density().cpu().numpy()
+    lib.close()
+    assert np.abs(d[own] - o.density(mixed["mu"])[own]).max() <= 1e-6
+
+
+def test_learned_bounds_out_of_distribution(nl, globule, mixed, sample_oracle):
+    import os
+    o, own = sample_oracle
+    weights = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                           "paper_2205_12182_gb300", "weights", "bounds_mlp.json")
+    lib = nl.Nolsm(precision=nl.PREC_MIXED_FP16, bounds=nl.BOUNDS_LEARNED)
+    pred = nl.BoundPredictor.load(weights)
+    lib.set_predictor(pred)
+    lib.build(globule)
+    lib.sign_batch(mixed["mu"])
+    d = lib.density().cpu().numpy()
+    lib.close()
+    assert np.abs(d[own] - o.density(mixed["mu"])[own]).max() <= 1e-3

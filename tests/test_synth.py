@@ -61,3 +61,47 @@ def test_config2_sizes():
     o = NolsmOracle.from_system(sysm)
     dims = np.array([len(o.index_set(b)) for b in range(0, 4096, 64)])
     assert 350 <= dims.min() and dims.max() <= 650
+
+
+@pytest.fixture(scope="module")
+def small_globule():
+    from synth import protein_globule
+    return protein_globule(23, n_protein=600, n_water=300, box=34.0, radius=14.0)
+
+
+def test_globule_geometry_and_blocks(small_globule):
+    from scipy.spatial import cKDTree
+    from synth.system import H
+    s = small_globule
+    n_p = 600
+    chain, box = s.coords[:n_p], s.box
+    centre = np.full(3, box / 2)
+    assert np.linalg.norm(chain - centre, axis=1).max() <= 14.0 + 1e-9
+    pairs = cKDTree(chain).query_pairs(1.2 - 1e-9, output_type="ndarray")
+    assert np.all(np.abs(pairs[:, 0] - pairs[:, 1]) == 1)           # only chain neighbours that close
+    o = s.coords[n_p::3]
+    assert np.linalg.norm(o - centre, axis=1).min() > 14.0
+    assert cKDTree(np.mod(o, box), boxsize=box).query_pairs(2.8 - 1e-9).__len__() == 0
+    assert cKDTree(chain).query(o)[0].min() >= 2.5
+    # blocks partition every basis function; at most 200 atoms each; waters kept whole
+    assert np.array_equal(np.sort(s.blk_cols), np.arange(s.n_basis))
+    atom_of = np.repeat(np.arange(s.n_atoms), np.diff(s.atom_bf_ptr))
+    for b in range(s.n_blocks):
+        atoms = np.unique(atom_of[s.block_cols(b)])
+        assert atoms.size <= 200
+        w = atoms[atoms >= n_p] - n_p
+        assert np.all(np.bincount(w // 3, minlength=1)[np.unique(w // 3)] == 3)
+    assert s.n_electrons == 2 * np.sum(s.element != H)
+
+
+def test_globule_overlap_and_gap(small_globule):
+    """Positive overlap, and a gap at N_e / 2 (2 electrons per heavy atom fill the heavy-atom s
+    band; the valence count would fall inside the p band)."""
+    s = small_globule
+    n = s.n_basis
+    h = csr_matrix(s.row_ptr, s.col, s.h, n).toarray()
+    sm = csr_matrix(s.row_ptr, s.col, s.s, n).toarray()
+    assert np.linalg.eigvalsh(sm)[0] >= 0.05
+    w = sla.eigh(h, sm, eigvals_only=True)
+    k = int(s.n_electrons // 2)
+    assert w[k] - w[k - 1] >= 0.05
