@@ -175,6 +175,10 @@ sgemm_nt_kernel(const Tile* __restrict__ tiles, const int32_t* __restrict__ n_ti
 // the nearest eigenvalue): scale 1.25 x the predicted radius, lower bound half the predicted
 // distance.  A scale below the rigorous Gershgorin one starts with one unscaled step, which maps
 // any eigenvalue in (0, sqrt 3) into (0, 1]; the Gershgorin scale stays the cap.
+// Smallest lower bound a prediction may set (out-of-distribution predictions of the distance to mu
+// have been two orders of magnitude low; at l = 1e-3 FP16 iterates then miss the 1e-3 accuracy bar).
+constexpr float kPredLowerFloor = 0.01f;
+
 __global__ void ns_state_kernel(int n_blocks, const double* __restrict__ lo, const double* __restrict__ hi,
                                 double mu, float margin, float l0, float l_floor, int scaled, int mode,
                                 const float* __restrict__ lz, const float* __restrict__ pred,
@@ -202,7 +206,11 @@ __global__ void ns_state_kernel(int n_blocks, const double* __restrict__ lo, con
     r = fmaxf(r, alpha_floor);
     if (r < alpha) { alpha = r; plain_first = true; }
     const float dist = exp10f(fminf(fmaxf(pred[3 * b + 2], -8.f), 1.f));
-    l = 0.5f * dist / alpha;
+    // A predicted bound far below the truth is an accuracy hazard, not only a cost: the first
+    // scaled step maps the top of the spectrum to about 2.6 l, where the rounding of the iterate's
+    // O(1) entries is a large relative error of those components.  Raising l above the truth only
+    // costs iterations (eigenvalues below l still grow every step, and the plain tail converges).
+    l = fmaxf(0.5f * dist / alpha, kPredLowerFloor);
   }
   NsState s;
   s.alpha = alpha;
