@@ -242,7 +242,7 @@ nolsm_status nolsm_create(nolsm_ctx** out, const nolsm_options* opt, void* cuda_
       ctx->opt.wait_budget <= 0 || ctx->opt.alpha_margin < 0 || ctx->opt.chol_precision < 0 ||
       ctx->opt.chol_precision > NOLSM_CHOL_DF64_SIMT || ctx->opt.bounds < NOLSM_BOUNDS_GERSHGORIN ||
       ctx->opt.bounds > NOLSM_BOUNDS_LEARNED || ctx->opt.lanczos_steps < 1 || ctx->opt.lanczos_steps > 64 ||
-      ctx->opt.schedule < NOLSM_SCHEDULE_PERSISTENT || ctx->opt.schedule > NOLSM_SCHEDULE_AUTO ||
+      ctx->opt.schedule < NOLSM_SCHEDULE_PERSISTENT || ctx->opt.schedule > NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED ||
       ctx->opt.refine_path < NOLSM_REFINE_TENSOR || ctx->opt.refine_path > NOLSM_REFINE_SIMT) {
     delete ctx;
     return NOLSM_EINVAL;
@@ -564,7 +564,8 @@ cudaError_t gemm_timed(nolsm_ctx* ctx, bool mixed, int phase, double mu) {
   }
   cudaError_t e = cudaEventRecord(ctx->gemm_ev[2 * k], ctx->stream);
   if (e != cudaSuccess) return e;
-  e = phase == 0 ? launch_ns_pair(ctx, mu) : mixed ? launch_gemm_tc(ctx, phase) : launch_gemm_f32(ctx, phase);
+  e = phase == 0 ? launch_ns_pair(ctx, mu, ctx->pair_interleaved) : mixed ? launch_gemm_tc(ctx, phase)
+                                                                     : launch_gemm_f32(ctx, phase);
   if (e != cudaSuccess) return e;
   ctx->gemm_ev_used = k + 1;
   ctx->n_launches += 1;
@@ -606,7 +607,10 @@ nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out) 
   int max_pad = 0;
   for (const auto& bd : ctx->h_blocks) max_pad = std::max(max_pad, bd.n_pad);
   const bool persistent = mixed && (ctx->opt.schedule == NOLSM_SCHEDULE_PERSISTENT ||
+                                    ctx->opt.schedule == NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED ||
                                     (ctx->opt.schedule == NOLSM_SCHEDULE_AUTO && max_pad < 1024));
+  ctx->pair_interleaved = ctx->opt.schedule == NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED ||
+                          (ctx->opt.schedule == NOLSM_SCHEDULE_AUTO && ctx->n_blocks >= 2 * ctx->num_sms);
   CK(launch_ns_init(ctx, mu, hk, mode, mode == NOLSM_BOUNDS_LANCZOS ? ctx->d_lz : nullptr, pred, !persistent));
   ctx->n_launches += persistent ? 1 : 2;
   const int tile_n = mixed ? tc_tile_n() : kTile;

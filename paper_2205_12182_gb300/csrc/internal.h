@@ -88,6 +88,7 @@ struct nolsm_ctx {
   int device = 0;
   int num_sms = 0;
   int pair_clusters = 0;        // resident 2-CTA clusters of the persistent product kernel
+  bool pair_interleaved = false;  // the persistent kernel takes two blocks per cluster
   void* d_cg_tmaps = nullptr;   // tensor maps of the congruence kernel (FP32 pools, per bin)
   size_t cg_tmap_cap = 0;
   bool cong_simt = false;       // congruence on the SIMT FP32 products (tests compare both)
@@ -249,7 +250,7 @@ cudaError_t launch_band_energy(nolsm_ctx* ctx);
 // sign_tc.cu (tcgen05 path)
 cudaError_t tc_prepare(nolsm_ctx* ctx);
 cudaError_t launch_gemm_tc(nolsm_ctx* ctx, int phase);
-cudaError_t launch_ns_pair(nolsm_ctx* ctx, double mu);
+cudaError_t launch_ns_pair(nolsm_ctx* ctx, double mu, bool interleaved);
 cudaError_t launch_congruence_tc(nolsm_ctx* ctx, float* t1);
 cudaError_t launch_slab_tc(nolsm_ctx* ctx);
 cudaError_t oz_prepare(nolsm_ctx* ctx);                        // items and tensor maps of the updates

@@ -892,6 +892,320 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PAIR_THREADS, 1) ns_
   cluster_sync_all();
 }
 
+// The persistent schedule with two blocks per cluster (NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED).
+// ns_pair_kernel passes a cluster barrier after every product of its one block: the tail of the
+// product (last epilogue, completion of its tensor stores, the skew between the two CTAs) and the
+// ramp of the next one leave the tensor pipe idle.  Here a cluster holds two blocks (slots) and
+// runs, per round, the phase-1 products of both, one barrier, the checks of both, the phase-2
+// products of both and one barrier, so each barrier covers two products and the second product's
+// loads and MMAs overlap the first one's tail.  Blocks are independent, so the arithmetic of every
+// block is that of ns_pair_kernel.  A slot whose block converges, fails or finds the queue empty is
+// refilled at the end of the round (its claim published before the round's second barrier); the
+// restart of a diverged block refills its X_0 before that barrier.  Every branch around a cluster
+// barrier depends only on values both CTAs read after a barrier, so both pass the same sequence.
+struct Pair2Ctl {
+  int block[2];                 // claimed block per slot (rank 0 writes it into both CTAs)
+  int n_local[2];               // tiles of each product held by this CTA, per slot
+  float rsq[2][2];              // ||T - I||_F^2 partial per slot and round parity
+  int abort_pub[2];             // this CTA's abort flag as published for the round, by parity
+  PairTile tiles[2][PAIR_MAX_TILES];
+};
+constexpr int PAIR2_SMEM = 1024 + PAIR_TAB_OFF + (int)sizeof(Pair2Ctl);
+static_assert(PAIR2_SMEM <= 227 * 1024, "shared memory of the interleaved persistent kernel");
+
+template <typename T>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PAIR_THREADS, 1) ns_pair2_kernel(const __grid_constant__ PairParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* stage_base = smem;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + PAIR_BAR_OFF);
+  uint64_t* full_bar = bars;                             // [PAIR_STAGES]
+  uint64_t* empty_bar = bars + PAIR_STAGES;              // [PAIR_STAGES]
+  uint64_t* tfull_bar = bars + 2 * PAIR_STAGES;          // [2]
+  uint64_t* tempty_bar = bars + 2 * PAIR_STAGES + 2;     // [2]
+  uint64_t* drain_bar = bars + 2 * PAIR_STAGES + 4;      // [1]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * PAIR_STAGES + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  Pair2Ctl* ctl = reinterpret_cast<Pair2Ctl*>(smem + PAIR_TAB_OFF);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  Pair2Ctl* ctl0 = cluster_peer(ctl, 0u);
+  Pair2Ctl* ctl1 = cluster_peer(ctl, 1u);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < PAIR_STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+    for (int a = 0; a < 2; ++a) { mbar_init(&tfull_bar[a], 1); mbar_init(&tempty_bar[a], 32 * PAIR_EPI_WARPS); }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    for (int k = 0; k < 2; ++k) ctl->rsq[k][0] = ctl->rsq[k][1] = 0.f;
+    ctl->abort_pub[0] = ctl->abort_pub[1] = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  cluster_sync_all();   // both CTAs initialised before either touches the other's shared memory
+  const uint32_t tmem_base = *tmem_slot;
+  const long long budget = p.budget;
+  const long long drain_budget = budget > (1LL << 22) ? budget : (1LL << 22);
+  const int q = warp & 3;
+
+  // ring state of each role, carried across products, slots and blocks
+  int ps = 0;
+  uint32_t pph = 0, armed = 0, arm_parity = 0;
+  int ms = 0;
+  uint32_t mph = 0, mtph[2] = {0u, 0u};
+  int macc = 0;
+  uint32_t etph[2] = {0u, 0u};
+  int eacc = 0;
+  int ebuf = 0;
+  int round = 0;
+
+  // one product of slot k: phase 1 T = X X^T -> B, phase 2 X+ = X B^T (as in ns_pair_kernel)
+  auto product = [&](int k, const BlockDesc& bd, const NsState& s, int phase, int par) {
+    const int ld = bd.n_pad;
+    const int n_local = ctl->n_local[k];
+    const PairTile* tiles = ctl->tiles[k];
+    if (warp == 0) {
+      if (lane == 0) {
+        const CUtensorMap* ma = p.tmaps + bd.bin * kMapsPerBin + s.cur;
+        const CUtensorMap* mb = (phase == 1) ? ma : p.tmaps + bd.bin * kMapsPerBin + 2;
+        const int rowbase = bd.pos * ld;
+        bool ok = true;
+        for (int i = 0; i < n_local && ok; ++i) {
+          const PairTile t = tiles[i];
+          const uint32_t bytes = A_BYTES + t.tn * TK * 2;
+          for (int k0 = 0; k0 < ld; k0 += TK) {
+            if (!mbar_wait(&empty_bar[ps], pph ^ 1u, budget, abort_flag)) { ok = false; break; }
+            mbar_expect_tx(&full_bar[ps], bytes);
+            uint8_t* a_dst = stage_base + ps * STAGE_BYTES;
+            uint8_t* b_dst = a_dst + A_BYTES;
+            tma_load_2d(a_dst, ma, &full_bar[ps], k0, rowbase + t.m0);
+            for (int h = 0; h < t.tn; h += TM) tma_load_2d(b_dst + h * TK * 2, mb, &full_bar[ps], k0, rowbase + t.n0 + h);
+            armed |= 1u << ps;
+            arm_parity = (arm_parity & ~(1u << ps)) | (pph << ps);
+            if (++ps == PAIR_STAGES) { ps = 0; pph ^= 1u; }
+          }
+        }
+        if (!ok) {
+          set_error(p.flags, NOLSM_ETIMEOUT);
+          *abort_flag = 1;
+        }
+      }
+    } else if (warp == 1) {
+      if (lane == 0) {
+        bool ok = true;
+        for (int i = 0; i < n_local && ok; ++i) {
+          const PairTile t = tiles[i];
+          const uint32_t idesc = make_idesc(Pack<T>::fmt, TM, t.tn);
+          if (!mbar_wait(&tempty_bar[macc], mtph[macc] ^ 1u, budget, abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t d_tmem = tmem_base + (uint32_t)(macc * TN);
+          for (int k0 = 0; k0 < ld; k0 += TK) {
+            if (!mbar_wait(&full_bar[ms], mph, budget, abort_flag)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t a_addr = smem_u32(stage_base + ms * STAGE_BYTES);
+            const uint64_t adesc = sw128_desc(a_addr);
+            const uint64_t bdesc = sw128_desc(a_addr + A_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < TK / 16; ++kk)
+              umma_f16(d_tmem, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), idesc, (k0 | kk) != 0);
+            umma_commit(&empty_bar[ms]);
+            if (++ms == PAIR_STAGES) { ms = 0; mph ^= 1u; }
+          }
+          if (!ok) break;
+          umma_commit(&tfull_bar[macc]);
+          mtph[macc] ^= 1u;
+          macc ^= 1;
+        }
+        if (!ok) {
+          set_error(p.flags, NOLSM_ETIMEOUT);
+          *abort_flag = 1;
+        }
+      }
+    } else {
+      T* out = reinterpret_cast<T*>(phase == 1 ? p.bbuf : (s.cur ? p.x0 : p.x1)) + bd.off_mat;
+      const CUtensorMap* smap = p.tmaps + bd.bin * kMapsPerBin + 3 + (phase == 1 ? 2 : (s.cur ^ 1));
+      const float c1 = 1.5f * s.a, c3 = 0.5f * s.a * s.a * s.a;
+      float rsq = 0.f;
+      for (int i = 0; i < n_local; ++i) {
+        const PairTile t = tiles[i];
+        // the outcome must be the same in all lanes: the tensor-memory loads below are warp-collective
+        if (!__all_sync(0xffffffffu, mbar_wait(&tfull_bar[eacc], etph[eacc], budget, abort_flag))) {
+          set_error(p.flags, NOLSM_ETIMEOUT);
+          *abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        // warps 2..5 take the left half of the tile's columns, warps 6..9 the right half
+        const int hw = t.tn / 2, h0 = ((warp - 2) / 4) * hw;
+        rsq += epi_tile<T, PAIR_NBUF, 32>(tmem_base + (uint32_t)(eacc * TN + h0), q, lane, out, ld, t.m0, t.n0 + h0, hw,
+                                      phase, c1, c3, smap, bd.pos * ld,
+                                      smem + PAIR_EPI_OFF + (warp - 2) * PAIR_NBUF * EPI_BUF_BYTES, ebuf);
+        tc_fence_before();
+        mbar_arrive(&tempty_bar[eacc]);
+        etph[eacc] ^= 1u;
+        eacc ^= 1;
+      }
+      if (phase == 1) {
+        for (int o = 16; o; o >>= 1) rsq += __shfl_xor_sync(0xffffffffu, rsq, o);
+        if (lane == 0) atomicAdd(&ctl->rsq[k][par], rsq);
+      }
+      if (lane == 0) bulk_wait0();           // this product's tensor stores are complete
+      __syncwarp();
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
+  };
+
+  int b[2] = {0, 0};
+  bool live[2] = {false, false};
+  BlockDesc bd[2];
+  NsState s[2];
+  // rank 0 claims the next block for slot k and writes it into both CTAs (read after a barrier)
+  auto claim = [&](int k) {
+    if (rank == 0 && threadIdx.x == 0) {
+      const int nb = atomicAdd(&p.flags->queue, 1);
+      ctl0->block[k] = nb;
+      ctl1->block[k] = nb;
+    }
+  };
+  // after a barrier that published ctl->block[k]: the slot's block, tile table and X_0 (all threads)
+  auto start = [&](int k) {
+    b[k] = ctl->block[k];
+    live[k] = b[k] < p.n_blocks;
+    if (!live[k]) return;
+    bd[k] = p.blocks[b[k]];
+    s[k] = p.st[b[k]];
+    if (threadIdx.x == 0) {
+      const int m = pair_tiles(bd[k].n_pad, rank, ctl->tiles[k]);
+      ctl->n_local[k] = m < 0 ? 0 : m;
+      if (m < 0) {
+        set_error(p.flags, NOLSM_EINVAL);
+        *abort_flag = 1;
+      }
+    }
+    pair_fill<T, PAIR_THREADS>(bd[k], p.a0, s[k].alpha, p.mu, reinterpret_cast<T*>(p.x0), rank);
+  };
+
+  claim(0);
+  claim(1);
+  cluster_sync_all();
+  start(0);
+  start(1);
+  __syncthreads();
+  cluster_sync_all();
+  while (live[0] || live[1]) {
+    const int par = round & 1;
+    for (int k = 0; k < 2; ++k)
+      if (live[k]) product(k, bd[k], s[k], 1, par);
+    if (threadIdx.x == 0) ctl->abort_pub[par] = *abort_flag;
+    cluster_sync_all();
+    const int aborted = ctl0->abort_pub[par] | ctl1->abort_pub[par];
+    float rsum[2];
+    for (int k = 0; k < 2; ++k) rsum[k] = ctl0->rsq[k][par] + ctl1->rsq[k][par];
+    if (threadIdx.x == 0) ctl->rsq[0][par ^ 1] = ctl->rsq[1][par ^ 1] = 0.f;   // last read one round ago
+    round += 1;
+    if (aborted) {
+      for (int k = 0; k < 2; ++k)
+        if (live[k] && rank == 0 && threadIdx.x == 0) p.st[b[k]] = s[k];
+      break;
+    }
+    bool go[2] = {false, false}, done[2] = {false, false};
+    for (int k = 0; k < 2; ++k) {
+      if (!live[k]) continue;
+      NsState& sk = s[k];
+      const BlockDesc& bk = bd[k];
+      const float res = sqrtf(rsum[k]);
+      if (p.detect_divergence && sk.iters >= 1 && sk.restarts == 0 &&
+          (!isfinite(res) || res > 1.5f * sqrtf((float)bk.n_pad))) {
+        // the scale was too small: restart from the Gershgorin scale (once per block); X_0 is
+        // refilled now and read after the round's second barrier
+        sk.restarts += 1;
+        sk.alpha = (float)(fmax(fabs(p.hi[b[k]] - p.mu), fabs(p.mu - p.lo[b[k]])) * (1.0 + p.margin));
+        sk.l = p.scaled ? fminf(p.l0, 1.f) : 1.f;   // p.l0 carries the format's floor
+        sk.a = cc_scale(sk.l);
+        sk.res = FLT_MAX;
+        sk.res_prev = FLT_MAX;
+        sk.cur = 0;
+        sk.grow = 0;
+        sk.status = kActive;
+        pair_fill<T, PAIR_THREADS>(bk, p.a0, sk.alpha, p.mu, reinterpret_cast<T*>(p.x0), rank);
+        continue;
+      }
+      if (!isfinite(res)) {
+        sk.status = kFailed;
+        sk.res = res;
+        if (rank == 0 && threadIdx.x == 0) set_error(p.flags, NOLSM_ENONFINITE);
+        done[k] = true;
+        continue;
+      }
+      sk.res_prev = sk.res;
+      sk.res = res;
+      const bool plain = sk.l >= 1.f;
+      if (res <= p.tol[b[k]]) { sk.status = kConverged; done[k] = true; continue; }
+      if (plain && sk.iters >= 2 && res < 0.25f && res > 0.5f * sk.res_prev) {
+        sk.status = kConverged;
+        done[k] = true;
+        continue;
+      }
+      if (sk.iters >= p.max_iter) {
+        sk.status = kFailed;
+        if (rank == 0 && threadIdx.x == 0) set_error(p.flags, NOLSM_ENOCONV);
+        done[k] = true;
+        continue;
+      }
+      go[k] = true;
+    }
+    for (int k = 0; k < 2; ++k)
+      if (done[k]) {
+        if (rank == 0 && threadIdx.x == 0) p.st[b[k]] = s[k];
+        claim(k);
+      }
+    for (int k = 0; k < 2; ++k)
+      if (go[k]) product(k, bd[k], s[k], 2, par);
+    __syncthreads();      // restart refills complete in this CTA before the barrier publishes them
+    cluster_sync_all();
+    for (int k = 0; k < 2; ++k)
+      if (go[k]) {
+        s[k].cur ^= 1;
+        s[k].iters += 1;
+        s[k].l = cc_next(s[k].l, s[k].a);
+        s[k].a = cc_scale(s[k].l);
+      }
+    if (done[0] || done[1]) {
+      for (int k = 0; k < 2; ++k)
+        if (done[k]) start(k);
+      __syncthreads();
+      cluster_sync_all();
+    }
+  }
+
+  // teardown: every copy and product issued here lands before shared and tensor memory go away
+  if (warp == 0 && lane == 0) {
+    volatile int never = 0;
+    for (int st = 0; st < PAIR_STAGES; ++st)
+      if (armed & (1u << st)) mbar_wait(&full_bar[st], (arm_parity >> st) & 1u, drain_budget, &never);
+  } else if (warp == 1 && lane == 0) {
+    umma_commit(drain_bar);
+    volatile int never = 0;
+    mbar_wait(drain_bar, 0, drain_budget, &never);
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+  }
+  cluster_sync_all();
+}
+
 // ---------------------------------------------------------------------------------------------
 // The refinement steps on the own-column slab and the block traces (Eq. 4, Eq. 8) on the tensor
 // cores.  With V_0 = W = L^-1[:, C_b] and X the final iterate in its FP16/BF16 storage, one step of
@@ -1824,6 +2138,10 @@ cudaError_t tc_prepare(nolsm_ctx* ctx) {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(ns_pair_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(ns_pair2_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR2_SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(ns_pair2_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR2_SMEM);
+    if (e != cudaSuccess) return e;
     attr_done = true;
   }
   return cudaSuccess;
@@ -2094,8 +2412,9 @@ cudaError_t launch_slab_tc(nolsm_ctx* ctx) {
   return cudaSuccess;
 }
 
-// The persistent schedule: one launch for the whole iteration of every block (see ns_pair_kernel).
-cudaError_t launch_ns_pair(nolsm_ctx* ctx, double mu) {
+// The persistent schedule: one launch for the whole iteration of every block (see ns_pair_kernel;
+// interleaved: two blocks per cluster, see ns_pair2_kernel).
+cudaError_t launch_ns_pair(nolsm_ctx* ctx, double mu, bool interleaved) {
   PairParams p;
   p.blocks = ctx->d_blocks;
   p.st = ctx->d_state;
@@ -2128,6 +2447,15 @@ cudaError_t launch_ns_pair(nolsm_ctx* ctx, double mu) {
                          : cudaOccupancyMaxActiveClusters(&n, ns_pair_kernel<__half>, &cfg);
     if (e != cudaSuccess) return e;
     ctx->pair_clusters = n > 0 ? n : ctx->num_sms / 2;
+  }
+  if (interleaved) {
+    // two slots per cluster: enough clusters for every block to start in the first round
+    const int clusters = std::max(1, std::min(ctx->pair_clusters, (ctx->n_blocks + 1) / 2));
+    if (bf16)
+      ns_pair2_kernel<__nv_bfloat16><<<2 * clusters, PAIR_THREADS, PAIR2_SMEM, ctx->stream>>>(p);
+    else
+      ns_pair2_kernel<__half><<<2 * clusters, PAIR_THREADS, PAIR2_SMEM, ctx->stream>>>(p);
+    return cudaGetLastError();
   }
   const int clusters = std::max(1, std::min(ctx->pair_clusters, ctx->n_blocks));
   if (bf16)

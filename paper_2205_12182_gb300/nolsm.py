@@ -21,7 +21,7 @@ MEM_DEVICE, MEM_HOST = 0, 1
 PREC_FP32, PREC_MIXED_FP16, PREC_MIXED_BF16 = 1, 2, 3
 BOUNDS_GERSHGORIN, BOUNDS_LANCZOS, BOUNDS_LEARNED = 0, 1, 2
 CHOL_FP64, CHOL_FP32, CHOL_FP64_INV64, CHOL_DF64, CHOL_DF64_SIMT = 0, 1, 2, 3, 4
-SCHEDULE_PERSISTENT, SCHEDULE_PER_PRODUCT, SCHEDULE_AUTO = 0, 1, 2
+SCHEDULE_PERSISTENT, SCHEDULE_PER_PRODUCT, SCHEDULE_AUTO, SCHEDULE_PERSISTENT_INTERLEAVED = 0, 1, 2, 3
 REFINE_TENSOR, REFINE_SIMT = 0, 1
 COMBINE_CUBIC, COMBINE_PERFORMANCE = 0, 1
 

@@ -82,12 +82,14 @@ def test_bad_pattern_rejected(nl, sys1):
     assert e.value.status == nl.EINVAL
 
 
-@pytest.mark.parametrize("stage", ["build", "sign"])
+@pytest.mark.parametrize("stage", ["build", "sign", "sign_interleaved"])
 def test_device_wait_budget_runs_out(nl, sys1, stage):
     """A one-poll budget on the tensor-core kernels' mbarrier waits (the congruence in the build, the
-    Newton-Schulz products in the sign evaluation): the kernel records ETIMEOUT, drains its own copies
-    and products, frees tensor memory and returns; the context recovers."""
-    lib = nl.Nolsm(precision=nl.PREC_MIXED_FP16, wait_budget=1 if stage == "build" else 1 << 22)
+    Newton-Schulz products in the sign evaluation, one or two blocks per cluster): the kernel records
+    ETIMEOUT, drains its own copies and products, frees tensor memory and returns; the context
+    recovers."""
+    kw = {"schedule": nl.SCHEDULE_PERSISTENT_INTERLEAVED} if stage == "sign_interleaved" else {}
+    lib = nl.Nolsm(precision=nl.PREC_MIXED_FP16, wait_budget=1 if stage == "build" else 1 << 22, **kw)
     with pytest.raises(nl.NolsmError) as e:
         lib.build(sys1)
         lib.set_wait_budget(1)

@@ -179,3 +179,51 @@ def test_persistent_and_per_product_schedules_agree(nl, sys1, orc1, mu1, bounds)
     assert np.abs(da - db).max() <= 1e-4
     assert np.abs(da - orc1.density(mu1)).max() <= 1e-3
     assert sa["n_electrons"] == pytest.approx(sb["n_electrons"], rel=1e-5)
+
+
+def _run(nl, system, mu, predictor=None, **kw):
+    lib = make(nl, system, nl.PREC_MIXED_FP16, **kw)
+    if predictor is not None:
+        lib.set_predictor(predictor)
+    st = lib.sign_batch(mu)
+    out = (st, lib.iters(), lib.density().cpu().numpy())
+    lib.close()
+    return out
+
+
+@pytest.mark.parametrize("bounds", [0, 2])
+def test_interleaved_persistent_kernel_is_identical(nl, bounds):
+    """Two blocks per cluster (products alternating, one cluster barrier per pair) against one block
+    per cluster: every block runs the same arithmetic, so iteration counts and densities agree bit for
+    bit.  1,000 waters with the 8 A neighbourhood (more than two blocks per SM: AUTO takes the
+    interleaved kernel)."""
+    import os
+    from synth import water_box
+    s = water_box(10, seed=7, neighbourhood=8.0)
+    pred = None
+    if bounds == nl.BOUNDS_LEARNED:
+        w = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                         "paper_2205_12182_gb300", "weights", "bounds_mlp.json")
+        pred = nl.BoundPredictor.load(w)
+    ref = _run(nl, s, -0.45, pred, bounds=bounds, schedule=nl.SCHEDULE_PERSISTENT)
+    for sched in (nl.SCHEDULE_PERSISTENT_INTERLEAVED, nl.SCHEDULE_AUTO):
+        st, it, d = _run(nl, s, -0.45, pred, bounds=bounds, schedule=sched)
+        np.testing.assert_array_equal(it, ref[1])
+        np.testing.assert_array_equal(d, ref[2])
+        assert st["n_electrons"] == ref[0]["n_electrons"]
+
+
+@pytest.mark.parametrize("n_blocks", [1, 7, 64])
+def test_interleaved_kernel_restarts_and_odd_counts(nl, sys1, mu1, n_blocks):
+    """The interleaved kernel on 1, 7 and 64 blocks of the 64-water box (odd counts: a slot finds the
+    queue empty while the other still iterates) with learned-mode state from a predictor whose radius
+    is far too small (scales at their floor): the same iterations, restarts and density as one block
+    per cluster."""
+    s = sys1.subset_blocks(np.arange(n_blocks))
+    norm = np.concatenate([np.zeros(32), np.ones(32), [mu1 - 0.05, mu1 + 0.05, -2.0], np.ones(3)]).astype(np.float32)
+    pred = nl.BoundPredictor(np.zeros(nl.N_PARAMS, np.float32), norm)
+    ref = _run(nl, s, mu1, pred, bounds=nl.BOUNDS_LEARNED, schedule=nl.SCHEDULE_PERSISTENT)
+    st, it, d = _run(nl, s, mu1, pred, bounds=nl.BOUNDS_LEARNED, schedule=nl.SCHEDULE_PERSISTENT_INTERLEAVED)
+    np.testing.assert_array_equal(it, ref[1])
+    np.testing.assert_array_equal(d, ref[2])
+    assert st["n_restarted"] == ref[0]["n_restarted"]
