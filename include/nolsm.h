@@ -102,13 +102,12 @@ typedef enum nolsm_schedule {
                                      iteration driven from the host; from n_pad 1024 on, the tiles
                                      are dealt round-robin so that all SMs share a few blocks'
                                      operands in L2 */
-  NOLSM_SCHEDULE_AUTO = 2,        /* while every block has n_pad < 1024 (the iterates of the blocks
-                                     in flight stay in L2): PERSISTENT_INTERLEAVED when there are at
-                                     least two blocks per SM, PERSISTENT otherwise; PER_PRODUCT from
-                                     n_pad 1024 on */
+  NOLSM_SCHEDULE_AUTO = 2,        /* PERSISTENT while every block has n_pad < 1024 (the iterates of
+                                     the blocks in flight stay in L2), PER_PRODUCT otherwise */
   NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED = 3  /* PERSISTENT with two blocks per cluster: the products
-                                     of both alternate and share one cluster barrier per pair, so
-                                     one block's product overlaps the other's tail (same arithmetic) */
+                                     of both alternate and share one cluster barrier per pair (same
+                                     arithmetic).  Twice the iterates in flight: at n_pad 512 they no
+                                     longer fit in L2, and it is slower than PERSISTENT there */
 } nolsm_schedule;
 
 /* Where the refinement steps on the own-column slab run on the mixed-precision paths (the FP32 path

@@ -609,8 +609,7 @@ nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out) 
   const bool persistent = mixed && (ctx->opt.schedule == NOLSM_SCHEDULE_PERSISTENT ||
                                     ctx->opt.schedule == NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED ||
                                     (ctx->opt.schedule == NOLSM_SCHEDULE_AUTO && max_pad < 1024));
-  ctx->pair_interleaved = ctx->opt.schedule == NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED ||
-                          (ctx->opt.schedule == NOLSM_SCHEDULE_AUTO && ctx->n_blocks >= 2 * ctx->num_sms);
+  ctx->pair_interleaved = ctx->opt.schedule == NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED;
   CK(launch_ns_init(ctx, mu, hk, mode, mode == NOLSM_BOUNDS_LANCZOS ? ctx->d_lz : nullptr, pred, !persistent));
   ctx->n_launches += persistent ? 1 : 2;
   const int tile_n = mixed ? tc_tile_n() : kTile;

@@ -195,8 +195,7 @@ def _run(nl, system, mu, predictor=None, **kw):
 def test_interleaved_persistent_kernel_is_identical(nl, bounds):
     """Two blocks per cluster (products alternating, one cluster barrier per pair) against one block
     per cluster: every block runs the same arithmetic, so iteration counts and densities agree bit for
-    bit.  1,000 waters with the 8 A neighbourhood (more than two blocks per SM: AUTO takes the
-    interleaved kernel)."""
+    bit.  1,000 waters with the 8 A neighbourhood (more than two blocks per SM)."""
     import os
     from synth import water_box
     s = water_box(10, seed=7, neighbourhood=8.0)
@@ -206,7 +205,7 @@ def test_interleaved_persistent_kernel_is_identical(nl, bounds):
                          "paper_2205_12182_gb300", "weights", "bounds_mlp.json")
         pred = nl.BoundPredictor.load(w)
     ref = _run(nl, s, -0.45, pred, bounds=bounds, schedule=nl.SCHEDULE_PERSISTENT)
-    for sched in (nl.SCHEDULE_PERSISTENT_INTERLEAVED, nl.SCHEDULE_AUTO):
+    for sched in (nl.SCHEDULE_PERSISTENT_INTERLEAVED,):
         st, it, d = _run(nl, s, -0.45, pred, bounds=bounds, schedule=sched)
         np.testing.assert_array_equal(it, ref[1])
         np.testing.assert_array_equal(d, ref[2])
