@@ -37,8 +37,10 @@ struct CostModel {
   double time_per_flop(int64_t n) const {
     if (n <= dim[0]) return time[0];
     if (n >= dim[n_points - 1]) return time[n_points - 1];
-    int32_t k = 0;
-    while (dim[k + 1] < n) ++k;
+    // the first size at or above n closes the interval (binary search over the ascending sizes)
+    const int32_t k = (int32_t)(std::lower_bound(dim + 1, dim + n_points, n,
+                                                 [](int32_t d, int64_t v) { return (int64_t)d < v; }) -
+                                (dim + 1));
     const int64_t n0 = dim[k], n1 = dim[k + 1];
     const double p0 = time[k], p1 = time[k + 1];
     const double frac = (double)(n - n0) / (double)(n1 - n0);
@@ -71,17 +73,6 @@ struct Later {
     return x.b > y.b;
   }
 };
-
-int64_t overlap(const std::vector<int32_t>& x, const std::vector<int32_t>& y) {
-  int64_t n = 0;
-  size_t i = 0, j = 0;
-  while (i < x.size() && j < y.size()) {
-    if (x[i] < y[j]) ++i;
-    else if (y[j] < x[i]) ++j;
-    else { ++n; ++i; ++j; }
-  }
-  return n;
-}
 
 void sorted_insert(std::vector<int32_t>& v, int32_t x) {
   auto it = std::lower_bound(v.begin(), v.end(), x);
@@ -179,17 +170,36 @@ extern "C" nolsm_status nolsm_combine_blocks(const nolsm_csr* pattern, int32_t n
     std::vector<std::vector<int32_t>> members((size_t)n_blocks);
     for (int32_t b = 0; b < n_blocks; ++b) members[b].push_back(b);
     std::priority_queue<Candidate, std::vector<Candidate>, Later> heap;
-    auto consider = [&](int32_t x, int32_t y) {
-      const int32_t a = std::min(x, y), b = std::max(x, y);
+    // |I_a n I_x| for the neighbours x of one block a: a's rows are stamped once, then each
+    // neighbour's rows are counted (O(n_a + sum n_x) instead of a merge per pair)
+    std::vector<uint32_t> stamp((size_t)N, 0u);
+    uint32_t epoch = 0;
+    auto stamp_rows = [&](int32_t a) {
+      if (++epoch == 0) {                        // wrapped: clear and start again
+        std::fill(stamp.begin(), stamp.end(), 0u);
+        epoch = 1;
+      }
+      for (int32_t r : idx[a]) stamp[r] = epoch;
+    };
+    auto stamped = [&](int32_t x) {
+      int64_t c = 0;
+      for (int32_t r : idx[x]) c += stamp[r] == epoch;
+      return c;
+    };
+    // the saving of combining a (rows stamped) with x, pushed when it pays
+    auto consider = [&](int32_t a_st, int32_t x) {
+      const int32_t a = std::min(a_st, x), b = std::max(a_st, x);
       const int64_t na = (int64_t)idx[a].size(), nb = (int64_t)idx[b].size();
-      const int64_t nm = na + nb - overlap(idx[a], idx[b]);
+      const int64_t nm = na + nb - stamped(x);
       if (nm > max_dim) return;
       const double g = model.saving(na, nb, nm);
       if (g > 0.0) heap.push(Candidate{g, a, b, version[a], version[b]});
     };
-    for (int32_t a = 0; a < n_blocks; ++a)
+    for (int32_t a = 0; a < n_blocks; ++a) {
+      stamp_rows(a);
       for (int32_t b : nbr[a])
         if (b > a) consider(a, b);
+    }
     std::vector<int32_t> merged;
     while (!heap.empty()) {
       const Candidate c = heap.top();
@@ -214,6 +224,7 @@ extern "C" nolsm_status nolsm_combine_blocks(const nolsm_csr* pattern, int32_t n
       std::vector<int32_t>().swap(nbr[b]);
       alive[b] = 0;
       ++version[a];
+      stamp_rows(a);
       for (int32_t x : nbr[a]) consider(a, x);
     }
 
