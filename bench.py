@@ -255,6 +255,8 @@ def run_ours(args):
         line["combination"] = combination(nolsm, predictor, system, checks if want else None)
     if not args.no_large and world == 1:
         line["largest_blocks"] = large_blocks(nolsm, predictor, pk, checks if want else None)
+    if not args.no_md and world == 1:
+        line["md_steps"] = md_steps(nolsm, predictor, system, checks if want else None)
     if not args.no_globule and world == 1:
         from synth import atom_blocks, make_config
         g = make_config(3)
@@ -444,6 +446,61 @@ def combination(nolsm, predictor, system, checks=None, steps=2, evals=3, tag="co
         m = out[name]["measured"]
         m["speedup_full_step"] = base["ms_per_step"] / m["ms_per_step"]
         m["speedup_products"] = base["products_ms_per_sign_evaluation"] / m["products_ms_per_sign_evaluation"]
+    return out
+
+
+def md_steps(nolsm, predictor, system, checks=None, steps=4):
+    """MD-like steps on the benchmark system: two geometries (the second with every atom moved by
+    N(0, 0.02^2) A per axis) alternate, so each step's kept bounds come from the other geometry.
+    A timed step: build, mu search, density and band energy, and for the kept-bounds run also the
+    Lanczos runs that keep the bounds for the next step (nolsm_keep_bounds, 64 steps).  Bounds:
+    learned (the headline's) against kept from the previous geometry with the mu search bracketed
+    by +-0.02 Ha around the previous mu."""
+    import torch
+    from synth import displaced
+    geo = [system, displaced(system, 0.02, seed=1234)]
+    d_dev = torch.empty(max(g.nnz for g in geo), dtype=torch.float64, device="cuda")
+    out = {"workload": "water-4096 and a displaced copy (0.02 A per axis), alternating", "steps": steps}
+    for name in ("learned", "kept"):
+        if name == "learned":
+            lib = nolsm.Nolsm(precision=nolsm.PREC_MIXED_FP16, bounds=nolsm.BOUNDS_LEARNED)
+            lib.set_predictor(predictor)
+        else:
+            lib = nolsm.Nolsm(precision=nolsm.PREC_MIXED_FP16, bounds=nolsm.BOUNDS_GIVEN)
+        mu_prev = None
+
+        def one(k):
+            nonlocal mu_prev
+            g = geo[k % 2]
+            lib.build(g)
+            if name == "kept" and mu_prev is not None:
+                mu, n, ms = lib.set_mu(g.n_electrons, mu_lo=mu_prev - 0.02, mu_hi=mu_prev + 0.02, tol_n=TOL_N)
+            else:
+                mu, n, ms = lib.set_mu(g.n_electrons, tol_n=TOL_N)
+            lib.density(d_dev[:g.nnz])
+            lib.band_energy()
+            if name == "kept":
+                lib.keep_bounds(64)
+            mu_prev = mu
+            return mu, ms
+
+        one(0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mus = []
+        for k in range(1, steps + 1):
+            mu, ms = one(k)
+            mus.append(ms)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / steps
+        st = lib.sign_batch(mu)
+        out[name] = {"value": system.n_atoms / dt, "unit": "atoms/s", "ms_per_step": dt * 1e3,
+                     "mu_steps": mus, "ns_iters_avg_last_geometry": st["iters_avg"],
+                     "restarted": st["n_restarted"]}
+        if checks is not None and name == "kept":
+            g = geo[steps % 2]
+            checks["md_steps." + name] = (g, lib.density().cpu().numpy(), mu, 2)
+        lib.close()
     return out
 
 
@@ -638,6 +695,7 @@ def main():
     ap.add_argument("--no-large", action="store_true", help="skip the large-block (32-molecule cluster) section")
     ap.add_argument("--no-combination", action="store_true", help="skip the submatrix-combination section")
     ap.add_argument("--no-globule", action="store_true", help="skip the protein-like globule section")
+    ap.add_argument("--no-md", action="store_true", help="skip the MD-like steps with kept bounds")
     ap.add_argument("--side", type=int, default=16,
                     help="molecules per box edge (16: the 4,096-molecule workload; smaller boxes for profiling)")
     args = ap.parse_args()

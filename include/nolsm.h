@@ -73,9 +73,14 @@ typedef enum nolsm_bounds {
   NOLSM_BOUNDS_GERSHGORIN = 0,  /* Gershgorin discs of A0 = L^-1 T(H0) L^-T */
   NOLSM_BOUNDS_LANCZOS = 1,     /* Lanczos extreme Ritz values of A0 widened by the last Lanczos
                                    coefficient; the first iteration is unscaled (see nolsm_sign_batch) */
-  NOLSM_BOUNDS_LEARNED = 2      /* network predictions (nolsm_set_predictor) for the scale and the lower
+  NOLSM_BOUNDS_LEARNED = 2,     /* network predictions (nolsm_set_predictor) for the scale and the lower
                                    bound; capped by Gershgorin, first iteration unscaled, a block whose
                                    residual blows up restarts from the Gershgorin scale */
+  NOLSM_BOUNDS_GIVEN = 3        /* per-block (lambda_min, lambda_max, log10 distance of mu to the
+                                   spectrum) kept from an earlier geometry with the same blocks
+                                   (nolsm_keep_bounds: the next MD or SCF step) or set by the caller
+                                   (nolsm_set_block_bounds), used as the network's predictions are
+                                   (same caps, floors and restart); Gershgorin while none are held */
 } nolsm_bounds;
 
 typedef enum nolsm_chol_precision {
@@ -336,6 +341,21 @@ nolsm_status nolsm_mlp_adam(nolsm_mlp* mlp, float lr, float beta1, float beta2, 
  * FP32 accumulation. */
 nolsm_status nolsm_mlp_predict(const nolsm_mlp* mlp, const float* x, int32_t n, float* y);
 void nolsm_mlp_destroy(nolsm_mlp* mlp);
+
+/* Bounds for the next geometry (the paper reruns the density step every MD time step, Section I;
+ * one geometry's spectra are a close guess for the next): Lanczos (steps <= 64, full
+ * reorthogonalisation) on A0 of the current build and on |A0 - mu| = X (A0 - mu) with the last sign
+ * evaluation's X and mu; keeps per block (smallest and largest Ritz value of A0, log10 of the
+ * smallest Ritz value of |A0 - mu|) in the context, where they survive the next
+ * nolsm_build_submatrices and serve NOLSM_BOUNDS_GIVEN while that build has as many blocks.
+ * Synchronises.  Errors: EINVAL (not built, steps out of range), ENOTBUILT (no sign evaluation
+ * yet), ENOMEM, ECUDA. */
+nolsm_status nolsm_keep_bounds(nolsm_ctx* ctx, int32_t steps);
+
+/* Set the NOLSM_BOUNDS_GIVEN bounds directly: n_blocks x 3 float32 (lambda_min, lambda_max, log10
+ * distance of mu to the spectrum) per block of the current build, in host or device memory
+ * (nolsm_memory), copied.  Synchronises.  Errors: EINVAL (not built, null), ENOMEM, ECUDA. */
+nolsm_status nolsm_set_block_bounds(nolsm_ctx* ctx, const float* bounds, int32_t memory);
 
 /* Use mlp (kept by the caller, alive while ctx uses it) for NOLSM_BOUNDS_LEARNED; NULL detaches. */
 nolsm_status nolsm_set_predictor(nolsm_ctx* ctx, const nolsm_mlp* mlp);

@@ -155,6 +155,8 @@ void release_pools(nolsm_ctx* ctx) {
   dfree(ctx->d_feat); ctx->d_feat = nullptr;
   dfree(ctx->d_pred); ctx->d_pred = nullptr;
   dfree(ctx->d_lz); ctx->d_lz = nullptr;
+  dfree(ctx->d_lz1); ctx->d_lz1 = nullptr;
+  dfree(ctx->d_given); ctx->d_given = nullptr;
   dfree(ctx->d_lz_basis); ctx->d_lz_basis = nullptr;
   dfree(ctx->d_t1); ctx->d_t1 = nullptr;
   ctx->caps.clear();
@@ -241,7 +243,7 @@ nolsm_status nolsm_create(nolsm_ctx** out, const nolsm_options* opt, void* cuda_
       ctx->opt.refine_iters < 0 || ctx->opt.refine_iters > 3 || !(ctx->opt.spin_factor > 0) ||
       ctx->opt.wait_budget <= 0 || ctx->opt.alpha_margin < 0 || ctx->opt.chol_precision < 0 ||
       ctx->opt.chol_precision > NOLSM_CHOL_DF64_SIMT || ctx->opt.bounds < NOLSM_BOUNDS_GERSHGORIN ||
-      ctx->opt.bounds > NOLSM_BOUNDS_LEARNED || ctx->opt.lanczos_steps < 1 || ctx->opt.lanczos_steps > 64 ||
+      ctx->opt.bounds > NOLSM_BOUNDS_GIVEN || ctx->opt.lanczos_steps < 1 || ctx->opt.lanczos_steps > 64 ||
       ctx->opt.schedule < NOLSM_SCHEDULE_PERSISTENT || ctx->opt.schedule > NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED ||
       ctx->opt.refine_path < NOLSM_REFINE_TENSOR || ctx->opt.refine_path > NOLSM_REFINE_SIMT) {
     delete ctx;
@@ -593,9 +595,17 @@ nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out) 
   const int hk = half_kind(ctx);
   CK(cudaEventRecord(ctx->ev0, ctx->stream));
   CK(phase_mark(ctx, NOLSM_PHASE_SIGN_SETUP));
-  const int mode = ctx->opt.bounds;
+  int mode = ctx->opt.bounds;
   const float* pred = nullptr;
-  if (mode == NOLSM_BOUNDS_LEARNED) {
+  if (mode == NOLSM_BOUNDS_GIVEN) {
+    // kept or given bounds enter as the network's predictions do; none yet: Gershgorin
+    if (ctx->given_blocks == ctx->n_blocks) {
+      pred = ctx->d_given;
+      mode = NOLSM_BOUNDS_LEARNED;
+    } else {
+      mode = NOLSM_BOUNDS_GERSHGORIN;
+    }
+  } else if (mode == NOLSM_BOUNDS_LEARNED) {
     if (!ctx->predictor) return fail(ctx, NOLSM_EINVAL, "learned bounds need nolsm_set_predictor");
     CK(dalloc(ctx, &ctx->d_feat, (size_t)32 * ctx->n_blocks));
     CK(dalloc(ctx, &ctx->d_pred, (size_t)3 * ctx->n_blocks));
@@ -816,6 +826,38 @@ nolsm_status nolsm_block_lanczos(nolsm_ctx* ctx, int32_t steps, int32_t op, floa
   if (op == 1 && !ctx->have_sign) return NOLSM_ENOTBUILT;
   if (ctx->sticky != NOLSM_OK) return ctx->sticky;
   return run_lanczos(ctx, ctx->last_mu, op, steps, out);
+}
+
+nolsm_status nolsm_keep_bounds(nolsm_ctx* ctx, int32_t steps) {
+  if (!ctx || !ctx->built || steps < 1 || steps > 64) return NOLSM_EINVAL;
+  if (!ctx->have_sign) return NOLSM_ENOTBUILT;
+  if (ctx->sticky != NOLSM_OK) return ctx->sticky;
+  // |A0 - mu| (needs the current X) into the first half of d_lz1, A0 into the second half (d_lz,
+  // which the Lanczos bounds mode reads, stays as it is)
+  CK(dalloc(ctx, &ctx->d_lz1, (size_t)8 * ctx->n_blocks));
+  CK(dalloc(ctx, &ctx->d_given, (size_t)3 * ctx->n_blocks));
+  float* lz_abs = ctx->d_lz1;
+  float* lz_a0 = ctx->d_lz1 + (size_t)4 * ctx->n_blocks;
+  nolsm_status st = run_lanczos(ctx, ctx->last_mu, 1, steps, lz_abs);
+  if (st != NOLSM_OK) return st;
+  st = run_lanczos(ctx, ctx->last_mu, 0, steps, lz_a0);
+  if (st != NOLSM_OK) return st;
+  CK(launch_given_from_lanczos(ctx, lz_a0, lz_abs, ctx->d_given));
+  ctx->n_launches += 1;
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->given_blocks = ctx->n_blocks;
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_set_block_bounds(nolsm_ctx* ctx, const float* bounds, int32_t memory) {
+  if (!ctx || !ctx->built || !bounds || (memory != NOLSM_MEM_HOST && memory != NOLSM_MEM_DEVICE)) return NOLSM_EINVAL;
+  if (ctx->sticky != NOLSM_OK) return ctx->sticky;
+  CK(dalloc(ctx, &ctx->d_given, (size_t)3 * ctx->n_blocks));
+  CK(cudaMemcpyAsync(ctx->d_given, bounds, sizeof(float) * 3 * ctx->n_blocks,
+                     memory == NOLSM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->given_blocks = ctx->n_blocks;
+  return NOLSM_OK;
 }
 
 nolsm_status nolsm_set_predictor(nolsm_ctx* ctx, const nolsm_mlp* mlp) {

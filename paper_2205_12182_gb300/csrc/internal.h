@@ -198,6 +198,9 @@ struct nolsm_ctx {
   float* d_feat = nullptr;      // n_blocks x 32 features
   float* d_pred = nullptr;      // n_blocks x 3 predictions
   float* d_lz = nullptr;        // n_blocks x 4 Lanczos results on A0
+  float* d_lz1 = nullptr;       // n_blocks x 4 Lanczos results on |A0 - mu| (kept bounds)
+  float* d_given = nullptr;     // n_blocks x 3 bounds kept from an earlier geometry or set by the caller
+  int32_t given_blocks = 0;     // blocks d_given describes (0: none)
   float* d_lz_basis = nullptr;  // Lanczos basis scratch
   float* d_rowd = nullptr;      // diag(A0) per row (stride kMaxDim per block)
   float* d_rowr = nullptr;      // Gershgorin radius per row (same layout)
@@ -264,6 +267,7 @@ constexpr int kSlabWide = 192;    // columns of a wide refinement piece
 cudaError_t launch_features(nolsm_ctx* ctx, double mu, float* feat);
 cudaError_t launch_features_mu(nolsm_ctx* ctx, double mu, float* feat);
 cudaError_t launch_lanczos(nolsm_ctx* ctx, double mu, int op, int k, float* basis, int64_t stride, float* out);
+cudaError_t launch_given_from_lanczos(nolsm_ctx* ctx, const float* lz_a0, const float* lz_abs, float* given);
 cudaError_t mlp_predict_on(const struct nolsm_mlp* m, cudaStream_t s, const float* x, int n, float* y);
 
 // index.cu

@@ -490,6 +490,22 @@ cudaError_t launch_features_mu(nolsm_ctx* ctx, double mu, float* feat) {
   return cudaGetLastError();
 }
 
+// Kept bounds for the next geometry: (smallest and largest Ritz value of A0, log10 of the smallest
+// Ritz value of |A0 - mu|) per block, the layout of the network's predictions.
+__global__ void given_from_lanczos_kernel(int n_blocks, const float* __restrict__ lz_a0, const float* __restrict__ lz_abs,
+                                          float* __restrict__ given) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_blocks) return;
+  given[3 * b + 0] = lz_a0[4 * b + 0];
+  given[3 * b + 1] = lz_a0[4 * b + 1];
+  given[3 * b + 2] = log10f(fmaxf(lz_abs[4 * b + 0], 1e-8f));
+}
+
+cudaError_t launch_given_from_lanczos(nolsm_ctx* ctx, const float* lz_a0, const float* lz_abs, float* given) {
+  given_from_lanczos_kernel<<<(ctx->n_blocks + 255) / 256, 256, 0, ctx->stream>>>(ctx->n_blocks, lz_a0, lz_abs, given);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_lanczos(nolsm_ctx* ctx, double mu, int op, int k, float* basis, int64_t stride, float* out) {
   int max_pad = 128;
   for (const auto& b : ctx->h_blocks) max_pad = std::max(max_pad, b.n_pad);

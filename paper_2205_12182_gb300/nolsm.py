@@ -19,7 +19,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOTPD", "ENOCONV", "EBRACKE
                 "ENONFINITE"]
 MEM_DEVICE, MEM_HOST = 0, 1
 PREC_FP32, PREC_MIXED_FP16, PREC_MIXED_BF16 = 1, 2, 3
-BOUNDS_GERSHGORIN, BOUNDS_LANCZOS, BOUNDS_LEARNED = 0, 1, 2
+BOUNDS_GERSHGORIN, BOUNDS_LANCZOS, BOUNDS_LEARNED, BOUNDS_GIVEN = 0, 1, 2, 3
 CHOL_FP64, CHOL_FP32, CHOL_FP64_INV64, CHOL_DF64, CHOL_DF64_SIMT = 0, 1, 2, 3, 4
 SCHEDULE_PERSISTENT, SCHEDULE_PER_PRODUCT, SCHEDULE_AUTO, SCHEDULE_PERSISTENT_INTERLEAVED = 0, 1, 2, 3
 REFINE_TENSOR, REFINE_SIMT = 0, 1
@@ -31,7 +31,7 @@ FUNCTIONS = ["nolsm_default_options", "nolsm_create", "nolsm_build_submatrices",
              "nolsm_band_energy_noalloc",
              "nolsm_block_features", "nolsm_block_lanczos", "nolsm_mlp_create", "nolsm_mlp_get_params",
              "nolsm_mlp_gradient", "nolsm_mlp_adam", "nolsm_mlp_predict", "nolsm_mlp_destroy", "nolsm_set_predictor",
-             "nolsm_combine_blocks", "nolsm_last_error", "nolsm_destroy"]
+             "nolsm_keep_bounds", "nolsm_set_block_bounds", "nolsm_combine_blocks", "nolsm_last_error", "nolsm_destroy"]
 
 PHASES = ("gather", "factor", "inverse", "congruence", "build_rest", "sign_setup", "products", "slab", "density",
           "energy", "factor_trsm", "factor_update")
@@ -103,6 +103,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "nolsm_mlp_predict": (i32, [P, P, i32, P]),
         "nolsm_mlp_destroy": (None, [P]),
         "nolsm_set_predictor": (i32, [P, P]),
+        "nolsm_keep_bounds": (i32, [P, i32]),
+        "nolsm_set_block_bounds": (i32, [P, P, i32]),
         "nolsm_combine_blocks": (i32, [C.POINTER(NolsmCsr), i32, P, P, P, P, i32, i32, P, P, i32, pi32, P, P, P, P, P,
                                        P, P]),
         "nolsm_last_error": (C.c_char_p, [P]),
@@ -352,6 +354,14 @@ def combine_blocks(system, criterion=COMBINE_CUBIC, pn=None, max_dim=4096):
                                extra_idx=r["extra_idx"]), r
 
 
+def nolsm_keep_bounds(ctx, steps=64):
+    _check(ctx, _lib.nolsm_keep_bounds(ctx, int(steps)))
+
+
+def nolsm_set_block_bounds(ctx, bounds, memory=MEM_DEVICE):
+    _check(ctx, _lib.nolsm_set_block_bounds(ctx, _ptr(bounds), int(memory)))
+
+
 def nolsm_last_error(ctx) -> str:
     return _lib.nolsm_last_error(ctx).decode()
 
@@ -478,6 +488,12 @@ class Nolsm:
 
     def phase_times(self, reset=False):
         return nolsm_phase_times(self.ctx, reset)
+
+    def keep_bounds(self, steps=64):
+        nolsm_keep_bounds(self.ctx, steps)
+
+    def set_block_bounds(self, bounds):
+        nolsm_set_block_bounds(self.ctx, bounds, MEM_HOST if isinstance(bounds, np.ndarray) else MEM_DEVICE)
 
     def set_wait_budget(self, budget):
         nolsm_set_wait_budget(self.ctx, budget)

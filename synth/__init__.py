@@ -6,4 +6,4 @@ the geometric neighbourhood lists.  It holds none of the method's arithmetic
 (no index-set rule, no matrix function, no trace): both the CUDA path and the
 CPU oracle take its output as plain arrays.
 """
-from .system import System, CONFIGS, make_config, water_box, water_clusters, isolated_waters, dimer_system, dense_blocks, protein_globule, atom_blocks  # noqa: F401
+from .system import System, CONFIGS, make_config, water_box, water_clusters, isolated_waters, dimer_system, dense_blocks, protein_globule, atom_blocks, displaced  # noqa: F401

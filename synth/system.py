@@ -530,6 +530,25 @@ def atom_blocks(system: System, neighbourhood: float | None = 8.0) -> System:
                                extra_ptr=ep, extra_idx=ei)
 
 
+def displaced(system: System, sigma: float, seed: int) -> System:
+    """The next geometry of a short MD-like trajectory: every atom moved by N(0, sigma^2) per axis,
+    H0 and S rebuilt on the new pattern with the same on-site energies (the diagonal of H0 is kept,
+    its noise included), the same column blocks and extra lists."""
+    import dataclasses
+    rng = np.random.Generator(np.random.PCG64(seed))
+    coords = system.coords + rng.normal(0.0, sigma, size=system.coords.shape)
+    _, row_ptr, col, h, s = build_matrices(coords, system.element, system.box, rng)
+    n = system.n_basis
+
+    def diag_pos(rp, cl):
+        rows = np.repeat(np.arange(n), np.diff(rp))
+        return np.flatnonzero(rows == cl)
+
+    h[diag_pos(row_ptr, col)] = system.h[diag_pos(system.row_ptr, system.col)]
+    return dataclasses.replace(system, name=system.name + f"+d{seed}", coords=coords, row_ptr=row_ptr, col=col,
+                               h=h, s=s)
+
+
 def dense_blocks(n: int, n_blocks: int, seed: int, noise: float = 0.1, n_unique: int | None = None) -> System:
     """n_blocks uncoupled dense blocks of dimension n (block-diagonal H0 and S, one column block
     per dense block, so every index set has exactly n entries): for timing the matrix products at
