@@ -256,7 +256,7 @@ def run_ours(args):
     if not args.no_large and world == 1:
         line["largest_blocks"] = large_blocks(nolsm, predictor, pk, checks if want else None)
     if not args.no_md and world == 1:
-        line["md_steps"] = md_steps(nolsm, predictor, system, checks if want else None)
+        line["md_steps"] = md_steps(nolsm, predictor, system, checks if want else None, keep_steps=args.keep_steps)
     if not args.no_globule and world == 1:
         from synth import atom_blocks, make_config
         g = make_config(3)
@@ -449,18 +449,19 @@ def combination(nolsm, predictor, system, checks=None, steps=2, evals=3, tag="co
     return out
 
 
-def md_steps(nolsm, predictor, system, checks=None, steps=4):
+def md_steps(nolsm, predictor, system, checks=None, steps=4, keep_steps=16):
     """MD-like steps on the benchmark system: two geometries (the second with every atom moved by
     N(0, 0.02^2) A per axis) alternate, so each step's kept bounds come from the other geometry.
     A timed step: build, mu search, density and band energy, and for the kept-bounds run also the
-    Lanczos runs that keep the bounds for the next step (nolsm_keep_bounds, 64 steps).  Bounds:
+    Lanczos runs that keep the bounds for the next step (nolsm_keep_bounds, `keep_steps` steps).  Bounds:
     learned (the headline's) against kept from the previous geometry with the mu search bracketed
     by +-0.02 Ha around the previous mu."""
     import torch
     from synth import displaced
     geo = [system, displaced(system, 0.02, seed=1234)]
     d_dev = torch.empty(max(g.nnz for g in geo), dtype=torch.float64, device="cuda")
-    out = {"workload": "water-4096 and a displaced copy (0.02 A per axis), alternating", "steps": steps}
+    out = {"workload": "water-4096 and a displaced copy (0.02 A per axis), alternating", "steps": steps,
+           "lanczos_steps_kept": keep_steps}
     for name in ("learned", "kept"):
         if name == "learned":
             lib = nolsm.Nolsm(precision=nolsm.PREC_MIXED_FP16, bounds=nolsm.BOUNDS_LEARNED)
@@ -480,7 +481,7 @@ def md_steps(nolsm, predictor, system, checks=None, steps=4):
             lib.density(d_dev[:g.nnz])
             lib.band_energy()
             if name == "kept":
-                lib.keep_bounds(64)
+                lib.keep_bounds(keep_steps)
             mu_prev = mu
             return mu, ms
 
@@ -696,6 +697,7 @@ def main():
     ap.add_argument("--no-combination", action="store_true", help="skip the submatrix-combination section")
     ap.add_argument("--no-globule", action="store_true", help="skip the protein-like globule section")
     ap.add_argument("--no-md", action="store_true", help="skip the MD-like steps with kept bounds")
+    ap.add_argument("--keep-steps", type=int, default=16, help="Lanczos steps of the kept bounds (MD-like steps)")
     ap.add_argument("--side", type=int, default=16,
                     help="molecules per box edge (16: the 4,096-molecule workload; smaller boxes for profiling)")
     args = ap.parse_args()
