@@ -105,3 +105,20 @@ def test_globule_overlap_and_gap(small_globule):
     w = sla.eigh(h, sm, eigvals_only=True)
     k = int(s.n_electrons // 2)
     assert w[k] - w[k - 1] >= 0.05
+
+
+def test_displaced_geometry_keeps_onsite_energies_and_blocks():
+    from synth import displaced
+    s = water_box(4, seed=3, neighbourhood=8.0)
+    d = displaced(s, 0.02, seed=5)
+    assert d.n_basis == s.n_basis and np.array_equal(d.blk_cols, s.blk_cols)
+    assert np.array_equal(d.extra_idx, s.extra_idx)
+    move = d.coords - s.coords
+    assert 0.005 < move.std() < 0.04
+    hs, hd = (csr_matrix(x.row_ptr, x.col, x.h, x.n_basis).toarray() for x in (s, d))
+    ss, sd = (csr_matrix(x.row_ptr, x.col, x.s, x.n_basis).toarray() for x in (s, d))
+    np.testing.assert_array_equal(np.diag(hd), np.diag(hs))
+    np.testing.assert_array_equal(hd, hd.T)
+    np.testing.assert_array_equal(sd, sd.T)
+    assert 0 < np.abs(hd - hs).max() < 0.05                  # a small step, not a new system
+    assert np.linalg.eigvalsh(sd)[0] > 0.05
