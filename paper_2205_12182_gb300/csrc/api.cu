@@ -230,6 +230,7 @@ nolsm_status nolsm_default_options(nolsm_options* opt) {
   opt->lanczos_steps = 24;
   opt->schedule = NOLSM_SCHEDULE_AUTO;
   opt->refine_path = NOLSM_REFINE_TENSOR;
+  opt->fp8_iters = 0;
   return NOLSM_OK;
 }
 
@@ -245,7 +246,8 @@ nolsm_status nolsm_create(nolsm_ctx** out, const nolsm_options* opt, void* cuda_
       ctx->opt.chol_precision > NOLSM_CHOL_DF64_SIMT || ctx->opt.bounds < NOLSM_BOUNDS_GERSHGORIN ||
       ctx->opt.bounds > NOLSM_BOUNDS_GIVEN || ctx->opt.lanczos_steps < 1 || ctx->opt.lanczos_steps > 64 ||
       ctx->opt.schedule < NOLSM_SCHEDULE_PERSISTENT || ctx->opt.schedule > NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED ||
-      ctx->opt.refine_path < NOLSM_REFINE_TENSOR || ctx->opt.refine_path > NOLSM_REFINE_SIMT) {
+      ctx->opt.refine_path < NOLSM_REFINE_TENSOR || ctx->opt.refine_path > NOLSM_REFINE_SIMT ||
+      ctx->opt.fp8_iters < 0 || ctx->opt.fp8_iters > ctx->opt.max_iter) {
     delete ctx;
     return NOLSM_EINVAL;
   }
@@ -620,6 +622,8 @@ nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out) 
                                     ctx->opt.schedule == NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED ||
                                     (ctx->opt.schedule == NOLSM_SCHEDULE_AUTO && max_pad < 1024));
   ctx->pair_interleaved = ctx->opt.schedule == NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED;
+  if (ctx->opt.fp8_iters > 0 && !persistent)
+    return fail(ctx, NOLSM_EINVAL, "fp8_iters needs a mixed-precision path on a persistent schedule");
   CK(launch_ns_init(ctx, mu, hk, mode, mode == NOLSM_BOUNDS_LANCZOS ? ctx->d_lz : nullptr, pred, !persistent));
   ctx->n_launches += persistent ? 1 : 2;
   const int tile_n = mixed ? tc_tile_n() : kTile;

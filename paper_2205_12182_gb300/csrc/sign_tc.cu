@@ -18,6 +18,7 @@
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp8.h>
 
 #include <cfloat>
 
@@ -234,7 +235,7 @@ __device__ __forceinline__ uint32_t sw64(int row, int col) {
 template <typename T, int NBUF, int LDW>
 __device__ __forceinline__ float epi_tile(uint32_t tmem_acc, int q, int lane, T* out, int ld, int m0, int n0, int tn,
                                           int phase, float c1, float c3, const CUtensorMap* smap, int rowbase,
-                                          uint8_t* stage, int& buf) {
+                                          uint8_t* stage, int& buf, bool q8 = false) {
   const int r0 = m0 + q * 32;
   const int r = r0 + lane;
   float rsq = 0.f;
@@ -259,6 +260,8 @@ __device__ __forceinline__ float epi_tile(uint32_t tmem_acc, int q, int lane, T*
           rsq = fmaf(w, e * e, rsq);
           x = c1 * d - c3 * x;
         }
+        // experiment (fp8_iters): the output rounded to an FP8 E4M3 value, stored in the iterate's format
+        if (q8) x = float(__nv_fp8_e4m3(x));
         fv[j] = x;
       }
       if (cg0 == r0) {
@@ -546,6 +549,7 @@ struct PairParams {
   int max_iter;
   int detect_divergence;
   int n_blocks;
+  int fp8_iters;                // experiment: iterations whose outputs are rounded to FP8 E4M3 values
 };
 
 struct PairTile {
@@ -779,7 +783,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PAIR_THREADS, 1) ns_
         const int hw = t.tn / 2, h0 = ((warp - 2) / 4) * hw;
         rsq += epi_tile<T, PAIR_NBUF, 32>(tmem_base + (uint32_t)(eacc * TN + h0), q, lane, out, ld, t.m0, t.n0 + h0, hw,
                                       phase, c1, c3, smap, bd.pos * ld,
-                                      smem + PAIR_EPI_OFF + (warp - 2) * PAIR_NBUF * EPI_BUF_BYTES, ebuf);
+                                      smem + PAIR_EPI_OFF + (warp - 2) * PAIR_NBUF * EPI_BUF_BYTES, ebuf,
+                                      s.iters < p.fp8_iters);
         tc_fence_before();
         mbar_arrive(&tempty_bar[eacc]);
         etph[eacc] ^= 1u;
@@ -1047,7 +1052,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PAIR_THREADS, 1) ns_
         const int hw = t.tn / 2, h0 = ((warp - 2) / 4) * hw;
         rsq += epi_tile<T, PAIR_NBUF, 32>(tmem_base + (uint32_t)(eacc * TN + h0), q, lane, out, ld, t.m0, t.n0 + h0, hw,
                                       phase, c1, c3, smap, bd.pos * ld,
-                                      smem + PAIR_EPI_OFF + (warp - 2) * PAIR_NBUF * EPI_BUF_BYTES, ebuf);
+                                      smem + PAIR_EPI_OFF + (warp - 2) * PAIR_NBUF * EPI_BUF_BYTES, ebuf,
+                                      s.iters < p.fp8_iters);
         tc_fence_before();
         mbar_arrive(&tempty_bar[eacc]);
         etph[eacc] ^= 1u;
@@ -2435,6 +2441,7 @@ cudaError_t launch_ns_pair(nolsm_ctx* ctx, double mu, bool interleaved) {
   p.max_iter = ctx->opt.max_iter;
   p.detect_divergence = ctx->opt.bounds != NOLSM_BOUNDS_GERSHGORIN;
   p.n_blocks = ctx->n_blocks;
+  p.fp8_iters = ctx->opt.fp8_iters;
   const bool bf16 = ctx->opt.precision == NOLSM_PREC_MIXED_BF16;
   if (ctx->pair_clusters <= 0) {
     cudaLaunchConfig_t cfg = {};

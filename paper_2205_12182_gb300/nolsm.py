@@ -50,7 +50,7 @@ class NolsmOptions(C.Structure):
                 ("scaled", C.c_int32), ("sign_tol", C.c_double), ("max_iter", C.c_int32),
                 ("refine_iters", C.c_int32), ("spin_factor", C.c_double), ("lower_bound", C.c_double),
                 ("alpha_margin", C.c_double), ("wait_budget", C.c_int64), ("lanczos_steps", C.c_int32),
-                ("schedule", C.c_int32), ("refine_path", C.c_int32)]
+                ("schedule", C.c_int32), ("refine_path", C.c_int32), ("fp8_iters", C.c_int32)]
 
 
 class NolsmSignStats(C.Structure):
