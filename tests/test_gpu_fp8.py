@@ -1,8 +1,10 @@
 """The FP8 experiment (survey: FP8 as a measured experiment): the first fp8_iters Newton-Schulz
 iterations round both product outputs to FP8 E4M3 values (the operand precision of an FP8 MMA,
-without its rate).  fp8_iters = 0 is the default path bit for bit; FP8 iterations run to
-convergence (finite results, same electron count to 1 %); the option needs a persistent schedule.
-The accuracy it reaches is measured against the oracle and recorded in the design notes."""
+without its rate).  fp8_iters = 0 is the default path bit for bit.  One or two FP8 iterations
+still converge (finite, electron count within 1 %) but miss the accuracy bar by two orders of
+magnitude: the rounding error a product leaves in the iterate is not removed by the later
+iterations (they converge to the sign of the perturbed iterate), so FP8's 3-bit mantissa costs
+about 0.1 in D.  The option needs a persistent schedule."""
 import numpy as np
 import pytest
 
@@ -43,12 +45,13 @@ def test_zero_fp8_iterations_is_the_default_path(nl, case):
     np.testing.assert_array_equal(d0, d1)
 
 
-@pytest.mark.parametrize("k", [2, 4])
-def test_fp8_iterations_converge(nl, case, k):
+@pytest.mark.parametrize("k", [1, 2])
+def test_fp8_iterations_converge_but_miss_the_bar(nl, case, k):
     s, o, mu = case
     st, d = run(nl, s, mu, fp8_iters=k)
     assert np.all(np.isfinite(d))
     assert st["n_electrons"] == pytest.approx(2 * o.electron_count(mu), rel=1e-2)
+    assert np.abs(d - o.density(mu)).max() > 1e-2
 
 
 def test_fp8_needs_a_persistent_schedule(nl, case):
