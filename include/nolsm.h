@@ -153,7 +153,7 @@ typedef struct nolsm_options {
   int32_t lanczos_steps;   /* Lanczos steps per block for NOLSM_BOUNDS_LANCZOS (default 24, at most 64) */
   int32_t schedule;        /* nolsm_schedule of the mixed-precision products (default AUTO) */
   int32_t refine_path;     /* nolsm_refine_path of the mixed-precision paths (default TENSOR) */
-  int32_t fp8_iters;       /* experiment (mixed paths, persistent schedules only): the first fp8_iters
+  int32_t fp8_iters;       /* experiment (mixed paths, schedule PERSISTENT or AUTO resolving to it): the first fp8_iters
                               Newton-Schulz iterations round both product outputs (B and X+) to FP8 E4M3
                               values before storing them, i.e. FP8 operands without the FP8 MMA rate
                               (default 0, at most max_iter) */

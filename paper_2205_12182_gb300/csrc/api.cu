@@ -622,8 +622,8 @@ nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out) 
                                     ctx->opt.schedule == NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED ||
                                     (ctx->opt.schedule == NOLSM_SCHEDULE_AUTO && max_pad < 1024));
   ctx->pair_interleaved = ctx->opt.schedule == NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED;
-  if (ctx->opt.fp8_iters > 0 && !persistent)
-    return fail(ctx, NOLSM_EINVAL, "fp8_iters needs a mixed-precision path on a persistent schedule");
+  if (ctx->opt.fp8_iters > 0 && (!persistent || ctx->pair_interleaved))
+    return fail(ctx, NOLSM_EINVAL, "fp8_iters needs a mixed-precision path on the persistent schedule");
   CK(launch_ns_init(ctx, mu, hk, mode, mode == NOLSM_BOUNDS_LANCZOS ? ctx->d_lz : nullptr, pred, !persistent));
   ctx->n_launches += persistent ? 1 : 2;
   const int tile_n = mixed ? tc_tile_n() : kTile;

@@ -232,10 +232,11 @@ __device__ __forceinline__ uint32_t sw64(int row, int col) {
 //   on:    entries c >= r at (r, c) and c > r also at (c, r), by plain stores.
 // Returns the lane's ||.||^2 part.  The caller waits for the tensor stores (bulk group) before the
 // results are read or the buffer goes away.
-template <typename T, int NBUF, int LDW>
+// Q8 (the FP8 experiment) rounds every output to an FP8 E4M3 value first.
+template <typename T, int NBUF, int LDW, bool Q8 = false>
 __device__ __forceinline__ float epi_tile(uint32_t tmem_acc, int q, int lane, T* out, int ld, int m0, int n0, int tn,
                                           int phase, float c1, float c3, const CUtensorMap* smap, int rowbase,
-                                          uint8_t* stage, int& buf, bool q8 = false) {
+                                          uint8_t* stage, int& buf) {
   const int r0 = m0 + q * 32;
   const int r = r0 + lane;
   float rsq = 0.f;
@@ -260,8 +261,7 @@ __device__ __forceinline__ float epi_tile(uint32_t tmem_acc, int q, int lane, T*
           rsq = fmaf(w, e * e, rsq);
           x = c1 * d - c3 * x;
         }
-        // experiment (fp8_iters): the output rounded to an FP8 E4M3 value, stored in the iterate's format
-        if (q8) x = float(__nv_fp8_e4m3(x));
+        if constexpr (Q8) x = float(__nv_fp8_e4m3(x));   // stored in the iterate's format
         fv[j] = x;
       }
       if (cg0 == r0) {
@@ -650,7 +650,9 @@ __device__ inline int pair_tiles(int ld, uint32_t rank, PairTile* out) {
   return k;
 }
 
-template <typename T>
+// Q8: the FP8 experiment's instantiation (outputs of the first p.fp8_iters iterations rounded to
+// FP8 E4M3 values); the default instantiation carries none of it.
+template <typename T, bool Q8>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PAIR_THREADS, 1) ns_pair_kernel(const __grid_constant__ PairParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -781,10 +783,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PAIR_THREADS, 1) ns_
         tc_fence_after();
         // warps 2..5 take the left half of the tile's columns, warps 6..9 the right half
         const int hw = t.tn / 2, h0 = ((warp - 2) / 4) * hw;
-        rsq += epi_tile<T, PAIR_NBUF, 32>(tmem_base + (uint32_t)(eacc * TN + h0), q, lane, out, ld, t.m0, t.n0 + h0, hw,
-                                      phase, c1, c3, smap, bd.pos * ld,
-                                      smem + PAIR_EPI_OFF + (warp - 2) * PAIR_NBUF * EPI_BUF_BYTES, ebuf,
-                                      s.iters < p.fp8_iters);
+        if constexpr (Q8) {
+          uint8_t* stg = smem + PAIR_EPI_OFF + (warp - 2) * PAIR_NBUF * EPI_BUF_BYTES;
+          if (s.iters < p.fp8_iters)   // the FP8 experiment (block-uniform)
+            rsq += epi_tile<T, PAIR_NBUF, 32, true>(tmem_base + (uint32_t)(eacc * TN + h0), q, lane, out, ld, t.m0,
+                                                    t.n0 + h0, hw, phase, c1, c3, smap, bd.pos * ld, stg, ebuf);
+          else
+            rsq += epi_tile<T, PAIR_NBUF, 32>(tmem_base + (uint32_t)(eacc * TN + h0), q, lane, out, ld, t.m0,
+                                              t.n0 + h0, hw, phase, c1, c3, smap, bd.pos * ld, stg, ebuf);
+        } else {
+          rsq += epi_tile<T, PAIR_NBUF, 32>(tmem_base + (uint32_t)(eacc * TN + h0), q, lane, out, ld, t.m0, t.n0 + h0, hw,
+                                        phase, c1, c3, smap, bd.pos * ld,
+                                        smem + PAIR_EPI_OFF + (warp - 2) * PAIR_NBUF * EPI_BUF_BYTES, ebuf);
+        }
         tc_fence_before();
         mbar_arrive(&tempty_bar[eacc]);
         etph[eacc] ^= 1u;
@@ -1052,8 +1063,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PAIR_THREADS, 1) ns_
         const int hw = t.tn / 2, h0 = ((warp - 2) / 4) * hw;
         rsq += epi_tile<T, PAIR_NBUF, 32>(tmem_base + (uint32_t)(eacc * TN + h0), q, lane, out, ld, t.m0, t.n0 + h0, hw,
                                       phase, c1, c3, smap, bd.pos * ld,
-                                      smem + PAIR_EPI_OFF + (warp - 2) * PAIR_NBUF * EPI_BUF_BYTES, ebuf,
-                                      s.iters < p.fp8_iters);
+                                      smem + PAIR_EPI_OFF + (warp - 2) * PAIR_NBUF * EPI_BUF_BYTES, ebuf);
         tc_fence_before();
         mbar_arrive(&tempty_bar[eacc]);
         etph[eacc] ^= 1u;
@@ -2140,9 +2150,15 @@ cudaError_t tc_prepare(nolsm_ctx* ctx) {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(ns_tc_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TOTAL);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(ns_pair_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM);
+    e = cudaFuncSetAttribute(ns_pair_kernel<__half, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(ns_pair_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM);
+    e = cudaFuncSetAttribute(ns_pair_kernel<__nv_bfloat16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             PAIR_SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(ns_pair_kernel<__half, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(ns_pair_kernel<__nv_bfloat16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             PAIR_SMEM);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(ns_pair2_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR2_SMEM);
     if (e != cudaSuccess) return e;
@@ -2450,8 +2466,8 @@ cudaError_t launch_ns_pair(nolsm_ctx* ctx, double mu, bool interleaved) {
     cfg.dynamicSmemBytes = PAIR_SMEM;
     cfg.stream = ctx->stream;
     int n = 0;
-    cudaError_t e = bf16 ? cudaOccupancyMaxActiveClusters(&n, ns_pair_kernel<__nv_bfloat16>, &cfg)
-                         : cudaOccupancyMaxActiveClusters(&n, ns_pair_kernel<__half>, &cfg);
+    cudaError_t e = bf16 ? cudaOccupancyMaxActiveClusters(&n, ns_pair_kernel<__nv_bfloat16, false>, &cfg)
+                         : cudaOccupancyMaxActiveClusters(&n, ns_pair_kernel<__half, false>, &cfg);
     if (e != cudaSuccess) return e;
     ctx->pair_clusters = n > 0 ? n : ctx->num_sms / 2;
   }
@@ -2465,10 +2481,15 @@ cudaError_t launch_ns_pair(nolsm_ctx* ctx, double mu, bool interleaved) {
     return cudaGetLastError();
   }
   const int clusters = std::max(1, std::min(ctx->pair_clusters, ctx->n_blocks));
-  if (bf16)
-    ns_pair_kernel<__nv_bfloat16><<<2 * clusters, PAIR_THREADS, PAIR_SMEM, ctx->stream>>>(p);
+  const bool q8 = p.fp8_iters > 0;
+  if (bf16 && q8)
+    ns_pair_kernel<__nv_bfloat16, true><<<2 * clusters, PAIR_THREADS, PAIR_SMEM, ctx->stream>>>(p);
+  else if (bf16)
+    ns_pair_kernel<__nv_bfloat16, false><<<2 * clusters, PAIR_THREADS, PAIR_SMEM, ctx->stream>>>(p);
+  else if (q8)
+    ns_pair_kernel<__half, true><<<2 * clusters, PAIR_THREADS, PAIR_SMEM, ctx->stream>>>(p);
   else
-    ns_pair_kernel<__half><<<2 * clusters, PAIR_THREADS, PAIR_SMEM, ctx->stream>>>(p);
+    ns_pair_kernel<__half, false><<<2 * clusters, PAIR_THREADS, PAIR_SMEM, ctx->stream>>>(p);
   return cudaGetLastError();
 }
 
