@@ -142,3 +142,19 @@ def test_errors_are_reported_before_any_output():
                                 nl.COMBINE_PERFORMANCE)
     with pytest.raises(nl.NolsmError):
         nl.nolsm_combine_blocks(s.n_basis, s.row_ptr, s.col, s.blk_ptr, s.blk_cols, max_dim=0)
+
+
+@pytest.mark.parametrize("reach,keep,n_blocks", [(2, 0.5, 10), (2, 1.0, 30), (6, 0.5, 30), (6, 1.0, 10)])
+@pytest.mark.parametrize("criterion", [oc.CUBIC, oc.PERFORMANCE])
+@pytest.mark.parametrize("seed", [20, 21])
+def test_same_groups_across_pattern_shapes(reach, keep, n_blocks, criterion, seed):
+    """Sparser and denser local couplings, few and many blocks, with extra lists and a cap that
+    binds: the native combination follows the reference merge for merge."""
+    row_ptr, col, blk_ptr, blk_cols, ep, ei, _ = random_instance(seed, n=96, n_blocks=n_blocks, reach=reach,
+                                                                 keep=keep, with_extra=True)
+    pn = (np.array([1, 6, 16, 40, 96], np.int32), np.array([5.0, 2.5, 1.2, 0.9, 0.85]))
+    for max_dim in (12, 40, 4096):
+        r = native((row_ptr, col, blk_ptr, blk_cols, ep, ei), criterion, pn, max_dim)
+        g, _ = oc.combine(row_ptr, col, blk_ptr, blk_cols, ep, ei, criterion, pn[0], pn[1], max_dim)
+        np.testing.assert_array_equal(r["group"], g)
+        np.testing.assert_array_equal(r["dim"], oc.combined_dims(row_ptr, col, blk_ptr, blk_cols, ep, ei, g))
