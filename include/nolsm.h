@@ -147,7 +147,8 @@ typedef struct nolsm_options {
   int32_t max_iter;        /* matrix iterations per sign evaluation (default 100) */
   int32_t refine_iters;    /* FP32 Newton-Schulz steps on the own-column slab (0..3, default 2) */
   double spin_factor;      /* electrons per orbital: N_e = spin_factor Tr(DS), E = spin_factor Tr(DH0) (default 2) */
-  double lower_bound;      /* scaled iteration: lower bound on |eig(X_0)| when bounds give none (default 1e-3) */
+  double lower_bound;      /* scaled iteration: lower bound on |eig(X_0)| when bounds give none (default 0.02;
+                              a bound far below the truth costs FP16 accuracy, one above it iterations) */
   double alpha_margin;     /* relative safety margin on the spectral radius bound (default 0.02) */
   int64_t wait_budget;     /* bound on every device-side spin wait, in polls (default 1<<22) */
   int32_t lanczos_steps;   /* Lanczos steps per block for NOLSM_BOUNDS_LANCZOS (default 24, at most 64) */

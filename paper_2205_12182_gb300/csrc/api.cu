@@ -224,7 +224,7 @@ nolsm_status nolsm_default_options(nolsm_options* opt) {
   opt->max_iter = 100;
   opt->refine_iters = 2;
   opt->spin_factor = 2.0;
-  opt->lower_bound = 1e-3;
+  opt->lower_bound = 0.02;
   opt->alpha_margin = 0.02;
   opt->wait_budget = 1LL << 22;
   opt->lanczos_steps = 24;

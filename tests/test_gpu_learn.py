@@ -147,15 +147,16 @@ def test_bad_predictions_cost_iterations_not_accuracy(nl, sys1, orc1, mu1, case)
 
 
 def test_trained_predictor_saves_iterations_on_held_out_box(nl):
-    """The committed predictor (trained on other seeds) against Gershgorin bounds on a held-out
-    1,728-molecule box: fewer iterations and bisection steps, same accuracy on sampled blocks."""
+    """The committed predictor (trained on other seeds) against Gershgorin bounds with no knowledge
+    of the gap (lower bound 1e-3) on a held-out 1,728-molecule box: fewer iterations and bisection
+    steps, same accuracy on sampled blocks."""
     import os
     from synth import water_box
     s = water_box(12, seed=201, neighbourhood=8.0)
     weights = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                            "paper_2205_12182_gb300", "weights", "bounds_mlp.json")
     pred = nl.BoundPredictor.load(weights)
-    g = nl.Nolsm(precision=nl.PREC_MIXED_FP16).build(s)
+    g = nl.Nolsm(precision=nl.PREC_MIXED_FP16, lower_bound=1e-3).build(s)
     mu_g, n_g, steps_g = g.set_mu(s.n_electrons, tol_n=1e-3)
     it_g = g.sign_batch(mu_g)["iters_avg"]
     lr = nl.Nolsm(precision=nl.PREC_MIXED_FP16, bounds=nl.BOUNDS_LEARNED).build(s)

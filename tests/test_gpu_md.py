@@ -5,7 +5,7 @@ and keeps per block (lambda_min, lambda_max, log10 distance of mu to the spectru
 geometry (every atom displaced by 0.02 A, same blocks) is built on the same context and its sign
 evaluations take those values as the scale and lower bound (NOLSM_BOUNDS_GIVEN), with mu searched
 in a bracket around the previous one.  Checked against the oracle on the new geometry, and against
-the Gershgorin bounds' iteration count.  The caller can also hand in bounds (here: the oracle's
+the iteration count of Gershgorin bounds with no knowledge of the gap (lower bound 1e-3).  The caller can also hand in bounds (here: the oracle's
 exact spectra of the 64-water box).
 """
 import numpy as np
@@ -39,7 +39,7 @@ def test_bounds_kept_for_the_next_geometry(nl):
     st = lib.sign_batch(mu1)
     d = lib.density().cpu().numpy()
     lib.close()
-    g = nl.Nolsm(precision=nl.PREC_MIXED_FP16).build(s1)
+    g = nl.Nolsm(precision=nl.PREC_MIXED_FP16, lower_bound=1e-3).build(s1)
     sg = g.sign_batch(mu1)
     g.close()
     assert st["iters_avg"] < sg["iters_avg"]
@@ -59,7 +59,7 @@ def test_bounds_given_by_the_caller(nl):
     st = lib.sign_batch(mu)
     d = lib.density().cpu().numpy()
     lib.close()
-    g = nl.Nolsm(precision=nl.PREC_MIXED_FP16).build(s)
+    g = nl.Nolsm(precision=nl.PREC_MIXED_FP16, lower_bound=1e-3).build(s)
     sg = g.sign_batch(mu)
     g.close()
     assert np.abs(d - o.density(mu)).max() <= 1e-3
