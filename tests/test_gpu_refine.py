@@ -61,7 +61,9 @@ def test_refine_paths_agree_on_molecule_blocks(nl, sys1, orc1, mu1, refine, prec
     tol = 2e-6 if prec == "fp16" else 5e-5
     assert np.abs(d - d2).max() <= tol
     assert st["n_electrons"] == pytest.approx(st2["n_electrons"], rel=tol)
-    if prec == "fp16":
+    # without a refinement step the FP16 iteration stops at ||X^2 - I||_F <= 0.05 (the stopping rule
+    # leaves the last digits to the FP32 steps), so only refined results are held to the 1e-3 bar
+    if prec == "fp16" and refine >= 1:
         assert np.abs(d - orc1.density(mu1)).max() <= 1e-3
 
 
