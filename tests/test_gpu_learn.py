@@ -90,9 +90,9 @@ def test_lanczos_extremes_and_distance(nl, sys1, orc1, mu1):
     ld = lib.lanczos(64, op=1).cpu().numpy()
     dist = np.array([np.min(np.abs(e - mu1)) for e in orc1.eps])
     # a Ritz value never lies below the smallest eigenvalue of the positive matrix X (A0 - mu); X is
-    # the FP32 iterate at its stopping tolerance, not the exact sign, so that matrix is |A0 - mu| to
-    # a relative 1e-3
-    assert np.all(ld[:, 0] >= dist * (1 - 1e-3) - 1e-6)
+    # the FP32 iterate stopped at ||X^2 - I||_F <= 0.02 (the FP32 steps on the own columns finish the
+    # convergence), so its eigenvalues are 1 to within 0.02 and that matrix is |A0 - mu| to 2 %
+    assert np.all(ld[:, 0] >= dist * (1 - 2e-2) - 1e-6)
     rel = np.abs(ld[:, 0] - dist) / dist
     assert np.median(rel) < 1e-2 and np.quantile(rel, 0.9) < 0.1
 
