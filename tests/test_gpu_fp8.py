@@ -1,4 +1,4 @@
-"""The FP8 experiment (survey: FP8 as a measured experiment): the first fp8_iters Newton-Schulz
+"""The FP8 experiment (FP8 operands as a measured alternative): the first fp8_iters Newton-Schulz
 iterations round both product outputs to FP8 E4M3 values (the operand precision of an FP8 MMA,
 without its rate).  fp8_iters = 0 is the default path bit for bit.  One or two FP8 iterations
 still converge (finite, electron count within 1 %) but miss the accuracy bar by two orders of
