@@ -158,3 +158,17 @@ def test_same_groups_across_pattern_shapes(reach, keep, n_blocks, criterion, see
         g, _ = oc.combine(row_ptr, col, blk_ptr, blk_cols, ep, ei, criterion, pn[0], pn[1], max_dim)
         np.testing.assert_array_equal(r["group"], g)
         np.testing.assert_array_equal(r["dim"], oc.combined_dims(row_ptr, col, blk_ptr, blk_cols, ep, ei, g))
+
+
+def test_measured_tables_are_usable():
+    """The committed p(n) tables (products and whole step): ascending sizes 64..4096, positive times
+    per flop, accepted by the native combination; the batch sizing of the measurement script."""
+    from paper_2205_12182_gb300.measure_pn import batch_size
+    for path in (nl.PN_TABLE, nl.PN_STEP_TABLE):
+        dims, times = nl.load_pn_table(path)
+        assert dims[0] == 64 and dims[-1] == 4096 and np.all(np.diff(dims) > 0)
+        assert np.all(times > 0) and np.all(np.isfinite(times))
+        r = native(arrays(make_config(1)), oc.PERFORMANCE, (dims, times))
+        assert r["n_blocks"] >= 1
+    assert batch_size(4096) == 5 and batch_size(64) == 16384
+    assert all(4 <= batch_size(n) and batch_size(n) * n * n <= max(1e8, 4 * n * n) for n in range(64, 4097, 64))
