@@ -235,6 +235,7 @@ def run_ours(args):
             / (cnt["gemm_ms"] * 1e-3) / 1e12 if cnt["gemm_ms"] > 0 else None,
             "pct_fp16_peak_measured": 100 * frac if frac else None,
             "gemm_ms_per_step": cnt["gemm_ms"] / args.steps,
+            "ms_per_mu_iteration": st["ms"],   # one sign evaluation at the converged mu (the paper's T_NOLSM unit)
             "ns_iters_avg": st["iters_avg"],
             "mu_steps": phase["steps"][-1],
         },
