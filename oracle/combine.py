@@ -32,8 +32,9 @@ Readings (the paper is silent or garbled; each is repeated in the design notes):
   block ids), the combined block takes the smaller id, and it stops when no
   candidate pays.
 
-Everything here is written for clarity, not speed: each step recomputes the
-savings of all candidate pairs from their index sets.
+Everything here is written for clarity, not speed: each step scans every pair
+of current blocks for the best saving; a pair's saving is computed from the two
+index sets once and forgotten when either block changes.
 """
 from __future__ import annotations
 
