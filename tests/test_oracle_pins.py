@@ -230,3 +230,25 @@ def test_table2_time_is_flops_over_performance():
     t = [fi / pi for fi, pi in zip(f, p)]
     assert t[0] / t[1] == pytest.approx(g["estimated_speedup"][1], abs=0.05)
     assert t[0] / t[2] == pytest.approx(g["estimated_speedup"][2], abs=0.05)
+
+
+# --------------------------------------------------------------- the approximation against the full matrix
+
+def test_neighbourhood_submatrices_approximate_the_full_density():
+    """343 waters with the 8 A neighbourhood: the submatrix densities (Eq. 8) against the exact density
+    of the whole matrix (dense generalized eigendecomposition), both at the exact mu (midway between
+    the exact HOMO and LUMO, so both occupy the same states): within 1e-3 on every stored entry.  The
+    same blocks combined into one block covering the system give the exact density."""
+    s = water_box(7, 5, neighbourhood=8.0)
+    h, sm = dense(s)
+    w, v = sla.eigh(h, sm)
+    k = int(s.n_electrons // 2)
+    mu = 0.5 * (w[k - 1] + w[k])
+    rows = np.repeat(np.arange(s.n_basis), np.diff(s.row_ptr))
+    exact = ((v * (w < mu)) @ v.T)[rows, s.col]
+    o = NolsmOracle.from_system(s).prepare()
+    assert np.abs(o.density(mu) - exact).max() <= 1e-3
+    one = s.subset_blocks(np.arange(s.n_blocks))
+    one.blk_ptr = np.array([0, s.blk_cols.size], np.int32)
+    one.extra_ptr = np.array([0, s.extra_idx.size], np.int32)
+    np.testing.assert_allclose(NolsmOracle.from_system(one).prepare().density(mu), exact, atol=1e-10)
