@@ -125,6 +125,12 @@ typedef enum nolsm_refine_path {
                                memory, one CTA per block beyond that) */
 } nolsm_refine_path;
 
+/* First point of the chemical-potential bisection (nolsm_set_mu). */
+typedef enum nolsm_mu_first {
+  NOLSM_MU_FIRST_AUFBAU = 0,    /* the Aufbau estimate from the diagonal of A0, when inside the bracket */
+  NOLSM_MU_FIRST_MIDPOINT = 1   /* the bracket midpoint: plain bisection from the first step */
+} nolsm_mu_first;
+
 /* One CSR matrix (see the conventions above). */
 typedef struct nolsm_csr {
   int64_t n;               /* dimension N */
@@ -158,6 +164,7 @@ typedef struct nolsm_options {
                               Newton-Schulz iterations round both product outputs (B and X+) to FP8 E4M3
                               values before storing them, i.e. FP8 operands without the FP8 MMA rate
                               (default 0, at most max_iter) */
+  int32_t mu_first;        /* nolsm_mu_first of nolsm_set_mu (default AUFBAU) */
 } nolsm_options;
 
 /* Statistics of the last sign evaluation. */
@@ -205,8 +212,9 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
 nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out);
 
 /* Chemical potential by bisection (Section V-A: the mu that makes the system
- * charge neutral).  The first point is an Aufbau estimate when it lies inside the
- * bracket: with k = floor(n_electrons / spin_factor) occupied orbitals, the midpoint
+ * charge neutral).  With nolsm_options.mu_first = AUFBAU (the default) the first point
+ * is an Aufbau estimate when it lies inside the bracket (MIDPOINT: the bracket
+ * midpoint, plain bisection): with k = floor(n_electrons / spin_factor) occupied orbitals, the midpoint
  * of the k-th and (k+1)-th smallest diagonal entries of A0 over the blocks' own
  * columns; every later step evaluates nolsm_sign_batch at the bracket midpoint.
  * It stops when |N(mu) - n_electrons| <= tol_n * n_electrons, when the bracket is
@@ -230,6 +238,20 @@ nolsm_status nolsm_band_energy(nolsm_ctx* ctx, double* e_out);
 
 /* Number of blocks, and n_b / |C_b| of block b (host query of the build). */
 nolsm_status nolsm_block_info(const nolsm_ctx* ctx, int32_t b, int32_t* n_b, int32_t* n_cols);
+
+/* Diagonal entries of A0 = L^-1 T_b(H0) L^-T at every block's own columns (the data of
+ * nolsm_set_mu's Aufbau first point), in block order: *count = sum_b |C_b|, copied to out (host,
+ * *count floats) when out is not NULL.  Lets ranks that hold different blocks agree on the same
+ * first point.  Errors: EINVAL (not built, count NULL). */
+nolsm_status nolsm_own_diagonal(const nolsm_ctx* ctx, int64_t* count, float* out);
+
+/* Per-block terms of the last sign evaluation's electron count and band energy (host arrays of
+ * n_blocks; either may be NULL): n_out[b] = spin_factor * sum_{j in C_b} (T_b(S) T_b(D))_jj and
+ * e_out[b] = spin_factor * sum_{j in C_b} (T_b(H0) T_b(D))_jj, the block's share of Tr(D S) and
+ * Tr(D H0) at that evaluation's mu (Eq. 4, Section V-A), accumulated in FP64.  Their sums are the
+ * evaluation's n_electrons and band_energy.  Synchronises.  Errors: ENOTBUILT (no sign evaluation),
+ * EINVAL (both outputs NULL), ECUDA. */
+nolsm_status nolsm_block_traces(const nolsm_ctx* ctx, double* n_out, double* e_out);
 
 /* Index set I_b of block b copied to idx_out (host, n_b entries). */
 nolsm_status nolsm_block_index_set(const nolsm_ctx* ctx, int32_t b, int32_t* idx_out);
@@ -287,21 +309,28 @@ typedef enum nolsm_phase {
 nolsm_status nolsm_phase_times(nolsm_ctx* ctx, double* ms, int32_t n, int32_t reset);
 
 /* Band energy spin_factor * sum_e d_val[e] * h_val[e] over nnz stored entries (the reduction of
- * nolsm_band_energy), for callers that must not allocate device memory: the call needs no
- * context, makes no cudaMalloc/cudaFree or other allocating call, and keeps its partial sums in
- * a fixed 32 KB array in device memory that the library declares at file scope (every GPU that
- * loads the library holds it until the process exits).  d_val and h_val are device arrays on
+ * nolsm_band_energy), for callers that must not allocate device memory at the point of the call:
+ * code between the steps of a molecular-dynamics integrator that runs under a fixed device-memory
+ * budget, runtimes that route every device allocation through their own pool, or a hot loop where
+ * an allocation would synchronise the device.  The call needs no context, makes no
+ * cudaMalloc/cudaFree or other allocating call, and keeps its partial sums in a fixed 128 KB array
+ * in device memory that the library declares at file scope.  d_val and h_val are device arrays on
  * one symmetric pattern (so H0_ji = H0_ij), e_out is one device double, all owned by the caller;
  * work is enqueued on cuda_stream (a cudaStream_t, NULL = legacy default stream) and the call
  * returns without synchronising.  The paper has no counterpart: this is a library convenience.
  * Limits and behaviour:
- *  - nnz may not exceed 268,435,456 (4,096 partial sums of 65,536 entries); larger inputs,
+ *  - nnz may not exceed 268,435,456 (16,384 partial sums of 16,384 entries); larger inputs,
  *    nnz <= 0, null pointers or spin_factor <= 0 return NOLSM_EINVAL before any launch.
- *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- *    that device current; make that first call before any stream capture.
- *  - Every call on a device shares the array and leaves its partial sums in it; calls whose work
+ *  - The array's code module is loaded into a context lazily (CUDA's default lazy loading): the
+ *    first call on each device (each context) loads it, which allocates the array and the code
+ *    and may synchronise.  A caller with a fixed memory budget makes one warm-up call before the
+ *    budget applies; make that first call before any stream capture.  Every call looks up the
+ *    array's device address (cudaGetSymbolAddress) in the current context, so a context created
+ *    after a cudaDeviceReset gets its own array.
+ *  - Every call in a context shares the array and leaves its partial sums in it; calls whose work
  *    overlaps on the GPU (other streams, no ordering between them) race on it.
- *  - Returns NOLSM_ECUDA when the lookup or a launch fails. */
+ *  - A CUDA error left pending by earlier work is cleared (not reported) before the first launch;
+ *    returns NOLSM_ECUDA when the lookup or one of this call's launches fails. */
 nolsm_status nolsm_band_energy_noalloc(int64_t nnz, const double* d_val, const double* h_val, double spin_factor,
                                        double* e_out, void* cuda_stream);
 

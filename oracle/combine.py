@@ -16,7 +16,7 @@ What the paper fixes (Section III-B-1):
   p(n) n^3, p(n) obtained by measuring the product throughput of the GPU at a
   set of sizes and interpolating.
 
-Readings (the paper is silent or garbled; each is repeated in the design notes):
+Readings (the paper is silent or garbled on these points; the readings are stated here in full):
 
 * p(n) is a time per flop (the reciprocal of the measured FLOP/s at size n):
   the paper calls it a performance but multiplies it by n^3 to get a run

@@ -24,7 +24,7 @@ sign(S_b^-1 H_b - mu) = S_b^-1/2 U sign(eps - mu) U^T S_b^1/2 and, with
 Q = S_b^-1/2 U,  D_b = Q diag(theta(mu - eps)) Q^T  where theta = (1 - sign)/2
 evaluated at eps - mu, i.e. 1 below mu, 0 above, 1/2 exactly at mu.
 
-Readings where the paper is silent (each is repeated in the design notes):
+Readings where the paper is silent (stated here in full):
 * closed shell: the electron count targets Tr(D S) = N_e / 2 per spin, and the
   reported band energy is spin_factor * Tr(D H0) with spin_factor = 2;
 * index set: the pattern rule of step (1), optionally unioned with a given list

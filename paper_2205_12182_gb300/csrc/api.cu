@@ -231,6 +231,7 @@ nolsm_status nolsm_default_options(nolsm_options* opt) {
   opt->schedule = NOLSM_SCHEDULE_AUTO;
   opt->refine_path = NOLSM_REFINE_TENSOR;
   opt->fp8_iters = 0;
+  opt->mu_first = NOLSM_MU_FIRST_AUFBAU;
   return NOLSM_OK;
 }
 
@@ -731,7 +732,7 @@ nolsm_status nolsm_set_mu(nolsm_ctx* ctx, double n_electrons, double mu_lo, doub
     // Aufbau first point: between the k-th and (k+1)-th smallest own-column diagonal entries of A0
     const int64_t k = (int64_t)std::floor(n_electrons / ctx->opt.spin_factor);
     std::vector<float> d = ctx->h_own_diag;
-    if (k >= 1 && k < (int64_t)d.size()) {
+    if (ctx->opt.mu_first == NOLSM_MU_FIRST_AUFBAU && k >= 1 && k < (int64_t)d.size()) {
       std::nth_element(d.begin(), d.begin() + k, d.end());
       const float above = d[(size_t)k];
       const float below = *std::max_element(d.begin(), d.begin() + k);
@@ -792,6 +793,36 @@ nolsm_status nolsm_band_energy(nolsm_ctx* ctx, double* e_out) {
   harvest_phases(ctx);
   if (st != NOLSM_OK) return st;
   *e_out = ctx->opt.spin_factor * ctx->h_flags->energy;
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_block_traces(const nolsm_ctx* ctx, double* n_out, double* e_out) {
+  if (!ctx || !ctx->have_sign) return NOLSM_ENOTBUILT;
+  if (!n_out && !e_out) return NOLSM_EINVAL;
+  const int64_t nb = ctx->n_blocks;
+  const int64_t n = ctx->traces_per_unit ? (int64_t)ctx->h_slab_units.size() / 4 : nb;
+  std::vector<double> bn((size_t)n), be((size_t)n);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess ||
+      cudaMemcpy(bn.data(), ctx->d_bn, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(be.data(), ctx->d_be, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return NOLSM_ECUDA;
+  std::vector<double> sn((size_t)nb, 0.0), se((size_t)nb, 0.0);
+  for (int64_t u = 0; u < n; ++u) {
+    const int32_t b = ctx->traces_per_unit ? ctx->h_slab_units[(size_t)(4 * u)] : (int32_t)u;
+    sn[b] += bn[u];
+    se[b] += be[u];
+  }
+  for (int64_t b = 0; b < nb; ++b) {
+    if (n_out) n_out[b] = ctx->opt.spin_factor * sn[b];
+    if (e_out) e_out[b] = ctx->opt.spin_factor * se[b];
+  }
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_own_diagonal(const nolsm_ctx* ctx, int64_t* count, float* out) {
+  if (!ctx || !ctx->built || !count) return NOLSM_EINVAL;
+  *count = (int64_t)ctx->h_own_diag.size();
+  if (out) std::copy(ctx->h_own_diag.begin(), ctx->h_own_diag.end(), out);
   return NOLSM_OK;
 }
 

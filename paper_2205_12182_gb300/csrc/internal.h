@@ -131,6 +131,7 @@ struct nolsm_ctx {
   double* d_hi = nullptr;
   double* d_bn = nullptr;       // per-block traces (per slab unit on the tensor-core refinement)
   double* d_be = nullptr;
+  bool traces_per_unit = false; // the last evaluation left its traces per slab unit (tensor-core refinement)
   // own-column pieces of the tensor-core refinement: (block, first column, columns), narrow pieces
   // (<= 32 columns) first, then wide ones (<= 192), each group largest block first
   int32_t* d_slab_units = nullptr;

@@ -6,17 +6,14 @@
 // allocation through their own pool, or a hot loop where an allocation would synchronise the
 // device.  For them this entry point computes the same reduction from caller-provided device
 // arrays, writing its intermediate sums into `g_partials` below, which every GPU that loads the
-// library holds (32 KB) until the process exits.
+// library holds (128 KB) until the process exits.
 #include "internal.h"
-
-#include <mutex>
 
 namespace {
 
-constexpr int kChunk = 1 << 16;                 // stored entries per partial sum
-constexpr int kMaxPartials = 4096;              // capacity of the scratch array
+constexpr int kChunk = 1 << 14;                 // stored entries per partial sum (one CTA each)
+constexpr int kMaxPartials = 1 << 14;           // capacity of the scratch array (128 KB)
 constexpr int64_t kMaxEntries = (int64_t)kChunk * kMaxPartials;   // 268,435,456
-constexpr int kMaxDevices = 64;
 
 // Scratch shared by every call on this device: the partial sums of the latest call.
 static __device__ __align__(256) double g_partials[kMaxPartials];
@@ -56,25 +53,16 @@ __global__ void __launch_bounds__(256) energy_total_kernel(int n, const double* 
   }
 }
 
-// Device address of g_partials for each device, resolved once per device.  In host code the
-// symbol is only a host-side stand-in, so kernels must be given the address returned by
-// cudaGetSymbolAddress with that device current.
-std::mutex g_mutex;
-double* g_scratch[kMaxDevices] = {};
-
+// Device address of g_partials in the current device's context.  In host code the symbol is only
+// a host-side stand-in, so kernels must be given the address cudaGetSymbolAddress returns with the
+// device current.  The lookup is repeated on every call (it allocates nothing once the module is
+// loaded): an address kept from an earlier call could belong to a context that was reset since,
+// or to another context of the same device.
 cudaError_t scratch_for_current_device(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_partials);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_partials);
-    if (e != cudaSuccess) return e;
-    g_scratch[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch[dev];
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 
@@ -88,7 +76,12 @@ extern "C" nolsm_status nolsm_band_energy_noalloc(int64_t nnz, const double* d_v
   if (scratch_for_current_device(&scratch) != cudaSuccess) return NOLSM_ECUDA;
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   const int n_part = (int)((nnz + kChunk - 1) / kChunk);
+  // A launch error is read (and cleared) with cudaGetLastError, which would also return an error
+  // left pending by earlier work of the caller.  Such an error is cleared here, before the first
+  // launch, so that the status below reports this call's own launches only.
+  (void)cudaGetLastError();
   energy_partials_kernel<<<n_part, 256, 0, stream>>>(nnz, d_val, h_val, scratch);
+  if (cudaGetLastError() != cudaSuccess) return NOLSM_ECUDA;
   energy_total_kernel<<<1, 256, 0, stream>>>(n_part, scratch, spin_factor, e_out);
   return cudaGetLastError() == cudaSuccess ? NOLSM_OK : NOLSM_ECUDA;
 }

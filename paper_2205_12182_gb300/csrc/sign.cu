@@ -1077,6 +1077,7 @@ cudaError_t launch_slab_traces(nolsm_ctx* ctx, int half) {
   if (e != cudaSuccess) return e;
   // per-block traces, or per own-column piece on the tensor-core path
   const int n = tc ? ctx->n_units_narrow + ctx->n_units_wide : ctx->n_blocks;
+  ctx->traces_per_unit = tc;
   sum_traces_kernel<<<1, 1024, 0, ctx->stream>>>(n, ctx->d_bn, ctx->d_be, ctx->d_flags);
   return cudaGetLastError();
 }

@@ -23,11 +23,12 @@ BOUNDS_GERSHGORIN, BOUNDS_LANCZOS, BOUNDS_LEARNED, BOUNDS_GIVEN = 0, 1, 2, 3
 CHOL_FP64, CHOL_FP32, CHOL_FP64_INV64, CHOL_DF64, CHOL_DF64_SIMT = 0, 1, 2, 3, 4
 SCHEDULE_PERSISTENT, SCHEDULE_PER_PRODUCT, SCHEDULE_AUTO, SCHEDULE_PERSISTENT_INTERLEAVED = 0, 1, 2, 3
 REFINE_TENSOR, REFINE_SIMT = 0, 1
+MU_FIRST_AUFBAU, MU_FIRST_MIDPOINT = 0, 1
 COMBINE_CUBIC, COMBINE_PERFORMANCE = 0, 1
 
 FUNCTIONS = ["nolsm_default_options", "nolsm_create", "nolsm_build_submatrices", "nolsm_sign_batch", "nolsm_set_mu",
              "nolsm_density", "nolsm_band_energy", "nolsm_block_info", "nolsm_block_index_set", "nolsm_block_bounds",
-             "nolsm_block_state", "nolsm_block_matrix", "nolsm_block_factor", "nolsm_counters", "nolsm_phase_times", "nolsm_set_wait_budget",
+             "nolsm_block_state", "nolsm_block_traces", "nolsm_own_diagonal", "nolsm_block_matrix", "nolsm_block_factor", "nolsm_counters", "nolsm_phase_times", "nolsm_set_wait_budget",
              "nolsm_band_energy_noalloc",
              "nolsm_block_features", "nolsm_block_lanczos", "nolsm_mlp_create", "nolsm_mlp_get_params",
              "nolsm_mlp_gradient", "nolsm_mlp_adam", "nolsm_mlp_predict", "nolsm_mlp_destroy", "nolsm_set_predictor",
@@ -50,7 +51,8 @@ class NolsmOptions(C.Structure):
                 ("scaled", C.c_int32), ("sign_tol", C.c_double), ("max_iter", C.c_int32),
                 ("refine_iters", C.c_int32), ("spin_factor", C.c_double), ("lower_bound", C.c_double),
                 ("alpha_margin", C.c_double), ("wait_budget", C.c_int64), ("lanczos_steps", C.c_int32),
-                ("schedule", C.c_int32), ("refine_path", C.c_int32), ("fp8_iters", C.c_int32)]
+                ("schedule", C.c_int32), ("refine_path", C.c_int32), ("fp8_iters", C.c_int32),
+                ("mu_first", C.c_int32)]
 
 
 class NolsmSignStats(C.Structure):
@@ -88,6 +90,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "nolsm_block_index_set": (i32, [P, i32, P]),
         "nolsm_block_bounds": (i32, [P, P, P]),
         "nolsm_block_state": (i32, [P, P, P, P]),
+        "nolsm_block_traces": (i32, [P, P, P]),
+        "nolsm_own_diagonal": (i32, [P, C.POINTER(C.c_int64), P]),
         "nolsm_block_matrix": (i32, [P, i32, i32, P]),
         "nolsm_block_factor": (i32, [P, i32, P]),
         "nolsm_counters": (i32, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), pf64, pf64, i32]),
@@ -205,6 +209,23 @@ def nolsm_block_state(ctx, n_blocks):
     st = np.empty(n_blocks, np.int32)
     _check(ctx, _lib.nolsm_block_state(ctx, it.ctypes.data, res.ctypes.data, st.ctypes.data))
     return it, res, st
+
+
+def nolsm_block_traces(ctx, n_blocks):
+    """(electron count, band energy) terms of every block at the last sign evaluation (host)."""
+    n = np.empty(n_blocks)
+    e = np.empty(n_blocks)
+    _check(ctx, _lib.nolsm_block_traces(ctx, n.ctypes.data, e.ctypes.data))
+    return n, e
+
+
+def nolsm_own_diagonal(ctx) -> np.ndarray:
+    """Diagonal of A0 at every own column (host float32, block order)."""
+    n = C.c_int64()
+    _check(ctx, _lib.nolsm_own_diagonal(ctx, C.byref(n), None))
+    out = np.empty(n.value, np.float32)
+    _check(ctx, _lib.nolsm_own_diagonal(ctx, C.byref(n), out.ctypes.data))
+    return out
 
 
 def nolsm_block_matrix(ctx, b, which=0) -> np.ndarray:
@@ -466,6 +487,12 @@ class Nolsm:
 
     def block_state(self):
         return nolsm_block_state(self.ctx, self.n_blocks)
+
+    def block_traces(self):
+        return nolsm_block_traces(self.ctx, self.n_blocks)
+
+    def own_diagonal(self):
+        return nolsm_own_diagonal(self.ctx)
 
     def features(self, mu):
         import torch

@@ -19,8 +19,8 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from oracle.nolsm import NolsmOracle  # noqa: E402
 from synth import make_config  # noqa: E402
+from oracle_pool import oracle_blocks, trace_bounds  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -41,18 +41,20 @@ def mixed(nl, globule):
     lib = nl.Nolsm(precision=nl.PREC_MIXED_FP16, lower_bound=0.02).build(globule)
     mu, n, steps = lib.set_mu(globule.n_electrons, tol_n=1e-3)
     dims = np.array([nl.nolsm_block_info(lib.ctx, b)[0] for b in range(globule.n_blocks)])
-    out = dict(mu=mu, n=n, d=lib.density().cpu().numpy(), e=lib.band_energy(), dims=dims)
+    n_b, e_b = lib.block_traces()
+    out = dict(mu=mu, n=n, d=lib.density().cpu().numpy(), e=lib.band_energy(), dims=dims, n_b=n_b, e_b=e_b)
     lib.close()
     return out
 
 
 @pytest.fixture(scope="module")
 def sample_oracle(globule, mixed):
-    order = np.argsort(mixed["dims"])
-    sample = np.unique([order[0], order[len(order) // 2], order[-1]])
-    o = NolsmOracle.from_system(globule, blocks=sample).prepare()
-    own = np.isin(globule.col, np.concatenate([globule.block_cols(int(b)) for b in sample]))
-    return o, own
+    """24 blocks spread over the size range (smallest, largest and 22 quantiles between), evaluated
+    by the oracle at the GPU's mu: per-block count and energy terms, D on their own columns."""
+    order = np.argsort(mixed["dims"], kind="stable")
+    sample = np.unique(order[np.linspace(0, len(order) - 1, 24).round().astype(int)])
+    o_n, o_e, pos, o_d = oracle_blocks(globule, sample, mixed["mu"])
+    return dict(sample=sample, o_n=o_n, o_e=o_e, pos=pos, o_d=o_d)
 
 
 def test_ragged_sizes(globule, mixed):
@@ -61,24 +63,41 @@ def test_ragged_sizes(globule, mixed):
 
 
 def test_mixed_path_parity(globule, mixed, sample_oracle):
-    o, own = sample_oracle
+    o = sample_oracle
+    assert len(o["sample"]) >= 20
     assert abs(mixed["n"] - globule.n_electrons) <= 1e-3 * globule.n_electrons
-    assert np.abs(mixed["d"][own] - o.density(mixed["mu"])[own]).max() <= 1e-3
+    assert np.abs(mixed["d"][o["pos"]] - o["o_d"]).max() <= 1e-3
     assert np.isfinite(mixed["e"])
+    assert mixed["n_b"].sum() == pytest.approx(mixed["n"], rel=1e-12)
+
+
+def test_mixed_path_block_traces(globule, mixed, sample_oracle):
+    """Each sampled block's share of N = Tr(D S) and E = 2 Tr(D H0) against the oracle's, within what
+    max|dD| <= 1e-3 on the block's own columns allows."""
+    o = sample_oracle
+    s = o["sample"]
+    bn, be = trace_bounds(globule, s, 1e-3)
+    assert np.all(np.abs(mixed["n_b"][s] - o["o_n"]) <= bn)
+    assert np.all(np.abs(mixed["e_b"][s] - o["o_e"]) <= be)
 
 
 def test_fp32_path_parity(nl, globule, mixed, sample_oracle):
-    o, own = sample_oracle
+    o = sample_oracle
     lib = nl.Nolsm(precision=nl.PREC_FP32).build(globule)
     lib.sign_batch(mixed["mu"])
     d = lib.density().cpu().numpy()
+    n_b, e_b = lib.block_traces()
     lib.close()
-    assert np.abs(d[own] - o.density(mixed["mu"])[own]).max() <= 1e-6
+    assert np.abs(d[o["pos"]] - o["o_d"]).max() <= 1e-6
+    s = o["sample"]
+    bn, be = trace_bounds(globule, s, 1e-6)
+    assert np.all(np.abs(n_b[s] - o["o_n"]) <= bn)
+    assert np.all(np.abs(e_b[s] - o["o_e"]) <= be)
 
 
 def test_learned_bounds_out_of_distribution(nl, globule, mixed, sample_oracle):
     import os
-    o, own = sample_oracle
+    o = sample_oracle
     weights = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                            "paper_2205_12182_gb300", "weights", "bounds_mlp.json")
     lib = nl.Nolsm(precision=nl.PREC_MIXED_FP16, bounds=nl.BOUNDS_LEARNED)
@@ -88,4 +107,4 @@ def test_learned_bounds_out_of_distribution(nl, globule, mixed, sample_oracle):
     lib.sign_batch(mixed["mu"])
     d = lib.density().cpu().numpy()
     lib.close()
-    assert np.abs(d[own] - o.density(mixed["mu"])[own]).max() <= 1e-3
+    assert np.abs(d[o["pos"]] - o["o_d"]).max() <= 1e-3

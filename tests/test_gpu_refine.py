@@ -17,6 +17,7 @@ pytestmark = pytest.mark.gpu
 
 from oracle.nolsm import NolsmOracle  # noqa: E402
 from synth import make_config, water_clusters  # noqa: E402
+from oracle_pool import oracle_blocks, trace_bounds  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -90,18 +91,23 @@ def test_wide_and_narrow_pieces_of_one_block(nl):
 
 def test_cluster_blocks_sampled_parity(nl):
     """32-molecule clusters with an 8 A halo (432 blocks, n_b ~ 1,870) through set_mu on the
-    default path; the oracle checks sampled blocks one by one at the GPU's mu."""
+    default path; the oracle checks 16 sampled blocks at the GPU's mu: D on their own columns and
+    each block's share of N = Tr(D S) and E = 2 Tr(D H0) (within what max|dD| <= 1e-3 allows)."""
     s = make_config(5)
     lib = nl.Nolsm(precision=nl.PREC_MIXED_FP16).build(s)
     mu, n, _ = lib.set_mu(s.n_electrons, tol_n=1e-3)
     assert abs(n - s.n_electrons) <= 1e-3 * s.n_electrons
     d = lib.density().cpu().numpy()
     e = lib.band_energy()
-    sample = np.random.default_rng(5).choice(s.n_blocks, 3, replace=False)
-    o = NolsmOracle.from_system(s, blocks=sample).prepare()
-    own = np.isin(s.col, np.concatenate([s.block_cols(int(b)) for b in sample]))
-    assert np.abs(d[own] - o.density(mu)[own]).max() <= 1e-3
-    assert np.isfinite(e)
+    n_b, e_b = lib.block_traces()
+    lib.close()
+    sample = np.sort(np.random.default_rng(5).choice(s.n_blocks, 16, replace=False))
+    o_n, o_e, pos, o_d = oracle_blocks(s, sample, mu)
+    assert np.abs(d[pos] - o_d).max() <= 1e-3
+    bn, be = trace_bounds(s, sample, 1e-3)
+    assert np.all(np.abs(n_b[sample] - o_n) <= bn)
+    assert np.all(np.abs(e_b[sample] - o_e) <= be)
+    assert n_b.sum() == pytest.approx(n, rel=1e-12) and np.isfinite(e)
 
 
 def test_schedules_agree_on_large_blocks(nl):
