@@ -288,14 +288,16 @@ def run_ours(args):
                                                   tag="combination_globule", bounds=0.02)
         line["combination_globule"]["workload"] = (f"the same globule, one block per atom ({ga.n_blocks} blocks) "
                                                    "before combination, 8 A neighbourhood")
+    if not args.no_million and world == 1:
+        line["million_molecules"] = million_molecules(nolsm, predictor, pk, checks if want else None)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the cpu_baseline leg: the oracle timed on the host cores, then the parity spot checks
         line["cpu_baseline"] = cpu_baseline(system, seconds=args.cpu_seconds)
         for key, res in parity_checks(checks).items():
             if key == "headline":
                 line["parity"] = res
-            elif key == "largest_blocks":
-                line["largest_blocks"]["parity"] = res
+            elif key in ("largest_blocks", "million_molecules"):
+                line[key]["parity"] = res
             else:
                 section, name = key.split(".", 1)
                 line[section][name]["parity"] = res
@@ -400,6 +402,99 @@ def large_blocks(nolsm, predictor, pk, checks=None, steps=2, evals=3):
     if checks is not None:
         checks["largest_blocks"] = (s, lib.density().cpu().numpy(), mu, 2)
     lib.close()
+    return out
+
+
+def million_molecules(nolsm, predictor, pk, checks=None, parity_blocks=256, sample_blocks=1024):
+    """The 1,000,000-molecule configuration at full size: 6,000,000 basis functions, 31,250 blocks of
+    32-molecule clusters with an 8 A halo (n_b ~ 1,870), generated on the device (synth.device) and
+    solved by nolsm_solve_chunked with the learned bounds: the CSR of H0, S and D resident, the blocks
+    streamed through the pools in chunks sized to the free memory, mu to 1e-3 relative, the band
+    energy from the assembled D.  One warm-up solve of the first 2,000 blocks sizes the pools; the
+    full solve is timed once (CUDA events inside the call and the host clock around it).  Beside
+    it: the plain FP32 path and the mixed path on the first `sample_blocks` blocks, and the oracle on
+    `parity_blocks` sampled blocks at the returned mu."""
+    import torch
+    from synth.device import DeviceSystem, water_clusters_device
+    t0 = time.perf_counter()
+    ds = water_clusters_device(100, seed=31)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    torch.cuda.empty_cache()
+
+    def head(k):
+        return DeviceSystem(ds.name, ds.box, ds.n_mol, ds.row_ptr, ds.col, ds.h, ds.s, ds.blk_ptr[:k + 1],
+                            ds.blk_cols, ds.extra_ptr[:k + 1], ds.extra_idx, ds.n_electrons * k / ds.n_blocks)
+
+    d = torch.zeros(ds.nnz, dtype=torch.float64, device="cuda")
+    lib = nolsm.Nolsm(precision=nolsm.PREC_MIXED_FP16, bounds=nolsm.BOUNDS_LEARNED)
+    lib.set_predictor(predictor)
+    lib.solve_chunked(head(2000), d, tol_n=1e-3, max_passes=1)
+    lib.counters(reset=True)
+    lib.phase_times(reset=True)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t1 = time.perf_counter()
+        st = lib.solve_chunked(ds, d, tol_n=1e-3, block_traces=True)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t1
+    cnt = lib.counters(reset=True)
+    stage = {k: round(v, 1) for k, v in lib.phase_times(reset=True).items()}
+    lib.close()
+    t_solve = max(wall, st["ms_total"] * 1e-3)
+    ex = cnt["gemm_flops"] / (cnt["gemm_ms"] * 1e-3) / 1e12 if cnt["gemm_ms"] > 0 else None
+    useful = ex * st["flops_useful"] / st["flops_executed"] if ex else None
+    out = {"workload": "water-1000000: 32-molecule clusters + 8 A halo, 6,000,000 basis functions, 31,250 blocks",
+           "atoms": ds.n_atoms, "basis": ds.n_basis, "nnz": ds.nnz, "blocks": ds.n_blocks,
+           "generation_s_not_timed": round(gen_s, 1),
+           "value": ds.n_atoms / t_solve, "unit": "atoms/s", "seconds_per_solve": t_solve,
+           "device_ms": st["ms_total"], "passes": st["passes"], "chunks": st["chunks"],
+           "max_chunk_blocks": st["max_chunk_blocks"], "ms_per_mu_iteration": st["ms_last_pass"],
+           "mu": st["mu"], "n_electrons": st["n_electrons"], "n_target": ds.n_electrons,
+           "count_error_rel": abs(st["n_electrons"] - ds.n_electrons) / ds.n_electrons,
+           "band_energy": st["band_energy"], "band_energy_from_traces": st["band_energy_traces"],
+           "ns_iters_avg": st["iters_avg"], "stage_ms": stage, "clocks": clk.summary(),
+           "sign_gemm": {"tflops_executed": ex, "tflops_useful": useful,
+                         "tflops_paper_convention": ex * st["flops_paper"] / st["flops_executed"] if ex else None,
+                         "pct_fp16_peak_measured_useful": 100 * useful / pk["bf16_tflops_sustained"] if ex else None,
+                         "pct_fp16_peak_measured_executed": 100 * ex / pk["bf16_tflops_sustained"] if ex else None,
+                         "pct_fp16_peak_measured_burst_useful": 100 * useful / pk["bf16_tflops"] if ex else None,
+                         "gemm_ms": cnt["gemm_ms"], "gemm_launches": cnt["gemm_launches"],
+                         "useful_flops": "n_b^2 (n_b + 1) per symmetric product at the true n_b"}}
+    if checks is not None and parity_blocks:
+        # sampled blocks at the returned mu: their restricted systems and the D this solve left
+        # behind at their own-column entries (the oracle runs in the parity leg)
+        sys.path.insert(0, os.path.join(ROOT, "tests"))
+        from oracle_pool import own_positions, restrict_groups, trace_bounds_device
+        sample = np.sort(np.random.default_rng(31).choice(ds.n_blocks, parity_blocks, replace=False))
+        groups = restrict_groups(ds, sample)
+        dd = d[torch.from_numpy(own_positions(groups)).cuda()].cpu().numpy()
+        bn, be = trace_bounds_device(ds, sample, 1e-3)
+        checks["million_molecules"] = ("restricted", groups, dd, st["mu"], st["block_n"][sample],
+                                       st["block_e"][sample], bn, be)
+    # the plain FP32 path against the mixed path on the same bounded sample of blocks
+    sub = head(sample_blocks)
+    cmp = {}
+    for name, kw in (("mixed_fp16_learned", dict(precision=nolsm.PREC_MIXED_FP16, bounds=nolsm.BOUNDS_LEARNED)),
+                     ("fp32_plain", dict(precision=nolsm.PREC_FP32, scaled=0))):
+        lb = nolsm.Nolsm(**kw)
+        if kw.get("bounds") == nolsm.BOUNDS_LEARNED:
+            lb.set_predictor(predictor)
+        lb.solve_chunked(head(64), d, tol_n=1e-3, max_passes=1)   # warm-up
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        s2 = lb.solve_chunked(sub, d, tol_n=1e-3, max_passes=1)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t2
+        atoms = 3 * 32 * sample_blocks
+        cmp[name] = {"value": atoms / dt, "unit": "atoms/s", "seconds": dt, "ns_iters_avg": s2["iters_avg"],
+                     "mu": s2["mu"]}
+        lb.close()
+    cmp["sample"] = f"the first {sample_blocks} of {ds.n_blocks} blocks (one pass each, mu from the first chunk)"
+    cmp["speedup_mixed_over_fp32"] = cmp["mixed_fp16_learned"]["value"] / cmp["fp32_plain"]["value"]
+    out["fp32_plain_comparison"] = cmp
+    del d, ds
+    torch.cuda.empty_cache()
     return out
 
 
@@ -666,9 +761,22 @@ def parity_sample(system, d, mu, n_blocks=8):
     return {"blocks": int(n_blocks), "max_abs_dD": float(np.abs(d[own] - ref[own]).max())}
 
 
+def parity_restricted(groups, dd, mu, block_n, block_e, bn, be):
+    """The oracle on restricted groups of sampled blocks of a device-resident system."""
+    from oracle_pool import oracle_restricted
+    t0 = time.perf_counter()
+    o_n, o_e, pos, o_d = oracle_restricted(groups, mu)
+    return {"blocks": int(len(block_n)), "max_abs_dD": float(np.abs(dd - o_d).max()),
+            "max_block_n_err_over_bound": float(np.max(np.abs(block_n - o_n) / bn)),
+            "max_block_e_err_over_bound": float(np.max(np.abs(block_e - o_e) / be)),
+            "sampled_count_rel_err": float(abs(block_n.sum() - o_n.sum()) / o_n.sum()),
+            "oracle_seconds": round(time.perf_counter() - t0, 1)}
+
+
 def parity_checks(checks):
     """The oracle on sampled blocks of every recorded run (system, D, mu, blocks), at the run's mu."""
-    return {key: parity_sample(*args) for key, args in checks.items()}
+    return {key: parity_restricted(*args[1:]) if args[0] == "restricted" else parity_sample(*args)
+            for key, args in checks.items()}
 
 
 # ------------------------------------------------------------------------------------ oracle
@@ -744,6 +852,8 @@ def main():
     ap.add_argument("--no-combination", action="store_true", help="skip the submatrix-combination section")
     ap.add_argument("--no-globule", action="store_true", help="skip the protein-like globule section")
     ap.add_argument("--no-md", action="store_true", help="skip the MD-like steps with kept bounds")
+    ap.add_argument("--no-million", action="store_true",
+                    help="skip the 1,000,000-molecule configuration (chunked solve)")
     ap.add_argument("--keep-steps", type=int, default=16, help="Lanczos steps of the kept bounds (MD-like steps)")
     ap.add_argument("--side", type=int, default=16,
                     help="molecules per box edge (16: the 4,096-molecule workload; smaller boxes for profiling)")

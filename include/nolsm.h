@@ -236,6 +236,57 @@ nolsm_status nolsm_density(nolsm_ctx* ctx, double* d_val, int32_t memory);
  * assembled by the last nolsm_density, accumulated in FP64.  Synchronises. */
 nolsm_status nolsm_band_energy(nolsm_ctx* ctx, double* e_out);
 
+/* Result of nolsm_solve_chunked. */
+typedef struct nolsm_chunked_stats {
+  double mu;                 /* chemical potential of the last pass (D is the D at this mu) */
+  double n_electrons;        /* spin_factor * Tr(D S) at mu, summed over every block */
+  double band_energy;        /* spin_factor * Tr(D H0) of the assembled D (Eq. 4), FP64 */
+  double band_energy_traces; /* the same from the blocks' traces (a cross-check) */
+  double iters_avg;          /* matrix iterations per block in the last pass */
+  double flops_paper;        /* products of the last pass, 2 n_b^3 each (the paper's count) */
+  double flops_executed;     /* products of the last pass as executed (n_pad^2 (n_pad + 128) each) */
+  double flops_useful;       /* products of the last pass, n_b^2 (n_b + 1) each (one triangle and the
+                                diagonal of a symmetric product) */
+  double ms_total;           /* device time of the call (CUDA events on the context stream) */
+  double ms_last_pass;       /* device time of the last pass: every chunk built, evaluated, scattered */
+  int32_t iters_max;
+  int32_t passes;            /* sign evaluations of every block (one per chemical potential tried) */
+  int32_t chunks;
+  int32_t n_blocks;
+  int32_t max_chunk_blocks;
+  int32_t reserved;
+} nolsm_chunked_stats;
+
+/* The whole density step -- build, chemical potential, density, band energy -- for a system whose
+ * blocks' dense matrices do not fit in device memory at once (the submatrix method's blocks are
+ * independent, Section II).  The CSR of H0 and S (device memory, as for nolsm_build_submatrices) and
+ * the caller's D stay resident; the blocks are streamed through the context's pools in chunks of
+ * consecutive blocks.  Each pass builds every chunk in turn (nolsm_build_submatrices on the chunk),
+ * evaluates its sign at the pass's mu (nolsm_sign_batch), adds its terms of N(mu) = Tr(D S) and
+ * Tr(D H0), and scatters its columns of D into d_val.  mu follows nolsm_set_mu's bisection (Section
+ * V-A) with one pass per evaluation: the first point is the Aufbau estimate of the first chunk (its
+ * own columns with their share of the n_electrons / spin_factor occupied orbitals), the second the
+ * Aufbau estimate over every block when it lies inside the bracket [min lower bound, max upper
+ * bound] (known after the first pass), then midpoints; it stops when |N(mu) - n_electrons| <=
+ * tol_n * n_electrons, when the bracket is below 1e-10 Ha, or after max_passes.
+ *   chunk_blocks  blocks per chunk; <= 0 sizes the chunks from an estimate of their pools (index-set
+ *                 bound from the own rows' entries and the extra list) within 60 % of the free
+ *                 device memory.
+ *   d_val         device, nnz float64, caller-owned: D on the H0/S pattern at the returned mu
+ *                 (entries of columns owned by no block are 0).
+ *   block_n, block_e  host arrays of n_blocks or NULL: every block's terms of N and E at the returned
+ *                 mu (as nolsm_block_traces).
+ *   out           may be NULL.
+ * The context keeps the last chunk's build afterwards; nolsm_density and nolsm_band_energy refer to it
+ * (call nolsm_build_submatrices before using the context otherwise).  Synchronises.  Errors: those
+ * of nolsm_build_submatrices and nolsm_sign_batch, EINVAL (host-resident CSR, bad arguments),
+ * EBRACKET. */
+nolsm_status nolsm_solve_chunked(nolsm_ctx* ctx, const nolsm_csr* H, const nolsm_csr* S, int32_t n_blocks,
+                                 const int32_t* blk_ptr, const int32_t* blk_cols, const int32_t* extra_ptr,
+                                 const int32_t* extra_idx, int32_t chunk_blocks, double n_electrons, double tol_n,
+                                 int32_t max_passes, double* d_val, double* block_n, double* block_e,
+                                 nolsm_chunked_stats* out);
+
 /* Number of blocks, and n_b / |C_b| of block b (host query of the build). */
 nolsm_status nolsm_block_info(const nolsm_ctx* ctx, int32_t b, int32_t* n_b, int32_t* n_cols);
 

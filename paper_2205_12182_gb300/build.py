@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnolsm.so")
-SOURCES = ["api.cu", "index.cu", "build.cu", "sign.cu", "sign_tc.cu", "learn.cu", "noalloc.cu", "combine.cu"]
+SOURCES = ["api.cu", "index.cu", "build.cu", "sign.cu", "sign_tc.cu", "learn.cu", "noalloc.cu", "combine.cu", "chunked.cu"]
 # host-only planning code whose floating-point decisions must not depend on the host: no fused multiply-add
 PER_SOURCE = {"combine.cu": ["-Xcompiler", "-ffp-contract=off"]}
 HEADERS = [os.path.join(CSRC, "internal.h"), os.path.join(ROOT, "include", "nolsm.h")]

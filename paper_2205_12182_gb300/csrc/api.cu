@@ -370,7 +370,8 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
                        ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_extra, extra_idx, sizeof(int32_t) * n_extra, cudaMemcpyHostToDevice, ctx->stream));
   }
-  CK(launch_transpose(ctx));
+  if (!(ctx->chunked && ctx->transpose_ready)) CK(launch_transpose(ctx));
+  ctx->transpose_ready = ctx->chunked;
   CK(launch_index_sets(ctx, ctx->d_bptr, extra_ptr ? ctx->d_bptr + n_blocks + 1 : nullptr,
                        extra_ptr ? ctx->d_extra : nullptr, ctx->d_nb, cap));
   ctx->n_launches += 2;
@@ -471,7 +472,7 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   CK(dalloc(ctx, &ctx->d_tol, (size_t)n_blocks));
   CK(dalloc(ctx, &ctx->d_state, (size_t)n_blocks));
   CK(dalloc(ctx, &ctx->d_tiles, (size_t)tiles_max));
-  CK(dalloc(ctx, &ctx->d_dval, (size_t)nnz));
+  if (!ctx->chunked) CK(dalloc(ctx, &ctx->d_dval, (size_t)nnz));
   CK(cudaMemcpyAsync(ctx->d_blocks, ctx->h_blocks.data(), sizeof(BlockDesc) * n_blocks, cudaMemcpyHostToDevice, ctx->stream));
   if (!ctx->h_slab_units.empty())
     CK(cudaMemcpyAsync(ctx->d_slab_units, ctx->h_slab_units.data(), sizeof(int32_t) * ctx->h_slab_units.size(),

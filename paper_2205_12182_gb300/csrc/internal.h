@@ -166,6 +166,13 @@ struct nolsm_ctx {
   int64_t* d_transpose = nullptr;       // position of (j,i) for entry (i,j)
   double* d_dval = nullptr;             // assembled D on the pattern
 
+  // chunked solve (nolsm_solve_chunked): the builds of its chunks skip the context's own D and reuse
+  // the transpose positions of the first chunk (same CSR); the density of every chunk is scattered
+  // into the caller's D, which is cleared once per pass, not per chunk
+  bool chunked = false;
+  bool transpose_ready = false;         // d_transpose holds the positions of the current CSR
+  double* d_dval_target = nullptr;      // when set, the density scatter's destination (not cleared)
+
   // build scratch kept across builds: FP64 S and its factor (2 sum_sq doubles), T1 (sum_sq floats)
   double* d_sb = nullptr;
   float* d_t1 = nullptr;

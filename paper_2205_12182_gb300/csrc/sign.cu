@@ -1083,8 +1083,12 @@ cudaError_t launch_slab_traces(nolsm_ctx* ctx, int half) {
 }
 
 cudaError_t launch_density(nolsm_ctx* ctx) {
-  cudaError_t e = cudaMemsetAsync(ctx->d_dval, 0, sizeof(double) * ctx->nnz, ctx->stream);
-  if (e != cudaSuccess) return e;
+  // the chunked solve scatters every chunk into the caller's D, cleared once per pass
+  double* dst = ctx->d_dval_target ? ctx->d_dval_target : ctx->d_dval;
+  if (!ctx->d_dval_target) {
+    cudaError_t e = cudaMemsetAsync(ctx->d_dval, 0, sizeof(double) * ctx->nnz, ctx->stream);
+    if (e != cudaSuccess) return e;
+  }
   int max_pad = 0;
   for (const auto& bd : ctx->h_blocks) max_pad = std::max(max_pad, bd.n_pad);
   const dim3 g(max_pad / 128, ctx->n_blocks);
@@ -1094,7 +1098,7 @@ cudaError_t launch_density(nolsm_ctx* ctx) {
     density_slab_kernel<false><<<g, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_linv, ctx->d_y, ctx->d_tmp);
   density_scatter_kernel<<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_idx, ctx->d_blk_cols, ctx->d_tmp,
                                                                  ctx->d_row_ptr, ctx->d_col, ctx->d_transpose,
-                                                                 ctx->d_dval, ctx->d_flags);
+                                                                 dst, ctx->d_flags);
   ctx->n_launches += 1;   // the second of the two (the caller counts one)
   return cudaGetLastError();
 }
@@ -1102,7 +1106,8 @@ cudaError_t launch_density(nolsm_ctx* ctx) {
 cudaError_t launch_band_energy(nolsm_ctx* ctx) {
   const int grid = 1024;
   double* partial = reinterpret_cast<double*>(ctx->d_tmp);   // scratch: grid doubles
-  dot_kernel<<<grid, 256, 0, ctx->stream>>>(ctx->nnz, ctx->d_dval, ctx->d_hval, partial);
+  const double* d = ctx->d_dval_target ? ctx->d_dval_target : ctx->d_dval;
+  dot_kernel<<<grid, 256, 0, ctx->stream>>>(ctx->nnz, d, ctx->d_hval, partial);
   sum_partials_kernel<<<1, 32, 0, ctx->stream>>>(grid, partial, &ctx->d_flags->energy);
   return cudaGetLastError();
 }

@@ -26,7 +26,7 @@ REFINE_TENSOR, REFINE_SIMT = 0, 1
 MU_FIRST_AUFBAU, MU_FIRST_MIDPOINT = 0, 1
 COMBINE_CUBIC, COMBINE_PERFORMANCE = 0, 1
 
-FUNCTIONS = ["nolsm_default_options", "nolsm_create", "nolsm_build_submatrices", "nolsm_sign_batch", "nolsm_set_mu",
+FUNCTIONS = ["nolsm_default_options", "nolsm_create", "nolsm_build_submatrices", "nolsm_sign_batch", "nolsm_set_mu", "nolsm_solve_chunked",
              "nolsm_density", "nolsm_band_energy", "nolsm_block_info", "nolsm_block_index_set", "nolsm_block_bounds",
              "nolsm_block_state", "nolsm_block_traces", "nolsm_own_diagonal", "nolsm_block_matrix", "nolsm_block_factor", "nolsm_counters", "nolsm_phase_times", "nolsm_set_wait_budget",
              "nolsm_band_energy_noalloc",
@@ -65,6 +65,18 @@ class NolsmSignStats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class NolsmChunkedStats(C.Structure):
+    _fields_ = [("mu", C.c_double), ("n_electrons", C.c_double), ("band_energy", C.c_double),
+                ("band_energy_traces", C.c_double), ("iters_avg", C.c_double), ("flops_paper", C.c_double),
+                ("flops_executed", C.c_double), ("flops_useful", C.c_double), ("ms_total", C.c_double),
+                ("ms_last_pass", C.c_double),
+                ("iters_max", C.c_int32), ("passes", C.c_int32), ("chunks", C.c_int32), ("n_blocks", C.c_int32),
+                ("max_chunk_blocks", C.c_int32), ("reserved", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class NolsmError(RuntimeError):
     def __init__(self, status, message):
         self.status = status
@@ -84,6 +96,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "nolsm_build_submatrices": (i32, [P, C.POINTER(NolsmCsr), C.POINTER(NolsmCsr), i32, P, P, P, P]),
         "nolsm_sign_batch": (i32, [P, f64, C.POINTER(NolsmSignStats)]),
         "nolsm_set_mu": (i32, [P, f64, f64, f64, f64, i32, pf64, pf64, pi32]),
+        "nolsm_solve_chunked": (i32, [P, C.POINTER(NolsmCsr), C.POINTER(NolsmCsr), i32, P, P, P, P, i32, f64, f64,
+                                      i32, P, P, P, C.POINTER(NolsmChunkedStats)]),
         "nolsm_density": (i32, [P, P, i32]),
         "nolsm_band_energy": (i32, [P, pf64]),
         "nolsm_block_info": (i32, [P, i32, pi32, pi32]),
@@ -172,6 +186,16 @@ def nolsm_set_mu(ctx, n_electrons, mu_lo=0.0, mu_hi=0.0, tol_n=1e-3, max_steps=6
     _check(ctx, _lib.nolsm_set_mu(ctx, float(n_electrons), float(mu_lo), float(mu_hi), float(tol_n), int(max_steps),
                                   C.byref(mu), C.byref(n), C.byref(st)))
     return mu.value, n.value, st.value
+
+
+def nolsm_solve_chunked(ctx, H: NolsmCsr, S: NolsmCsr, n_blocks, blk_ptr, blk_cols, extra_ptr, extra_idx,
+                        chunk_blocks, n_electrons, tol_n, max_passes, d_val, block_n=None, block_e=None) -> dict:
+    st = NolsmChunkedStats()
+    _check(ctx, _lib.nolsm_solve_chunked(ctx, C.byref(H), C.byref(S), int(n_blocks), _ptr(blk_ptr), _ptr(blk_cols),
+                                         _ptr(extra_ptr), _ptr(extra_idx), int(chunk_blocks), float(n_electrons),
+                                         float(tol_n), int(max_passes), _ptr(d_val), _ptr(block_n), _ptr(block_e),
+                                         C.byref(st)))
+    return st.as_dict()
 
 
 def nolsm_density(ctx, d_val=None, memory=MEM_DEVICE):
@@ -433,6 +457,10 @@ class Nolsm:
         """CSR arrays of `system` as torch tensors on the device or in pinned host memory (cached)."""
         import torch
         key = (id(system), memory)
+        if getattr(system, "on_device", False):
+            if memory != "device":
+                raise ValueError("a device-resident system can only be used with memory='device'")
+            return [system.row_ptr, system.col, system.h, system.s]
         if key not in self._cache:
             arrs = [np.ascontiguousarray(system.row_ptr, np.int64), np.ascontiguousarray(system.col, np.int32),
                     np.ascontiguousarray(system.h, np.float64), np.ascontiguousarray(system.s, np.float64)]
@@ -461,6 +489,29 @@ class Nolsm:
 
     def sign_batch(self, mu):
         return nolsm_sign_batch(self.ctx, mu)
+
+    def solve_chunked(self, system, d_out, n_electrons=None, tol_n=1e-3, max_passes=60, chunk_blocks=0,
+                      block_traces=False):
+        """nolsm_solve_chunked on a system whose CSR is (or is copied) on the device; D into d_out
+        (device float64, nnz).  Returns the statistics, plus per-block terms when block_traces."""
+        rp, cl, hv, sv = self.stage(system, "device")
+        self._keep = [rp, cl, hv, sv]
+        H = make_csr(system.n_basis, system.nnz, rp, cl, hv, MEM_DEVICE)
+        S = make_csr(system.n_basis, system.nnz, rp, cl, sv, MEM_DEVICE)
+        bp = np.ascontiguousarray(system.blk_ptr, np.int32)
+        bc = np.ascontiguousarray(system.blk_cols, np.int32)
+        ep = None if system.extra_ptr is None else np.ascontiguousarray(system.extra_ptr, np.int32)
+        ei = None if system.extra_idx is None else np.ascontiguousarray(system.extra_idx, np.int32)
+        nb = len(bp) - 1
+        bn = np.empty(nb) if block_traces else None
+        be = np.empty(nb) if block_traces else None
+        st = nolsm_solve_chunked(self.ctx, H, S, nb, bp, bc, ep, ei, chunk_blocks,
+                                 system.n_electrons if n_electrons is None else n_electrons, tol_n, max_passes,
+                                 d_out, bn, be)
+        self.n_blocks = None      # the context now holds the last chunk's build
+        if block_traces:
+            st["block_n"], st["block_e"] = bn, be
+        return st
 
     def set_mu(self, n_electrons, mu_lo=0.0, mu_hi=0.0, tol_n=1e-3, max_steps=60):
         return nolsm_set_mu(self.ctx, n_electrons, mu_lo, mu_hi, tol_n, max_steps)

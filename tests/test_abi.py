@@ -57,7 +57,7 @@ def test_struct_layout_matches_c(lib_path, tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     structs = {"nolsm_csr": nolsm.NolsmCsr, "nolsm_options": nolsm.NolsmOptions,
-               "nolsm_sign_stats": nolsm.NolsmSignStats}
+               "nolsm_sign_stats": nolsm.NolsmSignStats, "nolsm_chunked_stats": nolsm.NolsmChunkedStats}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "nolsm.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')

@@ -142,7 +142,8 @@ def test_bad_predictions_cost_iterations_not_accuracy(nl, sys1, orc1, mu1, case)
     lib.set_predictor(pred)
     st = lib.sign_batch(mu1)
     assert np.abs(lib.density().cpu().numpy() - orc1.density(mu1)).max() <= 1e-3
-    assert st["n_electrons"] == pytest.approx(2 * orc1.electron_count(mu1), rel=1e-4)
+    # 64 blocks: the FP16 count error is about 5e-7 relative (test_gpu_parity.py explains the 5e-6)
+    assert st["n_electrons"] == pytest.approx(2 * orc1.electron_count(mu1), rel=5e-6)
     if case == "radius_far_too_small":
         # the scale never drops below the Gershgorin scale / 1.7, so the iteration cannot diverge
         assert st["n_restarted"] == 0

@@ -3,6 +3,12 @@
 Tolerances: max|dD| <= 1e-6 (FP32 path) and <= 1e-3 (mixed FP16 path) over the stored entries
 of D; |dE_band| <= 1e-4 Ha per atom; electron count within 1e-6 relative (FP32 path).  The
 oracle is re-evaluated at the chemical potential the GPU returns.
+
+Electron count on the mixed path: the FP16 rounding of the iterate leaves each block's share of
+N = Tr(D S) (a partial trace over its own columns) off by a few 1e-5 electrons, independently from
+block to block, so the relative error of N falls like 1 / sqrt(blocks): on these 64-block boxes it
+is about 5e-7 and reaches 1.5e-6 (the tests allow MIXED_N_REL = 5e-6); from a few hundred blocks on
+it is below 1e-6 (the 4,096-block benchmark system is held to 1e-6 in test_gpu_headline.py).
 """
 import numpy as np
 import pytest
@@ -12,6 +18,8 @@ pytestmark = pytest.mark.gpu
 
 from oracle.nolsm import NolsmOracle  # noqa: E402
 from synth import make_config, isolated_waters, dimer_system, water_box  # noqa: E402
+
+MIXED_N_REL = 5e-6
 
 
 @pytest.fixture(scope="module")
@@ -83,7 +91,7 @@ def test_mixed_fp16_path_parity(nl, sys1, orc1, mu1, scaled):
     lib = make(nl, sys1, nl.PREC_MIXED_FP16, scaled=scaled)
     st = lib.sign_batch(mu1)
     n_ref = 2 * orc1.electron_count(mu1)
-    assert st["n_electrons"] == pytest.approx(n_ref, rel=1e-4)
+    assert st["n_electrons"] == pytest.approx(n_ref, rel=MIXED_N_REL)
     dmax, _ = _dmax(nl, lib, orc1, mu1)
     assert dmax <= 1e-3, dmax
     assert abs(lib.band_energy() - orc1.band_energy_of_mu(mu1)) / sys1.n_atoms <= 1e-4
@@ -96,7 +104,7 @@ def test_set_mu_mixed(nl, sys1, orc1):
     # oracle at the GPU's mu: the gap around mu (distance to the nearest block eigenvalue)
     gap = min(np.min(np.abs(e - mu)) for e in orc1.eps)
     assert gap >= 1e-3
-    assert 2 * orc1.electron_count(mu) == pytest.approx(n, rel=1e-4)
+    assert 2 * orc1.electron_count(mu) == pytest.approx(n, rel=MIXED_N_REL)
     dmax, _ = _dmax(nl, lib, orc1, mu)
     assert dmax <= 1e-3
 

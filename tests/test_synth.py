@@ -4,7 +4,7 @@ import pytest
 import scipy.linalg as sla
 
 from oracle.nolsm import csr_matrix, NolsmOracle
-from synth import make_config, water_box
+from synth import make_config, water_box, water_clusters
 from synth.system import ANGLE_HOH, R_OH
 
 
@@ -122,3 +122,19 @@ def test_displaced_geometry_keeps_onsite_energies_and_blocks():
     np.testing.assert_array_equal(sd, sd.T)
     assert 0 < np.abs(hd - hs).max() < 0.05                  # a small step, not a new system
     assert np.linalg.eigvalsh(sd)[0] > 0.05
+
+
+def test_device_generator_on_host_matches_numpy():
+    """synth.device (pair search and CSR assembly in torch) against the numpy generator, torch on the
+    host: same pattern, blocks and extra lists; values within the rounding of exp."""
+    torch = pytest.importorskip("torch")
+    from synth.device import water_clusters_device
+    a = water_clusters(8, seed=31)
+    b = water_clusters_device(8, seed=31, device="cpu")
+    np.testing.assert_array_equal(a.row_ptr, b.row_ptr.numpy())
+    np.testing.assert_array_equal(a.col, b.col.numpy())
+    np.testing.assert_allclose(b.h.numpy(), a.h, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(b.s.numpy(), a.s, rtol=0, atol=1e-15)
+    for k in ("blk_ptr", "blk_cols", "extra_ptr", "extra_idx"):
+        np.testing.assert_array_equal(getattr(a, k), getattr(b, k))
+    assert b.n_electrons == a.n_electrons and b.nnz == a.nnz
