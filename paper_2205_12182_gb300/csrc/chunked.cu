@@ -74,22 +74,29 @@ extern "C" nolsm_status nolsm_solve_chunked(nolsm_ctx* ctx, const nolsm_csr* H, 
   const int64_t N = H->n, nnz = H->nnz;
   if (N <= 0 || nnz <= 0 || S->n != N || S->nnz != nnz) return fail(ctx, NOLSM_EINVAL, "H and S must share the pattern");
 
-  // ---- chunks: consecutive blocks, either chunk_blocks at a time or as many as an estimate of their
-  // pools allows within 60 % of the free device memory (dimension bound: own rows' entries + extra)
+  // ---- chunks: consecutive blocks, either chunk_blocks at a time or as many as fit within 60 % of
+  // the free device memory (plus the context's own pools, which the chunks reuse).  The pool bytes of
+  // a block are estimated from a bound on its dimension (its own rows' entries plus its extra list)
+  // scaled by the largest ratio of actual to estimated bytes among the blocks built so far, so the
+  // first chunk is sized conservatively and the later ones from the measured dimensions.  The cuts
+  // of the first pass are kept for the later ones.
   std::vector<int32_t> cut{0};
+  std::vector<double> est;
+  double budget = 0.0, ratio = 1.0;   // estimate scale; 1 until the first chunk has been built
+  bool measured = false;
   if (chunk_blocks > 0) {
     for (int32_t b = chunk_blocks; b < n_blocks; b += chunk_blocks) cut.push_back(b);
+    cut.push_back(n_blocks);
   } else {
     std::vector<int64_t> rp((size_t)N + 1);
     if (cudaMemcpy(rp.data(), H->row_ptr, sizeof(int64_t) * (N + 1), cudaMemcpyDeviceToHost) != cudaSuccess)
       return fail(ctx, NOLSM_ECUDA, "row pointers");
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return fail(ctx, NOLSM_ECUDA, "cudaMemGetInfo");
-    // the context's pools are reused by the chunks: count them as available
     double held = 0.0;
     for (const auto& c : ctx->caps) held += (double)c.second;
-    const double budget = 0.6 * ((double)free_b + held);
-    double used = 0.0;
+    budget = 0.6 * ((double)free_b + held);
+    est.resize((size_t)n_blocks);
     for (int32_t b = 0; b < n_blocks; ++b) {
       int64_t m = extra_ptr ? extra_ptr[b + 1] - extra_ptr[b] : 0;
       for (int32_t k = blk_ptr[b]; k < blk_ptr[b + 1]; ++k) {
@@ -97,17 +104,16 @@ extern "C" nolsm_status nolsm_solve_chunked(nolsm_ctx* ctx, const nolsm_csr* H, 
         if (c < 0 || c >= N) return fail(ctx, NOLSM_EINVAL, "block column out of range");
         m += rp[c + 1] - rp[c];
       }
-      const double need = block_bytes(m, blk_ptr[b + 1] - blk_ptr[b], mixed);
-      if (used > 0 && used + need > budget) {
-        cut.push_back(b);
-        used = 0.0;
-      }
-      used += need;
+      est[b] = block_bytes(m, blk_ptr[b + 1] - blk_ptr[b], mixed);
     }
   }
-  cut.push_back(n_blocks);
-  const int n_chunks = (int)cut.size() - 1;
-
+  // end of the chunk that starts at b0 (first pass, automatic sizing)
+  auto next_cut = [&](int32_t b0) {
+    double used = 0.0;
+    int32_t b = b0;
+    while (b < n_blocks && (b == b0 || used + ratio * est[b] <= budget)) used += ratio * est[b++];
+    return b;
+  };
   ChunkedMode mode(ctx, d_val);
   const int64_t total_cols = blk_ptr[n_blocks];
   const double n_occ = n_electrons / ctx->opt.spin_factor;
@@ -136,7 +142,8 @@ extern "C" nolsm_status nolsm_solve_chunked(nolsm_ctx* ctx, const nolsm_csr* H, 
     int64_t it_sum = 0;
     int32_t it_max = 0;
     double fp = 0.0, fe = 0.0, fu = 0.0;
-    for (int c = 0; c < n_chunks; ++c) {
+    for (int c = 0; c + 1 < (int)cut.size() || (chunk_blocks <= 0 && pass == 0 && cut.back() < n_blocks); ++c) {
+      if (c + 1 >= (int)cut.size()) cut.push_back(next_cut(cut.back()));
       const int32_t b0 = cut[c], b1 = cut[c + 1], nb = b1 - b0;
       bp.resize((size_t)nb + 1);
       for (int32_t b = 0; b <= nb; ++b) bp[b] = blk_ptr[b0 + b] - blk_ptr[b0];
@@ -150,6 +157,13 @@ extern "C" nolsm_status nolsm_solve_chunked(nolsm_ctx* ctx, const nolsm_csr* H, 
       }
       nolsm_status s = nolsm_build_submatrices(ctx, H, S, nb, bp.data(), blk_cols + blk_ptr[b0], ep_c, ei_c);
       if (s != NOLSM_OK) return s;
+      if (chunk_blocks <= 0 && pass == 0) {
+        double r = 0.0;
+        for (int32_t b = 0; b < nb; ++b)
+          r = std::max(r, 1.1 * block_bytes(ctx->h_blocks[b].n, bp[b + 1] - bp[b], mixed) / est[b0 + b]);
+        ratio = measured ? std::max(ratio, r) : r;
+        measured = true;
+      }
       if (pass == 0) {
         lo = std::min(lo, *std::min_element(ctx->h_lo.begin(), ctx->h_lo.end()));
         hi = std::max(hi, *std::max_element(ctx->h_hi.begin(), ctx->h_hi.end()));
@@ -228,10 +242,10 @@ extern "C" nolsm_status nolsm_solve_chunked(nolsm_ctx* ctx, const nolsm_csr* H, 
   st.band_energy = ctx->opt.spin_factor * ctx->h_flags->energy;
   st.band_energy_traces = e_tr;
   st.passes = pass;
-  st.chunks = n_chunks;
+  st.chunks = (int32_t)cut.size() - 1;
   st.n_blocks = n_blocks;
   st.max_chunk_blocks = 0;
-  for (int c = 0; c < n_chunks; ++c) st.max_chunk_blocks = std::max(st.max_chunk_blocks, cut[c + 1] - cut[c]);
+  for (size_t c = 0; c + 1 < cut.size(); ++c) st.max_chunk_blocks = std::max(st.max_chunk_blocks, cut[c + 1] - cut[c]);
   st.ms_total = ms_all;
   if (out) *out = st;
   return NOLSM_OK;

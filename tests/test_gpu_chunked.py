@@ -74,7 +74,9 @@ def test_chunked_equals_one_build(nl, clusters):
     np.testing.assert_array_equal(st["block_e"], e_b)
     assert st["n_electrons"] == pytest.approx(ref["n_electrons"], rel=1e-13)
     assert st["band_energy"] == pytest.approx(e_1, rel=1e-13)
-    assert st["band_energy_traces"] == pytest.approx(st["band_energy"], rel=1e-9)
+    # D's entries are the FP32 products L^-T Y, the traces FP64 sums over the FP32 slabs: the two
+    # energies agree to FP32 rounding
+    assert abs(st["band_energy_traces"] - st["band_energy"]) / s.n_atoms <= 1e-5
 
 
 def test_chunked_bisection_passes(nl, clusters):
@@ -105,7 +107,7 @@ def test_million_molecules_sampled_parity(nl):
     st = lib.solve_chunked(ds, d, tol_n=1e-3, block_traces=True)
     lib.close()
     assert st["chunks"] > 1 and abs(st["n_electrons"] - ds.n_electrons) <= 1e-3 * ds.n_electrons
-    assert st["band_energy_traces"] == pytest.approx(st["band_energy"], rel=1e-9)
+    assert abs(st["band_energy_traces"] - st["band_energy"]) / ds.n_atoms <= 1e-5
     sample = np.sort(np.random.default_rng(31).choice(ds.n_blocks, 32, replace=False))
     o_n, o_e, pos, o_d = oracle_device_blocks(ds, sample, st["mu"])
     dd = d[torch.from_numpy(pos).cuda()].cpu().numpy()
