@@ -199,8 +199,10 @@ nolsm_status nolsm_create(nolsm_ctx** ctx, const nolsm_options* opt, void* cuda_
  * (a geometric neighbourhood).  blk_* and extra_* are host arrays.  The call
  * gathers T_b(H0) and T_b(S), factors T_b(S) = L L^T, forms A0 = L^-1 T_b(H0) L^-T
  * (so that sign(T_b(S)^-1 T_b(H0) - mu) = L^-T sign(A0 - mu) L^T) and its spectral
- * bounds.  n_b = |I_b| must not exceed 4096.  Errors: EINVAL (sizes, pattern,
- * n_b), ENOTPD, ENONFINITE, ENOMEM, ECUDA. */
+ * bounds.  n_b = |I_b| must not exceed 16384 (Table II's submatrices reach 10,737); while every
+ * block has n_b <= 4096 the index sets take 4096 entries per block, otherwise 16384.  Blocks with
+ * n_pad > 4096 run the per-product schedule whatever nolsm_options.schedule says.  Errors: EINVAL
+ * (sizes, pattern, n_b), ENOTPD, ENONFINITE, ENOMEM, ECUDA. */
 nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const nolsm_csr* S,
                                      int32_t n_blocks, const int32_t* blk_ptr, const int32_t* blk_cols,
                                      const int32_t* extra_ptr, const int32_t* extra_idx);

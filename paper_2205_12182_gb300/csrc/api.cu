@@ -353,10 +353,11 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   for (int64_t r = 0; r < N; ++r) max_deg = std::max<int64_t>(max_deg, rp[r + 1] - rp[r]);
   if (max_cand > cap && max_deg > cap - kMaxDim)
     return fail(ctx, NOLSM_EINVAL, "a row of the pattern holds more than 28672 entries");
+  ctx->idx_stride = kMaxDim;
 
   // ---- transpose positions, pattern checks and index sets on the device
   CK(dalloc(ctx, &ctx->d_transpose, (size_t)nnz));
-  CK(dalloc(ctx, &ctx->d_idx, (size_t)n_blocks * kMaxDim));
+  CK(dalloc(ctx, &ctx->d_idx, (size_t)n_blocks * ctx->idx_stride));
   CK(dalloc(ctx, &ctx->d_own, (size_t)n_cols));
   CK(dalloc(ctx, &ctx->d_blk_cols, (size_t)n_cols));
   CK(dalloc(ctx, &ctx->d_bptr, (size_t)(2 * (n_blocks + 1))));
@@ -373,18 +374,30 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   if (!(ctx->chunked && ctx->transpose_ready)) CK(launch_transpose(ctx));
   ctx->transpose_ready = ctx->chunked;
   CK(launch_index_sets(ctx, ctx->d_bptr, extra_ptr ? ctx->d_bptr + n_blocks + 1 : nullptr,
-                       extra_ptr ? ctx->d_extra : nullptr, ctx->d_nb, cap));
+                       extra_ptr ? ctx->d_extra : nullptr, ctx->d_nb, cap, ctx->idx_stride));
   ctx->n_launches += 2;
-  std::vector<int32_t> nb((size_t)n_blocks);
-  CK(cudaMemcpyAsync(nb.data(), ctx->d_nb, sizeof(int32_t) * n_blocks, cudaMemcpyDeviceToHost, ctx->stream));
   {
     nolsm_status st0 = check_device_flags(ctx);
+    if (st0 == NOLSM_OK && ctx->h_flags->oversize > 0) {
+      // some index set holds more than 4096 rows: every block again with the wide stride (blocks up
+      // to 16384; larger ones are an EINVAL error of the kernel)
+      ctx->idx_stride = kMaxDimLarge;
+      cap = kMaxCandidates;
+      CK(dalloc(ctx, &ctx->d_idx, (size_t)n_blocks * ctx->idx_stride));
+      CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(DevFlags), ctx->stream));
+      CK(launch_index_sets(ctx, ctx->d_bptr, extra_ptr ? ctx->d_bptr + n_blocks + 1 : nullptr,
+                           extra_ptr ? ctx->d_extra : nullptr, ctx->d_nb, cap, ctx->idx_stride));
+      ctx->n_launches += 1;
+      st0 = check_device_flags(ctx);
+    }
     if (st0 != NOLSM_OK) {
       ctx->last_error = "pattern not symmetric / columns out of order or range / missing diagonal, or a "
-                        "submatrix dimension above 4096";
+                        "submatrix dimension above 16384";
       return st0;
     }
   }
+  std::vector<int32_t> nb((size_t)n_blocks);
+  CK(cudaMemcpy(nb.data(), ctx->d_nb, sizeof(int32_t) * n_blocks, cudaMemcpyDeviceToHost));
 
   // ---- layout: bins of equal n_pad stored contiguously (tensor maps stack a bin's matrices)
   ctx->h_blocks.assign((size_t)n_blocks, BlockDesc{});
@@ -401,7 +414,7 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
     bd.n_pad = pad_dim(bd.n);
     bd.c = blk_ptr[b + 1] - blk_ptr[b];
     bd.col0 = blk_ptr[b];
-    bd.off_idx = (int64_t)b * kMaxDim;
+    bd.off_idx = (int64_t)b * ctx->idx_stride;
     bd.off_own = blk_ptr[b];
     ctx->flops_paper_iter += 2.0 * 2.0 * (double)bd.n * bd.n * bd.n;
     ctx->flops_exec_iter += 2.0 * (double)bd.n_pad * bd.n_pad * (bd.n_pad + kTile);
@@ -422,7 +435,7 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   }
   ctx->sum_sq = off_mat;
   ctx->sum_slab = off_slab;
-  ctx->sum_idx = (int64_t)n_blocks * kMaxDim;
+  ctx->sum_idx = (int64_t)n_blocks * ctx->idx_stride;
   ctx->sum_own = n_cols;
   int64_t tiles_max = 0;
   for (const auto& bd : ctx->h_blocks) tiles_max += (int64_t)(bd.n_pad / kTile) * (bd.n_pad / kTile);
@@ -524,8 +537,8 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   // the trace slab takes the factor's FP32 rounding (FP32 and double-float modes) or the FP64 factor
   const int l32 = chol32 || chol_mode == NOLSM_CHOL_DF64 || chol_mode == NOLSM_CHOL_DF64_SIMT;
   CK(launch_slabs_impl(ctx, l32 ? (const void*)(sb + ctx->sum_sq) : (const void*)sb, l32, ctx->d_t1));
-  CK(dalloc(ctx, &ctx->d_rowd, (size_t)ctx->n_blocks * kMaxDim));
-  CK(dalloc(ctx, &ctx->d_rowr, (size_t)ctx->n_blocks * kMaxDim));
+  CK(dalloc(ctx, &ctx->d_rowd, (size_t)ctx->n_blocks * ctx->idx_stride));
+  CK(dalloc(ctx, &ctx->d_rowr, (size_t)ctx->n_blocks * ctx->idx_stride));
   CK(launch_bounds(ctx));
   CK(dalloc(ctx, &ctx->d_own_diag, (size_t)std::max<int64_t>(ctx->sum_own, 1)));
   CK(launch_own_diag(ctx));
@@ -620,9 +633,12 @@ nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out) 
   }
   int max_pad = 0;
   for (const auto& bd : ctx->h_blocks) max_pad = std::max(max_pad, bd.n_pad);
-  const bool persistent = mixed && (ctx->opt.schedule == NOLSM_SCHEDULE_PERSISTENT ||
-                                    ctx->opt.schedule == NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED ||
-                                    (ctx->opt.schedule == NOLSM_SCHEDULE_AUTO && max_pad < 1024));
+  // the persistent kernels hold a product's tile list per CTA for n_pad <= 4096; larger blocks always
+  // run per-product launches
+  const bool persistent = mixed && max_pad <= kMaxDim &&
+                          (ctx->opt.schedule == NOLSM_SCHEDULE_PERSISTENT ||
+                           ctx->opt.schedule == NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED ||
+                           (ctx->opt.schedule == NOLSM_SCHEDULE_AUTO && max_pad < 1024));
   ctx->pair_interleaved = ctx->opt.schedule == NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED;
   if (ctx->opt.fp8_iters > 0 && (!persistent || ctx->pair_interleaved))
     return fail(ctx, NOLSM_EINVAL, "fp8_iters needs a mixed-precision path on the persistent schedule");

@@ -1085,7 +1085,7 @@ __global__ void gershgorin_kernel(const BlockDesc* __restrict__ blocks, const fl
       d += __shfl_xor_sync(0xffffffffu, d, o);
     }
     if (lane == 0 && row_diag) {
-      row_diag[bd.off_idx + r] = d;      // per-row data for features at any mu (stride kMaxDim)
+      row_diag[bd.off_idx + r] = d;      // per-row data for features at any mu (index-set stride)
       row_rad[bd.off_idx + r] = rad;
     }
     rad *= up;

@@ -45,9 +45,9 @@ double aufbau(std::vector<float> d, int64_t k) {
 // n_pad^2: A0, L^-1, T1 in FP32, S and its factor in 2 x FP64, three iterate buffers of 2 or 4
 // bytes; slabs, per-row tables and the factor's slice planes are small beside them).
 double block_bytes(int64_t n, int64_t cols, bool mixed) {
-  const double np = (double)pad_dim((int)std::min<int64_t>(n, kMaxDim));
+  const double np = (double)pad_dim((int)std::min<int64_t>(n, kMaxDimLarge));
   const double sq = np * np;
-  return sq * (3 * 4 + 16 + 3 * (mixed ? 2 : 4)) + np * (double)cols * 4 * 10 + 2.0 * kMaxDim * 4 +
+  return sq * (3 * 4 + 16 + 3 * (mixed ? 2 : 4)) + np * (double)cols * 4 * 10 + 3.0 * kMaxDim * 4 +
          7.0 * 64 * 2 * np + 64.0 * 1024;
 }
 

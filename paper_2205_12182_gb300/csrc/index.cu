@@ -38,9 +38,10 @@ __global__ void transpose_kernel(int64_t n, const int64_t* __restrict__ row_ptr,
 }
 
 // Sort cand[0, m) ascending (bitonic, padded to a power of two with INT_MAX) and write its distinct
-// values to I (at most kMaxDim of them; the count is returned in full).  The distinct values are then
+// values to I (at most max_dim of them; the count is returned in full).  The distinct values are then
 // copied back to cand[0, count) so that further candidates can be appended.
-__device__ int sort_unique(int32_t* cand, int m, int32_t* __restrict__ I, int32_t* warp_tot, int32_t* s_base) {
+__device__ int sort_unique(int32_t* cand, int m, int32_t* __restrict__ I, int32_t* warp_tot, int32_t* s_base,
+                           int max_dim) {
   const int tid = threadIdx.x;
   int p2 = 1;
   while (p2 < m) p2 <<= 1;
@@ -73,7 +74,7 @@ __device__ int sort_unique(int32_t* cand, int m, int32_t* __restrict__ I, int32_
     for (int w = 0; w < warp; ++w) off += warp_tot[w];
     const int32_t v = (i < m) ? cand[i] : 0;
     __syncthreads();
-    if (keep && off + before < kMaxDim) I[off + before] = v;
+    if (keep && off + before < max_dim) I[off + before] = v;
     if (tid == 0) {
       int t = 0;
       for (int w = 0; w < nw; ++w) t += warp_tot[w];
@@ -82,31 +83,33 @@ __device__ int sort_unique(int32_t* cand, int m, int32_t* __restrict__ I, int32_
     __syncthreads();
   }
   const int nb = *s_base;
-  for (int i = tid; i < min(nb, kMaxDim); i += blockDim.x) cand[i] = I[i];
+  for (int i = tid; i < min(nb, max_dim); i += blockDim.x) cand[i] = I[i];
   __syncthreads();
   return nb;
 }
 
 // One CTA per block: gather the candidate rows into shared memory, bitonic sort, keep the first
-// of every run of equal values.  I_b goes to idx[b * kMaxDim ...], |I_b| to n_out[b], and the
+// of every run of equal values.  I_b goes to idx[b * max_dim ...], |I_b| to n_out[b], and the
 // local position of own column j to own[blk_ptr[b] + j].  When the next column's rows (or the next
 // piece of the extra list) would overflow the cap entries, the candidates so far are sorted and made
-// distinct first (at most kMaxDim remain).  More than kMaxDim distinct rows, or one column with more
-// than cap - kMaxDim rows, is an EINVAL error for the block.
+// distinct first (at most max_dim remain).  More than max_dim distinct rows, or one column with more
+// than cap - max_dim rows, is counted in flags->oversize while max_dim < kMaxDimLarge (the build
+// then widens the stride and runs again) and is an EINVAL error for the block at kMaxDimLarge.
 __global__ void __launch_bounds__(512) index_set_kernel(int64_t n, const int64_t* __restrict__ row_ptr,
                                                         const int32_t* __restrict__ col,
                                                         const int32_t* __restrict__ blk_ptr,
                                                         const int32_t* __restrict__ blk_cols,
                                                         const int32_t* __restrict__ extra_ptr,
                                                         const int32_t* __restrict__ extra_idx, int cap,
-                                                        int32_t* __restrict__ idx, int32_t* __restrict__ own,
-                                                        int32_t* __restrict__ n_out, DevFlags* flags) {
+                                                        int max_dim, int32_t* __restrict__ idx,
+                                                        int32_t* __restrict__ own, int32_t* __restrict__ n_out,
+                                                        DevFlags* flags) {
   extern __shared__ int32_t cand[];          // cap entries
   __shared__ int32_t warp_tot[16];
   __shared__ int32_t s_base;
   const int b = blockIdx.x;
   const int tid = threadIdx.x;
-  int32_t* I = idx + (int64_t)b * kMaxDim;
+  int32_t* I = idx + (int64_t)b * max_dim;
   int m = 0;                                 // block-uniform candidate count
   bool bad = false;
   // candidates: the rows of every own column (row c's columns: the pattern is symmetric) + extras
@@ -117,8 +120,8 @@ __global__ void __launch_bounds__(512) index_set_kernel(int64_t n, const int64_t
     const int64_t e0 = row_ptr[c], e1 = row_ptr[c + 1];
     const int deg = (int)(e1 - e0);
     if (m + deg > cap) {
-      m = sort_unique(cand, m, I, warp_tot, &s_base);
-      if (m > kMaxDim || m + deg > cap) { bad = true; break; }
+      m = sort_unique(cand, m, I, warp_tot, &s_base, max_dim);
+      if (m > max_dim || m + deg > cap) { bad = true; break; }
     }
     for (int i = tid; i < deg; i += blockDim.x) cand[m + i] = col[e0 + i];
     m += deg;
@@ -128,8 +131,8 @@ __global__ void __launch_bounds__(512) index_set_kernel(int64_t n, const int64_t
     const int32_t x0 = extra_ptr[b], x1 = extra_ptr[b + 1];
     for (int32_t s = x0; s < x1 && !bad;) {
       if (m == cap) {
-        m = sort_unique(cand, m, I, warp_tot, &s_base);
-        if (m >= cap || m > kMaxDim) { bad = true; break; }
+        m = sort_unique(cand, m, I, warp_tot, &s_base, max_dim);
+        if (m >= cap || m > max_dim) { bad = true; break; }
       }
       const int take = min(x1 - s, cap - m);
       for (int i = tid; i < take; i += blockDim.x) {
@@ -142,10 +145,13 @@ __global__ void __launch_bounds__(512) index_set_kernel(int64_t n, const int64_t
       __syncthreads();
     }
   }
-  const int nb = bad ? kMaxDim + 1 : sort_unique(cand, m, I, warp_tot, &s_base);
+  const int nb = bad ? max_dim + 1 : sort_unique(cand, m, I, warp_tot, &s_base, max_dim);
   if (tid == 0) n_out[b] = bad ? 0 : nb;
-  if (nb > kMaxDim) {
-    if (tid == 0) set_error(flags, NOLSM_EINVAL);
+  if (nb > max_dim) {
+    if (tid == 0) {
+      if (max_dim < kMaxDimLarge) atomicAdd(&flags->oversize, 1);
+      else set_error(flags, NOLSM_EINVAL);
+    }
     return;
   }
   // own-column positions (every own column is its own row's diagonal, so it is in I_b)
@@ -173,7 +179,7 @@ cudaError_t launch_transpose(nolsm_ctx* ctx) {
 }
 
 cudaError_t launch_index_sets(nolsm_ctx* ctx, const int32_t* d_blk_ptr, const int32_t* d_extra_ptr,
-                              const int32_t* d_extra_idx, int32_t* d_nb, int cap) {
+                              const int32_t* d_extra_idx, int32_t* d_nb, int cap, int max_dim) {
   if (!d_blk_ptr || !d_nb || !ctx->d_blk_cols || !ctx->d_idx || !ctx->d_own || (cap & (cap - 1)) != 0)
     return cudaErrorInvalidValue;
   const size_t smem = sizeof(int32_t) * (size_t)cap;
@@ -185,7 +191,7 @@ cudaError_t launch_index_sets(nolsm_ctx* ctx, const int32_t* d_blk_ptr, const in
   }
   index_set_kernel<<<ctx->n_blocks, 512, smem, ctx->stream>>>(ctx->n, ctx->d_row_ptr, ctx->d_col, d_blk_ptr,
                                                               ctx->d_blk_cols, d_extra_ptr, d_extra_idx, cap,
-                                                              ctx->d_idx, ctx->d_own, d_nb, ctx->d_flags);
+                                                              max_dim, ctx->d_idx, ctx->d_own, d_nb, ctx->d_flags);
   return cudaGetLastError();
 }
 

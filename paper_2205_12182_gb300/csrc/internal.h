@@ -15,7 +15,8 @@ namespace nolsm {
 
 // Output tile edge of every matrix-product kernel; submatrices are padded to it.
 constexpr int kTile = 128;
-constexpr int kMaxDim = 4096;
+constexpr int kMaxDim = 4096;           // index-set stride while every block has n_b <= 4096
+constexpr int kMaxDimLarge = 16384;     // largest n_b (index-set stride when some block exceeds 4096)
 constexpr int kMaxCandidates = 32768;   // own-column rows + extra indices of one block
 
 inline int pad_dim(int n) { return (n + kTile - 1) / kTile * kTile; }
@@ -73,7 +74,7 @@ struct DevFlags {
   int32_t n_active;     // blocks still iterating
   int32_t queue;        // next block to claim (persistent schedule)
   int32_t slab_queue[2];  // next unit to claim by the tensor-core slab kernels (narrow, wide)
-  int32_t pad1;
+  int32_t oversize;     // blocks whose index set exceeded the current stride (the build widens it)
   double sum_n;         // sum of block traces Tr(S D) over own columns
   double sum_e;         // same for Tr(H D)
   double energy;        // band energy reduction
@@ -108,6 +109,7 @@ struct nolsm_ctx {
   float* d_own_diag = nullptr;
   std::vector<int32_t> h_iters;
   int64_t sum_sq = 0, sum_slab = 0, sum_idx = 0, sum_own = 0;
+  int32_t idx_stride = nolsm::kMaxDim;  // entries per block in the index-set and per-row pools
   double flops_paper_iter = 0.0, flops_exec_iter = 0.0;
 
   // device memory owned by the context
@@ -281,7 +283,7 @@ cudaError_t mlp_predict_on(const struct nolsm_mlp* m, cudaStream_t s, const floa
 // index.cu
 cudaError_t launch_transpose(nolsm_ctx* ctx);
 cudaError_t launch_index_sets(nolsm_ctx* ctx, const int32_t* d_blk_ptr, const int32_t* d_extra_ptr,
-                              const int32_t* d_extra_idx, int32_t* d_nb, int cap);
+                              const int32_t* d_extra_idx, int32_t* d_nb, int cap, int max_dim);
 
 // generic SIMT NT product used by the build: C_b = A_b B_b^T on the block table
 cudaError_t launch_sgemm_nt(nolsm_ctx* ctx, const float* a, const float* b, float* c, int a_lower, int b_lower,

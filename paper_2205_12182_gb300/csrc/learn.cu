@@ -511,6 +511,13 @@ cudaError_t launch_lanczos(nolsm_ctx* ctx, double mu, int op, int k, float* basi
   for (const auto& b : ctx->h_blocks) max_pad = std::max(max_pad, b.n_pad);
   const size_t smem = sizeof(float) * 2 * (size_t)max_pad;
   const int hk = (ctx->opt.precision == NOLSM_PREC_MIXED_FP16) ? 1 : (ctx->opt.precision == NOLSM_PREC_MIXED_BF16 ? 2 : 0);
+  if (smem > 48 * 1024) {   // blocks above n_pad 6144
+    cudaError_t e = hk == 0 ? cudaFuncSetAttribute(lanczos_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                  : hk == 1 ? cudaFuncSetAttribute(lanczos_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                            : cudaFuncSetAttribute(lanczos_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   if (hk == 0)
     lanczos_kernel<float><<<ctx->n_blocks, 256, smem, ctx->stream>>>(ctx->d_blocks, ctx->d_a0, ctx->d_state,
                                                                      (const float*)ctx->d_x[0], (const float*)ctx->d_x[1],
