@@ -283,6 +283,7 @@ def run_ours(args):
         line["globule"]["workload"] = (f"protein-like globule, {g.n_atoms} atoms ({g.n_basis} basis functions), "
                                        f"{g.n_blocks} blocks of 10-200 atoms, 8 A neighbourhood; Gershgorin "
                                        "bounds, lower bound 0.02")
+        line["globule_schedules"] = globule_schedules(nolsm, g)
         ga = atom_blocks(g)
         line["combination_globule"] = combination(nolsm, predictor, ga, checks if want else None,
                                                   tag="combination_globule", bounds=0.02)
@@ -583,6 +584,47 @@ def combination(nolsm, predictor, system, checks=None, steps=2, evals=3, tag="co
         m = out[name]["measured"]
         m["speedup_full_step"] = base["ms_per_step"] / m["ms_per_step"]
         m["speedup_products"] = base["products_ms_per_sign_evaluation"] / m["products_ms_per_sign_evaluation"]
+    return out
+
+
+def globule_schedules(nolsm, g, evals=3):
+    """The ragged globule's products (n_b 163-2,678) under each product schedule: the built-in AUTO
+    rule, AUTO with the autotuner's measured table (a split evaluation: the bins that prefer the
+    persistent kernel in one persistent launch, the rest in per-product launches), and every single
+    schedule.  Products ms per sign evaluation (stage timer) at the converged mu, Gershgorin bounds
+    with lower bound 0.02."""
+    import torch
+    try:
+        table = nolsm.load_schedule_table()
+    except OSError:
+        table = None
+    cases = [("auto_builtin", nolsm.SCHEDULE_AUTO, None), ("persistent", nolsm.SCHEDULE_PERSISTENT, None),
+             ("per_product", nolsm.SCHEDULE_PER_PRODUCT, None),
+             ("interleaved", nolsm.SCHEDULE_PERSISTENT_INTERLEAVED, None)]
+    if table is not None:
+        cases.insert(1, ("auto_measured_table", nolsm.SCHEDULE_AUTO, table))
+    out = {"workload": f"protein-like globule, {g.n_atoms} atoms, {g.n_blocks} blocks", "evaluations": evals,
+           "table": None if table is None else "paper_2205_12182_gb300/weights/schedule_gb300.json"}
+    mu = None
+    for name, sched, tab in cases:
+        lib = nolsm.Nolsm(precision=nolsm.PREC_MIXED_FP16, lower_bound=0.02, schedule=sched)
+        if tab is not None:
+            lib.set_schedule_table(tab)
+        lib.build(g)
+        if mu is None:
+            mu = lib.set_mu(g.n_electrons, tol_n=TOL_N)[0]
+        lib.sign_batch(mu)
+        torch.cuda.synchronize()
+        lib.phase_times(reset=True)
+        for _ in range(evals):
+            st = lib.sign_batch(mu)
+        ms = lib.phase_times(reset=True)["products"] / evals
+        sc, nq = lib.last_schedule()
+        out[name] = {"products_ms_per_sign_evaluation": ms, "ns_iters_avg": st["iters_avg"],
+                     "schedule_run": {-2: "split"}.get(sc, ["persistent", "per_product", "auto", "interleaved"][sc]),
+                     "persistent_blocks": nq,
+                     "products_tflops_paper_convention": st["flops_paper"] / (ms * 1e-3) / 1e12}
+        lib.close()
     return out
 
 

@@ -107,8 +107,9 @@ typedef enum nolsm_schedule {
                                      iteration driven from the host; from n_pad 1024 on, the tiles
                                      are dealt round-robin so that all SMs share a few blocks'
                                      operands in L2 */
-  NOLSM_SCHEDULE_AUTO = 2,        /* PERSISTENT while every block has n_pad < 1024 (the iterates of
-                                     the blocks in flight stay in L2), PER_PRODUCT otherwise */
+  NOLSM_SCHEDULE_AUTO = 2,        /* the measured table of nolsm_set_schedule_table when one is set;
+                                     otherwise PERSISTENT while every block has n_pad < 1024 (the
+                                     iterates of the blocks in flight stay in L2), PER_PRODUCT otherwise */
   NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED = 3  /* PERSISTENT with two blocks per cluster: the products
                                      of both alternate and share one cluster barrier per pair (same
                                      arithmetic).  Twice the iterates in flight: at n_pad 512 they no
@@ -288,6 +289,23 @@ nolsm_status nolsm_solve_chunked(nolsm_ctx* ctx, const nolsm_csr* H, const nolsm
                                  const int32_t* extra_idx, int32_t chunk_blocks, double n_electrons, double tol_n,
                                  int32_t max_passes, double* d_val, double* block_n, double* block_e,
                                  nolsm_chunked_stats* out);
+
+/* Measured schedule table for NOLSM_SCHEDULE_AUTO (the library's autotuner,
+ * paper_2205_12182_gb300/autotune.py, writes one from timings of the products at each n_pad): entry i
+ * says which schedule ran the products of blocks with n_pad[i-1] < n_pad <= n_pad[i] fastest (the
+ * first entry covers everything below, the last everything above).  With a table, every sign
+ * evaluation takes the blocks whose entry is PERSISTENT or PERSISTENT_INTERLEAVED into one persistent
+ * launch (largest first; the variant preferred by the larger share of their n_pad^3) and runs the
+ * others, and every block above n_pad 4096, with per-product launches after it.  n_pad ascending and
+ * positive, schedule one of PERSISTENT, PER_PRODUCT, PERSISTENT_INTERLEAVED; n_entries = 0 removes
+ * the table (AUTO is then persistent while every n_pad < 1024).  Copied.  Errors: EINVAL. */
+nolsm_status nolsm_set_schedule_table(nolsm_ctx* ctx, int32_t n_entries, const int32_t* n_pad, const int32_t* schedule);
+
+/* Schedule of the last sign evaluation: *schedule = PERSISTENT, PERSISTENT_INTERLEAVED or PER_PRODUCT
+ * when every block ran it, -2 when the evaluation was split (a persistent launch, then per-product
+ * launches); *persistent_blocks = blocks of the persistent launch.  Either may be NULL.
+ * Errors: ENOTBUILT (no sign evaluation). */
+nolsm_status nolsm_last_schedule(const nolsm_ctx* ctx, int32_t* schedule, int32_t* persistent_blocks);
 
 /* Number of blocks, and n_b / |C_b| of block b (host query of the build). */
 nolsm_status nolsm_block_info(const nolsm_ctx* ctx, int32_t b, int32_t* n_b, int32_t* n_cols);

@@ -631,24 +631,66 @@ nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out) 
     ctx->n_launches += 2;
     pred = ctx->d_pred;
   }
+  // Schedule of every block.  The persistent kernels hold a product's tile list per CTA for n_pad <=
+  // 4096; larger blocks always run per-product launches.  AUTO takes the measured table
+  // (nolsm_set_schedule_table) when one is set, else the built-in rule (persistent while every
+  // n_pad < 1024).  Blocks that prefer a persistent schedule form the queue of one persistent launch;
+  // the others follow in per-product launches (a split evaluation).
   int max_pad = 0;
   for (const auto& bd : ctx->h_blocks) max_pad = std::max(max_pad, bd.n_pad);
-  // the persistent kernels hold a product's tile list per CTA for n_pad <= 4096; larger blocks always
-  // run per-product launches
-  const bool persistent = mixed && max_pad <= kMaxDim &&
-                          (ctx->opt.schedule == NOLSM_SCHEDULE_PERSISTENT ||
-                           ctx->opt.schedule == NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED ||
-                           (ctx->opt.schedule == NOLSM_SCHEDULE_AUTO && max_pad < 1024));
-  ctx->pair_interleaved = ctx->opt.schedule == NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED;
+  std::vector<int32_t> queue;
+  bool interleaved = ctx->opt.schedule == NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED;
+  if (mixed) {
+    const int sch = ctx->opt.schedule;
+    if (sch == NOLSM_SCHEDULE_PERSISTENT || sch == NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED) {
+      if (max_pad <= kMaxDim)
+        for (int32_t b = 0; b < ctx->n_blocks; ++b) queue.push_back(b);
+    } else if (sch == NOLSM_SCHEDULE_AUTO && ctx->sched_pad.empty()) {
+      if (max_pad < 1024)
+        for (int32_t b = 0; b < ctx->n_blocks; ++b) queue.push_back(b);
+    } else if (sch == NOLSM_SCHEDULE_AUTO) {
+      // per block the entry of the smallest tabulated n_pad >= its own (the last one beyond); the
+      // persistent variant is the one preferred by the larger share of the queue's n_pad^3
+      double w_plain = 0.0, w_inter = 0.0;
+      for (int32_t b = 0; b < ctx->n_blocks; ++b) {
+        const int np = ctx->h_blocks[b].n_pad;
+        size_t k = 0;
+        while (k + 1 < ctx->sched_pad.size() && ctx->sched_pad[k] < np) ++k;
+        const int kind = ctx->sched_kind[k];
+        if (np > kMaxDim || kind == NOLSM_SCHEDULE_PER_PRODUCT) continue;
+        queue.push_back(b);
+        (kind == NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED ? w_inter : w_plain) += (double)np * np * np;
+      }
+      interleaved = w_inter > w_plain;
+      // largest blocks first: the queue's tail is then made of short jobs
+      std::stable_sort(queue.begin(), queue.end(),
+                       [&](int32_t a, int32_t c) { return ctx->h_blocks[a].n_pad > ctx->h_blocks[c].n_pad; });
+    }
+  }
+  const bool persistent = !queue.empty() && (int32_t)queue.size() == ctx->n_blocks;
+  const bool split = !queue.empty() && !persistent;
+  ctx->pair_interleaved = interleaved;
+  ctx->n_queue = (int32_t)queue.size();
+  ctx->last_schedule = persistent ? (interleaved ? NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED : NOLSM_SCHEDULE_PERSISTENT)
+                                  : split ? -2 : NOLSM_SCHEDULE_PER_PRODUCT;
+  if (split) {
+    CK(dalloc(ctx, &ctx->d_queue, queue.size()));
+    CK(cudaMemcpyAsync(ctx->d_queue, queue.data(), sizeof(int32_t) * queue.size(), cudaMemcpyHostToDevice,
+                       ctx->stream));
+  }
   if (ctx->opt.fp8_iters > 0 && (!persistent || ctx->pair_interleaved))
     return fail(ctx, NOLSM_EINVAL, "fp8_iters needs a mixed-precision path on the persistent schedule");
+  // X_0 of the per-product blocks (in a split evaluation every block's; the persistent kernel forms
+  // its own blocks' X_0 again)
   CK(launch_ns_init(ctx, mu, hk, mode, mode == NOLSM_BOUNDS_LANCZOS ? ctx->d_lz : nullptr, pred, !persistent));
   ctx->n_launches += persistent ? 1 : 2;
   const int tile_n = mixed ? tc_tile_n() : kTile;
   const int check_every = 4;
   ctx->gemm_ev_used = 0;
   CK(phase_mark(ctx, NOLSM_PHASE_PRODUCTS));
-  if (persistent) CK(gemm_timed(ctx, mixed, 0, mu));   // the whole iteration of every block
+  // the whole iteration of the queued blocks, on the device; the per-product loop below then sees
+  // them converged (or failed) and runs the remaining blocks
+  if (!queue.empty()) CK(gemm_timed(ctx, mixed, 0, mu));
   for (int it = 0; !persistent && it <= ctx->opt.max_iter; ++it) {
     CK(launch_ns_tiles_n(ctx, tile_n));
     CK(gemm_timed(ctx, mixed, 1, mu));
@@ -840,6 +882,28 @@ nolsm_status nolsm_own_diagonal(const nolsm_ctx* ctx, int64_t* count, float* out
   if (!ctx || !ctx->built || !count) return NOLSM_EINVAL;
   *count = (int64_t)ctx->h_own_diag.size();
   if (out) std::copy(ctx->h_own_diag.begin(), ctx->h_own_diag.end(), out);
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_set_schedule_table(nolsm_ctx* ctx, int32_t n_entries, const int32_t* n_pad,
+                                      const int32_t* schedule) {
+  if (!ctx) return NOLSM_EINVAL;
+  if (n_entries < 0 || (n_entries > 0 && (!n_pad || !schedule))) return fail(ctx, NOLSM_EINVAL, "bad schedule table");
+  for (int32_t i = 0; i < n_entries; ++i) {
+    if (n_pad[i] <= 0 || (i > 0 && n_pad[i] <= n_pad[i - 1])) return fail(ctx, NOLSM_EINVAL, "table sizes must ascend");
+    if (schedule[i] != NOLSM_SCHEDULE_PERSISTENT && schedule[i] != NOLSM_SCHEDULE_PER_PRODUCT &&
+        schedule[i] != NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED)
+      return fail(ctx, NOLSM_EINVAL, "table schedules must be PERSISTENT, PER_PRODUCT or PERSISTENT_INTERLEAVED");
+  }
+  ctx->sched_pad.assign(n_pad, n_pad + n_entries);
+  ctx->sched_kind.assign(schedule, schedule + n_entries);
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_last_schedule(const nolsm_ctx* ctx, int32_t* schedule, int32_t* persistent_blocks) {
+  if (!ctx || !ctx->have_sign) return NOLSM_ENOTBUILT;
+  if (schedule) *schedule = ctx->last_schedule;
+  if (persistent_blocks) *persistent_blocks = ctx->n_queue;
   return NOLSM_OK;
 }
 

@@ -216,6 +216,14 @@ struct nolsm_ctx {
   float* d_rowr = nullptr;      // Gershgorin radius per row (same layout)
   float* d_feat_static = nullptr;   // mu-independent features (n_blocks x 32)
 
+  // schedule of the mixed-precision products (nolsm_set_schedule_table): per n_pad, the measured best
+  // schedule; a sign evaluation whose blocks prefer different schedules runs the persistent kernel on
+  // the queue d_queue[0, n_queue) and per-product launches on the remaining blocks
+  std::vector<int32_t> sched_pad, sched_kind;
+  int32_t* d_queue = nullptr;
+  int32_t n_queue = 0;                  // blocks of the persistent launch (n_blocks: all of them)
+  int32_t last_schedule = -1;           // schedule the last sign evaluation ran (nolsm_schedule, or -2: split)
+
   double last_mu = 0.0;
   nolsm_sign_stats last_stats{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;

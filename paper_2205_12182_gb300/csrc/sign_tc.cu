@@ -550,7 +550,15 @@ struct PairParams {
   int detect_divergence;
   int n_blocks;
   int fp8_iters;                // experiment: iterations whose outputs are rounded to FP8 E4M3 values
+  const int32_t* queue_map;     // blocks this launch takes, in queue order (NULL: every block, 0..n_blocks)
+  int n_queue;                  // entries of the queue
 };
+
+// The q-th block of a persistent launch's queue, or n_blocks once the queue is exhausted.
+__device__ __forceinline__ int queue_block(const PairParams& p, int q) {
+  if (q >= p.n_queue) return p.n_blocks;
+  return p.queue_map ? p.queue_map[q] : q;
+}
 
 struct PairTile {
   int16_t m0, n0, tn, pad;
@@ -813,7 +821,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PAIR_THREADS, 1) ns_
 
   for (;;) {
     if (rank == 0 && threadIdx.x == 0) {
-      const int b = atomicAdd(&p.flags->queue, 1);
+      const int b = queue_block(p, atomicAdd(&p.flags->queue, 1));
       ctl0->block = b;
       ctl1->block = b;
     }
@@ -1086,7 +1094,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PAIR_THREADS, 1) ns_
   // rank 0 claims the next block for slot k and writes it into both CTAs (read after a barrier)
   auto claim = [&](int k) {
     if (rank == 0 && threadIdx.x == 0) {
-      const int nb = atomicAdd(&p.flags->queue, 1);
+      const int nb = queue_block(p, atomicAdd(&p.flags->queue, 1));
       ctl0->block[k] = nb;
       ctl1->block[k] = nb;
     }
@@ -2458,6 +2466,8 @@ cudaError_t launch_ns_pair(nolsm_ctx* ctx, double mu, bool interleaved) {
   p.detect_divergence = ctx->opt.bounds != NOLSM_BOUNDS_GERSHGORIN;
   p.n_blocks = ctx->n_blocks;
   p.fp8_iters = ctx->opt.fp8_iters;
+  p.queue_map = ctx->n_queue < ctx->n_blocks ? ctx->d_queue : nullptr;
+  p.n_queue = ctx->n_queue;
   const bool bf16 = ctx->opt.precision == NOLSM_PREC_MIXED_BF16;
   if (ctx->pair_clusters <= 0) {
     cudaLaunchConfig_t cfg = {};
@@ -2473,14 +2483,14 @@ cudaError_t launch_ns_pair(nolsm_ctx* ctx, double mu, bool interleaved) {
   }
   if (interleaved) {
     // two slots per cluster: enough clusters for every block to start in the first round
-    const int clusters = std::max(1, std::min(ctx->pair_clusters, (ctx->n_blocks + 1) / 2));
+    const int clusters = std::max(1, std::min(ctx->pair_clusters, (ctx->n_queue + 1) / 2));
     if (bf16)
       ns_pair2_kernel<__nv_bfloat16><<<2 * clusters, PAIR_THREADS, PAIR2_SMEM, ctx->stream>>>(p);
     else
       ns_pair2_kernel<__half><<<2 * clusters, PAIR_THREADS, PAIR2_SMEM, ctx->stream>>>(p);
     return cudaGetLastError();
   }
-  const int clusters = std::max(1, std::min(ctx->pair_clusters, ctx->n_blocks));
+  const int clusters = std::max(1, std::min(ctx->pair_clusters, ctx->n_queue));
   const bool q8 = p.fp8_iters > 0;
   if (bf16 && q8)
     ns_pair_kernel<__nv_bfloat16, true><<<2 * clusters, PAIR_THREADS, PAIR_SMEM, ctx->stream>>>(p);

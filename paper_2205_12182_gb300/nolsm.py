@@ -32,7 +32,7 @@ FUNCTIONS = ["nolsm_default_options", "nolsm_create", "nolsm_build_submatrices",
              "nolsm_band_energy_noalloc",
              "nolsm_block_features", "nolsm_block_lanczos", "nolsm_mlp_create", "nolsm_mlp_get_params",
              "nolsm_mlp_gradient", "nolsm_mlp_adam", "nolsm_mlp_predict", "nolsm_mlp_destroy", "nolsm_set_predictor",
-             "nolsm_keep_bounds", "nolsm_set_block_bounds", "nolsm_combine_blocks", "nolsm_last_error", "nolsm_destroy"]
+             "nolsm_keep_bounds", "nolsm_set_block_bounds", "nolsm_set_schedule_table", "nolsm_last_schedule", "nolsm_combine_blocks", "nolsm_last_error", "nolsm_destroy"]
 
 PHASES = ("gather", "factor", "inverse", "congruence", "build_rest", "sign_setup", "products", "slab", "density",
           "energy", "factor_trsm", "factor_update")
@@ -122,6 +122,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "nolsm_mlp_destroy": (None, [P]),
         "nolsm_set_predictor": (i32, [P, P]),
         "nolsm_keep_bounds": (i32, [P, i32]),
+        "nolsm_set_schedule_table": (i32, [P, i32, P, P]),
+        "nolsm_last_schedule": (i32, [P, pi32, pi32]),
         "nolsm_set_block_bounds": (i32, [P, P, i32]),
         "nolsm_combine_blocks": (i32, [C.POINTER(NolsmCsr), i32, P, P, P, P, i32, i32, P, P, i32, pi32, P, P, P, P, P,
                                        P, P]),
@@ -399,6 +401,32 @@ def combine_blocks(system, criterion=COMBINE_CUBIC, pn=None, max_dim=4096):
                                extra_idx=r["extra_idx"]), r
 
 
+def nolsm_set_schedule_table(ctx, n_pad, schedule):
+    """Measured schedule per n_pad for SCHEDULE_AUTO (host arrays; empty removes the table)."""
+    n_pad = np.ascontiguousarray(n_pad, np.int32)
+    schedule = np.ascontiguousarray(schedule, np.int32)
+    _check(ctx, _lib.nolsm_set_schedule_table(ctx, int(n_pad.shape[0]), _ptr(n_pad) if n_pad.size else None,
+                                              _ptr(schedule) if schedule.size else None))
+
+
+def nolsm_last_schedule(ctx):
+    """(schedule of the last sign evaluation, or -2 for a split one; blocks of its persistent launch)."""
+    sc, nq = C.c_int32(), C.c_int32()
+    _check(ctx, _lib.nolsm_last_schedule(ctx, C.byref(sc), C.byref(nq)))
+    return sc.value, nq.value
+
+
+SCHEDULE_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "schedule_gb300.json")
+
+
+def load_schedule_table(path: str = SCHEDULE_TABLE):
+    """(n_pad, schedule) of a table written by paper_2205_12182_gb300.autotune."""
+    import json
+    with open(path) as f:
+        d = json.load(f)
+    return np.asarray(d["n_pad"], np.int32), np.asarray(d["schedule"], np.int32)
+
+
 def nolsm_keep_bounds(ctx, steps=64):
     _check(ctx, _lib.nolsm_keep_bounds(ctx, int(steps)))
 
@@ -569,6 +597,14 @@ class Nolsm:
 
     def keep_bounds(self, steps=64):
         nolsm_keep_bounds(self.ctx, steps)
+
+    def set_schedule_table(self, table=None):
+        """The autotuner's table ((n_pad, schedule) arrays, or the committed file when None)."""
+        n_pad, sched = load_schedule_table() if table is None else table
+        nolsm_set_schedule_table(self.ctx, n_pad, sched)
+
+    def last_schedule(self):
+        return nolsm_last_schedule(self.ctx)
 
     def set_block_bounds(self, bounds):
         nolsm_set_block_bounds(self.ctx, bounds, MEM_HOST if isinstance(bounds, np.ndarray) else MEM_DEVICE)

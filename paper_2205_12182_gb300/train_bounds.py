@@ -1,7 +1,8 @@
 """Train the spectral-bound predictor on submatrix spectra that the method itself computes.
 
-For every training system (seeded water boxes with the 8 A neighbourhood, held apart from the
-benchmark seeds) the library builds the submatrices in FP32, and for a set of chemical potentials
+For every training system -- seeded water boxes with the 8 A neighbourhood and protein-like
+globules (the 10-200-atom blocks of 30,000-atom systems, n_b 160-2,700), all held apart from the
+benchmark seeds -- the library builds the submatrices in FP32, and for a set of chemical potentials
 it evaluates the sign and then runs Lanczos:
 
 * on A0 (64 steps): lambda_min, lambda_max -- the targets of outputs 0 and 1;
@@ -30,7 +31,9 @@ if ROOT not in sys.path:
 
 TRAIN_SEEDS_4096 = (100, 101, 102, 103, 104)
 TRAIN_SEEDS_1000 = tuple(range(110, 120))
+TRAIN_SEEDS_GLOBULE = tuple(range(100, 112))
 HELDOUT = ((16, 11), (16, 200), (12, 201))
+HELDOUT_GLOBULE = (200, 201, 202)
 MU_OFFSETS = (-0.05, -0.02, -0.01, 0.0, 0.01, 0.02, 0.05)
 
 
@@ -86,10 +89,11 @@ def train(nolsm, x, y, epochs=40, batch=512, lr=2e-3, seed=0, log=print):
 
 
 def iteration_study(nolsm, bp, system, mu):
-    """Average NS iterations and accuracy proxies at mu for Gershgorin, Lanczos and learned bounds."""
+    """Average NS iterations and accuracy proxies at mu for Gershgorin bounds (the library's default
+    lower bound 0.02, and the uninformed 1e-3), Lanczos and learned bounds."""
     out = {}
-    for name, kw in (("gershgorin", {}), ("lanczos", {"bounds": nolsm.BOUNDS_LANCZOS}),
-                     ("learned", {"bounds": nolsm.BOUNDS_LEARNED})):
+    for name, kw in (("gershgorin", {}), ("gershgorin_lower_bound_1e-3", {"lower_bound": 1e-3}),
+                     ("lanczos", {"bounds": nolsm.BOUNDS_LANCZOS}), ("learned", {"bounds": nolsm.BOUNDS_LEARNED})):
         lib = nolsm.Nolsm(precision=nolsm.PREC_MIXED_FP16, **kw).build(system)
         if name == "learned":
             lib.set_predictor(bp)
@@ -100,11 +104,22 @@ def iteration_study(nolsm, bp, system, mu):
     return out
 
 
+def _globule(seed):
+    from synth import protein_globule
+    return protein_globule(seed, name=f"globule30000-s{seed}")
+
+
+def globules(seeds):
+    """Globule systems generated in parallel on the host cores (a spawn pool: numpy work only)."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(len(seeds), os.cpu_count() or 1)) as pool:
+        return pool.map(_globule, list(seeds))
+
+
 def main():
     import torch
     from paper_2205_12182_gb300.build import build
     build()
-    from paper_2205_12182_gb300 import nolsm
     from synth import water_box
 
     ap = argparse.ArgumentParser()
@@ -112,8 +127,12 @@ def main():
     ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--quick", action="store_true", help="two small training systems (smoke run)")
     a = ap.parse_args()
-    torch.cuda.set_device(0)
     t0 = time.time()
+    g_train = globules(TRAIN_SEEDS_GLOBULE[:1] if a.quick else TRAIN_SEEDS_GLOBULE)
+    g_held = [] if a.quick else globules(HELDOUT_GLOBULE)
+    print(f"globules generated ({time.time() - t0:.1f} s)", flush=True)
+    from paper_2205_12182_gb300 import nolsm
+    torch.cuda.set_device(0)
     xs, ys = [], []
     specs = [(10, s) for s in TRAIN_SEEDS_1000[:2]] if a.quick else \
         [(16, s) for s in TRAIN_SEEDS_4096] + [(10, s) for s in TRAIN_SEEDS_1000]
@@ -123,9 +142,15 @@ def main():
         xs.append(x)
         ys.append(y)
         print(f"system side={side} seed={seed}: {x.shape[0]} samples ({time.time() - t0:.1f} s)", flush=True)
+    for g in g_train:
+        x, y, _ = system_samples(nolsm, g, seed=len(xs))
+        xs.append(x)
+        ys.append(y)
+        print(f"system {g.name}: {x.shape[0]} samples ({time.time() - t0:.1f} s)", flush=True)
     x, y = torch.cat(xs), torch.cat(ys)
     bp, hist = train(nolsm, x, y, epochs=a.epochs)
-    report = {"train_samples": int(x.shape[0]), "train_systems": [list(s) for s in specs], "loss": hist[-1],
+    report = {"train_samples": int(x.shape[0]),
+              "train_systems": [list(s) for s in specs] + [g.name for g in g_train], "loss": hist[-1],
               "heldout": []}
     for side, seed in ([] if a.quick else HELDOUT):
         sysm = water_box(side, seed, neighbourhood=8.0)
@@ -134,6 +159,14 @@ def main():
         err = (pred - yh).abs().mean(0).cpu().numpy()
         study = iteration_study(nolsm, bp, sysm, mu0)
         report["heldout"].append({"side": side, "seed": seed, "mu": mu0,
+                                  "mae": {"lambda_min": float(err[0]), "lambda_max": float(err[1]),
+                                          "log10_dist": float(err[2])}, "iterations": study})
+        print(json.dumps(report["heldout"][-1]), flush=True)
+    for g in g_held:
+        xh, yh, mu0 = system_samples(nolsm, g, n_random_mu=0, seed=0)
+        err = (bp.predict(xh) - yh).abs().mean(0).cpu().numpy()
+        study = iteration_study(nolsm, bp, g, mu0)
+        report["heldout"].append({"system": g.name, "mu": mu0,
                                   "mae": {"lambda_min": float(err[0]), "lambda_max": float(err[1]),
                                           "log10_dist": float(err[2])}, "iterations": study})
         print(json.dumps(report["heldout"][-1]), flush=True)
