@@ -109,3 +109,29 @@ def set_mu_distributed(lib, n_electrons_global, tol_n=1e-3, max_steps=60, group=
                            lib.options.spin_factor)
     return bisect_shared(lambda mu: lib.sign_batch(mu)["n_electrons"], lambda v: allreduce_sum(v, group),
                          n_electrons_global, lo, hi, tol_n, max_steps, mu0=mu0)
+
+
+def lpt_partition(costs, n_ranks):
+    """Blocks to ranks by longest processing time first: blocks in decreasing cost (ties by index),
+    each to the rank with the smallest load so far (ties to the lower rank).  Returns one ascending
+    array of block indices per rank."""
+    import heapq
+    costs = np.asarray(costs, np.float64)
+    order = sorted(range(len(costs)), key=lambda b: (-costs[b], b))
+    heap = [(0.0, r) for r in range(n_ranks)]
+    parts = [[] for _ in range(n_ranks)]
+    for b in order:
+        load, r = heapq.heappop(heap)
+        parts[r].append(b)
+        heapq.heappush(heap, (load + float(costs[b]), r))
+    return [np.array(sorted(p), dtype=np.int64) for p in parts]
+
+
+def block_cost_estimate(system):
+    """Predicted cost of every block for the partition: (own columns + extra indices)^3, an upper
+    bound of n_b^3 that needs no index sets (the products cost 2 n_b^3 per product)."""
+    bp = np.asarray(system.blk_ptr, np.int64)
+    n = np.diff(bp).astype(np.float64)
+    if system.extra_ptr is not None:
+        n = n + np.diff(np.asarray(system.extra_ptr, np.int64))
+    return n ** 3

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 import torch.multiprocessing as mp
 
-from paper_2205_12182_gb300.distributed import aufbau_point, bisect_shared
+from paper_2205_12182_gb300.distributed import aufbau_point, bisect_shared, lpt_partition
 
 
 def _worker(rank, world, port, out):
@@ -72,3 +72,60 @@ def test_aufbau_point_rule():
 def test_bracket_error():
     with pytest.raises(RuntimeError):
         bisect_shared(lambda m: 0.0, lambda v: v, 10.0, -1.0, 1.0, 1e-6, max_steps=80)
+
+
+def test_lpt_partition_rule():
+    """Every block once; the greedy rule replayed by hand on a small case; balance within LPT's bound
+    (max load <= (4/3 - 1/(3 m)) x the optimum, here against the lower bound max(total / m, max cost))."""
+    costs = np.array([7.0, 3.0, 5.0, 5.0, 2.0, 8.0, 1.0])
+    parts = lpt_partition(costs, 3)
+    assert sorted(np.concatenate(parts).tolist()) == list(range(7))
+    # decreasing cost: 8 (b5) -> r0, 7 (b0) -> r1, 5 (b2) -> r2, 5 (b3) -> r2? no: loads 8, 7, 5 -> r2 has 5,
+    # so b3 -> r2 (load 5 is the smallest) making 10; 3 (b1) -> r1 (7 -> 10); 2 (b4) -> r0 (8 -> 10);
+    # 1 (b6) -> r0 (10, ties to the lower rank) -> 11
+    assert [p.tolist() for p in parts] == [[4, 5, 6], [0, 1], [2, 3]]
+    rng = np.random.default_rng(0)
+    for m in (2, 3, 5):
+        c = rng.uniform(1, 100, size=50) ** 1.5
+        loads = [c[p].sum() for p in lpt_partition(c, m)]
+        assert max(loads) <= (4 / 3 - 1 / (3 * m)) * max(c.sum() / m, c.max()) + 1e-9
+
+
+def _worker_lpt(rank, world, port, out):
+    import torch.distributed as dist
+    from oracle.nolsm import NolsmOracle
+    from synth import make_config
+    from paper_2205_12182_gb300.distributed import allreduce_minmax, allreduce_sum, block_cost_estimate
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    s = make_config(1)
+    mine = lpt_partition(block_cost_estimate(s) + np.arange(s.n_blocks), world)[rank]
+    o = NolsmOracle.from_system(s, blocks=mine).prepare()
+    lo, hi = o.spectral_bounds()
+    lo, hi = allreduce_minmax(lo - 1e-3, hi + 1e-3)
+    mu, n, steps = bisect_shared(lambda m: 2 * o.electron_count(m), allreduce_sum, s.n_electrons, lo, hi, 1e-3)
+    e = allreduce_sum([o.band_energy_of_mu(mu)])[0]
+    out[rank] = (mu, n, steps, e, mine.tolist())
+    dist.destroy_process_group()
+
+
+def test_lpt_ranks_agree_with_single_process():
+    """One system partitioned over two gloo ranks by LPT: the shared bisection and the summed band
+    energy equal one process over every block; the ranks' blocks cover the system once."""
+    from oracle.nolsm import NolsmOracle
+    from synth import make_config
+    world = 2
+    mgr = mp.Manager()
+    out = mgr.dict()
+    port = 29600 + os.getpid() % 1000
+    mp.start_processes(_worker_lpt, args=(world, port, out), nprocs=world, join=True, start_method="spawn")
+    s = make_config(1)
+    assert sorted(out[0][4] + out[1][4]) == list(range(s.n_blocks))
+    o = NolsmOracle.from_system(s).prepare()
+    lo, hi = o.spectral_bounds()
+    mu1, n1, st1 = bisect_shared(lambda m: 2 * o.electron_count(m), lambda v: v, s.n_electrons, lo - 1e-3, hi + 1e-3, 1e-3)
+    for r in range(world):
+        assert out[r][0] == pytest.approx(mu1, abs=1e-12) and out[r][2] == st1
+        assert out[r][1] == pytest.approx(n1, rel=1e-12)
+        assert out[r][3] == pytest.approx(o.band_energy_of_mu(mu1), rel=1e-12)
