@@ -172,3 +172,20 @@ def test_measured_tables_are_usable():
         assert r["n_blocks"] >= 1
     assert batch_size(4096) == 5 and batch_size(64) == 16384
     assert all(4 <= batch_size(n) and batch_size(n) * n * n <= max(1e8, 4 * n * n) for n in range(64, 4097, 64))
+
+
+def test_committed_schedule_table_is_usable():
+    """The autotuner's committed schedule table: ascending n_pad from 128 to 4,096, schedules the
+    library accepts in a table (persistent, per-product, persistent interleaved), one timing per
+    schedule and size, and the recorded choice the fastest of them."""
+    import json
+    d = json.load(open(nl.SCHEDULE_TABLE))
+    n_pad, sched = nl.load_schedule_table()
+    assert n_pad[0] == 128 and n_pad[-1] == 4096 and np.all(np.diff(n_pad) > 0)
+    assert set(sched.tolist()) <= {nl.SCHEDULE_PERSISTENT, nl.SCHEDULE_PER_PRODUCT, nl.SCHEDULE_PERSISTENT_INTERLEAVED}
+    kind = {"persistent": nl.SCHEDULE_PERSISTENT, "interleaved": nl.SCHEDULE_PERSISTENT_INTERLEAVED,
+            "per_product": nl.SCHEDULE_PER_PRODUCT}
+    for i in range(len(n_pad)):
+        times = {k: d["ms"][k][i] for k in kind}
+        assert all(t > 0 for t in times.values())
+        assert sched[i] == kind[min(times, key=times.get)]
