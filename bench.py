@@ -596,10 +596,11 @@ def combination(nolsm, predictor, system, checks=None, steps=2, evals=3, tag="co
 
 def globule_schedules(nolsm, g, evals=3):
     """The ragged globule's products (n_b 163-2,678) under each product schedule: the built-in AUTO
-    rule, AUTO with the autotuner's measured table (a split evaluation: the bins that prefer the
-    persistent kernel in one persistent launch, the rest in per-product launches), and every single
-    schedule.  Products ms per sign evaluation (stage timer) at the converged mu, Gershgorin bounds
-    with lower bound 0.02."""
+    rule, AUTO with the autotuner's measured table and times (the predicted fastest of the single
+    schedules and the split), the table's per-bin choice alone (a split evaluation: the bins that
+    prefer the persistent kernel in one persistent launch, the rest in per-product launches), and
+    every single schedule.  Products ms per sign evaluation (stage timer) at the converged mu,
+    Gershgorin bounds with lower bound 0.02."""
     import torch
     try:
         table = nolsm.load_schedule_table()
@@ -610,6 +611,8 @@ def globule_schedules(nolsm, g, evals=3):
              ("interleaved", nolsm.SCHEDULE_PERSISTENT_INTERLEAVED, None)]
     if table is not None:
         cases.insert(1, ("auto_measured_table", nolsm.SCHEDULE_AUTO, table))
+        # the table's per-bin choice without its times: always the split evaluation
+        cases.insert(2, ("split_by_table_bins", nolsm.SCHEDULE_AUTO, table[:2]))
     out = {"workload": f"protein-like globule, {g.n_atoms} atoms, {g.n_blocks} blocks", "evaluations": evals,
            "table": None if table is None else "paper_2205_12182_gb300/weights/schedule_gb300.json"}
     mu = None

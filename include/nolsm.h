@@ -293,13 +293,21 @@ nolsm_status nolsm_solve_chunked(nolsm_ctx* ctx, const nolsm_csr* H, const nolsm
 /* Measured schedule table for NOLSM_SCHEDULE_AUTO (the library's autotuner,
  * paper_2205_12182_gb300/autotune.py, writes one from timings of the products at each n_pad): entry i
  * says which schedule ran the products of blocks with n_pad[i-1] < n_pad <= n_pad[i] fastest (the
- * first entry covers everything below, the last everything above).  With a table, every sign
- * evaluation takes the blocks whose entry is PERSISTENT or PERSISTENT_INTERLEAVED into one persistent
- * launch (largest first; the variant preferred by the larger share of their n_pad^3) and runs the
- * others, and every block above n_pad 4096, with per-product launches after it.  n_pad ascending and
- * positive, schedule one of PERSISTENT, PER_PRODUCT, PERSISTENT_INTERLEAVED; n_entries = 0 removes
- * the table (AUTO is then persistent while every n_pad < 1024).  Copied.  Errors: EINVAL. */
-nolsm_status nolsm_set_schedule_table(nolsm_ctx* ctx, int32_t n_entries, const int32_t* n_pad, const int32_t* schedule);
+ * first entry covers everything below, the last everything above).  ms_per_block (NULL, or
+ * 3 n_entries values: per entry the products' time per block and sign evaluation under PERSISTENT,
+ * PER_PRODUCT and PERSISTENT_INTERLEAVED, measured in full batches) lets AUTO predict a batch:
+ *  - without times, every sign evaluation takes the blocks whose entry is PERSISTENT or
+ *    PERSISTENT_INTERLEAVED into one persistent launch (largest first; the variant preferred by the
+ *    larger share of their n_pad^3) and runs the others, and every block above n_pad 4096, with
+ *    per-product launches after it (a split evaluation);
+ *  - with times, AUTO predicts the batch's products time under each single schedule (the sum of its
+ *    blocks' times) and under that split (plus the persistent launch's tail: its last block alone,
+ *    about its time per block times the clusters) and runs the smallest.
+ * n_pad ascending and positive, schedule one of PERSISTENT, PER_PRODUCT, PERSISTENT_INTERLEAVED, times
+ * positive; n_entries = 0 removes the table (AUTO is then persistent while every n_pad < 1024).
+ * Copied.  Errors: EINVAL. */
+nolsm_status nolsm_set_schedule_table(nolsm_ctx* ctx, int32_t n_entries, const int32_t* n_pad, const int32_t* schedule,
+                                      const double* ms_per_block);
 
 /* Schedule of the last sign evaluation: *schedule = PERSISTENT, PERSISTENT_INTERLEAVED or PER_PRODUCT
  * when every block ran it, -2 when the evaluation was split (a persistent launch, then per-product

@@ -652,16 +652,49 @@ nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out) 
       // per block the entry of the smallest tabulated n_pad >= its own (the last one beyond); the
       // persistent variant is the one preferred by the larger share of the queue's n_pad^3
       double w_plain = 0.0, w_inter = 0.0;
+      std::vector<size_t> entry((size_t)ctx->n_blocks);
       for (int32_t b = 0; b < ctx->n_blocks; ++b) {
         const int np = ctx->h_blocks[b].n_pad;
         size_t k = 0;
         while (k + 1 < ctx->sched_pad.size() && ctx->sched_pad[k] < np) ++k;
+        entry[b] = k;
         const int kind = ctx->sched_kind[k];
         if (np > kMaxDim || kind == NOLSM_SCHEDULE_PER_PRODUCT) continue;
         queue.push_back(b);
         (kind == NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED ? w_inter : w_plain) += (double)np * np * np;
       }
       interleaved = w_inter > w_plain;
+      if (!ctx->sched_ms.empty() && !queue.empty()) {
+        // With measured times: predicted products time of the batch under each single schedule (the
+        // sum of the blocks' per-block times, measured in full batches) and under the split (each
+        // block at its entry's best, plus the tail of the persistent launch: its last block runs on
+        // one cluster while the others idle, about that block's time on the whole GPU times the
+        // clusters).  The smallest prediction decides.
+        const auto ms = [&](int32_t b, int s) { return ctx->sched_ms[3 * entry[b] + s]; };
+        const int ncl = std::max(1, ctx->pair_clusters > 0 ? ctx->pair_clusters : ctx->num_sms / 2);
+        double t_p = 0.0, t_pp = 0.0, t_i = 0.0, t_split = 0.0, tail = 0.0;
+        std::vector<char> in_q((size_t)ctx->n_blocks, 0);
+        for (int32_t b : queue) in_q[b] = 1;
+        for (int32_t b = 0; b < ctx->n_blocks; ++b) {
+          t_p += ms(b, 0);
+          t_pp += ms(b, 1);
+          t_i += ms(b, 2);
+          const int qs = interleaved ? 2 : 0;
+          t_split += in_q[b] ? ms(b, qs) : ms(b, 1);
+          if (in_q[b]) tail = std::max(tail, ms(b, qs) * ncl);
+        }
+        const bool all_fit = max_pad <= kMaxDim;
+        const double best_single = all_fit ? std::min(t_pp, std::min(t_p, t_i)) : t_pp;
+        if ((int32_t)queue.size() < ctx->n_blocks && t_split + tail < best_single) {
+          // keep the split
+        } else {
+          queue.clear();
+          if (all_fit && best_single < t_pp) {
+            interleaved = t_i < t_p;
+            for (int32_t b = 0; b < ctx->n_blocks; ++b) queue.push_back(b);
+          }
+        }
+      }
       // largest blocks first: the queue's tail is then made of short jobs
       std::stable_sort(queue.begin(), queue.end(),
                        [&](int32_t a, int32_t c) { return ctx->h_blocks[a].n_pad > ctx->h_blocks[c].n_pad; });
@@ -886,7 +919,7 @@ nolsm_status nolsm_own_diagonal(const nolsm_ctx* ctx, int64_t* count, float* out
 }
 
 nolsm_status nolsm_set_schedule_table(nolsm_ctx* ctx, int32_t n_entries, const int32_t* n_pad,
-                                      const int32_t* schedule) {
+                                      const int32_t* schedule, const double* ms_per_block) {
   if (!ctx) return NOLSM_EINVAL;
   if (n_entries < 0 || (n_entries > 0 && (!n_pad || !schedule))) return fail(ctx, NOLSM_EINVAL, "bad schedule table");
   for (int32_t i = 0; i < n_entries; ++i) {
@@ -895,8 +928,14 @@ nolsm_status nolsm_set_schedule_table(nolsm_ctx* ctx, int32_t n_entries, const i
         schedule[i] != NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED)
       return fail(ctx, NOLSM_EINVAL, "table schedules must be PERSISTENT, PER_PRODUCT or PERSISTENT_INTERLEAVED");
   }
+  if (ms_per_block)
+    for (int32_t i = 0; i < 3 * n_entries; ++i)
+      if (!(ms_per_block[i] > 0) || !std::isfinite(ms_per_block[i]))
+        return fail(ctx, NOLSM_EINVAL, "table times must be positive and finite");
   ctx->sched_pad.assign(n_pad, n_pad + n_entries);
   ctx->sched_kind.assign(schedule, schedule + n_entries);
+  if (ms_per_block) ctx->sched_ms.assign(ms_per_block, ms_per_block + 3 * n_entries);
+  else ctx->sched_ms.clear();
   return NOLSM_OK;
 }
 

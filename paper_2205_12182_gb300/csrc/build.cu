@@ -908,6 +908,7 @@ __global__ void __launch_bounds__(NW * 32) trinv_kernel(const BlockDesc* __restr
 // a block row has few column blocks), operand chunks double-buffered in shared memory with cp.async,
 // the four partial tiles summed in shared memory (which also makes the k-sum two-level).
 constexpr int kInvWarps = 4;
+static_assert(32 / kInvWarps == 8, "the product loop of trinv_tile_kernel takes 8 values of k per warp");
 
 __device__ __forceinline__ void cp_async16_b(void* smem_dst, const void* gsrc) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
@@ -983,11 +984,23 @@ __global__ void __launch_bounds__(kInvWarps * 32, 4) trinv_tile_kernel(const Blo
           cp_async_wait_group<0>();
         }
         __syncthreads();
+        // this warp's 8 values of k in two halves of 4: X_kc in registers, each row's L_ik as one
+        // 16-byte broadcast (every accumulator still takes its 8 terms in k order)
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+          float bv[4];
 #pragma unroll
-        for (int kk = 0; kk < 32 / kInvWarps; ++kk) {
-          const float bv = Bs[buf][kw + kk][lane];
+          for (int j = 0; j < 4; ++j) bv[j] = Bs[buf][kw + 4 * h + j][lane];
 #pragma unroll
-          for (int r = 0; r < 32; ++r) acc[r] = fmaf(As[buf][r][kw + kk], bv, acc[r]);
+          for (int r = 0; r < 32; ++r) {
+            const float4 a = *reinterpret_cast<const float4*>(&As[buf][r][kw + 4 * h]);
+            float v = acc[r];
+            v = fmaf(a.x, bv[0], v);
+            v = fmaf(a.y, bv[1], v);
+            v = fmaf(a.z, bv[2], v);
+            v = fmaf(a.w, bv[3], v);
+            acc[r] = v;
+          }
         }
         __syncthreads();
       }

@@ -220,6 +220,7 @@ struct nolsm_ctx {
   // schedule; a sign evaluation whose blocks prefer different schedules runs the persistent kernel on
   // the queue d_queue[0, n_queue) and per-product launches on the remaining blocks
   std::vector<int32_t> sched_pad, sched_kind;
+  std::vector<double> sched_ms;         // per entry: ms per block of PERSISTENT, PER_PRODUCT, INTERLEAVED (or empty)
   int32_t* d_queue = nullptr;
   int32_t n_queue = 0;                  // blocks of the persistent launch (n_blocks: all of them)
   int32_t last_schedule = -1;           // schedule the last sign evaluation ran (nolsm_schedule, or -2: split)

@@ -122,7 +122,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "nolsm_mlp_destroy": (None, [P]),
         "nolsm_set_predictor": (i32, [P, P]),
         "nolsm_keep_bounds": (i32, [P, i32]),
-        "nolsm_set_schedule_table": (i32, [P, i32, P, P]),
+        "nolsm_set_schedule_table": (i32, [P, i32, P, P, P]),
         "nolsm_last_schedule": (i32, [P, pi32, pi32]),
         "nolsm_set_block_bounds": (i32, [P, P, i32]),
         "nolsm_combine_blocks": (i32, [C.POINTER(NolsmCsr), i32, P, P, P, P, i32, i32, P, P, i32, pi32, P, P, P, P, P,
@@ -401,12 +401,15 @@ def combine_blocks(system, criterion=COMBINE_CUBIC, pn=None, max_dim=4096):
                                extra_idx=r["extra_idx"]), r
 
 
-def nolsm_set_schedule_table(ctx, n_pad, schedule):
-    """Measured schedule per n_pad for SCHEDULE_AUTO (host arrays; empty removes the table)."""
+def nolsm_set_schedule_table(ctx, n_pad, schedule, ms_per_block=None):
+    """Measured schedule per n_pad for SCHEDULE_AUTO (host arrays; empty removes the table); optional
+    per-block times (n x 3: persistent, per-product, interleaved) for AUTO's prediction."""
     n_pad = np.ascontiguousarray(n_pad, np.int32)
     schedule = np.ascontiguousarray(schedule, np.int32)
+    ms = None if ms_per_block is None else np.ascontiguousarray(ms_per_block, np.float64).reshape(-1)
     _check(ctx, _lib.nolsm_set_schedule_table(ctx, int(n_pad.shape[0]), _ptr(n_pad) if n_pad.size else None,
-                                              _ptr(schedule) if schedule.size else None))
+                                              _ptr(schedule) if schedule.size else None,
+                                              _ptr(ms) if ms is not None and ms.size else None))
 
 
 def nolsm_last_schedule(ctx):
@@ -420,11 +423,15 @@ SCHEDULE_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weigh
 
 
 def load_schedule_table(path: str = SCHEDULE_TABLE):
-    """(n_pad, schedule) of a table written by paper_2205_12182_gb300.autotune."""
+    """(n_pad, schedule, ms per block of persistent / per-product / interleaved) of a table written by
+    paper_2205_12182_gb300.autotune (the batch times divided by the batch's blocks)."""
     import json
     with open(path) as f:
         d = json.load(f)
-    return np.asarray(d["n_pad"], np.int32), np.asarray(d["schedule"], np.int32)
+    blocks = np.asarray(d["blocks"], np.float64)
+    ms = np.stack([np.asarray(d["ms"][k], np.float64) / blocks for k in ("persistent", "per_product", "interleaved")],
+                  axis=1)
+    return np.asarray(d["n_pad"], np.int32), np.asarray(d["schedule"], np.int32), ms
 
 
 def nolsm_keep_bounds(ctx, steps=64):
@@ -599,9 +606,10 @@ class Nolsm:
         nolsm_keep_bounds(self.ctx, steps)
 
     def set_schedule_table(self, table=None):
-        """The autotuner's table ((n_pad, schedule) arrays, or the committed file when None)."""
-        n_pad, sched = load_schedule_table() if table is None else table
-        nolsm_set_schedule_table(self.ctx, n_pad, sched)
+        """The autotuner's table ((n_pad, schedule[, ms per block]) arrays, or the committed file when
+        None)."""
+        t = load_schedule_table() if table is None else table
+        nolsm_set_schedule_table(self.ctx, *t)
 
     def last_schedule(self):
         return nolsm_last_schedule(self.ctx)

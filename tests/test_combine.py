@@ -180,7 +180,8 @@ def test_committed_schedule_table_is_usable():
     schedule and size, and the recorded choice the fastest of them."""
     import json
     d = json.load(open(nl.SCHEDULE_TABLE))
-    n_pad, sched = nl.load_schedule_table()
+    n_pad, sched, ms = nl.load_schedule_table()
+    assert ms.shape == (len(n_pad), 3) and np.all(ms > 0)
     assert n_pad[0] == 128 and n_pad[-1] == 4096 and np.all(np.diff(n_pad) > 0)
     assert set(sched.tolist()) <= {nl.SCHEDULE_PERSISTENT, nl.SCHEDULE_PER_PRODUCT, nl.SCHEDULE_PERSISTENT_INTERLEAVED}
     kind = {"persistent": nl.SCHEDULE_PERSISTENT, "interleaved": nl.SCHEDULE_PERSISTENT_INTERLEAVED,

@@ -81,11 +81,34 @@ def test_single_schedule_tables(nl, ragged, kind):
     np.testing.assert_array_equal(r["d"], ref["d"])
 
 
+def test_predicted_choice_with_times(nl, ragged):
+    """With per-block times AUTO predicts the batch: times that make the persistent launch's tail
+    cost more than the split saves give one schedule for every block; times that make the split
+    clearly cheaper keep it."""
+    n_pad = np.array([1024, 8192])
+    sched = np.array([nl.SCHEDULE_PERSISTENT, nl.SCHEDULE_PER_PRODUCT])
+    # persistent barely faster on the small bin, far slower on the large one: no split
+    ms = np.array([[1.00, 1.01, 1.2], [50.0, 5.0, 90.0]])
+    r = run(nl, ragged, table=(n_pad, sched, ms))
+    assert r["sched"] == (nl.SCHEDULE_PER_PRODUCT, 0)
+    # persistent far faster on the small bin (even with the tail of its last block): split
+    ms = np.array([[0.001, 1.0, 0.002], [50.0, 5.0, 90.0]])
+    r = run(nl, ragged, table=(n_pad, sched, ms))
+    assert r["sched"] == (-2, 8)
+    # every block fits the persistent kernel and it is predicted fastest: one persistent launch
+    ms = np.array([[0.001, 1.0, 0.002], [0.5, 5.0, 0.7]])
+    r = run(nl, ragged, table=(n_pad, np.array([nl.SCHEDULE_PERSISTENT, nl.SCHEDULE_PERSISTENT]), ms))
+    assert r["sched"] == (nl.SCHEDULE_PERSISTENT, 10)
+
+
 def test_bad_tables_are_refused(nl):
     lib = nl.Nolsm(precision=nl.PREC_MIXED_FP16)
     with pytest.raises(nl.NolsmError):
         nl.nolsm_set_schedule_table(lib.ctx, np.array([512, 256]), np.array([0, 1]))
     with pytest.raises(nl.NolsmError):
         nl.nolsm_set_schedule_table(lib.ctx, np.array([512]), np.array([nl.SCHEDULE_AUTO]))
+    with pytest.raises(nl.NolsmError):
+        nl.nolsm_set_schedule_table(lib.ctx, np.array([512]), np.array([nl.SCHEDULE_PERSISTENT]),
+                                    np.array([[1.0, -1.0, 1.0]]))
     nl.nolsm_set_schedule_table(lib.ctx, np.array([], np.int32), np.array([], np.int32))   # removes it
     lib.close()
