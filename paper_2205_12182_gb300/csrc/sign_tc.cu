@@ -2,11 +2,14 @@
 // path: FP16 (or BF16) operands, FP32 accumulation in tensor memory, sm_103a tcgen05.
 //
 // One persistent kernel per product over a tile list of the blocks still iterating.  Each CTA
-// (1 per SM, 192 threads) runs three roles:
-//   warp 0      TMA producer: 128x64 A boxes and 128x64 B boxes (128B swizzle) into a 4-stage ring
+// (1 per SM) runs three roles:
+//   warp 0      TMA producer: 128x64 A boxes and 128x64 B boxes (128B swizzle) into a ring of
+//               4 stages (blocks below n_pad 1024) or 3 (larger blocks)
 //   warp 1      MMA issuer (one thread): tcgen05.mma M=128, N=tile_n (<=256), K=16, into one of
 //               two TMEM accumulators (256 columns each); allocates and frees tensor memory
-//   warps 2..5  epilogue: tcgen05.ld of the accumulator, the iteration's arithmetic, stores
+//   warps 2..   epilogue: tcgen05.ld of the accumulator, the iteration's arithmetic, stores; one
+//               warp per TMEM lane quarter (small blocks) or two, each taking half of a tile's
+//               columns with double-buffered staging (larger blocks: long tiles back to back)
 // Phase 1 (T = X X^T, X symmetric) writes B = 1.5 a I - 0.5 a^3 T and adds ||T - I||_F^2 of the
 // tile to the block's accumulator; phase 2 writes X+ = X B^T.  All operands are symmetric, so
 // row-major storage is the K-major layout of both operands.
@@ -28,23 +31,17 @@ namespace {
 constexpr int TM = 128;           // tile rows (MMA M)
 constexpr int TN = 256;           // tile columns (MMA N, last tile of a block may be 128)
 constexpr int TK = 64;            // K per stage: one 128-byte swizzle atom of 16-bit elements
-constexpr int STAGES = 4;
 constexpr int A_BYTES = TM * TK * 2;          // 16 KB
 constexpr int B_BYTES = TN * TK * 2;          // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int TMEM_COLS = 512;                // two 256-column FP32 accumulators
-constexpr int NUM_THREADS = 192;
+constexpr int NUM_THREADS = 192;              // the refinement kernel's roles (producer, issuer, 4 epilogue warps)
 // per bin: loads of X0, X1, B (64 x 128 boxes), stores into them (32 x 32 boxes), and loads of the
 // refinement's four split slab pools hi0, lo0, hi1, lo1 (64 x 16 boxes)
 constexpr int kMapsPerBin = 10;
 constexpr int EPI_BUF_BYTES = 4096;           // one staging buffer: a 32 x 32 chunk and its transpose
-// shared memory: [stages | epilogue staging, NBUF buffers per epilogue warp | barriers | tables],
-// 1024-byte aligned base; the per-product kernel single-buffers (its tile table is large), the
-// persistent kernel double-buffers
-constexpr int EPI_OFF = STAGES * STAGE_BYTES;
-template <int NBUF> constexpr int bar_off() { return EPI_OFF + 4 * NBUF * EPI_BUF_BYTES; }
-template <int NBUF> constexpr int tab_off() { return bar_off<NBUF>() + 256; }
-template <int NBUF> constexpr int smem_bytes() { return 1024 /*align*/ + tab_off<NBUF>(); }
+// shared memory of the product kernels: [stages | epilogue staging, NBUF buffers per epilogue warp |
+// barriers | tables], 1024-byte aligned base (TcShape below, and the persistent kernels' PAIR_*)
 
 struct TcParams {
   const Tile* tiles;
@@ -319,24 +316,40 @@ struct TileInfo {
 };
 constexpr int MAX_LOCAL = 200;                // tiles per CTA per launch
 constexpr int INFO_BYTES = MAX_LOCAL * (int)sizeof(TileInfo);
-constexpr int TC_NBUF = 1;
-constexpr int SMEM_TOTAL = smem_bytes<TC_NBUF>() + INFO_BYTES;
-static_assert(SMEM_TOTAL <= 227 * 1024, "shared memory of the per-product kernel");
 
-template <typename T>
-__global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_constant__ TcParams p) {
+// Shapes of the per-product kernel: NST operand stages of 48 KB, EPIW epilogue warps (4: one per
+// tensor-memory lane quarter; 8: two per quarter, each taking half of a tile's columns) with NBUF
+// staging buffers each.  Shared memory: [stages | epilogue staging | barriers | tile table].
+template <int NST, int EPIW, int NBUF>
+struct TcShape {
+  static constexpr int epi_off = NST * STAGE_BYTES;
+  static constexpr int bar_off = epi_off + EPIW * NBUF * EPI_BUF_BYTES;
+  static constexpr int tab_off = bar_off + 256;
+  static constexpr int smem = 1024 + tab_off + INFO_BYTES;
+  static constexpr int threads = 64 + 32 * EPIW;
+  static_assert(smem <= 227 * 1024, "shared memory of the per-product kernel");
+  static_assert(8 * (2 * NST + 5) + 8 <= 256, "barrier area of the per-product kernel");
+  static_assert(EPIW == 4 || EPIW == 8, "one or two epilogue warps per lane quarter");
+};
+using TcNarrow = TcShape<4, 4, 1>;   // four 48 KB stages in flight, one epilogue warp per quarter
+using TcWide = TcShape<3, 8, 2>;     // three stages, two double-buffered epilogue warps per quarter
+
+template <typename T, int NST, int EPIW, int NBUF>
+__global__ void __launch_bounds__(TcShape<NST, EPIW, NBUF>::threads, 1)
+    ns_tc_kernel(const __grid_constant__ TcParams p) {
+  using L = TcShape<NST, EPIW, NBUF>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* stage_base = smem;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + bar_off<TC_NBUF>());
-  uint64_t* full_bar = bars;                       // [STAGES]
-  uint64_t* empty_bar = bars + STAGES;             // [STAGES]
-  uint64_t* tfull_bar = bars + 2 * STAGES;         // [2]
-  uint64_t* tempty_bar = bars + 2 * STAGES + 2;    // [2]
-  uint64_t* drain_bar = bars + 2 * STAGES + 4;     // [1]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::bar_off);
+  uint64_t* full_bar = bars;                    // [NST]
+  uint64_t* empty_bar = bars + NST;             // [NST]
+  uint64_t* tfull_bar = bars + 2 * NST;         // [2]
+  uint64_t* tempty_bar = bars + 2 * NST + 2;    // [2]
+  uint64_t* drain_bar = bars + 2 * NST + 4;     // [1]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NST + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  TileInfo* info = reinterpret_cast<TileInfo*>(smem + tab_off<TC_NBUF>());
+  TileInfo* info = reinterpret_cast<TileInfo*>(smem + L::tab_off);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // The list holds a block's tiles together.  Small blocks: each CTA takes a contiguous run, so one
@@ -351,7 +364,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_cons
   const int n_local = p.interleave
                           ? (span > (int)blockIdx.x ? (span - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0)
                           : p.tile_base + (int)(((int64_t)span * (blockIdx.x + 1)) / gridDim.x) - first;
-  for (int i = threadIdx.x; i < n_local; i += NUM_THREADS) {
+  for (int i = threadIdx.x; i < n_local; i += L::threads) {
     const Tile tl = p.tiles[first + i * step];
     const BlockDesc bd = p.blocks[tl.block];
     const NsState s = p.st[tl.block];
@@ -374,8 +387,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_cons
     info[i] = f;
   }
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
-    for (int a = 0; a < 2; ++a) { mbar_init(&tfull_bar[a], 1); mbar_init(&tempty_bar[a], 128); }
+    for (int s = 0; s < NST; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+    for (int a = 0; a < 2; ++a) { mbar_init(&tfull_bar[a], 1); mbar_init(&tempty_bar[a], 32 * EPIW); }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -416,7 +429,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_cons
           for (int h = 0; h < f.tn; h += TM) tma_load_2d(b_dst + h * TK * 2, mb, &full_bar[s], k0, f.row_b + h);
           armed |= 1u << s;
           arm_parity = (arm_parity & ~(1u << s)) | (ph << s);
-          if (++s == STAGES) { s = 0; ph ^= 1u; }
+          if (++s == NST) { s = 0; ph ^= 1u; }
         }
       }
       if (!ok) {
@@ -425,7 +438,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_cons
       }
       // every copy this thread issued must land before the CTA's shared memory is released
       volatile int never = 0;
-      for (int st = 0; st < STAGES; ++st)
+      for (int st = 0; st < NST; ++st)
         if (armed & (1u << st)) mbar_wait(&full_bar[st], (arm_parity >> st) & 1u, drain_budget, &never);
     }
   } else if (warp == 1) {
@@ -455,7 +468,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_cons
             umma_f16(d_tmem, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), idesc, (k0 | kk) != 0);
           }
           umma_commit(&empty_bar[s]);        // stage free once these MMAs have read it
-          if (++s == STAGES) { s = 0; ph ^= 1u; }
+          if (++s == NST) { s = 0; ph ^= 1u; }
         }
         if (!ok) break;
         umma_commit(&tfull_bar[acc]);        // accumulator ready for the epilogue
@@ -490,9 +503,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) ns_tc_kernel(const __grid_cons
       }
       tc_fence_after();
       T* out = pools[f.out_sel] + f.out_off;
-      float rsq = epi_tile<T, TC_NBUF, 64>(tmem_base + (uint32_t)(acc * TN), q, lane, out, ld, f.m0, f.n0, tn, p.phase, f.c1,
-                                       f.c3, p.tmaps + f.map_s, f.row_a - f.m0,
-                                       smem + EPI_OFF + (warp - 2) * TC_NBUF * EPI_BUF_BYTES, ebuf);
+      // EPIW == 8: warps 2..5 take the left half of the tile's columns, warps 6..9 the right half
+      const int hw = EPIW == 8 ? tn / 2 : tn, h0 = EPIW == 8 ? ((warp - 2) / 4) * hw : 0;
+      float rsq = epi_tile<T, NBUF, 64>(tmem_base + (uint32_t)(acc * TN + h0), q, lane, out, ld, f.m0, f.n0 + h0, hw,
+                                        p.phase, f.c1, f.c3, p.tmaps + f.map_s, f.row_a - f.m0,
+                                        smem + L::epi_off + (warp - 2) * NBUF * EPI_BUF_BYTES, ebuf);
       tc_fence_before();
       mbar_arrive(&tempty_bar[acc]);
       tph[acc] ^= 1u;
@@ -1851,7 +1866,7 @@ __global__ void __launch_bounds__(CG_THREADS, 1) cong_tc_kernel(const __grid_con
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + CG_BAR_OFF);
-  uint64_t* full_bar = bars;                       // [STAGES] TMA landed
+  uint64_t* full_bar = bars;                       // [CG_STAGES] TMA landed
   uint64_t* conv_bar = bars + CG_STAGES;           // [STAGES] split done
   uint64_t* empty_bar = bars + 2 * CG_STAGES;      // [STAGES] MMA done with the stage
   uint64_t* tfull_bar = bars + 3 * CG_STAGES;      // [2]
@@ -2154,9 +2169,15 @@ cudaError_t tc_prepare(nolsm_ctx* ctx) {
   if (e != cudaSuccess) return e;
   static bool attr_done = false;
   if (!attr_done) {
-    e = cudaFuncSetAttribute(ns_tc_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TOTAL);
+    e = cudaFuncSetAttribute(ns_tc_kernel<__half, 4, 4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcNarrow::smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(ns_tc_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TOTAL);
+    e = cudaFuncSetAttribute(ns_tc_kernel<__nv_bfloat16, 4, 4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TcNarrow::smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(ns_tc_kernel<__half, 3, 8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcWide::smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(ns_tc_kernel<__nv_bfloat16, 3, 8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TcWide::smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(ns_pair_kernel<__half, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_SMEM);
     if (e != cudaSuccess) return e;
@@ -2201,10 +2222,16 @@ cudaError_t launch_gemm_tc(nolsm_ctx* ctx, int phase) {
   const int64_t per_launch = (int64_t)MAX_LOCAL * grid;
   for (int64_t base = 0; base < std::max<int64_t>(ctx->max_tiles_tc, 1); base += per_launch) {
     p.tile_base = (int)base;
-    if (ctx->opt.precision == NOLSM_PREC_MIXED_BF16)
-      ns_tc_kernel<__nv_bfloat16><<<grid, NUM_THREADS, SMEM_TOTAL, ctx->stream>>>(p);
-    else
-      ns_tc_kernel<__half><<<grid, NUM_THREADS, SMEM_TOTAL, ctx->stream>>>(p);
+    // large blocks (long K loops, 128 x 256 tiles back to back): the shape with two double-buffered
+    // epilogue warps per lane quarter keeps the epilogue of a tile within the next tile's products
+    const bool bf = ctx->opt.precision == NOLSM_PREC_MIXED_BF16;
+    if (p.interleave) {
+      if (bf) ns_tc_kernel<__nv_bfloat16, 3, 8, 2><<<grid, TcWide::threads, TcWide::smem, ctx->stream>>>(p);
+      else ns_tc_kernel<__half, 3, 8, 2><<<grid, TcWide::threads, TcWide::smem, ctx->stream>>>(p);
+    } else {
+      if (bf) ns_tc_kernel<__nv_bfloat16, 4, 4, 1><<<grid, TcNarrow::threads, TcNarrow::smem, ctx->stream>>>(p);
+      else ns_tc_kernel<__half, 4, 4, 1><<<grid, TcNarrow::threads, TcNarrow::smem, ctx->stream>>>(p);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
