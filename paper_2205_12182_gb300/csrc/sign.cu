@@ -871,6 +871,77 @@ __global__ void __launch_bounds__(256) density_slab_kernel(const BlockDesc* __re
   }
 }
 
+// The same back-transform for blocks with many own columns on the mixed paths: a CTA takes 128
+// rows x 64 columns of D_b[:, C_b] (grid: row tiles, 64-column tiles, blocks), each thread an 8 x 4
+// piece in registers, so L^-1 is read once per 64 columns instead of once per 8 and a step of k
+// costs three 16-byte shared loads for 32 FMAs.  Every output takes its terms in ascending k with
+// one FMA each, as density_slab_kernel<false> does: the results are the same bit for bit.
+__global__ void __launch_bounds__(256) density_slab_wide_kernel(const BlockDesc* __restrict__ blocks,
+                                                                const float* __restrict__ linv,
+                                                                const float* __restrict__ y,
+                                                                float* __restrict__ dslab) {
+  __shared__ __align__(16) float Ls[32][128];   // L^-1[k0 + kk][r0 + i]
+  __shared__ __align__(16) float Ys[32][64];    // Y[k0 + kk][c0 + j]
+  const BlockDesc bd = blocks[blockIdx.z];
+  const int ld = bd.n_pad, c = bd.c;
+  const int r0 = blockIdx.x * 128, c0 = blockIdx.y * 64;
+  if (r0 >= ld || c0 >= c) return;
+  const float* Li = linv + bd.off_mat;
+  const float* Y = y + bd.off_slab;
+  float* Dsl = dslab + bd.off_slab;
+  const int tid = threadIdx.x;
+  const int rg = tid & 15, cg = tid >> 4;        // rows rg*8 .. +8, columns cg*4 .. +4
+  float acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int k0 = r0; k0 < ld; k0 += 32) {
+    // L^-1 rows k0 .. k0+31, columns r0 .. r0+127: 1,024 float4, four per thread (coalesced rows)
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int e = tid + 256 * t;
+      const int kk = e >> 5, i4 = (e & 31) * 4;
+      *reinterpret_cast<float4*>(&Ls[kk][i4]) =
+          *reinterpret_cast<const float4*>(Li + (int64_t)(k0 + kk) * ld + r0 + i4);
+    }
+    // Y columns c0 .. c0+63, rows k0 .. k0+31 (column-major slab): 512 float4 along k, two per thread
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int e = tid + 256 * t;
+      const int j = e >> 3, k4 = (e & 7) * 4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (c0 + j < c) v = *reinterpret_cast<const float4*>(Y + (int64_t)(c0 + j) * ld + k0 + k4);
+      Ys[k4][j] = v.x;
+      Ys[k4 + 1][j] = v.y;
+      Ys[k4 + 2][j] = v.z;
+      Ys[k4 + 3][j] = v.w;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < 32; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&Ls[kk][rg * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&Ls[kk][rg * 8 + 4]);
+      const float4 b = *reinterpret_cast<const float4*>(&Ys[kk][cg * 4]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int cc = c0 + cg * 4 + j;
+    if (cc >= c) continue;
+    float* out = Dsl + (int64_t)cc * ld + r0 + rg * 8;
+    *reinterpret_cast<float4*>(out) = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+    *reinterpret_cast<float4*>(out + 4) = make_float4(acc[4][j], acc[5][j], acc[6][j], acc[7][j]);
+  }
+}
+
 // Step 3: every stored entry (r, c) of an own column c is written to its CSR position transpose[e]
 // (e = the entry (c, r) of row c; the pattern is symmetric) from the block's D slab.
 __global__ void __launch_bounds__(256) density_scatter_kernel(const BlockDesc* __restrict__ blocks,
@@ -1089,11 +1160,17 @@ cudaError_t launch_density(nolsm_ctx* ctx) {
     cudaError_t e = cudaMemsetAsync(ctx->d_dval, 0, sizeof(double) * ctx->nnz, ctx->stream);
     if (e != cudaSuccess) return e;
   }
-  int max_pad = 0;
-  for (const auto& bd : ctx->h_blocks) max_pad = std::max(max_pad, bd.n_pad);
+  int max_pad = 0, max_c = 0;
+  for (const auto& bd : ctx->h_blocks) {
+    max_pad = std::max(max_pad, bd.n_pad);
+    max_c = std::max(max_c, bd.c);
+  }
   const dim3 g(max_pad / 128, ctx->n_blocks);
   if (ctx->opt.precision == NOLSM_PREC_FP32)
     density_slab_kernel<true><<<g, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_linv, ctx->d_y, ctx->d_tmp);
+  else if (max_c >= 32)   // many own columns: 64-column tiles (same results as the narrow kernel)
+    density_slab_wide_kernel<<<dim3(max_pad / 128, (max_c + 63) / 64, ctx->n_blocks), 256, 0, ctx->stream>>>(
+        ctx->d_blocks, ctx->d_linv, ctx->d_y, ctx->d_tmp);
   else
     density_slab_kernel<false><<<g, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_linv, ctx->d_y, ctx->d_tmp);
   density_scatter_kernel<<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_idx, ctx->d_blk_cols, ctx->d_tmp,
