@@ -226,7 +226,8 @@ __device__ __forceinline__ uint32_t sw64(int row, int col) {
 // antisymmetric rounding errors each step once converged:
 //   above: the chunk goes to (rows, cols) and its transpose to (cols, rows), both staged in the
 //          warp's shared buffer and written by two tensor stores (lane 0, asynchronous);
-//   on:    entries c >= r at (r, c) and c > r also at (c, r), by plain stores.
+//   on:    entries c >= r at (r, c) and c > r also at (c, r): the symmetric box is assembled in the
+//          staging buffer from the chunk and its transpose and written by one tensor store.
 // Returns the lane's ||.||^2 part.  The caller waits for the tensor stores (bulk group) before the
 // results are read or the buffer goes away.
 // Q8 (the FP8 experiment) rounds every output to an FP8 E4M3 value first.
@@ -261,15 +262,7 @@ __device__ __forceinline__ float epi_tile(uint32_t tmem_acc, int q, int lane, T*
         if constexpr (Q8) x = float(__nv_fp8_e4m3(x));   // stored in the iterate's format
         fv[j] = x;
       }
-      if (cg0 == r0) {
-        T* orow = out + (int64_t)r * ld;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          if (cg0 + j >= r) orow[cg0 + j] = Pack<T>::one(fv[j]);
-          if (cg0 + j > r) out[(int64_t)(cg0 + j) * ld + r] = Pack<T>::one(fv[j]);
-        }
-        continue;
-      }
+      const bool diag = cg0 == r0;           // warp-uniform
       // the store that last used this buffer (NBUF chunks ago) has read it
       if (lane == 0) {
         if (NBUF == 1) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
@@ -285,11 +278,20 @@ __device__ __forceinline__ float epi_tile(uint32_t tmem_acc, int q, int lane, T*
                        Pack<T>::two(fv[8 * u + 4], fv[8 * u + 5]), Pack<T>::two(fv[8 * u + 6], fv[8 * u + 7]));
 #pragma unroll
       for (int j = 0; j < 32; ++j) *reinterpret_cast<T*>(M + sw64(j, lane)) = Pack<T>::one(fv[j]);
+      if (diag) {
+        // on the diagonal the chunk is its own mirror: entry (lane, c) below the diagonal takes the
+        // upper-triangle value computed by lane c, which M holds at (lane, c); one store then writes
+        // the symmetric 32 x 32 box
+        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < 31; ++c)
+          if (c < lane) *reinterpret_cast<T*>(D + sw64(lane, c)) = *reinterpret_cast<const T*>(M + sw64(lane, c));
+      }
       fence_async_smem();
       __syncwarp();
       if (lane == 0) {
         tma_store_2d(smap, D, cg0, rowbase + r0);
-        tma_store_2d(smap, M, r0, rowbase + cg0);
+        if (!diag) tma_store_2d(smap, M, r0, rowbase + cg0);
         bulk_commit();
       }
       buf = (NBUF == 1) ? 0 : buf ^ 1;
