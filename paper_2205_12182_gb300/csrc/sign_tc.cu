@@ -276,16 +276,17 @@ __device__ __forceinline__ float epi_tile(uint32_t tmem_acc, int q, int lane, T*
         *reinterpret_cast<uint4*>(D + sw64(lane, 8 * u)) =
             make_uint4(Pack<T>::two(fv[8 * u], fv[8 * u + 1]), Pack<T>::two(fv[8 * u + 2], fv[8 * u + 3]),
                        Pack<T>::two(fv[8 * u + 4], fv[8 * u + 5]), Pack<T>::two(fv[8 * u + 6], fv[8 * u + 7]));
-#pragma unroll
-      for (int j = 0; j < 32; ++j) *reinterpret_cast<T*>(M + sw64(j, lane)) = Pack<T>::one(fv[j]);
       if (diag) {
-        // on the diagonal the chunk is its own mirror: entry (lane, c) below the diagonal takes the
-        // upper-triangle value computed by lane c, which M holds at (lane, c); one store then writes
-        // the symmetric 32 x 32 box
+        // on the diagonal the chunk is its own mirror: once every row is in place, lane c writes its
+        // upper-triangle entries (c, j), j > c, over the entries (j, c) below the diagonal, and one
+        // store writes the symmetric 32 x 32 box
         __syncwarp();
 #pragma unroll
-        for (int c = 0; c < 31; ++c)
-          if (c < lane) *reinterpret_cast<T*>(D + sw64(lane, c)) = *reinterpret_cast<const T*>(M + sw64(lane, c));
+        for (int j = 1; j < 32; ++j)
+          if (j > lane) *reinterpret_cast<T*>(D + sw64(j, lane)) = Pack<T>::one(fv[j]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) *reinterpret_cast<T*>(M + sw64(j, lane)) = Pack<T>::one(fv[j]);
       }
       fence_async_smem();
       __syncwarp();
