@@ -524,7 +524,9 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
     CK(dalloc(ctx, &ctx->d_oz_exp, (size_t)ctx->sum_pad));
     CK(dalloc(ctx, &ctx->d_oz_planes, (size_t)(7 * kOzPanel) * (size_t)ctx->sum_pad));
     CK(dalloc(ctx, &ctx->d_oz_items, (size_t)(2 * items)));
-    CK(dalloc(ctx, &ctx->d_oz_tmaps, (size_t)256));
+    int n_bins = 0;
+    for (const auto& bd : ctx->h_blocks) n_bins = std::max(n_bins, bd.bin + 1);
+    CK(dalloc(ctx, &ctx->d_oz_tmaps, (size_t)128 * (size_t)(2 + 2 * n_bins)));   // CUtensorMap: 128 bytes
     CK(dalloc(ctx, &ctx->d_oz_w, (size_t)4096 * (size_t)n_blocks));
     CK(oz_prepare(ctx));
   }

@@ -217,6 +217,11 @@ __device__ __forceinline__ uint32_t sw64(int row, int col) {
   return (uint32_t)(row * 64 + ((((col * 2) >> 4) ^ ((row >> 1) & 3)) << 4) + ((col * 2) & 15));
 }
 
+// byte offset of (row, byte column) in a 128-byte-row box with the 128-byte swizzle (16-byte unit XOR row % 8)
+__device__ __forceinline__ uint32_t sw128(int row, int colbytes) {
+  return (uint32_t)(row * 128 + ((((colbytes >> 4) ^ (row & 7))) << 4) + (colbytes & 15));
+}
+
 // Epilogue of one tile (one warp = 32 rows of the 128-row tile, lane = row): the accumulator
 // columns in chunks of 32, phase 1's arithmetic (B = c1 I - c3 T and ||T - I||^2 of the stored
 // triangle), FP16/BF16 stores.  Tiles lie on or above the block diagonal and the row slices of the
@@ -1555,20 +1560,32 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) slab_tc_kernel(const __grid_co
 // in double-float from the smallest up, scales by the power of two and subtracts from C (pairs in
 // place).
 // Work item = (block, 32 columns n0): the seven 32 x 64 B planes of rows n0.. stay in shared memory
-// (double-buffered across items) while the 128-row A tiles of rows >= n0 - 127 stream through an
-// eight-stage ring, one plane per stage; 28 pairs x 4 K-steps = 112 MMAs (M = 128, N = 32, K = 16)
-// per tile into 7 x 32 accumulator columns, two accumulator sets.  Items go round-robin to the CTAs
-// (neighbouring columns of one block run side by side and share its A planes in L2).  Roles (320
+// (double-buffered across items) while the 128-row A tiles of rows >= n0 - 127 stream through a
+// six-stage ring, one plane per stage.  Plane s of A meets the B planes t = 0 .. 6 - s in one MMA of
+// N = 32 (7 - s) (the B planes are stacked, so its output columns are the accumulators of levels
+// s .. 6): 7 x 4 K-steps = 28 MMAs (M = 128, K = 16) per tile into 7 x 32 accumulator columns, two
+// accumulator sets.  The tile's 128 x 32 pairs of C
+// (32 KB) come into shared memory by two tensor copies issued with the tile's planes (two C buffers,
+// so the next tile's C is in flight while the epilogue works) and go back by one tensor store per
+// epilogue warp (its 32 rows x 16 columns); the pool is read and written as whole boxes instead of
+// per-lane rows that the epilogue would wait on.  Items go round-robin to the CTAs (neighbouring
+// columns of one block run side by side and share its A planes in L2).  Roles (320
 // threads): warp 0 TMA producer, warp 1 MMA issuer, warps 2..9 epilogue (two per TMEM lane quarter,
 // 16 columns each).  Waits are bounded as in ns_tc_kernel.
+// A 128-row box that starts 64 rows before the end of the block reaches into the next block of the
+// bin's stack: its loads are harmless and unused, and no store is issued for a 32-row group that
+// starts at or past n (so nothing outside the block's own rows is written).
 constexpr int OZ_NSL = 7;
 constexpr int OZ_TN = 32;
-constexpr int OZ_NST = 8;
+constexpr int OZ_NST = 6;
 constexpr int OZ_A_BYTES = TM * kOzPanel * 2;                  // one plane of a 128-row tile
 constexpr int OZ_PLANE_B = OZ_TN * kOzPanel * 2;               // one plane of 32 rows
 constexpr int OZ_B_BYTES = OZ_NSL * OZ_PLANE_B;                // 28 KB
 constexpr int OZ_B_OFF = OZ_NST * OZ_A_BYTES;
-constexpr int OZ_BAR_OFF = OZ_B_OFF + 2 * OZ_B_BYTES;
+constexpr int OZ_CBOX_BYTES = TM * 16 * 8;                     // 128 rows x 16 pairs (128-byte rows)
+constexpr int OZ_C_BYTES = 2 * OZ_CBOX_BYTES;                  // the tile's 128 x 32 pairs of C
+constexpr int OZ_C_OFF = OZ_B_OFF + 2 * OZ_B_BYTES;
+constexpr int OZ_BAR_OFF = OZ_C_OFF + 2 * OZ_C_BYTES;
 constexpr int OZ_SMEM = 1024 + OZ_BAR_OFF + 256;
 constexpr int OZ_THREADS = 320;
 constexpr int OZ_ACC = 256;                                     // column offset of the second set
@@ -1580,7 +1597,8 @@ struct OzParams {
   const int32_t* items;         // (block, n0) pairs of this panel
   int n_items;
   const BlockDesc* blocks;
-  const CUtensorMap* maps;      // [0]: 64 x 128 boxes, [1]: 64 x 32 boxes over the slice planes
+  const CUtensorMap* maps;      // [0]: 64 x 128 boxes, [1]: 64 x 32 boxes over the slice planes;
+                                // per bin [2 + 2 bin]: 16 x 128 loads, [3 + 2 bin]: 16 x 32 stores of C
   double* pool;
   const int32_t* scale_exp;
   int t0;                       // first trailing row / column
@@ -1611,8 +1629,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) chol_update_kernel(const __grid
   uint64_t* bempty_bar = bars + 2 * OZ_NST + 2;     // [2]
   uint64_t* tfull_bar = bars + 2 * OZ_NST + 4;      // [2]
   uint64_t* tempty_bar = bars + 2 * OZ_NST + 6;     // [2]
-  uint64_t* drain_bar = bars + 2 * OZ_NST + 8;      // [1]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * OZ_NST + 9);
+  uint64_t* cfull_bar = bars + 2 * OZ_NST + 8;      // [2] the tile's C landed
+  uint64_t* cempty_bar = bars + 2 * OZ_NST + 10;    // [2] every epilogue warp's store has read its C
+  uint64_t* drain_bar = bars + 2 * OZ_NST + 12;     // [1]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * OZ_NST + 13);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1623,6 +1643,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) chol_update_kernel(const __grid
       mbar_init(&bempty_bar[a], 1);
       mbar_init(&tfull_bar[a], 1);
       mbar_init(&tempty_bar[a], 256);
+      mbar_init(&cfull_bar[a], 1);
+      mbar_init(&cempty_bar[a], 8);
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -1644,14 +1666,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) chol_update_kernel(const __grid
 
   if (warp == 0) {
     if (lane == 0) {
-      int ps = 0, bb = 0;
-      uint32_t pph = 0, bph[2] = {0u, 0u};
-      uint32_t armed = 0, arm_parity = 0, barmed = 0, barm_parity = 0;
+      int ps = 0, bb = 0, cb = 0;
+      uint32_t pph = 0, bph[2] = {0u, 0u}, cph[2] = {0u, 0u};
+      uint32_t armed = 0, arm_parity = 0, barmed = 0, barm_parity = 0, carmed = 0, carm_parity = 0;
       bool ok = true;
       for (int it = blockIdx.x; it < p.n_items && ok; it += gridDim.x) {
         const int b = p.items[2 * it], n0 = p.items[2 * it + 1];
         const BlockDesc bd = p.blocks[b];
         const int np = bd.n_pad, rbase = 7 * bd.row_off;
+        const CUtensorMap* cmap = p.maps + 2 + 2 * bd.bin;
+        const int crow = bd.pos * np;
         if (!mbar_wait(&bempty_bar[bb], bph[bb] ^ 1u, budget, abort_flag)) { ok = false; break; }
         mbar_expect_tx(&bfull_bar[bb], OZ_B_BYTES);
         uint8_t* bdst = smem + OZ_B_OFF + bb * OZ_B_BYTES;
@@ -1660,7 +1684,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) chol_update_kernel(const __grid
         barm_parity = (barm_parity & ~(1u << bb)) | (bph[bb] << bb);
         bph[bb] ^= 1u;
         bb ^= 1;
-        for (int m0 = oz_first_m(t0, n0); m0 < bd.n && ok; m0 += TM)
+        for (int m0 = oz_first_m(t0, n0); m0 < bd.n && ok; m0 += TM) {
+          // the tile's C: two 128 x 16 boxes of pairs
+          if (!mbar_wait(&cempty_bar[cb], cph[cb] ^ 1u, budget, abort_flag)) { ok = false; break; }
+          mbar_expect_tx(&cfull_bar[cb], OZ_C_BYTES);
+          uint8_t* cdst = smem + OZ_C_OFF + cb * OZ_C_BYTES;
+          tma_load_2d(cdst, cmap, &cfull_bar[cb], n0, crow + m0);
+          tma_load_2d(cdst + OZ_CBOX_BYTES, cmap, &cfull_bar[cb], n0 + 16, crow + m0);
+          carmed |= 1u << cb;
+          carm_parity = (carm_parity & ~(1u << cb)) | (cph[cb] << cb);
+          cph[cb] ^= 1u;
+          cb ^= 1;
           for (int s = 0; s < OZ_NSL; ++s) {
             if (!mbar_wait(&empty_bar[ps], pph ^ 1u, budget, abort_flag)) { ok = false; break; }
             mbar_expect_tx(&full_bar[ps], OZ_A_BYTES);
@@ -1669,6 +1703,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) chol_update_kernel(const __grid
             arm_parity = (arm_parity & ~(1u << ps)) | (pph << ps);
             if (++ps == OZ_NST) { ps = 0; pph ^= 1u; }
           }
+        }
       }
       if (!ok) {
         set_error(p.flags, NOLSM_ETIMEOUT);
@@ -1678,12 +1713,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) chol_update_kernel(const __grid
       volatile int never = 0;
       for (int s = 0; s < OZ_NST; ++s)
         if (armed & (1u << s)) mbar_wait(&full_bar[s], (arm_parity >> s) & 1u, drain_budget, &never);
-      for (int a = 0; a < 2; ++a)
+      for (int a = 0; a < 2; ++a) {
         if (barmed & (1u << a)) mbar_wait(&bfull_bar[a], (barm_parity >> a) & 1u, drain_budget, &never);
+        if (carmed & (1u << a)) mbar_wait(&cfull_bar[a], (carm_parity >> a) & 1u, drain_budget, &never);
+      }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = make_idesc(1, TM, OZ_TN);   // BF16 operands
       int ms = 0, bb = 0, acc = 0;
       uint32_t mph = 0, bph[2] = {0u, 0u}, tph[2] = {0u, 0u};
       bool ok = true;
@@ -1700,14 +1736,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) chol_update_kernel(const __grid
           for (int s = 0; s < OZ_NSL; ++s) {
             if (!mbar_wait(&full_bar[ms], mph, budget, abort_flag)) { ok = false; break; }
             tc_fence_after();
+            // A plane s against B planes t = 0 .. 6 - s in one MMA: the planes lie back to back (32 rows
+            // each), so output column 32 t + j lands in the accumulator of level s + t, column j
             const uint64_t adesc = sw128_desc(smem_u32(smem + ms * OZ_A_BYTES));
-            for (int t = 0; t + s < OZ_NSL; ++t) {
-              const uint64_t bdesc = sw128_desc(b_addr + (uint32_t)(t * OZ_PLANE_B));
-              const uint32_t d = d0 + (uint32_t)((s + t) * OZ_TN);
+            const uint64_t bdesc = sw128_desc(b_addr);
+            const uint32_t idesc = make_idesc(1, TM, OZ_TN * (OZ_NSL - s));   // BF16 operands
+            const uint32_t d = d0 + (uint32_t)(s * OZ_TN);
 #pragma unroll
-              for (int kk = 0; kk < kOzPanel / 16; ++kk)
-                umma_f16(d, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), idesc, (s | kk) != 0);
-            }
+            for (int kk = 0; kk < kOzPanel / 16; ++kk)
+              umma_f16(d, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), idesc, (s | kk) != 0);
             umma_commit(&empty_bar[ms]);
             if (++ms == OZ_NST) { ms = 0; mph ^= 1u; }
           }
@@ -1731,38 +1768,51 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) chol_update_kernel(const __grid
     }
   } else {
     const int q = warp & 3, half = (warp - 2) >> 2;
-    int acc = 0;
-    uint32_t tph[2] = {0u, 0u};
+    int acc = 0, cb = 0, pend = -1;
+    uint32_t tph[2] = {0u, 0u}, cph[2] = {0u, 0u};
     for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
       const int b = p.items[2 * it], n0 = p.items[2 * it + 1];
       const BlockDesc bd = p.blocks[b];
       const int np = bd.n_pad, n = bd.n;
-      float2* C = reinterpret_cast<float2*>(p.pool + bd.off_mat);
+      const CUtensorMap* smap = p.maps + 3 + 2 * bd.bin;
       const int32_t* ex = p.scale_exp + bd.row_off;
       bool stop = false;
       for (int m0 = oz_first_m(t0, n0); m0 < n; m0 += TM) {
-        if (!__all_sync(0xffffffffu, mbar_wait(&tfull_bar[acc], tph[acc], budget, abort_flag))) {
+        // the previous tile's store has read its C buffer: hand the buffer back to the producer
+        if (pend >= 0) {
+          if (lane == 0) {
+            bulk_wait_read0();
+            mbar_arrive(&cempty_bar[pend]);
+          }
+          pend = -1;
+        }
+        const bool got = mbar_wait(&cfull_bar[cb], cph[cb], budget, abort_flag) &&
+                         mbar_wait(&tfull_bar[acc], tph[acc], budget, abort_flag);
+        if (!__all_sync(0xffffffffu, got)) {
           set_error(p.flags, NOLSM_ETIMEOUT);
           *abort_flag = 1;
           stop = true;
           break;
         }
         tc_fence_after();
-        const int r = m0 + q * 32 + lane;
+        const int rw0 = m0 + q * 32;              // first row of this warp
+        const int r = rw0 + lane;
         const int er = r < n ? ex[r] : 0;
+        uint8_t* cbox = smem + OZ_C_OFF + cb * OZ_C_BYTES + half * OZ_CBOX_BYTES;   // 128 rows x 16 pairs
+        const int crow = q * 32 + lane;           // this lane's row in the box
         for (int ch = 0; ch < 2; ++ch) {
           const int c0 = n0 + half * 16 + ch * 8;
-          if (c0 > m0 + q * 32 + 31) continue;       // chunk above every row of this warp (uniform)
+          if (c0 > rw0 + 31) continue;            // chunk above every row of this warp (uniform)
           uint32_t v[OZ_NSL][8];
           const uint32_t tb = tmem_base + (uint32_t)(acc * OZ_ACC + half * 16 + ch * 8) + ((uint32_t)(q * 32) << 16);
 #pragma unroll
           for (int l = 0; l < OZ_NSL; ++l) tmem_ld8(tb + (uint32_t)(l * OZ_TN), v[l]);
           tmem_wait_ld();
           if (r >= n || c0 > r) continue;
-          float4* crow = reinterpret_cast<float4*>(C + (int64_t)r * np + c0);
+          // the lane's 8 pairs: 64 bytes = four 16-byte units of its 128-byte row (128-byte swizzle)
           float4 cv[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) cv[u] = crow[u];
+          for (int u = 0; u < 4; ++u) cv[u] = *reinterpret_cast<const float4*>(cbox + sw128(crow, ch * 64 + 16 * u));
           float* cf = reinterpret_cast<float*>(cv);
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
@@ -1793,15 +1843,28 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) chol_update_kernel(const __grid
             cf[2 * j + 1] = (s - (sh - bb3)) + (t - bb3);
           }
 #pragma unroll
-          for (int u = 0; u < 4; ++u) crow[u] = cv[u];
+          for (int u = 0; u < 4; ++u) *reinterpret_cast<float4*>(cbox + sw128(crow, ch * 64 + 16 * u)) = cv[u];
         }
         tc_fence_before();
         mbar_arrive(&tempty_bar[acc]);
         tph[acc] ^= 1u;
         acc ^= 1;
+        // this warp's 32 rows x 16 columns back to the pool, when it changed any of them: rows from
+        // n on are left alone (a group that starts before n ends before n_pad)
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0 && rw0 < n && n0 + half * 16 <= rw0 + 31) {
+          tma_store_2d(smap, cbox + q * 32 * 128, n0 + half * 16, bd.pos * np + rw0);
+          bulk_commit();
+        }
+        pend = cb;
+        cph[cb] ^= 1u;
+        cb ^= 1;
       }
       if (stop) break;
     }
+    if (lane == 0) bulk_wait0();                  // every store of this warp has landed
+    __syncwarp();
   }
   tc_fence_before();
   __syncthreads();
@@ -1860,10 +1923,6 @@ __device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint6
       : "memory");
 }
 
-// byte offset of (row, byte column) in a 128-byte-row box with the 128-byte swizzle (16-byte unit XOR row % 8)
-__device__ __forceinline__ uint32_t sw128(int row, int colbytes) {
-  return (uint32_t)(row * 128 + ((((colbytes >> 4) ^ (row & 7))) << 4) + (colbytes & 15));
-}
 
 __global__ void __launch_bounds__(CG_THREADS, 1) cong_tc_kernel(const __grid_constant__ CgParams p) {
   extern __shared__ uint8_t smem_raw[];
@@ -2329,8 +2388,9 @@ cudaError_t launch_congruence_tc(nolsm_ctx* ctx, float* t1) {
 
 int tc_tile_n() { return TN; }
 
-// Work items (block, 32-column chunk) of every panel's trailing update, and two tensor maps over the
-// slice planes (7 n_pad rows of 64 BF16 per block, blocks in layout order).
+// Work items (block, 32-column chunk) of every panel's trailing update, two tensor maps over the
+// slice planes (7 n_pad rows of 64 BF16 per block, blocks in layout order) and two per bin over the
+// double-float pool the factor is computed in (ctx->d_sb).
 cudaError_t oz_prepare(nolsm_ctx* ctx) {
   auto encode = get_encode();
   if (!encode || !ctx->d_oz_planes) return cudaErrorNotSupported;
@@ -2354,7 +2414,9 @@ cudaError_t oz_prepare(nolsm_ctx* ctx) {
                                     cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) return e;
   }
-  CUtensorMap maps[2];
+  int n_bins = 0;
+  for (const auto& b : ctx->h_blocks) n_bins = std::max(n_bins, b.bin + 1);
+  std::vector<CUtensorMap> maps((size_t)(2 + 2 * n_bins));
   const uint64_t rows = (uint64_t)7 * (uint64_t)std::max<int64_t>(ctx->sum_pad, 1);
   cuuint64_t gdim[2] = {(cuuint64_t)kOzPanel, rows};
   cuuint64_t gstride[1] = {(cuuint64_t)kOzPanel * 2};
@@ -2369,7 +2431,33 @@ cudaError_t oz_prepare(nolsm_ctx* ctx) {
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemcpyAsync(ctx->d_oz_tmaps, maps, sizeof(maps), cudaMemcpyHostToDevice, ctx->stream);
+  // per bin, over the pool of double-float pairs (8 bytes an entry, the bin's blocks stacked as
+  // n_pad-row matrices): 16 x 128 loads and 16 x 32 stores of the updated tiles, 128-byte swizzle
+  std::vector<int64_t> bin_off(n_bins, 0), bin_cnt(n_bins, 0);
+  std::vector<int> bin_pad(n_bins, 0);
+  for (const auto& b : ctx->h_blocks) {
+    if (b.pos == 0) bin_off[b.bin] = b.off_mat;
+    bin_cnt[b.bin] += 1;
+    bin_pad[b.bin] = b.n_pad;
+  }
+  for (int bi = 0; bi < n_bins && r == CUDA_SUCCESS; ++bi) {
+    const uint64_t np = (uint64_t)bin_pad[bi];
+    cuuint64_t cdim[2] = {np, np * (uint64_t)std::max<int64_t>(bin_cnt[bi], 1)};
+    cuuint64_t cstride[1] = {np * 8};
+    cuuint32_t cbox_l[2] = {16, (cuuint32_t)TM};
+    cuuint32_t cbox_s[2] = {16, 32};
+    void* base = ctx->d_sb + bin_off[bi];
+    r = encode(&maps[2 + 2 * bi], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, base, cdim, cstride, cbox_l, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r == CUDA_SUCCESS)
+      r = encode(&maps[3 + 2 * bi], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, base, cdim, cstride, cbox_s, estr,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemcpyAsync(ctx->d_oz_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                                  cudaMemcpyHostToDevice, ctx->stream);
   if (e != cudaSuccess) return e;
   e = cudaStreamSynchronize(ctx->stream);   // maps is a host temporary
   if (e != cudaSuccess) return e;
