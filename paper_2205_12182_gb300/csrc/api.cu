@@ -136,7 +136,9 @@ void release_pools(nolsm_ctx* ctx) {
   dfree(ctx->d_oz_planes); ctx->d_oz_planes = nullptr;
   dfree(ctx->d_oz_items); ctx->d_oz_items = nullptr;
   dfree(ctx->d_oz_tmaps); ctx->d_oz_tmaps = nullptr;
-  dfree(ctx->d_oz_w); ctx->d_oz_w = nullptr;
+  dfree(ctx->d_oz_m); ctx->d_oz_m = nullptr;
+  dfree(ctx->d_oz_f); ctx->d_oz_f = nullptr;
+  dfree(ctx->d_tr_items); ctx->d_tr_items = nullptr;
   dfree(ctx->d_own_diag); ctx->d_own_diag = nullptr;
   dfree(ctx->d_resacc); ctx->d_resacc = nullptr;
   dfree(ctx->d_tol); ctx->d_tol = nullptr;
@@ -526,8 +528,12 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
     CK(dalloc(ctx, &ctx->d_oz_items, (size_t)(2 * items)));
     int n_bins = 0;
     for (const auto& bd : ctx->h_blocks) n_bins = std::max(n_bins, bd.bin + 1);
-    CK(dalloc(ctx, &ctx->d_oz_tmaps, (size_t)128 * (size_t)(2 + 2 * n_bins)));   // CUtensorMap: 128 bytes
-    CK(dalloc(ctx, &ctx->d_oz_w, (size_t)4096 * (size_t)n_blocks));
+    CK(dalloc(ctx, &ctx->d_oz_tmaps, (size_t)128 * (size_t)(3 + 2 * n_bins)));   // CUtensorMap: 128 bytes
+    CK(dalloc(ctx, &ctx->d_oz_m, (size_t)7 * 4096 * (size_t)n_blocks));
+    CK(dalloc(ctx, &ctx->d_oz_f, (size_t)68 * (size_t)n_blocks));
+    int64_t tr_items = 0;
+    for (const auto& bd : ctx->h_blocks) tr_items += (int64_t)(bd.n_pad / kOzPanel + 1) * (bd.n_pad / 128 + 1);
+    CK(dalloc(ctx, &ctx->d_tr_items, (size_t)(2 * tr_items)));
     CK(oz_prepare(ctx));
   }
   CK(phase_mark(ctx, NOLSM_PHASE_FACTOR));

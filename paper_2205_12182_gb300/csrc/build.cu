@@ -643,19 +643,22 @@ __device__ __forceinline__ void pivot32(df32 (*P)[65], df32 (*X)[33], df32* rk, 
 }
 
 // The 64 x 64 diagonal block [c0, c0 + 64) of a panel, whose earlier panels' contributions are
-// already subtracted: L11 in place (pairs) and, when rows follow below, W = L11^-T (64 x 64 pairs)
-// for chol_trsm_kernel.  The CTA runs the two 32 x 32 pivots (pivot32) and shares the
-// 32 x 32 x 32 products between its four warps:
+// already subtracted: L11 in place (pairs) and, when rows follow below, Minv = L11^-1 for the TRSM of
+// the rows below (chol_trsm_tc_kernel) as seven BF16 slice planes, row c on the scale 2^f_c >=
+// max_k |Minv[c, k]|, with f_0 .. f_63 and g = max_k e_k over the panel's rows in mout_f.  The CTA
+// runs the two 32 x 32 pivots (pivot32) and shares the 32 x 32 x 32 products between its four warps:
 //   L_ba = A_ba L_aa^-T,  A_cc -= L_ba L_ba^T,  T = L_ba L_aa^-1,  X = -L_cc^-1 T,
 // so that L11^-1 = [[L_aa^-1, 0], [X, L_cc^-1]].  Entries past n are taken as the identity.  In the
 // first panel each row's slicing exponent e_r (2^e_r >= sqrt(S_rr)) is written first.
 __global__ void __launch_bounds__(128, 3) chol_diag64_kernel(const BlockDesc* __restrict__ blocks,
                                                              double* __restrict__ pool, DevFlags* flags, int c0,
                                                              int32_t* __restrict__ scale_exp,
-                                                             float2* __restrict__ wout) {
+                                                             uint16_t* __restrict__ mout,
+                                                             int32_t* __restrict__ mout_f) {
   __shared__ df32 M[64][65];         // the block (lower triangle used)
   __shared__ df32 Xa[32][33], Xc[32][33], T[32][33], X[32][33];
   __shared__ df32 rk[32];
+  __shared__ int fexp[64];
   __shared__ int s_bad;
   const BlockDesc bd = blocks[blockIdx.x];
   const int n = bd.n, ld = bd.n_pad;
@@ -706,7 +709,7 @@ __global__ void __launch_bounds__(128, 3) chol_diag64_kernel(const BlockDesc* __
     const int r = e >> 6, c = e & 63;
     if (r < nb && c <= r) A[(int64_t)(c0 + r) * ld + c0 + c] = make_float2(M[r][c].h, M[r][c].l);
   }
-  if (wout && n > c0 + 64) {
+  if (mout && n > c0 + 64) {
     // T = L_ba L_aa^-1, X = -L_cc^-1 T
     for (int i = warp * 8; i < warp * 8 + 8; ++i) {
       df32 acc = {0.f, 0.f};
@@ -720,14 +723,38 @@ __global__ void __launch_bounds__(128, 3) chol_diag64_kernel(const BlockDesc* __
       X[i][lane] = df_norm(acc);
     }
     __syncthreads();
-    float2* W = wout + (int64_t)blockIdx.x * 4096;   // W[k][c] = (L11^-1)[c][k]
+    // Minv[c][k] = (L11^-1)[c][k]: lower triangular
+    auto minv = [&](int c, int k) -> df32 {
+      if (k < 32 && c < 32) return Xa[c][k];
+      if (k >= 32 && c >= 32) return Xc[c - 32][k - 32];
+      if (k < 32) return X[c - 32][k];
+      return df32{0.f, 0.f};
+    };
+    int32_t* F = mout_f + (int64_t)blockIdx.x * 68;
+    if (tid < 64) {
+      float mx = 0.f;
+      for (int k = 0; k <= tid; ++k) mx = fmaxf(mx, fabsf(minv(tid, k).h));
+      int e = 0;
+      frexpf(mx > 0.f ? mx : 1.f, &e);     // 2^e > max |h|, so 2^e >= max |h + l|
+      fexp[tid] = e;
+      F[tid] = e;
+    } else if (tid == 64) {
+      int g = -1000;
+      for (int k = 0; k < 64; ++k) g = max(g, scale_exp[bd.row_off + c0 + k]);
+      F[64] = g;
+    }
+    __syncthreads();
+    uint16_t* P = mout + (int64_t)blockIdx.x * 7 * 4096;   // plane s: 64 rows c x 64 columns k
     for (int e = tid; e < 4096; e += 128) {
-      const int k = e >> 6, c = e & 63;
-      df32 v = {0.f, 0.f};
-      if (k < 32 && c < 32) v = Xa[c][k];
-      else if (k >= 32 && c >= 32) v = Xc[c - 32][k - 32];
-      else if (k < 32) v = X[c - 32][k];
-      W[e] = make_float2(v.h, v.l);
+      const int c = e >> 6, k = e & 63;
+      const df32 v = minv(c, k);
+      float q[7];
+      oz_slices(v.h, v.l, oz_scale(fexp[c]), q);
+#pragma unroll
+      for (int sl = 0; sl < 7; ++sl) {
+        const __nv_bfloat16 b = __float2bfloat16_rn(q[sl]);
+        P[sl * 4096 + e] = *reinterpret_cast<const uint16_t*>(&b);
+      }
     }
   }
   if (tid == 0 && s_bad) set_error(flags, NOLSM_ENOTPD);
@@ -751,74 +778,6 @@ __global__ void factor_f32_kernel(const BlockDesc* __restrict__ blocks, int n_bl
         v = p.x + p.y;
       }
       L[e] = v;
-    }
-  }
-}
-
-// Rows below a 64-column panel's diagonal block, L21 = A21 W with W = L11^-T from the diagonal
-// launch, in double-float; the result replaces A21 in place, and its slices go to the planes of the
-// trailing update (Ozaki, Ogita, Oishi & Rump 2012: error-free splitting into short pieces whose
-// products and sums are exact).  Row r's entries x (a pair with |x| <= 2^e_r, e_r from the diagonal
-// launch) are written as seven integers q_0..q_6 with x = 2^(e_r - 7) sum_s q_s 2^(-7 s) + rest,
-// |rest| <= 2^(e_r - 50): |q_0| <= 128 and |q_s| <= 64 after, each exact in BF16.  Plane s of the
-// block is an n_pad x 64 BF16 matrix at row 7 row_off + s n_pad of the slice pool; rows below n are
-// never read.  Grid: (64-row chunk, block); four
-// warps per CTA = two 32-row tiles x two column halves (lane = column; W is upper triangular, so
-// the first half sums over k < 32 only).  Dynamic shared memory: W (32 KB) and the A rows (32 KB).
-constexpr int kTrsmSmem = 2 * 64 * 64 * (int)sizeof(df32);
-__global__ void __launch_bounds__(128) chol_trsm_kernel(const BlockDesc* __restrict__ blocks, double* __restrict__ pool,
-                                                        const float2* __restrict__ wmat,
-                                                        const int32_t* __restrict__ scale_exp,
-                                                        __nv_bfloat16* __restrict__ planes, int c0) {
-  extern __shared__ df32 trsm_smem[];
-  df32(*Ws)[64] = reinterpret_cast<df32(*)[64]>(trsm_smem);
-  df32(*As)[64] = reinterpret_cast<df32(*)[64]>(trsm_smem + 64 * 64);   // 64 rows
-  const int b = blockIdx.y;
-  const BlockDesc bd = blocks[b];
-  const int n = bd.n, ld = bd.n_pad, t0 = c0 + 64;
-  const int rbase = t0 + blockIdx.x * 64;
-  if (rbase >= n) return;
-  float2* A = reinterpret_cast<float2*>(pool + bd.off_mat);
-  const float2* W = wmat + (int64_t)b * 4096;
-  for (int e = threadIdx.x; e < 4096; e += 128) {
-    const float2 w = W[e];
-    Ws[e >> 6][e & 63] = {w.x, w.y};
-    const int r = rbase + (e >> 6);
-    const float2 a = r < n ? A[(int64_t)r * ld + c0 + (e & 63)] : make_float2(0.f, 0.f);
-    As[e >> 6][e & 63] = {a.x, a.y};
-  }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tile = warp >> 1, h = warp & 1, c = 32 * h + lane;
-  df32 acc[32];
-#pragma unroll
-  for (int r = 0; r < 32; ++r) acc[r] = {0.f, 0.f};
-  const int kmax = 32 * (h + 1);
-#pragma unroll 2
-  for (int k = 0; k < kmax; ++k) {
-    const df32 wv = Ws[k][c];
-#pragma unroll
-    for (int r = 0; r < 32; ++r) df_fma(acc[r], As[32 * tile + r][k], wv);
-  }
-  __nv_bfloat16* P = planes + (int64_t)7 * bd.row_off * 64;
-#pragma unroll 4
-  for (int r = 0; r < 32; ++r) {
-    const int row = rbase + 32 * tile + r;
-    if (row >= n) break;
-    const df32 v = df_norm(acc[r]);
-    A[(int64_t)row * ld + c0 + c] = make_float2(v.h, v.l);
-    const float sc = ldexpf(1.f, 7 - scale_exp[bd.row_off + row]);
-    float hh = v.h * sc, ll = v.l * sc;
-#pragma unroll
-    for (int s = 0; s < 7; ++s) {
-      const float q = rintf(hh);
-      P[((int64_t)s * ld + row) * 64 + c] = __float2bfloat16_rn(q);
-      const float d = hh - q;
-      const float sum = d + ll;
-      const float bb = sum - d;
-      const float err = (d - (sum - bb)) + (ll - bb);
-      hh = sum * 128.f;
-      ll = err * 128.f;
     }
   }
 }
@@ -1140,30 +1099,20 @@ cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode) {
   float* s32 = reinterpret_cast<float*>(sb + ctx->sum_sq);   // FP32 factor lives in the scratch half
   cudaError_t e = cudaSuccess;
   if (mode == NOLSM_CHOL_DF64) {
-    // blocked by 64-column panels: the 64 x 64 diagonal block and W = L11^-T (FP32 pipe, FP64
-    // 32 x 32 pivots), the rows below L21 = A21 W with their slices (FP32 pipe), and the trailing
-    // update from the slices on the tensor cores
-    static bool trsm_attr = false;
-    if (!trsm_attr) {
-      e = cudaFuncSetAttribute(chol_trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmSmem);
-      if (e != cudaSuccess) return e;
-      trsm_attr = true;
-    }
+    // blocked by 64-column panels: the 64 x 64 diagonal block and the slices of L11^-1 (FP32 pipe,
+    // double-float 32 x 32 pivots), the rows below L21 = A21 L11^-T with their slices, and the
+    // trailing update from the slices, both on the tensor cores
     int max_n = 0;
     for (const auto& bd : ctx->h_blocks) max_n = std::max(max_n, bd.n);
     for (int pnl = 0; pnl * kOzPanel < max_n; ++pnl) {
       const int c0 = pnl * kOzPanel;
       if (pnl > 0 && (e = phase_mark(ctx, NOLSM_PHASE_FACTOR)) != cudaSuccess) return e;
       chol_diag64_kernel<<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, sb, ctx->d_flags, c0, ctx->d_oz_exp,
-                                                                 ctx->d_oz_w);
+                                                                 ctx->d_oz_m, ctx->d_oz_f);
       ctx->n_launches += 1;
       if (c0 + kOzPanel >= max_n) break;
-      const dim3 tg((max_n - c0 - kOzPanel + 63) / 64, ctx->n_blocks);
       if ((e = phase_mark(ctx, NOLSM_PHASE_FACTOR_TRSM)) != cudaSuccess) return e;
-      chol_trsm_kernel<<<tg, 128, kTrsmSmem, ctx->stream>>>(ctx->d_blocks, sb, ctx->d_oz_w, ctx->d_oz_exp,
-                                                            reinterpret_cast<__nv_bfloat16*>(ctx->d_oz_planes), c0);
-      ctx->n_launches += 1;
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if ((e = launch_chol_trsm_tc(ctx, pnl, sb)) != cudaSuccess) return e;
       if ((e = phase_mark(ctx, NOLSM_PHASE_FACTOR_UPDATE)) != cudaSuccess) return e;
       if ((e = launch_chol_update_tc(ctx, pnl, sb)) != cudaSuccess) return e;
     }

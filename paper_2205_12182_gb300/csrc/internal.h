@@ -144,9 +144,15 @@ struct nolsm_ctx {
   uint16_t* d_oz_planes = nullptr;
   int32_t* d_oz_items = nullptr;
   uint8_t* d_oz_tmaps = nullptr;
-  float2* d_oz_w = nullptr;          // W = L11^-T of the current panel, 64 x 64 pairs per block
+  // M = L11^-1 of the current panel: seven BF16 slice planes of 64 x 64 per block, each row c on its
+  // own scale 2^f_c; per block 68 ints: f_0 .. f_63 and g = the largest row exponent of the panel
+  uint16_t* d_oz_m = nullptr;
+  int32_t* d_oz_f = nullptr;
+  int32_t* d_tr_items = nullptr;     // (block, first row) of every panel's 128-row TRSM tiles
   std::vector<int32_t> h_oz_items;
   std::vector<int64_t> h_oz_panel;   // item offset of panel p (size panels + 1)
+  std::vector<int32_t> h_tr_items;
+  std::vector<int64_t> h_tr_panel;   // TRSM item offset of panel p (size panels + 1)
   int64_t sum_pad = 0;
   std::vector<int32_t> h_slab_units;
   int32_t n_units_narrow = 0, n_units_wide = 0;
@@ -277,6 +283,7 @@ cudaError_t launch_congruence_tc(nolsm_ctx* ctx, float* t1);
 cudaError_t launch_slab_tc(nolsm_ctx* ctx);
 cudaError_t oz_prepare(nolsm_ctx* ctx);                        // items and tensor maps of the updates
 cudaError_t launch_chol_update_tc(nolsm_ctx* ctx, int panel, double* pool);
+cudaError_t launch_chol_trsm_tc(nolsm_ctx* ctx, int panel, double* pool);
 constexpr int kOzPanel = 64;      // panel width of the blocked double-float Cholesky
 int tc_tile_n();
 constexpr int kSlabNarrow = 32;   // columns of a narrow refinement piece
@@ -293,6 +300,28 @@ cudaError_t mlp_predict_on(const struct nolsm_mlp* m, cudaStream_t s, const floa
 cudaError_t launch_transpose(nolsm_ctx* ctx);
 cudaError_t launch_index_sets(nolsm_ctx* ctx, const int32_t* d_blk_ptr, const int32_t* d_extra_ptr,
                               const int32_t* d_extra_idx, int32_t* d_nb, int cap, int max_dim);
+
+#ifdef __CUDACC__
+// Seven 7-bit integer slices of a double-float value h + l on the scale 2^e (|h + l| <= 2^e), given
+// sc = 2^(7 - e) (oz_scale): h + l = 2^(e - 7) sum_s q_s 2^(-7 s) + rest with |q_0| <= 128,
+// |q_s| <= 64 after it and |rest| <= 2^(e - 50); every q_s is exact in BF16 (error-free splitting,
+// Ozaki, Ogita, Oishi & Rump 2012).  The remainder of each step is carried exactly by a TwoSum with
+// the low word.
+__device__ __forceinline__ float oz_scale(int e) { return ldexpf(1.f, 7 - e); }
+__device__ __forceinline__ void oz_slices(float h, float l, float sc, float (&q)[7]) {
+  float hh = h * sc, ll = l * sc;
+#pragma unroll
+  for (int s = 0; s < 7; ++s) {
+    q[s] = rintf(hh);
+    const float d = hh - q[s];
+    const float sum = d + ll;
+    const float bb = sum - d;
+    const float err = (d - (sum - bb)) + (ll - bb);
+    hh = sum * 128.f;
+    ll = err * 128.f;
+  }
+}
+#endif
 
 // generic SIMT NT product used by the build: C_b = A_b B_b^T on the block table
 cudaError_t launch_sgemm_nt(nolsm_ctx* ctx, const float* a, const float* b, float* c, int a_lower, int b_lower,

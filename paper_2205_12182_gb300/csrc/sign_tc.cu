@@ -1798,6 +1798,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) chol_update_kernel(const __grid
         const int rw0 = m0 + q * 32;              // first row of this warp
         const int r = rw0 + lane;
         const int er = r < n ? ex[r] : 0;
+        // e_c of this warp's 16 columns (lane l < 16 holds column n0 + 16 half + l; handed out by shuffles)
+        const int cl = n0 + half * 16 + (lane & 15);
+        const int ecl = cl < n ? ex[cl] : 0;
         uint8_t* cbox = smem + OZ_C_OFF + cb * OZ_C_BYTES + half * OZ_CBOX_BYTES;   // 128 rows x 16 pairs
         const int crow = q * 32 + lane;           // this lane's row in the box
         for (int ch = 0; ch < 2; ++ch) {
@@ -1808,6 +1811,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) chol_update_kernel(const __grid
 #pragma unroll
           for (int l = 0; l < OZ_NSL; ++l) tmem_ld8(tb + (uint32_t)(l * OZ_TN), v[l]);
           tmem_wait_ld();
+          int ec[8];                              // every lane takes part in the shuffles
+#pragma unroll
+          for (int j = 0; j < 8; ++j) ec[j] = __shfl_sync(0xffffffffu, ecl, ch * 8 + j);
           if (r >= n || c0 > r) continue;
           // the lane's 8 pairs: 64 bytes = four 16-byte units of its 128-byte row (128-byte swizzle)
           float4 cv[4];
@@ -1828,7 +1834,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) chol_update_kernel(const __grid
               lo += (h - (s - bb2)) + (x - bb2);
               h = s;
             }
-            const float sc = __int_as_float((127 + er + ex[c] - 14) << 23);
+            const float sc = __int_as_float((127 + er + ec[j] - 14) << 23);
             h *= sc;
             lo *= sc;
             // C - (h + lo), renormalised
@@ -1865,6 +1871,323 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) chol_update_kernel(const __grid
     }
     if (lane == 0) bulk_wait0();                  // every store of this warp has landed
     __syncwarp();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// TRSM of the blocked double-float Cholesky on the tensor cores: after the diagonal block of panel
+// [c0, c0 + 64) is factored, the rows below it become L21 = A21 L11^-T, i.e.
+//   L21[r, c] = sum_{k in panel} A21[r, k] Minv[c, k],   Minv = L11^-1 (lower triangular),
+// with the same exact slicing as the trailing update (Ozaki, Ogita, Oishi & Rump 2012).  A21[r, k]
+// is split on the scale 2^(e_r + g), g = max_k e_k over the panel's rows: by Cauchy-Schwarz on the
+// rows of the factor |A21[r, k]| <= sqrt(S_rr S_kk) <= 2^(e_r + g).  Row c of Minv is split on its own
+// scale 2^f_c (chol_diag64_kernel).  So
+//   L21[r, c] = 2^(e_r + g + f_c - 14) sum_l 2^(-7 l) sum_{s + t = l} sum_k q_s(r, k) p_t(c, k),
+// every level sum exact in FP32 (at most 7 x 64 products of at most 2^14), the pairs with s + t > 6
+// (below 2^-49 of the scale per term) dropped.  The epilogue adds the levels in double-float, writes
+// L21 as pairs over A21 and its slices on the row scale e_r into the planes the trailing update reads.
+// Work item = (block, 128 rows m0 of the rows below the diagonal block): the CTA keeps the block's
+// Minv planes (both 32-column halves, 56 KB) while its items follow each other (contiguous runs of
+// the item list per CTA), the item's 128 x 64 A21 pairs arrive as four 128 x 16 tensor copies through
+// a three-box staging ring, converter warps slice them into seven A planes in shared memory, and the
+// MMA issuer runs, per half and per A plane s, one MMA against the stacked
+// B planes t = 0 .. 6 - s (N = 32 (7 - s)), so the 7 levels x 32 columns of a half land in one of
+// the two accumulator sets.  Roles (448 threads): warp 0 TMA producer (Minv planes), warp 1 MMA
+// issuer, warps 2..5 converter, warps 6..13 epilogue (one per TMEM lane quarter and half).  Waits
+// are bounded as in ns_tc_kernel.  Rows from n on are neither read nor written.
+constexpr int TR_THREADS = 448;
+constexpr int TR_A_OFF = 0;                                    // 7 A planes of 128 x 64 BF16
+constexpr int TR_B_OFF = OZ_NSL * OZ_A_BYTES;                  // 2 halves x 7 planes of 32 x 64 BF16
+constexpr int TR_NSS = 3;                                      // staging ring of A21 boxes (128 x 16 pairs)
+constexpr int TR_S_OFF = TR_B_OFF + 2 * OZ_B_BYTES;
+constexpr int TR_BAR_OFF = TR_S_OFF + TR_NSS * OZ_CBOX_BYTES;
+constexpr int TR_SMEM = 1024 + TR_BAR_OFF + 256;
+static_assert(TR_SMEM <= 227 * 1024, "shared memory of the TRSM kernel");
+
+struct TrParams {
+  const int32_t* items;         // (block, m0) pairs of this panel, grouped by block
+  int n_items;
+  const BlockDesc* blocks;
+  const CUtensorMap* mmap;      // 64 x 32 boxes over the Minv planes (7 x 64 rows per block)
+  const CUtensorMap* cmaps;     // per bin [2 bin]: 16 x 128 boxes over the pool of pairs
+  double* pool;                 // factor in double-float pairs (8 bytes an entry)
+  const int32_t* scale_exp;     // e_r per row (row_off indexing)
+  const int32_t* mf;            // per block: f_0 .. f_63, g
+  __nv_bfloat16* planes;        // slices of L21 for the trailing update
+  int c0;
+  DevFlags* flags;
+  long long budget;
+};
+
+__global__ void __launch_bounds__(TR_THREADS, 1) chol_trsm_tc_kernel(const __grid_constant__ TrParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TR_BAR_OFF);
+  uint64_t* bfull_bar = bars;          // Minv planes landed
+  uint64_t* bempty_bar = bars + 1;     // the MMAs on the previous block's planes are done
+  uint64_t* afull_bar = bars + 2;      // the converter wrote the item's A planes
+  uint64_t* aempty_bar = bars + 3;     // the MMAs on the A planes are done
+  uint64_t* tfull_bar = bars + 4;      // both accumulator sets hold the item's levels
+  uint64_t* tempty_bar = bars + 5;     // the epilogue has read them
+  uint64_t* drain_bar = bars + 6;
+  uint64_t* sfull_bar = bars + 7;      // [TR_NSS] an A21 box landed in the staging ring
+  uint64_t* sempty_bar = bars + 7 + TR_NSS;   // [TR_NSS] the converter has read it
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 7 + 2 * TR_NSS);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // contiguous run of the item list (consecutive items of one block reuse its Minv planes)
+  const int first = (int)(((int64_t)p.n_items * blockIdx.x) / gridDim.x);
+  const int last = (int)(((int64_t)p.n_items * (blockIdx.x + 1)) / gridDim.x);
+  if (threadIdx.x == 0) {
+    mbar_init(bfull_bar, 1);
+    mbar_init(bempty_bar, 1);
+    mbar_init(afull_bar, 128);
+    mbar_init(aempty_bar, 1);
+    mbar_init(tfull_bar, 1);
+    mbar_init(tempty_bar, 256);
+    mbar_init(drain_bar, 1);
+    for (int i = 0; i < TR_NSS; ++i) {
+      mbar_init(&sfull_bar[i], 1);
+      mbar_init(&sempty_bar[i], 128);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const long long budget = p.budget;
+  const long long drain_budget = budget > (1LL << 22) ? budget : (1LL << 22);
+  const int c0 = p.c0;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer: Minv planes per block,
+    // the item's A21 pairs as four 128 x 16 boxes through the staging ring
+    if (lane == 0) {
+      int cur = -1, ps = 0;
+      uint32_t bph = 0, pph = 0;
+      bool armed = false, ok = true;
+      uint32_t arm_parity = 0, sarmed = 0, sarm_parity = 0;
+      for (int it = first; it < last && ok; ++it) {
+        const int b = p.items[2 * it], m0 = p.items[2 * it + 1];
+        const BlockDesc bd = p.blocks[b];
+        if (b != cur) {
+          cur = b;
+          if (!mbar_wait(bempty_bar, bph ^ 1u, budget, abort_flag)) { ok = false; break; }
+          mbar_expect_tx(bfull_bar, 2 * OZ_B_BYTES);
+          for (int h = 0; h < 2; ++h)
+            for (int t = 0; t < OZ_NSL; ++t)
+              tma_load_2d(smem + TR_B_OFF + h * OZ_B_BYTES + t * OZ_PLANE_B, p.mmap, bfull_bar, 0,
+                          (b * OZ_NSL + t) * 64 + 32 * h);
+          armed = true;
+          arm_parity = bph;
+          bph ^= 1u;
+        }
+        const CUtensorMap* cmap = p.cmaps + 2 * bd.bin;
+        for (int box = 0; box < 4; ++box) {
+          if (!mbar_wait(&sempty_bar[ps], pph ^ 1u, budget, abort_flag)) { ok = false; break; }
+          mbar_expect_tx(&sfull_bar[ps], OZ_CBOX_BYTES);
+          tma_load_2d(smem + TR_S_OFF + ps * OZ_CBOX_BYTES, cmap, &sfull_bar[ps], c0 + 16 * box, bd.pos * bd.n_pad + m0);
+          sarmed |= 1u << ps;
+          sarm_parity = (sarm_parity & ~(1u << ps)) | (pph << ps);
+          if (++ps == TR_NSS) { ps = 0; pph ^= 1u; }
+        }
+      }
+      if (!ok) {
+        set_error(p.flags, NOLSM_ETIMEOUT);
+        *abort_flag = 1;
+      }
+      volatile int never = 0;
+      if (armed) mbar_wait(bfull_bar, arm_parity, drain_budget, &never);
+      for (int i = 0; i < TR_NSS; ++i)
+        if (sarmed & (1u << i)) mbar_wait(&sfull_bar[i], (sarm_parity >> i) & 1u, drain_budget, &never);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int cur = -1;
+      uint32_t bph = 0, aph = 0, tph = 0;
+      bool ok = true;
+      for (int it = first; it < last && ok; ++it) {
+        const int b = p.items[2 * it];
+        if (b != cur) {
+          if (cur >= 0) umma_commit(bempty_bar);   // the previous block's planes are free once its MMAs are done
+          cur = b;
+          if (!mbar_wait(bfull_bar, bph, budget, abort_flag)) { ok = false; break; }
+          bph ^= 1u;
+        }
+        if (!mbar_wait(afull_bar, aph, budget, abort_flag) || !mbar_wait(tempty_bar, tph ^ 1u, budget, abort_flag)) {
+          ok = false;
+          break;
+        }
+        aph ^= 1u;
+        tc_fence_after();
+        for (int h = 0; h < 2; ++h) {
+          const uint64_t bdesc = sw128_desc(smem_u32(smem + TR_B_OFF + h * OZ_B_BYTES));
+          for (int s = 0; s < OZ_NSL; ++s) {
+            const uint64_t adesc = sw128_desc(smem_u32(smem + TR_A_OFF + s * OZ_A_BYTES));
+            const uint32_t idesc = make_idesc(1, TM, OZ_TN * (OZ_NSL - s));
+            const uint32_t d = tmem_base + (uint32_t)(h * OZ_ACC + s * OZ_TN);
+#pragma unroll
+            for (int kk = 0; kk < kOzPanel / 16; ++kk)
+              umma_f16(d, adesc + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), idesc, (s | kk) != 0);
+          }
+        }
+        umma_commit(aempty_bar);
+        umma_commit(tfull_bar);
+        tph ^= 1u;
+      }
+      if (!ok) {
+        set_error(p.flags, NOLSM_ETIMEOUT);
+        *abort_flag = 1;
+      }
+      umma_commit(drain_bar);
+      volatile int never = 0;
+      mbar_wait(drain_bar, 0, drain_budget, &never);
+    }
+  } else if (warp < 6) {
+    // ------------------------------------------------------------ converter: A21 pairs -> 7 A planes
+    // (thread = row of the tile; per staged box its 16 pairs, two 16-byte units of every plane)
+    const int ct = threadIdx.x - 64;   // 0..127
+    uint32_t aph = 0, sph = 0;
+    int ss = 0;
+    bool ok = true;
+    for (int it = first; it < last && ok; ++it) {
+      const int b = p.items[2 * it], m0 = p.items[2 * it + 1];
+      const BlockDesc bd = p.blocks[b];
+      const int r = m0 + ct;
+      const float esc = oz_scale(r < bd.n ? p.scale_exp[bd.row_off + r] + p.mf[(int64_t)b * 68 + 64] : 0);
+      if (!mbar_wait(aempty_bar, aph ^ 1u, budget, abort_flag)) { ok = false; break; }
+      aph ^= 1u;
+      for (int box = 0; box < 4; ++box) {
+        if (!mbar_wait(&sfull_bar[ss], sph, budget, abort_flag)) { ok = false; break; }
+        const uint8_t* st = smem + TR_S_OFF + ss * OZ_CBOX_BYTES;
+        float f[32];
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+          const float4 x = r < bd.n ? *reinterpret_cast<const float4*>(st + sw128(ct, 16 * w)) : make_float4(0.f, 0.f, 0.f, 0.f);
+          f[4 * w] = x.x;
+          f[4 * w + 1] = x.y;
+          f[4 * w + 2] = x.z;
+          f[4 * w + 3] = x.w;
+        }
+        // the next tensor copy into this slot (async proxy) must not overtake these generic reads
+        fence_async_smem();
+        mbar_arrive(&sempty_bar[ss]);
+        if (++ss == TR_NSS) { ss = 0; sph ^= 1u; }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          uint32_t pk[7][4];
+#pragma unroll
+          for (int x = 0; x < 8; x += 2) {
+            float q0[7], q1[7];
+            oz_slices(f[16 * u + 2 * x], f[16 * u + 2 * x + 1], esc, q0);
+            oz_slices(f[16 * u + 2 * x + 2], f[16 * u + 2 * x + 3], esc, q1);
+#pragma unroll
+            for (int sl = 0; sl < 7; ++sl) pk[sl][x >> 1] = Pack<__nv_bfloat16>::two(q0[sl], q1[sl]);
+          }
+#pragma unroll
+          for (int sl = 0; sl < 7; ++sl)
+            *reinterpret_cast<uint4*>(smem + TR_A_OFF + sl * OZ_A_BYTES + sw128(ct, 16 * (2 * box + u))) =
+                make_uint4(pk[sl][0], pk[sl][1], pk[sl][2], pk[sl][3]);
+        }
+      }
+      if (!ok) break;
+      fence_async_smem();
+      mbar_arrive(afull_bar);
+    }
+    if (!ok) {
+      set_error(p.flags, NOLSM_ETIMEOUT);
+      *abort_flag = 1;
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3, h = (warp - 6) >> 2;   // a warp reads the TMEM lanes of quarter warp % 4
+    uint32_t tph = 0;
+    for (int it = first; it < last; ++it) {
+      const int b = p.items[2 * it], m0 = p.items[2 * it + 1];
+      const BlockDesc bd = p.blocks[b];
+      const int n = bd.n, ld = bd.n_pad;
+      if (!__all_sync(0xffffffffu, mbar_wait(tfull_bar, tph, budget, abort_flag))) {
+        set_error(p.flags, NOLSM_ETIMEOUT);
+        *abort_flag = 1;
+        break;
+      }
+      tph ^= 1u;
+      tc_fence_after();
+      const int r = m0 + q * 32 + lane;
+      const int32_t* F = p.mf + (int64_t)b * 68;
+      const int er = r < n ? p.scale_exp[bd.row_off + r] : 0;
+      const int eg = er + F[64] - 14;
+      const float rsc = oz_scale(er);
+      const int fl = F[32 * h + lane];            // f_c of this half's column lane, shared by shuffles
+      float2* Lrow = reinterpret_cast<float2*>(p.pool + bd.off_mat) + (int64_t)r * ld + c0;
+      __nv_bfloat16* P = p.planes + ((int64_t)7 * bd.row_off + r) * 64;
+      for (int j = 0; j < 4; ++j) {
+        const int cb = 32 * h + 8 * j;            // first of this chunk's 8 columns of the panel
+        uint32_t v[OZ_NSL][8];
+        const uint32_t tb = tmem_base + (uint32_t)(h * OZ_ACC + 8 * j) + ((uint32_t)(q * 32) << 16);
+#pragma unroll
+        for (int l = 0; l < OZ_NSL; ++l) tmem_ld8(tb + (uint32_t)(l * OZ_TN), v[l]);
+        tmem_wait_ld();
+        int fc[8];                                // every lane takes part in the shuffles
+#pragma unroll
+        for (int x = 0; x < 8; ++x) fc[x] = __shfl_sync(0xffffffffu, fl, 8 * j + x);
+        if (r >= n) continue;
+        float out[16];
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+          // sum_l v_l 2^(-7 l) in double-float, smallest level first (every term is exact)
+          float hi = __uint_as_float(v[OZ_NSL - 1][x]) * 0x1p-42f, lo = 0.f;
+#pragma unroll
+          for (int l = OZ_NSL - 2; l >= 0; --l) {
+            const float y = __uint_as_float(v[l][x]) * __int_as_float((127 - 7 * l) << 23);
+            const float s = hi + y;
+            const float bb = s - hi;
+            lo += (hi - (s - bb)) + (y - bb);
+            hi = s;
+          }
+          const float sc = __int_as_float((127 + eg + fc[x]) << 23);
+          hi *= sc;
+          lo *= sc;
+          const float s = hi + lo;                // renormalised pair
+          const float bb = s - hi;
+          out[2 * x] = s;
+          out[2 * x + 1] = (hi - (s - bb)) + (lo - bb);
+        }
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+          reinterpret_cast<float4*>(Lrow + cb)[w] = make_float4(out[4 * w], out[4 * w + 1], out[4 * w + 2], out[4 * w + 3]);
+        // slices of the row on its own scale for the trailing update: plane s, row r, columns cb ..
+        uint32_t pk[7][4];
+#pragma unroll
+        for (int x = 0; x < 8; x += 2) {
+          float q0[7], q1[7];
+          oz_slices(out[2 * x], out[2 * x + 1], rsc, q0);
+          oz_slices(out[2 * x + 2], out[2 * x + 3], rsc, q1);
+#pragma unroll
+          for (int sl = 0; sl < 7; ++sl) pk[sl][x >> 1] = Pack<__nv_bfloat16>::two(q0[sl], q1[sl]);
+        }
+#pragma unroll
+        for (int sl = 0; sl < 7; ++sl)
+          *reinterpret_cast<uint4*>(P + (int64_t)sl * ld * 64 + cb) = make_uint4(pk[sl][0], pk[sl][1], pk[sl][2], pk[sl][3]);
+      }
+      tc_fence_before();
+      mbar_arrive(tempty_bar);
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -2409,6 +2732,23 @@ cudaError_t oz_prepare(nolsm_ctx* ctx) {
     }
   }
   ctx->h_oz_panel[panels] = (int64_t)ctx->h_oz_items.size() / 2;
+  // TRSM items of every panel: (block, 128-row tile) of the rows below its diagonal block
+  ctx->h_tr_items.clear();
+  ctx->h_tr_panel.assign((size_t)panels + 1, 0);
+  for (int pnl = 0; pnl < panels; ++pnl) {
+    ctx->h_tr_panel[pnl] = (int64_t)ctx->h_tr_items.size() / 2;
+    const int t0 = (pnl + 1) * kOzPanel;
+    for (int32_t b = 0; b < ctx->n_blocks; ++b) {
+      const BlockDesc& bd = ctx->h_blocks[b];
+      for (int m0 = t0; m0 < bd.n; m0 += TM) ctx->h_tr_items.insert(ctx->h_tr_items.end(), {b, m0});
+    }
+  }
+  ctx->h_tr_panel[panels] = (int64_t)ctx->h_tr_items.size() / 2;
+  if (!ctx->h_tr_items.empty()) {
+    cudaError_t e = cudaMemcpyAsync(ctx->d_tr_items, ctx->h_tr_items.data(), sizeof(int32_t) * ctx->h_tr_items.size(),
+                                    cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return e;
+  }
   if (!ctx->h_oz_items.empty()) {
     cudaError_t e = cudaMemcpyAsync(ctx->d_oz_items, ctx->h_oz_items.data(), sizeof(int32_t) * ctx->h_oz_items.size(),
                                     cudaMemcpyHostToDevice, ctx->stream);
@@ -2416,7 +2756,7 @@ cudaError_t oz_prepare(nolsm_ctx* ctx) {
   }
   int n_bins = 0;
   for (const auto& b : ctx->h_blocks) n_bins = std::max(n_bins, b.bin + 1);
-  std::vector<CUtensorMap> maps((size_t)(2 + 2 * n_bins));
+  std::vector<CUtensorMap> maps((size_t)(3 + 2 * n_bins));
   const uint64_t rows = (uint64_t)7 * (uint64_t)std::max<int64_t>(ctx->sum_pad, 1);
   cuuint64_t gdim[2] = {(cuuint64_t)kOzPanel, rows};
   cuuint64_t gstride[1] = {(cuuint64_t)kOzPanel * 2};
@@ -2456,6 +2796,15 @@ cudaError_t oz_prepare(nolsm_ctx* ctx) {
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   }
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  // the TRSM's Minv planes: 7 x 64 rows of 64 BF16 per block, 64 x 32 boxes
+  {
+    cuuint64_t mdim[2] = {(cuuint64_t)kOzPanel, (cuuint64_t)7 * 64 * (cuuint64_t)std::max(ctx->n_blocks, 1)};
+    cuuint64_t mstride[1] = {(cuuint64_t)kOzPanel * 2};
+    r = encode(&maps[2 + 2 * n_bins], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ctx->d_oz_m, mdim, mstride, box_b, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
   cudaError_t e = cudaMemcpyAsync(ctx->d_oz_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(),
                                   cudaMemcpyHostToDevice, ctx->stream);
   if (e != cudaSuccess) return e;
@@ -2465,9 +2814,36 @@ cudaError_t oz_prepare(nolsm_ctx* ctx) {
   if (!attr_done) {
     e = cudaFuncSetAttribute(chol_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(chol_trsm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TR_SMEM);
+    if (e != cudaSuccess) return e;
     attr_done = true;
   }
   return cudaSuccess;
+}
+
+cudaError_t launch_chol_trsm_tc(nolsm_ctx* ctx, int panel, double* pool) {
+  if (panel + 1 >= (int)ctx->h_tr_panel.size()) return cudaSuccess;
+  const int64_t first = ctx->h_tr_panel[panel], count = ctx->h_tr_panel[panel + 1] - first;
+  if (count <= 0) return cudaSuccess;
+  int n_bins = 0;
+  for (const auto& b : ctx->h_blocks) n_bins = std::max(n_bins, b.bin + 1);
+  TrParams p;
+  p.items = ctx->d_tr_items + 2 * first;
+  p.n_items = (int)count;
+  p.blocks = ctx->d_blocks;
+  p.mmap = reinterpret_cast<const CUtensorMap*>(ctx->d_oz_tmaps) + 2 + 2 * n_bins;
+  p.cmaps = reinterpret_cast<const CUtensorMap*>(ctx->d_oz_tmaps) + 2;
+  p.pool = pool;
+  p.scale_exp = ctx->d_oz_exp;
+  p.mf = ctx->d_oz_f;
+  p.planes = reinterpret_cast<__nv_bfloat16*>(ctx->d_oz_planes);
+  p.c0 = panel * kOzPanel;
+  p.flags = ctx->d_flags;
+  p.budget = ctx->opt.wait_budget;
+  const int grid = (int)std::min<int64_t>(ctx->num_sms, count);
+  chol_trsm_tc_kernel<<<grid, TR_THREADS, TR_SMEM, ctx->stream>>>(p);
+  ctx->n_launches += 1;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_chol_update_tc(nolsm_ctx* ctx, int panel, double* pool) {
