@@ -144,6 +144,7 @@ void release_pools(nolsm_ctx* ctx) {
   dfree(ctx->d_tol); ctx->d_tol = nullptr;
   dfree(ctx->d_state); ctx->d_state = nullptr;
   dfree(ctx->d_tiles); ctx->d_tiles = nullptr;
+  dfree(ctx->d_cg_kbeg); ctx->d_cg_kbeg = nullptr;
   dfree(ctx->d_transpose); ctx->d_transpose = nullptr;
   dfree(ctx->d_dval); ctx->d_dval = nullptr;
   dfree(ctx->d_csr_own); ctx->d_csr_own = nullptr;
@@ -487,6 +488,7 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   CK(dalloc(ctx, &ctx->d_tol, (size_t)n_blocks));
   CK(dalloc(ctx, &ctx->d_state, (size_t)n_blocks));
   CK(dalloc(ctx, &ctx->d_tiles, (size_t)tiles_max));
+  CK(dalloc(ctx, &ctx->d_cg_kbeg, (size_t)tiles_max));
   if (!ctx->chunked) CK(dalloc(ctx, &ctx->d_dval, (size_t)nnz));
   CK(cudaMemcpyAsync(ctx->d_blocks, ctx->h_blocks.data(), sizeof(BlockDesc) * n_blocks, cudaMemcpyHostToDevice, ctx->stream));
   if (!ctx->h_slab_units.empty())
@@ -533,13 +535,14 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
     CK(dalloc(ctx, &ctx->d_oz_f, (size_t)68 * (size_t)n_blocks));
     int64_t tr_items = 0;
     for (const auto& bd : ctx->h_blocks) tr_items += (int64_t)(bd.n_pad / kOzPanel + 1) * (bd.n_pad / 128 + 1);
-    CK(dalloc(ctx, &ctx->d_tr_items, (size_t)(2 * tr_items)));
+    CK(dalloc(ctx, &ctx->d_tr_items, (size_t)tr_items));
     CK(oz_prepare(ctx));
   }
+  // FP32 path: SIMT inverse and congruence products with two-level sums; mixed: tensor cores (3 x TF32)
+  ctx->cong_simt = !mixed;
   CK(phase_mark(ctx, NOLSM_PHASE_FACTOR));
   CK(launch_cholesky_inverse(ctx, sb, chol_mode));   // marks the inverse stage between its launches
   CK(phase_mark(ctx, NOLSM_PHASE_CONGRUENCE));
-  ctx->cong_simt = !mixed;   // FP32 path: SIMT products with two-level sums; mixed: tensor cores (3 x TF32)
   CK(launch_congruence(ctx, ctx->d_t1));
   CK(phase_mark(ctx, NOLSM_PHASE_BUILD_REST));
   // the trace slab takes the factor's FP32 rounding (FP32 and double-float modes) or the FP64 factor

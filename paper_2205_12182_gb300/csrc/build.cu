@@ -874,9 +874,16 @@ __device__ __forceinline__ void cp_async16_b(void* smem_dst, const void* gsrc) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
 }
 
+// DIAG: the same inverse of each 128 x 128 diagonal block of L alone (grid (block, diagonal block)),
+// for the tiled inverse whose off-diagonal blocks run on the tensor cores (trinv_tc): the CTA also
+// zeroes the blocks right of its diagonal block in its rows (the strict upper triangle of L^-1)
+// and writes the transpose of its diagonal block into ypool (Y = X^T, the tiled inverse's second
+// operand).
+template <bool DIAG>
 __global__ void __launch_bounds__(kInvWarps * 32, 4) trinv_tile_kernel(const BlockDesc* __restrict__ blocks,
                                                                        const float* __restrict__ lpool,
-                                                                       float* __restrict__ xpool) {
+                                                                       float* __restrict__ xpool,
+                                                                       float* __restrict__ ypool) {
   __shared__ __align__(16) float As[2][32][32];   // L_ik chunk, read as broadcasts
   __shared__ __align__(16) float Bs[2][32][32];   // X_kc chunk, row k contiguous
   __shared__ float red[kInvWarps][32][32];
@@ -884,13 +891,17 @@ __global__ void __launch_bounds__(kInvWarps * 32, 4) trinv_tile_kernel(const Blo
   __shared__ float Li[32][33];
   __shared__ float rli[32];
   const BlockDesc bd = blocks[blockIdx.x];
-  const int n = bd.n, ld = bd.n_pad;
-  const float* L = lpool + bd.off_mat;
-  float* X = xpool + bd.off_mat;
+  const int ld = bd.n_pad;
+  const int o = DIAG ? 128 * (int)blockIdx.y : 0;          // first row and column of the diagonal block
+  if (o >= ld) return;
+  const int n = DIAG ? max(0, min(128, bd.n - o)) : bd.n;   // rows of the block below n
+  const int span = DIAG ? 128 : ld;
+  const float* L = lpool + bd.off_mat + (int64_t)o * ld + o;
+  float* X = xpool + bd.off_mat + (int64_t)o * ld + o;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // entries never written below: the strict upper triangle and the padding stay zero
-  for (int r = warp; r < ld; r += kInvWarps)
-    for (int c = lane; c < ld; c += 32)
+  for (int r = warp; r < span; r += kInvWarps)
+    for (int c = lane; c < (DIAG ? ld - o : span); c += 32)
       if (c > r || r >= n) X[(int64_t)r * ld + c] = 0.f;
   // rows [row0, row0 + 32) x columns [col0, col0 + 32) of a matrix into a chunk (zero rows >= rows)
   auto load_chunk = [&](float(*dst)[32], const float* src, int row0, int col0, int rows) {
@@ -985,6 +996,14 @@ __global__ void __launch_bounds__(kInvWarps * 32, 4) trinv_tile_kernel(const Blo
       if (r < ibw && c <= r) X[(int64_t)(i0 + r) * ld + i0 + c] = Xi[r][c];
     }
     __syncthreads();
+  }
+  if constexpr (DIAG) {
+    // Y's diagonal block is X's transposed (the CTA's own global writes are visible after the barrier)
+    float* Y = ypool + bd.off_mat + (int64_t)o * ld + o;
+    for (int e = tid; e < 128 * 128; e += kInvWarps * 32) {
+      const int r = e >> 7, c = e & 127;
+      Y[(int64_t)c * ld + r] = X[(int64_t)r * ld + c];
+    }
   }
 }
 
@@ -1121,12 +1140,15 @@ cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode) {
                                                                                        s32);
     ctx->n_launches += 1;
     if ((e = phase_mark(ctx, NOLSM_PHASE_INVERSE)) != cudaSuccess) return e;
-    trinv_tile_kernel<<<ctx->n_blocks, kInvWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
+    // mixed paths: the tiled inverse with its off-diagonal blocks on the tensor cores (three TF32
+    // passes, the congruence's arithmetic); FP32 path: the SIMT inverse with two-level sums
+    if (!ctx->cong_simt) return launch_trinv_tc(ctx, s32, ctx->d_t1);
+    trinv_tile_kernel<false><<<ctx->n_blocks, kInvWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv, nullptr);
   } else if (mode == NOLSM_CHOL_DF64_SIMT) {
     cholesky_df_kernel<<<ctx->n_blocks, kCholWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, ctx->d_flags, 0,
                                                                           1 << 30, nullptr, 1 << 30, nullptr);
     if ((e = phase_mark(ctx, NOLSM_PHASE_INVERSE)) != cudaSuccess) return e;
-    trinv_tile_kernel<<<ctx->n_blocks, kInvWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
+    trinv_tile_kernel<false><<<ctx->n_blocks, kInvWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv, nullptr);
   } else if (mode == NOLSM_CHOL_FP64_INV64) {
     cholesky_kernel<double, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, sb, nullptr, ctx->d_flags);
     if ((e = phase_mark(ctx, NOLSM_PHASE_INVERSE)) != cudaSuccess) return e;
@@ -1135,14 +1157,21 @@ cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode) {
   } else if (mode == NOLSM_CHOL_FP64) {
     cholesky_kernel<double, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, ctx->d_flags);
     if ((e = phase_mark(ctx, NOLSM_PHASE_INVERSE)) != cudaSuccess) return e;
-    trinv_tile_kernel<<<ctx->n_blocks, kInvWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
+    trinv_tile_kernel<false><<<ctx->n_blocks, kInvWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv, nullptr);
   } else {
     to_f32_kernel<double><<<sq_grid(ctx->n_blocks), 256, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, 0);
     cholesky_kernel<float, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, s32, nullptr, ctx->d_flags);
     if ((e = phase_mark(ctx, NOLSM_PHASE_INVERSE)) != cudaSuccess) return e;
-    trinv_tile_kernel<<<ctx->n_blocks, kInvWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
+    trinv_tile_kernel<false><<<ctx->n_blocks, kInvWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv, nullptr);
   }
   return cudaGetLastError();
+}
+
+// X_ii = L_ii^-1 of every 128 x 128 diagonal block, Y_ii = X_ii^T, strict upper blocks of X zeroed
+void trinv_diag_launch(nolsm_ctx* ctx, const float* l32, float* ypool, int max_nb) {
+  trinv_tile_kernel<true><<<dim3(ctx->n_blocks, max_nb), kInvWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, l32,
+                                                                                         ctx->d_linv, ypool);
+  ctx->n_launches += 1;
 }
 
 cudaError_t launch_congruence(nolsm_ctx* ctx, float* t1) {

@@ -37,6 +37,14 @@ struct BlockDesc {
   int64_t off_slab; // n_pad*c element offset in every slab pool (column-major, ld = n_pad)
 };
 
+// One 128-row tile of the tensor-core TRSM with what its roles need about the block, resolved on
+// the host: a role loads one record instead of the dependent chain item -> block descriptor.
+struct TrItem {
+  int32_t b, m0, n, ld;       // block, first row of the tile, n_b, n_pad
+  int32_t row_off, pos, bin, pad;
+  int64_t off_mat;
+};
+
 // Newton-Schulz state of one block during a sign evaluation.
 struct NsState {
   float alpha;      // X_0 = (A0 - mu I) / alpha
@@ -148,10 +156,10 @@ struct nolsm_ctx {
   // own scale 2^f_c; per block 68 ints: f_0 .. f_63 and g = the largest row exponent of the panel
   uint16_t* d_oz_m = nullptr;
   int32_t* d_oz_f = nullptr;
-  int32_t* d_tr_items = nullptr;     // (block, first row) of every panel's 128-row TRSM tiles
+  nolsm::TrItem* d_tr_items = nullptr;   // every panel's 128-row TRSM tiles
   std::vector<int32_t> h_oz_items;
   std::vector<int64_t> h_oz_panel;   // item offset of panel p (size panels + 1)
-  std::vector<int32_t> h_tr_items;
+  std::vector<nolsm::TrItem> h_tr_items;
   std::vector<int64_t> h_tr_panel;   // TRSM item offset of panel p (size panels + 1)
   int64_t sum_pad = 0;
   std::vector<int32_t> h_slab_units;
@@ -161,6 +169,7 @@ struct nolsm_ctx {
   nolsm::NsState* d_state = nullptr;
   nolsm::Tile* d_tiles = nullptr;
   int64_t max_tiles = 0;        // full tile count (capacity of d_tiles)
+  int32_t* d_cg_kbeg = nullptr; // first K of each tile of the tiled inverse (capacity max_tiles)
   int64_t max_tiles_tc = 0;     // upper-triangular tensor-core tiles of all blocks
   nolsm::DevFlags* d_flags = nullptr;
   nolsm::DevFlags* h_flags = nullptr;   // pinned mirror
@@ -284,6 +293,8 @@ cudaError_t launch_slab_tc(nolsm_ctx* ctx);
 cudaError_t oz_prepare(nolsm_ctx* ctx);                        // items and tensor maps of the updates
 cudaError_t launch_chol_update_tc(nolsm_ctx* ctx, int panel, double* pool);
 cudaError_t launch_chol_trsm_tc(nolsm_ctx* ctx, int panel, double* pool);
+cudaError_t launch_trinv_tc(nolsm_ctx* ctx, const float* l32, float* ypool);   // mixed paths' L^-1
+void trinv_diag_launch(nolsm_ctx* ctx, const float* l32, float* ypool, int max_nb);
 constexpr int kOzPanel = 64;      // panel width of the blocked double-float Cholesky
 int tc_tile_n();
 constexpr int kSlabNarrow = 32;   // columns of a narrow refinement piece

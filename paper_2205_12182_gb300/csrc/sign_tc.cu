@@ -1911,9 +1911,8 @@ constexpr int TR_SMEM = 1024 + TR_BAR_OFF + 256;
 static_assert(TR_SMEM <= 227 * 1024, "shared memory of the TRSM kernel");
 
 struct TrParams {
-  const int32_t* items;         // (block, m0) pairs of this panel, grouped by block
+  const TrItem* items;          // this panel's tiles, grouped by block
   int n_items;
-  const BlockDesc* blocks;
   const CUtensorMap* mmap;      // 64 x 32 boxes over the Minv planes (7 x 64 rows per block)
   const CUtensorMap* cmaps;     // per bin [2 bin]: 16 x 128 boxes over the pool of pairs
   double* pool;                 // factor in double-float pairs (8 bytes an entry)
@@ -1982,8 +1981,8 @@ __global__ void __launch_bounds__(TR_THREADS, 1) chol_trsm_tc_kernel(const __gri
       bool armed = false, ok = true;
       uint32_t arm_parity = 0, sarmed = 0, sarm_parity = 0;
       for (int it = first; it < last && ok; ++it) {
-        const int b = p.items[2 * it], m0 = p.items[2 * it + 1];
-        const BlockDesc bd = p.blocks[b];
+        const TrItem ti = p.items[it];
+        const int b = ti.b;
         if (b != cur) {
           cur = b;
           if (!mbar_wait(bempty_bar, bph ^ 1u, budget, abort_flag)) { ok = false; break; }
@@ -1996,11 +1995,11 @@ __global__ void __launch_bounds__(TR_THREADS, 1) chol_trsm_tc_kernel(const __gri
           arm_parity = bph;
           bph ^= 1u;
         }
-        const CUtensorMap* cmap = p.cmaps + 2 * bd.bin;
+        const CUtensorMap* cmap = p.cmaps + 2 * ti.bin;
         for (int box = 0; box < 4; ++box) {
           if (!mbar_wait(&sempty_bar[ps], pph ^ 1u, budget, abort_flag)) { ok = false; break; }
           mbar_expect_tx(&sfull_bar[ps], OZ_CBOX_BYTES);
-          tma_load_2d(smem + TR_S_OFF + ps * OZ_CBOX_BYTES, cmap, &sfull_bar[ps], c0 + 16 * box, bd.pos * bd.n_pad + m0);
+          tma_load_2d(smem + TR_S_OFF + ps * OZ_CBOX_BYTES, cmap, &sfull_bar[ps], c0 + 16 * box, ti.pos * ti.ld + ti.m0);
           sarmed |= 1u << ps;
           sarm_parity = (sarm_parity & ~(1u << ps)) | (pph << ps);
           if (++ps == TR_NSS) { ps = 0; pph ^= 1u; }
@@ -2022,7 +2021,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1) chol_trsm_tc_kernel(const __gri
       uint32_t bph = 0, aph = 0, tph = 0;
       bool ok = true;
       for (int it = first; it < last && ok; ++it) {
-        const int b = p.items[2 * it];
+        const int b = p.items[it].b;
         if (b != cur) {
           if (cur >= 0) umma_commit(bempty_bar);   // the previous block's planes are free once its MMAs are done
           cur = b;
@@ -2065,11 +2064,14 @@ __global__ void __launch_bounds__(TR_THREADS, 1) chol_trsm_tc_kernel(const __gri
     uint32_t aph = 0, sph = 0;
     int ss = 0;
     bool ok = true;
+    // the next item's record is loaded one item ahead (no dependent load waits at the item's start)
+    TrItem nx = first < last ? p.items[first] : TrItem{};
     for (int it = first; it < last && ok; ++it) {
-      const int b = p.items[2 * it], m0 = p.items[2 * it + 1];
-      const BlockDesc bd = p.blocks[b];
-      const int r = m0 + ct;
-      const float esc = oz_scale(r < bd.n ? p.scale_exp[bd.row_off + r] + p.mf[(int64_t)b * 68 + 64] : 0);
+      const TrItem ti = nx;
+      if (it + 1 < last) nx = p.items[it + 1];
+      const int r = ti.m0 + ct;
+      const bool live = r < ti.n;
+      const float esc = oz_scale(live ? p.scale_exp[ti.row_off + r] + p.mf[(int64_t)ti.b * 68 + 64] : 0);
       if (!mbar_wait(aempty_bar, aph ^ 1u, budget, abort_flag)) { ok = false; break; }
       aph ^= 1u;
       for (int box = 0; box < 4; ++box) {
@@ -2078,7 +2080,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1) chol_trsm_tc_kernel(const __gri
         float f[32];
 #pragma unroll
         for (int w = 0; w < 8; ++w) {
-          const float4 x = r < bd.n ? *reinterpret_cast<const float4*>(st + sw128(ct, 16 * w)) : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float4 x = live ? *reinterpret_cast<const float4*>(st + sw128(ct, 16 * w)) : make_float4(0.f, 0.f, 0.f, 0.f);
           f[4 * w] = x.x;
           f[4 * w + 1] = x.y;
           f[4 * w + 2] = x.z;
@@ -2117,10 +2119,18 @@ __global__ void __launch_bounds__(TR_THREADS, 1) chol_trsm_tc_kernel(const __gri
     // ------------------------------------------------------------ epilogue
     const int q = warp & 3, h = (warp - 6) >> 2;   // a warp reads the TMEM lanes of quarter warp % 4
     uint32_t tph = 0;
+    // the next item's record is loaded one item ahead; the exponents it points to are loaded before
+    // the wait for the accumulators, so that neither load chain stalls the epilogue
+    TrItem nx = first < last ? p.items[first] : TrItem{};
     for (int it = first; it < last; ++it) {
-      const int b = p.items[2 * it], m0 = p.items[2 * it + 1];
-      const BlockDesc bd = p.blocks[b];
-      const int n = bd.n, ld = bd.n_pad;
+      const TrItem ti = nx;
+      if (it + 1 < last) nx = p.items[it + 1];
+      const int n = ti.n, ld = ti.ld;
+      const int r = ti.m0 + q * 32 + lane;
+      const int32_t* F = p.mf + (int64_t)ti.b * 68;
+      const int er = r < n ? p.scale_exp[ti.row_off + r] : 0;
+      const int g = F[64];
+      const int fl = F[32 * h + lane];            // f_c of this half's column lane, shared by shuffles
       if (!__all_sync(0xffffffffu, mbar_wait(tfull_bar, tph, budget, abort_flag))) {
         set_error(p.flags, NOLSM_ETIMEOUT);
         *abort_flag = 1;
@@ -2128,14 +2138,10 @@ __global__ void __launch_bounds__(TR_THREADS, 1) chol_trsm_tc_kernel(const __gri
       }
       tph ^= 1u;
       tc_fence_after();
-      const int r = m0 + q * 32 + lane;
-      const int32_t* F = p.mf + (int64_t)b * 68;
-      const int er = r < n ? p.scale_exp[bd.row_off + r] : 0;
-      const int eg = er + F[64] - 14;
+      const int eg = er + g - 14;
       const float rsc = oz_scale(er);
-      const int fl = F[32 * h + lane];            // f_c of this half's column lane, shared by shuffles
-      float2* Lrow = reinterpret_cast<float2*>(p.pool + bd.off_mat) + (int64_t)r * ld + c0;
-      __nv_bfloat16* P = p.planes + ((int64_t)7 * bd.row_off + r) * 64;
+      float2* Lrow = reinterpret_cast<float2*>(p.pool + ti.off_mat) + (int64_t)r * ld + c0;
+      __nv_bfloat16* P = p.planes + ((int64_t)7 * ti.row_off + r) * 64;
       for (int j = 0; j < 4; ++j) {
         const int cb = 32 * h + 8 * j;            // first of this chunk's 8 columns of the panel
         uint32_t v[OZ_NSL][8];
@@ -2224,12 +2230,16 @@ constexpr int CG_THREADS = 320;
 constexpr int CG_TMEM_COLS = 256;                           // two 128-column accumulators
 static_assert(CG_SMEM <= 227 * 1024, "shared memory of the congruence kernel");
 
+constexpr int CG_POOLS = 5;  // 0 L^-1, 1 A0 pool, 2 T1 (Y = X^T during the inverse), 3 L (FP32), 4 R^T scratch
 struct CgParams {
   const Tile* tiles;
+  const int32_t* kbeg;        // first K of each tile (NULL: 0)
   int n_tiles;
   const BlockDesc* blocks;
-  const CUtensorMap* tmaps;   // per bin: loads of [L^-1, A0 pool, T1], stores into [L^-1, A0 pool, T1]
-  int map_a, map_b, map_c;    // pools of A, B and the output (0 L^-1, 1 A0 pool, 2 T1)
+  const CUtensorMap* tmaps;   // per bin: loads of the CG_POOLS pools, then stores into them
+  int map_a, map_b, map_c;    // pools of A, B and the output
+  int map_t;                  // pool that also receives the transposed output (-1: none)
+  int neg;                    // store -C
   int sym;
   int interleave;             // 1: tile i to CTA i mod grid (large blocks); 0: contiguous runs
   float* out_pool;
@@ -2301,10 +2311,11 @@ __global__ void __launch_bounds__(CG_THREADS, 1) cong_tc_kernel(const __grid_con
       for (int i = 0; i < n_local && ok; ++i) {
         const Tile tl = p.tiles[first + i * step];
         const BlockDesc bd = p.blocks[tl.block];
-        const CUtensorMap* ma = p.tmaps + bd.bin * 6 + p.map_a;
-        const CUtensorMap* mb = p.tmaps + bd.bin * 6 + p.map_b;
+        const CUtensorMap* ma = p.tmaps + bd.bin * 2 * CG_POOLS + p.map_a;
+        const CUtensorMap* mb = p.tmaps + bd.bin * 2 * CG_POOLS + p.map_b;
         const int rowbase = bd.pos * bd.n_pad;
-        for (int k0 = 0; k0 < tl.kend; k0 += CG_TK) {
+        const int kb = p.kbeg ? p.kbeg[first + i * step] : 0;
+        for (int k0 = kb; k0 < tl.kend; k0 += CG_TK) {
           if (!mbar_wait(&empty_bar[s], ph ^ 1u, budget, abort_flag)) { ok = false; break; }
           mbar_expect_tx(&full_bar[s], 2 * CG_BOX_BYTES);
           uint8_t* st = smem + s * CG_STAGE_BYTES;
@@ -2337,7 +2348,8 @@ __global__ void __launch_bounds__(CG_THREADS, 1) cong_tc_kernel(const __grid_con
         if (!mbar_wait(&tempty_bar[acc], tph[acc] ^ 1u, budget, abort_flag)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * CG_TN);
-        for (int k0 = 0; k0 < tl.kend; k0 += CG_TK) {
+        const int kb = p.kbeg ? p.kbeg[first + i * step] : 0;
+        for (int k0 = kb; k0 < tl.kend; k0 += CG_TK) {
           if (!mbar_wait(&conv_bar[s], ph, budget, abort_flag)) { ok = false; break; }
           tc_fence_after();
           const uint32_t base = smem_u32(smem + s * CG_STAGE_BYTES);
@@ -2346,7 +2358,7 @@ __global__ void __launch_bounds__(CG_THREADS, 1) cong_tc_kernel(const __grid_con
 #pragma unroll
           for (int kk = 0; kk < CG_TK / 8; ++kk) {
             const uint64_t o = (uint64_t)(kk * 2);   // 8 FP32 = 32 bytes along K inside the swizzle atom
-            umma_tf32(d_tmem, al + o, bh + o, idesc, (k0 | kk) != 0);
+            umma_tf32(d_tmem, al + o, bh + o, idesc, (k0 != kb || kk != 0) ? 1u : 0u);
             umma_tf32(d_tmem, ah + o, bl + o, idesc, 1u);
             umma_tf32(d_tmem, ah + o, bh + o, idesc, 1u);
           }
@@ -2373,8 +2385,9 @@ __global__ void __launch_bounds__(CG_THREADS, 1) cong_tc_kernel(const __grid_con
     uint32_t ph = 0;
     for (int i = 0; i < n_local; ++i) {
       const Tile tl = p.tiles[first + i * step];
+      const int kb = p.kbeg ? p.kbeg[first + i * step] : 0;
       bool ok = true;
-      for (int k0 = 0; k0 < tl.kend; k0 += CG_TK) {
+      for (int k0 = kb; k0 < tl.kend; k0 += CG_TK) {
         if (!mbar_wait(&full_bar[s], ph, budget, abort_flag)) { ok = false; break; }
         uint8_t* st = smem + s * CG_STAGE_BYTES;
         // 2 boxes x 16 KB = 2048 float4; 16 per thread (position-wise, so the swizzle is irrelevant)
@@ -2419,13 +2432,18 @@ __global__ void __launch_bounds__(CG_THREADS, 1) cong_tc_kernel(const __grid_con
       }
       tc_fence_after();
       const int ld = bd.n_pad, rowbase = bd.pos * ld;
-      const CUtensorMap* smap = p.tmaps + bd.bin * 6 + 3 + p.map_c;
+      const CUtensorMap* smap = p.tmaps + bd.bin * 2 * CG_POOLS + CG_POOLS + p.map_c;
+      const bool mir = p.sym || p.map_t >= 0;   // the transposed chunk is stored too
+      const CUtensorMap* tmap = p.sym ? smap : p.tmaps + bd.bin * 2 * CG_POOLS + CG_POOLS + (p.map_t < 0 ? 0 : p.map_t);
+      const uint32_t sgn = p.neg ? 0x80000000u : 0u;
       float* out = p.out_pool + bd.off_mat;
       const int r0 = tl.m0 + q * 32, r = r0 + lane;
       for (int c0 = 0; c0 < CG_TN; c0 += 32) {
         const int cg0 = tl.n0 + c0;
         uint32_t v[32];
         tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * CG_TN + c0), v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] ^= sgn;
         if (p.sym && cg0 < r0) continue;        // below the diagonal: the mirror of another chunk
         if (p.sym && cg0 == r0) {
 #pragma unroll
@@ -2443,7 +2461,7 @@ __global__ void __launch_bounds__(CG_THREADS, 1) cong_tc_kernel(const __grid_con
 #pragma unroll
         for (int u = 0; u < 8; ++u)
           *reinterpret_cast<uint4*>(D + sw128(lane, 16 * u)) = make_uint4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
-        if (p.sym) {
+        if (mir) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) *reinterpret_cast<uint32_t*>(M + sw128(j, 4 * lane)) = v[j];
         }
@@ -2451,7 +2469,7 @@ __global__ void __launch_bounds__(CG_THREADS, 1) cong_tc_kernel(const __grid_con
         __syncwarp();
         if (lane == 0) {
           tma_store_2d(smap, D, cg0, rowbase + r0);
-          if (p.sym) tma_store_2d(smap, M, r0, rowbase + cg0);
+          if (mir) tma_store_2d(tmap, M, r0, rowbase + cg0);
           bulk_commit();
         }
       }
@@ -2623,10 +2641,10 @@ cudaError_t launch_gemm_tc(nolsm_ctx* ctx, int phase) {
   return cudaSuccess;
 }
 
-// The congruence on the tensor cores: T1 = L^-1 T_b(H0) (all tiles; L^-1 is lower triangular, so a
-// tile's K stops at m0 + 128), then A0 = T1 L^-T (tiles on or above the diagonal, K stops at
-// n0 + 128, output mirrored).  Tensor maps over the FP32 pools are encoded here, per bin.
-cudaError_t launch_congruence_tc(nolsm_ctx* ctx, float* t1) {
+// Tensor maps of the 3 x TF32 product kernel, per bin over the FP32 pools L^-1, A0, T1, L (the
+// factor's FP32 rounding) and the R^T scratch (loads: 128 x 32 boxes, stores: 32 x 32 boxes).  L and
+// the scratch lie in the second half of the build's FP64 scratch (sb + sum_sq).
+cudaError_t cg_maps(nolsm_ctx* ctx, float* t1) {
   auto encode = get_encode();
   if (!encode) return cudaErrorNotSupported;
   int n_bins = 0;
@@ -2638,26 +2656,25 @@ cudaError_t launch_congruence_tc(nolsm_ctx* ctx, float* t1) {
     bin_cnt[b.bin] += 1;
     bin_pad[b.bin] = b.n_pad;
   }
-  std::vector<CUtensorMap> maps((size_t)n_bins * 6);
-  int max_pad = 0;
-  for (const auto& b : ctx->h_blocks) max_pad = std::max(max_pad, b.n_pad);
-  float* pools[3] = {ctx->d_linv, ctx->d_a0, t1};
+  std::vector<CUtensorMap> maps((size_t)n_bins * 2 * CG_POOLS);
+  float* l32 = reinterpret_cast<float*>(ctx->d_sb + ctx->sum_sq);
+  float* pools[CG_POOLS] = {ctx->d_linv, ctx->d_a0, t1, l32, l32 + ctx->sum_sq};
   for (int bi = 0; bi < n_bins; ++bi)
-    for (int pi = 0; pi < 3; ++pi) {
+    for (int pi = 0; pi < CG_POOLS; ++pi) {
       const uint64_t np = (uint64_t)bin_pad[bi];
       void* base = pools[pi] + bin_off[bi];
       cuuint64_t gdim[2] = {np, np * (uint64_t)bin_cnt[bi]};
       cuuint64_t gstride[1] = {np * 4};
       cuuint32_t estr[2] = {1, 1};
       cuuint32_t box[2] = {CG_TK, TM};
-      CUresult r = encode(&maps[(size_t)bi * 6 + pi], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, gdim, gstride, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      CUresult r = encode(&maps[(size_t)bi * 2 * CG_POOLS + pi], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, gdim, gstride,
+                          box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
       cuuint32_t sbox[2] = {32, 32};
-      r = encode(&maps[(size_t)bi * 6 + 3 + pi], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, gdim, gstride, sbox, estr,
-                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      r = encode(&maps[(size_t)bi * 2 * CG_POOLS + CG_POOLS + pi], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, gdim,
+                 gstride, sbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                 CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     }
   if (ctx->cg_tmap_cap < maps.size()) {
@@ -2670,12 +2687,46 @@ cudaError_t launch_congruence_tc(nolsm_ctx* ctx, float* t1) {
   cudaError_t e = cudaMemcpyAsync(ctx->d_cg_tmaps, maps.data(), maps.size() * sizeof(CUtensorMap),
                                   cudaMemcpyHostToDevice, ctx->stream);
   if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(ctx->stream);   // maps is a host temporary
+  if (e != cudaSuccess) return e;
   static bool attr_done = false;
   if (!attr_done) {
     e = cudaFuncSetAttribute(cong_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CG_SMEM);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
+  return cudaSuccess;
+}
+
+CgParams cg_params(nolsm_ctx* ctx, const Tile* tiles, const int32_t* kbeg, int n_tiles, int a, int b, int c, int t,
+                   int neg, int sym, float* out) {
+  int max_pad = 0;
+  for (const auto& bd : ctx->h_blocks) max_pad = std::max(max_pad, bd.n_pad);
+  CgParams p;
+  p.tiles = tiles;
+  p.kbeg = kbeg;
+  p.n_tiles = n_tiles;
+  p.blocks = ctx->d_blocks;
+  p.tmaps = reinterpret_cast<const CUtensorMap*>(ctx->d_cg_tmaps);
+  p.map_a = a;
+  p.map_b = b;
+  p.map_c = c;
+  p.map_t = t;
+  p.neg = neg;
+  p.sym = sym;
+  p.interleave = max_pad >= 1024;
+  p.out_pool = out;
+  p.flags = ctx->d_flags;
+  p.budget = ctx->opt.wait_budget;
+  return p;
+}
+
+// The congruence on the tensor cores: T1 = L^-1 T_b(H0) (all tiles; L^-1 is lower triangular, so a
+// tile's K stops at m0 + 128), then A0 = T1 L^-T (tiles on or above the diagonal, K stops at
+// n0 + 128, output mirrored).
+cudaError_t launch_congruence_tc(nolsm_ctx* ctx, float* t1) {
+  cudaError_t e = cg_maps(ctx, t1);
+  if (e != cudaSuccess) return e;
   for (int pass = 0; pass < 2; ++pass) {
     std::vector<Tile> tl;
     for (int32_t i = 0; i < ctx->n_blocks; ++i) {
@@ -2689,22 +2740,68 @@ cudaError_t launch_congruence_tc(nolsm_ctx* ctx, float* t1) {
     if (e != cudaSuccess) return e;
     e = cudaStreamSynchronize(ctx->stream);   // tl is a host temporary
     if (e != cudaSuccess) return e;
-    CgParams p;
-    p.tiles = ctx->d_tiles;
-    p.n_tiles = (int)tl.size();
-    p.blocks = ctx->d_blocks;
-    p.tmaps = reinterpret_cast<const CUtensorMap*>(ctx->d_cg_tmaps);
-    p.map_a = pass ? 2 : 0;                   // T1 : L^-1
-    p.map_b = pass ? 0 : 1;                   // L^-1 : T_b(H0) in the A0 pool
-    p.map_c = pass ? 1 : 2;                   // A0 pool : T1
-    p.sym = pass;
-    p.interleave = max_pad >= 1024;
-    p.out_pool = pass ? ctx->d_a0 : t1;
-    p.flags = ctx->d_flags;
-    p.budget = ctx->opt.wait_budget;
+    // pass 0: T1 (pool 2) = L^-1 (pool 0) x T_b(H0) (A0 pool, 1); pass 1: A0 pool = T1 x L^-1, mirrored
+    const CgParams p = pass ? cg_params(ctx, ctx->d_tiles, nullptr, (int)tl.size(), 2, 0, 1, -1, 0, 1, ctx->d_a0)
+                            : cg_params(ctx, ctx->d_tiles, nullptr, (int)tl.size(), 0, 1, 2, -1, 0, 0, t1);
     cong_tc_kernel<<<ctx->num_sms, CG_THREADS, CG_SMEM, ctx->stream>>>(p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// L^-1 of every block (mixed paths) by 128-row block rows, X = L^-1 and its transpose Y = X^T:
+//   X_ii = L_ii^-1 (SIMT, trinv_tile_kernel<true>, which also writes Y_ii and zeroes the strict upper
+//   blocks), then for i = 1, 2, ...:
+//   R_ic^T = sum_{k=c}^{i-1} Y_ck L_ik^T   and   X_ic = -X_ii R_ic  (Y_ci = X_ic^T stored beside it)
+// for every c < i, as 3 x TF32 tensor-core products over tile lists (two launches per block row: the
+// second needs the first's R^T, the next row needs this row's X and Y).  Y lives in the T1 pool (T1 is
+// formed after the inverse), R^T in the scratch after the FP32 factor.
+cudaError_t launch_trinv_tc(nolsm_ctx* ctx, const float* l32, float* ypool) {
+  int max_nb = 0;
+  for (const auto& bd : ctx->h_blocks) max_nb = std::max(max_nb, bd.n_pad / TM);
+  trinv_diag_launch(ctx, l32, ypool, max_nb);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || max_nb < 2) return e;
+  if ((e = cg_maps(ctx, ypool)) != cudaSuccess) return e;
+  std::vector<Tile> tl;
+  std::vector<int32_t> kb;
+  std::vector<int64_t> start;   // launch k covers [start[k], start[k + 1])
+  for (int i = 1; i < max_nb; ++i)
+    for (int prod = 0; prod < 2; ++prod) {
+      start.push_back((int64_t)tl.size());
+      for (int32_t b = 0; b < ctx->n_blocks; ++b) {
+        if (ctx->h_blocks[b].n_pad / TM <= i) continue;
+        for (int c = 0; c < i; ++c) {
+          if (prod == 0) {
+            tl.push_back(Tile{b, TM * c, TM * i, TM * i});   // R^T tile (c, i), K over [128 c, 128 i)
+            kb.push_back(TM * c);
+          } else {
+            tl.push_back(Tile{b, TM * i, TM * c, TM * (i + 1)});   // X tile (i, c), K over the block row i
+            kb.push_back(TM * i);
+          }
+        }
+      }
+    }
+  start.push_back((int64_t)tl.size());
+  if ((int64_t)tl.size() > ctx->max_tiles) return cudaErrorInvalidValue;
+  e = cudaMemcpyAsync(ctx->d_tiles, tl.data(), tl.size() * sizeof(Tile), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->d_cg_kbeg, kb.data(), kb.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);   // host temporaries
+  if (e != cudaSuccess) return e;
+  float* rt = const_cast<float*>(l32) + ctx->sum_sq;
+  for (size_t k = 0; k + 1 < start.size(); ++k) {
+    const int n = (int)(start[k + 1] - start[k]);
+    if (n == 0) continue;
+    const Tile* t = ctx->d_tiles + start[k];
+    const int32_t* kp = ctx->d_cg_kbeg + start[k];
+    // pools: 0 X = L^-1, 2 Y, 3 L, 4 R^T
+    const CgParams p = (k % 2 == 0) ? cg_params(ctx, t, kp, n, 2, 3, 4, -1, 0, 0, rt)
+                                    : cg_params(ctx, t, kp, n, 0, 4, 0, 2, 1, 0, ctx->d_linv);
+    cong_tc_kernel<<<ctx->num_sms, CG_THREADS, CG_SMEM, ctx->stream>>>(p);
+    ctx->n_launches += 1;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -2736,16 +2833,17 @@ cudaError_t oz_prepare(nolsm_ctx* ctx) {
   ctx->h_tr_items.clear();
   ctx->h_tr_panel.assign((size_t)panels + 1, 0);
   for (int pnl = 0; pnl < panels; ++pnl) {
-    ctx->h_tr_panel[pnl] = (int64_t)ctx->h_tr_items.size() / 2;
+    ctx->h_tr_panel[pnl] = (int64_t)ctx->h_tr_items.size();
     const int t0 = (pnl + 1) * kOzPanel;
     for (int32_t b = 0; b < ctx->n_blocks; ++b) {
       const BlockDesc& bd = ctx->h_blocks[b];
-      for (int m0 = t0; m0 < bd.n; m0 += TM) ctx->h_tr_items.insert(ctx->h_tr_items.end(), {b, m0});
+      for (int m0 = t0; m0 < bd.n; m0 += TM)
+        ctx->h_tr_items.push_back(TrItem{b, m0, bd.n, bd.n_pad, bd.row_off, bd.pos, bd.bin, 0, bd.off_mat});
     }
   }
-  ctx->h_tr_panel[panels] = (int64_t)ctx->h_tr_items.size() / 2;
+  ctx->h_tr_panel[panels] = (int64_t)ctx->h_tr_items.size();
   if (!ctx->h_tr_items.empty()) {
-    cudaError_t e = cudaMemcpyAsync(ctx->d_tr_items, ctx->h_tr_items.data(), sizeof(int32_t) * ctx->h_tr_items.size(),
+    cudaError_t e = cudaMemcpyAsync(ctx->d_tr_items, ctx->h_tr_items.data(), sizeof(TrItem) * ctx->h_tr_items.size(),
                                     cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) return e;
   }
@@ -2828,9 +2926,8 @@ cudaError_t launch_chol_trsm_tc(nolsm_ctx* ctx, int panel, double* pool) {
   int n_bins = 0;
   for (const auto& b : ctx->h_blocks) n_bins = std::max(n_bins, b.bin + 1);
   TrParams p;
-  p.items = ctx->d_tr_items + 2 * first;
+  p.items = ctx->d_tr_items + first;
   p.n_items = (int)count;
-  p.blocks = ctx->d_blocks;
   p.mmap = reinterpret_cast<const CUtensorMap*>(ctx->d_oz_tmaps) + 2 + 2 * n_bins;
   p.cmaps = reinterpret_cast<const CUtensorMap*>(ctx->d_oz_tmaps) + 2;
   p.pool = pool;
