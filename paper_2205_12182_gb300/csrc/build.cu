@@ -925,11 +925,18 @@ __global__ void __launch_bounds__(kInvWarps * 32, 4) trinv_tile_kernel(const Blo
       __syncwarp();
       rli[lane] = 1.f / Li[lane][lane];
       __syncwarp();
-      for (int r = 0; r < 32; ++r) {
-        float v = (r == lane) ? 1.f : 0.f;
-        if (r > lane)
-          for (int q = lane; q < r; ++q) v = fmaf(-Li[r][q], Xi[q][lane], v);
-        Xi[r][lane] = (r >= lane) ? v * rli[r] : 0.f;
+      // right-looking, lane = column, the partial rows in registers: once row q is final, its terms
+      // leave every later row.  Row r still takes -L_rq x_q for q = 0, 1, ..., r - 1 in that order, and
+      // the terms with q < lane are exact zeros, so the result is the left-looking sum's bit for bit.
+      float acc[32];
+#pragma unroll
+      for (int r = 0; r < 32; ++r) acc[r] = (r == lane) ? 1.f : 0.f;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const float xq = (q >= lane) ? acc[q] * rli[q] : 0.f;
+        Xi[q][lane] = xq;
+#pragma unroll
+        for (int r = q + 1; r < 32; ++r) acc[r] = fmaf(-Li[r][q], xq, acc[r]);
       }
     }
     __syncthreads();
@@ -998,11 +1005,16 @@ __global__ void __launch_bounds__(kInvWarps * 32, 4) trinv_tile_kernel(const Blo
     __syncthreads();
   }
   if constexpr (DIAG) {
-    // Y's diagonal block is X's transposed (the CTA's own global writes are visible after the barrier)
+    // Y's diagonal block is X's transposed, by 32 x 32 tiles through shared memory (both sides
+    // coalesced; the CTA's own global writes are visible after the barrier)
     float* Y = ypool + bd.off_mat + (int64_t)o * ld + o;
-    for (int e = tid; e < 128 * 128; e += kInvWarps * 32) {
-      const int r = e >> 7, c = e & 127;
-      Y[(int64_t)c * ld + r] = X[(int64_t)r * ld + c];
+    float(*T)[33] = reinterpret_cast<float(*)[33]>(&red[0][0][0]);
+    for (int t = 0; t < 16; ++t) {
+      const int ti = t >> 2, tj = t & 3;
+      for (int e = tid; e < 1024; e += kInvWarps * 32) T[e >> 5][e & 31] = X[(int64_t)(32 * ti + (e >> 5)) * ld + 32 * tj + (e & 31)];
+      __syncthreads();
+      for (int e = tid; e < 1024; e += kInvWarps * 32) Y[(int64_t)(32 * tj + (e >> 5)) * ld + 32 * ti + (e & 31)] = T[e & 31][e >> 5];
+      __syncthreads();
     }
   }
 }
