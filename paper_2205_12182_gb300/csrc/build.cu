@@ -603,43 +603,50 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
 
 // ---- the 64 x 64 diagonal block of the blocked double-float Cholesky ----------------------------
 // The CTA (128 threads) factors a 32 x 32 SPD block in shared memory, P = L L^T in place (lower
-// triangle), and writes X = L^-1 (lower triangle, zero above).  Right-looking in both: per column,
-// one thread takes the pivot, the column is scaled, and the trailing update is shared by all
-// threads.  rk receives the reciprocal pivots.  Sets *bad when a pivot is not positive (it is then
-// taken as 1).
+// triangle), and writes X = L^-1 (lower triangle, zero above).  Right-looking in both, one barrier
+// per column: every thread forms the pivot and its reciprocal itself, an update scales the column
+// entries it needs on the fly, and the scaled column is written back one column later (when no
+// thread reads it any more), so every entry takes the same operations as with a scaled column
+// written first.  rk receives the reciprocal pivots.  Sets *bad when a pivot is not positive (it is
+// then taken as 1).
 __device__ __forceinline__ void pivot32(df32 (*P)[65], df32 (*X)[33], df32* rk, int* bad) {
   const int tid = threadIdx.x;
   for (int k = 0; k < 32; ++k) {
-    if (tid == 0) {
-      df32 d = P[k][k];
-      if (!(d.h > 0.f)) { *bad = 1; d = {1.f, 0.f}; }
-      const df32 s = df_sqrt(d);
-      P[k][k] = s;
-      rk[k] = df_recip(s);
+    df32 d = P[k][k];
+    if (!(d.h > 0.f)) {
+      if (tid == 0) *bad = 1;
+      d = {1.f, 0.f};
     }
-    __syncthreads();
-    if (tid > k && tid < 32) P[tid][k] = df_mul(P[tid][k], rk[k]);
-    __syncthreads();
+    const df32 sq = df_sqrt(d);
+    const df32 r = df_recip(sq);
+    const df32 own = (tid > k && tid < 32) ? df_mul(P[tid][k], r) : df32{0.f, 0.f};
     const int m = 31 - k;                       // trailing rows / columns
     for (int e = tid; e < m * m; e += 128) {
       const int i = k + 1 + e / m, j = k + 1 + e % m;
-      if (j <= i) df_fms(P[i][j], P[i][k], P[j][k]);
+      if (j <= i) df_fms(P[i][j], df_mul(P[i][k], r), df_mul(P[j][k], r));
     }
-    __syncthreads();
+    __syncthreads();                            // column k read by every thread; P[k+1][k+1] final
+    if (tid == 0) {
+      P[k][k] = sq;
+      rk[k] = r;
+    }
+    if (tid > k && tid < 32) P[tid][k] = own;
   }
   for (int e = tid; e < 1024; e += 128) X[e >> 5][e & 31] = {((e >> 5) == (e & 31)) ? 1.f : 0.f, 0.f};
   __syncthreads();
   for (int q = 0; q < 32; ++q) {
-    // row q of X is final once scaled: X[q][c] = (delta_qc - sum_{p<q} L[q][p] X[p][c]) / L[q][q]
-    if (tid <= q) X[q][tid] = df_mul(X[q][tid], rk[q]);
-    __syncthreads();
+    // row q of X is final once scaled: X[q][c] = (delta_qc - sum_{p<q} L[q][p] X[p][c]) / L[q][q];
+    // the updates below scale it on the fly, thread c stores it after the barrier
+    const df32 own = (tid <= q) ? df_mul(X[q][tid], rk[q]) : df32{0.f, 0.f};
     const int rows = 31 - q, cols = q + 1;      // X[r][c] -= L[r][q] X[q][c] for r > q, c <= q
     for (int e = tid; e < rows * cols; e += 128) {
       const int r = q + 1 + e / cols, c = e % cols;
-      df_fms(X[r][c], P[r][q], X[q][c]);
+      df_fms(X[r][c], P[r][q], df_mul(X[q][c], rk[q]));
     }
     __syncthreads();
+    if (tid <= q) X[q][tid] = own;
   }
+  __syncthreads();
 }
 
 // The 64 x 64 diagonal block [c0, c0 + 64) of a panel, whose earlier panels' contributions are
@@ -654,7 +661,8 @@ __global__ void __launch_bounds__(128, 3) chol_diag64_kernel(const BlockDesc* __
                                                              double* __restrict__ pool, DevFlags* flags, int c0,
                                                              int32_t* __restrict__ scale_exp,
                                                              uint16_t* __restrict__ mout,
-                                                             int32_t* __restrict__ mout_f) {
+                                                             int32_t* __restrict__ mout_f,
+                                                             float* __restrict__ l32) {
   __shared__ df32 M[64][65];         // the block (lower triangle used)
   __shared__ df32 Xa[32][33], Xc[32][33], T[32][33], X[32][33];
   __shared__ df32 rk[32];
@@ -707,8 +715,16 @@ __global__ void __launch_bounds__(128, 3) chol_diag64_kernel(const BlockDesc* __
   pivot32(reinterpret_cast<df32(*)[65]>(&M[32][32]), Xc, rk, &s_bad);
   for (int e = tid; e < 64 * 64; e += 128) {
     const int r = e >> 6, c = e & 63;
-    if (r < nb && c <= r) A[(int64_t)(c0 + r) * ld + c0 + c] = make_float2(M[r][c].h, M[r][c].l);
+    if (r < nb && c <= r) {
+      const int64_t o = (int64_t)(c0 + r) * ld + c0 + c;
+      A[o] = make_float2(M[r][c].h, M[r][c].l);
+      if (l32) l32[bd.off_mat + o] = M[r][c].h + M[r][c].l;   // the factor's FP32 rounding fl(h + l)
+    }
   }
+  // the FP32 factor's padding rows are read as operands (times zeros of the inverse): zero them once,
+  // in the block's last panel; its strict upper triangle is never read
+  if (l32 && n <= c0 + 64)
+    for (int64_t e = tid; e < (int64_t)(ld - n) * ld; e += 128) l32[bd.off_mat + (int64_t)n * ld + e] = 0.f;
   if (mout && n > c0 + 64) {
     // T = L_ba L_aa^-1, X = -L_cc^-1 T
     for (int i = warp * 8; i < warp * 8 + 8; ++i) {
@@ -758,28 +774,6 @@ __global__ void __launch_bounds__(128, 3) chol_diag64_kernel(const BlockDesc* __
     }
   }
   if (tid == 0 && s_bad) set_error(flags, NOLSM_ENOTPD);
-}
-
-// The factor's FP32 rounding fl(h + l) from the pairs (lower triangle; zero above the diagonal and
-// on the padding), every block at once.
-__global__ void factor_f32_kernel(const BlockDesc* __restrict__ blocks, int n_blocks, const double* __restrict__ pool,
-                                  float* __restrict__ l32) {
-  for (int b = blockIdx.y; b < n_blocks; b += gridDim.y) {
-    const BlockDesc bd = blocks[b];
-    const int n = bd.n, ld = bd.n_pad;
-    const float2* A = reinterpret_cast<const float2*>(pool + bd.off_mat);
-    float* L = l32 + bd.off_mat;
-    const int64_t total = (int64_t)ld * ld;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-      const int r = (int)(e / ld), c = (int)(e % ld);
-      float v = 0.f;
-      if (r < n && c <= r) {
-        const float2 p = A[e];
-        v = p.x + p.y;
-      }
-      L[e] = v;
-    }
-  }
 }
 
 // Inverse of the lower-triangular L into X (out of place), by block rows of 32:
@@ -1139,18 +1133,15 @@ cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode) {
       const int c0 = pnl * kOzPanel;
       if (pnl > 0 && (e = phase_mark(ctx, NOLSM_PHASE_FACTOR)) != cudaSuccess) return e;
       chol_diag64_kernel<<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, sb, ctx->d_flags, c0, ctx->d_oz_exp,
-                                                                 ctx->d_oz_m, ctx->d_oz_f);
+                                                                 ctx->d_oz_m, ctx->d_oz_f, s32);
       ctx->n_launches += 1;
       if (c0 + kOzPanel >= max_n) break;
       if ((e = phase_mark(ctx, NOLSM_PHASE_FACTOR_TRSM)) != cudaSuccess) return e;
-      if ((e = launch_chol_trsm_tc(ctx, pnl, sb)) != cudaSuccess) return e;
+      if ((e = launch_chol_trsm_tc(ctx, pnl, sb, s32)) != cudaSuccess) return e;
       if ((e = phase_mark(ctx, NOLSM_PHASE_FACTOR_UPDATE)) != cudaSuccess) return e;
       if ((e = launch_chol_update_tc(ctx, pnl, sb)) != cudaSuccess) return e;
     }
-    if ((e = phase_mark(ctx, NOLSM_PHASE_FACTOR)) != cudaSuccess) return e;
-    factor_f32_kernel<<<dim3(8, std::min(ctx->n_blocks, 8192)), 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->n_blocks, sb,
-                                                                                       s32);
-    ctx->n_launches += 1;
+    // (the diagonal and TRSM kernels wrote the factor's FP32 rounding beside the pairs)
     if ((e = phase_mark(ctx, NOLSM_PHASE_INVERSE)) != cudaSuccess) return e;
     // mixed paths: the tiled inverse with its off-diagonal blocks on the tensor cores (three TF32
     // passes, the congruence's arithmetic); FP32 path: the SIMT inverse with two-level sums

@@ -292,7 +292,7 @@ cudaError_t launch_congruence_tc(nolsm_ctx* ctx, float* t1);
 cudaError_t launch_slab_tc(nolsm_ctx* ctx);
 cudaError_t oz_prepare(nolsm_ctx* ctx);                        // items and tensor maps of the updates
 cudaError_t launch_chol_update_tc(nolsm_ctx* ctx, int panel, double* pool);
-cudaError_t launch_chol_trsm_tc(nolsm_ctx* ctx, int panel, double* pool);
+cudaError_t launch_chol_trsm_tc(nolsm_ctx* ctx, int panel, double* pool, float* l32);
 cudaError_t launch_trinv_tc(nolsm_ctx* ctx, const float* l32, float* ypool);   // mixed paths' L^-1
 void trinv_diag_launch(nolsm_ctx* ctx, const float* l32, float* ypool, int max_nb);
 constexpr int kOzPanel = 64;      // panel width of the blocked double-float Cholesky

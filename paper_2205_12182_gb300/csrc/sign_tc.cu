@@ -1919,6 +1919,7 @@ struct TrParams {
   const int32_t* scale_exp;     // e_r per row (row_off indexing)
   const int32_t* mf;            // per block: f_0 .. f_63, g
   __nv_bfloat16* planes;        // slices of L21 for the trailing update
+  float* l32;                   // the factor's FP32 rounding fl(h + l) (same layout as the pool)
   int c0;
   DevFlags* flags;
   long long budget;
@@ -2141,6 +2142,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1) chol_trsm_tc_kernel(const __gri
       const int eg = er + g - 14;
       const float rsc = oz_scale(er);
       float2* Lrow = reinterpret_cast<float2*>(p.pool + ti.off_mat) + (int64_t)r * ld + c0;
+      float* L32row = p.l32 + ti.off_mat + (int64_t)r * ld + c0;
       __nv_bfloat16* P = p.planes + ((int64_t)7 * ti.row_off + r) * 64;
       for (int j = 0; j < 4; ++j) {
         const int cb = 32 * h + 8 * j;            // first of this chunk's 8 columns of the panel
@@ -2177,6 +2179,11 @@ __global__ void __launch_bounds__(TR_THREADS, 1) chol_trsm_tc_kernel(const __gri
 #pragma unroll
         for (int w = 0; w < 4; ++w)
           reinterpret_cast<float4*>(Lrow + cb)[w] = make_float4(out[4 * w], out[4 * w + 1], out[4 * w + 2], out[4 * w + 3]);
+#pragma unroll
+        for (int w = 0; w < 2; ++w)
+          reinterpret_cast<float4*>(L32row + cb)[w] =
+              make_float4(out[8 * w] + out[8 * w + 1], out[8 * w + 2] + out[8 * w + 3], out[8 * w + 4] + out[8 * w + 5],
+                          out[8 * w + 6] + out[8 * w + 7]);
         // slices of the row on its own scale for the trailing update: plane s, row r, columns cb ..
         uint32_t pk[7][4];
 #pragma unroll
@@ -2919,7 +2926,7 @@ cudaError_t oz_prepare(nolsm_ctx* ctx) {
   return cudaSuccess;
 }
 
-cudaError_t launch_chol_trsm_tc(nolsm_ctx* ctx, int panel, double* pool) {
+cudaError_t launch_chol_trsm_tc(nolsm_ctx* ctx, int panel, double* pool, float* l32) {
   if (panel + 1 >= (int)ctx->h_tr_panel.size()) return cudaSuccess;
   const int64_t first = ctx->h_tr_panel[panel], count = ctx->h_tr_panel[panel + 1] - first;
   if (count <= 0) return cudaSuccess;
@@ -2934,6 +2941,7 @@ cudaError_t launch_chol_trsm_tc(nolsm_ctx* ctx, int panel, double* pool) {
   p.scale_exp = ctx->d_oz_exp;
   p.mf = ctx->d_oz_f;
   p.planes = reinterpret_cast<__nv_bfloat16*>(ctx->d_oz_planes);
+  p.l32 = l32;
   p.c0 = panel * kOzPanel;
   p.flags = ctx->d_flags;
   p.budget = ctx->opt.wait_budget;
