@@ -86,6 +86,72 @@ __global__ void gather_kernel(const BlockDesc* __restrict__ blocks, const int32_
   }
 }
 
+// The same gather for blocks up to n_pad kGatherRowMax, written row by row: a warp assembles a dense
+// row of T_b(H0) and T_b(S) in its own shared-memory buffer (zeros, the row's stored entries, the
+// unit diagonal on the padding) and writes it once with 16-byte stores, so every byte of the two
+// pools is written once and coalesced.  Dynamic shared memory: I_b, then per warp n_pad floats and
+// n_pad 8-byte entries.
+constexpr int kGatherRowMax = 2048;
+constexpr int kGatherWarps = 8;
+__global__ void __launch_bounds__(kGatherWarps * 32) gather_rows_kernel(
+    const BlockDesc* __restrict__ blocks, const int32_t* __restrict__ idx_pool, const int64_t* __restrict__ row_ptr,
+    const int32_t* __restrict__ col, const double* __restrict__ hval, const double* __restrict__ sval,
+    float* __restrict__ hb, double* __restrict__ sb, DevFlags* flags, int pairs, int max_n, int max_ld) {
+  extern __shared__ __align__(16) uint8_t g_smem[];
+  int32_t* s_idx = reinterpret_cast<int32_t*>(g_smem);
+  const BlockDesc bd = blocks[blockIdx.x];
+  const int n = bd.n, ld = bd.n_pad;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* wbuf = g_smem + (((size_t)max_n * 4 + 15) & ~(size_t)15) + (size_t)warp * max_ld * 12;
+  float* hrow = reinterpret_cast<float*>(wbuf);
+  double* srow = reinterpret_cast<double*>(wbuf + (size_t)max_ld * 4);
+  float2* srow2 = reinterpret_cast<float2*>(srow);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s_idx[i] = idx_pool[bd.off_idx + i];
+  __syncthreads();
+  for (int p = warp; p < ld; p += kGatherWarps) {
+    for (int c = lane; c < ld; c += 32) {
+      hrow[c] = 0.f;
+      const bool one = c == p && p >= n;
+      if (pairs) srow2[c] = make_float2(one ? 1.f : 0.f, 0.f);
+      else srow[c] = one ? 1.0 : 0.0;
+    }
+    __syncwarp();
+    if (p < n) {
+      const int32_t r = s_idx[p];
+      const int64_t e0 = row_ptr[r], e1 = row_ptr[r + 1];
+      // eight entries per lane in flight: their loads are issued before the first lookup
+      for (int64_t eb = e0; eb < e1; eb += 8 * 32) {
+        int32_t cv[8];
+        double hv[8], sv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int64_t e = eb + lane + 32 * u;
+          cv[u] = e < e1 ? col[e] : -1;
+          hv[u] = e < e1 ? hval[e] : 0.0;
+          sv[u] = e < e1 ? sval[e] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (cv[u] < 0) continue;
+          const int q = lower_bound_i32(s_idx, n, cv[u]);
+          if (q < n && s_idx[q] == cv[u]) {
+            if (!isfinite(hv[u]) || !isfinite(sv[u])) set_error(flags, NOLSM_ENONFINITE);
+            hrow[q] = (float)hv[u];
+            if (pairs) srow2[q] = df_pair_from_f64(sv[u]);
+            else srow[q] = sv[u];
+          }
+        }
+      }
+    }
+    __syncwarp();
+    float4* H = reinterpret_cast<float4*>(hb + bd.off_mat + (int64_t)p * ld);
+    float4* S = reinterpret_cast<float4*>(sb + bd.off_mat + (int64_t)p * ld);
+    for (int c = lane; c < ld / 4; c += 32) H[c] = reinterpret_cast<const float4*>(hrow)[c];
+    for (int c = lane; c < ld / 2; c += 32) S[c] = reinterpret_cast<const float4*>(srow)[c];
+    __syncwarp();
+  }
+}
+
 // ----------------------------------------------------------------------------------------------
 // Warp-tile helper: a warp computes a 32x32 tile acc[r] (lane = output column) of
 //   acc[r][lane] = sum_k Arow[r][k] * Bcol[k][lane]
@@ -1106,8 +1172,23 @@ inline dim3 sq_grid(int n_blocks) { return dim3(64, n_blocks); }
 }  // namespace
 
 cudaError_t launch_gather(nolsm_ctx* ctx, float* hb, double* sb) {
-  int max_n = 0;
-  for (auto& b : ctx->h_blocks) max_n = std::max(max_n, b.n);
+  int max_n = 0, max_ld = 0;
+  for (auto& b : ctx->h_blocks) {
+    max_n = std::max(max_n, b.n);
+    max_ld = std::max(max_ld, b.n_pad);
+  }
+  const int pairs_ = ctx->opt.chol_precision == NOLSM_CHOL_DF64 || ctx->opt.chol_precision == NOLSM_CHOL_DF64_SIMT;
+  if (max_ld <= kGatherRowMax) {
+    const size_t rsmem = (((size_t)max_n * 4 + 15) & ~(size_t)15) + (size_t)kGatherWarps * max_ld * 12;
+    if (rsmem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(gather_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem);
+      if (e != cudaSuccess) return e;
+    }
+    gather_rows_kernel<<<ctx->n_blocks, kGatherWarps * 32, rsmem, ctx->stream>>>(
+        ctx->d_blocks, ctx->d_idx, ctx->d_row_ptr, ctx->d_col, ctx->d_hval, ctx->d_sval, hb, sb, ctx->d_flags, pairs_,
+        max_n, max_ld);
+    return cudaGetLastError();
+  }
   const size_t smem = sizeof(int32_t) * (size_t)max_n;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
