@@ -750,14 +750,18 @@ def rooflines(stage_ms, cnt, steps, n_b, pk, sm_max_mhz, props, products_per_lau
       tiles) beside it;
     * chol_update_kernel ('factor_update'): tensor cores, the executed BF16 FLOP of the slice-pair
       products (28 pairs x 2 x 128 x 32 x 64 per tile);
-    * chol_trsm_kernel ('factor_trsm'): double-float multiply-adds on the FP32 pipe, 3,072 per trailing
-      row per panel (32 columns x 32 k + 32 columns x 64 k), 2 FP64-equivalent flops each; peak: every
-      SM issues 128 FP32 operations per clock and a double-float multiply-add costs 12 of them;
-    * trinv_tile_kernel ('inverse'): FP32 pipe, n_b^3 / 6 multiply-adds per block."""
+    * chol_trsm_tc_kernel ('factor_trsm'): the FP32 pipe, which splits every entry of A21 into seven
+      slices, adds the seven level sums of the result in double-float and splits the result again
+      (76 + 56 + 76 = 208 FP32 operations per entry of L21, 64 entries per trailing row per panel; the
+      slice products themselves are a small tensor-core load); peak: 128 FP32 operations per SM and
+      clock;
+    * the triangular inverse ('inverse', mixed paths: 128 x 128 diagonal blocks on the FP32 pipe, the
+      off-diagonal blocks as three-pass TF32 tensor-core products): n_b^3 / 3 FP32-accurate flops per
+      block against the three-pass TF32 rate (TF32 at half the BF16 dense rate, three passes)."""
     mhz = sm_max_mhz or 2070.0
     sms = props.multi_processor_count
-    df_peak = sms * 128 * mhz * 1e6 / 12.0 * 2.0 / 1e12
-    f32_peak = sms * 128 * mhz * 1e6 * 2.0 / 1e12
+    alu_peak = sms * 128 * mhz * 1e6 / 1e12   # FP32 operations (not FMA-doubled)
+    tf32x3_peak = pk["bf16_tflops_sustained"] / 2.0 / 3.0
     out = []
     prod_ms = stage_ms.get("products", 0.0)
     if prod_ms > 0 and cnt["gemm_flops"] > 0:
@@ -785,20 +789,24 @@ def rooflines(stage_ms, cnt, steps, n_b, pk, sm_max_mhz, props, products_per_lau
     trsm_ms = stage_ms.get("factor_trsm", 0.0)
     if trsm_ms > 0:
         rows = sum(max(int(n) - t0, 0) for n in n_b for t0 in range(64, int(n), 64))
-        flop = rows * 3072 * 2.0
-        ach = flop / (trsm_ms * 1e-3) / 1e12
-        out.append({"kernel": "chol_trsm_kernel (rows below each 64 x 64 diagonal block, double-float)",
-                    "bound": "alu", "achieved": ach, "peak": df_peak, "unit": "TFLOP/s (FP64-equivalent)",
-                    "frac": ach / df_peak,
-                    "peak_source": f"derived: {sms} SMs x 128 FP32 ops/clk x {mhz:.0f} MHz / 12 ops per double-float "
-                                   "multiply-add", "ms_per_step": trsm_ms, "traffic": None})
+        ops = rows * 64 * 208.0
+        ach = ops / (trsm_ms * 1e-3) / 1e12
+        out.append({"kernel": "chol_trsm_tc_kernel (rows below each 64 x 64 diagonal block: exact slices, "
+                              "tcgen05 slice products, double-float recombination)",
+                    "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "T FP32 operations/s",
+                    "frac": ach / alu_peak,
+                    "work": "208 FP32 operations per entry of L21 (slicing A21, adding the seven levels, slicing L21)",
+                    "peak_source": f"derived: {sms} SMs x 128 FP32 operations/clk x {mhz:.0f} MHz",
+                    "ms_per_step": trsm_ms, "traffic": None})
     inv_ms = stage_ms.get("inverse", 0.0)
     if inv_ms > 0:
         flop = float(np.sum(n_b ** 3) / 3.0)
         ach = flop / (inv_ms * 1e-3) / 1e12
-        out.append({"kernel": "trinv_tile_kernel (L^-1 in FP32)", "bound": "alu", "achieved": ach, "peak": f32_peak,
-                    "unit": "TFLOP/s", "frac": ach / f32_peak,
-                    "peak_source": f"derived: {sms} SMs x 128 FP32 FMA/clk x 2 x {mhz:.0f} MHz",
+        out.append({"kernel": "L^-1 (trinv_tile_kernel<true> on the 128 x 128 diagonal blocks, cong_tc_kernel "
+                              "three-pass TF32 products off the diagonal)",
+                    "bound": "tensor", "achieved": ach, "peak": tf32x3_peak, "unit": "TFLOP/s (FP32-accurate)",
+                    "frac": ach / tf32x3_peak,
+                    "peak_source": pk["source"] + " bf16 sustained / 2 (TF32 dense rate) / 3 (three passes)",
                     "ms_per_step": inv_ms, "traffic": None})
     return out
 

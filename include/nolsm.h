@@ -132,6 +132,17 @@ typedef enum nolsm_mu_first {
   NOLSM_MU_FIRST_MIDPOINT = 1   /* the bracket midpoint: plain bisection from the first step */
 } nolsm_mu_first;
 
+/* How the per-product schedule drives its iteration (the persistent schedules run it inside their
+ * one launch). */
+typedef enum nolsm_loop {
+  NOLSM_LOOP_GRAPH = 0,   /* one CUDA graph launch per sign evaluation: a conditional while node whose
+                             body is one iteration (tile lists, both products, the convergence test)
+                             and whose last kernel decides on the device whether another iteration runs;
+                             the graph is captured once per build and reused at every mu */
+  NOLSM_LOOP_HOST = 1     /* the same launches issued from the host, which polls the device flags every
+                             fourth iteration */
+} nolsm_loop;
+
 /* One CSR matrix (see the conventions above). */
 typedef struct nolsm_csr {
   int64_t n;               /* dimension N */
@@ -166,6 +177,7 @@ typedef struct nolsm_options {
                               values before storing them, i.e. FP8 operands without the FP8 MMA rate
                               (default 0, at most max_iter) */
   int32_t mu_first;        /* nolsm_mu_first of nolsm_set_mu (default AUFBAU) */
+  int32_t loop;            /* nolsm_loop of the per-product schedule (default GRAPH) */
 } nolsm_options;
 
 /* Statistics of the last sign evaluation. */

@@ -112,6 +112,15 @@ cudaError_t dalloc(nolsm_ctx* ctx, T** p, size_t count) {
   return e;
 }
 
+// The captured per-product iteration (its kernels' arguments name the context's pools).
+void release_loop_graph(nolsm_ctx* ctx) {
+  if (ctx->loop_exec) cudaGraphExecDestroy(ctx->loop_exec);
+  if (ctx->loop_graph) cudaGraphDestroy(ctx->loop_graph);
+  ctx->loop_exec = nullptr;
+  ctx->loop_graph = nullptr;
+  for (auto& k : ctx->loop_key) k = -1;
+}
+
 void release_pools(nolsm_ctx* ctx) {
   dfree(ctx->d_blocks); ctx->d_blocks = nullptr;
   dfree(ctx->d_idx); ctx->d_idx = nullptr;
@@ -163,6 +172,7 @@ void release_pools(nolsm_ctx* ctx) {
   dfree(ctx->d_lz_basis); ctx->d_lz_basis = nullptr;
   dfree(ctx->d_t1); ctx->d_t1 = nullptr;
   ctx->caps.clear();
+  release_loop_graph(ctx);
   ctx->built = ctx->have_sign = ctx->have_density = false;
 }
 
@@ -235,6 +245,7 @@ nolsm_status nolsm_default_options(nolsm_options* opt) {
   opt->refine_path = NOLSM_REFINE_TENSOR;
   opt->fp8_iters = 0;
   opt->mu_first = NOLSM_MU_FIRST_AUFBAU;
+  opt->loop = NOLSM_LOOP_GRAPH;
   return NOLSM_OK;
 }
 
@@ -251,7 +262,8 @@ nolsm_status nolsm_create(nolsm_ctx** out, const nolsm_options* opt, void* cuda_
       ctx->opt.bounds > NOLSM_BOUNDS_GIVEN || ctx->opt.lanczos_steps < 1 || ctx->opt.lanczos_steps > 64 ||
       ctx->opt.schedule < NOLSM_SCHEDULE_PERSISTENT || ctx->opt.schedule > NOLSM_SCHEDULE_PERSISTENT_INTERLEAVED ||
       ctx->opt.refine_path < NOLSM_REFINE_TENSOR || ctx->opt.refine_path > NOLSM_REFINE_SIMT ||
-      ctx->opt.fp8_iters < 0 || ctx->opt.fp8_iters > ctx->opt.max_iter) {
+      ctx->opt.fp8_iters < 0 || ctx->opt.fp8_iters > ctx->opt.max_iter || ctx->opt.loop < NOLSM_LOOP_GRAPH ||
+      ctx->opt.loop > NOLSM_LOOP_HOST) {
     delete ctx;
     return NOLSM_EINVAL;
   }
@@ -281,6 +293,7 @@ void nolsm_destroy(nolsm_ctx* ctx) {
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   for (auto e : ctx->gemm_ev) cudaEventDestroy(e);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
 }
 
@@ -297,6 +310,7 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   ctx->sticky = NOLSM_OK;   // a new build clears the sticky error
   ctx->last_error.clear();
   ctx->built = ctx->have_sign = ctx->have_density = false;
+  ctx->build_gen += 1;      // a captured iteration graph names the previous build's pools
   if (!H || !S || !blk_ptr || !blk_cols || n_blocks <= 0) return fail(ctx, NOLSM_EINVAL, "null argument or no blocks");
   if (H->n != S->n || H->nnz != S->nnz || H->n <= 0 || H->nnz <= 0 || H->memory != S->memory ||
       H->n > INT32_MAX)
@@ -735,16 +749,76 @@ nolsm_status nolsm_sign_batch(nolsm_ctx* ctx, double mu, nolsm_sign_stats* out) 
   // the whole iteration of the queued blocks, on the device; the per-product loop below then sees
   // them converged (or failed) and runs the remaining blocks
   if (!queue.empty()) CK(gemm_timed(ctx, mixed, 0, mu));
-  for (int it = 0; !persistent && it <= ctx->opt.max_iter; ++it) {
+  CK(launch_set_loop_mu(ctx, mu));   // the restart kernels read mu on the device
+  const bool restart = mode != NOLSM_BOUNDS_GERSHGORIN;
+  if (!persistent && ctx->opt.loop == NOLSM_LOOP_GRAPH) {
+    // the whole per-product iteration as one graph launch: a while node whose body is one iteration
+    // and whose condition the body's last kernel sets on the device (no host round trip)
+    const int64_t key[6] = {ctx->build_gen, ctx->opt.precision, restart ? 1 : 0, tile_n, ctx->opt.max_iter,
+                            ctx->opt.wait_budget};
+    if (!ctx->loop_exec || !std::equal(key, key + 6, ctx->loop_key)) {
+      release_loop_graph(ctx);
+      cudaGraph_t g = nullptr, body = nullptr;
+      cudaGraphConditionalHandle h;
+      CK(cudaGraphCreate(&g, 0));
+      ctx->loop_graph = g;
+      CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+      cudaGraphNodeParams np = {};
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = h;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      cudaGraphNode_t node;
+      CK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+      body = np.conditional.phGraph_out[0];
+      // captured on a stream of the context's own (the caller's may be the legacy default stream, which
+      // cannot be captured); the launchers below issue to ctx->stream, so it points there meanwhile
+      if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+      cudaStream_t user_stream = ctx->stream;
+      CK(cudaStreamBeginCaptureToGraph(ctx->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+      ctx->stream = ctx->cap_stream;
+      cudaError_t ce = launch_ns_tiles_n(ctx, tile_n);
+      if (ce == cudaSuccess) ce = mixed ? launch_gemm_tc(ctx, 1) : launch_gemm_f32(ctx, 1);
+      if (ce == cudaSuccess) ce = launch_ns_check_impl(ctx, ctx->d_tol, restart);
+      if (ce == cudaSuccess) ce = launch_ns_tiles_n(ctx, tile_n);
+      if (ce == cudaSuccess) ce = mixed ? launch_gemm_tc(ctx, 2) : launch_gemm_f32(ctx, 2);
+      if (ce == cudaSuccess) ce = launch_ns_advance(ctx);
+      if (ce == cudaSuccess && restart) ce = launch_ns_restart(ctx, hk);
+      if (ce == cudaSuccess) ce = launch_loop_cond(ctx, h);
+      cudaGraph_t captured = nullptr;
+      const cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &captured);
+      ctx->stream = user_stream;
+      CK(ce);
+      CK(ee);
+      CK(cudaGraphInstantiate(&ctx->loop_exec, g, 0));
+      std::copy(key, key + 6, ctx->loop_key);
+    }
+    CK(launch_loop_reset(ctx));
+    const int k = ctx->gemm_ev_used;   // the products' interval is the graph's
+    if ((int)ctx->gemm_ev.size() < 2 * (k + 1)) {
+      cudaEvent_t a, b;
+      CK(cudaEventCreate(&a));
+      CK(cudaEventCreate(&b));
+      ctx->gemm_ev.push_back(a);
+      ctx->gemm_ev.push_back(b);
+    }
+    CK(cudaEventRecord(ctx->gemm_ev[2 * k], ctx->stream));
+    CK(cudaGraphLaunch(ctx->loop_exec, ctx->stream));
+    CK(cudaEventRecord(ctx->gemm_ev[2 * k + 1], ctx->stream));
+    ctx->gemm_ev_used = k + 1;
+    ctx->n_launches += 3;
+    ctx->n_gemm += 1;
+  }
+  for (int it = 0; !persistent && ctx->opt.loop != NOLSM_LOOP_GRAPH && it <= ctx->opt.max_iter; ++it) {
     CK(launch_ns_tiles_n(ctx, tile_n));
     CK(gemm_timed(ctx, mixed, 1, mu));
-    CK(launch_ns_check_impl(ctx, ctx->d_tol, mode != NOLSM_BOUNDS_GERSHGORIN));
+    CK(launch_ns_check_impl(ctx, ctx->d_tol, restart));
     CK(launch_ns_tiles_n(ctx, tile_n));
     CK(gemm_timed(ctx, mixed, 2, mu));
     CK(launch_ns_advance(ctx));
     ctx->n_launches += 4;
-    if (mode != NOLSM_BOUNDS_GERSHGORIN) {
-      CK(launch_ns_restart(ctx, mu, hk));
+    if (restart) {
+      CK(launch_ns_restart(ctx, hk));
       ctx->n_launches += 2;
     }
     if (it % check_every == check_every - 1 || it == ctx->opt.max_iter) {

@@ -86,7 +86,9 @@ struct DevFlags {
   double sum_n;         // sum of block traces Tr(S D) over own columns
   double sum_e;         // same for Tr(H D)
   double energy;        // band energy reduction
-  double pad2;
+  double mu;            // chemical potential of the current sign evaluation (read by the restart kernels)
+  int32_t loop_iter;    // iterations run by the captured per-product loop
+  int32_t pad3;
 };
 
 }  // namespace nolsm
@@ -196,6 +198,14 @@ struct nolsm_ctx {
   // capacity in bytes of every pool the context owns (pools only grow)
   std::vector<std::pair<void**, size_t>> caps;
 
+  // the per-product iteration captured as one graph (a while node over one iteration), rebuilt after
+  // every build and whenever the captured choices change
+  cudaGraph_t loop_graph = nullptr;
+  cudaGraphExec_t loop_exec = nullptr;
+  cudaStream_t cap_stream = nullptr;   // where the graph is captured
+  int64_t build_gen = 0;
+  int64_t loop_key[6] = {-1, -1, -1, -1, -1, -1};
+
   // tensor-core operand descriptors (device array of CUtensorMap, opaque bytes)
   void* d_tmaps = nullptr;
   int n_tmaps = 0;
@@ -272,7 +282,10 @@ cudaError_t launch_own_diag(nolsm_ctx* ctx);   // d_own_diag from the per-row di
 // sign.cu (SIMT path, control, slab traces)
 cudaError_t launch_ns_init(nolsm_ctx* ctx, double mu, int half, int mode, const float* lz, const float* pred,
                            bool fill);
-cudaError_t launch_ns_restart(nolsm_ctx* ctx, double mu, int half);
+cudaError_t launch_ns_restart(nolsm_ctx* ctx, int half);          // mu from DevFlags::mu
+cudaError_t launch_set_loop_mu(nolsm_ctx* ctx, double mu);
+cudaError_t launch_loop_cond(nolsm_ctx* ctx, cudaGraphConditionalHandle h);
+cudaError_t launch_loop_reset(nolsm_ctx* ctx);
 cudaError_t launch_ns_tiles(nolsm_ctx* ctx);
 cudaError_t launch_ns_tiles_n(nolsm_ctx* ctx, int tile_n);
 cudaError_t launch_ns_check_impl(nolsm_ctx* ctx, const float* tol_b);

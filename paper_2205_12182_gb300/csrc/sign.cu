@@ -231,9 +231,11 @@ __global__ void ns_state_kernel(int n_blocks, const double* __restrict__ lo, con
 template <typename T>
 __global__ void ns_restart_fill_kernel(const BlockDesc* __restrict__ blocks, const float* __restrict__ a0,
                                        const NsState* __restrict__ st, const double* __restrict__ lo,
-                                       const double* __restrict__ hi, double mu, float margin, T* __restrict__ x0) {
+                                       const double* __restrict__ hi, const double* __restrict__ mu_p, float margin,
+                                       T* __restrict__ x0) {
   const int b = blockIdx.x;
   if (st[b].status != kRestart) return;
+  const double mu = *mu_p;
   const BlockDesc bd = blocks[b];
   const int n = bd.n, ld = bd.n_pad;
   const float alpha = (float)(fmax(fabs(hi[b] - mu), fabs(mu - lo[b])) * (1.0 + margin));
@@ -249,8 +251,9 @@ __global__ void ns_restart_fill_kernel(const BlockDesc* __restrict__ blocks, con
 }
 
 __global__ void ns_restart_state_kernel(int n_blocks, const double* __restrict__ lo, const double* __restrict__ hi,
-                                        double mu, float margin, float l0, int scaled, NsState* __restrict__ st,
-                                        float* __restrict__ resacc) {
+                                        const double* __restrict__ mu_p, float margin, float l0, int scaled,
+                                        NsState* __restrict__ st, float* __restrict__ resacc) {
+  const double mu = *mu_p;
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= n_blocks) return;
   NsState s = st[b];
@@ -1070,9 +1073,12 @@ cudaError_t launch_ns_check_impl(nolsm_ctx* ctx, const float* tol_b, int detect_
 
 cudaError_t launch_ns_check_impl(nolsm_ctx* ctx, const float* tol_b) { return launch_ns_check_impl(ctx, tol_b, 0); }
 
-cudaError_t launch_ns_restart(nolsm_ctx* ctx, double mu, int half) {
+// mu is read on the device from DevFlags::mu (set_loop_mu), so that the launches also serve a captured
+// iteration graph whatever the chemical potential
+cudaError_t launch_ns_restart(nolsm_ctx* ctx, int half) {
   const dim3 g(ctx->n_blocks);
   const float margin = (float)ctx->opt.alpha_margin;
+  const double* mu = &ctx->d_flags->mu;
   if (half == 0)
     ns_restart_fill_kernel<float><<<g, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_a0, ctx->d_state, ctx->d_lo,
                                                               ctx->d_hi, mu, margin, (float*)ctx->d_x[0]);
@@ -1186,6 +1192,32 @@ cudaError_t launch_band_energy(nolsm_ctx* ctx) {
   const double* d = ctx->d_dval_target ? ctx->d_dval_target : ctx->d_dval;
   dot_kernel<<<grid, 256, 0, ctx->stream>>>(ctx->nnz, d, ctx->d_hval, partial);
   sum_partials_kernel<<<1, 32, 0, ctx->stream>>>(grid, partial, &ctx->d_flags->energy);
+  return cudaGetLastError();
+}
+
+
+namespace {
+__global__ void set_loop_mu_kernel(DevFlags* f, double mu) { f->mu = mu; }
+
+// End of one captured iteration: run the next while no error is recorded, some block was still
+// iterating at this iteration's start and the iteration budget is not spent.
+__global__ void loop_cond_kernel(cudaGraphConditionalHandle h, DevFlags* f, int max_iter) {
+  const int it = ++f->loop_iter;
+  cudaGraphSetConditional(h, (f->error == 0 && f->n_active > 0 && it <= max_iter) ? 1u : 0u);
+}
+__global__ void loop_reset_kernel(DevFlags* f) { f->loop_iter = 0; }
+}  // namespace
+
+cudaError_t launch_set_loop_mu(nolsm_ctx* ctx, double mu) {
+  set_loop_mu_kernel<<<1, 1, 0, ctx->stream>>>(ctx->d_flags, mu);
+  return cudaGetLastError();
+}
+cudaError_t launch_loop_cond(nolsm_ctx* ctx, cudaGraphConditionalHandle h) {
+  loop_cond_kernel<<<1, 1, 0, ctx->stream>>>(h, ctx->d_flags, ctx->opt.max_iter);
+  return cudaGetLastError();
+}
+cudaError_t launch_loop_reset(nolsm_ctx* ctx) {
+  loop_reset_kernel<<<1, 1, 0, ctx->stream>>>(ctx->d_flags);
   return cudaGetLastError();
 }
 

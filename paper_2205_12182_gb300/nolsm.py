@@ -24,6 +24,7 @@ CHOL_FP64, CHOL_FP32, CHOL_FP64_INV64, CHOL_DF64, CHOL_DF64_SIMT = 0, 1, 2, 3, 4
 SCHEDULE_PERSISTENT, SCHEDULE_PER_PRODUCT, SCHEDULE_AUTO, SCHEDULE_PERSISTENT_INTERLEAVED = 0, 1, 2, 3
 REFINE_TENSOR, REFINE_SIMT = 0, 1
 MU_FIRST_AUFBAU, MU_FIRST_MIDPOINT = 0, 1
+LOOP_GRAPH, LOOP_HOST = 0, 1
 COMBINE_CUBIC, COMBINE_PERFORMANCE = 0, 1
 
 FUNCTIONS = ["nolsm_default_options", "nolsm_create", "nolsm_build_submatrices", "nolsm_sign_batch", "nolsm_set_mu", "nolsm_solve_chunked",
@@ -52,7 +53,7 @@ class NolsmOptions(C.Structure):
                 ("refine_iters", C.c_int32), ("spin_factor", C.c_double), ("lower_bound", C.c_double),
                 ("alpha_margin", C.c_double), ("wait_budget", C.c_int64), ("lanczos_steps", C.c_int32),
                 ("schedule", C.c_int32), ("refine_path", C.c_int32), ("fp8_iters", C.c_int32),
-                ("mu_first", C.c_int32)]
+                ("mu_first", C.c_int32), ("loop", C.c_int32)]
 
 
 class NolsmSignStats(C.Structure):

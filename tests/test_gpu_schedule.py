@@ -112,3 +112,25 @@ def test_bad_tables_are_refused(nl):
                                     np.array([[1.0, -1.0, 1.0]]))
     nl.nolsm_set_schedule_table(lib.ctx, np.array([], np.int32), np.array([], np.int32))   # removes it
     lib.close()
+
+
+def test_graph_loop_equals_host_loop(nl, ragged):
+    """The per-product iteration as one captured graph (a device-side while loop) runs the same kernels
+    in the same order as the host-driven loop: identical iterations and density, at two chemical
+    potentials in a row (the graph is captured once and reused; mu is read on the device), with the
+    restart path of learned-style bounds exercised by Lanczos bounds."""
+    out = {}
+    for loop in (nl.LOOP_HOST, nl.LOOP_GRAPH):
+        lib = nl.Nolsm(precision=nl.PREC_MIXED_FP16, schedule=nl.SCHEDULE_PER_PRODUCT, loop=loop,
+                       bounds=nl.BOUNDS_LANCZOS)
+        lib.build(ragged)
+        res = []
+        for mu in (-0.25, -0.3):
+            st = lib.sign_batch(mu)
+            res.append((lib.iters().copy(), lib.density().cpu().numpy(), st["n_electrons"]))
+        out[loop] = res
+        lib.close()
+    for (ih, dh, nh), (ig, dg, ng) in zip(out[nl.LOOP_HOST], out[nl.LOOP_GRAPH]):
+        np.testing.assert_array_equal(ig, ih)
+        np.testing.assert_array_equal(dg, dh)
+        assert ng == nh
