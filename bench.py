@@ -797,7 +797,7 @@ def rooflines(stage_ms, cnt, steps, n_b, pk, sm_max_mhz, props, products_per_lau
                     "frac": ach / alu_peak,
                     "work": "208 FP32 operations per entry of L21 (slicing A21, adding the seven levels, slicing L21)",
                     "peak_source": f"derived: {sms} SMs x 128 FP32 operations/clk x {mhz:.0f} MHz",
-                    "ms_per_step": trsm_ms, "traffic": None})
+                    "ms_per_step": trsm_ms, "traffic": traffic_per_launch("chol_trsm_tc_kernel", rows)})
     inv_ms = stage_ms.get("inverse", 0.0)
     if inv_ms > 0:
         flop = float(np.sum(n_b ** 3) / 3.0)
