@@ -723,14 +723,16 @@ __device__ __forceinline__ void pivot32(df32 (*P)[65], df32 (*X)[33], df32* rk, 
 //   L_ba = A_ba L_aa^-T,  A_cc -= L_ba L_ba^T,  T = L_ba L_aa^-1,  X = -L_cc^-1 T,
 // so that L11^-1 = [[L_aa^-1, 0], [X, L_cc^-1]].  Entries past n are taken as the identity.  In the
 // first panel each row's slicing exponent e_r (2^e_r >= sqrt(S_rr)) is written first.
-__global__ void __launch_bounds__(128, 3) chol_diag64_kernel(const BlockDesc* __restrict__ blocks,
+__global__ void __launch_bounds__(128, 4) chol_diag64_kernel(const BlockDesc* __restrict__ blocks,
                                                              double* __restrict__ pool, DevFlags* flags, int c0,
                                                              int32_t* __restrict__ scale_exp,
                                                              uint16_t* __restrict__ mout,
                                                              int32_t* __restrict__ mout_f,
                                                              float* __restrict__ l32) {
-  __shared__ df32 M[64][65];         // the block (lower triangle used)
-  __shared__ df32 Xa[32][33], Xc[32][33], T[32][33], X[32][33];
+  // the block (lower triangle); its unused upper-right 32 x 32 quarter holds the temporary T, and
+  // once L11 is written out its lower-left quarter receives X (four CTAs per SM fit)
+  __shared__ df32 M[64][65];
+  __shared__ df32 Xa[32][33], Xc[32][33];
   __shared__ df32 rk[32];
   __shared__ int fexp[64];
   __shared__ int s_bad;
@@ -765,10 +767,10 @@ __global__ void __launch_bounds__(128, 3) chol_diag64_kernel(const BlockDesc* __
   for (int i = warp * 8; i < warp * 8 + 8; ++i) {
     df32 acc = {0.f, 0.f};
     for (int k = 0; k <= lane; ++k) df_fma(acc, M[32 + i][k], Xa[lane][k]);
-    T[i][lane] = df_norm(acc);
+    M[i][32 + lane] = df_norm(acc);
   }
   __syncthreads();
-  for (int i = warp * 8; i < warp * 8 + 8; ++i) M[32 + i][lane] = T[i][lane];
+  for (int i = warp * 8; i < warp * 8 + 8; ++i) M[32 + i][lane] = M[i][32 + lane];
   __syncthreads();
   // A_cc[i][j] -= sum_k L_ba[i][k] L_ba[j][k]   (j <= i)
   for (int i = warp * 8; i < warp * 8 + 8; ++i) {
@@ -796,20 +798,20 @@ __global__ void __launch_bounds__(128, 3) chol_diag64_kernel(const BlockDesc* __
     for (int i = warp * 8; i < warp * 8 + 8; ++i) {
       df32 acc = {0.f, 0.f};
       for (int k = lane; k < 32; ++k) df_fma(acc, M[32 + i][k], Xa[k][lane]);
-      T[i][lane] = df_norm(acc);
+      M[i][32 + lane] = df_norm(acc);            // T
     }
-    __syncthreads();
+    __syncthreads();                             // T complete, L_ba (and L11's write-out) read
     for (int i = warp * 8; i < warp * 8 + 8; ++i) {
       df32 acc = {0.f, 0.f};
-      for (int k = 0; k <= i; ++k) df_fms(acc, Xc[i][k], T[k][lane]);
-      X[i][lane] = df_norm(acc);
+      for (int k = 0; k <= i; ++k) df_fms(acc, Xc[i][k], M[k][32 + lane]);
+      M[32 + i][lane] = df_norm(acc);            // X
     }
     __syncthreads();
     // Minv[c][k] = (L11^-1)[c][k]: lower triangular
     auto minv = [&](int c, int k) -> df32 {
       if (k < 32 && c < 32) return Xa[c][k];
       if (k >= 32 && c >= 32) return Xc[c - 32][k - 32];
-      if (k < 32) return X[c - 32][k];
+      if (k < 32) return M[c][k];                // X
       return df32{0.f, 0.f};
     };
     int32_t* F = mout_f + (int64_t)blockIdx.x * 68;
