@@ -163,6 +163,7 @@ void release_pools(nolsm_ctx* ctx) {
   dfree(ctx->d_tmaps); ctx->d_tmaps = nullptr;
   dfree(ctx->d_cg_tmaps); ctx->d_cg_tmaps = nullptr;
   ctx->cg_tmap_cap = 0;
+  ctx->cg_maps_gen = -1;
   dfree(ctx->d_sb); ctx->d_sb = nullptr;
   dfree(ctx->d_feat); ctx->d_feat = nullptr;
   dfree(ctx->d_pred); ctx->d_pred = nullptr;
@@ -564,13 +565,12 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   CK(launch_slabs_impl(ctx, l32 ? (const void*)(sb + ctx->sum_sq) : (const void*)sb, l32, ctx->d_t1));
   CK(dalloc(ctx, &ctx->d_rowd, (size_t)ctx->n_blocks * ctx->idx_stride));
   CK(dalloc(ctx, &ctx->d_rowr, (size_t)ctx->n_blocks * ctx->idx_stride));
-  CK(launch_bounds(ctx));
+  // the Gershgorin bounds and the mu-independent features in one pass over A0 (the mu-dependent
+  // features are refreshed in O(n) per evaluation)
+  CK(dalloc(ctx, &ctx->d_feat_static, (size_t)32 * ctx->n_blocks));
+  CK(launch_bounds_features(ctx, ctx->d_feat_static));
   CK(dalloc(ctx, &ctx->d_own_diag, (size_t)std::max<int64_t>(ctx->sum_own, 1)));
   CK(launch_own_diag(ctx));
-  ctx->n_launches += 1;
-  // mu-independent features once per build (the mu-dependent ones are refreshed in O(n))
-  CK(dalloc(ctx, &ctx->d_feat_static, (size_t)32 * ctx->n_blocks));
-  CK(launch_features(ctx, 0.0, ctx->d_feat_static));
   ctx->n_launches += 1;
   if (ctx->opt.bounds == NOLSM_BOUNDS_LANCZOS) {
     nolsm_status st_l = run_lanczos(ctx, 0.0, 0, ctx->opt.lanczos_steps, nullptr);

@@ -1128,47 +1128,6 @@ __global__ void own_diag_kernel(const BlockDesc* __restrict__ blocks, const int3
     out[bd.off_own + j] = row_diag[bd.off_idx + own_pool[bd.off_own + j]];
 }
 
-// Gershgorin bounds of A0 (real n x n part): [min_i a_ii - R_i, max_i a_ii + R_i].
-__global__ void gershgorin_kernel(const BlockDesc* __restrict__ blocks, const float* __restrict__ a0,
-                                  double* __restrict__ lo, double* __restrict__ hi, float* __restrict__ row_diag,
-                                  float* __restrict__ row_rad, DevFlags* flags) {
-  const BlockDesc bd = blocks[blockIdx.x];
-  const int n = bd.n, ld = bd.n_pad;
-  const float* A = a0 + bd.off_mat;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  // FP32 sums; the radius is rounded up by a relative n*2^-23 so the discs stay enclosing
-  float wlo = FLT_MAX, whi = -FLT_MAX;
-  const float up = 1.f + (float)n * 1.2e-7f;
-  for (int r = warp; r < n; r += nwarps) {
-    float rad = 0.f, d = 0.f;
-    for (int c = lane; c < n; c += 32) {
-      const float v = A[(int64_t)r * ld + c];
-      if (c == r) d = v; else rad += fabsf(v);
-    }
-    for (int o = 16; o; o >>= 1) {
-      rad += __shfl_xor_sync(0xffffffffu, rad, o);
-      d += __shfl_xor_sync(0xffffffffu, d, o);
-    }
-    if (lane == 0 && row_diag) {
-      row_diag[bd.off_idx + r] = d;      // per-row data for features at any mu (index-set stride)
-      row_rad[bd.off_idx + r] = rad;
-    }
-    rad *= up;
-    wlo = fminf(wlo, d - rad);
-    whi = fmaxf(whi, d + rad);
-  }
-  __shared__ float slo[32], shi[32];
-  if (lane == 0) { slo[warp] = wlo; shi[warp] = whi; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float l = FLT_MAX, h = -FLT_MAX;
-    for (int i = 0; i < nwarps; ++i) { l = fminf(l, slo[i]); h = fmaxf(h, shi[i]); }
-    if (!isfinite(l) || !isfinite(h)) set_error(flags, NOLSM_ENONFINITE);
-    lo[blockIdx.x] = l;
-    hi[blockIdx.x] = h;
-  }
-}
-
 inline dim3 sq_grid(int n_blocks) { return dim3(64, n_blocks); }
 
 }  // namespace
@@ -1282,12 +1241,6 @@ cudaError_t launch_slabs_impl(nolsm_ctx* ctx, const void* lfac, int fp32, const 
 
 cudaError_t launch_own_diag(nolsm_ctx* ctx) {
   own_diag_kernel<<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_own, ctx->d_rowd, ctx->d_own_diag);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_bounds(nolsm_ctx* ctx) {
-  gershgorin_kernel<<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_a0, ctx->d_lo, ctx->d_hi,
-                                                             ctx->d_rowd, ctx->d_rowr, ctx->d_flags);
   return cudaGetLastError();
 }
 

@@ -102,6 +102,8 @@ struct nolsm_ctx {
   bool pair_interleaved = false;  // the persistent kernel takes two blocks per cluster
   void* d_cg_tmaps = nullptr;   // tensor maps of the congruence kernel (FP32 pools, per bin)
   size_t cg_tmap_cap = 0;
+  int64_t cg_maps_gen = -1;     // build whose pools the maps describe, and its T1 pool
+  const float* cg_maps_t1 = nullptr;
   bool cong_simt = false;       // congruence on the SIMT FP32 products (tests compare both)
   nolsm_status sticky = NOLSM_OK;
   std::string last_error;
@@ -276,7 +278,6 @@ cudaError_t launch_gather(nolsm_ctx* ctx, float* hb, double* sb);
 cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode);
 cudaError_t launch_congruence(nolsm_ctx* ctx, float* t1_scratch);
 cudaError_t launch_slabs_impl(nolsm_ctx* ctx, const void* lfac, int fp32, const float* t1);
-cudaError_t launch_bounds(nolsm_ctx* ctx);
 cudaError_t launch_own_diag(nolsm_ctx* ctx);   // d_own_diag from the per-row diagonal of A0
 
 // sign.cu (SIMT path, control, slab traces)
@@ -314,7 +315,7 @@ constexpr int kSlabNarrow = 32;   // columns of a narrow refinement piece
 constexpr int kSlabWide = 192;    // columns of a wide refinement piece
 
 // learn.cu
-cudaError_t launch_features(nolsm_ctx* ctx, double mu, float* feat);
+cudaError_t launch_bounds_features(nolsm_ctx* ctx, float* feat);   // Gershgorin bounds + static features
 cudaError_t launch_features_mu(nolsm_ctx* ctx, double mu, float* feat);
 cudaError_t launch_lanczos(nolsm_ctx* ctx, double mu, int op, int k, float* basis, int64_t stride, float* out);
 cudaError_t launch_given_from_lanczos(nolsm_ctx* ctx, const float* lz_a0, const float* lz_abs, float* given);

@@ -38,9 +38,14 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
 
 // ------------------------------------------------------------------------------------------ features
 // 32 numbers per block, all O(n^2) from A0 and mu (see the list in nolsm_block_features).
+// The same pass over A0 also yields the Gershgorin bounds [min_i a_ii - R_i, max_i a_ii + R_i] of the
+// real n x n part (FP32 sums, each radius rounded up by a relative n 2^-23 so that the discs stay
+// enclosing; written to glo / ghi) and the per-row diagonal and radius; the features take those bounds.
 __global__ void __launch_bounds__(256) features_kernel(const BlockDesc* __restrict__ blocks, const float* __restrict__ a0,
-                                                       const double* __restrict__ glo, const double* __restrict__ ghi,
-                                                       double mu, float margin, float* __restrict__ feat) {
+                                                       double* __restrict__ glo, double* __restrict__ ghi,
+                                                       double mu, float margin, float* __restrict__ feat,
+                                                       float* __restrict__ row_diag, float* __restrict__ row_rad,
+                                                       DevFlags* flags) {
   __shared__ float red[8];
   const BlockDesc bd = blocks[blockIdx.x];
   const int n = bd.n, ld = bd.n_pad;
@@ -50,6 +55,8 @@ __global__ void __launch_bounds__(256) features_kernel(const BlockDesc* __restri
   float s_d = 0, s_d2 = 0, s_d3 = 0, s_d4 = 0, mn_d = FLT_MAX, mx_d = -FLT_MAX;
   float s_off2 = 0, s_r = 0, s_r2 = 0, mx_r = 0, s_abs = 0, mx_abs = 0;
   float below = 0, near05 = 0, near1 = 0, mn_dist = FLT_MAX, in_disc = 0, s_edge = 0, mn_edge = FLT_MAX;
+  float wlo = FLT_MAX, whi = -FLT_MAX;
+  const float up = 1.f + (float)n * 1.2e-7f;   // Gershgorin radius rounded up by a relative n 2^-23
   for (int r = warp; r < n; r += 8) {
     float rad = 0.f, off2 = 0.f, mabs = 0.f, dg = 0.f;
     for (int c = lane; c < n; c += 32) {
@@ -62,6 +69,13 @@ __global__ void __launch_bounds__(256) features_kernel(const BlockDesc* __restri
       off2 += __shfl_xor_sync(0xffffffffu, off2, o);
       dg += __shfl_xor_sync(0xffffffffu, dg, o);
       mabs = fmaxf(mabs, __shfl_xor_sync(0xffffffffu, mabs, o));
+    }
+    if (lane == 0) {
+      row_diag[bd.off_idx + r] = dg;      // per-row data for features at any mu (index-set stride)
+      row_rad[bd.off_idx + r] = rad;
+      const float ru = rad * up;
+      wlo = fminf(wlo, dg - ru);
+      whi = fmaxf(whi, dg + ru);
     }
     if (lane == 0) {
       s_d += dg; s_d2 += dg * dg; s_d3 += dg * dg * dg; s_d4 += dg * dg * dg * dg;
@@ -80,13 +94,13 @@ __global__ void __launch_bounds__(256) features_kernel(const BlockDesc* __restri
   __shared__ float part[24][8];
   if (lane == 0) {
     const float v[24] = {s_d, s_d2, s_d3, s_d4, -mn_d, mx_d, s_off2, s_r, s_r2, mx_r, s_abs, mx_abs,
-                         below, near05, near1, -mn_dist, in_disc, s_edge, -mn_edge, 0, 0, 0, 0, 0};
+                         below, near05, near1, -mn_dist, in_disc, s_edge, -mn_edge, -wlo, whi, 0, 0, 0};
     for (int i = 0; i < 24; ++i) part[i][warp] = v[i];
   }
   __syncthreads();
   if (threadIdx.x < 24) {
     const int i = threadIdx.x;
-    const bool is_max = (i == 4 || i == 5 || i == 9 || i == 11 || i == 15 || i == 18);
+    const bool is_max = (i == 4 || i == 5 || i == 9 || i == 11 || i == 15 || i == 18 || i == 19 || i == 20);
     float t = is_max ? -FLT_MAX : 0.f;
     for (int w = 0; w < 8; ++w) t = is_max ? fmaxf(t, part[i][w]) : t + part[i][w];
     part[i][0] = t;
@@ -98,7 +112,10 @@ __global__ void __launch_bounds__(256) features_kernel(const BlockDesc* __restri
     const float m3 = part[2][0] / nf - 3 * md * part[1][0] / nf + 2 * md * md * md;
     const float m4 = part[3][0] / nf - 4 * md * part[2][0] / nf + 6 * md * md * part[1][0] / nf - 3 * md * md * md * md;
     const float tr2 = (part[1][0] + part[6][0]) / nf;     // Tr(A0^2)/n
-    const float lo = (float)glo[blockIdx.x], hi = (float)ghi[blockIdx.x];
+    const float lo = -part[19][0], hi = part[20][0];
+    if (!isfinite(lo) || !isfinite(hi)) atomicCAS(&flags->error, 0, (int)NOLSM_ENONFINITE);
+    glo[blockIdx.x] = lo;
+    ghi[blockIdx.x] = hi;
     const float alpha_g = fmaxf(fabsf(hi - m), fabsf(m - lo)) * (1.f + margin);
     const float mr = part[7][0] / nf;
     float* f = feat + (int64_t)blockIdx.x * NI;
@@ -478,9 +495,12 @@ constexpr size_t PRED_SMEM = sizeof(float) * (NH * 33 + NH * 129 + NO * NH + NI 
 
 // ------------------------------------------------------------------------------------------ launchers
 
-cudaError_t launch_features(nolsm_ctx* ctx, double mu, float* feat) {
-  features_kernel<<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_a0, ctx->d_lo, ctx->d_hi, mu,
-                                                          (float)ctx->opt.alpha_margin, feat);
+// One pass over A0 for the Gershgorin bounds, the per-row diagonal and radius and the mu-independent
+// features (at mu = 0) of every block.
+cudaError_t launch_bounds_features(nolsm_ctx* ctx, float* feat) {
+  features_kernel<<<ctx->n_blocks, 256, 0, ctx->stream>>>(ctx->d_blocks, ctx->d_a0, ctx->d_lo, ctx->d_hi, 0.0,
+                                                                (float)ctx->opt.alpha_margin, feat, ctx->d_rowd,
+                                                                ctx->d_rowr, ctx->d_flags);
   return cudaGetLastError();
 }
 

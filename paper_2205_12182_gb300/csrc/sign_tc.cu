@@ -2652,6 +2652,7 @@ cudaError_t launch_gemm_tc(nolsm_ctx* ctx, int phase) {
 // factor's FP32 rounding) and the R^T scratch (loads: 128 x 32 boxes, stores: 32 x 32 boxes).  L and
 // the scratch lie in the second half of the build's FP64 scratch (sb + sum_sq).
 cudaError_t cg_maps(nolsm_ctx* ctx, float* t1) {
+  if (ctx->cg_maps_gen == ctx->build_gen && ctx->cg_maps_t1 == t1) return cudaSuccess;   // encoded for this build
   auto encode = get_encode();
   if (!encode) return cudaErrorNotSupported;
   int n_bins = 0;
@@ -2702,6 +2703,8 @@ cudaError_t cg_maps(nolsm_ctx* ctx, float* t1) {
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
+  ctx->cg_maps_gen = ctx->build_gen;
+  ctx->cg_maps_t1 = t1;
   return cudaSuccess;
 }
 
