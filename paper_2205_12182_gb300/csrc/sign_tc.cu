@@ -1310,6 +1310,10 @@ struct SlabLayout {
 template <typename T, int NMAX, int NST>
 __global__ void __launch_bounds__(NUM_THREADS, 1) slab_tc_kernel(const __grid_constant__ SlabParams p) {
   using L = SlabLayout<NMAX, NST>;
+  // tensor memory: two accumulator sets of N <= NMAX columns (narrow pieces take 64 columns, so that
+  // two CTAs share an SM)
+  constexpr int ACC = NMAX <= 32 ? 32 : TN;
+  constexpr uint32_t ALLOC = NMAX <= 32 ? 64u : (uint32_t)TMEM_COLS;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* stage_base = smem;
@@ -1334,7 +1338,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) slab_tc_kernel(const __grid_co
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TMEM_COLS)
+                 "r"(ALLOC)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -1417,7 +1421,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) slab_tc_kernel(const __grid_co
           for (int m0 = 0; m0 < ld && ok; m0 += TM) {
             if (!mbar_wait(&tempty_bar[macc], mtph[macc] ^ 1u, budget, abort_flag)) { ok = false; break; }
             tc_fence_after();
-            const uint32_t d_tmem = tmem_base + (uint32_t)(macc * TN);
+            const uint32_t d_tmem = tmem_base + (uint32_t)(macc * ACC);
             for (int k0 = 0; k0 < ld; k0 += TK) {
               if (!mbar_wait(&full_bar[ms], mph, budget, abort_flag)) { ok = false; break; }
               tc_fence_after();
@@ -1456,7 +1460,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) slab_tc_kernel(const __grid_co
           }
           tc_fence_after();
           const int m = m0 + q * 32 + lane;
-          const uint32_t tb = tmem_base + (uint32_t)(eacc * TN) + ((uint32_t)(q * 32) << 16);
+          const uint32_t tb = tmem_base + (uint32_t)(eacc * ACC) + ((uint32_t)(q * 32) << 16);
           for (int j0 = 0; j0 < N; j0 += 16) {
             uint32_t v[16];
             tmem_ld16(tb + (uint32_t)j0, v);
@@ -1543,7 +1547,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) slab_tc_kernel(const __grid_co
   __syncthreads();
   tc_fence_after();
   if (warp == 1) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(ALLOC) : "memory");
   }
 }
 
@@ -2974,19 +2978,20 @@ cudaError_t launch_chol_update_tc(nolsm_ctx* ctx, int panel, double* pool) {
   return cudaGetLastError();
 }
 
-// The refinement on the tensor cores: narrow pieces (<= 32 columns, eight 24 KB stages), then wide
+// The refinement on the tensor cores: narrow pieces (<= 32 columns, four 24 KB stages, 64 tensor-memory
+// columns, two CTAs per SM so that one piece's chain of dependent products hides the other's), then wide
 // ones (<= 192 columns, three 64 KB stages), one persistent CTA per SM each.  Slab scratch: P1 and
 // F1 (FP32), then the four split pools hi0, lo0, hi1, lo1 in the iterate's format.
 cudaError_t launch_slab_tc(nolsm_ctx* ctx) {
   const bool bf16 = ctx->opt.precision == NOLSM_PREC_MIXED_BF16;
-  using LN = SlabLayout<kSlabNarrow, 8>;
+  using LN = SlabLayout<kSlabNarrow, 4>;
   using LW = SlabLayout<kSlabWide, 3>;
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(slab_tc_kernel<__half, kSlabNarrow, 8>,
+    cudaError_t e = cudaFuncSetAttribute(slab_tc_kernel<__half, kSlabNarrow, 4>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, LN::SMEM);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(slab_tc_kernel<__nv_bfloat16, kSlabNarrow, 8>,
+      e = cudaFuncSetAttribute(slab_tc_kernel<__nv_bfloat16, kSlabNarrow, 4>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, LN::SMEM);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(slab_tc_kernel<__half, kSlabWide, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -3021,9 +3026,9 @@ cudaError_t launch_slab_tc(nolsm_ctx* ctx) {
     p.queue = &ctx->d_flags->slab_queue[0];
     p.bn = ctx->d_bn;
     p.be = ctx->d_be;
-    const int grid = std::min(ctx->num_sms, ctx->n_units_narrow);
-    if (bf16) slab_tc_kernel<__nv_bfloat16, kSlabNarrow, 8><<<grid, NUM_THREADS, LN::SMEM, ctx->stream>>>(p);
-    else slab_tc_kernel<__half, kSlabNarrow, 8><<<grid, NUM_THREADS, LN::SMEM, ctx->stream>>>(p);
+    const int grid = std::min(2 * ctx->num_sms, ctx->n_units_narrow);   // two CTAs per SM
+    if (bf16) slab_tc_kernel<__nv_bfloat16, kSlabNarrow, 4><<<grid, NUM_THREADS, LN::SMEM, ctx->stream>>>(p);
+    else slab_tc_kernel<__half, kSlabNarrow, 4><<<grid, NUM_THREADS, LN::SMEM, ctx->stream>>>(p);
     ctx->n_launches += 1;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
