@@ -1213,6 +1213,9 @@ nolsm_status nolsm_block_matrix(const nolsm_ctx* ctx, int32_t b, int32_t which, 
     if (cudaMemcpy2D(out, sizeof(float) * bd.n, src, sizeof(float) * bd.n_pad, sizeof(float) * bd.n, bd.n,
                      cudaMemcpyDeviceToHost) != cudaSuccess)
       return NOLSM_ECUDA;
+    if (which == 1)   // L^-1 is lower triangular (the mixed paths leave the blocks above unwritten)
+      for (int r = 0; r < bd.n; ++r)
+        for (int c = r + 1; c < bd.n; ++c) out[(size_t)r * bd.n + c] = 0.f;
     return NOLSM_OK;
   }
   const void* pool = which == 2 ? ctx->d_x[0] : which == 3 ? ctx->d_x[1] : ctx->d_b;

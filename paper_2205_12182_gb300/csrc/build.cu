@@ -728,7 +728,8 @@ __global__ void __launch_bounds__(128, 4) chol_diag64_kernel(const BlockDesc* __
                                                              int32_t* __restrict__ scale_exp,
                                                              uint16_t* __restrict__ mout,
                                                              int32_t* __restrict__ mout_f,
-                                                             float* __restrict__ l32) {
+                                                             float* __restrict__ l32,
+                                                             float* __restrict__ x32) {
   // the block (lower triangle); its unused upper-right 32 x 32 quarter holds the temporary T, and
   // once L11 is written out its lower-left quarter receives X (four CTAs per SM fit)
   __shared__ df32 M[64][65];
@@ -793,7 +794,8 @@ __global__ void __launch_bounds__(128, 4) chol_diag64_kernel(const BlockDesc* __
   // in the block's last panel; its strict upper triangle is never read
   if (l32 && n <= c0 + 64)
     for (int64_t e = tid; e < (int64_t)(ld - n) * ld; e += 128) l32[bd.off_mat + (int64_t)n * ld + e] = 0.f;
-  if (mout && n > c0 + 64) {
+  const bool want_m = mout && n > c0 + 64;
+  if (want_m || x32) {
     // T = L_ba L_aa^-1, X = -L_cc^-1 T
     for (int i = warp * 8; i < warp * 8 + 8; ++i) {
       df32 acc = {0.f, 0.f};
@@ -807,13 +809,29 @@ __global__ void __launch_bounds__(128, 4) chol_diag64_kernel(const BlockDesc* __
       M[32 + i][lane] = df_norm(acc);            // X
     }
     __syncthreads();
-    // Minv[c][k] = (L11^-1)[c][k]: lower triangular
-    auto minv = [&](int c, int k) -> df32 {
-      if (k < 32 && c < 32) return Xa[c][k];
-      if (k >= 32 && c >= 32) return Xc[c - 32][k - 32];
-      if (k < 32) return M[c][k];                // X
-      return df32{0.f, 0.f};
-    };
+  }
+  // Minv[c][k] = (L11^-1)[c][k]: lower triangular
+  auto minv = [&](int c, int k) -> df32 {
+    if (k < 32 && c < 32) return Xa[c][k];
+    if (k >= 32 && c >= 32) return Xc[c - 32][k - 32];
+    if (k < 32) return M[c][k];                  // X
+    return df32{0.f, 0.f};
+  };
+  if (x32) {
+    // the FP32 rounding of L11^-1 as the diagonal 64 x 64 block of the mixed paths' L^-1 (zero above
+    // the diagonal and on the padding rows)
+    float* Xo = x32 + bd.off_mat + (int64_t)c0 * ld + c0;
+    for (int e = tid; e < 4096; e += 128) {
+      const int r = e >> 6, c = e & 63;
+      float v = 0.f;
+      if (r < nb && c <= r) {
+        const df32 m = minv(r, c);
+        v = m.h + m.l;
+      }
+      Xo[(int64_t)r * ld + c] = v;
+    }
+  }
+  if (want_m) {
     int32_t* F = mout_f + (int64_t)blockIdx.x * 68;
     if (tid < 64) {
       float mx = 0.f;
@@ -936,16 +954,9 @@ __device__ __forceinline__ void cp_async16_b(void* smem_dst, const void* gsrc) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
 }
 
-// DIAG: the same inverse of each 128 x 128 diagonal block of L alone (grid (block, diagonal block)),
-// for the tiled inverse whose off-diagonal blocks run on the tensor cores (trinv_tc): the CTA also
-// zeroes the blocks right of its diagonal block in its rows (the strict upper triangle of L^-1)
-// and writes the transpose of its diagonal block into ypool (Y = X^T, the tiled inverse's second
-// operand).
-template <bool DIAG>
 __global__ void __launch_bounds__(kInvWarps * 32, 4) trinv_tile_kernel(const BlockDesc* __restrict__ blocks,
                                                                        const float* __restrict__ lpool,
-                                                                       float* __restrict__ xpool,
-                                                                       float* __restrict__ ypool) {
+                                                                       float* __restrict__ xpool) {
   __shared__ __align__(16) float As[2][32][32];   // L_ik chunk, read as broadcasts
   __shared__ __align__(16) float Bs[2][32][32];   // X_kc chunk, row k contiguous
   __shared__ float red[kInvWarps][32][32];
@@ -953,17 +964,13 @@ __global__ void __launch_bounds__(kInvWarps * 32, 4) trinv_tile_kernel(const Blo
   __shared__ float Li[32][33];
   __shared__ float rli[32];
   const BlockDesc bd = blocks[blockIdx.x];
-  const int ld = bd.n_pad;
-  const int o = DIAG ? 128 * (int)blockIdx.y : 0;          // first row and column of the diagonal block
-  if (o >= ld) return;
-  const int n = DIAG ? max(0, min(128, bd.n - o)) : bd.n;   // rows of the block below n
-  const int span = DIAG ? 128 : ld;
-  const float* L = lpool + bd.off_mat + (int64_t)o * ld + o;
-  float* X = xpool + bd.off_mat + (int64_t)o * ld + o;
+  const int n = bd.n, ld = bd.n_pad;
+  const float* L = lpool + bd.off_mat;
+  float* X = xpool + bd.off_mat;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // entries never written below: the strict upper triangle and the padding stay zero
-  for (int r = warp; r < span; r += kInvWarps)
-    for (int c = lane; c < (DIAG ? ld - o : span); c += 32)
+  for (int r = warp; r < ld; r += kInvWarps)
+    for (int c = lane; c < ld; c += 32)
       if (c > r || r >= n) X[(int64_t)r * ld + c] = 0.f;
   // rows [row0, row0 + 32) x columns [col0, col0 + 32) of a matrix into a chunk (zero rows >= rows)
   auto load_chunk = [&](float(*dst)[32], const float* src, int row0, int col0, int rows) {
@@ -1066,19 +1073,6 @@ __global__ void __launch_bounds__(kInvWarps * 32, 4) trinv_tile_kernel(const Blo
     }
     __syncthreads();
   }
-  if constexpr (DIAG) {
-    // Y's diagonal block is X's transposed, by 32 x 32 tiles through shared memory (both sides
-    // coalesced; the CTA's own global writes are visible after the barrier)
-    float* Y = ypool + bd.off_mat + (int64_t)o * ld + o;
-    float(*T)[33] = reinterpret_cast<float(*)[33]>(&red[0][0][0]);
-    for (int t = 0; t < 16; ++t) {
-      const int ti = t >> 2, tj = t & 3;
-      for (int e = tid; e < 1024; e += kInvWarps * 32) T[e >> 5][e & 31] = X[(int64_t)(32 * ti + (e >> 5)) * ld + 32 * tj + (e & 31)];
-      __syncthreads();
-      for (int e = tid; e < 1024; e += kInvWarps * 32) Y[(int64_t)(32 * tj + (e >> 5)) * ld + 32 * ti + (e & 31)] = T[e & 31][e >> 5];
-      __syncthreads();
-    }
-  }
 }
 
 // FP64 -> FP32 square copy with zero padding; optional transpose-free.
@@ -1110,7 +1104,7 @@ __global__ void slabs_kernel(const BlockDesc* __restrict__ blocks, const int32_t
     for (int i = threadIdx.x; i < ld; i += blockDim.x) {
       const int64_t o = bd.off_slab + (int64_t)j * ld + i;
       if (i < n) {
-        w[o] = linv32[bd.off_mat + (int64_t)i * ld + p];
+        w[o] = i >= p ? linv32[bd.off_mat + (int64_t)i * ld + p] : 0.f;   // L^-1 is lower triangular
         z[o] = t1[bd.off_mat + (int64_t)i * ld + p];
         lc[o] = (i <= p) ? (float)lfac[bd.off_mat + (int64_t)p * ld + i] : 0.f;
       } else {
@@ -1175,7 +1169,8 @@ cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode) {
       const int c0 = pnl * kOzPanel;
       if (pnl > 0 && (e = phase_mark(ctx, NOLSM_PHASE_FACTOR)) != cudaSuccess) return e;
       chol_diag64_kernel<<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, sb, ctx->d_flags, c0, ctx->d_oz_exp,
-                                                                 ctx->d_oz_m, ctx->d_oz_f, s32);
+                                                                 ctx->d_oz_m, ctx->d_oz_f, s32,
+                                                                 ctx->cong_simt ? nullptr : ctx->d_linv);
       ctx->n_launches += 1;
       if (c0 + kOzPanel >= max_n) break;
       if ((e = phase_mark(ctx, NOLSM_PHASE_FACTOR_TRSM)) != cudaSuccess) return e;
@@ -1188,12 +1183,12 @@ cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode) {
     // mixed paths: the tiled inverse with its off-diagonal blocks on the tensor cores (three TF32
     // passes, the congruence's arithmetic); FP32 path: the SIMT inverse with two-level sums
     if (!ctx->cong_simt) return launch_trinv_tc(ctx, s32, ctx->d_t1);
-    trinv_tile_kernel<false><<<ctx->n_blocks, kInvWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv, nullptr);
+    trinv_tile_kernel<<<ctx->n_blocks, kInvWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
   } else if (mode == NOLSM_CHOL_DF64_SIMT) {
     cholesky_df_kernel<<<ctx->n_blocks, kCholWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, ctx->d_flags, 0,
                                                                           1 << 30, nullptr, 1 << 30, nullptr);
     if ((e = phase_mark(ctx, NOLSM_PHASE_INVERSE)) != cudaSuccess) return e;
-    trinv_tile_kernel<false><<<ctx->n_blocks, kInvWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv, nullptr);
+    trinv_tile_kernel<<<ctx->n_blocks, kInvWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
   } else if (mode == NOLSM_CHOL_FP64_INV64) {
     cholesky_kernel<double, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, sb, nullptr, ctx->d_flags);
     if ((e = phase_mark(ctx, NOLSM_PHASE_INVERSE)) != cudaSuccess) return e;
@@ -1202,20 +1197,91 @@ cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode) {
   } else if (mode == NOLSM_CHOL_FP64) {
     cholesky_kernel<double, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, ctx->d_flags);
     if ((e = phase_mark(ctx, NOLSM_PHASE_INVERSE)) != cudaSuccess) return e;
-    trinv_tile_kernel<false><<<ctx->n_blocks, kInvWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv, nullptr);
+    trinv_tile_kernel<<<ctx->n_blocks, kInvWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
   } else {
     to_f32_kernel<double><<<sq_grid(ctx->n_blocks), 256, 0, ctx->stream>>>(ctx->d_blocks, sb, s32, 0);
     cholesky_kernel<float, 4><<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, s32, nullptr, ctx->d_flags);
     if ((e = phase_mark(ctx, NOLSM_PHASE_INVERSE)) != cudaSuccess) return e;
-    trinv_tile_kernel<false><<<ctx->n_blocks, kInvWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv, nullptr);
+    trinv_tile_kernel<<<ctx->n_blocks, kInvWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, s32, ctx->d_linv);
   }
   return cudaGetLastError();
 }
 
+// The 128 x 128 diagonal blocks of the mixed paths' L^-1 from the 64 x 64 ones the blocked factor
+// left in X (L11^-1 of every panel, computed in double-float and rounded):
+//   [[A, 0], [B, C]]^-1 = [[A^-1, 0], [-C^-1 B A^-1, C^-1]],
+// the off-diagonal quarter by two 64 x 64 x 64 FP32 products (B from the factor's FP32 rounding).
+// The CTA writes zeros where the block lies past n (panels past n were never factored) and the
+// block's transpose into ypool (Y = X^T, the tiled inverse's second operand); the blocks right of
+// the diagonal block stay unwritten (nothing reads them).  Grid: (block,
+// diagonal block); 256 threads; dynamic shared memory: A^-1, C^-1, B and B A^-1 (64 x 65 floats
+// each, kTrinv128Smem).
+constexpr int kTrinv128Smem = 4 * 64 * 65 * (int)sizeof(float);
+__global__ void __launch_bounds__(256) trinv128_kernel(const BlockDesc* __restrict__ blocks,
+                                                       const float* __restrict__ lpool, float* __restrict__ xpool,
+                                                       float* __restrict__ ypool) {
+  extern __shared__ float t128_smem[];
+  float(*Ai)[65] = reinterpret_cast<float(*)[65]>(t128_smem);
+  float(*Ci)[65] = Ai + 64;
+  float(*Bq)[65] = Ci + 64;
+  float(*Tq)[65] = Bq + 64;
+  const BlockDesc bd = blocks[blockIdx.x];
+  const int ld = bd.n_pad, n = bd.n;
+  const int o = 128 * (int)blockIdx.y;
+  if (o >= ld) return;
+  const int tid = threadIdx.x;
+  float* X = xpool + bd.off_mat;
+  const float* L = lpool + bd.off_mat;
+  const bool live_a = o < n, live_c = o + 64 < n;   // diagonal 64-blocks that were factored
+  // the upper-right quarter inside the diagonal block (the blocks right of it are never read: the
+  // products stop their K at the diagonal block, the slabs take the lower triangle only)
+  for (int e = tid; e < 4096; e += 256) X[(int64_t)(o + (e >> 6)) * ld + o + 64 + (e & 63)] = 0.f;
+  for (int e = tid; e < 4096; e += 256) {
+    const int r = e >> 6, c = e & 63;
+    Ai[r][c] = live_a ? X[(int64_t)(o + r) * ld + o + c] : 0.f;
+    Ci[r][c] = live_c ? X[(int64_t)(o + 64 + r) * ld + o + 64 + c] : 0.f;
+    Bq[r][c] = live_c ? L[(int64_t)(o + 64 + r) * ld + o + c] : 0.f;
+  }
+  __syncthreads();
+  // T = B A^-1 (A^-1 lower triangular: k >= c), then the quarter -C^-1 T (C^-1 lower: k <= r)
+  for (int e = tid; e < 4096; e += 256) {
+    const int r = e >> 6, c = e & 63;
+    float acc = 0.f;
+    for (int k = c; k < 64; ++k) acc = fmaf(Bq[r][k], Ai[k][c], acc);
+    Tq[r][c] = acc;
+  }
+  __syncthreads();
+  for (int e = tid; e < 4096; e += 256) {
+    const int r = e >> 6, c = e & 63;
+    float acc = 0.f;
+    for (int k = 0; k <= r; ++k) acc = fmaf(Ci[r][k], Tq[k][c], acc);
+    X[(int64_t)(o + 64 + r) * ld + o + c] = -acc;
+    if (!live_a) X[(int64_t)(o + r) * ld + o + c] = 0.f;
+    if (!live_c) X[(int64_t)(o + 64 + r) * ld + o + 64 + c] = 0.f;
+  }
+  __syncthreads();
+  // Y's diagonal block is X's transposed, by 32 x 32 tiles through shared memory (both sides
+  // coalesced; the CTA's own global writes are visible after the barrier)
+  float* Y = ypool + bd.off_mat + (int64_t)o * ld + o;
+  const float* Xd = X + (int64_t)o * ld + o;
+  float(*T)[65] = Tq;
+  for (int t = 0; t < 16; ++t) {
+    const int ti = t >> 2, tj = t & 3;
+    for (int e = tid; e < 1024; e += 256) T[e >> 5][e & 31] = Xd[(int64_t)(32 * ti + (e >> 5)) * ld + 32 * tj + (e & 31)];
+    __syncthreads();
+    for (int e = tid; e < 1024; e += 256) Y[(int64_t)(32 * tj + (e >> 5)) * ld + 32 * ti + (e & 31)] = T[e & 31][e >> 5];
+    __syncthreads();
+  }
+}
+
 // X_ii = L_ii^-1 of every 128 x 128 diagonal block, Y_ii = X_ii^T, strict upper blocks of X zeroed
 void trinv_diag_launch(nolsm_ctx* ctx, const float* l32, float* ypool, int max_nb) {
-  trinv_tile_kernel<true><<<dim3(ctx->n_blocks, max_nb), kInvWarps * 32, 0, ctx->stream>>>(ctx->d_blocks, l32,
-                                                                                         ctx->d_linv, ypool);
+  static bool attr_done = false;
+  if (!attr_done &&
+      cudaFuncSetAttribute(trinv128_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrinv128Smem) == cudaSuccess)
+    attr_done = true;
+  trinv128_kernel<<<dim3(ctx->n_blocks, max_nb), 256, kTrinv128Smem, ctx->stream>>>(ctx->d_blocks, l32, ctx->d_linv,
+                                                                                    ypool);
   ctx->n_launches += 1;
 }
 
