@@ -764,21 +764,35 @@ __global__ void __launch_bounds__(128, 4) chol_diag64_kernel(const BlockDesc* __
   }
   __syncthreads();
   pivot32(M, Xa, rk, &s_bad);
+  // The 32 x 32 x 32 products below take two rows per pass: two independent double-float chains per
+  // thread (every sum keeps its own order).
   // L_ba[i][j] = sum_{k <= j} A_ba[i][k] (L_aa^-1)[j][k]
-  for (int i = warp * 8; i < warp * 8 + 8; ++i) {
-    df32 acc = {0.f, 0.f};
-    for (int k = 0; k <= lane; ++k) df_fma(acc, M[32 + i][k], Xa[lane][k]);
-    M[i][32 + lane] = df_norm(acc);
+  for (int i = warp * 8; i < warp * 8 + 8; i += 2) {
+    df32 acc0 = {0.f, 0.f}, acc1 = {0.f, 0.f};
+    for (int k = 0; k <= lane; ++k) {
+      const df32 x = Xa[lane][k];
+      df_fma(acc0, M[32 + i][k], x);
+      df_fma(acc1, M[33 + i][k], x);
+    }
+    M[i][32 + lane] = df_norm(acc0);
+    M[i + 1][32 + lane] = df_norm(acc1);
   }
   __syncthreads();
   for (int i = warp * 8; i < warp * 8 + 8; ++i) M[32 + i][lane] = M[i][32 + lane];
   __syncthreads();
   // A_cc[i][j] -= sum_k L_ba[i][k] L_ba[j][k]   (j <= i)
-  for (int i = warp * 8; i < warp * 8 + 8; ++i) {
-    if (lane > i) continue;
-    df32 acc = M[32 + i][32 + lane];
-    for (int k = 0; k < 32; ++k) df_fms(acc, M[32 + i][k], M[32 + lane][k]);
-    M[32 + i][32 + lane] = df_norm(acc);
+  for (int i = warp * 8; i < warp * 8 + 8; i += 2) {
+    if (lane > i + 1) continue;
+    const bool both = lane <= i;
+    df32 acc0 = both ? M[32 + i][32 + lane] : df32{0.f, 0.f};
+    df32 acc1 = M[33 + i][32 + lane];
+    for (int k = 0; k < 32; ++k) {
+      const df32 y = M[32 + lane][k];
+      if (both) df_fms(acc0, M[32 + i][k], y);
+      df_fms(acc1, M[33 + i][k], y);
+    }
+    if (both) M[32 + i][32 + lane] = df_norm(acc0);
+    M[33 + i][32 + lane] = df_norm(acc1);
   }
   __syncthreads();
   pivot32(reinterpret_cast<df32(*)[65]>(&M[32][32]), Xc, rk, &s_bad);
@@ -796,17 +810,29 @@ __global__ void __launch_bounds__(128, 4) chol_diag64_kernel(const BlockDesc* __
     for (int64_t e = tid; e < (int64_t)(ld - n) * ld; e += 128) l32[bd.off_mat + (int64_t)n * ld + e] = 0.f;
   const bool want_m = mout && n > c0 + 64;
   if (want_m || x32) {
-    // T = L_ba L_aa^-1, X = -L_cc^-1 T
-    for (int i = warp * 8; i < warp * 8 + 8; ++i) {
-      df32 acc = {0.f, 0.f};
-      for (int k = lane; k < 32; ++k) df_fma(acc, M[32 + i][k], Xa[k][lane]);
-      M[i][32 + lane] = df_norm(acc);            // T
+    // T = L_ba L_aa^-1, X = -L_cc^-1 T (two rows per pass; row i's X sum stops at k = i, since
+    // L_cc^-1 is lower triangular)
+    for (int i = warp * 8; i < warp * 8 + 8; i += 2) {
+      df32 acc0 = {0.f, 0.f}, acc1 = {0.f, 0.f};
+      for (int k = lane; k < 32; ++k) {
+        const df32 x = Xa[k][lane];
+        df_fma(acc0, M[32 + i][k], x);
+        df_fma(acc1, M[33 + i][k], x);
+      }
+      M[i][32 + lane] = df_norm(acc0);           // T
+      M[i + 1][32 + lane] = df_norm(acc1);
     }
     __syncthreads();                             // T complete, L_ba (and L11's write-out) read
-    for (int i = warp * 8; i < warp * 8 + 8; ++i) {
-      df32 acc = {0.f, 0.f};
-      for (int k = 0; k <= i; ++k) df_fms(acc, Xc[i][k], M[k][32 + lane]);
-      M[32 + i][lane] = df_norm(acc);            // X
+    for (int i = warp * 8; i < warp * 8 + 8; i += 2) {
+      df32 acc0 = {0.f, 0.f}, acc1 = {0.f, 0.f};
+      for (int k = 0; k <= i; ++k) {
+        const df32 t = M[k][32 + lane];
+        df_fms(acc0, Xc[i][k], t);
+        df_fms(acc1, Xc[i + 1][k], t);
+      }
+      df_fms(acc1, Xc[i + 1][i + 1], M[i + 1][32 + lane]);
+      M[32 + i][lane] = df_norm(acc0);           // X
+      M[33 + i][lane] = df_norm(acc1);
     }
     __syncthreads();
   }
