@@ -676,7 +676,9 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
 // written first.  rk receives the reciprocal pivots.  Sets *bad when a pivot is not positive (it is
 // then taken as 1).
 __device__ __forceinline__ void pivot32(df32 (*P)[65], df32 (*X)[33], df32* rk, int* bad) {
-  const int tid = threadIdx.x;
+  // lane = column, the four warps take every fourth row: no index arithmetic beyond the loops, and
+  // a lane's scaled column entry is formed once per step
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int k = 0; k < 32; ++k) {
     df32 d = P[k][k];
     if (!(d.h > 0.f)) {
@@ -686,10 +688,10 @@ __device__ __forceinline__ void pivot32(df32 (*P)[65], df32 (*X)[33], df32* rk, 
     const df32 sq = df_sqrt(d);
     const df32 r = df_recip(sq);
     const df32 own = (tid > k && tid < 32) ? df_mul(P[tid][k], r) : df32{0.f, 0.f};
-    const int m = 31 - k;                       // trailing rows / columns
-    for (int e = tid; e < m * m; e += 128) {
-      const int i = k + 1 + e / m, j = k + 1 + e % m;
-      if (j <= i) df_fms(P[i][j], df_mul(P[i][k], r), df_mul(P[j][k], r));
+    if (lane > k) {
+      const df32 b = df_mul(P[lane][k], r);
+      for (int i = k + 1 + warp; i < 32; i += 4)
+        if (lane <= i) df_fms(P[i][lane], df_mul(P[i][k], r), b);
     }
     __syncthreads();                            // column k read by every thread; P[k+1][k+1] final
     if (tid == 0) {
@@ -704,10 +706,9 @@ __device__ __forceinline__ void pivot32(df32 (*P)[65], df32 (*X)[33], df32* rk, 
     // row q of X is final once scaled: X[q][c] = (delta_qc - sum_{p<q} L[q][p] X[p][c]) / L[q][q];
     // the updates below scale it on the fly, thread c stores it after the barrier
     const df32 own = (tid <= q) ? df_mul(X[q][tid], rk[q]) : df32{0.f, 0.f};
-    const int rows = 31 - q, cols = q + 1;      // X[r][c] -= L[r][q] X[q][c] for r > q, c <= q
-    for (int e = tid; e < rows * cols; e += 128) {
-      const int r = q + 1 + e / cols, c = e % cols;
-      df_fms(X[r][c], P[r][q], df_mul(X[q][c], rk[q]));
+    if (lane <= q) {                            // X[r][c] -= L[r][q] X[q][c] for r > q, c <= q
+      const df32 xq = df_mul(X[q][lane], rk[q]);
+      for (int rr = q + 1 + warp; rr < 32; rr += 4) df_fms(X[rr][lane], P[rr][q], xq);
     }
     __syncthreads();
     if (tid <= q) X[q][tid] = own;
