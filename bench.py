@@ -755,8 +755,9 @@ def rooflines(stage_ms, cnt, steps, n_b, pk, sm_max_mhz, props, products_per_lau
       (76 + 56 + 76 = 208 FP32 operations per entry of L21, 64 entries per trailing row per panel; the
       slice products themselves are a small tensor-core load); peak: 128 FP32 operations per SM and
       clock;
-    * the triangular inverse ('inverse', mixed paths: 128 x 128 diagonal blocks on the FP32 pipe, the
-      off-diagonal blocks as three-pass TF32 tensor-core products): n_b^3 / 3 FP32-accurate flops per
+    * the triangular inverse ('inverse', mixed paths: 128 x 128 diagonal blocks from the factor's
+      64 x 64 inverses on the FP32 pipe, the off-diagonal blocks as three-pass TF32 tensor-core
+      products): n_b^3 / 3 FP32-accurate flops per
       block against the three-pass TF32 rate (TF32 at half the BF16 dense rate, three passes)."""
     mhz = sm_max_mhz or 2070.0
     sms = props.multi_processor_count
@@ -802,8 +803,8 @@ def rooflines(stage_ms, cnt, steps, n_b, pk, sm_max_mhz, props, products_per_lau
     if inv_ms > 0:
         flop = float(np.sum(n_b ** 3) / 3.0)
         ach = flop / (inv_ms * 1e-3) / 1e12
-        out.append({"kernel": "L^-1 (trinv_tile_kernel<true> on the 128 x 128 diagonal blocks, cong_tc_kernel "
-                              "three-pass TF32 products off the diagonal)",
+        out.append({"kernel": "L^-1 (trinv128_kernel on the 128 x 128 diagonal blocks from the factor's 64 x 64 "
+                              "inverses, cong_tc_kernel three-pass TF32 products off the diagonal)",
                     "bound": "tensor", "achieved": ach, "peak": tf32x3_peak, "unit": "TFLOP/s (FP32-accurate)",
                     "frac": ach / tf32x3_peak,
                     "peak_source": pk["source"] + " bf16 sustained / 2 (TF32 dense rate) / 3 (three passes)",

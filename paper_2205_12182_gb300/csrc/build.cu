@@ -1282,22 +1282,22 @@ __global__ void __launch_bounds__(256) trinv128_kernel(const BlockDesc* __restri
     const int r = e >> 6, c = e & 63;
     float acc = 0.f;
     for (int k = 0; k <= r; ++k) acc = fmaf(Ci[r][k], Tq[k][c], acc);
+    Bq[r][c] = -acc;                             // the quarter (B is no longer needed)
     X[(int64_t)(o + 64 + r) * ld + o + c] = -acc;
     if (!live_a) X[(int64_t)(o + r) * ld + o + c] = 0.f;
     if (!live_c) X[(int64_t)(o + 64 + r) * ld + o + 64 + c] = 0.f;
   }
   __syncthreads();
-  // Y's diagonal block is X's transposed, by 32 x 32 tiles through shared memory (both sides
-  // coalesced; the CTA's own global writes are visible after the barrier)
+  // Y's diagonal block is X's transposed, written from shared memory: Y[c][r] = X[r][c] with
+  // X = [[A^-1, 0], [quarter, C^-1]] (consecutive threads take consecutive r: coalesced rows of Y,
+  // conflict-free columns of the 65-wide arrays)
   float* Y = ypool + bd.off_mat + (int64_t)o * ld + o;
-  const float* Xd = X + (int64_t)o * ld + o;
-  float(*T)[65] = Tq;
-  for (int t = 0; t < 16; ++t) {
-    const int ti = t >> 2, tj = t & 3;
-    for (int e = tid; e < 1024; e += 256) T[e >> 5][e & 31] = Xd[(int64_t)(32 * ti + (e >> 5)) * ld + 32 * tj + (e & 31)];
-    __syncthreads();
-    for (int e = tid; e < 1024; e += 256) Y[(int64_t)(32 * tj + (e >> 5)) * ld + 32 * ti + (e & 31)] = T[e & 31][e >> 5];
-    __syncthreads();
+  for (int e = tid; e < 128 * 128; e += 256) {
+    const int c = e >> 7, r = e & 127;
+    float v;
+    if (c < 64) v = r < 64 ? Ai[r][c] : Bq[r - 64][c];
+    else v = r < 64 ? 0.f : Ci[r - 64][c - 64];
+    Y[(int64_t)c * ld + r] = v;
   }
 }
 
