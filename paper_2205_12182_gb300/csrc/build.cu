@@ -1271,19 +1271,34 @@ __global__ void __launch_bounds__(256) trinv128_kernel(const BlockDesc* __restri
   }
   __syncthreads();
   // T = B A^-1 (A^-1 lower triangular: k >= c), then the quarter -C^-1 T (C^-1 lower: k <= r)
-  for (int e = tid; e < 4096; e += 256) {
+  for (int e = tid; e < 4096; e += 512) {        // two rows per pass (independent chains)
     const int r = e >> 6, c = e & 63;
-    float acc = 0.f;
-    for (int k = c; k < 64; ++k) acc = fmaf(Bq[r][k], Ai[k][c], acc);
-    Tq[r][c] = acc;
+    float acc0 = 0.f, acc1 = 0.f;
+    for (int k = c; k < 64; ++k) {
+      const float a = Ai[k][c];
+      acc0 = fmaf(Bq[r][k], a, acc0);
+      acc1 = fmaf(Bq[r + 4][k], a, acc1);
+    }
+    Tq[r][c] = acc0;
+    Tq[r + 4][c] = acc1;
   }
   __syncthreads();
+  for (int e = tid; e < 4096; e += 512) {        // rows r and r + 4 (row r's sum stops at k = r)
+    const int r = e >> 6, c = e & 63;
+    float acc0 = 0.f, acc1 = 0.f;
+    for (int k = 0; k <= r; ++k) {
+      const float t = Tq[k][c];
+      acc0 = fmaf(Ci[r][k], t, acc0);
+      acc1 = fmaf(Ci[r + 4][k], t, acc1);
+    }
+    for (int k = r + 1; k <= r + 4; ++k) acc1 = fmaf(Ci[r + 4][k], Tq[k][c], acc1);
+    Bq[r][c] = -acc0;                            // the quarter (B is no longer needed)
+    Bq[r + 4][c] = -acc1;
+    X[(int64_t)(o + 64 + r) * ld + o + c] = -acc0;
+    X[(int64_t)(o + 68 + r) * ld + o + c] = -acc1;
+  }
   for (int e = tid; e < 4096; e += 256) {
     const int r = e >> 6, c = e & 63;
-    float acc = 0.f;
-    for (int k = 0; k <= r; ++k) acc = fmaf(Ci[r][k], Tq[k][c], acc);
-    Bq[r][c] = -acc;                             // the quarter (B is no longer needed)
-    X[(int64_t)(o + 64 + r) * ld + o + c] = -acc;
     if (!live_a) X[(int64_t)(o + r) * ld + o + c] = 0.f;
     if (!live_c) X[(int64_t)(o + 64 + r) * ld + o + 64 + c] = 0.f;
   }

@@ -59,10 +59,23 @@ __global__ void __launch_bounds__(256) features_kernel(const BlockDesc* __restri
   const float up = 1.f + (float)n * 1.2e-7f;   // Gershgorin radius rounded up by a relative n 2^-23
   for (int r = warp; r < n; r += 8) {
     float rad = 0.f, off2 = 0.f, mabs = 0.f, dg = 0.f;
-    for (int c = lane; c < n; c += 32) {
-      const float v = A[(int64_t)r * ld + c];
-      if (c == r) dg = v;
-      else { rad += fabsf(v); off2 += v * v; mabs = fmaxf(mabs, fabsf(v)); }
+    // 16-byte loads, four in flight per lane; the padding columns of A0 are zero and add nothing
+    const float4* Ar = reinterpret_cast<const float4*>(A + (int64_t)r * ld);
+    for (int c4 = lane; c4 < ld / 4; c4 += 4 * 32) {
+      float4 v4[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v4[u] = c4 + 32 * u < ld / 4 ? __ldg(Ar + c4 + 32 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float vv[4] = {v4[u].x, v4[u].y, v4[u].z, v4[u].w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c = 4 * (c4 + 32 * u) + j;
+          const float v = vv[j];
+          if (c == r) dg = v;
+          else { rad += fabsf(v); off2 += v * v; mabs = fmaxf(mabs, fabsf(v)); }
+        }
+      }
     }
     for (int o = 16; o; o >>= 1) {
       rad += __shfl_xor_sync(0xffffffffu, rad, o);
