@@ -252,22 +252,36 @@ __device__ __forceinline__ float epi_tile(uint32_t tmem_acc, int q, int lane, T*
     for (int h = 0; h < LDW / 32; ++h) {
       const int cg0 = n0 + cl + 32 * h;
       if (cg0 < r0) continue;                // whole chunk below the diagonal (warp-uniform)
-      float fv[32];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        float x = __uint_as_float(v[32 * h + j]);
-        if (phase == 1) {
-          const int cg = cg0 + j;
-          const float d = (cg == r) ? 1.f : 0.f;
-          const float e = x - d;
-          const float w = (cg > r) ? 2.f : ((cg == r) ? 1.f : 0.f);
-          rsq = fmaf(w, e * e, rsq);
-          x = c1 * d - c3 * x;
-        }
-        if constexpr (Q8) x = float(__nv_fp8_e4m3(x));   // stored in the iterate's format
-        fv[j] = x;
-      }
       const bool diag = cg0 == r0;           // warp-uniform
+      float fv[32];
+      if (phase == 1 && !diag) {
+        // strictly above the diagonal: weight 2, no identity term (the same operations as below
+        // with d = 0 and w = 2)
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float x = __uint_as_float(v[32 * h + j]);
+          rsq = fmaf(2.f, x * x, rsq);
+          fv[j] = 0.f - c3 * x;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          float x = __uint_as_float(v[32 * h + j]);
+          if (phase == 1) {
+            const int cg = cg0 + j;
+            const float d = (cg == r) ? 1.f : 0.f;
+            const float e = x - d;
+            const float w = (cg > r) ? 2.f : ((cg == r) ? 1.f : 0.f);
+            rsq = fmaf(w, e * e, rsq);
+            x = c1 * d - c3 * x;
+          }
+          fv[j] = x;
+        }
+      }
+      if constexpr (Q8) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) fv[j] = float(__nv_fp8_e4m3(fv[j]));   // stored in the iterate's format
+      }
       // the store that last used this buffer (NBUF chunks ago) has read it
       if (lane == 0) {
         if (NBUF == 1) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
@@ -820,10 +834,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PAIR_THREADS, 1) ns_
             rsq += epi_tile<T, PAIR_NBUF, 32, true>(tmem_base + (uint32_t)(eacc * TN + h0), q, lane, out, ld, t.m0,
                                                     t.n0 + h0, hw, phase, c1, c3, smap, bd.pos * ld, stg, ebuf);
           else
-            rsq += epi_tile<T, PAIR_NBUF, 32>(tmem_base + (uint32_t)(eacc * TN + h0), q, lane, out, ld, t.m0,
+            rsq += epi_tile<T, PAIR_NBUF, 64>(tmem_base + (uint32_t)(eacc * TN + h0), q, lane, out, ld, t.m0,
                                               t.n0 + h0, hw, phase, c1, c3, smap, bd.pos * ld, stg, ebuf);
         } else {
-          rsq += epi_tile<T, PAIR_NBUF, 32>(tmem_base + (uint32_t)(eacc * TN + h0), q, lane, out, ld, t.m0, t.n0 + h0, hw,
+          rsq += epi_tile<T, PAIR_NBUF, 64>(tmem_base + (uint32_t)(eacc * TN + h0), q, lane, out, ld, t.m0, t.n0 + h0, hw,
                                         phase, c1, c3, smap, bd.pos * ld,
                                         smem + PAIR_EPI_OFF + (warp - 2) * PAIR_NBUF * EPI_BUF_BYTES, ebuf);
         }
