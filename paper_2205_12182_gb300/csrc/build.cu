@@ -687,11 +687,13 @@ __device__ __forceinline__ void pivot32(df32 (*P)[65], df32 (*X)[33], df32* rk, 
     }
     const df32 sq = df_sqrt(d);
     const df32 r = df_recip(sq);
-    const df32 own = (tid > k && tid < 32) ? df_mul(P[tid][k], r) : df32{0.f, 0.f};
-    if (lane > k) {
-      const df32 b = df_mul(P[lane][k], r);
-      for (int i = k + 1 + warp; i < 32; i += 4)
-        if (lane <= i) df_fms(P[i][lane], df_mul(P[i][k], r), b);
+    // lane c forms the scaled entry of row c once; row i's entry reaches the other lanes by shuffles
+    // (the same value each lane would form itself)
+    const df32 b = df_mul(P[lane][k], r);
+    const df32 own = (tid > k && tid < 32) ? b : df32{0.f, 0.f};
+    for (int i = k + 1 + warp; i < 32; i += 4) {
+      const df32 bi = {__shfl_sync(0xffffffffu, b.h, i), __shfl_sync(0xffffffffu, b.l, i)};
+      if (lane > k && lane <= i) df_fms(P[i][lane], bi, b);
     }
     __syncthreads();                            // column k read by every thread; P[k+1][k+1] final
     if (tid == 0) {
