@@ -668,15 +668,18 @@ __global__ void __launch_bounds__(kCholWarps * 32, 3) cholesky_df_kernel(const B
 }
 
 // ---- the 64 x 64 diagonal block of the blocked double-float Cholesky ----------------------------
-// The CTA (128 threads) factors a 32 x 32 SPD block in shared memory, P = L L^T in place (lower
+// The CTA (kDiagWarps warps) factors a 32 x 32 SPD block in shared memory, P = L L^T in place (lower
 // triangle), and writes X = L^-1 (lower triangle, zero above).  Right-looking in both, one barrier
 // per column: every thread forms the pivot and its reciprocal itself, an update scales the column
 // entries it needs on the fly, and the scaled column is written back one column later (when no
 // thread reads it any more), so every entry takes the same operations as with a scaled column
 // written first.  rk receives the reciprocal pivots.  Sets *bad when a pivot is not positive (it is
 // then taken as 1).
+constexpr int kDiagWarps = 8;
+constexpr int kDiagThreads = 32 * kDiagWarps;
+constexpr int kDiagRows = 32 / kDiagWarps;       // rows of a 32 x 32 product per warp
 __device__ __forceinline__ void pivot32(df32 (*P)[65], df32 (*X)[33], df32* rk, int* bad) {
-  // lane = column, the four warps take every fourth row: no index arithmetic beyond the loops, and
+  // lane = column, warp w takes the rows w, w + kDiagWarps, ...: no index arithmetic beyond the loops, and
   // a lane's scaled column entry is formed once per step
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int k = 0; k < 32; ++k) {
@@ -691,7 +694,7 @@ __device__ __forceinline__ void pivot32(df32 (*P)[65], df32 (*X)[33], df32* rk, 
     // (the same value each lane would form itself)
     const df32 b = df_mul(P[lane][k], r);
     const df32 own = (tid > k && tid < 32) ? b : df32{0.f, 0.f};
-    for (int i = k + 1 + warp; i < 32; i += 4) {
+    for (int i = k + 1 + warp; i < 32; i += kDiagWarps) {
       const df32 bi = {__shfl_sync(0xffffffffu, b.h, i), __shfl_sync(0xffffffffu, b.l, i)};
       if (lane > k && lane <= i) df_fms(P[i][lane], bi, b);
     }
@@ -702,7 +705,7 @@ __device__ __forceinline__ void pivot32(df32 (*P)[65], df32 (*X)[33], df32* rk, 
     }
     if (tid > k && tid < 32) P[tid][k] = own;
   }
-  for (int e = tid; e < 1024; e += 128) X[e >> 5][e & 31] = {((e >> 5) == (e & 31)) ? 1.f : 0.f, 0.f};
+  for (int e = tid; e < 1024; e += kDiagThreads) X[e >> 5][e & 31] = {((e >> 5) == (e & 31)) ? 1.f : 0.f, 0.f};
   __syncthreads();
   for (int q = 0; q < 32; ++q) {
     // row q of X is final once scaled: X[q][c] = (delta_qc - sum_{p<q} L[q][p] X[p][c]) / L[q][q];
@@ -710,7 +713,7 @@ __device__ __forceinline__ void pivot32(df32 (*P)[65], df32 (*X)[33], df32* rk, 
     const df32 own = (tid <= q) ? df_mul(X[q][tid], rk[q]) : df32{0.f, 0.f};
     if (lane <= q) {                            // X[r][c] -= L[r][q] X[q][c] for r > q, c <= q
       const df32 xq = df_mul(X[q][lane], rk[q]);
-      for (int rr = q + 1 + warp; rr < 32; rr += 4) df_fms(X[rr][lane], P[rr][q], xq);
+      for (int rr = q + 1 + warp; rr < 32; rr += kDiagWarps) df_fms(X[rr][lane], P[rr][q], xq);
     }
     __syncthreads();
     if (tid <= q) X[q][tid] = own;
@@ -722,11 +725,11 @@ __device__ __forceinline__ void pivot32(df32 (*P)[65], df32 (*X)[33], df32* rk, 
 // already subtracted: L11 in place (pairs) and, when rows follow below, Minv = L11^-1 for the TRSM of
 // the rows below (chol_trsm_tc_kernel) as seven BF16 slice planes, row c on the scale 2^f_c >=
 // max_k |Minv[c, k]|, with f_0 .. f_63 and g = max_k e_k over the panel's rows in mout_f.  The CTA
-// runs the two 32 x 32 pivots (pivot32) and shares the 32 x 32 x 32 products between its four warps:
+// runs the two 32 x 32 pivots (pivot32) and shares the 32 x 32 x 32 products between its warps:
 //   L_ba = A_ba L_aa^-T,  A_cc -= L_ba L_ba^T,  T = L_ba L_aa^-1,  X = -L_cc^-1 T,
 // so that L11^-1 = [[L_aa^-1, 0], [X, L_cc^-1]].  Entries past n are taken as the identity.  In the
 // first panel each row's slicing exponent e_r (2^e_r >= sqrt(S_rr)) is written first.
-__global__ void __launch_bounds__(128, 4) chol_diag64_kernel(const BlockDesc* __restrict__ blocks,
+__global__ void __launch_bounds__(kDiagThreads, 4) chol_diag64_kernel(const BlockDesc* __restrict__ blocks,
                                                              double* __restrict__ pool, DevFlags* flags, int c0,
                                                              int32_t* __restrict__ scale_exp,
                                                              uint16_t* __restrict__ mout,
@@ -748,7 +751,7 @@ __global__ void __launch_bounds__(128, 4) chol_diag64_kernel(const BlockDesc* __
   const int nb = min(64, n - c0);
   if (tid == 0) s_bad = 0;
   if (c0 == 0 && scale_exp)
-    for (int r = tid; r < ld; r += 128) {
+    for (int r = tid; r < ld; r += kDiagThreads) {
       int e = 0;
       if (r < n) {
         const float2 d = A[(int64_t)r * ld + r];
@@ -756,7 +759,7 @@ __global__ void __launch_bounds__(128, 4) chol_diag64_kernel(const BlockDesc* __
       }
       scale_exp[bd.row_off + r] = e;
     }
-  for (int e = tid; e < 64 * 64; e += 128) {
+  for (int e = tid; e < 64 * 64; e += kDiagThreads) {
     const int r = e >> 6, c = e & 63;
     df32 v = {(r == c) ? 1.f : 0.f, 0.f};
     if (r < nb && c <= r) {
@@ -770,7 +773,7 @@ __global__ void __launch_bounds__(128, 4) chol_diag64_kernel(const BlockDesc* __
   // The 32 x 32 x 32 products below take two rows per pass: two independent double-float chains per
   // thread (every sum keeps its own order).
   // L_ba[i][j] = sum_{k <= j} A_ba[i][k] (L_aa^-1)[j][k]
-  for (int i = warp * 8; i < warp * 8 + 8; i += 2) {
+  for (int i = warp * kDiagRows; i < warp * kDiagRows + kDiagRows; i += 2) {
     df32 acc0 = {0.f, 0.f}, acc1 = {0.f, 0.f};
     for (int k = 0; k <= lane; ++k) {
       const df32 x = Xa[lane][k];
@@ -781,10 +784,10 @@ __global__ void __launch_bounds__(128, 4) chol_diag64_kernel(const BlockDesc* __
     M[i + 1][32 + lane] = df_norm(acc1);
   }
   __syncthreads();
-  for (int i = warp * 8; i < warp * 8 + 8; ++i) M[32 + i][lane] = M[i][32 + lane];
+  for (int i = warp * kDiagRows; i < warp * kDiagRows + kDiagRows; ++i) M[32 + i][lane] = M[i][32 + lane];
   __syncthreads();
   // A_cc[i][j] -= sum_k L_ba[i][k] L_ba[j][k]   (j <= i)
-  for (int i = warp * 8; i < warp * 8 + 8; i += 2) {
+  for (int i = warp * kDiagRows; i < warp * kDiagRows + kDiagRows; i += 2) {
     if (lane > i + 1) continue;
     const bool both = lane <= i;
     df32 acc0 = both ? M[32 + i][32 + lane] : df32{0.f, 0.f};
@@ -799,7 +802,7 @@ __global__ void __launch_bounds__(128, 4) chol_diag64_kernel(const BlockDesc* __
   }
   __syncthreads();
   pivot32(reinterpret_cast<df32(*)[65]>(&M[32][32]), Xc, rk, &s_bad);
-  for (int e = tid; e < 64 * 64; e += 128) {
+  for (int e = tid; e < 64 * 64; e += kDiagThreads) {
     const int r = e >> 6, c = e & 63;
     if (r < nb && c <= r) {
       const int64_t o = (int64_t)(c0 + r) * ld + c0 + c;
@@ -810,12 +813,12 @@ __global__ void __launch_bounds__(128, 4) chol_diag64_kernel(const BlockDesc* __
   // the FP32 factor's padding rows are read as operands (times zeros of the inverse): zero them once,
   // in the block's last panel; its strict upper triangle is never read
   if (l32 && n <= c0 + 64)
-    for (int64_t e = tid; e < (int64_t)(ld - n) * ld; e += 128) l32[bd.off_mat + (int64_t)n * ld + e] = 0.f;
+    for (int64_t e = tid; e < (int64_t)(ld - n) * ld; e += kDiagThreads) l32[bd.off_mat + (int64_t)n * ld + e] = 0.f;
   const bool want_m = mout && n > c0 + 64;
   if (want_m || x32) {
     // T = L_ba L_aa^-1, X = -L_cc^-1 T (two rows per pass; row i's X sum stops at k = i, since
     // L_cc^-1 is lower triangular)
-    for (int i = warp * 8; i < warp * 8 + 8; i += 2) {
+    for (int i = warp * kDiagRows; i < warp * kDiagRows + kDiagRows; i += 2) {
       df32 acc0 = {0.f, 0.f}, acc1 = {0.f, 0.f};
       for (int k = lane; k < 32; ++k) {
         const df32 x = Xa[k][lane];
@@ -826,7 +829,7 @@ __global__ void __launch_bounds__(128, 4) chol_diag64_kernel(const BlockDesc* __
       M[i + 1][32 + lane] = df_norm(acc1);
     }
     __syncthreads();                             // T complete, L_ba (and L11's write-out) read
-    for (int i = warp * 8; i < warp * 8 + 8; i += 2) {
+    for (int i = warp * kDiagRows; i < warp * kDiagRows + kDiagRows; i += 2) {
       df32 acc0 = {0.f, 0.f}, acc1 = {0.f, 0.f};
       for (int k = 0; k <= i; ++k) {
         const df32 t = M[k][32 + lane];
@@ -850,7 +853,7 @@ __global__ void __launch_bounds__(128, 4) chol_diag64_kernel(const BlockDesc* __
     // the FP32 rounding of L11^-1 as the diagonal 64 x 64 block of the mixed paths' L^-1 (zero above
     // the diagonal and on the padding rows)
     float* Xo = x32 + bd.off_mat + (int64_t)c0 * ld + c0;
-    for (int e = tid; e < 4096; e += 128) {
+    for (int e = tid; e < 4096; e += kDiagThreads) {
       const int r = e >> 6, c = e & 63;
       float v = 0.f;
       if (r < nb && c <= r) {
@@ -876,7 +879,7 @@ __global__ void __launch_bounds__(128, 4) chol_diag64_kernel(const BlockDesc* __
     }
     __syncthreads();
     uint16_t* P = mout + (int64_t)blockIdx.x * 7 * 4096;   // plane s: 64 rows c x 64 columns k
-    for (int e = tid; e < 4096; e += 128) {
+    for (int e = tid; e < 4096; e += kDiagThreads) {
       const int c = e >> 6, k = e & 63;
       const df32 v = minv(c, k);
       float q[7];
@@ -1197,7 +1200,7 @@ cudaError_t launch_cholesky_inverse(nolsm_ctx* ctx, double* sb, int mode) {
     for (int pnl = 0; pnl * kOzPanel < max_n; ++pnl) {
       const int c0 = pnl * kOzPanel;
       if (pnl > 0 && (e = phase_mark(ctx, NOLSM_PHASE_FACTOR)) != cudaSuccess) return e;
-      chol_diag64_kernel<<<ctx->n_blocks, 128, 0, ctx->stream>>>(ctx->d_blocks, sb, ctx->d_flags, c0, ctx->d_oz_exp,
+      chol_diag64_kernel<<<ctx->n_blocks, kDiagThreads, 0, ctx->stream>>>(ctx->d_blocks, sb, ctx->d_flags, c0, ctx->d_oz_exp,
                                                                  ctx->d_oz_m, ctx->d_oz_f, s32,
                                                                  ctx->cong_simt ? nullptr : ctx->d_linv);
       ctx->n_launches += 1;
