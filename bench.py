@@ -728,6 +728,10 @@ def traffic_per_launch(kernel, units):
         return None
 
 
+OZ_SLICES = 6                                   # 8-bit slices per double-float value (csrc/internal.h)
+TRSM_OPS_PER_ENTRY = 2 * (10 * OZ_SLICES + 6) + 8 * OZ_SLICES
+
+
 def oz_update_tiles(n_b, panel=64, tm=128, tn=32):
     """128 x 32 tiles of the tensor-core trailing updates of the blocked double-float Cholesky (the
     library's work items: per panel, 32-column chunks of the trailing columns, and their 128-row
@@ -749,12 +753,12 @@ def rooflines(stage_ms, cnt, steps, n_b, pk, sm_max_mhz, props, products_per_lau
       product at the true n_b) over its time; the executed fraction (padded n_pad, whole diagonal
       tiles) beside it;
     * chol_update_kernel ('factor_update'): tensor cores, the executed BF16 FLOP of the slice-pair
-      products (28 pairs x 2 x 128 x 32 x 64 per tile);
-    * chol_trsm_tc_kernel ('factor_trsm'): the FP32 pipe, which splits every entry of A21 into seven
-      slices, adds the seven level sums of the result in double-float and splits the result again
-      (76 + 56 + 76 = 208 FP32 operations per entry of L21, 64 entries per trailing row per panel; the
-      slice products themselves are a small tensor-core load); peak: 128 FP32 operations per SM and
-      clock;
+      products (OZ_SLICES (OZ_SLICES + 1) / 2 = 21 pairs x 2 x 128 x 32 x 64 per tile);
+    * chol_trsm_tc_kernel ('factor_trsm'): the FP32 pipe, which splits every entry of A21 into six
+      slices, adds the six level sums of the result in double-float and splits the result again
+      (66 + 48 + 66 = 180 FP32 operations per entry of L21: 10 per slice and 6 more per splitting,
+      8 per level; 64 entries per trailing row per panel; the slice products themselves are a small
+      tensor-core load); peak: 128 FP32 operations per SM and clock;
     * the triangular inverse ('inverse', mixed paths: 128 x 128 diagonal blocks from the factor's
       64 x 64 inverses on the FP32 pipe, the off-diagonal blocks as three-pass TF32 tensor-core
       products): n_b^3 / 3 FP32-accurate flops per
@@ -779,7 +783,7 @@ def rooflines(stage_ms, cnt, steps, n_b, pk, sm_max_mhz, props, products_per_lau
     upd_ms = stage_ms.get("factor_update", 0.0)
     if upd_ms > 0:
         tiles = oz_update_tiles(n_b)
-        flop = tiles * 28 * 2.0 * 128 * 32 * 64
+        flop = tiles * (OZ_SLICES * (OZ_SLICES + 1) // 2) * 2.0 * 128 * 32 * 64
         ach = flop / (upd_ms * 1e-3) / 1e12
         out.append({"kernel": "chol_update_kernel (Cholesky trailing updates from exact BF16 slices, tcgen05; "
                               "7 launches per step, traffic summed)",
@@ -790,13 +794,14 @@ def rooflines(stage_ms, cnt, steps, n_b, pk, sm_max_mhz, props, products_per_lau
     trsm_ms = stage_ms.get("factor_trsm", 0.0)
     if trsm_ms > 0:
         rows = sum(max(int(n) - t0, 0) for n in n_b for t0 in range(64, int(n), 64))
-        ops = rows * 64 * 208.0
+        ops = rows * 64 * float(TRSM_OPS_PER_ENTRY)
         ach = ops / (trsm_ms * 1e-3) / 1e12
         out.append({"kernel": "chol_trsm_tc_kernel (rows below each 64 x 64 diagonal block: exact slices, "
                               "tcgen05 slice products, double-float recombination)",
                     "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "T FP32 operations/s",
                     "frac": ach / alu_peak,
-                    "work": "208 FP32 operations per entry of L21 (slicing A21, adding the seven levels, slicing L21)",
+                    "work": f"{TRSM_OPS_PER_ENTRY} FP32 operations per entry of L21 (slicing A21, adding the "
+                            f"{OZ_SLICES} levels, slicing L21)",
                     "peak_source": f"derived: {sms} SMs x 128 FP32 operations/clk x {mhz:.0f} MHz",
                     "ms_per_step": trsm_ms, "traffic": traffic_per_launch("chol_trsm_tc_kernel", rows)})
     inv_ms = stage_ms.get("inverse", 0.0)

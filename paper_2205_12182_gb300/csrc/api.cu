@@ -541,12 +541,12 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
     int64_t items = 0;
     for (const auto& bd : ctx->h_blocks) items += (int64_t)(bd.n_pad / kOzPanel + 1) * (bd.n_pad / 32 + 1);
     CK(dalloc(ctx, &ctx->d_oz_exp, (size_t)ctx->sum_pad));
-    CK(dalloc(ctx, &ctx->d_oz_planes, (size_t)(7 * kOzPanel) * (size_t)ctx->sum_pad));
+    CK(dalloc(ctx, &ctx->d_oz_planes, (size_t)(kOzSlices * kOzPanel) * (size_t)ctx->sum_pad));
     CK(dalloc(ctx, &ctx->d_oz_items, (size_t)(2 * items)));
     int n_bins = 0;
     for (const auto& bd : ctx->h_blocks) n_bins = std::max(n_bins, bd.bin + 1);
     CK(dalloc(ctx, &ctx->d_oz_tmaps, (size_t)128 * (size_t)(3 + 2 * n_bins)));   // CUtensorMap: 128 bytes
-    CK(dalloc(ctx, &ctx->d_oz_m, (size_t)7 * 4096 * (size_t)n_blocks));
+    CK(dalloc(ctx, &ctx->d_oz_m, (size_t)kOzSlices * 4096 * (size_t)n_blocks));
     CK(dalloc(ctx, &ctx->d_oz_f, (size_t)68 * (size_t)n_blocks));
     int64_t tr_items = 0;
     for (const auto& bd : ctx->h_blocks) tr_items += (int64_t)(bd.n_pad / kOzPanel + 1) * (bd.n_pad / 128 + 1);

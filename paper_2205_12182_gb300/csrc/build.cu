@@ -723,7 +723,7 @@ __device__ __forceinline__ void pivot32(df32 (*P)[65], df32 (*X)[33], df32* rk, 
 
 // The 64 x 64 diagonal block [c0, c0 + 64) of a panel, whose earlier panels' contributions are
 // already subtracted: L11 in place (pairs) and, when rows follow below, Minv = L11^-1 for the TRSM of
-// the rows below (chol_trsm_tc_kernel) as seven BF16 slice planes, row c on the scale 2^f_c >=
+// the rows below (chol_trsm_tc_kernel) as kOzSlices BF16 slice planes, row c on the scale 2^f_c >=
 // max_k |Minv[c, k]|, with f_0 .. f_63 and g = max_k e_k over the panel's rows in mout_f.  The CTA
 // runs the two 32 x 32 pivots (pivot32) and shares the 32 x 32 x 32 products between its warps:
 //   L_ba = A_ba L_aa^-T,  A_cc -= L_ba L_ba^T,  T = L_ba L_aa^-1,  X = -L_cc^-1 T,
@@ -878,14 +878,14 @@ __global__ void __launch_bounds__(kDiagThreads, 4) chol_diag64_kernel(const Bloc
       F[64] = g;
     }
     __syncthreads();
-    uint16_t* P = mout + (int64_t)blockIdx.x * 7 * 4096;   // plane s: 64 rows c x 64 columns k
+    uint16_t* P = mout + (int64_t)blockIdx.x * kOzSlices * 4096;   // plane s: 64 rows c x 64 columns k
     for (int e = tid; e < 4096; e += kDiagThreads) {
       const int c = e >> 6, k = e & 63;
       const df32 v = minv(c, k);
-      float q[7];
+      float q[kOzSlices];
       oz_slices(v.h, v.l, oz_scale(fexp[c]), q);
 #pragma unroll
-      for (int sl = 0; sl < 7; ++sl) {
+      for (int sl = 0; sl < kOzSlices; ++sl) {
         const __nv_bfloat16 b = __float2bfloat16_rn(q[sl]);
         P[sl * 4096 + e] = *reinterpret_cast<const uint16_t*>(&b);
       }

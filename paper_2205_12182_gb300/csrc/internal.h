@@ -150,13 +150,13 @@ struct nolsm_ctx {
   // (<= 32 columns) first, then wide ones (<= 192), each group largest block first
   int32_t* d_slab_units = nullptr;
   // blocked double-float Cholesky with tensor-core trailing updates: slicing exponent per row,
-  // seven BF16 slice planes per row of the current panel, work items (block, first column) of
+  // kOzSlices BF16 slice planes per row of the current panel, work items (block, first column) of
   // every panel's update and where each panel's items start
   int32_t* d_oz_exp = nullptr;
   uint16_t* d_oz_planes = nullptr;
   int32_t* d_oz_items = nullptr;
   uint8_t* d_oz_tmaps = nullptr;
-  // M = L11^-1 of the current panel: seven BF16 slice planes of 64 x 64 per block, each row c on its
+  // M = L11^-1 of the current panel: kOzSlices BF16 slice planes of 64 x 64 per block, each row c on its
   // own scale 2^f_c; per block 68 ints: f_0 .. f_63 and g = the largest row exponent of the panel
   uint16_t* d_oz_m = nullptr;
   int32_t* d_oz_f = nullptr;
@@ -326,24 +326,30 @@ cudaError_t launch_transpose(nolsm_ctx* ctx);
 cudaError_t launch_index_sets(nolsm_ctx* ctx, const int32_t* d_blk_ptr, const int32_t* d_extra_ptr,
                               const int32_t* d_extra_idx, int32_t* d_nb, int cap, int max_dim);
 
+// Exact slicing of double-float values for the tensor-core factor (Ozaki, Ogita, Oishi & Rump
+// 2012): kOzSlices integer slices of kOzBits bits each, 48 bits in all (the pairs' precision).
+constexpr int kOzSlices = 6;
+constexpr int kOzBits = 8;
 #ifdef __CUDACC__
-// Seven 7-bit integer slices of a double-float value h + l on the scale 2^e (|h + l| <= 2^e), given
-// sc = 2^(7 - e) (oz_scale): h + l = 2^(e - 7) sum_s q_s 2^(-7 s) + rest with |q_0| <= 128,
-// |q_s| <= 64 after it and |rest| <= 2^(e - 50); every q_s is exact in BF16 (error-free splitting,
-// Ozaki, Ogita, Oishi & Rump 2012).  The remainder of each step is carried exactly by a TwoSum with
-// the low word.
-__device__ __forceinline__ float oz_scale(int e) { return ldexpf(1.f, 7 - e); }
-__device__ __forceinline__ void oz_slices(float h, float l, float sc, float (&q)[7]) {
+// The slices of h + l on the scale 2^e (|h + l| <= 2^e), given sc = 2^(8 - e) (oz_scale):
+// h + l = 2^(e - 8) sum_s q_s 2^(-8 s) + rest with |q_0| <= 256, |q_s| <= 128 after it and
+// |rest| <= 2^(e - 49); every q_s is an integer exact in BF16 (8 significant bits).  A product of two
+// slices is exact (at most 2^16), and the sum over a 64-wide panel of the products of one level
+// l = s + t <= 5 is at most 64 (l + 3) 2^14 <= 2^23 (level 0: 2^22), an integer exact in FP32.  The
+// remainder of each step is carried exactly by a TwoSum with the low word.
+__device__ __forceinline__ float oz_scale(int e) { return ldexpf(1.f, kOzBits - e); }
+__device__ __forceinline__ void oz_slices(float h, float l, float sc, float (&q)[kOzSlices]) {
+  constexpr float radix = (float)(1 << kOzBits);
   float hh = h * sc, ll = l * sc;
 #pragma unroll
-  for (int s = 0; s < 7; ++s) {
+  for (int s = 0; s < kOzSlices; ++s) {
     q[s] = rintf(hh);
     const float d = hh - q[s];
     const float sum = d + ll;
     const float bb = sum - d;
     const float err = (d - (sum - bb)) + (ll - bb);
-    hh = sum * 128.f;
-    ll = err * 128.f;
+    hh = sum * radix;
+    ll = err * radix;
   }
 }
 #endif

@@ -1568,20 +1568,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) slab_tc_kernel(const __grid_co
 // ---------------------------------------------------------------------------------------------
 // Trailing update of the blocked double-float Cholesky on the tensor cores.  After panel p (columns
 // [c0, c0 + 64)) is factored, every trailing entry C[r, c] (c0 + 64 <= c <= r) loses
-// sum_{k in panel} L[r, k] L[c, k].  Each L entry is split into seven 7-bit integers on its row's
-// scale (chol_trsm_kernel; Ozaki, Ogita, Oishi & Rump 2012), so
-//   L[r, k] L[c, k] = 2^(e_r + e_c - 14) sum_{s, t} q_s(r, k) q_t(c, k) 2^(-7 (s + t))
-// and the pairs with s + t = l <= 6 are summed over k by BF16 MMAs into the FP32 tensor-memory
-// accumulator of level l: every product is an integer of at most 2^14 and a level sums at most
-// 7 x 64 of them (< 2^23), so the accumulators are exact.  Pairs with s + t > 6 lie below 2^-49 of
-// the scale and are dropped (the double-float arithmetic keeps 2^-48).  The epilogue adds the levels
+// sum_{k in panel} L[r, k] L[c, k].  Each L entry is split into six 8-bit integers on its row's
+// scale (oz_slices; Ozaki, Ogita, Oishi & Rump 2012), so
+//   L[r, k] L[c, k] = 2^(e_r + e_c - 16) sum_{s, t} q_s(r, k) q_t(c, k) 2^(-8 (s + t))
+// and the pairs with s + t = l <= 5 are summed over k by BF16 MMAs into the FP32 tensor-memory
+// accumulator of level l: every product is an integer of at most 2^16 and a level's sum stays at
+// or below 2^23, so the accumulators are exact.  Pairs with s + t > 5 lie below 2^-47 of the scale
+// per term and are dropped (the double-float arithmetic keeps 2^-48).  The epilogue adds the levels
 // in double-float from the smallest up, scales by the power of two and subtracts from C (pairs in
 // place).
-// Work item = (block, 32 columns n0): the seven 32 x 64 B planes of rows n0.. stay in shared memory
+// Work item = (block, 32 columns n0): the six 32 x 64 B planes of rows n0.. stay in shared memory
 // (double-buffered across items) while the 128-row A tiles of rows >= n0 - 127 stream through a
-// six-stage ring, one plane per stage.  Plane s of A meets the B planes t = 0 .. 6 - s in one MMA of
-// N = 32 (7 - s) (the B planes are stacked, so its output columns are the accumulators of levels
-// s .. 6): 7 x 4 K-steps = 28 MMAs (M = 128, K = 16) per tile into 7 x 32 accumulator columns, two
+// six-stage ring, one plane per stage.  Plane s of A meets the B planes t = 0 .. 5 - s in one MMA of
+// N = 32 (6 - s) (the B planes are stacked, so its output columns are the accumulators of levels
+// s .. 5): 6 x 4 K-steps = 24 MMAs (M = 128, K = 16, 21 slice pairs) per tile into 6 x 32
+// accumulator columns, two
 // accumulator sets.  The tile's 128 x 32 pairs of C
 // (32 KB) come into shared memory by two tensor copies issued with the tile's planes (two C buffers,
 // so the next tile's C is in flight while the epilogue works) and go back by one tensor store per
@@ -1593,12 +1594,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) slab_tc_kernel(const __grid_co
 // A 128-row box that starts 64 rows before the end of the block reaches into the next block of the
 // bin's stack: its loads are harmless and unused, and no store is issued for a 32-row group that
 // starts at or past n (so nothing outside the block's own rows is written).
-constexpr int OZ_NSL = 7;
+constexpr int OZ_NSL = kOzSlices;
 constexpr int OZ_TN = 32;
 constexpr int OZ_NST = 6;
 constexpr int OZ_A_BYTES = TM * kOzPanel * 2;                  // one plane of a 128-row tile
 constexpr int OZ_PLANE_B = OZ_TN * kOzPanel * 2;               // one plane of 32 rows
-constexpr int OZ_B_BYTES = OZ_NSL * OZ_PLANE_B;                // 28 KB
+constexpr int OZ_B_BYTES = OZ_NSL * OZ_PLANE_B;                // 24 KB
 constexpr int OZ_B_OFF = OZ_NST * OZ_A_BYTES;
 constexpr int OZ_CBOX_BYTES = TM * 16 * 8;                     // 128 rows x 16 pairs (128-byte rows)
 constexpr int OZ_C_BYTES = 2 * OZ_CBOX_BYTES;                  // the tile's 128 x 32 pairs of C
@@ -1691,7 +1692,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) chol_update_kernel(const __grid
       for (int it = blockIdx.x; it < p.n_items && ok; it += gridDim.x) {
         const int b = p.items[2 * it], n0 = p.items[2 * it + 1];
         const BlockDesc bd = p.blocks[b];
-        const int np = bd.n_pad, rbase = 7 * bd.row_off;
+        const int np = bd.n_pad, rbase = OZ_NSL * bd.row_off;
         const CUtensorMap* cmap = p.maps + 2 + 2 * bd.bin;
         const int crow = bd.pos * np;
         if (!mbar_wait(&bempty_bar[bb], bph[bb] ^ 1u, budget, abort_flag)) { ok = false; break; }
@@ -1754,7 +1755,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) chol_update_kernel(const __grid
           for (int s = 0; s < OZ_NSL; ++s) {
             if (!mbar_wait(&full_bar[ms], mph, budget, abort_flag)) { ok = false; break; }
             tc_fence_after();
-            // A plane s against B planes t = 0 .. 6 - s in one MMA: the planes lie back to back (32 rows
+            // A plane s against B planes t = 0 .. 5 - s in one MMA: the planes lie back to back (32 rows
             // each), so output column 32 t + j lands in the accumulator of level s + t, column j
             const uint64_t adesc = sw128_desc(smem_u32(smem + ms * OZ_A_BYTES));
             const uint64_t bdesc = sw128_desc(b_addr);
@@ -1842,17 +1843,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) chol_update_kernel(const __grid
           for (int j = 0; j < 8; ++j) {
             const int c = c0 + j;
             if (c > r) break;
-            // sum_l v_l 2^(-7 l) in double-float, smallest level first (every term is exact)
-            float h = __uint_as_float(v[OZ_NSL - 1][j]) * 0x1p-42f, lo = 0.f;
+            // sum_l v_l 2^(-8 l) in double-float, smallest level first (every term is exact)
+            float h = __uint_as_float(v[OZ_NSL - 1][j]) * 0x1p-40f, lo = 0.f;
 #pragma unroll
             for (int l = OZ_NSL - 2; l >= 0; --l) {
-              const float x = __uint_as_float(v[l][j]) * __int_as_float((127 - 7 * l) << 23);
+              const float x = __uint_as_float(v[l][j]) * __int_as_float((127 - kOzBits * l) << 23);
               const float s = h + x;
               const float bb2 = s - h;
               lo += (h - (s - bb2)) + (x - bb2);
               h = s;
             }
-            const float sc = __int_as_float((127 + er + ec[j] - 14) << 23);
+            const float sc = __int_as_float((127 + er + ec[j] - 2 * kOzBits) << 23);
             h *= sc;
             lo *= sc;
             // C - (h + lo), renormalised
@@ -1906,22 +1907,22 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) chol_update_kernel(const __grid
 // is split on the scale 2^(e_r + g), g = max_k e_k over the panel's rows: by Cauchy-Schwarz on the
 // rows of the factor |A21[r, k]| <= sqrt(S_rr S_kk) <= 2^(e_r + g).  Row c of Minv is split on its own
 // scale 2^f_c (chol_diag64_kernel).  So
-//   L21[r, c] = 2^(e_r + g + f_c - 14) sum_l 2^(-7 l) sum_{s + t = l} sum_k q_s(r, k) p_t(c, k),
-// every level sum exact in FP32 (at most 7 x 64 products of at most 2^14), the pairs with s + t > 6
-// (below 2^-49 of the scale per term) dropped.  The epilogue adds the levels in double-float, writes
+//   L21[r, c] = 2^(e_r + g + f_c - 16) sum_l 2^(-8 l) sum_{s + t = l} sum_k q_s(r, k) p_t(c, k),
+// every level sum exact in FP32 (at most 2^23, see oz_slices), the pairs with s + t > 5 (below
+// 2^-47 of the scale per term) dropped.  The epilogue adds the levels in double-float, writes
 // L21 as pairs over A21 and its slices on the row scale e_r into the planes the trailing update reads.
 // Work item = (block, 128 rows m0 of the rows below the diagonal block): the CTA keeps the block's
-// Minv planes (both 32-column halves, 56 KB) while its items follow each other (contiguous runs of
+// Minv planes (both 32-column halves, 48 KB) while its items follow each other (contiguous runs of
 // the item list per CTA), the item's 128 x 64 A21 pairs arrive as four 128 x 16 tensor copies through
-// a three-box staging ring, converter warps slice them into seven A planes in shared memory, and the
+// a three-box staging ring, converter warps slice them into six A planes in shared memory, and the
 // MMA issuer runs, per half and per A plane s, one MMA against the stacked
-// B planes t = 0 .. 6 - s (N = 32 (7 - s)), so the 7 levels x 32 columns of a half land in one of
+// B planes t = 0 .. 5 - s (N = 32 (6 - s)), so the 6 levels x 32 columns of a half land in one of
 // the two accumulator sets.  Roles (448 threads): warp 0 TMA producer (Minv planes), warp 1 MMA
 // issuer, warps 2..5 converter, warps 6..13 epilogue (one per TMEM lane quarter and half).  Waits
 // are bounded as in ns_tc_kernel.  Rows from n on are neither read nor written.
 constexpr int TR_THREADS = 448;
-constexpr int TR_A_OFF = 0;                                    // 7 A planes of 128 x 64 BF16
-constexpr int TR_B_OFF = OZ_NSL * OZ_A_BYTES;                  // 2 halves x 7 planes of 32 x 64 BF16
+constexpr int TR_A_OFF = 0;                                    // 6 A planes of 128 x 64 BF16
+constexpr int TR_B_OFF = OZ_NSL * OZ_A_BYTES;                  // 2 halves x 6 planes of 32 x 64 BF16
 constexpr int TR_NSS = 3;                                      // staging ring of A21 boxes (128 x 16 pairs)
 constexpr int TR_S_OFF = TR_B_OFF + 2 * OZ_B_BYTES;
 constexpr int TR_BAR_OFF = TR_S_OFF + TR_NSS * OZ_CBOX_BYTES;
@@ -1931,7 +1932,7 @@ static_assert(TR_SMEM <= 227 * 1024, "shared memory of the TRSM kernel");
 struct TrParams {
   const TrItem* items;          // this panel's tiles, grouped by block
   int n_items;
-  const CUtensorMap* mmap;      // 64 x 32 boxes over the Minv planes (7 x 64 rows per block)
+  const CUtensorMap* mmap;      // 64 x 32 boxes over the Minv planes (6 x 64 rows per block)
   const CUtensorMap* cmaps;     // per bin [2 bin]: 16 x 128 boxes over the pool of pairs
   double* pool;                 // factor in double-float pairs (8 bytes an entry)
   const int32_t* scale_exp;     // e_r per row (row_off indexing)
@@ -2077,7 +2078,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1) chol_trsm_tc_kernel(const __gri
       mbar_wait(drain_bar, 0, drain_budget, &never);
     }
   } else if (warp < 6) {
-    // ------------------------------------------------------------ converter: A21 pairs -> 7 A planes
+    // ------------------------------------------------------------ converter: A21 pairs -> 6 A planes
     // (thread = row of the tile; per staged box its 16 pairs, two 16-byte units of every plane)
     const int ct = threadIdx.x - 64;   // 0..127
     uint32_t aph = 0, sph = 0;
@@ -2111,17 +2112,17 @@ __global__ void __launch_bounds__(TR_THREADS, 1) chol_trsm_tc_kernel(const __gri
         if (++ss == TR_NSS) { ss = 0; sph ^= 1u; }
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-          uint32_t pk[7][4];
+          uint32_t pk[OZ_NSL][4];
 #pragma unroll
           for (int x = 0; x < 8; x += 2) {
-            float q0[7], q1[7];
+            float q0[OZ_NSL], q1[OZ_NSL];
             oz_slices(f[16 * u + 2 * x], f[16 * u + 2 * x + 1], esc, q0);
             oz_slices(f[16 * u + 2 * x + 2], f[16 * u + 2 * x + 3], esc, q1);
 #pragma unroll
-            for (int sl = 0; sl < 7; ++sl) pk[sl][x >> 1] = Pack<__nv_bfloat16>::two(q0[sl], q1[sl]);
+            for (int sl = 0; sl < OZ_NSL; ++sl) pk[sl][x >> 1] = Pack<__nv_bfloat16>::two(q0[sl], q1[sl]);
           }
 #pragma unroll
-          for (int sl = 0; sl < 7; ++sl)
+          for (int sl = 0; sl < OZ_NSL; ++sl)
             *reinterpret_cast<uint4*>(smem + TR_A_OFF + sl * OZ_A_BYTES + sw128(ct, 16 * (2 * box + u))) =
                 make_uint4(pk[sl][0], pk[sl][1], pk[sl][2], pk[sl][3]);
         }
@@ -2157,11 +2158,11 @@ __global__ void __launch_bounds__(TR_THREADS, 1) chol_trsm_tc_kernel(const __gri
       }
       tph ^= 1u;
       tc_fence_after();
-      const int eg = er + g - 14;
+      const int eg = er + g - 2 * kOzBits;
       const float rsc = oz_scale(er);
       float2* Lrow = reinterpret_cast<float2*>(p.pool + ti.off_mat) + (int64_t)r * ld + c0;
       float* L32row = p.l32 + ti.off_mat + (int64_t)r * ld + c0;
-      __nv_bfloat16* P = p.planes + ((int64_t)7 * ti.row_off + r) * 64;
+      __nv_bfloat16* P = p.planes + ((int64_t)OZ_NSL * ti.row_off + r) * 64;
       for (int j = 0; j < 4; ++j) {
         const int cb = 32 * h + 8 * j;            // first of this chunk's 8 columns of the panel
         uint32_t v[OZ_NSL][8];
@@ -2176,11 +2177,11 @@ __global__ void __launch_bounds__(TR_THREADS, 1) chol_trsm_tc_kernel(const __gri
         float out[16];
 #pragma unroll
         for (int x = 0; x < 8; ++x) {
-          // sum_l v_l 2^(-7 l) in double-float, smallest level first (every term is exact)
-          float hi = __uint_as_float(v[OZ_NSL - 1][x]) * 0x1p-42f, lo = 0.f;
+          // sum_l v_l 2^(-8 l) in double-float, smallest level first (every term is exact)
+          float hi = __uint_as_float(v[OZ_NSL - 1][x]) * 0x1p-40f, lo = 0.f;
 #pragma unroll
           for (int l = OZ_NSL - 2; l >= 0; --l) {
-            const float y = __uint_as_float(v[l][x]) * __int_as_float((127 - 7 * l) << 23);
+            const float y = __uint_as_float(v[l][x]) * __int_as_float((127 - kOzBits * l) << 23);
             const float s = hi + y;
             const float bb = s - hi;
             lo += (hi - (s - bb)) + (y - bb);
@@ -2203,17 +2204,17 @@ __global__ void __launch_bounds__(TR_THREADS, 1) chol_trsm_tc_kernel(const __gri
               make_float4(out[8 * w] + out[8 * w + 1], out[8 * w + 2] + out[8 * w + 3], out[8 * w + 4] + out[8 * w + 5],
                           out[8 * w + 6] + out[8 * w + 7]);
         // slices of the row on its own scale for the trailing update: plane s, row r, columns cb ..
-        uint32_t pk[7][4];
+        uint32_t pk[OZ_NSL][4];
 #pragma unroll
         for (int x = 0; x < 8; x += 2) {
-          float q0[7], q1[7];
+          float q0[OZ_NSL], q1[OZ_NSL];
           oz_slices(out[2 * x], out[2 * x + 1], rsc, q0);
           oz_slices(out[2 * x + 2], out[2 * x + 3], rsc, q1);
 #pragma unroll
-          for (int sl = 0; sl < 7; ++sl) pk[sl][x >> 1] = Pack<__nv_bfloat16>::two(q0[sl], q1[sl]);
+          for (int sl = 0; sl < OZ_NSL; ++sl) pk[sl][x >> 1] = Pack<__nv_bfloat16>::two(q0[sl], q1[sl]);
         }
 #pragma unroll
-        for (int sl = 0; sl < 7; ++sl)
+        for (int sl = 0; sl < OZ_NSL; ++sl)
           *reinterpret_cast<uint4*>(P + (int64_t)sl * ld * 64 + cb) = make_uint4(pk[sl][0], pk[sl][1], pk[sl][2], pk[sl][3]);
       }
       tc_fence_before();
@@ -2883,7 +2884,7 @@ cudaError_t oz_prepare(nolsm_ctx* ctx) {
   int n_bins = 0;
   for (const auto& b : ctx->h_blocks) n_bins = std::max(n_bins, b.bin + 1);
   std::vector<CUtensorMap> maps((size_t)(3 + 2 * n_bins));
-  const uint64_t rows = (uint64_t)7 * (uint64_t)std::max<int64_t>(ctx->sum_pad, 1);
+  const uint64_t rows = (uint64_t)OZ_NSL * (uint64_t)std::max<int64_t>(ctx->sum_pad, 1);
   cuuint64_t gdim[2] = {(cuuint64_t)kOzPanel, rows};
   cuuint64_t gstride[1] = {(cuuint64_t)kOzPanel * 2};
   cuuint32_t estr[2] = {1, 1};
@@ -2922,9 +2923,9 @@ cudaError_t oz_prepare(nolsm_ctx* ctx) {
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   }
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  // the TRSM's Minv planes: 7 x 64 rows of 64 BF16 per block, 64 x 32 boxes
+  // the TRSM's Minv planes: 6 x 64 rows of 64 BF16 per block, 64 x 32 boxes
   {
-    cuuint64_t mdim[2] = {(cuuint64_t)kOzPanel, (cuuint64_t)7 * 64 * (cuuint64_t)std::max(ctx->n_blocks, 1)};
+    cuuint64_t mdim[2] = {(cuuint64_t)kOzPanel, (cuuint64_t)OZ_NSL * 64 * (cuuint64_t)std::max(ctx->n_blocks, 1)};
     cuuint64_t mstride[1] = {(cuuint64_t)kOzPanel * 2};
     r = encode(&maps[2 + 2 * n_bins], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ctx->d_oz_m, mdim, mstride, box_b, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
