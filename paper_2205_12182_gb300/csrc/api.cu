@@ -154,6 +154,9 @@ void release_pools(nolsm_ctx* ctx) {
   dfree(ctx->d_state); ctx->d_state = nullptr;
   dfree(ctx->d_tiles); ctx->d_tiles = nullptr;
   dfree(ctx->d_cg_kbeg); ctx->d_cg_kbeg = nullptr;
+  dfree(ctx->d_bt); ctx->d_bt = nullptr;
+  ctx->bt_dev = ctx->bt_kdev = nullptr;
+  ctx->bt_layout.clear();
   dfree(ctx->d_transpose); ctx->d_transpose = nullptr;
   dfree(ctx->d_dval); ctx->d_dval = nullptr;
   dfree(ctx->d_csr_own); ctx->d_csr_own = nullptr;
@@ -503,7 +506,15 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   CK(dalloc(ctx, &ctx->d_tol, (size_t)n_blocks));
   CK(dalloc(ctx, &ctx->d_state, (size_t)n_blocks));
   CK(dalloc(ctx, &ctx->d_tiles, (size_t)tiles_max));
-  CK(dalloc(ctx, &ctx->d_cg_kbeg, (size_t)tiles_max));
+  // the build's product tile lists: congruence passes (all 128 x 128 tiles, then those on or above
+  // the diagonal) and the tiled inverse (two launches per block row i >= 1, i tiles each)
+  ctx->bt_cap = 0;
+  for (const auto& bd : ctx->h_blocks) {
+    const int64_t q = bd.n_pad / kTile;
+    ctx->bt_cap += q * q + q * (q + 1) / 2 + q * (q - 1);
+  }
+  CK(dalloc(ctx, &ctx->d_bt, (size_t)ctx->bt_cap));
+  CK(dalloc(ctx, &ctx->d_cg_kbeg, (size_t)ctx->bt_cap));
   if (!ctx->chunked) CK(dalloc(ctx, &ctx->d_dval, (size_t)nnz));
   CK(cudaMemcpyAsync(ctx->d_blocks, ctx->h_blocks.data(), sizeof(BlockDesc) * n_blocks, cudaMemcpyHostToDevice, ctx->stream));
   if (!ctx->h_slab_units.empty())
@@ -515,7 +526,8 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
     // refinement steps need ||X^2 - I||_F ~ 2 delta no smaller than 0.02 (r >= 2: 3.4 delta^4 is
     // FP32 rounding for delta = 0.01) or 4e-4 (r = 1); never below the operand format's floor
     // 8 u sqrt(n) and never above 0.05.  Each further full iteration only adds rounding.
-    std::vector<float> tol((size_t)n_blocks);
+    std::vector<float>& tol = ctx->h_tol;   // the upload's source, kept until the next build
+    tol.assign((size_t)n_blocks, 0.f);
     const double u = unit_roundoff(ctx);
     const int r = ctx->opt.refine_iters;
     const double t_refine = r >= 2 ? 0.02 : r == 1 ? 4e-4 : 0.0;
@@ -524,7 +536,6 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
       tol[b] = (float)(ctx->opt.sign_tol > 0 ? ctx->opt.sign_tol : std::min(0.05, std::max(d, t_refine)));
     }
     CK(cudaMemcpyAsync(ctx->d_tol, tol.data(), sizeof(float) * n_blocks, cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
   }
 
   // ---- gather (H FP32 into A0's pool, S FP64), factor, inverse, congruence, slabs, bounds

@@ -104,6 +104,10 @@ struct nolsm_ctx {
   size_t cg_tmap_cap = 0;
   int64_t cg_maps_gen = -1;     // build whose pools the maps describe, and its T1 pool
   const float* cg_maps_t1 = nullptr;
+  // host copies of uploaded tensor maps and per-block tolerances: the sources of their asynchronous
+  // uploads stay alive until the next build, so the uploads need no wait on the stream
+  std::vector<uint8_t> h_cg_maps, h_oz_maps;
+  std::vector<float> h_tol;
   bool cong_simt = false;       // congruence on the SIMT FP32 products (tests compare both)
   nolsm_status sticky = NOLSM_OK;
   std::string last_error;
@@ -173,7 +177,15 @@ struct nolsm_ctx {
   nolsm::NsState* d_state = nullptr;
   nolsm::Tile* d_tiles = nullptr;
   int64_t max_tiles = 0;        // full tile count (capacity of d_tiles)
-  int32_t* d_cg_kbeg = nullptr; // first K of each tile of the tiled inverse (capacity max_tiles)
+  // the tile lists of the build's tensor-core products (the congruence's two passes, then the tiled
+  // inverse's launches) with each tile's first K, kept while the block layout stays the same
+  nolsm::Tile* d_bt = nullptr;
+  int32_t* d_cg_kbeg = nullptr;
+  int64_t bt_cap = 0;                          // capacity of both, in tiles
+  std::vector<nolsm::BlockDesc> bt_layout;     // the layout the device lists were made for
+  const void* bt_dev = nullptr;                // and the buffers they were written to
+  const void* bt_kdev = nullptr;
+  std::vector<int64_t> bt_start;               // launch k covers [bt_start[k], bt_start[k + 1])
   int64_t max_tiles_tc = 0;     // upper-triangular tensor-core tiles of all blocks
   nolsm::DevFlags* d_flags = nullptr;
   nolsm::DevFlags* h_flags = nullptr;   // pinned mirror

@@ -24,6 +24,7 @@
 #include <cuda_fp8.h>
 
 #include <cfloat>
+#include <cstring>
 
 namespace nolsm {
 namespace {
@@ -2711,10 +2712,12 @@ cudaError_t cg_maps(nolsm_ctx* ctx, float* t1) {
     if (e != cudaSuccess) return e;
     ctx->cg_tmap_cap = maps.size();
   }
-  cudaError_t e = cudaMemcpyAsync(ctx->d_cg_tmaps, maps.data(), maps.size() * sizeof(CUtensorMap),
+  // one encode per build (both callers pass the build's T1 pool); the upload's source lives in the
+  // context until the next build
+  ctx->h_cg_maps.assign(reinterpret_cast<const uint8_t*>(maps.data()),
+                        reinterpret_cast<const uint8_t*>(maps.data() + maps.size()));
+  cudaError_t e = cudaMemcpyAsync(ctx->d_cg_tmaps, ctx->h_cg_maps.data(), ctx->h_cg_maps.size(),
                                   cudaMemcpyHostToDevice, ctx->stream);
-  if (e != cudaSuccess) return e;
-  e = cudaStreamSynchronize(ctx->stream);   // maps is a host temporary
   if (e != cudaSuccess) return e;
   static bool attr_done = false;
   if (!attr_done) {
@@ -2750,52 +2753,34 @@ CgParams cg_params(nolsm_ctx* ctx, const Tile* tiles, const int32_t* kbeg, int n
   return p;
 }
 
-// The congruence on the tensor cores: T1 = L^-1 T_b(H0) (all tiles; L^-1 is lower triangular, so a
-// tile's K stops at m0 + 128), then A0 = T1 L^-T (tiles on or above the diagonal, K stops at
-// n0 + 128, output mirrored).
-cudaError_t launch_congruence_tc(nolsm_ctx* ctx, float* t1) {
-  cudaError_t e = cg_maps(ctx, t1);
-  if (e != cudaSuccess) return e;
+// The tile lists of the build's tensor-core products in one device list, made and uploaded only when
+// the block layout differs from the one they were made for (a rebuild of the same system neither
+// uploads nor waits on the stream):
+//   launch 0: congruence pass 0, T1 = L^-1 T_b(H0): all tiles; L^-1 is lower triangular, so a tile's
+//             K stops at m0 + 128;
+//   launch 1: congruence pass 1, A0 = T1 L^-T: tiles on or above the diagonal, K stops at n0 + 128;
+//   launches 2, 3, ...: the tiled inverse, two per block row i >= 1 (launch_trinv_tc).
+static cudaError_t build_tile_lists(nolsm_ctx* ctx) {
+  const size_t nbk = ctx->h_blocks.size();
+  if (ctx->bt_dev == ctx->d_bt && ctx->bt_kdev == ctx->d_cg_kbeg && ctx->d_bt && ctx->bt_layout.size() == nbk &&
+      std::memcmp(ctx->bt_layout.data(), ctx->h_blocks.data(), nbk * sizeof(BlockDesc)) == 0)
+    return cudaSuccess;
+  std::vector<Tile> tl;
+  std::vector<int32_t> kb;
+  std::vector<int64_t> start;
   for (int pass = 0; pass < 2; ++pass) {
-    std::vector<Tile> tl;
+    start.push_back((int64_t)tl.size());
     for (int32_t i = 0; i < ctx->n_blocks; ++i) {
       const BlockDesc& bd = ctx->h_blocks[i];
       for (int m0 = 0; m0 < bd.n_pad; m0 += TM)
-        for (int n0 = pass ? m0 : 0; n0 < bd.n_pad; n0 += CG_TN)
+        for (int n0 = pass ? m0 : 0; n0 < bd.n_pad; n0 += CG_TN) {
           tl.push_back(Tile{i, m0, n0, std::min(bd.n_pad, (pass ? n0 : m0) + TM)});
+          kb.push_back(0);
+        }
     }
-    if ((int64_t)tl.size() > ctx->max_tiles) return cudaErrorInvalidValue;
-    e = cudaMemcpyAsync(ctx->d_tiles, tl.data(), tl.size() * sizeof(Tile), cudaMemcpyHostToDevice, ctx->stream);
-    if (e != cudaSuccess) return e;
-    e = cudaStreamSynchronize(ctx->stream);   // tl is a host temporary
-    if (e != cudaSuccess) return e;
-    // pass 0: T1 (pool 2) = L^-1 (pool 0) x T_b(H0) (A0 pool, 1); pass 1: A0 pool = T1 x L^-1, mirrored
-    const CgParams p = pass ? cg_params(ctx, ctx->d_tiles, nullptr, (int)tl.size(), 2, 0, 1, -1, 0, 1, ctx->d_a0)
-                            : cg_params(ctx, ctx->d_tiles, nullptr, (int)tl.size(), 0, 1, 2, -1, 0, 0, t1);
-    cong_tc_kernel<<<ctx->num_sms, CG_THREADS, CG_SMEM, ctx->stream>>>(p);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
   }
-  return cudaSuccess;
-}
-
-// L^-1 of every block (mixed paths) by 128-row block rows, X = L^-1 and its transpose Y = X^T:
-//   X_ii = L_ii^-1 (SIMT, trinv_tile_kernel<true>, which also writes Y_ii and zeroes the strict upper
-//   blocks), then for i = 1, 2, ...:
-//   R_ic^T = sum_{k=c}^{i-1} Y_ck L_ik^T   and   X_ic = -X_ii R_ic  (Y_ci = X_ic^T stored beside it)
-// for every c < i, as 3 x TF32 tensor-core products over tile lists (two launches per block row: the
-// second needs the first's R^T, the next row needs this row's X and Y).  Y lives in the T1 pool (T1 is
-// formed after the inverse), R^T in the scratch after the FP32 factor.
-cudaError_t launch_trinv_tc(nolsm_ctx* ctx, const float* l32, float* ypool) {
   int max_nb = 0;
   for (const auto& bd : ctx->h_blocks) max_nb = std::max(max_nb, bd.n_pad / TM);
-  trinv_diag_launch(ctx, l32, ypool, max_nb);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || max_nb < 2) return e;
-  if ((e = cg_maps(ctx, ypool)) != cudaSuccess) return e;
-  std::vector<Tile> tl;
-  std::vector<int32_t> kb;
-  std::vector<int64_t> start;   // launch k covers [start[k], start[k + 1])
   for (int i = 1; i < max_nb; ++i)
     for (int prod = 0; prod < 2; ++prod) {
       start.push_back((int64_t)tl.size());
@@ -2813,18 +2798,60 @@ cudaError_t launch_trinv_tc(nolsm_ctx* ctx, const float* l32, float* ypool) {
       }
     }
   start.push_back((int64_t)tl.size());
-  if ((int64_t)tl.size() > ctx->max_tiles) return cudaErrorInvalidValue;
-  e = cudaMemcpyAsync(ctx->d_tiles, tl.data(), tl.size() * sizeof(Tile), cudaMemcpyHostToDevice, ctx->stream);
+  if ((int64_t)tl.size() > ctx->bt_cap) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemcpyAsync(ctx->d_bt, tl.data(), tl.size() * sizeof(Tile), cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ctx->d_cg_kbeg, kb.data(), kb.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);   // host temporaries
   if (e != cudaSuccess) return e;
+  ctx->bt_start.swap(start);
+  ctx->bt_layout = ctx->h_blocks;
+  ctx->bt_dev = ctx->d_bt;
+  ctx->bt_kdev = ctx->d_cg_kbeg;
+  return cudaSuccess;
+}
+
+// The congruence on the tensor cores over launches 0 and 1 of the build's tile lists; the second
+// pass mirrors its output.
+cudaError_t launch_congruence_tc(nolsm_ctx* ctx, float* t1) {
+  cudaError_t e = cg_maps(ctx, t1);
+  if (e == cudaSuccess) e = build_tile_lists(ctx);
+  if (e != cudaSuccess) return e;
+  for (int pass = 0; pass < 2; ++pass) {
+    const int n = (int)(ctx->bt_start[pass + 1] - ctx->bt_start[pass]);
+    const Tile* t = ctx->d_bt + ctx->bt_start[pass];
+    // pass 0: T1 (pool 2) = L^-1 (pool 0) x T_b(H0) (A0 pool, 1); pass 1: A0 pool = T1 x L^-1, mirrored
+    const CgParams p = pass ? cg_params(ctx, t, nullptr, n, 2, 0, 1, -1, 0, 1, ctx->d_a0)
+                            : cg_params(ctx, t, nullptr, n, 0, 1, 2, -1, 0, 0, t1);
+    cong_tc_kernel<<<ctx->num_sms, CG_THREADS, CG_SMEM, ctx->stream>>>(p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// L^-1 of every block (mixed paths) by 128-row block rows, X = L^-1 and its transpose Y = X^T:
+//   X_ii = L_ii^-1 (trinv_diag_launch: the 128 x 128 diagonal blocks, which also writes Y_ii and
+//   zeroes the strict upper blocks), then for i = 1, 2, ...:
+//   R_ic^T = sum_{k=c}^{i-1} Y_ck L_ik^T   and   X_ic = -X_ii R_ic  (Y_ci = X_ic^T stored beside it)
+// for every c < i, as 3 x TF32 tensor-core products over launches 2, 3, ... of the build's tile lists
+// (two launches per block row: the second needs the first's R^T, the next row needs this row's X and
+// Y).  Y lives in the T1 pool (T1 is formed after the inverse), R^T in the scratch after the FP32
+// factor.
+cudaError_t launch_trinv_tc(nolsm_ctx* ctx, const float* l32, float* ypool) {
+  int max_nb = 0;
+  for (const auto& bd : ctx->h_blocks) max_nb = std::max(max_nb, bd.n_pad / TM);
+  trinv_diag_launch(ctx, l32, ypool, max_nb);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || max_nb < 2) return e;
+  if ((e = cg_maps(ctx, ypool)) != cudaSuccess) return e;
+  if ((e = build_tile_lists(ctx)) != cudaSuccess) return e;
   float* rt = const_cast<float*>(l32) + ctx->sum_sq;
-  for (size_t k = 0; k + 1 < start.size(); ++k) {
-    const int n = (int)(start[k + 1] - start[k]);
+  for (size_t k = 2; k + 1 < ctx->bt_start.size(); ++k) {
+    const int n = (int)(ctx->bt_start[k + 1] - ctx->bt_start[k]);
     if (n == 0) continue;
-    const Tile* t = ctx->d_tiles + start[k];
-    const int32_t* kp = ctx->d_cg_kbeg + start[k];
+    const Tile* t = ctx->d_bt + ctx->bt_start[k];
+    const int32_t* kp = ctx->d_cg_kbeg + ctx->bt_start[k];
     // pools: 0 X = L^-1, 2 Y, 3 L, 4 R^T
     const CgParams p = (k % 2 == 0) ? cg_params(ctx, t, kp, n, 2, 3, 4, -1, 0, 0, rt)
                                     : cg_params(ctx, t, kp, n, 0, 4, 0, 2, 1, 0, ctx->d_linv);
@@ -2838,7 +2865,7 @@ cudaError_t launch_trinv_tc(nolsm_ctx* ctx, const float* l32, float* ypool) {
 int tc_tile_n() { return TN; }
 
 // Work items (block, 32-column chunk) of every panel's trailing update, two tensor maps over the
-// slice planes (7 n_pad rows of 64 BF16 per block, blocks in layout order) and two per bin over the
+// slice planes (OZ_NSL n_pad rows of 64 BF16 per block, blocks in layout order) and two per bin over the
 // double-float pool the factor is computed in (ctx->d_sb).
 cudaError_t oz_prepare(nolsm_ctx* ctx) {
   auto encode = get_encode();
@@ -2932,10 +2959,10 @@ cudaError_t oz_prepare(nolsm_ctx* ctx) {
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   }
-  cudaError_t e = cudaMemcpyAsync(ctx->d_oz_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(),
-                                  cudaMemcpyHostToDevice, ctx->stream);
-  if (e != cudaSuccess) return e;
-  e = cudaStreamSynchronize(ctx->stream);   // maps is a host temporary
+  ctx->h_oz_maps.assign(reinterpret_cast<const uint8_t*>(maps.data()),
+                        reinterpret_cast<const uint8_t*>(maps.data() + maps.size()));
+  cudaError_t e = cudaMemcpyAsync(ctx->d_oz_tmaps, ctx->h_oz_maps.data(), ctx->h_oz_maps.size(),
+                                  cudaMemcpyHostToDevice, ctx->stream);   // source kept in the context
   if (e != cudaSuccess) return e;
   static bool attr_done = false;
   if (!attr_done) {
