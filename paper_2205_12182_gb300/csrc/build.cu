@@ -88,9 +88,11 @@ __global__ void gather_kernel(const BlockDesc* __restrict__ blocks, const int32_
 
 // The same gather for blocks up to n_pad kGatherRowMax, written row by row: a warp assembles a dense
 // row of T_b(H0) and T_b(S) in its own shared-memory buffer (zeros, the row's stored entries, the
-// unit diagonal on the padding) and writes it once with 16-byte stores, so every byte of the two
-// pools is written once and coalesced.  Dynamic shared memory: I_b, then per warp n_pad floats and
-// n_pad 8-byte entries.
+// unit diagonal on the padding) and writes it once with 16-byte stores, so every byte written is
+// written once and coalesced.  In the double-float modes only the lower triangle of T_b(S) (up to the
+// pair that holds the diagonal) is written: the factor reads no other entry (the trailing updates'
+// boxes that reach above the diagonal are read and written back unused).  Dynamic shared memory: I_b,
+// then per warp n_pad floats and n_pad 8-byte entries.
 constexpr int kGatherRowMax = 2048;
 constexpr int kGatherWarps = 8;
 __global__ void __launch_bounds__(kGatherWarps * 32) gather_rows_kernel(
@@ -147,7 +149,8 @@ __global__ void __launch_bounds__(kGatherWarps * 32) gather_rows_kernel(
     float4* H = reinterpret_cast<float4*>(hb + bd.off_mat + (int64_t)p * ld);
     float4* S = reinterpret_cast<float4*>(sb + bd.off_mat + (int64_t)p * ld);
     for (int c = lane; c < ld / 4; c += 32) H[c] = reinterpret_cast<const float4*>(hrow)[c];
-    for (int c = lane; c < ld / 2; c += 32) S[c] = reinterpret_cast<const float4*>(srow)[c];
+    const int s_end = pairs ? p / 2 + 1 : ld / 2;   // 16-byte units (two entries) of row p written
+    for (int c = lane; c < s_end; c += 32) S[c] = reinterpret_cast<const float4*>(srow)[c];
     __syncwarp();
   }
 }
