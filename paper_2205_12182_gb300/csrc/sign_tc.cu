@@ -1823,14 +1823,22 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) chol_update_kernel(const __grid
         const int ecl = cl < n ? ex[cl] : 0;
         uint8_t* cbox = smem + OZ_C_OFF + cb * OZ_C_BYTES + half * OZ_CBOX_BYTES;   // 128 rows x 16 pairs
         const int crow = q * 32 + lane;           // this lane's row in the box
+        // both 8-column chunks' levels are loaded before one wait (a chunk above every row of this
+        // warp is skipped; warp-uniform)
+        uint32_t vv[2][OZ_NSL][8];
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) {
+          if (n0 + half * 16 + ch * 8 > rw0 + 31) continue;
+          const uint32_t tb = tmem_base + (uint32_t)(acc * OZ_ACC + half * 16 + ch * 8) + ((uint32_t)(q * 32) << 16);
+#pragma unroll
+          for (int l = 0; l < OZ_NSL; ++l) tmem_ld8(tb + (uint32_t)(l * OZ_TN), vv[ch][l]);
+        }
+        tmem_wait_ld();
+#pragma unroll
         for (int ch = 0; ch < 2; ++ch) {
           const int c0 = n0 + half * 16 + ch * 8;
           if (c0 > rw0 + 31) continue;            // chunk above every row of this warp (uniform)
-          uint32_t v[OZ_NSL][8];
-          const uint32_t tb = tmem_base + (uint32_t)(acc * OZ_ACC + half * 16 + ch * 8) + ((uint32_t)(q * 32) << 16);
-#pragma unroll
-          for (int l = 0; l < OZ_NSL; ++l) tmem_ld8(tb + (uint32_t)(l * OZ_TN), v[l]);
-          tmem_wait_ld();
+          const uint32_t (&v)[OZ_NSL][8] = vv[ch];
           int ec[8];                              // every lane takes part in the shuffles
 #pragma unroll
           for (int j = 0; j < 8; ++j) ec[j] = __shfl_sync(0xffffffffu, ecl, ch * 8 + j);
