@@ -88,10 +88,10 @@ typedef enum nolsm_chol_precision {
   NOLSM_CHOL_FP32 = 1,          /* factor and inverse in FP32 */
   NOLSM_CHOL_FP64_INV64 = 2,    /* factor and inverse in FP64 */
   NOLSM_CHOL_DF64 = 3,          /* factor in double-float pairs (Dekker; 48-bit significand), stored as
-                                   FP64; inverse in FP32.  Blocked by 64-column panels: each panel on
-                                   the FP32 pipe (FP64 32x32 diagonal blocks), the trailing updates on the
-                                   tensor cores from exact 8-bit slices of the factor (Ozaki scheme, 48
-                                   bits).  The factor feeds the rest of the path through its FP32
+                                   FP64; inverse in FP32.  Blocked by 64-column panels: each panel's
+                                   64x64 diagonal block in double-float on the FP32 pipe, the rows
+                                   below it and the trailing updates on the tensor cores from exact
+                                   8-bit slices (Ozaki scheme, 48 bits).  The factor feeds the rest of the path through its FP32
                                    rounding (and the trace slab), where it agrees with the FP64 factor */
   NOLSM_CHOL_DF64_SIMT = 4      /* the same double-float factor with every update on the FP32 pipe
                                    (one left-looking launch) */
