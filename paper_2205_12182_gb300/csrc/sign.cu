@@ -851,9 +851,20 @@ __global__ void __launch_bounds__(256) density_slab_kernel(const BlockDesc* __re
   for (int c0 = 0; c0 < c; c0 += 8) {
     AccSel<COMP> acc[4];
     for (int k0 = r0; k0 < ld; k0 += 32) {
-      for (int e = tid; e < 32 * 128; e += blockDim.x) {
-        const int kk = e >> 7, ii = e & 127;
-        Ls[kk][ii] = Li[(int64_t)(k0 + kk) * ld + r0 + ii];
+      {
+        // all sixteen loads of the thread are issued before the first store (256 threads, one
+        // 128-byte row segment per warp and load)
+        float lv[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          const int e = tid + 256 * t;
+          lv[t] = Li[(int64_t)(k0 + (e >> 7)) * ld + r0 + (e & 127)];
+        }
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          const int e = tid + 256 * t;
+          Ls[e >> 7][e & 127] = lv[t];
+        }
       }
       {
         const int kk = tid >> 3, cc = tid & 7;
