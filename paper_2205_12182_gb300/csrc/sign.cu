@@ -848,34 +848,35 @@ __global__ void __launch_bounds__(256) density_slab_kernel(const BlockDesc* __re
   float* Dsl = dslab + bd.off_slab;
   const int tid = threadIdx.x;
   const int row = tid >> 1, cb = (tid & 1) * 4;
+  // a thread's sixteen L^-1 loads of a 32-row step (one 128-byte row segment per warp and load) and
+  // its Y load are issued one step ahead, before the current step's products
+  auto load_step = [&](int k0, int c0, float (&lv)[16], float& yv) {
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      const int e = tid + 256 * t;
+      lv[t] = Li[(int64_t)(k0 + (e >> 7)) * ld + r0 + (e & 127)];
+    }
+    const int kk = tid >> 3, cc = tid & 7;
+    yv = (c0 + cc < c) ? Y[(int64_t)(c0 + cc) * ld + k0 + kk] : 0.f;
+  };
   for (int c0 = 0; c0 < c; c0 += 8) {
     AccSel<COMP> acc[4];
+    float lv[16], yv;
+    load_step(r0, c0, lv, yv);
     for (int k0 = r0; k0 < ld; k0 += 32) {
-      {
-        // all sixteen loads of the thread are issued before the first store (256 threads, one
-        // 128-byte row segment per warp and load)
-        float lv[16];
 #pragma unroll
-        for (int t = 0; t < 16; ++t) {
-          const int e = tid + 256 * t;
-          lv[t] = Li[(int64_t)(k0 + (e >> 7)) * ld + r0 + (e & 127)];
-        }
-#pragma unroll
-        for (int t = 0; t < 16; ++t) {
-          const int e = tid + 256 * t;
-          Ls[e >> 7][e & 127] = lv[t];
-        }
+      for (int t = 0; t < 16; ++t) {
+        const int e = tid + 256 * t;
+        Ls[e >> 7][e & 127] = lv[t];
       }
-      {
-        const int kk = tid >> 3, cc = tid & 7;
-        Vs[kk][cc] = (c0 + cc < c) ? Y[(int64_t)(c0 + cc) * ld + k0 + kk] : 0.f;
-      }
+      Vs[tid >> 3][tid & 7] = yv;
       __syncthreads();
+      if (k0 + 32 < ld) load_step(k0 + 32, c0, lv, yv);
 #pragma unroll 8
       for (int kk = 0; kk < 32; ++kk) {
-        const float lv = Ls[kk][row];
+        const float l = Ls[kk][row];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q].add_prod(lv, Vs[kk][cb + q]);
+        for (int q = 0; q < 4; ++q) acc[q].add_prod(l, Vs[kk][cb + q]);
       }
       __syncthreads();
     }
