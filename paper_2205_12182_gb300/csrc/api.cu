@@ -164,6 +164,7 @@ void release_pools(nolsm_ctx* ctx) {
   dfree(ctx->d_extra); ctx->d_extra = nullptr;
   dfree(ctx->d_nb); ctx->d_nb = nullptr;
   dfree(ctx->d_tmaps); ctx->d_tmaps = nullptr;
+  ctx->tmap_cap = 0;
   dfree(ctx->d_cg_tmaps); ctx->d_cg_tmaps = nullptr;
   ctx->cg_tmap_cap = 0;
   ctx->cg_maps_gen = -1;
@@ -588,6 +589,9 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
     if (st_l != NOLSM_OK) return st_l;
   }
   CK(phase_mark(ctx, -1));
+  // the products' tensor maps are encoded on the host while the build's kernels still run (the
+  // upload follows them on the stream)
+  if (mixed) CK(tc_prepare(ctx));
   nolsm_status st = check_device_flags(ctx);
   harvest_phases(ctx);
   if (st != NOLSM_OK) return st;
@@ -597,7 +601,6 @@ nolsm_status nolsm_build_submatrices(nolsm_ctx* ctx, const nolsm_csr* H, const n
   CK(cudaMemcpy(ctx->h_hi.data(), ctx->d_hi, sizeof(double) * n_blocks, cudaMemcpyDeviceToHost));
   ctx->h_own_diag.resize((size_t)ctx->sum_own);
   CK(cudaMemcpy(ctx->h_own_diag.data(), ctx->d_own_diag, sizeof(float) * ctx->sum_own, cudaMemcpyDeviceToHost));
-  if (mixed) CK(tc_prepare(ctx));
   ctx->built = true;
   return NOLSM_OK;
 }

@@ -106,7 +106,7 @@ struct nolsm_ctx {
   const float* cg_maps_t1 = nullptr;
   // host copies of uploaded tensor maps and per-block tolerances: the sources of their asynchronous
   // uploads stay alive until the next build, so the uploads need no wait on the stream
-  std::vector<uint8_t> h_cg_maps, h_oz_maps;
+  std::vector<uint8_t> h_cg_maps, h_oz_maps, h_tc_maps;
   std::vector<float> h_tol;
   bool cong_simt = false;       // congruence on the SIMT FP32 products (tests compare both)
   nolsm_status sticky = NOLSM_OK;
@@ -222,6 +222,7 @@ struct nolsm_ctx {
 
   // tensor-core operand descriptors (device array of CUtensorMap, opaque bytes)
   void* d_tmaps = nullptr;
+  size_t tmap_cap = 0;            // capacity of d_tmaps, in maps
   int n_tmaps = 0;
 
   // counters (nolsm_counters): every launch through a launcher, and event pairs around the

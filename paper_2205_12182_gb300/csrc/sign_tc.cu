@@ -2597,13 +2597,21 @@ cudaError_t tc_prepare(nolsm_ctx* ctx) {
       if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     }
   }
-  if (ctx->d_tmaps) cudaFree(ctx->d_tmaps);
-  cudaError_t e = cudaMalloc(&ctx->d_tmaps, maps.size() * sizeof(CUtensorMap));
-  if (e != cudaSuccess) return e;
+  // the device copy keeps its allocation across builds (it only grows), and the upload's source lives
+  // in the context until the next build, so a build neither frees nor waits here
+  cudaError_t e = cudaSuccess;
+  if (ctx->tmap_cap < maps.size()) {
+    if (ctx->d_tmaps) cudaFree(ctx->d_tmaps);
+    ctx->d_tmaps = nullptr;
+    ctx->tmap_cap = 0;
+    e = cudaMalloc(&ctx->d_tmaps, maps.size() * sizeof(CUtensorMap));
+    if (e != cudaSuccess) return e;
+    ctx->tmap_cap = maps.size();
+  }
   ctx->n_tmaps = (int)maps.size();
-  e = cudaMemcpyAsync(ctx->d_tmaps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, ctx->stream);
-  if (e != cudaSuccess) return e;
-  e = cudaStreamSynchronize(ctx->stream);
+  ctx->h_tc_maps.assign(reinterpret_cast<const uint8_t*>(maps.data()),
+                        reinterpret_cast<const uint8_t*>(maps.data() + maps.size()));
+  e = cudaMemcpyAsync(ctx->d_tmaps, ctx->h_tc_maps.data(), ctx->h_tc_maps.size(), cudaMemcpyHostToDevice, ctx->stream);
   if (e != cudaSuccess) return e;
   static bool attr_done = false;
   if (!attr_done) {
